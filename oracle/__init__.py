@@ -1,0 +1,194 @@
+"""CPU FP64 oracle of the FMM cell-interaction passes -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, the package's ``smoke()`` check and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never imports, links or
+calls it, and the two share no code; both read their inputs from ``synth``.
+
+The arithmetic lives in ``ot_oracle.c`` (plain C, FP64, compiled without fast
+math or FMA contraction); this module only builds it and marshals numpy arrays.
+See ``ot_oracle.c`` for the formulas and the passage of the paper each follows.
+
+Parity pins (tests/test_oracle_*.py) check it against sympy derivatives,
+exact polynomial integrals, brute-force point-mass sums, closed-form
+potentials and conservation invariants.  The angular-momentum correction is
+pinned only by its antisymmetry (Newton III) and by its being the missing
+order-(1,3) gradient term: parity unpinned beyond that.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ot_oracle.c")
+_LIB = os.path.join(_HERE, "libot_oracle.so")
+_lib = None
+
+NCOMP = 20
+NCELL = 512
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no fast math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
+               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    lib.oracle_D.argtypes = [P, P]
+    lib.oracle_D.restype = None
+    lib.oracle_comp_exponents.argtypes = [I, P]
+    lib.oracle_comp_exponents.restype = I
+    lib.oracle_moments.argtypes = [I, P, P, P, ctypes.c_double, P, P]
+    lib.oracle_moments.restype = I
+    lib.oracle_pass.argtypes = [I, P, P, P, ctypes.c_double, P, P, I, I, P, P, P, P, P]
+    lib.oracle_pass.restype = ctypes.c_longlong
+    lib.oracle_pass_adjoint.argtypes = [I, P, P, P, ctypes.c_double, I, P, P, P]
+    lib.oracle_pass_adjoint.restype = I
+    lib.oracle_l2l.argtypes = [P, P, P]
+    lib.oracle_l2l.restype = None
+    lib.oracle_full_solve.argtypes = [I, P, P, P, ctypes.c_double, P, P]
+    lib.oracle_full_solve.restype = I
+    lib.oracle_set_threads.argtypes = [I]
+    lib.oracle_set_threads.restype = None
+    lib.oracle_get_threads.argtypes = []
+    lib.oracle_get_threads.restype = I
+    _lib = lib
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _tree_args(tree):
+    level = np.ascontiguousarray(tree.level, dtype=np.int32)
+    coord = np.ascontiguousarray(tree.coord, dtype=np.int32)
+    leaf = np.ascontiguousarray(tree.is_leaf, dtype=np.uint8)
+    return level, coord, leaf
+
+
+def set_threads(k: int) -> None:
+    _load().oracle_set_threads(int(k))
+
+
+def get_threads() -> int:
+    return int(_load().oracle_get_threads())
+
+
+def component_exponents():
+    """[35, 3] exponent triples of the stored components (ranks 0..4)."""
+    lib = _load()
+    out = np.zeros((35, 3), dtype=np.int32)
+    e = np.zeros(3, dtype=np.int32)
+    for c in range(35):
+        lib.oracle_comp_exponents(c, _p(e))
+        out[c] = e
+    return out
+
+
+def D(R) -> np.ndarray:
+    """Derivatives of G = -1/r of orders 0..4 at R (35 stored components)."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    out = np.zeros(35)
+    _load().oracle_D(_p(R), _p(out))
+    return out
+
+
+def moments(tree, rho) -> np.ndarray:
+    """[n, 20, 512] cell moments: uniform-cube moments for childless nodes,
+    exact M2M of the children otherwise."""
+    level, coord, leaf = _tree_args(tree)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    M = np.zeros((tree.n, NCOMP, NCELL))
+    _load().oracle_moments(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(rho), _p(M))
+    return M
+
+
+def run_pass(tree, pass_kind: str, M=None, m=None, targets=None):
+    """Evaluate one pass for the listed targets ([k, 2] node, cell) or all cells.
+
+    Returns dict(L=[k,20], S=[k,20], npairs=int) plus Lc, Sc ([k,3]) for the
+    multipole pass.  ``pass_kind`` is "multipole" (sources = non-leaf cells,
+    uses M) or "monopole" (sources = leaf cells and virtual descendants of
+    coarser leaves, uses m)."""
+    level, coord, leaf = _tree_args(tree)
+    kind = {"multipole": 1, "monopole": 2}[pass_kind]
+    if targets is None:
+        nt = tree.n * NCELL
+        tg = None
+    else:
+        tg = np.ascontiguousarray(targets, dtype=np.int32).reshape(-1, 2)
+        nt = tg.shape[0]
+    Mv = np.ascontiguousarray(M, dtype=np.float64) if M is not None else None
+    mv = np.ascontiguousarray(m, dtype=np.float64) if m is not None else None
+    if kind == 1 and Mv is None:
+        raise ValueError("multipole pass needs M")
+    if kind == 2 and mv is None:
+        raise ValueError("monopole pass needs m")
+    L = np.zeros((nt, NCOMP))
+    S = np.zeros((nt, NCOMP))
+    Lc = np.zeros((nt, 3))
+    Sc = np.zeros((nt, 3))
+    npairs = _load().oracle_pass(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Mv), _p(mv), kind,
+                                 nt, _p(tg), _p(L), _p(Lc), _p(S), _p(Sc))
+    out = dict(L=L, S=S, npairs=int(npairs))
+    if kind == 1:
+        out.update(Lc=Lc, Sc=Sc)
+    return out
+
+
+def run_pass_grid(tree, pass_kind, M=None, m=None):
+    """All cells; returns L [n,20,512] (and Lc [n,3,512]) in the library layout."""
+    r = run_pass(tree, pass_kind, M=M, m=m)
+    n = tree.n
+    out = dict(L=r["L"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(),
+               S=r["S"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(), npairs=r["npairs"])
+    if "Lc" in r:
+        out["Lc"] = r["Lc"].reshape(n, NCELL, 3).transpose(0, 2, 1).copy()
+        out["Sc"] = r["Sc"].reshape(n, NCELL, 3).transpose(0, 2, 1).copy()
+    return out
+
+
+def pass_adjoint(tree, pass_kind: str, Lbar):
+    """Transposed sum of a pass: Mbar [n,20,512] (multipole) or mbar [n,512]."""
+    level, coord, leaf = _tree_args(tree)
+    kind = {"multipole": 1, "monopole": 2}[pass_kind]
+    Lbar = np.ascontiguousarray(Lbar, dtype=np.float64)
+    Mbar = np.zeros((tree.n, NCOMP, NCELL))
+    mbar = np.zeros((tree.n, NCELL))
+    _load().oracle_pass_adjoint(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, kind, _p(Lbar),
+                                _p(Mbar), _p(mbar))
+    return Mbar if kind == 1 else mbar
+
+
+def l2l(Lp, d) -> np.ndarray:
+    Lp = np.ascontiguousarray(Lp, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    out = np.zeros(NCOMP)
+    _load().oracle_l2l(_p(Lp), _p(d), _p(out))
+    return out
+
+
+def full_solve(tree, rho) -> np.ndarray:
+    """[n, 20, 512] total local expansion of every cell (potential = [:, 0])."""
+    level, coord, leaf = _tree_args(tree)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    L = np.zeros((tree.n, NCOMP, NCELL))
+    _load().oracle_full_solve(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(rho), _p(L))
+    return L

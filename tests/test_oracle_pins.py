@@ -1,0 +1,510 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each pin is chosen so that a plausible mistake (a dropped term, a wrong sign,
+factorial or multiplicity, a transposed index, a missed or doubled pair)
+fails at least one of them:
+
+* Green's-function derivatives against sympy's symbolic differentiation.
+* Cell moments and their M2M shift against exact polynomial integrals.
+* Every term of the n + m <= 3 contraction against brute-force point
+  clusters: the error of the local Taylor model must fall as the 4th power
+  of the cluster and evaluation radius (a wrong order-k term leaves an error
+  of order k <= 3).  The angular-momentum term must lift the order of the
+  gradient and force errors from 3 to 4 the same way.
+* Newton's third law over closed pair sets; harmonicity of the expansions.
+* Pair coverage: a single point mass through the full multilevel solve must
+  give -1/r at every other leaf cell (a missed or doubled pair would not).
+* Full solve against the brute-force pairwise sum and against the closed-form
+  potential of a uniform sphere.
+* The transposed sums against the forward passes (dot-product identity).
+* Virtual descendants of a coarse leaf against explicitly refined leaves.
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import sympy
+
+import synth
+
+# storage order of the 20 (35) components: sorted index tuples, lexicographic
+def _exps(maxrank=4):
+    out = []
+    for k in range(maxrank + 1):
+        for t in itertools.combinations_with_replacement(range(3), k):
+            out.append(tuple(t.count(a) for a in range(3)))
+    return out
+
+
+EXPS = _exps(4)
+EXP20 = EXPS[:20]
+RANK = np.array([sum(e) for e in EXPS])
+
+
+def _fact(e):
+    return math.factorial(e[0]) * math.factorial(e[1]) * math.factorial(e[2])
+
+
+def taylor(L, delta):
+    """sum over stored J of L[J] delta^J / J!  (the local expansion)."""
+    return sum(L[c] * np.prod(np.power(delta, EXP20[c])) / _fact(EXP20[c]) for c in range(20))
+
+
+def point_cluster_moments(mu, pos, centre):
+    """Raw moments sum mu (y - X)^K of point masses (definition of a moment)."""
+    d = pos - centre
+    return np.array([np.sum(mu * np.prod(d ** np.array(e), axis=1)) for e in EXP20])
+
+
+# ---------------------------------------------------------------------------
+# derivatives of G = -1/r
+# ---------------------------------------------------------------------------
+
+def test_component_order_matches_storage_convention(orc):
+    assert orc.component_exponents().tolist() == [list(e) for e in EXPS]
+
+
+@pytest.mark.parametrize("R", [(1, 2, 2), (3, -4, 12), (-2, 3, 6), (1, 1, 1), (0, 0, 5), (-7, 0, 3)])
+def test_D_matches_sympy(orc, R):
+    x, y, z = sympy.symbols("x y z", real=True)
+    G = -1 / sympy.sqrt(x ** 2 + y ** 2 + z ** 2)
+    sub = {x: sympy.Integer(R[0]), y: sympy.Integer(R[1]), z: sympy.Integer(R[2])}
+    got = orc.D(np.array(R, dtype=float))
+    for c, e in enumerate(EXPS):
+        expr = sympy.diff(G, x, e[0], y, e[1], z, e[2])
+        exact = float(sympy.N(expr.subs(sub), 40))
+        scale = 1.0 / np.linalg.norm(R) ** (RANK[c] + 1)
+        assert abs(got[c] - exact) <= 1e-14 * max(abs(exact), scale), (R, e, got[c], exact)
+
+
+# ---------------------------------------------------------------------------
+# moments
+# ---------------------------------------------------------------------------
+
+def _axis_int(e, lo, hi):
+    """exact int_lo^hi t^e dt with Fractions"""
+    return (Fraction(hi) ** (e + 1) - Fraction(lo) ** (e + 1)) / (e + 1)
+
+
+def test_cube_moments_exact(orc):
+    tree = synth.single_subgrid(level=2, h=0.5, leaf=True)
+    rho = np.full((1, 512), 1.75)
+    M = orc.moments(tree, rho)
+    h = Fraction(1, 2)
+    for c, e in enumerate(EXP20):
+        exact = Fraction(7, 4)
+        for a in range(3):
+            exact *= _axis_int(e[a], -h / 2, h / 2)
+        assert M[0, c, 77] == pytest.approx(float(exact), rel=1e-15, abs=1e-300)
+
+
+def test_m2m_matches_exact_integrals(orc):
+    tree = synth.uniform_tree(1, h_leaf=1.0)     # root (h=2) + 8 leaves (h=1)
+    rng = np.random.default_rng(11)
+    rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    M = orc.moments(tree, rho)
+    idx = tree.index()
+    root = idx[(0, 0, 0, 0)]
+    for cell in (0, 9, 200, 511):
+        gp = np.array([cell % 8, (cell // 8) % 8, cell // 64])
+        XP = (gp + 0.5) * 2.0
+        exact = np.zeros(20)
+        for b in itertools.product((0, 1), repeat=3):
+            gc = 2 * gp + np.array(b)
+            node = idx[(1, *(gc // 8))]
+            cc = int((gc % 8) @ np.array([1, 8, 64]))
+            lo = gc * 1.0 - XP
+            for c, e in enumerate(EXP20):
+                v = Fraction(rho[node, cc])
+                for a in range(3):
+                    v *= _axis_int(e[a], Fraction(lo[a]), Fraction(lo[a] + 1))
+                exact[c] += float(v)
+        np.testing.assert_allclose(M[root, :, cell], exact, rtol=1e-13, atol=1e-13 * exact[0])
+
+
+# ---------------------------------------------------------------------------
+# the contraction, term by term, against brute-force point clusters
+# ---------------------------------------------------------------------------
+
+def _single_node_tree():
+    return synth.single_subgrid(level=1, h=1.0, leaf=False)   # h = 1 cells, no halo
+
+
+def _cell(i, j, k):
+    return i + 8 * j + 64 * k
+
+
+def _order(errs, scales):
+    return np.polyfit(np.log(scales), np.log(errs), 1)[0]
+
+
+def _cluster(rng, k=7):
+    mu = rng.uniform(0.2, 1.0, size=k)
+    u = rng.standard_normal((k, 3))
+    return mu, u
+
+
+def test_multipole_pass_taylor_order(orc):
+    """L from the multipole pass reproduces the direct potential of a random
+    point cluster with error O(s^4) when the cluster radius and the
+    evaluation offset both scale with s."""
+    tree = _single_node_tree()
+    rng = np.random.default_rng(5)
+    mu, u = _cluster(rng)
+    A, B = (0, 0, 0), (4, 1, 0)          # |o|^2 = 17 > 12, parents at (2,0,0): far
+    XA, XB = np.array(A) + 0.5, np.array(B) + 0.5
+    dirs = rng.standard_normal((6, 3))
+    errs, scales = [], [0.4, 0.2, 0.1, 0.05]
+    for s in scales:
+        M = np.zeros((1, 20, 512))
+        pos = XB + s * u
+        M[0, :, _cell(*B)] = point_cluster_moments(mu, pos, XB)
+        r = orc.run_pass(tree, "multipole", M=M, targets=[[0, _cell(*A)]])
+        L = r["L"][0]
+        e = 0.0
+        for d in dirs:
+            delta = s * d / np.linalg.norm(d)
+            exact = -np.sum(mu / np.linalg.norm(XA + delta - pos, axis=1))
+            e = max(e, abs(taylor(L, delta) - exact))
+        errs.append(e)
+    order = _order(errs, scales)
+    assert 3.7 < order < 4.4, (errs, order)
+
+
+def test_multipole_pass_exact_for_point_masses(orc):
+    """With point masses (no higher moments) every L[J] is an exact derivative,
+    so L[0] equals the direct sum -sum m / r to rounding."""
+    tree = _single_node_tree()
+    rng = np.random.default_rng(6)
+    M = np.zeros((1, 20, 512))
+    M[0, 0] = rng.uniform(0.5, 1.5, 512)
+    A = _cell(3, 4, 2)
+    r = orc.run_pass(tree, "multipole", M=M, targets=[[0, A]])
+    gA = np.array([3, 4, 2])
+    exact = 0.0
+    n = 0
+    for c in range(512):
+        g = np.array([c % 8, (c // 8) % 8, c // 64])
+        o = g - gA
+        n2 = o @ o
+        op = np.floor_divide(gA % 2 + o, 2)
+        if n2 > 12 and op @ op <= 12:
+            exact -= M[0, 0, c] / math.sqrt(n2)
+            n += 1
+    assert r["npairs"] == n
+    assert r["L"][0, 0] == pytest.approx(exact, rel=1e-14)
+
+
+def test_monopole_pass_taylor_order(orc):
+    """Point-mass sources: the only error of the local model is the degree-3
+    truncation in the evaluation offset, O(s^4)."""
+    tree = synth.single_subgrid(level=1, h=1.0, leaf=True)
+    rng = np.random.default_rng(7)
+    m = np.zeros((1, 512))
+    srcs = [(5, 1, 2), (0, 6, 6), (3, 2, 3)]   # two far, one near
+    for s_ in srcs:
+        m[0, _cell(*s_)] = rng.uniform(0.5, 1.5)
+    A = (1, 2, 3)
+    XA = np.array(A) + 0.5
+    r = orc.run_pass(tree, "monopole", m=m, targets=[[0, _cell(*A)]])
+    L = r["L"][0]
+    dirs = rng.standard_normal((6, 3))
+    errs, scales = [], [0.4, 0.2, 0.1, 0.05]
+    for s in scales:
+        e = 0.0
+        for d in dirs:
+            delta = s * d / np.linalg.norm(d)
+            exact = -sum(m[0, _cell(*q)] / np.linalg.norm(XA + delta - (np.array(q) + 0.5)) for q in srcs)
+            e = max(e, abs(taylor(L, delta) - exact))
+        errs.append(e)
+    order = _order(errs, scales)
+    assert 3.7 < order < 4.4, (errs, order)
+
+
+def _force(Mt, L, Lc=None):
+    """F_i = -(M0 L_i + sum_j M_j L_ij + 1/2 sum_jk M_jk L_ijk) - m Lc_i,
+    full index sums over the stored symmetric components."""
+    comp = {e: c for c, e in enumerate(EXP20)}
+
+    def key(*idx):
+        e = [0, 0, 0]
+        for a in idx:
+            e[a] += 1
+        return comp[tuple(e)]
+    F = np.zeros(3)
+    for i in range(3):
+        f = Mt[0] * L[key(i)]
+        for j in range(3):
+            f += Mt[key(j)] * L[key(i, j)]
+        for j in range(3):
+            for k in range(3):
+                f += 0.5 * Mt[key(j, k)] * L[key(i, j, k)]
+        if Lc is not None:
+            f += Mt[0] * Lc[i]
+        F[i] = -f
+    return F
+
+
+def test_angular_term_lifts_gradient_order(orc):
+    """A point-mass target and a random-cluster source: L1 alone has an O(s^3)
+    gradient error (the source octupole term is truncated); L1 + Lc is O(s^4)."""
+    tree = _single_node_tree()
+    rng = np.random.default_rng(8)
+    mu, u = _cluster(rng)
+    A, B = (0, 0, 0), (4, 1, 0)
+    XA, XB = np.array(A) + 0.5, np.array(B) + 0.5
+    e1, e2, scales = [], [], [0.4, 0.2, 0.1, 0.05]
+    for s in scales:
+        M = np.zeros((1, 20, 512))
+        pos = XB + s * u
+        M[0, :, _cell(*B)] = point_cluster_moments(mu, pos, XB)
+        M[0, 0, _cell(*A)] = 1.0          # target: unit point mass
+        r = orc.run_pass(tree, "multipole", M=M, targets=[[0, _cell(*A)]])
+        L, Lc = r["L"][0], r["Lc"][0]
+        R = XA - pos
+        exact = np.sum(mu[:, None] * R / np.linalg.norm(R, axis=1)[:, None] ** 3, axis=0)
+        e1.append(np.max(np.abs(L[1:4] - exact)))
+        e2.append(np.max(np.abs(L[1:4] + Lc - exact)))
+    o1, o2 = _order(e1, scales), _order(e2, scales)
+    assert 2.7 < o1 < 3.4, (e1, o1)
+    assert 3.7 < o2 < 4.4, (e2, o2)
+
+
+def test_angular_term_lifts_force_order_for_cluster_target(orc):
+    """A random-cluster target and a point-mass source: the force on the target
+    cluster from the expansion has an O(s^3) error without Lc, O(s^4) with it
+    (this pins the -(m_B/m_A) M3_A part of the correction)."""
+    tree = _single_node_tree()
+    rng = np.random.default_rng(9)
+    mu, u = _cluster(rng)
+    A, B = (0, 0, 0), (4, 1, 0)
+    XA, XB = np.array(A) + 0.5, np.array(B) + 0.5
+    mB = 1.3
+    e1, e2, scales = [], [], [0.4, 0.2, 0.1, 0.05]
+    for s in scales:
+        M = np.zeros((1, 20, 512))
+        pos = XA + s * u
+        MA = point_cluster_moments(mu, pos, XA)
+        M[0, :, _cell(*A)] = MA
+        M[0, 0, _cell(*B)] = mB
+        r = orc.run_pass(tree, "multipole", M=M, targets=[[0, _cell(*A)]])
+        L, Lc = r["L"][0], r["Lc"][0]
+        R = pos - XB
+        exact = -np.sum(mu[:, None] * mB * R / np.linalg.norm(R, axis=1)[:, None] ** 3, axis=0)
+        e1.append(np.max(np.abs(_force(MA, L) - exact)))
+        e2.append(np.max(np.abs(_force(MA, L, Lc) - exact)))
+    o1, o2 = _order(e1, scales), _order(e2, scales)
+    assert 2.7 < o1 < 3.4, (e1, o1)
+    assert 3.7 < o2 < 4.4, (e2, o2)
+
+
+# ---------------------------------------------------------------------------
+# invariants
+# ---------------------------------------------------------------------------
+
+def _traces(L):
+    comp = {e: c for c, e in enumerate(EXP20)}
+    t2 = L[..., comp[(2, 0, 0)]] + L[..., comp[(0, 2, 0)]] + L[..., comp[(0, 0, 2)]]
+    t3 = [L[..., comp[(3, 0, 0)]] + L[..., comp[(1, 2, 0)]] + L[..., comp[(1, 0, 2)]],
+          L[..., comp[(2, 1, 0)]] + L[..., comp[(0, 3, 0)]] + L[..., comp[(0, 1, 2)]],
+          L[..., comp[(2, 0, 1)]] + L[..., comp[(0, 2, 1)]] + L[..., comp[(0, 0, 3)]]]
+    return t2, t3
+
+
+def test_harmonic_and_isotropic_cancellation(orc):
+    tree = _single_node_tree()
+    M = synth.random_moments(tree, seed=12)
+    r = orc.run_pass_grid(tree, "multipole", M=M)
+    L, S = r["L"], r["S"]
+    t2, t3 = _traces(L.transpose(0, 2, 1))
+    assert np.max(np.abs(t2)) <= 1e-13 * np.max(S[:, 4:10])
+    for t in t3:
+        assert np.max(np.abs(t)) <= 1e-13 * np.max(S[:, 10:20])
+    # an isotropic second moment contributes nothing
+    Mi = M.copy()
+    for c in (4, 7, 9):
+        Mi[:, c] += 0.37
+    ri = orc.run_pass_grid(tree, "multipole", M=Mi)
+    assert np.max(np.abs(ri["L"] - L)) <= 1e-13 * np.max(S)
+
+
+@pytest.mark.parametrize("with_lc", [False, True])
+def test_newton_third_law_multipole(orc, with_lc):
+    """Over a pair set closed under o -> -o (one isolated sub-grid) the
+    expansion forces sum to zero to rounding, with and without Lc."""
+    tree = _single_node_tree()
+    M = synth.random_moments(tree, seed=13)
+    r = orc.run_pass_grid(tree, "multipole", M=M)
+    L, Lc = r["L"][0].T, r["Lc"][0].T
+    F = np.array([_force(M[0, :, a], L[a], Lc[a] if with_lc else None) for a in range(512)])
+    scale = np.sum(np.abs(F))
+    assert np.max(np.abs(F.sum(axis=0))) <= 1e-13 * scale
+
+
+def test_newton_third_law_monopole_level(orc):
+    tree = synth.uniform_level(1, 1.0)     # 8 leaf sub-grids, 16^3 cells
+    rng = np.random.default_rng(14)
+    m = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    r = orc.run_pass_grid(tree, "monopole", m=m)
+    F = -(m[:, None, :] * r["L"][:, 1:4, :])
+    assert np.max(np.abs(F.sum(axis=(0, 2)))) <= 1e-13 * np.sum(np.abs(F))
+
+
+# ---------------------------------------------------------------------------
+# local-expansion shift
+# ---------------------------------------------------------------------------
+
+def test_l2l_is_exact_taylor_shift_of_cubic(orc):
+    rng = np.random.default_rng(15)
+    for _ in range(5):
+        Lp = rng.standard_normal(20)
+        d = rng.uniform(-0.7, 0.7, 3)
+        Lc = orc.l2l(Lp, d)
+        for _ in range(5):
+            delta = rng.uniform(-1, 1, 3)
+            assert taylor(Lc, delta) == pytest.approx(taylor(Lp, d + delta), rel=1e-13, abs=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# full multilevel solve
+# ---------------------------------------------------------------------------
+
+def _leaf_cells(tree):
+    pos, ids = [], []
+    for i in np.nonzero(tree.is_leaf)[0]:
+        pos.append(synth.cell_centres(tree, i))
+        ids.append(np.stack([np.full(512, i), np.arange(512)], axis=1))
+    return np.concatenate(pos), np.concatenate(ids)
+
+
+@pytest.mark.parametrize("src", [(0, 0, 0), (9, 4, 13), (15, 15, 15)])
+def test_single_mass_covered_exactly_once(orc, src):
+    """One unit point mass: the full solve must give -1/r at every other leaf
+    cell (a pair missed by the stencils would give 0, a doubled pair -2/r)."""
+    tree = synth.uniform_tree(1, 1.0)
+    pos, ids = _leaf_cells(tree)
+    idx = tree.index()
+    node = idx[(1, src[0] // 8, src[1] // 8, src[2] // 8)]
+    cell = (src[0] % 8) + 8 * (src[1] % 8) + 64 * (src[2] % 8)
+    rho = np.zeros((tree.n, 512))
+    rho[node, cell] = 1.0                       # h = 1: mass 1
+    L = orc.full_solve(tree, rho)
+    phi = L[ids[:, 0], 0, ids[:, 1]]
+    r = np.linalg.norm(pos - (np.array(src) + 0.5), axis=1)
+    mask = r > 0
+    rel = np.abs(phi[mask] + 1.0 / r[mask]) * r[mask]
+    assert np.max(rel) < 2e-2, np.max(rel)
+    assert phi[~mask][0] == 0.0
+
+
+def test_full_solve_matches_direct_sum(orc):
+    tree = synth.uniform_tree(1, 1.0)
+    rng = np.random.default_rng(16)
+    rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    L = orc.full_solve(tree, rho)
+    pos, ids = _leaf_cells(tree)
+    m = rho[ids[:, 0], ids[:, 1]]
+    sample = rng.choice(len(pos), 300, replace=False)
+    for k in sample:
+        d = np.linalg.norm(pos - pos[k], axis=1)
+        d[k] = np.inf
+        exact = -np.sum(m / d)
+        grad = np.sum(m[:, None] * (pos[k] - pos) / d[:, None] ** 3, axis=0)
+        got = L[ids[k, 0], :, ids[k, 1]]
+        assert abs(got[0] - exact) < 2e-4 * abs(exact)
+        assert np.max(np.abs(got[1:4] - grad)) < 1e-2 * np.max(np.abs(grad)) + 1e-3 * abs(exact) / 16
+
+
+@pytest.mark.slow
+def test_uniform_sphere_closed_form_converges(orc):
+    """Phi of a uniform sphere, -M (3R^2 - r^2) / (2R^3) inside: the voxelised
+    full solve approaches it as the sphere gets more cells."""
+    errs = []
+    tree = synth.uniform_tree(1, 1.0)            # 16^3 leaf cells
+    pos, ids = _leaf_cells(tree)
+    c = np.full(3, 8.0)
+    for R in (3.0, 6.0):
+        inside = np.linalg.norm(pos - c, axis=1) < R
+        rho = np.zeros((tree.n, 512))
+        rho[ids[inside, 0], ids[inside, 1]] = 1.0
+        L = orc.full_solve(tree, rho)
+        phi = L[ids[:, 0], 0, ids[:, 1]]
+        Mtot = inside.sum()                          # discrete mass
+        r = np.linalg.norm(pos - c, axis=1)
+        exact = np.where(r < R, -Mtot * (3 * R * R - r * r) / (2 * R ** 3), -Mtot / r)
+        core = r < R / 2
+        errs.append(np.max(np.abs(phi[core] - exact[core]) / np.abs(exact[core])))
+    assert errs[1] < errs[0] and errs[1] < 0.05, errs
+
+
+# ---------------------------------------------------------------------------
+# adjoints
+# ---------------------------------------------------------------------------
+
+def _small_adaptive():
+    def refine(level, coord, h0):
+        return level == 1 and tuple(coord) in {(0, 0, 0), (1, 0, 0)}
+    return synth.adaptive_tree(refine, 1, 2, 16.0)
+
+
+@pytest.mark.parametrize("which", ["single", "adaptive"])
+def test_multipole_adjoint_dot_product(orc, which):
+    tree = _single_node_tree() if which == "single" else _small_adaptive()
+    rng = np.random.default_rng(17)
+    M = synth.random_moments(tree, seed=18)
+    Lbar = rng.standard_normal((tree.n, 20, 512))
+    L = orc.run_pass_grid(tree, "multipole", M=M)["L"]
+    Mbar = orc.pass_adjoint(tree, "multipole", Lbar)
+    a, b = np.sum(L * Lbar), np.sum(M * Mbar)
+    assert a == pytest.approx(b, rel=1e-12)
+
+
+@pytest.mark.parametrize("which", ["level", "adaptive"])
+def test_monopole_adjoint_dot_product(orc, which):
+    tree = synth.uniform_level(1, 1.0) if which == "level" else _small_adaptive()
+    rng = np.random.default_rng(19)
+    m = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    Lbar = rng.standard_normal((tree.n, 20, 512))
+    L = orc.run_pass_grid(tree, "monopole", m=m)["L"]
+    mbar = orc.pass_adjoint(tree, "monopole", Lbar)
+    assert np.sum(L * Lbar) == pytest.approx(np.sum(m * mbar), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# virtual descendants of a coarse leaf
+# ---------------------------------------------------------------------------
+
+def test_virtual_descendants_equal_refined_leaves(orc):
+    """A coarse leaf seen from a finer level holds 1/8^d of its cell mass in
+    each virtual descendant: identical to refining it into real leaves."""
+    tree = _small_adaptive()
+    rng = np.random.default_rng(20)
+    m = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    idx = tree.index()
+    # refine one coarse level-1 leaf explicitly
+    coarse = (1, 1, 1, 0)
+    assert tree.is_leaf[idx[coarse]] == 1
+    lv, co, lf = list(tree.level), [tuple(c) for c in tree.coord], list(tree.is_leaf)
+    k = idx[coarse]
+    lf[k] = 0
+    new_m = [m[i] for i in range(tree.n)]
+    for b in itertools.product((0, 1), repeat=3):
+        cc = (2 * coarse[1] + b[0], 2 * coarse[2] + b[1], 2 * coarse[3] + b[2])
+        lv.append(2)
+        co.append(cc)
+        lf.append(1)
+        child = np.empty(512)
+        for a in range(512):
+            g = np.array([a % 8, (a // 8) % 8, a // 64]) + 8 * np.array(cc)
+            gp = g // 2 - 8 * np.array(coarse[1:])
+            child[a] = m[k, gp[0] + 8 * gp[1] + 64 * gp[2]] / 8
+        new_m.append(child)
+    ref = synth.Tree(np.array(lv, np.int32), np.array(co, np.int32), np.array(lf, np.uint8), tree.h0)
+    m2 = np.array(new_m)
+    targets = [[i, a] for i in range(tree.n) if tree.level[i] == 2 for a in range(0, 512, 37)]
+    r1 = orc.run_pass(tree, "monopole", m=m, targets=targets)
+    r2 = orc.run_pass(ref, "monopole", m=m2, targets=targets)
+    assert r1["npairs"] == r2["npairs"]
+    np.testing.assert_allclose(r1["L"], r2["L"], rtol=0, atol=1e-14 * np.max(r1["S"]))
