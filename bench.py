@@ -1,0 +1,395 @@
+"""Benchmark of the FMM cell-interaction hot path on one or more B300s.
+
+One step = the whole path over the uniform 64^3 polytrope workload (512 leaf
+sub-grids plus the coarse levels 0-2: 585 sub-grids, 299,520 cells):
+moments from densities, both interaction passes in one persistent launch
+replayed from a CUDA graph (multipole pass at the coarse levels, point-mass
+pass with near field at the leaves), the adjoint of both passes (transposed
+stencil, a gather over sources) for a seeded L-bar, and the adjoint of the
+moments.  Throughput = (forward + adjoint pairs) / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the same
+workload (the path needs no data exchange between replicas); value = pairs of
+all ranks / max over ranks of the timed region.  The reference arm times the
+CPU oracle (the slow, plain FP64 implementation the tests check against) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-cell interactions/s FP64 (fwd, fwd+adjoint) and % of B300 FP64 roofline"
+UNIT = "interactions/s"
+WORKLOAD = ("uniform level: 512 leaf sub-grids (64^3 cells, h=1) + coarse levels 0-2, n=1 polytrope "
+            "R=28 rho_c=1 floor 1e-10 centred; multipole + monopole passes in one batched launch, then the adjoint")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--schedule", choices=["persistent", "per_subgrid"], default="persistent")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        busy = [s for s in sm if mx and s > 0.25 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+
+def make_workload():
+    import synth
+    tree, rho = synth.config2()
+    rng = np.random.default_rng(4)
+    probes = synth.config4_probes()
+    # L-bar of the differentiation workload: dloss/dL0 at 1000 probe cells
+    # plus a seeded N(0,1) L-bar on all 20 components of every cell (so every
+    # adjoint lane does full work)
+    Lbar = rng.standard_normal((tree.n, 20, 512))
+    return tree, rho, Lbar, probes
+
+
+def fwd_flops(info):
+    """algorithmic FP64 flops of one forward pass: 2 x FMAs per in-domain pair
+    (16 per point-mass pair, 70 per multipole pair, 100 with the angular term)"""
+    multi_plain = info["pairs_multipole"] - info["pairs_angular"]
+    return 2 * (16 * info["pairs_monopole"] + 70 * multi_plain + 100 * info["pairs_angular"])
+
+
+def adj_flops(info):
+    return 2 * (16 * info["pairs_monopole"] + 70 * info["pairs_multipole"])
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2303_08058_b300 as ot
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tree, rho_h, Lbar_h, _ = make_workload()
+    g = ot.OTGrid.from_tree(tree)
+    sched = ot.OT_SCHED_PER_SUBGRID if args.schedule == "per_subgrid" else ot.OT_SCHED_PERSISTENT
+    g.set_schedule(sched, 4, 0, not args.no_graph)
+    rho = torch.as_tensor(rho_h, device=dev)
+    Lbar = torch.as_tensor(Lbar_h, device=dev)
+    M, m = g.moments(rho)
+    L = g.zeros(tree.n, 20, 512)
+    Lc = g.zeros(tree.n, 3, 512)
+    tuned = None
+    if args.autotune:
+        tuned = g.autotune(M, m, L, Lc)
+    info = g.info()
+    Mb = g.zeros(tree.n, 20, 512)
+    mb = g.zeros(tree.n, 512)
+    rb = g.zeros(tree.n, 512)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        g.moments(rho, M, m)
+        g.interactions(M, m, L, Lc)
+        g.backward(Lbar, Mb, mb)
+        g.moments_backward(Mb, mb, rb)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.check()
+
+    # -- timed region: K steps, L2 flushed between steps (outside the events) --
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop()
+    g.check()
+
+    # -- dominant kernel: the fused forward launch, timed alone --------------
+    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in fe:
+        flush.zero_()
+        a.record(stream)
+        g.interactions(M, m, L, Lc)
+        b.record(stream)
+    be = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in be:
+        flush.zero_()
+        a.record(stream)
+        g.backward(Lbar, Mb, mb)
+        b.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = statistics.median(a.elapsed_time(b) for a, b in fe)
+    adj_ms = statistics.median(a.elapsed_time(b) for a, b in be)
+
+    # -- FP64 FMA peak, measured on this GPU at the clocks it runs now --------
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = nsm * 4, 4000
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    ot.fp64_fma_probe(out, blocks, 200)
+    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for a, b in pe:
+        a.record(stream)
+        ot.fp64_fma_probe(out, blocks, iters)
+        b.record(stream)
+    torch.cuda.synchronize()
+    probe_ms = min(a.elapsed_time(b) for a, b in pe)
+    peak_tflops = 2.0 * blocks * 256 * iters * 16 / (probe_ms * 1e-3) / 1e12
+
+    # -- end to end: host buffers, copies inside the timed region -------------
+    rho_pin = torch.as_tensor(rho_h).pin_memory()
+    Lbar_pin = torch.as_tensor(Lbar_h).pin_memory()
+    L_out = torch.empty((tree.n, 20, 512), dtype=torch.float64).pin_memory()
+    rb_out = torch.empty((tree.n, 512), dtype=torch.float64).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for a, b in e2e_ev:
+        flush.zero_()
+        a.record(stream)
+        rho.copy_(rho_pin, non_blocking=True)
+        Lbar.copy_(Lbar_pin, non_blocking=True)
+        step()
+        L_out.copy_(L, non_blocking=True)
+        rb_out.copy_(rb, non_blocking=True)
+        b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = statistics.median(a.elapsed_time(b) for a, b in e2e_ev)
+
+    pairs_fwd = info["pairs_multipole"] + info["pairs_monopole"]
+    pairs_step = 2 * pairs_fwd
+    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(total_s, world)
+    value = world * args.steps * pairs_step / total_s
+    ms_per_step = total_s * 1e3 / args.steps
+    ach = fwd_flops(info) / (fwd_ms * 1e-3) / 1e12
+    n_m2m = int(len({int(l) for l in tree.level[tree.is_leaf == 0]}))
+    launches_step = (1 + n_m2m) + 2 + 2 + (1 if info["n_virtual"] else 0) + (1 + n_m2m + 1)
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded polytrope densities, seeded L-bar)",
+        "config": {"workload": WORKLOAD, "subgrids": tree.n, "cells": tree.n * 512,
+                   "pairs_fwd": pairs_fwd, "pairs_adj": pairs_fwd,
+                   "pairs_multipole": info["pairs_multipole"], "pairs_monopole": info["pairs_monopole"],
+                   "schedule": args.schedule, "graph": not args.no_graph,
+                   "tile": {"warps_per_block": info["warps_per_block"], "blocks_per_sm": info["blocks_per_sm"]},
+                   "autotuned": tuned, "l2": "flushed between steps (256 MB write outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "fwd": {"value": pairs_fwd / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
+        "adjoint": {"value": pairs_fwd / (adj_ms * 1e-3), "unit": UNIT, "ms": adj_ms},
+        "roofline": {"bound": "alu", "kernel": "forward_kernel<3> (both passes, one launch)",
+                     "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
+                     "traffic": None, "peak_source": "measured: FP64 FMA probe on this GPU, this run",
+                     "adjoint_achieved": adj_flops(info) / (adj_ms * 1e-3) / 1e12},
+        "e2e": {"value": world * pairs_step / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(rho_pin.numel() * 8 + Lbar_pin.numel() * 8),
+                "d2h_bytes_per_step": int(L_out.numel() * 8 + rb_out.numel() * 8), "ms": e2e_ms},
+        "gpu_launches": launches_step * args.steps,
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    return res, tree, rho_h
+
+
+def cpu_baseline(tree, rho_h, seconds, seed=7):
+    """The oracle as it stands on this host's cores: forward of both passes on
+    seeded random target cells, batches until `seconds` have elapsed."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    M = oracle.moments(tree, rho_h)
+    m = np.ascontiguousarray(M[:, 0, :])
+    rng = np.random.default_rng(seed)
+    pairs, t_used, ntg = 0, 0.0, 0
+    while t_used < seconds:
+        tg = np.stack([rng.integers(0, tree.n, 64 * cores), rng.integers(0, 512, 64 * cores)], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        r1 = oracle.run_pass(tree, "multipole", M=M, targets=tg)
+        r2 = oracle.run_pass(tree, "monopole", m=m, targets=tg)
+        t_used += time.perf_counter() - t0
+        pairs += r1["npairs"] + r2["npairs"]
+        ntg += len(tg)
+    return {"value": pairs / t_used, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"forward of both passes for {ntg} random target cells of the workload "
+                      f"({pairs} pairs, {t_used:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, each step a bounded sample: forward of both
+    passes and the transposed sums for 32 x cores random target cells."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    tree, rho_h, Lbar_h, _ = make_workload()
+    M = oracle.moments(tree, rho_h)
+    m = np.ascontiguousarray(M[:, 0, :])
+    rng = np.random.default_rng(8)
+    per = 32 * cores
+
+    per_adj = max(8, per // cores)   # the transposed sums scatter, so they run on one core
+
+    def step():
+        tg = np.stack([rng.integers(0, tree.n, per), rng.integers(0, 512, per)], 1).astype(np.int32)
+        r1 = oracle.run_pass(tree, "multipole", M=M, targets=tg)
+        r2 = oracle.run_pass(tree, "monopole", m=m, targets=tg)
+        _, a1 = oracle.pass_adjoint(tree, "multipole", Lbar_h, with_s="pairs", targets=tg[:per_adj])
+        _, a2 = oracle.pass_adjoint(tree, "monopole", Lbar_h, with_s="pairs", targets=tg[:per_adj])
+        return r1["npairs"] + r2["npairs"] + a1 + a2
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    pairs = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = pairs / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "subgrids": tree.n, "cells": tree.n * 512,
+                       "parallelism": "host cores (OpenMP)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"per step: forward of both passes for {per} random target cells "
+                                       f"(OpenMP) and the transposed sums of both passes for {per_adj} of them "
+                                       f"(serial scatter)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, rank, world)))
+        return 0
+    rank, world = dist_init(args)
+    res, tree, rho_h = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = cpu_baseline(tree, rho_h, args.cpu_seconds)
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * ot.h -- C ABI of the B300 FMM cell-interaction library (libotfmm.so).
+ *
+ * The operations are the stencil-based cell-to-cell interactions of a fast
+ * multipole gravity solver on an adaptive octree whose nodes each carry an
+ * 8x8x8 sub-grid of cells, every kernel working on one sub-grid plus the
+ * ghost cells of its neighbours (the paper, Sec. 2.1 and Sec. 2.2.1: FMM
+ * gravity solver on an octree of 8^3 sub-grids; kernels per sub-grid with
+ * ghost layers).  The paper fixes FP64 (Sec. 4.1.1); it gives no formulas, so
+ * the definitions below are the project's reading of the method:
+ *
+ *   Units G = 1, Green's function G(R) = -1/|R|.
+ *   Cell moments (raw, about the geometric cell centre), 20 per cell:
+ *     M[K] = int rho(y) (y - X)^K dy, |K| <= 3.
+ *   Taylor coefficients of the potential at a cell centre, 20 per cell:
+ *     L[J] = d^J Phi(X), |J| <= 3.
+ *   Component order (both): 0; x y z; xx xy xz yy yz zz;
+ *     xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz.
+ *   Contraction with the symmetric n + m <= 3 truncation:
+ *     L_A[J] += sum_{m <= 3-|J|} ((-1)^m/m!) sum_{i in {x,y,z}^m} M_B[i] d^{J u i} G(X_A - X_B).
+ *   Opening rule theta = 0.5: cells at integer offset o are well separated iff
+ *     |o|^2 > 12.  A pair is "far" at level l >= 1 when its parents are not well
+ *     separated, at level 0 whenever it is well separated; "near" pairs
+ *     (0 < |o|^2 <= 12) are evaluated for leaf targets only.  Per target parity
+ *     there are 1253 far offsets; there are 178 near offsets.
+ *   Source classes: cells of non-leaf nodes are multipole sources; cells of
+ *     leaf nodes are point masses; a same-level position with no node but
+ *     covered by a coarser leaf is a virtual descendant holding 8^-d of that
+ *     leaf's cell mass (coarse-fine boundary); anything else is empty.
+ *
+ * Memory and ownership.  Every array argument is a DEVICE pointer owned by
+ * the caller, 16-byte aligned, densely packed in the layout given, and must
+ * stay valid until the work queued on `stream` has finished.  The library
+ * owns the grid metadata, its work lists, its scratch arena and its CUDA
+ * graphs; all of them live inside the ot_grid handle.
+ *
+ * Errors.  Every call returns OT_OK or an error code and never throws.  A
+ * call returns after queueing its work on `stream` (a cudaStream_t; NULL is
+ * the legacy default stream); its status covers argument checks and launch
+ * errors.  Faults detected by the kernels' own bounds checks are latched in
+ * a device status word that ot_grid_check() reads (it synchronizes).
+ * ot_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef OT_H
+#define OT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ot_grid ot_grid;
+
+typedef enum {
+    OT_OK = 0,
+    OT_EINVAL = 1,     /* bad argument: null, misaligned, out of range, bad tree */
+    OT_ENOMEM = 2,     /* device or host allocation failed                      */
+    OT_ECUDA = 3,      /* a CUDA runtime call failed                            */
+    OT_ETIMEOUT = 4,   /* a bounded device-side wait ran out                    */
+    OT_ESTATE = 5,     /* handle in a bad state (e.g. a latched device fault)   */
+    OT_ENOTSUP = 6,    /* valid request this build does not implement           */
+    OT_EDEVICE = 7     /* a kernel's own bounds check fired                      */
+} ot_status;
+
+/* Grid description.  Node i sits at `level[i]` with integer position
+ * `coord[3i..3i+2]` in [0, 2^level); its cell (a,b,c) has flat index
+ * a + 8b + 64c and centre (8*coord + (a,b,c) + 0.5) * h0 / 2^level.
+ * `is_leaf[i]` selects the source class of its cells (see above).
+ * (level, coord) pairs must be unique; level <= 20.  Host pointers, read
+ * during ot_grid_create only. */
+typedef struct {
+    int32_t n_subgrids;
+    const int32_t* level;      /* [n]    */
+    const int32_t* coord;      /* [n][3] */
+    const uint8_t* is_leaf;    /* [n]    */
+    double h0;                 /* cell size at level 0, > 0 */
+    int32_t stencil_c;         /* opening rule |o|^2 > c; 0 or 12 (theta = 0.5) */
+    uint32_t flags;            /* OT_GEOMETRIC_CENTRES (the only mode built)  */
+} ot_grid_desc;
+
+#define OT_GEOMETRIC_CENTRES 0u
+
+/* Execution schedule of the interaction kernels. */
+typedef enum {
+    OT_SCHED_PERSISTENT = 0,   /* one persistent launch over a device work list */
+    OT_SCHED_PER_SUBGRID = 1   /* one launch per target sub-grid (the plain path) */
+} ot_schedule;
+
+/* Summary of a grid (host struct filled by ot_grid_info). */
+typedef struct {
+    int32_t n_subgrids;
+    int32_t n_virtual;             /* virtual descendant sub-grids seen by the adjoint */
+    int32_t max_level;
+    int32_t far_offsets;           /* per parity (1253 at theta = 0.5) */
+    int32_t near_offsets;          /* 178 */
+    int32_t root_offsets;          /* 3196 */
+    int64_t pairs_multipole;       /* in-domain (target, source) pairs of each pass */
+    int64_t pairs_monopole;
+    int64_t pairs_virtual;         /* part of pairs_monopole with a virtual source */
+    int64_t pairs_angular;         /* part of pairs_multipole with a non-leaf target */
+    int64_t lanes_fwd;             /* warp lanes run by the forward pair loops of both
+                                      passes, lanes with an empty source included */
+    int64_t fma_fwd;               /* FP64 FMAs issued by those lanes (16 per point-mass
+                                      lane, 70 per multipole lane, 100 with the angular term) */
+    int64_t fma_adj;               /* same for the adjoint pair loops */
+    int32_t schedule;              /* ot_schedule in use */
+    int32_t warps_per_block;       /* tile shape in use */
+    int32_t blocks_per_sm;
+    int32_t graphs_enabled;
+} ot_grid_info_t;
+
+/* Builds neighbour tables, stencils, the derivative table, work lists and the
+ * scratch arena on the current device.  `stream` orders the uploads.
+ * Errors: OT_EINVAL (bad description), OT_ENOMEM, OT_ECUDA, OT_ENOTSUP
+ * (stencil_c other than 12, flags other than geometric centres). */
+ot_status ot_grid_create(const ot_grid_desc* desc, void* stream, ot_grid** out);
+
+/* Frees everything the handle owns (synchronizes the device first). NULL is OK. */
+ot_status ot_grid_destroy(ot_grid* grid);
+
+ot_status ot_grid_info(const ot_grid* grid, ot_grid_info_t* info);
+
+/* Cell moments from densities (the input preparation): rho [n][512] (cell
+ * densities sampled at cell centres) -> M [n][20][512], m [n][512] (= M[:,0]).
+ * Nodes with all 8 children present get the exact binomial (M2M) shift of
+ * their children's moments to their own cell centres; other nodes get the
+ * moments of uniform cubes (M0 = rho h^3, Mii = rho h^5/12).  M and m are
+ * overwritten. */
+ot_status ot_moments(ot_grid* grid, const double* rho, double* M, double* m, void* stream);
+
+/* Adjoint of ot_moments: rhobar [n][512] (overwritten) from Mbar [n][20][512]
+ * and mbar [n][512] (either may be NULL = zero). */
+ot_status ot_moments_backward(ot_grid* grid, const double* Mbar, const double* mbar,
+                              double* rhobar, void* stream);
+
+/* Multipole pass: every target cell of every node gathers the multipole
+ * sources of its stencil.  M [n][20][512] in; L [n][20][512] OVERWRITTEN;
+ * Lc [n][3][512] (angular-momentum correction, non-leaf targets with
+ * non-zero mass, multipole sources only; may be NULL) overwritten:
+ *   Lc_A[i] = -(1/6) sum_B sum_{jkl} (M3_B - (m_B/m_A) M3_A)[jkl] d^{ijkl} G.
+ * `centres` must be NULL (geometric cell centres), else OT_ENOTSUP. */
+ot_status ot_multipole_interactions(ot_grid* grid, const double* M, const double* centres,
+                                    double* L, double* Lc, void* stream);
+
+/* Monopole pass: every target cell gathers the point-mass sources of its
+ * stencil (leaf cells, virtual descendants of coarser leaves).  m [n][512] in;
+ * L [n][20][512] is ACCUMULATED into (call after the multipole pass, or zero it). */
+ot_status ot_monopole_interactions(ot_grid* grid, const double* m, double* L, void* stream);
+
+/* Both passes fused in one batched launch (the schedule set by
+ * ot_set_schedule; replayed from a CUDA graph when graphs are enabled).
+ * L overwritten with the sum of both passes; Lc as above (may be NULL). */
+ot_status ot_interactions(ot_grid* grid, const double* M, const double* m,
+                          double* L, double* Lc, void* stream);
+
+/* Adjoint of both passes with respect to their sources (Lc not included):
+ *   Mbar = (d L / d M)^T Lbar  for the multipole pass  [n][20][512] overwritten,
+ *   mbar = (d L / d m)^T Lbar  for the monopole pass   [n][512]     overwritten,
+ * with virtual descendants' gradients restricted onto their coarse leaf.
+ * Runs the transposed stencil (a gather over sources); stores nothing from
+ * the forward pass.  Mbar / mbar may be NULL to skip that half. */
+ot_status ot_interactions_backward(ot_grid* grid, const double* Lbar, double* Mbar,
+                                   double* mbar, void* stream);
+
+/* Schedule and tile shape of later calls (forward and adjoint; the plain
+ * schedule launches once per target sub-grid forward and once per source
+ * sub-grid in the adjoint).  warps_per_block in {2,4,8},
+ * blocks_per_sm in {0 (max resident), 1..16}; use_graph 0/1. */
+ot_status ot_set_schedule(ot_grid* grid, int32_t schedule, int32_t warps_per_block,
+                          int32_t blocks_per_sm, int32_t use_graph);
+
+/* Times every tile shape of the persistent schedule on the given buffers
+ * (which it overwrites) with CUDA events and keeps the fastest; writes the
+ * chosen (warps_per_block, blocks_per_sm) and its time in ms to the outputs.
+ * Synchronizes `stream`. */
+ot_status ot_autotune(ot_grid* grid, const double* M, const double* m, double* L, double* Lc,
+                      void* stream, int32_t* best_warps, int32_t* best_blocks, double* best_ms);
+
+/* Reads and clears the device status word (synchronizes `stream`): OT_OK, or
+ * OT_EDEVICE with the failing work item in ot_last_error(). */
+ot_status ot_grid_check(ot_grid* grid, void* stream);
+
+/* FP64 FMA throughput probe (the roofline denominator): `blocks` x 256
+ * threads each run `iters` rounds of 16 independent FMA chains; out [blocks*256]
+ * receives the chain results (keeps them live).  Time it with events. */
+ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, void* stream);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* ot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OT_H */

@@ -58,8 +58,10 @@ def _load():
     lib.oracle_moments.restype = I
     lib.oracle_pass.argtypes = [I, P, P, P, ctypes.c_double, P, P, I, I, P, P, P, P, P]
     lib.oracle_pass.restype = ctypes.c_longlong
-    lib.oracle_pass_adjoint.argtypes = [I, P, P, P, ctypes.c_double, I, P, P, P]
+    lib.oracle_pass_adjoint.argtypes = [I, P, P, P, ctypes.c_double, I, P, P, P, P]
     lib.oracle_pass_adjoint.restype = I
+    lib.oracle_pass_adjoint_targets.argtypes = [I, P, P, P, ctypes.c_double, I, P, P, P, P, I, P]
+    lib.oracle_pass_adjoint_targets.restype = ctypes.c_longlong
     lib.oracle_l2l.argtypes = [P, P, P]
     lib.oracle_l2l.restype = None
     lib.oracle_full_solve.argtypes = [I, P, P, P, ctypes.c_double, P, P]
@@ -165,16 +167,23 @@ def run_pass_grid(tree, pass_kind, M=None, m=None):
     return out
 
 
-def pass_adjoint(tree, pass_kind: str, Lbar):
-    """Transposed sum of a pass: Mbar [n,20,512] (multipole) or mbar [n,512]."""
+def pass_adjoint(tree, pass_kind: str, Lbar, with_s: bool = False, targets=None):
+    """Transposed sum of a pass: Mbar [n,20,512] (multipole) or mbar [n,512];
+    with ``with_s`` also the matching sum of |terms|.  ``targets`` ([k, 2]
+    node, cell) restricts the scatter to those target cells."""
     level, coord, leaf = _tree_args(tree)
     kind = {"multipole": 1, "monopole": 2}[pass_kind]
     Lbar = np.ascontiguousarray(Lbar, dtype=np.float64)
     Mbar = np.zeros((tree.n, NCOMP, NCELL))
     mbar = np.zeros((tree.n, NCELL))
-    _load().oracle_pass_adjoint(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, kind, _p(Lbar),
-                                _p(Mbar), _p(mbar))
-    return Mbar if kind == 1 else mbar
+    S = np.zeros_like(Mbar if kind == 1 else mbar)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int32).reshape(-1, 2)
+    npairs = _load().oracle_pass_adjoint_targets(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, kind, _p(Lbar),
+                                        _p(Mbar), _p(mbar), _p(S), 0 if tg is None else tg.shape[0], _p(tg))
+    out = Mbar if kind == 1 else mbar
+    if with_s == "pairs":
+        return out, int(npairs)
+    return (out, S) if with_s else out
 
 
 def l2l(Lp, d) -> np.ndarray:

@@ -415,21 +415,41 @@ long long oracle_pass(int n, const int* level, const int* coord, const uint8_t* 
     return total;
 }
 
+long long oracle_pass_adjoint_targets(int n, const int* level, const int* coord, const uint8_t* is_leaf,
+                                      double h0, int pass, const double* Lbar, double* Mbar, double* mbar,
+                                      double* Sbar, int nt, const int* targets);
+
 /* Transposed sums of a pass: walk exactly the pairs of the forward pass and
  * scatter Lbar[A] through the transposed coefficients onto the source.
  * pass 1 -> Mbar [n][20][512] (gradient w.r.t. the stored components of M);
- * pass 2 -> mbar [n][512] (virtual descendants scatter onto their leaf). */
+ * pass 2 -> mbar [n][512] (virtual descendants scatter onto their leaf).
+ * Sbar (same shape, may be NULL) receives the sum of |terms|. */
 int oracle_pass_adjoint(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
-                        int pass, const double* Lbar, double* Mbar, double* mbar) {
+                        int pass, const double* Lbar, double* Mbar, double* mbar, double* Sbar) {
+    oracle_pass_adjoint_targets(n, level, coord, is_leaf, h0, pass, Lbar, Mbar, mbar, Sbar, 0, NULL);
+    return 0;
+}
+
+/* Same, scattering only from the listed target cells ([nt][2] node, cell);
+ * returns the number of pairs walked. */
+long long oracle_pass_adjoint_targets(int n, const int* level, const int* coord, const uint8_t* is_leaf,
+                                      double h0, int pass, const double* Lbar, double* Mbar, double* mbar,
+                                      double* Sbar, int nt, const int* targets) {
     otree t;
+    long long npairs = 0;
     tree_init(&t, n, level, coord, is_leaf, h0);
-    if (pass == 1) memset(Mbar, 0, sizeof(double) * (size_t)n * NCOMP * NCELL);
-    else memset(mbar, 0, sizeof(double) * (size_t)n * NCELL);
-    for (int T = 0; T < n; T++) {
+    size_t nout = (pass == 1) ? (size_t)n * NCOMP * NCELL : (size_t)n * NCELL;
+    if (pass == 1) memset(Mbar, 0, sizeof(double) * nout);
+    else memset(mbar, 0, sizeof(double) * nout);
+    if (Sbar) memset(Sbar, 0, sizeof(double) * nout);
+    long total = targets ? nt : (long)n * NCELL;
+    for (long k = 0; k < total; k++) {
+        int T = targets ? targets[2 * k] : (int)(k / NCELL);
+        int a = targets ? targets[2 * k + 1] : (int)(k % NCELL);
         int l = level[T];
         double h = h0 / pow(2.0, l);
         int leafT = is_leaf[T];
-        for (int a = 0; a < NCELL; a++) {
+        {
             long g[3] = {8L * coord[3 * T] + (a & 7), 8L * coord[3 * T + 1] + ((a >> 3) & 7),
                          8L * coord[3 * T + 2] + (a >> 6)};
             const double* LA = Lbar + (size_t)T * NCOMP * NCELL + a;
@@ -445,13 +465,18 @@ int oracle_pass_adjoint(int n, const int* level, const int* coord, const uint8_t
                         int cls = source_lookup(&t, l, q, &B, &cb, &scale);
                         if (pass == 1 && cls != 1) continue;
                         if (pass == 2 && cls != 2 && cls != 3) continue;
+                        npairs++;
                         double R[3] = {-o[0] * h, -o[1] * h, -o[2] * h};
                         double D[NCOMP4];
                         oracle_D(R, D);
                         if (pass == 2) {
-                            double acc = 0.0;
-                            for (int J = 0; J < NCOMP; J++) acc += LA[(size_t)J * NCELL] * D[J];
+                            double acc = 0.0, sacc = 0.0;
+                            for (int J = 0; J < NCOMP; J++) {
+                                acc += LA[(size_t)J * NCELL] * D[J];
+                                sacc += fabs(LA[(size_t)J * NCELL] * D[J]);
+                            }
                             mbar[(size_t)B * NCELL + cb] += scale * acc;
+                            if (Sbar) Sbar[(size_t)B * NCELL + cb] += scale * sacc;
                             continue;
                         }
                         double* MB = Mbar + (size_t)B * NCOMP * NCELL + cb;
@@ -468,7 +493,9 @@ int oracle_pass_adjoint(int n, const int* level, const int* coord, const uint8_t
                                     for (int s = 0; s < mm; s++) { it[s] = v % 3; v /= 3; }
                                     for (int s = 0; s < nJ; s++) full[s] = comp_idx[J][s];
                                     for (int s = 0; s < mm; s++) full[nJ + s] = it[s];
-                                    MB[(size_t)comp_of(it, mm) * NCELL] += cm * lbar * D[comp_of(full, nJ + mm)];
+                                    double term = cm * lbar * D[comp_of(full, nJ + mm)];
+                                    MB[(size_t)comp_of(it, mm) * NCELL] += term;
+                                    if (Sbar) Sbar[(size_t)B * NCOMP * NCELL + (size_t)comp_of(it, mm) * NCELL + cb] += fabs(term);
                                 }
                             }
                         }
@@ -476,7 +503,7 @@ int oracle_pass_adjoint(int n, const int* level, const int* coord, const uint8_t
         }
     }
     tree_free(&t);
-    return 0;
+    return npairs;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,138 @@
+"""Emit ot_contract.inc: straight-line FP64 contraction code for the kernels.
+
+Run as ``python gen_contract.py`` (the build does it when the .inc is stale).
+
+The kernels contract with the *traceless-reduced* index sets.  Every
+derivative tensor d^k G of G = -1/r is harmonic (traceless in every index
+pair), so
+
+* of a target's 20 Taylor coefficients only the 16 whose multi-index has at
+  most one z (``IND16`` below) are accumulated; the other 4 follow per cell
+  from zz = -(xx + yy), xzz = -(xxx + xyy), yzz = -(xxy + yyy),
+  zzz = -(xxz + yyz);
+* a source's second and third moments enter only through 5 and 7 reduced
+  combinations (the z-z traces folded into the other components), so the
+  16 reduced source moments use the same index set ``IND16``.
+
+With both sides reduced, one multipole pair costs 70 FMAs for the 16
+coefficients (instead of 84 with all 20 components), one point-mass pair 16
+(instead of 20), and the transposed (adjoint) contractions cost the same.
+
+Derivative-table row layout (36 doubles per integer offset):
+  [0..15]  the IND16 components of ranks 0..3
+  [16..19] zz, xzz, yzz, zzz
+  [20..34] rank 4 in storage order (xxxx xxxy xxxz xxyy xxyz xxzz xyyy xyyz
+           xyzz xzzz yyyy yyyz yyzz yzzz zzzz)
+  [35]     padding
+"""
+import itertools
+import os
+
+IND16 = [(0, 0, 0),
+         (1, 0, 0), (0, 1, 0), (0, 0, 1),
+         (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1),
+         (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (0, 3, 0), (0, 2, 1)]
+EXTRA = [(0, 0, 2), (1, 0, 2), (0, 1, 2), (0, 0, 3)]
+RANK4 = [tuple(t.count(a) for a in range(3))
+         for t in itertools.combinations_with_replacement(range(3), 4)]
+ROW = IND16 + EXTRA + RANK4
+ROWIDX = {e: i for i, e in enumerate(ROW)}
+assert len(ROW) == 35
+
+
+def rank(e):
+    return sum(e)
+
+
+def add(a, b):
+    return tuple(x + y for x, y in zip(a, b))
+
+
+R3 = [k for k, e in enumerate(IND16) if rank(e) == 3]          # reduced octupole slots 9..15
+# independent rank-4 components (at most one z) accumulated for the
+# angular term's target-side sum, and the three derived ones
+T4 = [e for e in RANK4 if e[2] <= 1]
+T4IDX = {e: i for i, e in enumerate(T4)}
+assert len(T4) == 9
+
+
+def t4_expr(e):
+    """expression of a rank-4 component (z count <= 2) in the t4[] accumulators"""
+    if e[2] <= 1:
+        return f"t4[{T4IDX[e]}]"
+    # e has zz: d_{..zz} = -d_{..xx} - d_{..yy}
+    base = (e[0], e[1], e[2] - 2)
+    return f"(-{t4_expr(add(base, (2, 0, 0)))} - {t4_expr(add(base, (0, 2, 0)))})"
+
+
+def emit():
+    out = []
+    w = out.append
+    w("// Generated by gen_contract.py -- do not edit.\n")
+    w("// Traceless-reduced FP64 contractions; see gen_contract.py for the layout.\n\n")
+
+    # point-mass source: a[J] += mass * d[J]
+    w("__device__ __forceinline__ void ot_mono_fwd(double (&a)[16], double mass, const double (&d)[36]) {\n")
+    for j in range(16):
+        w(f"  a[{j}] = fma(mass, d[{j}], a[{j}]);\n")
+    w("}\n\n")
+
+    # multipole source: a[J] += sum_K r[K] d[J+K]
+    terms = []
+    for j, ej in enumerate(IND16):
+        for k, ek in enumerate(IND16):
+            if rank(ej) + rank(ek) <= 3:
+                terms.append((j, k, ROWIDX[add(ej, ek)]))
+    assert len(terms) == 70, len(terms)
+    w("// 70 FMAs\n")
+    w("__device__ __forceinline__ void ot_multi_fwd(double (&a)[16], const double (&r)[16], const double (&d)[36]) {\n")
+    # order: by source component so consecutive FMAs hit different accumulators
+    for k in range(16):
+        for (j, kk, di) in terms:
+            if kk == k:
+                w(f"  a[{j}] = fma(r[{k}], d[{di}], a[{j}]);\n")
+    w("}\n\n")
+
+    # angular term, source part: c[i] += sum_{K in R3} r[K] d[e_i + K];
+    # target part accumulator: t4[q] += mB * d[q]
+    w("// 21 + 9 FMAs\n")
+    w("__device__ __forceinline__ void ot_angular_fwd(double (&c)[3], double (&t4)[9], const double (&r)[16],\n"
+      "                                               double mB, const double (&d)[36]) {\n")
+    for i in range(3):
+        ei = tuple(1 if a == i else 0 for a in range(3))
+        for k in R3:
+            w(f"  c[{i}] = fma(r[{k}], d[{ROWIDX[add(ei, IND16[k])]}], c[{i}]);\n")
+    for q, e in enumerate(T4):
+        w(f"  t4[{q}] = fma(mB, d[{ROWIDX[e]}], t4[{q}]);\n")
+    w("}\n\n")
+
+    # angular epilogue: out[i] = sum_{K in R3} rA[K] * T4[e_i + K]
+    w("__device__ __forceinline__ void ot_angular_target(double (&out)[3], const double (&t4)[9], const double (&rA)[16]) {\n")
+    for i in range(3):
+        ei = tuple(1 if a == i else 0 for a in range(3))
+        parts = [f"rA[{k}] * {t4_expr(add(ei, IND16[k]))}" for k in R3]
+        w(f"  out[{i}] = " + " + ".join(parts) + ";\n")
+    w("}\n\n")
+
+    # adjoint, multipole source: g[K] += sum_J lb[J] d[J+K]
+    w("// 70 FMAs\n")
+    w("__device__ __forceinline__ void ot_multi_adj(double (&g)[16], const double (&lb)[16], const double (&d)[36]) {\n")
+    for j in range(16):
+        for (jj, k, di) in terms:
+            if jj == j:
+                w(f"  g[{k}] = fma(lb[{j}], d[{di}], g[{k}]);\n")
+    w("}\n\n")
+
+    # adjoint, point-mass source: g[s] += sum_J lb[J] d[J]  (4 partial sums)
+    w("// 16 FMAs\n")
+    w("__device__ __forceinline__ void ot_mono_adj(double (&g)[4], const double (&lb)[16], const double (&d)[36]) {\n")
+    for j in range(16):
+        w(f"  g[{j % 4}] = fma(lb[{j}], d[{j}], g[{j % 4}]);\n")
+    w("}\n")
+    return "".join(out)
+
+
+if __name__ == "__main__":
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "ot_contract.inc"), "w") as f:
+        f.write(emit())

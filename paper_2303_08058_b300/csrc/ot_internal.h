@@ -1,0 +1,105 @@
+// Library-internal declarations shared by the host code (ot_lib.cu) and the
+// kernels (ot_kernels.cu).  Not part of the public ABI (include/ot.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace otk {
+
+constexpr int NCELL = 512;        // cells per 8^3 sub-grid
+constexpr int NCOMP = 20;         // moments / Taylor coefficients of orders 0..3
+constexpr int NRED = 16;          // traceless-reduced components
+constexpr int DROW = 36;          // doubles per derivative-table row
+constexpr int NOFF = 15 * 15 * 15;  // integer offsets in [-7, 7]^3
+constexpr int MAXLEV = 21;        // levels 0..20
+
+// Neighbour-table entry (one per 3x3x3 neighbour of a sub-grid at its own level).
+//   x: node index (real node, or the coarse leaf of a virtual descendant)
+//   y: kind (bits 0-1) | d (bits 2-4, virtual depth) | ov.x << 8 | ov.y << 16 | ov.z << 24
+// kind: 0 empty, 1 multipole cells (non-leaf node), 2 point masses (leaf node),
+// 3 virtual descendant of a coarser leaf: level-l local cell s maps to the
+// leaf's cell ((ov + s) >> d) per axis and holds 8^-d of its mass.
+enum Kind : int { K_NONE = 0, K_MULTI = 1, K_LEAF = 2, K_VIRT = 3 };
+
+// Stencil lists are packed offsets (ox + 8) | (oy + 8) << 8 | (oz + 8) << 16.
+// Table row of offset o: (ox + 7) + 15 (oy + 7) + 225 (oz + 7); the row holds
+// the derivatives of G at R = -o (unit spacing), i.e. for the pair
+// target -> source at offset o.  The row of -o is NOFF - 1 - row(o).
+
+struct Lists {
+    const int* lists;      // far[8][far_len] | near[near_len] | root[root_len]
+    int far_len, near_len, root_len;
+    int near_off, root_off;
+};
+
+struct FwdParams {
+    const int* items;      // packed (node << 4) | (parity << 1) | half
+    int n_items;
+    int* counter;          // persistent queue head (zeroed before the launch)
+    const int2* nbr;       // [n][27]
+    const int* ninfo;      // [n]: level | is_leaf << 8
+    const double* Dt;      // [NOFF][DROW]
+    Lists L;
+    const double* Mhat;    // [n][16][512] reduced scaled moments (non-leaf nodes)
+    const double* m;       // [n][512]
+    double* Lout;          // [n][20][512]
+    double* Lc;            // [n][3][512] or null
+    int accumulate;
+    int n_nodes;
+    int* status;           // [2]: first error code, its item
+    double hinv[MAXLEV];   // 1 / h_l
+};
+
+struct AdjParams {
+    const int* items;      // packed (src << 4) | (parity << 1) | half; src >= n_nodes: virtual
+    int n_items;
+    int* counter;
+    const int2* nbr;       // [n][27] real nodes
+    const int2* vnbr;      // [nvirt][27] virtual nodes
+    const int* ninfo;      // [n]
+    const int* vinfo;      // [nvirt]: level
+    const double* Dt;
+    Lists L;
+    const double* Lrbar;   // [n][16][512] reduced scaled adjoint of L
+    double* Mbar;          // [n][20][512] or null
+    double* mbar;          // [n][512] or null
+    double* vbar;          // [nvirt][512]
+    int n_nodes;
+    int* status;
+    double hinv[MAXLEV];
+};
+
+struct PrepParams {
+    const double* src;     // M [n][20][512] (forward) or Lbar (adjoint)
+    double* dst;           // [n][16][512]
+    const int* nodes;      // node list
+    int n_list;
+    const int* ninfo;
+    double hinv[MAXLEV];
+};
+
+// launchers (ot_kernels.cu)
+cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid,
+                           cudaStream_t s);
+cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wpb, int grid,
+                           cudaStream_t s);
+cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s);
+cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);
+cudaError_t launch_restrict_virtual(const double* vbar, const int* vmap, int n_pairs_map,
+                                    double* mbar, cudaStream_t s);
+cudaError_t launch_cube_moments(const double* rho, double* M, double* m, const int* nodes, int n_list,
+                                const int* ninfo, const double* hinv, cudaStream_t s);
+cudaError_t launch_m2m(double* M, double* m, const int* parents, int n_list, const int* children,
+                       const int* ninfo, const double* hinv, cudaStream_t s);
+cudaError_t launch_moments_adjoint_init(const double* Mbar, const double* mbar, double* Mb, int n,
+                                        cudaStream_t s);
+cudaError_t launch_m2m_adjoint(double* Mb, const int* parents, int n_list, const int* children,
+                               const int* ninfo, const double* hinv, cudaStream_t s);
+cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nodes, int n_list,
+                                const int* ninfo, const double* hinv, cudaStream_t s);
+cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
+int forward_max_blocks_per_sm(int mode, int wpb);
+int adjoint_max_blocks_per_sm(int mode, int wpb);
+
+}  // namespace otk

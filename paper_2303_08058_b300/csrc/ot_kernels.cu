@@ -1,0 +1,730 @@
+// FP64 CUDA kernels for sm_103a: the stencil walk of the multipole and
+// monopole interaction passes, its transposed (adjoint) walk, cell moments
+// with their M2M shift, and the FP64 FMA probe.
+//
+// Design (B300): the interaction passes are bound by the FP64 FMA pipe, which
+// on this part runs at a small fraction of the FP32 rate; memory traffic per
+// pair is a few bytes.  So every FP64 operation that is not a contraction FMA
+// is moved out of the pair loop:
+//   * derivative tensors come from a table of integer offsets (geometric cell
+//     centres make D depend on the offset only; the level enters as powers of
+//     h applied once per cell);
+//   * source moments are pre-scaled once per cell by (-1)^m/m!, the index
+//     multiplicity and h^-m, and reduced to 16 traceless combinations;
+//   * only the 16 independent Taylor coefficients are accumulated.
+// A warp owns 32 target cells of one parity class of one sub-grid, so the
+// stencil offset, its table row and the neighbour lookup are warp-uniform;
+// integer address arithmetic runs on the integer pipes.
+#include "ot_internal.h"
+
+namespace otk {
+
+#include "ot_contract.inc"
+
+__device__ __forceinline__ void report(int* status, int code, int item) {
+    if (atomicCAS(status, 0, code) == 0) atomicExch(status + 1, item);
+}
+
+// 2^e built from its bit pattern (exact; |e| < 1000)
+__device__ __forceinline__ double pow2i(int e) {
+    return __longlong_as_double(static_cast<long long>(1023 + e) << 52);
+}
+
+__device__ __forceinline__ void load_row16(double (&d)[36], const double* __restrict__ Dt, int row) {
+    const double2* p = reinterpret_cast<const double2*>(Dt + static_cast<size_t>(row) * DROW);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const double2 v = __ldg(p + i);
+        d[2 * i] = v.x;
+        d[2 * i + 1] = v.y;
+    }
+}
+
+__device__ __forceinline__ void load_row(double (&d)[36], const double* __restrict__ Dt, int row) {
+    const double2* p = reinterpret_cast<const double2*>(Dt + static_cast<size_t>(row) * DROW);
+#pragma unroll
+    for (int i = 0; i < 18; ++i) {
+        const double2 v = __ldg(p + i);
+        d[2 * i] = v.x;
+        d[2 * i + 1] = v.y;
+    }
+}
+
+__device__ __forceinline__ int offset_row(int ox, int oy, int oz) {
+    return (ox + 7) + 15 * (oy + 7) + 225 * (oz + 7);
+}
+
+// lane -> local cell of the warp's 32 cells of parity `par`, half `half`
+__device__ __forceinline__ void lane_cell(int lane, int par, int half, int& x, int& y, int& z) {
+    x = (par & 1) + 2 * (lane & 3);
+    y = ((par >> 1) & 1) + 2 * ((lane >> 2) & 3);
+    z = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
+}
+
+// ---------------------------------------------------------------------------
+// forward stencil walk
+// ---------------------------------------------------------------------------
+
+template <int MODE>
+__device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
+                                             int tx, int ty, int tz, const int2* __restrict__ s_nb,
+                                             const FwdParams& p, double (&a)[16], double (&c)[3],
+                                             double (&t4)[9], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        const int sx = tx + ox, sy = ty + oy, sz = tz + oz;   // in [-7, 14]
+        const int nb = ((sx + 8) >> 3) + 3 * ((sy + 8) >> 3) + 9 * ((sz + 8) >> 3);
+        const int2 e = s_nb[nb];
+        int kind = e.y & 3;
+        if (kind != K_NONE && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
+            report(p.status, 1, item);
+            kind = K_NONE;
+        }
+        const int lcell = (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+        const int row = offset_row(ox, oy, oz);
+        if (MODE & 2) {
+            const bool mono = kind >= K_LEAF;
+            if (__any_sync(0xffffffffu, mono)) {
+                double mass = 0.0;
+                if (kind == K_LEAF) {
+                    mass = __ldg(p.m + static_cast<size_t>(e.x) * NCELL + lcell);
+                } else if (kind == K_VIRT) {
+                    const unsigned meta = static_cast<unsigned>(e.y);
+                    const int d = (meta >> 2) & 7;
+                    const int vx = static_cast<int>(((meta >> 8) & 0xffu) + (sx & 7)) >> d;
+                    const int vy = static_cast<int>(((meta >> 16) & 0xffu) + (sy & 7)) >> d;
+                    const int vz = static_cast<int>((meta >> 24) + (sz & 7)) >> d;
+                    mass = __ldg(p.m + static_cast<size_t>(e.x) * NCELL + vx + 8 * vy + 64 * vz) * pow2i(-3 * d);
+                }
+                double d[36];
+                load_row16(d, p.Dt, row);
+                ot_mono_fwd(a, mass, d);
+            }
+        }
+        if (MODE & 1) {
+            const bool multi = kind == K_MULTI;
+            if (__any_sync(0xffffffffu, multi)) {
+                double r[16];
+                if (multi) {
+                    const double* src = p.Mhat + static_cast<size_t>(e.x) * NRED * NCELL + lcell;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) r[q] = __ldg(src + q * NCELL);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) r[q] = 0.0;
+                }
+                double d[36];
+                load_row(d, p.Dt, row);
+                ot_multi_fwd(a, r, d);
+                if (angular) ot_angular_fwd(c, t4, r, r[0], d);
+            }
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_forward(const FwdParams& p, int node, int level, bool leafT, int tcell,
+                                              const double (&a)[16], const double (&c)[3],
+                                              const double (&t4)[9]) {
+    const double h1 = p.hinv[level], h2 = h1 * h1, h3 = h2 * h1, h4 = h2 * h2;
+    double L[20];
+    L[0] = a[0] * h1;
+    L[1] = a[1] * h2;
+    L[2] = a[2] * h2;
+    L[3] = a[3] * h2;
+    L[4] = a[4] * h3;
+    L[5] = a[5] * h3;
+    L[6] = a[6] * h3;
+    L[7] = a[7] * h3;
+    L[8] = a[8] * h3;
+    L[9] = -(a[4] + a[7]) * h3;
+    L[10] = a[9] * h4;
+    L[11] = a[10] * h4;
+    L[12] = a[11] * h4;
+    L[13] = a[12] * h4;
+    L[14] = a[13] * h4;
+    L[15] = -(a[9] + a[12]) * h4;
+    L[16] = a[14] * h4;
+    L[17] = a[15] * h4;
+    L[18] = -(a[10] + a[14]) * h4;
+    L[19] = -(a[11] + a[15]) * h4;
+    double* out = p.Lout + static_cast<size_t>(node) * NCOMP * NCELL + tcell;
+    if (p.accumulate) {
+#pragma unroll
+        for (int q = 0; q < 20; ++q) out[q * NCELL] += L[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 20; ++q) out[q * NCELL] = L[q];
+    }
+    if ((MODE & 1) && p.Lc != nullptr) {
+        double lc[3] = {0.0, 0.0, 0.0};
+        if (!leafT) {
+            const double* mh = p.Mhat + static_cast<size_t>(node) * NRED * NCELL + tcell;
+            const double mA = mh[0];
+            if (mA != 0.0) {
+                double rA[16];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) rA[q] = 0.0;
+#pragma unroll
+                for (int q = 9; q < 16; ++q) rA[q] = mh[q * NCELL];
+                double o[3];
+                ot_angular_target(o, t4, rA);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) lc[i] = h2 * (c[i] - o[i] / mA);
+            }
+        }
+        double* lo = p.Lc + static_cast<size_t>(node) * 3 * NCELL + tcell;
+        lo[0] = lc[0];
+        lo[NCELL] = lc[1];
+        lo[2 * NCELL] = lc[2];
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int persistent) {
+    __shared__ int2 s_nb[8][27];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    int it = blockIdx.x * wpb + warp;
+    for (;;) {
+        if (persistent) {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(p.counter, 1);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= p.n_items) break;
+        const int item = __ldg(p.items + it);
+        const int node = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        if (lane < 27) s_nb[warp][lane] = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
+        __syncwarp();
+        const int info = __ldg(p.ninfo + node);
+        const int level = info & 0xff;
+        const bool leafT = (info >> 8) & 1;
+        int tx, ty, tz;
+        lane_cell(lane, par, half, tx, ty, tz);
+        double a[16], c[3], t4[9];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) c[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) t4[q] = 0.0;
+        const int* l1 = (level == 0) ? p.L.lists + p.L.root_off : p.L.lists + par * p.L.far_len;
+        const int n1 = (level == 0) ? p.L.root_len : p.L.far_len;
+        walk_forward<MODE>(l1, n1, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, it);
+        if (leafT)
+            walk_forward<MODE>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p, a,
+                               c, t4, it);
+        store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
+        __syncwarp();
+        if (!persistent) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (transposed) stencil walk: a gather over source cells
+// ---------------------------------------------------------------------------
+
+// Source B of parity p gathers from targets A = B + o' for o' in the forward
+// list of parity p (far pairs are symmetric under o -> -o with the parities
+// swapped), with the table row of the forward offset o = -o'.
+template <bool MULTI>
+__device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int len, bool near_seg,
+                                             int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
+                                             const AdjParams& p, double (&g)[16], double (&g4)[4],
+                                             int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        const int tx = sx0 + ox, ty = sy0 + oy, tz = sz0 + oz;
+        const int nb = ((tx + 8) >> 3) + 3 * ((ty + 8) >> 3) + 9 * ((tz + 8) >> 3);
+        const int2 e = s_nb[nb];
+        const int kind = e.y & 3;
+        bool valid = (kind == K_MULTI || kind == K_LEAF) && (!near_seg || kind == K_LEAF);
+        if (valid && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
+            report(p.status, 2, item);
+            valid = false;
+        }
+        if (!__any_sync(0xffffffffu, valid)) continue;
+        const int tcell = (tx & 7) + 8 * (ty & 7) + 64 * (tz & 7);
+        double lb[16];
+        if (valid) {
+            const double* src = p.Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + tcell;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) lb[q] = __ldg(src + q * NCELL);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) lb[q] = 0.0;
+        }
+        const int row = NOFF - 1 - offset_row(ox, oy, oz);
+        double d[36];
+        if (MULTI) {
+            load_row(d, p.Dt, row);
+            ot_multi_adj(g, lb, d);
+        } else {
+            load_row16(d, p.Dt, row);
+            ot_mono_adj(g4, lb, d);
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int persistent) {
+    __shared__ int2 s_nb[8][27];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    int it = blockIdx.x * wpb + warp;
+    for (;;) {
+        if (persistent) {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(p.counter, 1);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= p.n_items) break;
+        const int item = __ldg(p.items + it);
+        const int src = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        const bool virt = src >= p.n_nodes;
+        const int2* nbt = virt ? p.vnbr + static_cast<size_t>(src - p.n_nodes) * 27
+                               : p.nbr + static_cast<size_t>(src) * 27;
+        if (lane < 27) s_nb[warp][lane] = __ldg(nbt + lane);
+        __syncwarp();
+        int level, skind;
+        if (virt) {
+            level = __ldg(p.vinfo + (src - p.n_nodes));
+            skind = K_VIRT;
+        } else {
+            const int info = __ldg(p.ninfo + src);
+            level = info & 0xff;
+            skind = ((info >> 8) & 1) ? K_LEAF : K_MULTI;
+        }
+        int sx, sy, sz;
+        lane_cell(lane, par, half, sx, sy, sz);
+        const int scell = sx + 8 * sy + 64 * sz;
+        const int* l1 = (level == 0) ? p.L.lists + p.L.root_off : p.L.lists + par * p.L.far_len;
+        const int n1 = (level == 0) ? p.L.root_len : p.L.far_len;
+        const int* l2 = p.L.lists + p.L.near_off;
+        const double h1 = p.hinv[level], h2 = h1 * h1, h3 = h2 * h1;
+        double g[16], g4[4];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) g[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g4[q] = 0.0;
+        if (skind == K_MULTI) {
+            if ((MODE & 1) && p.Mbar != nullptr) {
+                walk_adjoint<true>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                walk_adjoint<true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                // expand the traceless reduction and apply (-1)^m/m! * multiplicity * h^-m
+                double Mb[20];
+                Mb[0] = g[0];
+                Mb[1] = -h1 * g[1];
+                Mb[2] = -h1 * g[2];
+                Mb[3] = -h1 * g[3];
+                Mb[4] = 0.5 * h2 * g[4];
+                Mb[5] = h2 * g[5];
+                Mb[6] = h2 * g[6];
+                Mb[7] = 0.5 * h2 * g[7];
+                Mb[8] = h2 * g[8];
+                Mb[9] = -0.5 * h2 * (g[4] + g[7]);
+                const double s6 = -h3 / 6.0, s2 = -0.5 * h3;
+                Mb[10] = s6 * g[9];
+                Mb[11] = s2 * g[10];
+                Mb[12] = s2 * g[11];
+                Mb[13] = s2 * g[12];
+                Mb[14] = -h3 * g[13];
+                Mb[15] = -s2 * (g[9] + g[12]);
+                Mb[16] = s6 * g[14];
+                Mb[17] = s2 * g[15];
+                Mb[18] = -s2 * (g[10] + g[14]);
+                Mb[19] = -s6 * (g[11] + g[15]);
+                double* out = p.Mbar + static_cast<size_t>(src) * NCOMP * NCELL + scell;
+#pragma unroll
+                for (int q = 0; q < 20; ++q) out[q * NCELL] = Mb[q];
+            }
+        } else if ((MODE & 2) && p.mbar != nullptr) {
+            walk_adjoint<false>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+            walk_adjoint<false>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
+            const double v = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+            if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = v;
+            else p.mbar[static_cast<size_t>(src) * NCELL + scell] = v;
+        }
+        __syncwarp();
+        if (!persistent) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// prescaling (once per cell)
+// ---------------------------------------------------------------------------
+
+// Mhat (reduced): (-1)^m/m! * multiplicity * h^-m * M, zz-traces folded.
+__global__ void prescale_moments_kernel(const PrepParams p) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.n_list * NCELL) return;
+    const int node = __ldg(p.nodes + t / NCELL), cell = t % NCELL;
+    const double h1 = p.hinv[__ldg(p.ninfo + node) & 0xff], h2 = h1 * h1, h3 = h2 * h1;
+    const double* M = p.src + static_cast<size_t>(node) * NCOMP * NCELL + cell;
+    double v[20];
+#pragma unroll
+    for (int q = 0; q < 20; ++q) v[q] = M[q * NCELL];
+    const double Mxx = 0.5 * h2 * v[4], Myy = 0.5 * h2 * v[7], Mzz = 0.5 * h2 * v[9];
+    const double a6 = -h3 / 6.0, a2 = -0.5 * h3;
+    const double Mxzz = a2 * v[15], Myzz = a2 * v[18], Mzzz = a6 * v[19];
+    double r[16];
+    r[0] = v[0];
+    r[1] = -h1 * v[1];
+    r[2] = -h1 * v[2];
+    r[3] = -h1 * v[3];
+    r[4] = Mxx - Mzz;
+    r[5] = h2 * v[5];
+    r[6] = h2 * v[6];
+    r[7] = Myy - Mzz;
+    r[8] = h2 * v[8];
+    r[9] = a6 * v[10] - Mxzz;
+    r[10] = a2 * v[11] - Myzz;
+    r[11] = a2 * v[12] - Mzzz;
+    r[12] = a2 * v[13] - Mxzz;
+    r[13] = -h3 * v[14];
+    r[14] = a6 * v[16] - Myzz;
+    r[15] = a2 * v[17] - Mzzz;
+    double* o = p.dst + static_cast<size_t>(node) * NRED * NCELL + cell;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) o[q * NCELL] = r[q];
+}
+
+// Lrbar (reduced): h^-(n+1) * Lbar, with the adjoint of the derived
+// components zz, xzz, yzz, zzz folded in.
+__global__ void prescale_adjoint_kernel(const PrepParams p) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.n_list * NCELL) return;
+    const int node = __ldg(p.nodes + t / NCELL), cell = t % NCELL;
+    const double h1 = p.hinv[__ldg(p.ninfo + node) & 0xff], h2 = h1 * h1, h3 = h2 * h1, h4 = h2 * h2;
+    const double* Lb = p.src + static_cast<size_t>(node) * NCOMP * NCELL + cell;
+    double v[20];
+#pragma unroll
+    for (int q = 0; q < 20; ++q) v[q] = Lb[q * NCELL];
+    double r[16];
+    r[0] = h1 * v[0];
+    r[1] = h2 * v[1];
+    r[2] = h2 * v[2];
+    r[3] = h2 * v[3];
+    r[4] = h3 * (v[4] - v[9]);
+    r[5] = h3 * v[5];
+    r[6] = h3 * v[6];
+    r[7] = h3 * (v[7] - v[9]);
+    r[8] = h3 * v[8];
+    r[9] = h4 * (v[10] - v[15]);
+    r[10] = h4 * (v[11] - v[18]);
+    r[11] = h4 * (v[12] - v[19]);
+    r[12] = h4 * (v[13] - v[15]);
+    r[13] = h4 * v[14];
+    r[14] = h4 * (v[16] - v[18]);
+    r[15] = h4 * (v[17] - v[19]);
+    double* o = p.dst + static_cast<size_t>(node) * NRED * NCELL + cell;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) o[q * NCELL] = r[q];
+}
+
+// mbar[P][c] += sum over its virtual descendant cells of 8^-d vbar
+__global__ void restrict_virtual_kernel(const double* __restrict__ vbar, const int* __restrict__ vmap,
+                                        int n_rows, double* __restrict__ mbar) {
+    // vmap: [n_rows] row headers (target P*512+c), then [n_rows+1] offsets,
+    // then entries (v*512 + s) | d << 28
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_rows) return;
+    const int* ptr = vmap + n_rows;
+    const int* ent = vmap + 2 * n_rows + 1;
+    double acc = 0.0;
+    for (int k = ptr[t]; k < ptr[t + 1]; ++k) {
+        const int e = ent[k];
+        acc += vbar[e & 0x0fffffff] * pow2i(-3 * (e >> 28));
+    }
+    mbar[vmap[t]] += acc;
+}
+
+// ---------------------------------------------------------------------------
+// moments
+// ---------------------------------------------------------------------------
+
+// exponent triples of the 20 stored components
+__constant__ int c_exp[20][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0}, {1, 0, 1},
+                                 {0, 2, 0}, {0, 1, 1}, {0, 0, 2}, {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0},
+                                 {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}};
+
+__device__ __forceinline__ int comp_of_exp(int a, int b, int c) {
+    const int k = a + b + c;
+    // position of (a,b,c) among the rank-k components in storage order
+    const int base = (k == 0) ? 0 : (k == 1) ? 1 : (k == 2) ? 4 : 10;
+    int idx = 0;
+    for (int q = base; q < base + (k + 1) * (k + 2) / 2; ++q) {
+        if (c_exp[q][0] == a && c_exp[q][1] == b && c_exp[q][2] == c) idx = q;
+    }
+    return idx;
+}
+
+__device__ __forceinline__ double binom3(int n, int k) {  // n <= 3
+    const double t[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+    return t[n][k];
+}
+
+// one-dimensional binomial shift of raw moments along `axis` by `d`
+__device__ void shift_axis(double (&M)[20], int axis, double d) {
+    double out[20];
+    for (int q = 0; q < 20; ++q) {
+        const int e[3] = {c_exp[q][0], c_exp[q][1], c_exp[q][2]};
+        double acc = 0.0;
+        double dp = 1.0;
+        for (int j = e[axis]; j >= 0; --j) {   // source exponent j along axis
+            int f[3] = {e[0], e[1], e[2]};
+            f[axis] = j;
+            acc = fma(binom3(e[axis], j) * dp, M[comp_of_exp(f[0], f[1], f[2])], acc);
+            dp *= d;
+        }
+        out[q] = acc;
+    }
+    for (int q = 0; q < 20; ++q) M[q] = out[q];
+}
+
+// transpose of shift_axis
+__device__ void shift_axis_t(double (&M)[20], int axis, double d) {
+    double out[20];
+    for (int q = 0; q < 20; ++q) out[q] = 0.0;
+    for (int q = 0; q < 20; ++q) {
+        const int e[3] = {c_exp[q][0], c_exp[q][1], c_exp[q][2]};
+        double dp = 1.0;
+        for (int j = e[axis]; j >= 0; --j) {
+            int f[3] = {e[0], e[1], e[2]};
+            f[axis] = j;
+            const int s = comp_of_exp(f[0], f[1], f[2]);
+            out[s] = fma(binom3(e[axis], j) * dp, M[q], out[s]);
+            dp *= d;
+        }
+    }
+    for (int q = 0; q < 20; ++q) M[q] = out[q];
+}
+
+__global__ void cube_moments_kernel(const double* __restrict__ rho, double* __restrict__ M, double* __restrict__ m,
+                                    const int* __restrict__ nodes, int n_list, const int* __restrict__ ninfo,
+                                    const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * NCELL) return;
+    const int node = nodes[t / NCELL], cell = t % NCELL;
+    const double h = 1.0 / hinv[ninfo[node] & 0xff];
+    const double r = rho[static_cast<size_t>(node) * NCELL + cell];
+    const double m0 = r * h * h * h;
+    const double q2 = m0 * h * h / 12.0;
+    double* o = M + static_cast<size_t>(node) * NCOMP * NCELL + cell;
+    for (int q = 0; q < 20; ++q) o[q * NCELL] = 0.0;
+    o[0] = m0;
+    o[4 * NCELL] = q2;
+    o[7 * NCELL] = q2;
+    o[9 * NCELL] = q2;
+    m[static_cast<size_t>(node) * NCELL + cell] = m0;
+}
+
+// parents[k]: node index; children[8k + b]: child node of octant b (x fastest)
+__global__ void m2m_kernel(double* __restrict__ M, double* __restrict__ m, const int* __restrict__ parents,
+                           int n_list, const int* __restrict__ children, const int* __restrict__ ninfo,
+                           const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * NCELL) return;
+    const int k = t / NCELL, cell = t % NCELL;
+    const int P = parents[k];
+    const int gx = cell & 7, gy = (cell >> 3) & 7, gz = cell >> 6;
+    const double hc = 0.5 / hinv[ninfo[P] & 0xff];
+    double acc[20];
+    for (int q = 0; q < 20; ++q) acc[q] = 0.0;
+    for (int b = 0; b < 8; ++b) {
+        const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+        const int cx = 2 * gx + bx, cy = 2 * gy + by, cz = 2 * gz + bz;   // in [0, 16)
+        const int oct = (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3);
+        const int C = children[8 * k + oct];
+        const int ccell = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
+        double v[20];
+        const double* src = M + static_cast<size_t>(C) * NCOMP * NCELL + ccell;
+        for (int q = 0; q < 20; ++q) v[q] = src[q * NCELL];
+        shift_axis(v, 0, (bx - 0.5) * hc);
+        shift_axis(v, 1, (by - 0.5) * hc);
+        shift_axis(v, 2, (bz - 0.5) * hc);
+        for (int q = 0; q < 20; ++q) acc[q] += v[q];
+    }
+    double* o = M + static_cast<size_t>(P) * NCOMP * NCELL + cell;
+    for (int q = 0; q < 20; ++q) o[q * NCELL] = acc[q];
+    m[static_cast<size_t>(P) * NCELL + cell] = acc[0];
+}
+
+__global__ void moments_adjoint_init_kernel(const double* __restrict__ Mbar, const double* __restrict__ mbar,
+                                            double* __restrict__ Mb, int n) {
+    const size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t total = static_cast<size_t>(n) * NCOMP * NCELL;
+    if (t >= total) return;
+    double v = Mbar ? Mbar[t] : 0.0;
+    const size_t comp = (t / NCELL) % NCOMP;
+    if (comp == 0 && mbar) v += mbar[(t / (NCOMP * NCELL)) * NCELL + t % NCELL];
+    Mb[t] = v;
+}
+
+// children's Mb += transpose of the parent's M2M applied to the parent's Mb
+__global__ void m2m_adjoint_kernel(double* __restrict__ Mb, const int* __restrict__ parents, int n_list,
+                                   const int* __restrict__ children, const int* __restrict__ ninfo,
+                                   const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * 8 * NCELL) return;
+    const int k = t / (8 * NCELL);
+    const int oct = (t / NCELL) % 8, ccell = t % NCELL;
+    const int P = parents[k];
+    const int C = children[8 * k + oct];
+    const int cx = (oct & 1) * 8 + (ccell & 7), cy = ((oct >> 1) & 1) * 8 + ((ccell >> 3) & 7),
+              cz = (oct >> 2) * 8 + (ccell >> 6);
+    const int pcell = (cx >> 1) + 8 * (cy >> 1) + 64 * (cz >> 1);
+    const double hc = 0.5 / hinv[ninfo[P] & 0xff];
+    double v[20];
+    const double* src = Mb + static_cast<size_t>(P) * NCOMP * NCELL + pcell;
+    for (int q = 0; q < 20; ++q) v[q] = src[q * NCELL];
+    shift_axis_t(v, 2, ((cz & 1) - 0.5) * hc);
+    shift_axis_t(v, 1, ((cy & 1) - 0.5) * hc);
+    shift_axis_t(v, 0, ((cx & 1) - 0.5) * hc);
+    double* o = Mb + static_cast<size_t>(C) * NCOMP * NCELL + ccell;
+    for (int q = 0; q < 20; ++q) o[q * NCELL] += v[q];
+}
+
+__global__ void cube_adjoint_kernel(const double* __restrict__ Mb, double* __restrict__ rhobar,
+                                    const int* __restrict__ nodes, int n_list, const int* __restrict__ ninfo,
+                                    const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * NCELL) return;
+    const int node = nodes[t / NCELL], cell = t % NCELL;
+    const double h = 1.0 / hinv[ninfo[node] & 0xff];
+    const double* b = Mb + static_cast<size_t>(node) * NCOMP * NCELL + cell;
+    const double h3 = h * h * h;
+    rhobar[static_cast<size_t>(node) * NCELL + cell] =
+        b[0] * h3 + (b[4 * NCELL] + b[7 * NCELL] + b[9 * NCELL]) * (h3 * h * h / 12.0);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, int iters) {
+    constexpr int K = 16;
+    double a[K];
+    const double b = 0.999999, c = 1e-6 * (1.0 + threadIdx.x * 1e-9);
+#pragma unroll
+    for (int j = 0; j < K; ++j) a[j] = 0.5 + 0.01 * j;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) a[j] = fma(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) s += a[j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    const dim3 block(32 * wpb);
+    const int per = persistent ? 1 : 0;
+    switch (mode) {
+        case 1: forward_kernel<1><<<grid, block, 0, s>>>(p, per); break;
+        case 2: forward_kernel<2><<<grid, block, 0, s>>>(p, per); break;
+        default: forward_kernel<3><<<grid, block, 0, s>>>(p, per); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wpb, int grid, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    const dim3 block(32 * wpb);
+    const int per = persistent ? 1 : 0;
+    switch (mode) {
+        case 1: adjoint_kernel<1><<<grid, block, 0, s>>>(p, per); break;
+        case 2: adjoint_kernel<2><<<grid, block, 0, s>>>(p, per); break;
+        default: adjoint_kernel<3><<<grid, block, 0, s>>>(p, per); break;
+    }
+    return cudaGetLastError();
+}
+
+int forward_max_blocks_per_sm(int mode, int wpb) {
+    int n = 0;
+    const void* f = (mode == 1) ? (const void*)forward_kernel<1>
+                  : (mode == 2) ? (const void*)forward_kernel<2> : (const void*)forward_kernel<3>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
+    return n;
+}
+
+int adjoint_max_blocks_per_sm(int mode, int wpb) {
+    int n = 0;
+    const void* f = (mode == 1) ? (const void*)adjoint_kernel<1>
+                  : (mode == 2) ? (const void*)adjoint_kernel<2> : (const void*)adjoint_kernel<3>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
+    return n;
+}
+
+static inline int blocks_for(long long n, int per) { return static_cast<int>((n + per - 1) / per); }
+
+cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s) {
+    if (p.n_list == 0) return cudaSuccess;
+    prescale_moments_kernel<<<blocks_for(1LL * p.n_list * NCELL, 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s) {
+    if (p.n_list == 0) return cudaSuccess;
+    prescale_adjoint_kernel<<<blocks_for(1LL * p.n_list * NCELL, 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_virtual(const double* vbar, const int* vmap, int n_rows, double* mbar, cudaStream_t s) {
+    if (n_rows == 0) return cudaSuccess;
+    restrict_virtual_kernel<<<blocks_for(n_rows, 256), 256, 0, s>>>(vbar, vmap, n_rows, mbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cube_moments(const double* rho, double* M, double* m, const int* nodes, int n_list,
+                                const int* ninfo, const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    cube_moments_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(rho, M, m, nodes, n_list, ninfo, hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2m(double* M, double* m, const int* parents, int n_list, const int* children,
+                       const int* ninfo, const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    m2m_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(M, m, parents, n_list, children, ninfo, hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_adjoint_init(const double* Mbar, const double* mbar, double* Mb, int n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    moments_adjoint_init_kernel<<<blocks_for(1LL * n * NCOMP * NCELL, 256), 256, 0, s>>>(Mbar, mbar, Mb, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2m_adjoint(double* Mb, const int* parents, int n_list, const int* children, const int* ninfo,
+                               const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    m2m_adjoint_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(Mb, parents, n_list, children,
+                                                                                  ninfo, hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nodes, int n_list, const int* ninfo,
+                                const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    cube_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(Mb, rhobar, nodes, n_list, ninfo, hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {
+    fp64_probe_kernel<<<blocks, 256, 0, s>>>(out, iters);
+    return cudaGetLastError();
+}
+
+}  // namespace otk

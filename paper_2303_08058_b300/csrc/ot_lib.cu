@@ -1,0 +1,1075 @@
+// Host side of libotfmm: grid geometry (neighbour tables, stencils, the
+// derivative table, virtual descendants), work lists and their ordering,
+// CUDA-graph capture and replay, the tile-shape autotuner, and the C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ot.h"
+#include "ot_internal.h"
+
+using namespace otk;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+static ot_status fail(ot_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define OT_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(OT_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                        __FILE__, __LINE__);                                                 \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// derivative table: d^K G for G = -1/|R| at integer R, by composing truncated
+// multivariate Taylor series:  |R + e|^2 = r^2 (1 + w),  w = (2 R.e + e.e) / r^2,
+// (1 + w)^(-1/2) = sum_k binom(-1/2, k) w^k, truncated at total degree 4;
+// d^K G = K! * (coefficient of e^K).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Poly4 {
+    double c[5][5][5];   // c[a][b][d] for a + b + d <= 4
+    Poly4() { std::memset(c, 0, sizeof(c)); }
+};
+
+Poly4 pmul(const Poly4& x, const Poly4& y) {
+    Poly4 z;
+    for (int a = 0; a <= 4; ++a)
+        for (int b = 0; a + b <= 4; ++b)
+            for (int d = 0; a + b + d <= 4; ++d) {
+                if (x.c[a][b][d] == 0.0) continue;
+                for (int e = 0; a + e <= 4; ++e)
+                    for (int f = 0; a + b + e + f <= 4; ++f)
+                        for (int g = 0; a + b + d + e + f + g <= 4; ++g)
+                            z.c[a + e][b + f][d + g] += x.c[a][b][d] * y.c[e][f][g];
+            }
+    return z;
+}
+
+double fact(int k) {
+    double r = 1.0;
+    for (int i = 2; i <= k; ++i) r *= i;
+    return r;
+}
+
+// row layout: IND16 (ranks 0..3 with at most one z), zz xzz yzz zzz, rank 4 in storage order
+const int ROW_EXP[35][3] = {
+    {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1},
+    {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1}, {0, 3, 0}, {0, 2, 1},
+    {0, 0, 2}, {1, 0, 2}, {0, 1, 2}, {0, 0, 3},
+    {4, 0, 0}, {3, 1, 0}, {3, 0, 1}, {2, 2, 0}, {2, 1, 1}, {2, 0, 2}, {1, 3, 0}, {1, 2, 1}, {1, 1, 2},
+    {1, 0, 3}, {0, 4, 0}, {0, 3, 1}, {0, 2, 2}, {0, 1, 3}, {0, 0, 4}};
+
+void derivative_row(const double R[3], double* row) {
+    const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    Poly4 w;
+    w.c[1][0][0] = 2.0 * R[0] / r2;
+    w.c[0][1][0] = 2.0 * R[1] / r2;
+    w.c[0][0][1] = 2.0 * R[2] / r2;
+    w.c[2][0][0] = 1.0 / r2;
+    w.c[0][2][0] = 1.0 / r2;
+    w.c[0][0][2] = 1.0 / r2;
+    // binom(-1/2, k): 1, -1/2, 3/8, -5/16, 35/128 ; Horner in w
+    const double bk[5] = {1.0, -0.5, 0.375, -0.3125, 0.2734375};
+    Poly4 s;
+    s.c[0][0][0] = bk[4];
+    for (int k = 3; k >= 0; --k) {
+        s = pmul(s, w);
+        s.c[0][0][0] += bk[k];
+    }
+    const double scale = -1.0 / std::sqrt(r2);
+    for (int q = 0; q < 35; ++q) {
+        const int a = ROW_EXP[q][0], b = ROW_EXP[q][1], d = ROW_EXP[q][2];
+        row[q] = scale * s.c[a][b][d] * fact(a) * fact(b) * fact(d);
+    }
+    row[35] = 0.0;
+}
+
+inline int pack_offset(int ox, int oy, int oz) { return (ox + 8) | ((oy + 8) << 8) | ((oz + 8) << 16); }
+inline int fdiv2(int a) { return (a >= 0) ? a / 2 : -((1 - a) / 2); }   // floor(a / 2)
+
+inline uint64_t node_key(int l, int x, int y, int z) {
+    return (static_cast<uint64_t>(l) << 60) | (static_cast<uint64_t>(x) << 40) |
+           (static_cast<uint64_t>(y) << 20) | static_cast<uint64_t>(z);
+}
+
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the grid handle
+// ---------------------------------------------------------------------------
+
+struct GraphKey {
+    int op;
+    const void* a;
+    const void* b;
+    const void* c;
+    const void* d;
+    int w, bps;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(op, a, b, c, d, w, bps) < std::tie(o.op, o.a, o.b, o.c, o.d, o.w, o.bps);
+    }
+};
+
+struct M2MLevel {
+    int level;
+    std::vector<int> parents;
+    std::vector<int> children;   // 8 per parent, octant x fastest
+    int* d_parents = nullptr;
+    int* d_children = nullptr;
+};
+
+struct ot_grid {
+    int n = 0, nvirt = 0, max_level = 0, device = 0, num_sms = 0;
+    double h0 = 1.0;
+    std::vector<int> level, is_leaf;
+    std::vector<int2> nbr, vnbr;
+    std::vector<int> ninfo, vinfo;
+    std::vector<int> lists;
+    int far_len = 0, near_len = 0, root_len = 0;
+    double hinv[MAXLEV];
+
+    // device buffers
+    std::vector<void*> allocs;
+    int2* d_nbr = nullptr;
+    int2* d_vnbr = nullptr;
+    int* d_ninfo = nullptr;
+    int* d_vinfo = nullptr;
+    double* d_Dt = nullptr;
+    int* d_lists = nullptr;
+    double* d_hinv = nullptr;
+    int* d_items_fwd[4] = {nullptr, nullptr, nullptr, nullptr};     // LPT order, by mode
+    int n_items_fwd[4] = {0, 0, 0, 0};
+    int* d_items_fwd_node = nullptr;                                 // node order (plain path)
+    std::vector<int> node_item_start;                                // [n + 1] into d_items_fwd_node
+    int* d_items_adj[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n_items_adj[4] = {0, 0, 0, 0};
+    int* d_items_adj_node[4] = {nullptr, nullptr, nullptr, nullptr};   // source order (plain path)
+    std::vector<int> adj_item_start[4];                                // [n + nvirt + 1]
+    int maxb_fwd[4][9] = {};
+    int maxb_adj[4][9] = {};
+    int* d_nonleaf = nullptr;
+    int n_nonleaf = 0;
+    int* d_all = nullptr;
+    int* d_cube = nullptr;
+    int n_cube = 0;
+    std::vector<M2MLevel> m2m;       // deepest parents first
+    int* d_vmap = nullptr;
+    int vmap_rows = 0;
+    double* d_Mhat = nullptr;
+    double* d_Lrbar = nullptr;
+    double* d_vbar = nullptr;
+    double* d_Mb = nullptr;
+    int* d_counters = nullptr;       // [0] forward, [1] adjoint
+    int* d_status = nullptr;         // [2]
+    cudaStream_t cap_stream = nullptr;
+
+    int schedule = OT_SCHED_PERSISTENT;
+    int wpb = 4, bps = 0, use_graph = 1;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+
+    ot_grid_info_t info{};
+
+    template <class T>
+    ot_status alloc(T** out, size_t count) {
+        void* p = nullptr;
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(OT_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+        }
+        allocs.push_back(p);
+        *out = static_cast<T*>(p);
+        return OT_OK;
+    }
+
+    template <class T>
+    ot_status upload(T** out, const std::vector<T>& v, cudaStream_t s) {
+        ot_status st = alloc(out, v.size());
+        if (st != OT_OK) return st;
+        if (!v.empty()) OT_CUDA(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        return OT_OK;
+    }
+
+    ~ot_grid() {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        for (void* p : allocs) cudaFree(p);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Builder {
+    const ot_grid_desc* desc;
+    std::unordered_map<uint64_t, int> index;
+
+    int find(int l, long x, long y, long z) const {
+        if (l < 0 || x < 0 || y < 0 || z < 0) return -1;
+        const long s = 1L << l;
+        if (x >= s || y >= s || z >= s) return -1;
+        auto it = index.find(node_key(l, (int)x, (int)y, (int)z));
+        return it == index.end() ? -1 : it->second;
+    }
+
+    // neighbour entry for same-level node position q at level l
+    ot_status entry(int l, const long q[3], bool for_adjoint, int2* out, int* vdepth, long* vq) const {
+        out->x = -1;
+        out->y = K_NONE;
+        *vdepth = 0;
+        const long s = 1L << l;
+        for (int a = 0; a < 3; ++a)
+            if (q[a] < 0 || q[a] >= s) return OT_OK;
+        int j = find(l, q[0], q[1], q[2]);
+        if (j >= 0) {
+            out->x = j;
+            out->y = desc->is_leaf[j] ? K_LEAF : K_MULTI;
+            return OT_OK;
+        }
+        if (for_adjoint) return OT_OK;     // targets are real nodes only
+        for (int d = 1; d <= l; ++d) {
+            j = find(l - d, q[0] >> d, q[1] >> d, q[2] >> d);
+            if (j < 0) continue;
+            if (!desc->is_leaf[j]) return OT_OK;   // covered by a non-leaf without finer data
+            if (d > 5) return fail(OT_EINVAL, "virtual descendant %d levels below its leaf (max 5)", d);
+            unsigned ov[3];
+            for (int a = 0; a < 3; ++a) ov[a] = static_cast<unsigned>(8 * (q[a] - ((q[a] >> d) << d)));
+            out->x = j;
+            out->y = static_cast<int>(K_VIRT | (d << 2) | (ov[0] << 8) | (ov[1] << 16) | (ov[2] << 24));
+            *vdepth = d;
+            for (int a = 0; a < 3; ++a) vq[a] = q[a];
+            return OT_OK;
+        }
+        return OT_OK;
+    }
+};
+
+}  // namespace
+
+static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s) {
+    const int n = desc->n_subgrids;
+    g->n = n;
+    g->h0 = desc->h0;
+    g->level.assign(desc->level, desc->level + n);
+    g->is_leaf.resize(n);
+    Builder B;
+    B.desc = desc;
+    B.index.reserve(static_cast<size_t>(n) * 2);
+    g->max_level = 0;
+    for (int i = 0; i < n; ++i) {
+        const int l = desc->level[i];
+        if (l < 0 || l >= MAXLEV) return fail(OT_EINVAL, "node %d: level %d outside [0, %d]", i, l, MAXLEV - 1);
+        const long s = 1L << l;
+        for (int a = 0; a < 3; ++a) {
+            const int c = desc->coord[3 * i + a];
+            if (c < 0 || c >= s) return fail(OT_EINVAL, "node %d: coord %d outside [0, 2^%d)", i, c, l);
+        }
+        if (desc->is_leaf[i] > 1) return fail(OT_EINVAL, "node %d: is_leaf must be 0 or 1", i);
+        g->is_leaf[i] = desc->is_leaf[i];
+        auto ins = B.index.emplace(node_key(l, desc->coord[3 * i], desc->coord[3 * i + 1], desc->coord[3 * i + 2]), i);
+        if (!ins.second) return fail(OT_EINVAL, "node %d duplicates node %d", i, ins.first->second);
+        g->max_level = std::max(g->max_level, l);
+    }
+    for (int l = 0; l < MAXLEV; ++l) g->hinv[l] = std::ldexp(1.0, l) / desc->h0;
+
+    // --- stencils -------------------------------------------------------------
+    const int c = 12;
+    std::vector<int> far[8], near, root;
+    for (int p = 0; p < 8; ++p) {
+        const int px = p & 1, py = (p >> 1) & 1, pz = (p >> 2) & 1;
+        for (int oz = -7; oz <= 7; ++oz)
+            for (int oy = -7; oy <= 7; ++oy)
+                for (int ox = -7; ox <= 7; ++ox) {
+                    const int n2 = ox * ox + oy * oy + oz * oz;
+                    const int qx = fdiv2(px + ox), qy = fdiv2(py + oy), qz = fdiv2(pz + oz);
+                    if (n2 > c && qx * qx + qy * qy + qz * qz <= c) far[p].push_back(pack_offset(ox, oy, oz));
+                }
+    }
+    for (int oz = -7; oz <= 7; ++oz)
+        for (int oy = -7; oy <= 7; ++oy)
+            for (int ox = -7; ox <= 7; ++ox) {
+                const int n2 = ox * ox + oy * oy + oz * oz;
+                if (n2 > 0 && n2 <= c) near.push_back(pack_offset(ox, oy, oz));
+                if (n2 > c) root.push_back(pack_offset(ox, oy, oz));
+            }
+    for (int p = 1; p < 8; ++p)
+        if (far[p].size() != far[0].size()) return fail(OT_EINVAL, "internal: parity stencils differ in size");
+    g->far_len = static_cast<int>(far[0].size());
+    g->near_len = static_cast<int>(near.size());
+    g->root_len = static_cast<int>(root.size());
+    g->lists.clear();
+    for (int p = 0; p < 8; ++p) g->lists.insert(g->lists.end(), far[p].begin(), far[p].end());
+    g->lists.insert(g->lists.end(), near.begin(), near.end());
+    g->lists.insert(g->lists.end(), root.begin(), root.end());
+
+    // --- derivative table ----------------------------------------------------
+    std::vector<double> Dt(static_cast<size_t>(NOFF) * DROW, 0.0);
+    for (int oz = -7; oz <= 7; ++oz)
+        for (int oy = -7; oy <= 7; ++oy)
+            for (int ox = -7; ox <= 7; ++ox) {
+                if (ox == 0 && oy == 0 && oz == 0) continue;
+                const double R[3] = {-1.0 * ox, -1.0 * oy, -1.0 * oz};
+                derivative_row(R, &Dt[static_cast<size_t>((ox + 7) + 15 * (oy + 7) + 225 * (oz + 7)) * DROW]);
+            }
+
+    // --- neighbour tables, virtual descendants --------------------------------
+    g->nbr.assign(static_cast<size_t>(n) * 27, int2{-1, K_NONE});
+    g->ninfo.resize(n);
+    std::map<std::tuple<int, long, long, long>, int> vindex;   // (level, q) -> virtual id
+    struct VNode { int level; long q[3]; int leaf; int d; };
+    std::vector<VNode> vnodes;
+    for (int i = 0; i < n; ++i) {
+        const int l = desc->level[i];
+        g->ninfo[i] = l | (g->is_leaf[i] << 8);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const long q[3] = {desc->coord[3 * i] + dx, desc->coord[3 * i + 1] + dy,
+                                       desc->coord[3 * i + 2] + dz};
+                    int2 e;
+                    int vd;
+                    long vq[3];
+                    ot_status st = B.entry(l, q, false, &e, &vd, vq);
+                    if (st != OT_OK) return st;
+                    g->nbr[static_cast<size_t>(i) * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = e;
+                    if ((e.y & 3) == K_VIRT) {
+                        auto key = std::make_tuple(l, q[0], q[1], q[2]);
+                        if (!vindex.count(key)) {
+                            vindex[key] = static_cast<int>(vnodes.size());
+                            vnodes.push_back(VNode{l, {q[0], q[1], q[2]}, e.x, vd});
+                        }
+                    }
+                }
+    }
+    g->nvirt = static_cast<int>(vnodes.size());
+    g->vnbr.assign(static_cast<size_t>(std::max(g->nvirt, 1)) * 27, int2{-1, K_NONE});
+    g->vinfo.assign(std::max(g->nvirt, 1), 0);
+    std::vector<std::pair<int, int>> vrows;   // (P*512 + pcell, entry)
+    for (int v = 0; v < g->nvirt; ++v) {
+        const VNode& V = vnodes[v];
+        g->vinfo[v] = V.level;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const long q[3] = {V.q[0] + dx, V.q[1] + dy, V.q[2] + dz};
+                    int2 e;
+                    int vd;
+                    long vq[3];
+                    ot_status st = B.entry(V.level, q, true, &e, &vd, vq);
+                    if (st != OT_OK) return st;
+                    g->vnbr[static_cast<size_t>(v) * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = e;
+                }
+        for (int sc = 0; sc < NCELL; ++sc) {
+            const int s3[3] = {sc & 7, (sc >> 3) & 7, sc >> 6};
+            int pc[3];
+            for (int a = 0; a < 3; ++a) {
+                const long ov = 8 * (V.q[a] - ((V.q[a] >> V.d) << V.d));
+                pc[a] = static_cast<int>((ov + s3[a]) >> V.d);
+            }
+            const int row = V.leaf * NCELL + pc[0] + 8 * pc[1] + 64 * pc[2];
+            vrows.emplace_back(row, (v * NCELL + sc) | (V.d << 28));
+        }
+    }
+    if (static_cast<long long>(g->nvirt) * NCELL >= (1LL << 28))
+        return fail(OT_EINVAL, "too many virtual descendant sub-grids (%d)", g->nvirt);
+    std::stable_sort(vrows.begin(), vrows.end(),
+                     [](const std::pair<int, int>& a, const std::pair<int, int>& b) { return a.first < b.first; });
+    std::vector<int> vmap;
+    {
+        std::vector<int> heads, ptr, ent;
+        for (size_t k = 0; k < vrows.size(); ++k) {
+            if (k == 0 || vrows[k].first != vrows[k - 1].first) {
+                heads.push_back(vrows[k].first);
+                ptr.push_back(static_cast<int>(k));
+            }
+            ent.push_back(vrows[k].second);
+        }
+        ptr.push_back(static_cast<int>(vrows.size()));
+        g->vmap_rows = static_cast<int>(heads.size());
+        vmap = heads;
+        vmap.insert(vmap.end(), ptr.begin(), ptr.end());
+        vmap.insert(vmap.end(), ent.begin(), ent.end());
+    }
+
+    // --- exact pair counts and per-item costs --------------------------------
+    // lane patterns: for each (parity, half) and list entry, which of the 27
+    // neighbours the warp's 32 cells reach; per neighbour, how many cells.
+    const int seg_len[3] = {g->far_len, g->near_len, g->root_len};
+    std::vector<uint32_t> mask[16][3];
+    long long cnt[3][27];
+    std::memset(cnt, 0, sizeof(cnt));
+    for (int ph = 0; ph < 16; ++ph) {
+        const int par = ph >> 1, half = ph & 1;
+        for (int sg = 0; sg < 3; ++sg) {
+            const int* lst = (sg == 0) ? &g->lists[par * g->far_len]
+                           : (sg == 1) ? &g->lists[8 * g->far_len] : &g->lists[8 * g->far_len + g->near_len];
+            mask[ph][sg].resize(seg_len[sg]);
+            for (int k = 0; k < seg_len[sg]; ++k) {
+                const int po = lst[k];
+                const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+                uint32_t m = 0;
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int tx = (par & 1) + 2 * (lane & 3), ty = ((par >> 1) & 1) + 2 * ((lane >> 2) & 3),
+                              tz = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
+                    const int nb = ((tx + ox + 8) >> 3) + 3 * ((ty + oy + 8) >> 3) + 9 * ((tz + oz + 8) >> 3);
+                    m |= 1u << nb;
+                    cnt[sg][nb]++;
+                }
+                mask[ph][sg][k] = m;
+            }
+        }
+    }
+    // forward costs (FMAs per lane) and counts
+    long long pairs_multi = 0, pairs_mono = 0, pairs_virt = 0, padded = 0, flops_multi_ang = 0, fma_fwd = 0,
+              fma_adj = 0;
+    std::vector<std::pair<long long, int>> fwd[4];
+    std::vector<int> node_order_items;
+    g->node_item_start.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        uint32_t mm = 0, mo = 0, mv = 0;
+        for (int j = 0; j < 27; ++j) {
+            const int k = g->nbr[static_cast<size_t>(i) * 27 + j].y & 3;
+            if (k == K_MULTI) mm |= 1u << j;
+            if (k == K_LEAF || k == K_VIRT) mo |= 1u << j;
+            if (k == K_VIRT) mv |= 1u << j;
+        }
+        const bool leaf = g->is_leaf[i];
+        const int s1 = (desc->level[i] == 0) ? 2 : 0;
+        for (int j = 0; j < 27; ++j) {
+            // cnt[sg][j] already sums over all 512 target cells of a sub-grid
+            const long long c1 = cnt[s1][j];
+            const long long cn = leaf ? cnt[1][j] : 0;
+            if (mm >> j & 1u) {
+                pairs_multi += c1 + cn;
+                if (!leaf) flops_multi_ang += c1;
+            }
+            if (mo >> j & 1u) pairs_mono += c1 + cn;
+            if (mv >> j & 1u) pairs_virt += c1 + cn;
+        }
+        g->node_item_start[i] = static_cast<int>(node_order_items.size());
+        for (int ph = 0; ph < 16; ++ph) {
+            const int par = ph >> 1;
+            long long cost[4] = {0, 0, 0, 0};   // by mode bit: [1] multi, [2] mono
+            long long lanes_m = 0, lanes_o = 0;
+            const int multi_fma = leaf ? 70 : 100;
+            auto scan = [&](int sg) {
+                const std::vector<uint32_t>& mk = mask[ph][sg];
+                for (size_t k = 0; k < mk.size(); ++k) {
+                    if (mk[k] & mm) { cost[1] += multi_fma; lanes_m += 32; }
+                    if (mk[k] & mo) { cost[2] += 16; lanes_o += 32; }
+                }
+            };
+            (void)par;
+            scan(s1);
+            if (leaf) scan(1);
+            padded += lanes_m + lanes_o;
+            fma_fwd += 32 * (cost[1] + cost[2]);
+            const int item = (i << 4) | ph;
+            node_order_items.push_back(item);
+            for (int mode = 1; mode <= 3; ++mode) {
+                long long cst = ((mode & 1) ? cost[1] : 0) + ((mode & 2) ? cost[2] : 0);
+                if (cst > 0) fwd[mode].emplace_back(cst, item);
+            }
+        }
+    }
+    g->node_item_start[n] = static_cast<int>(node_order_items.size());
+    for (int mode = 1; mode <= 3; ++mode)
+        std::stable_sort(fwd[mode].begin(), fwd[mode].end(),
+                         [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
+                             return a.first > b.first;
+                         });
+    // adjoint items: real sources by class, virtual sources
+    std::vector<std::pair<long long, int>> adj[4];
+    auto adj_cost = [&](const int2* tbl, int lvl, int per_pair, int ph) {
+        uint32_t tv = 0, tl = 0;
+        for (int j = 0; j < 27; ++j) {
+            const int k = tbl[j].y & 3;
+            if (k == K_MULTI || k == K_LEAF) tv |= 1u << j;
+            if (k == K_LEAF) tl |= 1u << j;
+        }
+        long long cst = 0;
+        const int s1 = (lvl == 0) ? 2 : 0;
+        for (uint32_t m : mask[ph][s1]) if (m & tv) cst += per_pair;
+        for (uint32_t m : mask[ph][1]) if (m & tl) cst += per_pair;
+        return cst;
+    };
+    std::vector<int> adj_node[4];
+    for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode].assign(n + g->nvirt + 1, 0);
+    for (int i = 0; i < n + g->nvirt; ++i) {
+        const bool virt = i >= n;
+        const bool leaf = virt || g->is_leaf[i];
+        const int2* tbl = virt ? &g->vnbr[static_cast<size_t>(i - n) * 27] : &g->nbr[static_cast<size_t>(i) * 27];
+        const int lvl = virt ? g->vinfo[i - n] : desc->level[i];
+        const int bit = leaf ? 2 : 1;
+        for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode][i] = static_cast<int>(adj_node[mode].size());
+        for (int ph = 0; ph < 16; ++ph) {
+            const long long cst = adj_cost(tbl, lvl, leaf ? 16 : 70, ph);
+            if (cst == 0) continue;
+            fma_adj += 32 * cst;
+            const int item = (i << 4) | ph;
+            for (int mode = 1; mode <= 3; ++mode)
+                if (mode & bit) {
+                    adj[mode].emplace_back(cst, item);
+                    adj_node[mode].push_back(item);
+                }
+        }
+    }
+    for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode][n + g->nvirt] = static_cast<int>(adj_node[mode].size());
+    for (int mode = 1; mode <= 3; ++mode)
+        std::stable_sort(adj[mode].begin(), adj[mode].end(),
+                         [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
+                             return a.first > b.first;
+                         });
+    if (static_cast<long long>(n + g->nvirt) >= (1LL << 27)) return fail(OT_EINVAL, "too many sub-grids");
+
+    // --- M2M schedule ---------------------------------------------------------
+    std::vector<int> nonleaf, all(n), cube;
+    for (int i = 0; i < n; ++i) {
+        all[i] = i;
+        if (!g->is_leaf[i]) nonleaf.push_back(i);
+    }
+    std::map<int, M2MLevel> lv;
+    for (int i = 0; i < n; ++i) {
+        const int l = desc->level[i];
+        int ch[8];
+        int nch = 0;
+        for (int b = 0; b < 8; ++b) {
+            ch[b] = B.find(l + 1, 2L * desc->coord[3 * i] + (b & 1), 2L * desc->coord[3 * i + 1] + ((b >> 1) & 1),
+                           2L * desc->coord[3 * i + 2] + (b >> 2));
+            if (ch[b] >= 0) nch++;
+        }
+        if (nch == 8) {
+            M2MLevel& L = lv[l];
+            L.level = l;
+            L.parents.push_back(i);
+            L.children.insert(L.children.end(), ch, ch + 8);
+        } else {
+            cube.push_back(i);
+        }
+    }
+    g->m2m.clear();
+    for (auto it = lv.rbegin(); it != lv.rend(); ++it) g->m2m.push_back(it->second);
+
+    // --- info -----------------------------------------------------------------
+    ot_grid_info_t& I = g->info;
+    std::memset(&I, 0, sizeof(I));
+    I.n_subgrids = n;
+    I.n_virtual = g->nvirt;
+    I.max_level = g->max_level;
+    I.far_offsets = g->far_len;
+    I.near_offsets = g->near_len;
+    I.root_offsets = g->root_len;
+    I.pairs_multipole = pairs_multi;
+    I.pairs_monopole = pairs_mono;
+    I.pairs_virtual = pairs_virt;
+    I.pairs_angular = flops_multi_ang;
+    I.lanes_fwd = padded;
+    I.fma_fwd = fma_fwd;
+    I.fma_adj = fma_adj;
+    for (int mode = 1; mode <= 3; ++mode)
+        for (int w = 2; w <= 8; w *= 2) {
+            g->maxb_fwd[mode][w] = forward_max_blocks_per_sm(mode, w);
+            g->maxb_adj[mode][w] = adjoint_max_blocks_per_sm(mode, w);
+        }
+
+    // --- uploads ----------------------------------------------------------------
+    ot_status st;
+#define UP(ptr, vec) \
+    if ((st = g->upload(&(ptr), vec, s)) != OT_OK) return st;
+    UP(g->d_nbr, g->nbr);
+    UP(g->d_vnbr, g->vnbr);
+    UP(g->d_ninfo, g->ninfo);
+    UP(g->d_vinfo, g->vinfo);
+    UP(g->d_Dt, Dt);
+    UP(g->d_lists, g->lists);
+    std::vector<double> hv(g->hinv, g->hinv + MAXLEV);
+    UP(g->d_hinv, hv);
+    for (int mode = 1; mode <= 3; ++mode) {
+        std::vector<int> items;
+        for (auto& pr : fwd[mode]) items.push_back(pr.second);
+        g->n_items_fwd[mode] = static_cast<int>(items.size());
+        UP(g->d_items_fwd[mode], items);
+        std::vector<int> aitems;
+        for (auto& pr : adj[mode]) aitems.push_back(pr.second);
+        g->n_items_adj[mode] = static_cast<int>(aitems.size());
+        UP(g->d_items_adj[mode], aitems);
+        UP(g->d_items_adj_node[mode], adj_node[mode]);
+    }
+    UP(g->d_items_fwd_node, node_order_items);
+    g->n_nonleaf = static_cast<int>(nonleaf.size());
+    UP(g->d_nonleaf, nonleaf);
+    UP(g->d_all, all);
+    g->n_cube = static_cast<int>(cube.size());
+    UP(g->d_cube, cube);
+    for (auto& L : g->m2m) {
+        UP(L.d_parents, L.parents);
+        UP(L.d_children, L.children);
+    }
+    UP(g->d_vmap, vmap);
+#undef UP
+    if ((st = g->alloc(&g->d_Mhat, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_counters, 4)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_status, 2)) != OT_OK) return st;
+    OT_CUDA(cudaMemsetAsync(g->d_status, 0, 2 * sizeof(int), s));
+    OT_CUDA(cudaMemsetAsync(g->d_counters, 0, 4 * sizeof(int), s));
+    return OT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static int grid_blocks(ot_grid* g, int bps_max) {
+    int bps = g->bps > 0 ? std::min(g->bps, bps_max) : bps_max;
+    if (bps < 1) bps = 1;
+    return g->num_sms * bps;
+}
+
+static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, int accumulate) {
+    FwdParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.counter = g->d_counters;
+    p.nbr = g->d_nbr;
+    p.ninfo = g->d_ninfo;
+    p.Dt = g->d_Dt;
+    p.L.lists = g->d_lists;
+    p.L.far_len = g->far_len;
+    p.L.near_len = g->near_len;
+    p.L.root_len = g->root_len;
+    p.L.near_off = 8 * g->far_len;
+    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.Mhat = g->d_Mhat;
+    p.m = m;
+    p.Lout = L;
+    p.Lc = Lc;
+    p.accumulate = accumulate;
+    p.n_nodes = g->n;
+    p.status = g->d_status;
+    for (int l = 0; l < MAXLEV; ++l) p.hinv[l] = g->hinv[l];
+    return p;
+}
+
+// enqueue one forward pass (mode 1, 2 or 3) on stream s
+static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const double* m, double* L, double* Lc,
+                                 int accumulate, cudaStream_t s) {
+    const size_t nL = static_cast<size_t>(g->n) * NCOMP * NCELL;
+    if (mode & 1) {
+        PrepParams pp;
+        std::memset(&pp, 0, sizeof(pp));
+        pp.src = M;
+        pp.dst = g->d_Mhat;
+        pp.nodes = g->d_nonleaf;
+        pp.n_list = g->n_nonleaf;
+        pp.ninfo = g->d_ninfo;
+        for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = g->hinv[l];
+        OT_CUDA(launch_prescale_moments(pp, s));
+    }
+    if (!accumulate) OT_CUDA(cudaMemsetAsync(L, 0, nL * sizeof(double), s));
+    if ((mode & 1) && Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
+    FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
+    // zeroed above, so the kernel always accumulates
+    if (g->schedule == OT_SCHED_PER_SUBGRID) {
+        p.items = g->d_items_fwd_node;
+        for (int i = 0; i < g->n; ++i) {
+            FwdParams q = p;
+            q.items = g->d_items_fwd_node + g->node_item_start[i];
+            q.n_items = g->node_item_start[i + 1] - g->node_item_start[i];
+            const int blocks = (q.n_items + g->wpb - 1) / g->wpb;
+            OT_CUDA(launch_forward(q, mode, false, g->wpb, blocks, s));
+        }
+    } else {
+        p.items = g->d_items_fwd[mode];
+        p.n_items = g->n_items_fwd[mode];
+        OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
+        OT_CUDA(launch_forward(p, mode, true, g->wpb, grid_blocks(g, g->maxb_fwd[mode][g->wpb]), s));
+    }
+    return OT_OK;
+}
+
+static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, double* mbar, cudaStream_t s) {
+    const int mode = (Mbar ? 1 : 0) | (mbar ? 2 : 0);
+    if (mode == 0) return OT_OK;
+    PrepParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.src = Lbar;
+    pp.dst = g->d_Lrbar;
+    pp.nodes = g->d_all;
+    pp.n_list = g->n;
+    pp.ninfo = g->d_ninfo;
+    for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = g->hinv[l];
+    OT_CUDA(launch_prescale_adjoint(pp, s));
+    if (Mbar) OT_CUDA(cudaMemsetAsync(Mbar, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
+    if (mbar) OT_CUDA(cudaMemsetAsync(mbar, 0, static_cast<size_t>(g->n) * NCELL * sizeof(double), s));
+    AdjParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.items = g->d_items_adj[mode];
+    p.n_items = g->n_items_adj[mode];
+    p.counter = g->d_counters + 1;
+    p.nbr = g->d_nbr;
+    p.vnbr = g->d_vnbr;
+    p.ninfo = g->d_ninfo;
+    p.vinfo = g->d_vinfo;
+    p.Dt = g->d_Dt;
+    p.L.lists = g->d_lists;
+    p.L.far_len = g->far_len;
+    p.L.near_len = g->near_len;
+    p.L.root_len = g->root_len;
+    p.L.near_off = 8 * g->far_len;
+    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.Lrbar = g->d_Lrbar;
+    p.Mbar = Mbar;
+    p.mbar = mbar;
+    p.vbar = g->d_vbar;
+    p.n_nodes = g->n;
+    p.status = g->d_status;
+    for (int l = 0; l < MAXLEV; ++l) p.hinv[l] = g->hinv[l];
+    if (g->schedule == OT_SCHED_PER_SUBGRID) {
+        // one launch per source sub-grid (real and virtual)
+        const std::vector<int>& st = g->adj_item_start[mode];
+        for (int i = 0; i + 1 < static_cast<int>(st.size()); ++i) {
+            AdjParams q = p;
+            q.items = g->d_items_adj_node[mode] + st[i];
+            q.n_items = st[i + 1] - st[i];
+            if (q.n_items == 0) continue;
+            OT_CUDA(launch_adjoint(q, mode, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s));
+        }
+    } else {
+        OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
+        OT_CUDA(launch_adjoint(p, mode, true, g->wpb, grid_blocks(g, g->maxb_adj[mode][g->wpb]), s));
+    }
+    if (mbar && g->vmap_rows > 0) OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
+    return OT_OK;
+}
+
+// run `body` directly, or capture it once into a graph keyed by `key` and replay
+template <class F>
+static ot_status run_graphed(ot_grid* g, const GraphKey& key, cudaStream_t s, F body) {
+    if (!g->use_graph || g->schedule != OT_SCHED_PERSISTENT) return body(s);
+    auto it = g->graphs.find(key);
+    if (it == g->graphs.end()) {
+        if (g->graphs.size() >= 16) {
+            cudaGraphExecDestroy(g->graphs.begin()->second);
+            g->graphs.erase(g->graphs.begin());
+        }
+        OT_CUDA(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        ot_status st = body(g->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (st != OT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(OT_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(OT_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        it = g->graphs.emplace(key, exec).first;
+    }
+    OT_CUDA(cudaGraphLaunch(it->second, s));
+    return OT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                           \
+    }                                                                       \
+    catch (const std::bad_alloc&) {                                         \
+        return fail(OT_ENOMEM, "host allocation failed");                   \
+    }                                                                       \
+    catch (...) {                                                           \
+        return fail(OT_EINVAL, "unexpected host exception");                \
+    }
+
+#define CHECK_PTR(p, name)                                                          \
+    do {                                                                            \
+        if ((p) == nullptr) return fail(OT_EINVAL, "%s is NULL", name);             \
+        if (!aligned16(p)) return fail(OT_EINVAL, "%s is not 16-byte aligned", name); \
+    } while (0)
+
+extern "C" {
+
+const char* ot_last_error(void) { return g_last_error.c_str(); }
+
+ot_status ot_grid_create(const ot_grid_desc* desc, void* stream, ot_grid** out) {
+    GUARD_BEGIN
+    if (!out) return fail(OT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(OT_EINVAL, "desc is NULL");
+    if (desc->n_subgrids <= 0) return fail(OT_EINVAL, "n_subgrids must be positive");
+    if (!desc->level || !desc->coord || !desc->is_leaf) return fail(OT_EINVAL, "desc arrays must not be NULL");
+    if (!(desc->h0 > 0.0) || !std::isfinite(desc->h0)) return fail(OT_EINVAL, "h0 must be positive and finite");
+    if (desc->stencil_c != 0 && desc->stencil_c != 12)
+        return fail(OT_ENOTSUP, "stencil_c %d not supported (only 12, theta = 0.5)", desc->stencil_c);
+    if (desc->flags != OT_GEOMETRIC_CENTRES) return fail(OT_ENOTSUP, "only geometric expansion centres are built");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ot_grid* g = new ot_grid();
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete g;
+        return fail(OT_ECUDA, "device query failed: %s", cudaGetErrorString(e));
+    }
+    ot_status st = build_grid(g, desc, s);
+    if (st == OT_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail(OT_ECUDA, "upload failed: %s", cudaGetErrorString(e));
+    }
+    if (st != OT_OK) {
+        delete g;
+        return st;
+    }
+    g->info.schedule = g->schedule;
+    g->info.warps_per_block = g->wpb;
+    g->info.blocks_per_sm = g->bps;
+    g->info.graphs_enabled = g->use_graph;
+    *out = g;
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_grid_destroy(ot_grid* grid) {
+    GUARD_BEGIN
+    if (!grid) return OT_OK;
+    cudaDeviceSynchronize();
+    delete grid;
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_grid_info(const ot_grid* grid, ot_grid_info_t* info) {
+    if (!grid || !info) return fail(OT_EINVAL, "grid and info must not be NULL");
+    *info = grid->info;
+    return OT_OK;
+}
+
+ot_status ot_set_schedule(ot_grid* g, int32_t schedule, int32_t warps_per_block, int32_t blocks_per_sm,
+                          int32_t use_graph) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (schedule != OT_SCHED_PERSISTENT && schedule != OT_SCHED_PER_SUBGRID)
+        return fail(OT_EINVAL, "unknown schedule %d", schedule);
+    if (warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8)
+        return fail(OT_EINVAL, "warps_per_block must be 2, 4 or 8");
+    if (blocks_per_sm < 0 || blocks_per_sm > 16) return fail(OT_EINVAL, "blocks_per_sm must be in [0, 16]");
+    if (use_graph != 0 && use_graph != 1) return fail(OT_EINVAL, "use_graph must be 0 or 1");
+    if (g->wpb != warps_per_block || g->bps != blocks_per_sm || g->schedule != schedule) {
+        for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
+        g->graphs.clear();
+    }
+    g->schedule = schedule;
+    g->wpb = warps_per_block;
+    g->bps = blocks_per_sm;
+    g->use_graph = use_graph;
+    g->info.schedule = schedule;
+    g->info.warps_per_block = warps_per_block;
+    g->info.blocks_per_sm = blocks_per_sm;
+    g->info.graphs_enabled = use_graph;
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_moments(ot_grid* g, const double* rho, double* M, double* m, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(rho, "rho");
+    CHECK_PTR(M, "M");
+    CHECK_PTR(m, "m");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OT_CUDA(launch_cube_moments(rho, M, m, g->d_cube, g->n_cube, g->d_ninfo, g->d_hinv, s));
+    for (auto& L : g->m2m)
+        OT_CUDA(launch_m2m(M, m, L.d_parents, static_cast<int>(L.parents.size()), L.d_children, g->d_ninfo,
+                           g->d_hinv, s));
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_moments_backward(ot_grid* g, const double* Mbar, const double* mbar, double* rhobar, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(rhobar, "rhobar");
+    if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
+    if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OT_CUDA(launch_moments_adjoint_init(Mbar, mbar, g->d_Mb, g->n, s));
+    for (auto it = g->m2m.rbegin(); it != g->m2m.rend(); ++it)
+        OT_CUDA(launch_m2m_adjoint(g->d_Mb, it->d_parents, static_cast<int>(it->parents.size()), it->d_children,
+                                   g->d_ninfo, g->d_hinv, s));
+    OT_CUDA(cudaMemsetAsync(rhobar, 0, static_cast<size_t>(g->n) * NCELL * sizeof(double), s));
+    OT_CUDA(launch_cube_adjoint(g->d_Mb, rhobar, g->d_cube, g->n_cube, g->d_ninfo, g->d_hinv, s));
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_multipole_interactions(ot_grid* g, const double* M, const double* centres, double* L, double* Lc,
+                                    void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (centres) return fail(OT_ENOTSUP, "explicit expansion centres are not built (pass NULL)");
+    CHECK_PTR(M, "M");
+    CHECK_PTR(L, "L");
+    if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GraphKey key{1, M, nullptr, L, Lc, g->wpb, g->bps};
+    return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward(g, 1, M, nullptr, L, Lc, 0, st); });
+    GUARD_END
+}
+
+ot_status ot_monopole_interactions(ot_grid* g, const double* m, double* L, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(m, "m");
+    CHECK_PTR(L, "L");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GraphKey key{2, nullptr, m, L, nullptr, g->wpb, g->bps};
+    return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward(g, 2, nullptr, m, L, nullptr, 1, st); });
+    GUARD_END
+}
+
+ot_status ot_interactions(ot_grid* g, const double* M, const double* m, double* L, double* Lc, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(M, "M");
+    CHECK_PTR(m, "m");
+    CHECK_PTR(L, "L");
+    if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GraphKey key{3, M, m, L, Lc, g->wpb, g->bps};
+    return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward(g, 3, M, m, L, Lc, 0, st); });
+    GUARD_END
+}
+
+ot_status ot_interactions_backward(ot_grid* g, const double* Lbar, double* Mbar, double* mbar, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(Lbar, "Lbar");
+    if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
+    if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GraphKey key{4, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps};
+    return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_backward(g, Lbar, Mbar, mbar, st); });
+    GUARD_END
+}
+
+ot_status ot_autotune(ot_grid* g, const double* M, const double* m, double* L, double* Lc, void* stream,
+                      int32_t* best_warps, int32_t* best_blocks, double* best_ms) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(M, "M");
+    CHECK_PTR(m, "m");
+    CHECK_PTR(L, "L");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int save_sched = g->schedule, save_w = g->wpb, save_b = g->bps, save_g = g->use_graph;
+    g->schedule = OT_SCHED_PERSISTENT;
+    g->use_graph = 0;
+    cudaEvent_t e0, e1;
+    OT_CUDA(cudaEventCreate(&e0));
+    OT_CUDA(cudaEventCreate(&e1));
+    double best = 1e30;
+    int bw = save_w, bb = save_b;
+    const int ws[3] = {2, 4, 8};
+    for (int wi = 0; wi < 3; ++wi) {
+        const int w = ws[wi];
+        const int maxb = g->maxb_fwd[3][w];
+        for (int b = 1; b <= std::min(maxb, 16); ++b) {
+            g->wpb = w;
+            g->bps = b;
+            ot_status st = enqueue_forward(g, 3, M, m, L, Lc, 0, s);   // warm-up
+            if (st != OT_OK) return st;
+            float best_run = 1e30f;
+            for (int r = 0; r < 2; ++r) {
+                OT_CUDA(cudaEventRecord(e0, s));
+                st = enqueue_forward(g, 3, M, m, L, Lc, 0, s);
+                if (st != OT_OK) return st;
+                OT_CUDA(cudaEventRecord(e1, s));
+                OT_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                OT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                best_run = std::min(best_run, ms);
+            }
+            if (best_run < best) {
+                best = best_run;
+                bw = w;
+                bb = b;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->schedule = save_sched;
+    g->use_graph = save_g;
+    g->wpb = save_w;
+    g->bps = save_b;
+    ot_status st = ot_set_schedule(g, save_sched, bw, bb, save_g);
+    if (st != OT_OK) return st;
+    if (best_warps) *best_warps = bw;
+    if (best_blocks) *best_blocks = bb;
+    if (best_ms) *best_ms = best;
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_grid_check(ot_grid* g, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h[2] = {0, 0};
+    OT_CUDA(cudaMemcpyAsync(h, g->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OT_CUDA(cudaStreamSynchronize(s));
+    if (h[0] != 0) {
+        OT_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(h), s));
+        OT_CUDA(cudaStreamSynchronize(s));
+        return fail(OT_EDEVICE, "device bounds check %d fired at work item %d", h[0], h[1]);
+    }
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, void* stream) {
+    GUARD_BEGIN
+    CHECK_PTR(out, "out");
+    if (blocks <= 0 || iters <= 0) return fail(OT_EINVAL, "blocks and iters must be positive");
+    OT_CUDA(launch_fp64_probe(out, blocks, iters, static_cast<cudaStream_t>(stream)));
+    return OT_OK;
+    GUARD_END
+}
+
+}  // extern "C"

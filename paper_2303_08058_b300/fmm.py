@@ -1,0 +1,162 @@
+"""Python face of the library: a grid handle over the C ABI and the autograd
+Function.  Device memory and streams come from PyTorch; every step of the
+interaction path (moments, both passes, adjoints) runs in libotfmm's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+NCOMP = 20
+NCELL = 512
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class OTGrid:
+    """Handle of one octree of 8^3 sub-grids on the current CUDA device.
+
+    level [n], coord [n, 3], is_leaf [n] describe the nodes (see include/ot.h);
+    h0 is the cell size at level 0.
+    """
+
+    def __init__(self, level, coord, is_leaf, h0: float, stream=None):
+        self.lib = _lib.load()
+        self.level = np.ascontiguousarray(level, dtype=np.int32)
+        self.coord = np.ascontiguousarray(coord, dtype=np.int32).reshape(-1, 3)
+        self.is_leaf = np.ascontiguousarray(is_leaf, dtype=np.uint8)
+        self.n = int(self.level.shape[0])
+        self.h0 = float(h0)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        desc = _lib.GridDesc(self.n, self.level.ctypes.data, self.coord.ctypes.data, self.is_leaf.ctypes.data,
+                             self.h0, 12, 0)
+        handle = ctypes.c_void_p()
+        _lib.check(self.lib.ot_grid_create(ctypes.byref(desc), _stream(stream), ctypes.byref(handle)))
+        self.handle = handle
+
+    @classmethod
+    def from_tree(cls, tree, stream=None):
+        return cls(tree.level, tree.coord, tree.is_leaf, tree.h0, stream=stream)
+
+    # -- lifetime ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.check(self.lib.ot_grid_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers -------------------------------------------------------------------
+    def zeros(self, *shape):
+        return torch.zeros(*shape, dtype=torch.float64, device=self.device)
+
+    def info(self) -> dict:
+        out = _lib.GridInfo()
+        _lib.check(self.lib.ot_grid_info(self.handle, ctypes.byref(out)))
+        return out.as_dict()
+
+    def check(self, stream=None):
+        _lib.check(self.lib.ot_grid_check(self.handle, _stream(stream)))
+
+    def set_schedule(self, schedule=_lib.OT_SCHED_PERSISTENT, warps_per_block=4, blocks_per_sm=0, use_graph=True):
+        _lib.check(self.lib.ot_set_schedule(self.handle, int(schedule), int(warps_per_block), int(blocks_per_sm),
+                                            int(bool(use_graph))))
+
+    def autotune(self, M, m, L, Lc=None, stream=None):
+        w, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _lib.check(self.lib.ot_autotune(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), _stream(stream),
+                                        ctypes.byref(w), ctypes.byref(b), ctypes.byref(ms)))
+        return dict(warps_per_block=w.value, blocks_per_sm=b.value, ms=ms.value)
+
+    # -- the path ------------------------------------------------------------------
+    def moments(self, rho, M=None, m=None, stream=None):
+        M = M if M is not None else self.zeros(self.n, NCOMP, NCELL)
+        m = m if m is not None else self.zeros(self.n, NCELL)
+        _lib.check(self.lib.ot_moments(self.handle, _ptr(rho), _ptr(M), _ptr(m), _stream(stream)))
+        return M, m
+
+    def moments_backward(self, Mbar=None, mbar=None, rhobar=None, stream=None):
+        rhobar = rhobar if rhobar is not None else self.zeros(self.n, NCELL)
+        _lib.check(self.lib.ot_moments_backward(self.handle, _ptr(Mbar), _ptr(mbar), _ptr(rhobar),
+                                                _stream(stream)))
+        return rhobar
+
+    def multipole(self, M, L=None, Lc=None, want_lc=True, stream=None):
+        L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
+        if Lc is None and want_lc:
+            Lc = self.zeros(self.n, 3, NCELL)
+        _lib.check(self.lib.ot_multipole_interactions(self.handle, _ptr(M), None, _ptr(L), _ptr(Lc),
+                                                      _stream(stream)))
+        return L, Lc
+
+    def monopole(self, m, L=None, stream=None):
+        L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
+        _lib.check(self.lib.ot_monopole_interactions(self.handle, _ptr(m), _ptr(L), _stream(stream)))
+        return L
+
+    def interactions(self, M, m, L=None, Lc=None, want_lc=True, stream=None):
+        L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
+        if Lc is None and want_lc:
+            Lc = self.zeros(self.n, 3, NCELL)
+        _lib.check(self.lib.ot_interactions(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), _stream(stream)))
+        return L, Lc
+
+    def backward(self, Lbar, Mbar=None, mbar=None, want=(True, True), stream=None):
+        if Mbar is None and want[0]:
+            Mbar = self.zeros(self.n, NCOMP, NCELL)
+        if mbar is None and want[1]:
+            mbar = self.zeros(self.n, NCELL)
+        _lib.check(self.lib.ot_interactions_backward(self.handle, _ptr(Lbar), _ptr(Mbar), _ptr(mbar),
+                                                     _stream(stream)))
+        return Mbar, mbar
+
+
+def fp64_fma_probe(out, blocks, iters, stream=None):
+    lib = _lib.load()
+    _lib.check(lib.ot_fp64_fma_probe(_ptr(out), int(blocks), int(iters), _stream(stream)))
+
+
+class FMMInteractions(torch.autograd.Function):
+    """rho [n, 512] -> L [n, 20, 512] (both passes, moments included).
+
+    The backward runs the transposed stencil kernels and the adjoint of the
+    moment computation; nothing from the forward pass is stored (the maps are
+    linear in rho, so the adjoint needs only the grid)."""
+
+    @staticmethod
+    def forward(ctx, grid: OTGrid, rho):
+        M, m = grid.moments(rho.contiguous())
+        L, _ = grid.interactions(M, m, want_lc=False)
+        ctx.grid = grid
+        return L
+
+    @staticmethod
+    def backward(ctx, Lbar):
+        grid = ctx.grid
+        Mbar, mbar = grid.backward(Lbar.contiguous())
+        rhobar = grid.moments_backward(Mbar, mbar)
+        return None, rhobar
+
+
+def potential_and_gradient(grid: OTGrid, rho):
+    """Differentiable L (potential, gradient, ...) of every cell from rho."""
+    return FMMInteractions.apply(grid, rho)

@@ -1,0 +1,119 @@
+"""CPU-side checks of the boundary: the shared library loads, exports every
+entry point include/ot.h declares, and rejects bad arguments before touching
+the device; the generated contraction code is current; the product package
+never imports the oracle."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = os.path.join(ROOT, "paper_2303_08058_b300")
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "ot.h")).read()
+    return sorted(set(re.findall(r"^(?:ot_status|const char\*)\s+(ot_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2303_08058_b300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2303_08058_b300 import _lib
+    decl = header_functions()
+    assert len(decl) >= 14
+    assert sorted(_lib.EXPORTS) == decl
+    for name in decl:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(PKG, "libotfmm.so")],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (ot_\w+)$", out, flags=re.M))
+    assert set(decl) <= exported
+
+
+def test_library_is_built_for_sm_103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", os.path.join(PKG, "libotfmm.so")],
+                         capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_host_argument_checks_without_device(lib):
+    from paper_2303_08058_b300 import _lib
+    out = ctypes.c_void_p()
+    assert lib.ot_grid_create(None, None, ctypes.byref(out)) == _lib.OT_EINVAL
+    assert b"desc" in lib.ot_last_error()
+    desc = _lib.GridDesc(0, None, None, None, 1.0, 12, 0)
+    assert lib.ot_grid_create(ctypes.byref(desc), None, ctypes.byref(out)) == _lib.OT_EINVAL
+    lv = np.array([1], np.int32)
+    co = np.zeros((1, 3), np.int32)
+    lf = np.ones(1, np.uint8)
+    desc = _lib.GridDesc(1, lv.ctypes.data, co.ctypes.data, lf.ctypes.data, 1.0, 24, 0)
+    assert lib.ot_grid_create(ctypes.byref(desc), None, ctypes.byref(out)) == _lib.OT_ENOTSUP
+    desc = _lib.GridDesc(1, lv.ctypes.data, co.ctypes.data, lf.ctypes.data, float("nan"), 12, 0)
+    assert lib.ot_grid_create(ctypes.byref(desc), None, ctypes.byref(out)) == _lib.OT_EINVAL
+    assert lib.ot_grid_destroy(None) == _lib.OT_OK
+    assert lib.ot_set_schedule(None, 0, 4, 0, 1) == _lib.OT_EINVAL
+    assert lib.ot_interactions(None, None, None, None, None, None) == _lib.OT_EINVAL
+    assert lib.ot_fp64_fma_probe(None, 1, 1, None) == _lib.OT_EINVAL
+
+
+def test_generated_contraction_code_is_current():
+    sys.path.insert(0, os.path.join(PKG, "csrc"))
+    try:
+        import gen_contract
+    finally:
+        sys.path.pop(0)
+    text = gen_contract.emit()
+    assert text == open(os.path.join(PKG, "csrc", "ot_contract.inc")).read()
+    body = text.split("ot_multi_fwd")[1].split("}")[0]
+    assert body.count("fma(") == 70
+    body = text.split("ot_mono_fwd")[1].split("}")[0]
+    assert body.count("fma(") == 16
+
+
+def test_product_never_touches_the_oracle():
+    for dirpath, _, files in os.walk(PKG):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".inc", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
+                assert "ot_oracle" not in text, f
+
+
+def test_generated_trees_are_2to1_balanced():
+    tree, _, _ = synth.config3()
+    idx = tree.index()
+    leaves = [(int(l), *map(int, c)) for l, c, f in zip(tree.level, tree.coord, tree.is_leaf) if f]
+    leafset = set(leaves)
+
+    def covering_leaf(l, q):
+        for d in range(0, l + 1):
+            t = (l - d, q[0] >> d, q[1] >> d, q[2] >> d)
+            if t in leafset:
+                return t
+        return None
+    for (l, x, y, z) in leaves[::7]:
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    q = (x + dx, y + dy, z + dz)
+                    if min(q) < 0 or max(q) >= 2 ** l:
+                        continue
+                    if (l, *q) in idx and not tree.is_leaf[idx[(l, *q)]]:
+                        # refined neighbour: its children touching us must be leaves
+                        continue
+                    cl = covering_leaf(l, q)
+                    assert cl is None or l - cl[0] <= 1

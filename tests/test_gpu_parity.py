@@ -1,0 +1,414 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: every Taylor coefficient within 1e-12 * S of the oracle, S being the
+oracle's sum of |terms| for that coefficient (the two differ in summation
+order, FMA contraction and the traceless reduction only).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import assert_parity, oracle_threads, sample_targets
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ot():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2303_08058_b300 as ot
+    ot.load()
+    return ot
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    oracle_threads(oracle)
+    return oracle
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu_fused(ot, tree, rho=None, M=None, m=None, schedule=None):
+    g = ot.OTGrid.from_tree(tree)
+    if schedule is not None:
+        g.set_schedule(*schedule)
+    if M is None:
+        Md, md = g.moments(dev(rho))
+    else:
+        Md, md = dev(M), dev(m)
+    L, Lc = g.interactions(Md, md)
+    torch.cuda.synchronize()
+    g.check()
+    return g, host(Md), host(md), host(L), host(Lc)
+
+
+def oracle_both(orc, tree, M, m, targets=None):
+    r1 = orc.run_pass(tree, "multipole", M=M, targets=targets)
+    r2 = orc.run_pass(tree, "monopole", m=m, targets=targets)
+    return r1["L"] + r2["L"], r1["S"] + r2["S"], r1["Lc"], r1["Sc"], r1["npairs"], r2["npairs"]
+
+
+def at_targets(L, targets):
+    return L[targets[:, 0], :, targets[:, 1]]
+
+
+def all_targets(tree):
+    return np.stack(np.meshgrid(np.arange(tree.n), np.arange(512), indexing="ij"), -1).reshape(-1, 2).astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# moments
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["uniform", "adaptive", "single"])
+def test_moments_match_oracle(ot, orc, which):
+    if which == "uniform":
+        tree = synth.uniform_tree(1, 1.0)
+    elif which == "adaptive":
+        tree = synth.adaptive_tree(lambda l, c, h0: l == 1 and tuple(c) in {(0, 0, 0), (1, 1, 0)}, 1, 3, 32.0)
+    else:
+        tree = synth.single_subgrid(1, 1.0)
+    rho = synth.uniform_random_density(tree, seed=31)
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    Mo = orc.moments(tree, rho)
+    scale = np.abs(Mo[:, :1, :]) * (tree.h(tree.level)[:, None, None] ** np.array(
+        [0] + [1] * 3 + [2] * 6 + [3] * 10)[None, :, None])
+    assert np.all(np.abs(host(M) - Mo) <= 1e-14 * scale + 1e-300)
+    np.testing.assert_array_equal(host(m), host(M)[:, 0, :])
+
+
+def test_moments_backward_dot_product(ot):
+    tree = synth.adaptive_tree(lambda l, c, h0: l == 1 and tuple(c) == (0, 1, 0), 1, 3, 32.0)
+    rng = np.random.default_rng(32)
+    rho = rng.uniform(0.5, 1.5, (tree.n, 512))
+    Mb = rng.standard_normal((tree.n, 20, 512))
+    mb = rng.standard_normal((tree.n, 512))
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    rb = g.moments_backward(dev(Mb), dev(mb))
+    lhs = np.sum(host(M) * Mb) + np.sum(host(m) * mb)
+    rhs = np.sum(rho * host(rb))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# forward passes, small cases (every cell)
+# ---------------------------------------------------------------------------
+
+def test_config1_multipole_all_cells(ot, orc):
+    """One isolated sub-grid of multipole cells (monopole + quadrupole moments)."""
+    tree, rho = synth.config1()
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L, Lc = g.multipole(M)
+    torch.cuda.synchronize()
+    r = orc.run_pass_grid(tree, "multipole", M=host(M))
+    assert_parity(host(L), r["L"], r["S"], what="L")
+    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc")
+    assert g.info()["pairs_multipole"] == r["npairs"]
+
+
+@pytest.mark.parametrize("seed", [41, 42])
+def test_single_subgrid_random_moments_all_terms(ot, orc, seed):
+    """Random moments of every order exercise every contraction term and the
+    angular correction (target and source octupoles)."""
+    tree = synth.single_subgrid(1, 0.5)
+    M = synth.random_moments(tree, seed=seed)
+    g = ot.OTGrid.from_tree(tree)
+    L, Lc = g.multipole(dev(M))
+    torch.cuda.synchronize()
+    r = orc.run_pass_grid(tree, "multipole", M=M)
+    assert_parity(host(L), r["L"], r["S"], what="L")
+    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc")
+    assert np.max(np.abs(r["Lc"])) > 0
+
+
+def test_root_leaf_subgrid_root_and_near_stencils(ot, orc):
+    """A lone root leaf: root stencil (all well-separated pairs) plus near pairs."""
+    tree = synth.single_subgrid(0, 1.0, leaf=True)
+    rng = np.random.default_rng(43)
+    m = rng.uniform(0.5, 1.5, (1, 512))
+    g = ot.OTGrid.from_tree(tree)
+    L = g.monopole(dev(m))
+    torch.cuda.synchronize()
+    r = orc.run_pass_grid(tree, "monopole", m=m)
+    assert_parity(host(L), r["L"], r["S"], what="L")
+    assert g.info()["pairs_monopole"] == r["npairs"] == 512 * 511
+
+
+def test_monopole_uniform_level(ot, orc):
+    tree = synth.uniform_level(1, 1.0)
+    rng = np.random.default_rng(44)
+    m = rng.uniform(0.5, 1.5, (tree.n, 512))
+    g = ot.OTGrid.from_tree(tree)
+    L = g.monopole(dev(m))
+    torch.cuda.synchronize()
+    r = orc.run_pass_grid(tree, "monopole", m=m)
+    assert_parity(host(L), r["L"], r["S"], what="L")
+    assert g.info()["pairs_monopole"] == r["npairs"]
+
+
+def test_fused_uniform_tree_with_coarse_levels(ot, orc):
+    tree = synth.uniform_tree(1, 1.0)
+    rho = synth.uniform_random_density(tree, seed=45)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    tg = all_targets(tree)
+    Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(L, tg), Lo, S, what="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    info = g.info()
+    assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
+
+
+def _small_adaptive():
+    """25 sub-grids: root, 8 at level 1 (two refined), 16 leaves at level 2."""
+    def refine(l, c, h0):
+        return l == 1 and tuple(c) in {(0, 0, 0), (1, 1, 0)}
+    return synth.adaptive_tree(refine, 1, 2, 16.0)
+
+
+def test_fused_adaptive_virtual_descendants(ot, orc):
+    """Mixed levels: virtual descendants of coarse leaves in the halo, near
+    pairs with refined (multipole) neighbours, mixed-class warps."""
+    tree = _small_adaptive()
+    rho = synth.uniform_random_density(tree, seed=46)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    info = g.info()
+    assert info["pairs_virtual"] > 0 and info["n_virtual"] > 0
+    tg = all_targets(tree)
+    Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(L, tg), Lo, S, what="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
+
+
+def test_separate_passes_equal_fused(ot):
+    tree = _small_adaptive()
+    rho = synth.uniform_random_density(tree, seed=47)
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L1, Lc1 = g.multipole(M)
+    L1 = g.monopole(m, L1)
+    L2, Lc2 = g.interactions(M, m)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(Lc1), host(Lc2))
+    np.testing.assert_allclose(host(L1), host(L2), rtol=1e-13, atol=1e-13 * np.abs(host(L2)).max())
+
+
+def test_schedules_are_bitwise_identical(ot):
+    """Persistent, graph-replayed and per-sub-grid launches run the same
+    per-target summation order: identical bits."""
+    tree = _small_adaptive()
+    rho = synth.uniform_random_density(tree, seed=48)
+    outs = []
+    for sched in [(0, 4, 0, True), (0, 2, 1, False), (1, 4, 0, False), (0, 8, 0, True)]:
+        g = ot.OTGrid.from_tree(tree)
+        g.set_schedule(*sched)
+        M, m = g.moments(dev(rho))
+        for _ in range(2):   # second call replays the graph
+            L, Lc = g.interactions(M, m)
+        Lb = dev(np.random.default_rng(1).standard_normal((tree.n, 20, 512)))
+        Mb, mb = g.backward(Lb)
+        torch.cuda.synchronize()
+        outs.append([host(L), host(Lc), host(Mb), host(mb)])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+
+def _sparse_lbar(tree, count, seed):
+    """L-bar non-zero (all 20 components) on `count` random target cells only,
+    so the oracle's scatter can be restricted to exactly those targets."""
+    rng = np.random.default_rng(seed)
+    tg = np.unique(np.stack([rng.integers(0, tree.n, count), rng.integers(0, 512, count)], 1), axis=0)
+    Lbar = np.zeros((tree.n, 20, 512))
+    Lbar[tg[:, 0], :, tg[:, 1]] = rng.standard_normal((len(tg), 20))
+    return Lbar, tg.astype(np.int32)
+
+
+def test_adjoint_dense_single_subgrid(ot, orc):
+    tree = synth.single_subgrid(1, 1.0)
+    Lbar = np.random.default_rng(50).standard_normal((1, 20, 512))
+    g = ot.OTGrid.from_tree(tree)
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True)
+    assert_parity(host(Mb), Mo, SM, what="Mbar")
+    assert np.all(host(mb) == 0)
+
+
+@pytest.mark.parametrize("which", ["uniform_tree", "adaptive", "leaf_level"])
+def test_adjoint_matches_oracle_transposed_sum(ot, orc, which):
+    tree = {"uniform_tree": lambda: synth.uniform_tree(1, 1.0),
+            "adaptive": _small_adaptive,
+            "leaf_level": lambda: synth.uniform_level(1, 1.0)}[which]()
+    Lbar, tg = _sparse_lbar(tree, 300, 51)
+    g = ot.OTGrid.from_tree(tree)
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg)
+    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
+    assert_parity(host(Mb), Mo, SM, what="Mbar")
+    assert_parity(host(mb), mo, Sm, what="mbar")
+    assert np.max(np.abs(mo)) > 0
+
+
+def test_adjoint_dot_product_gpu(ot):
+    tree = _small_adaptive()
+    rng = np.random.default_rng(52)
+    M = synth.random_moments(tree, seed=53)
+    m = rng.uniform(0.5, 1.5, (tree.n, 512))
+    Lbar = rng.standard_normal((tree.n, 20, 512))
+    g = ot.OTGrid.from_tree(tree)
+    L, _ = g.interactions(dev(M), dev(m), want_lc=False)
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    lhs = np.sum(host(L) * Lbar)
+    rhs = np.sum(M * host(Mb)) + np.sum(m * host(mb))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_autograd_matches_central_differences(ot):
+    """loss = sum over probes of (L0)^2 on a small uniform tree; gradient with
+    respect to densities via the adjoint kernels against central differences
+    (FD is exact for a quadratic loss up to rounding)."""
+    tree = synth.uniform_tree(1, 1.0)
+    rho0 = synth.sample_density(tree, lambda x: synth.polytrope_density(x, (8.0, 8.0, 8.0), 6.0))
+    leaf_nodes = np.nonzero(tree.is_leaf)[0]
+    rng = np.random.default_rng(54)
+    probes = np.stack([rng.choice(leaf_nodes, 50), rng.integers(0, 512, 50)], 1)
+    g = ot.OTGrid.from_tree(tree)
+    rho = dev(rho0).requires_grad_(True)
+    L = ot.potential_and_gradient(g, rho)
+    loss = (L[probes[:, 0], 0, probes[:, 1]] ** 2).sum()
+    loss.backward()
+    grad = host(rho.grad)
+
+    def f(r):
+        with torch.no_grad():
+            Lr = ot.potential_and_gradient(g, dev(r))
+            return float((Lr[probes[:, 0], 0, probes[:, 1]] ** 2).sum())
+    cells = [(int(n), int(c)) for n, c in zip(rng.choice(leaf_nodes, 16), rng.integers(0, 512, 16))]
+    cells += [(0, 100), (int(np.nonzero(tree.level == 0)[0][0]), 7)]   # coarse nodes: gradient 0
+    for (n, c) in cells:
+        step = 1e-6 * max(rho0[n, c], 1e-3)
+        rp, rm = rho0.copy(), rho0.copy()
+        rp[n, c] += step
+        rm[n, c] -= step
+        fd = (f(rp) - f(rm)) / (2 * step)
+        scale = max(abs(fd), 1e-6 * np.max(np.abs(grad)))
+        assert abs(grad[n, c] - fd) <= 1e-4 * scale, (n, c, grad[n, c], fd)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads in the benchmark's launch configuration (sampled)
+# ---------------------------------------------------------------------------
+
+def test_config2_full_size_sampled(ot, orc):
+    tree, rho = synth.config2()
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    tg = np.concatenate([sample_targets(tree, 96, 61, levels=[3]), sample_targets(tree, 48, 62, levels=[0, 1, 2])])
+    Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(L, tg), Lo, S, what="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    # every leaf cell: potential negative, the field points inward (towards the star centre)
+    leaf = tree.level == 3
+    assert np.all(L[leaf, 0, :] < 0)
+
+
+def test_config2_adjoint_full_size_dot_product(ot):
+    tree, rho = synth.config2()
+    rng = np.random.default_rng(63)
+    Lbar = rng.standard_normal((tree.n, 20, 512))
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L, _ = g.interactions(M, m, want_lc=False)
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    lhs = np.sum(host(L) * Lbar)
+    rhs = np.sum(host(M) * host(Mb)) + np.sum(host(m) * host(mb))
+    assert lhs == pytest.approx(rhs, rel=1e-11)
+
+
+def test_config2_adjoint_sampled_against_oracle(ot, orc):
+    """Sampled sources of the full-size adjoint against the oracle's transposed
+    sum restricted to those sources (probe-style L-bar: L0 at 1000 cells)."""
+    tree, rho = synth.config2()
+    probes = synth.config4_probes()
+    leaf_nodes = np.nonzero(tree.level == 3)[0]
+    Lbar = np.zeros((tree.n, 20, 512))
+    Lbar[leaf_nodes[probes // 512], 0, probes % 512] = np.random.default_rng(64).standard_normal(len(probes))
+    g = ot.OTGrid.from_tree(tree)
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    tg = np.stack([leaf_nodes[probes // 512], probes % 512], 1).astype(np.int32)
+    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
+    assert_parity(host(mb), mo, Sm, what="mbar")
+    assert np.all(host(Mb) == 0)    # L-bar only on leaf cells: no multipole source sees it
+
+
+@pytest.mark.parametrize("cfg", ["config3", "config5"])
+def test_adaptive_workloads_sampled(ot, orc, cfg):
+    if cfg == "config3":
+        tree, rho, _ = synth.config3()
+    else:
+        tree, rho = synth.config5_step(0)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    info = g.info()
+    assert info["pairs_virtual"] > 0
+    tg = sample_targets(tree, 160, 65)
+    Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(L, tg), Lo, S, what="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+
+
+# ---------------------------------------------------------------------------
+# boundary behaviour
+# ---------------------------------------------------------------------------
+
+def test_abi_rejects_bad_input(ot):
+    lvl = np.array([1, 1], np.int32)
+    with pytest.raises(ot.OTError, match="OT_EINVAL"):
+        ot.OTGrid(lvl, np.zeros((2, 3), np.int32), np.ones(2, np.uint8), 1.0)      # duplicate node
+    with pytest.raises(ot.OTError, match="OT_EINVAL"):
+        ot.OTGrid(np.array([1], np.int32), np.array([[2, 0, 0]], np.int32), np.ones(1, np.uint8), 1.0)
+    with pytest.raises(ot.OTError, match="OT_EINVAL"):
+        ot.OTGrid(np.array([1], np.int32), np.zeros((1, 3), np.int32), np.ones(1, np.uint8), -1.0)
+    tree = synth.single_subgrid(1, 1.0)
+    g = ot.OTGrid.from_tree(tree)
+    M = torch.zeros(1 * 20 * 512 + 1, dtype=torch.float64, device="cuda")
+    L = torch.zeros(20 * 512, dtype=torch.float64, device="cuda")
+    import ctypes
+    from paper_2303_08058_b300 import _lib
+    lib = _lib.load()
+    st = lib.ot_multipole_interactions(g.handle, ctypes.c_void_p(M.data_ptr() + 8), None,
+                                       ctypes.c_void_p(L.data_ptr()), None, None)
+    assert st == _lib.OT_EINVAL and b"aligned" in lib.ot_last_error()
+    st = lib.ot_multipole_interactions(g.handle, ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(M.data_ptr()),
+                                       ctypes.c_void_p(L.data_ptr()), None, None)
+    assert st == _lib.OT_ENOTSUP
+    assert lib.ot_interactions(None, None, None, None, None, None) == _lib.OT_EINVAL
+    g.check()
+
+
+def test_fp64_probe_runs(ot):
+    out = torch.zeros(148 * 256, dtype=torch.float64, device="cuda")
+    ot.fp64_fma_probe(out, 148, 100)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(host(out))) and np.all(host(out) > 0)
