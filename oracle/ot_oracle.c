@@ -382,10 +382,15 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                             int it[3] = {code % 3, (code / 3) % 3, code / 9};
                             int full[4] = {i, it[0], it[1], it[2]};
                             int c3 = comp_of(it, 3);
-                            double nB = MB[(size_t)c3 * NCELL] - (mB / mA) * M[((size_t)T * NCOMP + c3) * NCELL + a];
-                            double term = -(1.0 / 6.0) * nB * D[comp_of(full, 4)];
+                            double M3A = M[((size_t)T * NCOMP + c3) * NCELL + a];
+                            double nB = MB[(size_t)c3 * NCELL] - (mB / mA) * M3A;
+                            double d4 = D[comp_of(full, 4)];
+                            double term = -(1.0 / 6.0) * nB * d4;
                             Lc[i] += term;
-                            Sc[i] += fabs(term);
+                            /* the term has two contributions, the source octupole and
+                             * the target octupole: count both in the magnitude sum */
+                            Sc[i] += fabs((1.0 / 6.0) * MB[(size_t)c3 * NCELL] * d4) +
+                                     fabs((1.0 / 6.0) * (mB / mA) * M3A * d4);
                         }
                     }
                 }
