@@ -448,61 +448,86 @@ __global__ void restrict_virtual_kernel(const double* __restrict__ vbar, const i
 // moments
 // ---------------------------------------------------------------------------
 
-// exponent triples of the 20 stored components
-__constant__ int c_exp[20][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0}, {1, 0, 1},
-                                 {0, 2, 0}, {0, 1, 1}, {0, 0, 2}, {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0},
-                                 {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}};
+// Moments in a dense [4][4][4] exponent array (entries with a+b+c <= 3 used);
+// every loop bound below is a compile-time constant, so after unrolling all
+// indices are static and the arrays live in registers.
+#define OT_STORAGE_EXPONENTS                                                                       \
+    {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, \
+     {0, 0, 2}, {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, \
+     {0, 1, 2}, {0, 0, 3}}
 
-__device__ __forceinline__ int comp_of_exp(int a, int b, int c) {
-    const int k = a + b + c;
-    // position of (a,b,c) among the rank-k components in storage order
-    const int base = (k == 0) ? 0 : (k == 1) ? 1 : (k == 2) ? 4 : 10;
-    int idx = 0;
-    for (int q = base; q < base + (k + 1) * (k + 2) / 2; ++q) {
-        if (c_exp[q][0] == a && c_exp[q][1] == b && c_exp[q][2] == c) idx = q;
-    }
-    return idx;
+struct Dense4 {
+    double v[4][4][4];
+};
+
+__device__ __forceinline__ void to_dense(const double* __restrict__ src, Dense4& D) {
+    constexpr int E[20][3] = OT_STORAGE_EXPONENTS;
+#pragma unroll
+    for (int q = 0; q < 20; ++q) D.v[E[q][0]][E[q][1]][E[q][2]] = src[q * NCELL];
 }
 
-__device__ __forceinline__ double binom3(int n, int k) {  // n <= 3
-    const double t[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
-    return t[n][k];
-}
-
-// one-dimensional binomial shift of raw moments along `axis` by `d`
-__device__ void shift_axis(double (&M)[20], int axis, double d) {
-    double out[20];
+__device__ __forceinline__ void from_dense(const Dense4& D, double* __restrict__ out, bool add) {
+    constexpr int E[20][3] = OT_STORAGE_EXPONENTS;
+#pragma unroll
     for (int q = 0; q < 20; ++q) {
-        const int e[3] = {c_exp[q][0], c_exp[q][1], c_exp[q][2]};
-        double acc = 0.0;
-        double dp = 1.0;
-        for (int j = e[axis]; j >= 0; --j) {   // source exponent j along axis
-            int f[3] = {e[0], e[1], e[2]};
-            f[axis] = j;
-            acc = fma(binom3(e[axis], j) * dp, M[comp_of_exp(f[0], f[1], f[2])], acc);
-            dp *= d;
-        }
-        out[q] = acc;
+        const double x = D.v[E[q][0]][E[q][1]][E[q][2]];
+        out[q * NCELL] = add ? out[q * NCELL] + x : x;
     }
-    for (int q = 0; q < 20; ++q) M[q] = out[q];
 }
 
-// transpose of shift_axis
-__device__ void shift_axis_t(double (&M)[20], int axis, double d) {
-    double out[20];
-    for (int q = 0; q < 20; ++q) out[q] = 0.0;
-    for (int q = 0; q < 20; ++q) {
-        const int e[3] = {c_exp[q][0], c_exp[q][1], c_exp[q][2]};
-        double dp = 1.0;
-        for (int j = e[axis]; j >= 0; --j) {
-            int f[3] = {e[0], e[1], e[2]};
-            f[axis] = j;
-            const int s = comp_of_exp(f[0], f[1], f[2]);
-            out[s] = fma(binom3(e[axis], j) * dp, M[q], out[s]);
-            dp *= d;
+// binomial shift of raw moments along one axis by d:
+//   out[..a..] = sum_{j <= a} C(a, j) d^(a-j) in[..j..]
+template <int AXIS>
+__device__ __forceinline__ void shift1(Dense4& D, double d) {
+    const double d2 = d * d, d3 = d2 * d;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; p + q < 4; ++q) {
+            double m[4];
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a)
+                m[a] = (AXIS == 0) ? D.v[a][p][q] : (AXIS == 1) ? D.v[p][a][q] : D.v[p][q][a];
+            const int top = 3 - p - q;
+            double o[4];
+            o[0] = m[0];
+            if (top >= 1) o[1] = m[1] + d * m[0];
+            if (top >= 2) o[2] = m[2] + 2.0 * d * m[1] + d2 * m[0];
+            if (top >= 3) o[3] = m[3] + 3.0 * d * m[2] + 3.0 * d2 * m[1] + d3 * m[0];
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a) {
+                if (AXIS == 0) D.v[a][p][q] = o[a];
+                else if (AXIS == 1) D.v[p][a][q] = o[a];
+                else D.v[p][q][a] = o[a];
+            }
         }
-    }
-    for (int q = 0; q < 20; ++q) M[q] = out[q];
+}
+
+// transpose of shift1
+template <int AXIS>
+__device__ __forceinline__ void shift1_t(Dense4& D, double d) {
+    const double d2 = d * d, d3 = d2 * d;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; p + q < 4; ++q) {
+            double g[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a)
+                g[a] = (AXIS == 0) ? D.v[a][p][q] : (AXIS == 1) ? D.v[p][a][q] : D.v[p][q][a];
+            const int top = 3 - p - q;
+            double o[4];
+            o[0] = g[0] + (top >= 1 ? d * g[1] : 0.0) + (top >= 2 ? d2 * g[2] : 0.0) + (top >= 3 ? d3 * g[3] : 0.0);
+            o[1] = (top >= 1 ? g[1] : 0.0) + (top >= 2 ? 2.0 * d * g[2] : 0.0) + (top >= 3 ? 3.0 * d2 * g[3] : 0.0);
+            o[2] = (top >= 2 ? g[2] : 0.0) + (top >= 3 ? 3.0 * d * g[3] : 0.0);
+            o[3] = (top >= 3 ? g[3] : 0.0);
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a) {
+                if (AXIS == 0) D.v[a][p][q] = o[a];
+                else if (AXIS == 1) D.v[p][a][q] = o[a];
+                else D.v[p][q][a] = o[a];
+            }
+        }
 }
 
 __global__ void cube_moments_kernel(const double* __restrict__ rho, double* __restrict__ M, double* __restrict__ m,
@@ -534,25 +559,34 @@ __global__ void m2m_kernel(double* __restrict__ M, double* __restrict__ m, const
     const int P = parents[k];
     const int gx = cell & 7, gy = (cell >> 3) & 7, gz = cell >> 6;
     const double hc = 0.5 / hinv[ninfo[P] & 0xff];
-    double acc[20];
-    for (int q = 0; q < 20; ++q) acc[q] = 0.0;
+    Dense4 acc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc.v[a][b][c] = 0.0;
+#pragma unroll 1
     for (int b = 0; b < 8; ++b) {
         const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
         const int cx = 2 * gx + bx, cy = 2 * gy + by, cz = 2 * gz + bz;   // in [0, 16)
         const int oct = (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3);
         const int C = children[8 * k + oct];
         const int ccell = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
-        double v[20];
-        const double* src = M + static_cast<size_t>(C) * NCOMP * NCELL + ccell;
-        for (int q = 0; q < 20; ++q) v[q] = src[q * NCELL];
-        shift_axis(v, 0, (bx - 0.5) * hc);
-        shift_axis(v, 1, (by - 0.5) * hc);
-        shift_axis(v, 2, (bz - 0.5) * hc);
-        for (int q = 0; q < 20; ++q) acc[q] += v[q];
+        Dense4 v;
+        to_dense(M + static_cast<size_t>(C) * NCOMP * NCELL + ccell, v);
+        shift1<0>(v, (bx - 0.5) * hc);
+        shift1<1>(v, (by - 0.5) * hc);
+        shift1<2>(v, (bz - 0.5) * hc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bb = 0; a + bb < 4; ++bb)
+#pragma unroll
+                for (int c = 0; a + bb + c < 4; ++c) acc.v[a][bb][c] += v.v[a][bb][c];
     }
-    double* o = M + static_cast<size_t>(P) * NCOMP * NCELL + cell;
-    for (int q = 0; q < 20; ++q) o[q * NCELL] = acc[q];
-    m[static_cast<size_t>(P) * NCELL + cell] = acc[0];
+    from_dense(acc, M + static_cast<size_t>(P) * NCOMP * NCELL + cell, false);
+    m[static_cast<size_t>(P) * NCELL + cell] = acc.v[0][0][0];
 }
 
 __global__ void moments_adjoint_init_kernel(const double* __restrict__ Mbar, const double* __restrict__ mbar,
@@ -580,14 +614,12 @@ __global__ void m2m_adjoint_kernel(double* __restrict__ Mb, const int* __restric
               cz = (oct >> 2) * 8 + (ccell >> 6);
     const int pcell = (cx >> 1) + 8 * (cy >> 1) + 64 * (cz >> 1);
     const double hc = 0.5 / hinv[ninfo[P] & 0xff];
-    double v[20];
-    const double* src = Mb + static_cast<size_t>(P) * NCOMP * NCELL + pcell;
-    for (int q = 0; q < 20; ++q) v[q] = src[q * NCELL];
-    shift_axis_t(v, 2, ((cz & 1) - 0.5) * hc);
-    shift_axis_t(v, 1, ((cy & 1) - 0.5) * hc);
-    shift_axis_t(v, 0, ((cx & 1) - 0.5) * hc);
-    double* o = Mb + static_cast<size_t>(C) * NCOMP * NCELL + ccell;
-    for (int q = 0; q < 20; ++q) o[q * NCELL] += v[q];
+    Dense4 v;
+    to_dense(Mb + static_cast<size_t>(P) * NCOMP * NCELL + pcell, v);
+    shift1_t<2>(v, ((cz & 1) - 0.5) * hc);
+    shift1_t<1>(v, ((cy & 1) - 0.5) * hc);
+    shift1_t<0>(v, ((cx & 1) - 0.5) * hc);
+    from_dense(v, Mb + static_cast<size_t>(C) * NCOMP * NCELL + ccell, true);
 }
 
 __global__ void cube_adjoint_kernel(const double* __restrict__ Mb, double* __restrict__ rhobar,
