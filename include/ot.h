@@ -177,6 +177,33 @@ ot_status ot_set_schedule(ot_grid* grid, int32_t schedule, int32_t warps_per_blo
 ot_status ot_autotune(ot_grid* grid, const double* M, const double* m, double* L, double* Lc,
                       void* stream, int32_t* best_warps, int32_t* best_blocks, double* best_ms);
 
+/* Allocation-free multipole pass.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory when they
+ * call the kernels -- code recording a CUDA graph by stream capture (an
+ * allocation is not a stream operation and breaks the capture), real-time
+ * loops that forbid allocator calls after set-up, hosts whose device memory
+ * is owned by another allocator.  It computes exactly what
+ * ot_multipole_interactions computes (same kernels, same summation order;
+ * M, L, Lc as there, centres implied NULL), but keeps its scratch (the
+ * pre-scaled, reduced source moments, 64 KiB per sub-grid) in one static
+ * device array of OT_NOALLOC_SCRATCH_BYTES instead of the grid's arena, and
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Limit: the non-leaf sub-grids' node indices must span at most
+ *     OT_NOALLOC_SCRATCH_BYTES / 64 KiB = 256 consecutive indices; larger
+ *     grids are rejected with OT_EINVAL and a message.
+ *   - The array is set up on the first call on each device (one
+ *     cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture.  Every device that loads the library holds
+ *     the array until the process exits.
+ *   - All calls share the one array, which keeps the last call's contents;
+ *     each call writes every scratch entry it reads before reading it, so
+ *     nothing needs clearing.  Calls whose GPU work overlaps (other streams,
+ *     other grids on the same device) race on the array: serialize them.
+ *   - No CUDA graph is recorded or replayed by this call. */
+#define OT_NOALLOC_SCRATCH_BYTES (16u << 20)
+ot_status ot_multipole_interactions_noalloc(ot_grid* grid, const double* M, double* L, double* Lc,
+                                            void* stream);
+
 /* Reads and clears the device status word (synchronizes `stream`): OT_OK, or
  * OT_EDEVICE with the failing work item in ot_last_error(). */
 ot_status ot_grid_check(ot_grid* grid, void* stream);

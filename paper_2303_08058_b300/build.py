@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libotfmm.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("ot_kernels.cu", "ot_lib.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("ot_kernels.cu", "ot_lib.cu", "ot_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("ot_internal.h", "ot_contract.inc", "gen_contract.py")] + \
     [os.path.join(ROOT, "include", "ot.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

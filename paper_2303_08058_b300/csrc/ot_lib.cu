@@ -775,6 +775,58 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     return OT_OK;
 }
 
+// Multipole pass with the reduced-moment scratch supplied by the caller
+// (the allocation-free entry point passes its static device array here).
+// The scratch covers the node-index span of the non-leaf sub-grids only;
+// nothing on this path allocates memory.
+ot_status otk_set_error(ot_status code, const char* msg) { return fail(code, "%s", msg); }
+
+ot_status otk_multipole_with_scratch(ot_grid* g, const double* M, double* L, double* Lc, double* scratch,
+                                     size_t scratch_doubles, cudaStream_t s) {
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!M || !aligned16(M)) return fail(OT_EINVAL, "M is NULL or not 16-byte aligned");
+    if (!L || !aligned16(L)) return fail(OT_EINVAL, "L is NULL or not 16-byte aligned");
+    if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
+    int dev = -1;
+    OT_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(OT_EINVAL, "grid lives on device %d, current device is %d", g->device, dev);
+    int lo = -1, hi = -1;
+    for (int i = 0; i < g->n; ++i)
+        if (!g->is_leaf[i]) {
+            if (lo < 0) lo = i;
+            hi = i;
+        }
+    const size_t per = static_cast<size_t>(NRED) * NCELL;
+    const size_t span = (lo < 0) ? 0 : static_cast<size_t>(hi - lo + 1);
+    if (span * per > scratch_doubles)
+        return fail(OT_EINVAL,
+                    "multipole sources span %zu sub-grids (node indices %d..%d); the static scratch holds %zu",
+                    span, lo, hi, scratch_doubles / per);
+    // Mhat of node i lives at scratch + (i - lo) * per; form the base address
+    // as an integer so no out-of-range pointer is created on the host.
+    const uintptr_t base = reinterpret_cast<uintptr_t>(scratch) - static_cast<uintptr_t>(lo < 0 ? 0 : lo) * per *
+                                                                       sizeof(double);
+    double* mhat = reinterpret_cast<double*>(base);
+    PrepParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.src = M;
+    pp.dst = mhat;
+    pp.nodes = g->d_nonleaf;
+    pp.n_list = g->n_nonleaf;
+    pp.ninfo = g->d_ninfo;
+    for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = g->hinv[l];
+    OT_CUDA(launch_prescale_moments(pp, s));
+    OT_CUDA(cudaMemsetAsync(L, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
+    if (Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
+    FwdParams p = fwd_params(g, nullptr, L, Lc, 1);
+    p.Mhat = mhat;
+    p.items = g->d_items_fwd[1];
+    p.n_items = g->n_items_fwd[1];
+    OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
+    OT_CUDA(launch_forward(p, 1, true, g->wpb, grid_blocks(g, g->maxb_fwd[1][g->wpb]), s));
+    return OT_OK;
+}
+
 // run `body` directly, or capture it once into a graph keyed by `key` and replay
 template <class F>
 static ot_status run_graphed(ot_grid* g, const GraphKey& key, cudaStream_t s, F body) {
