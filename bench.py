@@ -41,14 +41,15 @@ WORKLOAD = ("uniform level: 512 leaf sub-grids (64^3 cells, h=1) + coarse levels
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--schedule", choices=["persistent", "per_subgrid"], default="persistent")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", default=None, help="WxB: warps per block x blocks per SM (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -63,8 +64,8 @@ def dist_init(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        if torch.cuda.is_available():
+        backend = os.environ.get("OT_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
             torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     elif torch.cuda.is_available():
@@ -83,7 +84,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    on_gpu = dist.get_backend() == "nccl"
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -166,27 +168,40 @@ def adj_flops(info):
     return 2 * (16 * info["pairs_monopole"] + 70 * info["pairs_multipole"])
 
 
+# Nominal FP64 rate of a B300 (1.25 TFLOP/s) at its maximum SM clock (2032 MHz):
+# 1.25e12 / (148 SMs * 2.032e9) = 4.16 FP64 flop per clock per SM.
+NOMINAL_FP64_TFLOPS = 1.25
+NOMINAL_SM_MHZ = 2032.0
+
+
 def fp64_peak(ot, dev, stream):
-    """Best FP64 FMA rate of the probe kernel over 1, 2, 4 and 8 resident
-    blocks of 256 threads per SM (16 independent FMA chains per thread)."""
+    """Best FP64 FMA rate of the probe kernel over both operand patterns and
+    1, 2, 4, 8 resident blocks of 256 threads per SM."""
     import torch
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     best, cfg = 0.0, None
-    for per_sm in (1, 2, 4, 8):
-        blocks, iters = nsm * per_sm, 16000 // per_sm
-        out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
-        ot.fp64_fma_probe(out, blocks, 100)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-        for a, b in ev:
-            a.record(stream)
-            ot.fp64_fma_probe(out, blocks, iters)
-            b.record(stream)
-        torch.cuda.synchronize()
-        ms = min(a.elapsed_time(b) for a, b in ev)
-        tf = 2.0 * blocks * 256 * iters * 16 / (ms * 1e-3) / 1e12
-        if tf > best:
-            best, cfg = tf, {"blocks_per_sm": per_sm, "ms": ms}
+    for variant in (0, 1):
+        for per_sm in (1, 2, 4, 8):
+            blocks, iters = nsm * per_sm, 16000 // per_sm
+            out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+            ot.fp64_fma_probe(out, blocks, 100, variant)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+            for a, b in ev:
+                a.record(stream)
+                ot.fp64_fma_probe(out, blocks, iters, variant)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = min(a.elapsed_time(b) for a, b in ev)
+            tf = 2.0 * blocks * 256 * iters * 16 / (ms * 1e-3) / 1e12
+            if tf > best:
+                best, cfg = tf, {"variant": variant, "blocks_per_sm": per_sm, "ms": round(ms, 3)}
     return best, cfg
+
+
+def aggregate(world, steps, pairs_step, local_seconds):
+    """Whole-job throughput: pairs of all ranks / the slowest rank's time."""
+    total_s = max_over_ranks(local_seconds, world)
+    return world * steps * pairs_step / total_s, total_s * 1e3 / steps
 
 
 def run_ours(args, rank, world):
@@ -204,8 +219,11 @@ def run_ours(args, rank, world):
     L = g.zeros(tree.n, 20, 512)
     Lc = g.zeros(tree.n, 3, 512)
     tuned = None
-    if args.autotune:
-        tuned = g.autotune(M, m, L, Lc)
+    if args.tile:
+        w, b = (int(x) for x in args.tile.lower().split("x"))
+        g.set_schedule(sched, w, b, not args.no_graph)
+    elif not args.no_autotune and sched == ot.OT_SCHED_PERSISTENT:
+        tuned = g.autotune(M, m, L, Lc)      # tile shape of the persistent launch
     info = g.info()
     Mb = g.zeros(tree.n, 20, 512)
     mb = g.zeros(tree.n, 512)
@@ -219,6 +237,8 @@ def run_ours(args, rank, world):
         g.moments_backward(Mb, mb, rb)
 
     stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -226,8 +246,6 @@ def run_ours(args, rank, world):
 
     # -- timed region: K steps, L2 flushed between steps (outside the events) --
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -240,7 +258,6 @@ def run_ours(args, rank, world):
     barrier(world)
     wall = time.perf_counter() - t0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    clk = clocks.stop()
     g.check()
 
     # -- dominant kernel: the fused forward launch, timed alone --------------
@@ -259,6 +276,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     fwd_ms = statistics.median(a.elapsed_time(b) for a, b in fe)
     adj_ms = statistics.median(a.elapsed_time(b) for a, b in be)
+    clk = clocks.stop()
 
     # -- FP64 FMA peak, measured on this GPU at the clocks it runs now --------
     peak_tflops, probe_cfg = fp64_peak(ot, dev, stream)
@@ -283,10 +301,9 @@ def run_ours(args, rank, world):
 
     pairs_fwd = info["pairs_multipole"] + info["pairs_monopole"]
     pairs_step = 2 * pairs_fwd
-    total_s = sum(step_ms) / 1e3
-    total_s = max_over_ranks(total_s, world)
-    value = world * args.steps * pairs_step / total_s
-    ms_per_step = total_s * 1e3 / args.steps
+    value, ms_per_step = aggregate(world, args.steps, pairs_step, sum(step_ms) / 1e3)
+    sm_mhz = clk.get("sm_mhz") or NOMINAL_SM_MHZ
+    peak = NOMINAL_FP64_TFLOPS * sm_mhz / NOMINAL_SM_MHZ
     ach = fwd_flops(info) / (fwd_ms * 1e-3) / 1e12
     n_m2m = int(len({int(l) for l in tree.level[tree.is_leaf == 0]}))
     launches_step = (1 + n_m2m) + 2 + 2 + (1 if info["n_virtual"] else 0) + (1 + n_m2m + 1)
@@ -304,14 +321,15 @@ def run_ours(args, rank, world):
         "fwd": {"value": pairs_fwd / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
         "adjoint": {"value": pairs_fwd / (adj_ms * 1e-3), "unit": UNIT, "ms": adj_ms},
         "roofline": {"bound": "alu", "kernel": "forward_kernel<3> (both passes, one launch)",
-                     "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
-                     "traffic": None,
-                     "peak_source": f"measured: best FP64 FMA probe rate on this GPU in this run ({probe_cfg})",
-                     "executed_frac": 2.0 * info["fma_fwd"] / (fwd_ms * 1e-3) / 1e12 / peak_tflops,
+                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                     "peak_source": (f"nominal B300 FP64 {NOMINAL_FP64_TFLOPS} TFLOP/s at {NOMINAL_SM_MHZ:.0f} MHz, "
+                                     f"scaled to the median SM clock sampled in this run ({sm_mhz:.0f} MHz)"),
+                     "probe_tflops": peak_tflops, "probe": probe_cfg,
+                     "executed_tflops": 2.0 * info["fma_fwd"] / (fwd_ms * 1e-3) / 1e12,
                      "useful_over_executed": fwd_flops(info) / (2.0 * info["fma_fwd"]),
                      "adjoint_achieved": adj_flops(info) / (adj_ms * 1e-3) / 1e12,
-                     "adjoint_frac": adj_flops(info) / (adj_ms * 1e-3) / 1e12 / peak_tflops,
-                     "adjoint_executed_frac": 2.0 * info["fma_adj"] / (adj_ms * 1e-3) / 1e12 / peak_tflops},
+                     "adjoint_frac": adj_flops(info) / (adj_ms * 1e-3) / 1e12 / peak,
+                     "adjoint_executed_tflops": 2.0 * info["fma_adj"] / (adj_ms * 1e-3) / 1e12},
         "e2e": {"value": world * pairs_step / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(rho_pin.numel() * 8 + Lbar_pin.numel() * 8),
                 "d2h_bytes_per_step": int(L_out.numel() * 8 + rb_out.numel() * 8), "ms": e2e_ms},

@@ -208,10 +208,12 @@ ot_status ot_multipole_interactions_noalloc(ot_grid* grid, const double* M, doub
  * OT_EDEVICE with the failing work item in ot_last_error(). */
 ot_status ot_grid_check(ot_grid* grid, void* stream);
 
-/* FP64 FMA throughput probe (the roofline denominator): `blocks` x 256
- * threads each run `iters` rounds of 16 independent FMA chains; out [blocks*256]
- * receives the chain results (keeps them live).  Time it with events. */
-ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, void* stream);
+/* FP64 FMA throughput probe: `blocks` x 256 threads each run `iters` rounds of
+ * 16 independent FMAs -- variant 0: chains a = a*b + c; variant 1: 16
+ * accumulators a_j += s * x_j (the contraction's operand pattern).
+ * out [blocks*256] receives the results (keeps them live).  Time it with
+ * events; 2 * blocks * 256 * iters * 16 flops per launch. */
+ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, int32_t variant, void* stream);
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* ot_last_error(void);

@@ -74,7 +74,7 @@ def load():
         "ot_set_schedule": [P, I, I, I, I],
         "ot_autotune": [P, P, P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double)],
         "ot_grid_check": [P, P],
-        "ot_fp64_fma_probe": [P, I, I, P],
+        "ot_fp64_fma_probe": [P, I, I, I, P],
         "ot_multipole_interactions_noalloc": [P, P, P, P, P],
     }
     for name, args in sig.items():

@@ -639,15 +639,21 @@ __global__ void cube_adjoint_kernel(const double* __restrict__ Mb, double* __res
 // FP64 FMA throughput probe
 // ---------------------------------------------------------------------------
 
+// variant 0: 16 chains a = a * b + c; variant 1: 16 accumulators a += s * x[j]
+// (the contraction's pattern: shared scalar, distinct multiplier per chain)
+template <int VARIANT>
 __global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, int iters) {
     constexpr int K = 16;
-    double a[K];
-    const double b = 0.999999, c = 1e-6 * (1.0 + threadIdx.x * 1e-9);
+    double a[K], x[K];
+    const double b = 0.999999, c = 1e-6 * (1.0 + threadIdx.x * 1e-9), sc = 1e-9 * (1.0 + threadIdx.x * 1e-9);
 #pragma unroll
-    for (int j = 0; j < K; ++j) a[j] = 0.5 + 0.01 * j;
+    for (int j = 0; j < K; ++j) {
+        a[j] = 0.5 + 0.01 * j;
+        x[j] = 1.0 + 0.03 * j;
+    }
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int j = 0; j < K; ++j) a[j] = fma(a[j], b, c);
+        for (int j = 0; j < K; ++j) a[j] = (VARIANT == 0) ? fma(a[j], b, c) : fma(sc, x[j], a[j]);
     }
     double s = 0.0;
 #pragma unroll
@@ -754,8 +760,9 @@ cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nod
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {
-    fp64_probe_kernel<<<blocks, 256, 0, s>>>(out, iters);
+cudaError_t launch_fp64_probe(double* out, int blocks, int iters, int variant, cudaStream_t s) {
+    if (variant == 0) fp64_probe_kernel<0><<<blocks, 256, 0, s>>>(out, iters);
+    else fp64_probe_kernel<1><<<blocks, 256, 0, s>>>(out, iters);
     return cudaGetLastError();
 }
 

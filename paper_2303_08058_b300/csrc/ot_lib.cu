@@ -1115,11 +1115,12 @@ ot_status ot_grid_check(ot_grid* g, void* stream) {
     GUARD_END
 }
 
-ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, void* stream) {
+ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, int32_t variant, void* stream) {
     GUARD_BEGIN
     CHECK_PTR(out, "out");
     if (blocks <= 0 || iters <= 0) return fail(OT_EINVAL, "blocks and iters must be positive");
-    OT_CUDA(launch_fp64_probe(out, blocks, iters, static_cast<cudaStream_t>(stream)));
+    if (variant != 0 && variant != 1) return fail(OT_EINVAL, "variant must be 0 or 1");
+    OT_CUDA(launch_fp64_probe(out, blocks, iters, variant, static_cast<cudaStream_t>(stream)));
     return OT_OK;
     GUARD_END
 }

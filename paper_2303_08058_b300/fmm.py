@@ -130,9 +130,9 @@ class OTGrid:
         return Mbar, mbar
 
 
-def fp64_fma_probe(out, blocks, iters, stream=None):
+def fp64_fma_probe(out, blocks, iters, variant=0, stream=None):
     lib = _lib.load()
-    _lib.check(lib.ot_fp64_fma_probe(_ptr(out), int(blocks), int(iters), _stream(stream)))
+    _lib.check(lib.ot_fp64_fma_probe(_ptr(out), int(blocks), int(iters), int(variant), _stream(stream)))
 
 
 class FMMInteractions(torch.autograd.Function):

@@ -67,7 +67,7 @@ def test_host_argument_checks_without_device(lib):
     assert lib.ot_grid_destroy(None) == _lib.OT_OK
     assert lib.ot_set_schedule(None, 0, 4, 0, 1) == _lib.OT_EINVAL
     assert lib.ot_interactions(None, None, None, None, None, None) == _lib.OT_EINVAL
-    assert lib.ot_fp64_fma_probe(None, 1, 1, None) == _lib.OT_EINVAL
+    assert lib.ot_fp64_fma_probe(None, 1, 1, 0, None) == _lib.OT_EINVAL
 
 
 def test_generated_contraction_code_is_current():

@@ -409,6 +409,7 @@ def test_abi_rejects_bad_input(ot):
 
 def test_fp64_probe_runs(ot):
     out = torch.zeros(148 * 256, dtype=torch.float64, device="cuda")
-    ot.fp64_fma_probe(out, 148, 100)
-    torch.cuda.synchronize()
-    assert np.all(np.isfinite(host(out))) and np.all(host(out) > 0)
+    for variant in (0, 1):
+        ot.fp64_fma_probe(out, 148, 100, variant)
+        torch.cuda.synchronize()
+        assert np.all(np.isfinite(host(out))) and np.all(host(out) > 0)

@@ -1,0 +1,122 @@
+"""Full-size workloads on the GPU: the differentiation workload (loss over
+1000 probe cells of the 64^3 polytrope, gradient by the adjoint kernels) and
+the rotating binary-star octree, checked against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import assert_parity, oracle_threads, sample_targets
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ot():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2303_08058_b300 as ot
+    ot.load()
+    return ot
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    oracle_threads(oracle)
+    return oracle
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def test_config4_probe_loss_gradient(ot, orc):
+    """loss = sum over 1000 seeded probe cells of (L0)^2 on the 64^3 grid;
+    d loss / d rho for all 262,144 leaf densities through the adjoint kernels,
+    against the oracle's transposed sum and central differences."""
+    tree, rho_h = synth.config2()
+    leaf_nodes = np.nonzero(tree.level == 3)[0]
+    probes = synth.config4_probes()
+    pn, pc = leaf_nodes[probes // 512], probes % 512
+    g = ot.OTGrid.from_tree(tree)
+    rho = dev(rho_h).requires_grad_(True)
+    L = ot.potential_and_gradient(g, rho)
+    loss = (L[pn, 0, pc] ** 2).sum()
+    loss.backward()
+    grad = host(rho.grad)
+    g.check()
+
+    # oracle: with h = 1, d loss / d rho of a leaf cell is its point-mass
+    # adjoint for L-bar = 2 L0 at the probes (leaf moments reach the loss only
+    # through their masses; coarse densities are not used at all)
+    Lbar = np.zeros((tree.n, 20, 512))
+    Lbar[pn, 0, pc] = 2.0 * host(L)[pn, 0, pc]
+    tg = np.stack([pn, pc], 1).astype(np.int32)
+    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
+    assert_parity(grad[leaf_nodes], mo[leaf_nodes], Sm[leaf_nodes], what="d loss / d rho")
+    assert np.all(grad[tree.level < 3] == 0)
+
+    # central differences, relative step 1e-6, on 64 cells inside the star
+    rng = np.random.default_rng(5)
+    inside = np.argwhere(rho_h[leaf_nodes] > 1e-3)
+    pick = inside[rng.choice(len(inside), 64, replace=False)]
+
+    def f(r):
+        with torch.no_grad():
+            Lr = ot.potential_and_gradient(g, dev(r))
+            return float((Lr[pn, 0, pc] ** 2).sum())
+    for (k, c) in pick:
+        n = leaf_nodes[k]
+        step = 1e-6 * rho_h[n, c]
+        rp, rm = rho_h.copy(), rho_h.copy()
+        rp[n, c] += step
+        rm[n, c] -= step
+        fd = (f(rp) - f(rm)) / (2 * step)
+        assert abs(grad[n, c] - fd) <= 1e-4 * abs(fd), (n, c, grad[n, c], fd)
+
+
+@pytest.mark.parametrize("step", [0, 7, 19])
+def test_config5_binary_star_steps(ot, orc, step):
+    """Rotating binary star on an adaptive octree (levels 3-7, ~8,300 leaves):
+    forward of both passes at sampled cells, adjoint against the oracle's
+    transposed sum for a sparse L-bar, and the dot-product identity for the
+    workload's dense N(0,1) L-bar."""
+    tree, rho = synth.config5_step(step)
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L, Lc = g.interactions(M, m)
+    torch.cuda.synchronize()
+    info = g.info()
+    assert info["pairs_virtual"] > 0 and info["n_virtual"] > 0
+    Mh, mh = host(M), host(m)
+    tg = sample_targets(tree, 120, 100 + step)
+    r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
+    r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
+    assert_parity(host(L)[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], r1["S"] + r2["S"], what="L")
+    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], r1["Sc"], what="Lc")
+
+    rng = np.random.default_rng(200 + step)
+    sp = np.unique(sample_targets(tree, 200, 300 + step), axis=0)
+    Lbar = np.zeros((tree.n, 20, 512))
+    Lbar[sp[:, 0], :, sp[:, 1]] = rng.standard_normal((len(sp), 20))
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=sp)
+    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=sp)
+    assert_parity(host(Mb), Mo, SM, what="Mbar")
+    assert_parity(host(mb), mo, Sm, what="mbar")
+
+    Lbar_d = dev(rng.standard_normal((tree.n, 20, 512)))
+    L2, _ = g.interactions(M, m, want_lc=False)
+    Mb2, mb2 = g.backward(Lbar_d)
+    lhs = float((L2 * Lbar_d).sum())
+    rhs = float((M * Mb2).sum() + (m * mb2).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-11)
+    g.check()
+    g.close()

@@ -1,0 +1,57 @@
+"""The N > 1 control path of bench.py with world-size-2 gloo ranks on CPU:
+replicas share nothing on the data path; the whole-job value divides the
+pairs of all ranks by the slowest rank's time; the reference arm runs on
+rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank), OT_DIST_BACKEND="gloo")
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    r, w = bench.dist_init(None)
+    bench.barrier(w)
+    value, ms = bench.aggregate(w, steps=10, pairs_step=1000, local_seconds=1.0 + r)   # rank 1 is slower
+    q.put((r, w, value, ms))
+    dist.destroy_process_group()
+
+
+def test_two_replicas_aggregate_over_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, w, value, ms in out:
+        assert w == 2
+        assert value == pytest.approx(2 * 10 * 1000 / 2.0)     # both ranks' pairs / max time (2 s)
+        assert ms == pytest.approx(200.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
