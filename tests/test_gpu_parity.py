@@ -115,8 +115,8 @@ def test_config1_multipole_all_cells(ot, orc):
     L, Lc = g.multipole(M)
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "multipole", M=host(M))
-    assert_parity(host(L), r["L"], r["S"], what="L")
-    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc")
+    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
+    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
     assert g.info()["pairs_multipole"] == r["npairs"]
 
 
@@ -130,8 +130,8 @@ def test_single_subgrid_random_moments_all_terms(ot, orc, seed):
     L, Lc = g.multipole(dev(M))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "multipole", M=M)
-    assert_parity(host(L), r["L"], r["S"], what="L")
-    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc")
+    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
+    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
     assert np.max(np.abs(r["Lc"])) > 0
 
 
@@ -144,7 +144,7 @@ def test_root_leaf_subgrid_root_and_near_stencils(ot, orc):
     L = g.monopole(dev(m))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "monopole", m=m)
-    assert_parity(host(L), r["L"], r["S"], what="L")
+    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
     assert g.info()["pairs_monopole"] == r["npairs"] == 512 * 511
 
 
@@ -156,7 +156,7 @@ def test_monopole_uniform_level(ot, orc):
     L = g.monopole(dev(m))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "monopole", m=m)
-    assert_parity(host(L), r["L"], r["S"], what="L")
+    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
     assert g.info()["pairs_monopole"] == r["npairs"]
 
 
@@ -166,8 +166,8 @@ def test_fused_uniform_tree_with_coarse_levels(ot, orc):
     g, M, m, L, Lc = gpu_fused(ot, tree, rho)
     tg = all_targets(tree)
     Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L")
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
     info = g.info()
     assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
 
@@ -189,8 +189,8 @@ def test_fused_adaptive_virtual_descendants(ot, orc):
     assert info["pairs_virtual"] > 0 and info["n_virtual"] > 0
     tg = all_targets(tree)
     Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L")
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
     assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
 
 
@@ -249,7 +249,7 @@ def test_adjoint_dense_single_subgrid(ot, orc):
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
     Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True)
-    assert_parity(host(Mb), Mo, SM, what="Mbar")
+    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
     assert np.all(host(mb) == 0)
 
 
@@ -264,7 +264,7 @@ def test_adjoint_matches_oracle_transposed_sum(ot, orc, which):
     torch.cuda.synchronize()
     Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg)
     mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
-    assert_parity(host(Mb), Mo, SM, what="Mbar")
+    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
     assert_parity(host(mb), mo, Sm, what="mbar")
     assert np.max(np.abs(mo)) > 0
 
@@ -325,8 +325,8 @@ def test_config2_full_size_sampled(ot, orc):
     g, M, m, L, Lc = gpu_fused(ot, tree, rho)
     tg = np.concatenate([sample_targets(tree, 96, 61, levels=[3]), sample_targets(tree, 48, 62, levels=[0, 1, 2])])
     Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L")
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
     # every leaf cell: potential negative, the field points inward (towards the star centre)
     leaf = tree.level == 3
     assert np.all(L[leaf, 0, :] < 0)
@@ -374,8 +374,8 @@ def test_adaptive_workloads_sampled(ot, orc, cfg):
     assert info["pairs_virtual"] > 0
     tg = sample_targets(tree, 160, 65)
     Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L")
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
 
 
 # ---------------------------------------------------------------------------

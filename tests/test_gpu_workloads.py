@@ -71,6 +71,7 @@ def test_config4_probe_loss_gradient(ot, orc):
         with torch.no_grad():
             Lr = ot.potential_and_gradient(g, dev(r))
             return float((Lr[pn, 0, pc] ** 2).sum())
+    loss0 = float(loss)
     for (k, c) in pick:
         n = leaf_nodes[k]
         step = 1e-6 * rho_h[n, c]
@@ -78,7 +79,10 @@ def test_config4_probe_loss_gradient(ot, orc):
         rp[n, c] += step
         rm[n, c] -= step
         fd = (f(rp) - f(rm)) / (2 * step)
-        assert abs(grad[n, c] - fd) <= 1e-4 * abs(fd), (n, c, grad[n, c], fd)
+        # FD of a quadratic is exact up to rounding: the relative bound, plus
+        # one ulp of the loss (the rounding of each loss evaluation) per step
+        noise = np.finfo(np.float64).eps * abs(loss0) / step
+        assert abs(grad[n, c] - fd) <= 1e-4 * abs(fd) + noise, (n, c, grad[n, c], fd, noise)
 
 
 @pytest.mark.parametrize("step", [0, 7, 19])
@@ -98,8 +102,8 @@ def test_config5_binary_star_steps(ot, orc, step):
     tg = sample_targets(tree, 120, 100 + step)
     r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
     r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
-    assert_parity(host(L)[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], r1["S"] + r2["S"], what="L")
-    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], r1["Sc"], what="Lc")
+    assert_parity(host(L)[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
+    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], r1["Sc"], what="Lc", block_axis=1)
 
     rng = np.random.default_rng(200 + step)
     sp = np.unique(sample_targets(tree, 200, 300 + step), axis=0)
@@ -109,7 +113,7 @@ def test_config5_binary_star_steps(ot, orc, step):
     torch.cuda.synchronize()
     Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=sp)
     mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=sp)
-    assert_parity(host(Mb), Mo, SM, what="Mbar")
+    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
     assert_parity(host(mb), mo, Sm, what="mbar")
 
     Lbar_d = dev(rng.standard_normal((tree.n, 20, 512)))
