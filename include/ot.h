@@ -101,9 +101,12 @@ typedef struct {
     int64_t pairs_angular;         /* part of pairs_multipole with a non-leaf target */
     int64_t lanes_fwd;             /* warp lanes run by the forward pair loops of both
                                       passes, lanes with an empty source included */
-    int64_t fma_fwd;               /* FP64 FMAs issued by those lanes (16 per point-mass
-                                      lane, 70 per multipole lane, 100 with the angular term) */
-    int64_t fma_adj;               /* same for the adjoint pair loops */
+    int64_t flops_fwd;             /* algorithmic FP64 flops of one forward launch over
+                                      the in-domain pairs (2 per FMA, 1 per add) */
+    int64_t flops_adj;             /* the same for the adjoint */
+    int64_t ops_fwd;               /* FP64 instructions x lanes one forward launch
+                                      executes, lanes with an empty source included */
+    int64_t ops_adj;               /* the same for the adjoint */
     int32_t schedule;              /* ot_schedule in use */
     int32_t warps_per_block;       /* tile shape in use */
     int32_t blocks_per_sm;

@@ -41,8 +41,8 @@ class GridInfo(ctypes.Structure):
                 ("far_offsets", ctypes.c_int32), ("near_offsets", ctypes.c_int32),
                 ("root_offsets", ctypes.c_int32), ("pairs_multipole", ctypes.c_int64),
                 ("pairs_monopole", ctypes.c_int64), ("pairs_virtual", ctypes.c_int64),
-                ("pairs_angular", ctypes.c_int64), ("lanes_fwd", ctypes.c_int64), ("fma_fwd", ctypes.c_int64),
-                ("fma_adj", ctypes.c_int64), ("schedule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("pairs_angular", ctypes.c_int64), ("lanes_fwd", ctypes.c_int64), ("flops_fwd", ctypes.c_int64),
+                ("flops_adj", ctypes.c_int64), ("ops_fwd", ctypes.c_int64), ("ops_adj", ctypes.c_int64), ("schedule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("graphs_enabled", ctypes.c_int32)]
 
     def as_dict(self):

@@ -18,6 +18,14 @@ With both sides reduced, one multipole pair costs 70 FMAs for the 16
 coefficients (instead of 84 with all 20 components), one point-mass pair 16
 (instead of 20), and the transposed (adjoint) contractions cost the same.
 
+Paired offsets.  When a target's list holds both o and -o, the two sources
+share one table row: d^k G(-R) = (-1)^k d^k G(R), so with the sum s and the
+difference d of the two sources' (reduced) moments, every FMA takes s when
+its derivative has even order and d when odd.  Two point-mass pairs then
+cost 16 FMAs + 2 adds, two multipole pairs 70 FMAs + 32 adds (+ 30 FMAs for
+the angular term, whose derivatives are all of order 4); the multipole
+adjoint pairs the same way on the two targets' L-bar.
+
 Derivative-table row layout (36 doubles per integer offset):
   [0..15]  the IND16 components of ranks 0..3
   [16..19] zz, xzz, yzz, zzz
@@ -123,11 +131,47 @@ def emit():
                 w(f"  g[{k}] = fma(lb[{j}], d[{di}], g[{k}]);\n")
     w("}\n\n")
 
+    # paired point-mass sources: a[J] += (even order ? s : d) * d[J]
+    w("// paired: 16 FMAs for two point-mass pairs (s = m+ + m-, d = m+ - m-)\n")
+    w("__device__ __forceinline__ void ot_mono_fwd_pair(double (&a)[16], double s, double dm, const double (&d)[36]) {\n")
+    for j in range(16):
+        w(f"  a[{j}] = fma({'s' if rank(IND16[j]) % 2 == 0 else 'dm'}, d[{j}], a[{j}]);\n")
+    w("}\n\n")
+
+    # paired multipole sources: a[J] += (even order of J+K ? rs[K] : rd[K]) * d[J+K]
+    w("// paired: 70 FMAs for two multipole pairs (rs = r+ + r-, rd = r+ - r-)\n")
+    w("__device__ __forceinline__ void ot_multi_fwd_pair(double (&a)[16], const double (&rs)[16], const double (&rd)[16],\n"
+      "                                                  const double (&d)[36]) {\n")
+    for k in range(16):
+        for (j, kk, di) in terms:
+            if kk == k:
+                src = "rs" if rank(ROW[di]) % 2 == 0 else "rd"
+                w(f"  a[{j}] = fma({src}[{k}], d[{di}], a[{j}]);\n")
+    w("}\n\n")
+
+    # paired multipole adjoint: g[K] += sum_J (even order of J+K ? ls[J] : ld[J]) * d[J+K]
+    w("// paired: 70 FMAs for two targets (ls = lb+ + lb-, ld = lb+ - lb-)\n")
+    w("__device__ __forceinline__ void ot_multi_adj_pair(double (&g)[16], const double (&ls)[16], const double (&ld)[16],\n"
+      "                                                  const double (&d)[36]) {\n")
+    for j in range(16):
+        for (jj, k, di) in terms:
+            if jj == j:
+                src = "ls" if rank(ROW[di]) % 2 == 0 else "ld"
+                w(f"  g[{k}] = fma({src}[{j}], d[{di}], g[{k}]);\n")
+    w("}\n\n")
+
     # adjoint, point-mass source: g[s] += sum_J lb[J] d[J]  (4 partial sums)
     w("// 16 FMAs\n")
     w("__device__ __forceinline__ void ot_mono_adj(double (&g)[4], const double (&lb)[16], const double (&d)[36]) {\n")
     for j in range(16):
         w(f"  g[{j % 4}] = fma(lb[{j}], d[{j}], g[{j % 4}]);\n")
+    w("}\n\n")
+    # the same with the row of -o: odd-order derivatives negated
+    w("// 16 FMAs (derivatives of the negated offset)\n")
+    w("__device__ __forceinline__ void ot_mono_adj_neg(double (&g)[4], const double (&lb)[16], const double (&d)[36]) {\n")
+    for j in range(16):
+        sign = "" if rank(IND16[j]) % 2 == 0 else "-"
+        w(f"  g[{j % 4}] = fma({sign}lb[{j}], d[{j}], g[{j % 4}]);\n")
     w("}\n")
     return "".join(out)
 

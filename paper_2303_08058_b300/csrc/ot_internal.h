@@ -27,9 +27,12 @@ enum Kind : int { K_NONE = 0, K_MULTI = 1, K_LEAF = 2, K_VIRT = 3 };
 // the derivatives of G at R = -o (unit spacing), i.e. for the pair
 // target -> source at offset o.  The row of -o is NOFF - 1 - row(o).
 
+// Each far list holds far_pairs entries standing for an offset o and its
+// negation -o (both in the list), then far_len - far_pairs single offsets.
+// The near and root lists are closed under negation: every entry is paired.
 struct Lists {
     const int* lists;      // far[8][far_len] | near[near_len] | root[root_len]
-    int far_len, near_len, root_len;
+    int far_len, far_pairs, near_len, root_len;
     int near_off, root_off;
 };
 

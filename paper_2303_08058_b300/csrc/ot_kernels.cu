@@ -65,7 +65,49 @@ __device__ __forceinline__ void lane_cell(int lane, int par, int half, int& x, i
 // forward stencil walk
 // ---------------------------------------------------------------------------
 
-template <int MODE>
+// point mass of the source at local position s (in [-7, 14]^3) seen through
+// neighbour entry e; 0 unless it is a leaf cell or a virtual descendant
+__device__ __forceinline__ double source_mass(const FwdParams& p, int2 e, int kind, int sx, int sy, int sz) {
+    if (kind == K_LEAF) return __ldg(p.m + static_cast<size_t>(e.x) * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7));
+    if (kind == K_VIRT) {
+        const unsigned meta = static_cast<unsigned>(e.y);
+        const int d = (meta >> 2) & 7;
+        const int vx = static_cast<int>(((meta >> 8) & 0xffu) + (sx & 7)) >> d;
+        const int vy = static_cast<int>(((meta >> 16) & 0xffu) + (sy & 7)) >> d;
+        const int vz = static_cast<int>((meta >> 24) + (sz & 7)) >> d;
+        return __ldg(p.m + static_cast<size_t>(e.x) * NCELL + vx + 8 * vy + 64 * vz) * pow2i(-3 * d);
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ void source_moments(const FwdParams& p, int2 e, bool multi, int sx, int sy, int sz,
+                                               double (&r)[16]) {
+    if (multi) {
+        const double* src = p.Mhat + static_cast<size_t>(e.x) * NRED * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) r[q] = __ldg(src + q * NCELL);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) r[q] = 0.0;
+    }
+}
+
+__device__ __forceinline__ int checked_kind(const FwdParams& p, int2 e, int item) {
+    int kind = e.y & 3;
+    if (kind != K_NONE && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
+        report(p.status, 1, item);
+        kind = K_NONE;
+    }
+    return kind;
+}
+
+__device__ __forceinline__ int nb_index(int sx, int sy, int sz) {
+    return ((sx + 8) >> 3) + 3 * ((sy + 8) >> 3) + 9 * ((sz + 8) >> 3);
+}
+
+// PAIRED: each entry o stands for the offsets o and -o (sources at t + o and
+// t - o share the table row of o, with odd-order derivatives negated for -o).
+template <int MODE, bool PAIRED>
 __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
                                              int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                              const FwdParams& p, double (&a)[16], double (&c)[3],
@@ -73,50 +115,51 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
-        const int sx = tx + ox, sy = ty + oy, sz = tz + oz;   // in [-7, 14]
-        const int nb = ((sx + 8) >> 3) + 3 * ((sy + 8) >> 3) + 9 * ((sz + 8) >> 3);
-        const int2 e = s_nb[nb];
-        int kind = e.y & 3;
-        if (kind != K_NONE && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
-            report(p.status, 1, item);
-            kind = K_NONE;
+        const int px = tx + ox, py = ty + oy, pz = tz + oz;   // in [-7, 14]
+        const int mx = tx - ox, my = ty - oy, mz = tz - oz;
+        const int2 ep = s_nb[nb_index(px, py, pz)];
+        const int kp = checked_kind(p, ep, item);
+        int2 em = make_int2(-1, 0);
+        int km = K_NONE;
+        if (PAIRED) {
+            em = s_nb[nb_index(mx, my, mz)];
+            km = checked_kind(p, em, item);
         }
-        const int lcell = (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
         const int row = offset_row(ox, oy, oz);
         if (MODE & 2) {
-            const bool mono = kind >= K_LEAF;
+            const bool mono = kp >= K_LEAF || km >= K_LEAF;
             if (__any_sync(0xffffffffu, mono)) {
-                double mass = 0.0;
-                if (kind == K_LEAF) {
-                    mass = __ldg(p.m + static_cast<size_t>(e.x) * NCELL + lcell);
-                } else if (kind == K_VIRT) {
-                    const unsigned meta = static_cast<unsigned>(e.y);
-                    const int d = (meta >> 2) & 7;
-                    const int vx = static_cast<int>(((meta >> 8) & 0xffu) + (sx & 7)) >> d;
-                    const int vy = static_cast<int>(((meta >> 16) & 0xffu) + (sy & 7)) >> d;
-                    const int vz = static_cast<int>((meta >> 24) + (sz & 7)) >> d;
-                    mass = __ldg(p.m + static_cast<size_t>(e.x) * NCELL + vx + 8 * vy + 64 * vz) * pow2i(-3 * d);
-                }
+                const double mp = source_mass(p, ep, kp, px, py, pz);
                 double d[36];
                 load_row16(d, p.Dt, row);
-                ot_mono_fwd(a, mass, d);
+                if (PAIRED) {
+                    const double mm = source_mass(p, em, km, mx, my, mz);
+                    ot_mono_fwd_pair(a, mp + mm, mp - mm, d);
+                } else {
+                    ot_mono_fwd(a, mp, d);
+                }
             }
         }
         if (MODE & 1) {
-            const bool multi = kind == K_MULTI;
+            const bool multi = kp == K_MULTI || km == K_MULTI;
             if (__any_sync(0xffffffffu, multi)) {
                 double r[16];
-                if (multi) {
-                    const double* src = p.Mhat + static_cast<size_t>(e.x) * NRED * NCELL + lcell;
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) r[q] = __ldg(src + q * NCELL);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) r[q] = 0.0;
-                }
+                source_moments(p, ep, kp == K_MULTI, px, py, pz, r);
                 double d[36];
                 load_row(d, p.Dt, row);
-                ot_multi_fwd(a, r, d);
+                if (PAIRED) {
+                    double rm[16];
+                    source_moments(p, em, km == K_MULTI, mx, my, mz, rm);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const double t = r[q];
+                        r[q] = t + rm[q];     // sum
+                        rm[q] = t - rm[q];    // difference
+                    }
+                    ot_multi_fwd_pair(a, r, rm, d);
+                } else {
+                    ot_multi_fwd(a, r, d);
+                }
                 if (angular) ot_angular_fwd(c, t4, r, r[0], d);
             }
         }
@@ -211,12 +254,18 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
         for (int q = 0; q < 3; ++q) c[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) t4[q] = 0.0;
-        const int* l1 = (level == 0) ? p.L.lists + p.L.root_off : p.L.lists + par * p.L.far_len;
-        const int n1 = (level == 0) ? p.L.root_len : p.L.far_len;
-        walk_forward<MODE>(l1, n1, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, it);
+        if (level == 0) {
+            walk_forward<MODE, true>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, tx, ty, tz, s_nb[warp], p, a,
+                                     c, t4, it);
+        } else {
+            const int* lf = p.L.lists + par * p.L.far_len;
+            walk_forward<MODE, true>(lf, p.L.far_pairs, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, it);
+            walk_forward<MODE, false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, tx, ty, tz,
+                                      s_nb[warp], p, a, c, t4, it);
+        }
         if (leafT)
-            walk_forward<MODE>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p, a,
-                               c, t4, it);
+            walk_forward<MODE, true>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p, a,
+                                     c, t4, it);
         store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
         __syncwarp();
         if (!persistent) break;
@@ -229,8 +278,9 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
 
 // Source B of parity p gathers from targets A = B + o' for o' in the forward
 // list of parity p (far pairs are symmetric under o -> -o with the parities
-// swapped), with the table row of the forward offset o = -o'.
-template <bool MULTI>
+// swapped), with the table row of the forward offset o = -o'.  A paired
+// entry o' also gathers from A = B - o' (row of o', odd orders negated).
+template <bool MULTI, bool PAIRED>
 __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int len, bool near_seg,
                                              int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
                                              const AdjParams& p, double (&g)[16], double (&g4)[4],
@@ -238,20 +288,31 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
-        const int tx = sx0 + ox, ty = sy0 + oy, tz = sz0 + oz;
-        const int nb = ((tx + 8) >> 3) + 3 * ((ty + 8) >> 3) + 9 * ((tz + 8) >> 3);
-        const int2 e = s_nb[nb];
-        const int kind = e.y & 3;
-        bool valid = (kind == K_MULTI || kind == K_LEAF) && (!near_seg || kind == K_LEAF);
-        if (valid && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
+        const int px = sx0 + ox, py = sy0 + oy, pz = sz0 + oz;
+        const int mx = sx0 - ox, my = sy0 - oy, mz = sz0 - oz;
+        const int2 ep = s_nb[nb_index(px, py, pz)];
+        int kp = ep.y & 3;
+        bool vp = (kp == K_MULTI || kp == K_LEAF) && (!near_seg || kp == K_LEAF);
+        if (vp && static_cast<unsigned>(ep.x) >= static_cast<unsigned>(p.n_nodes)) {
             report(p.status, 2, item);
-            valid = false;
+            vp = false;
         }
-        if (!__any_sync(0xffffffffu, valid)) continue;
-        const int tcell = (tx & 7) + 8 * (ty & 7) + 64 * (tz & 7);
+        int2 em = make_int2(-1, 0);
+        bool vm = false;
+        if (PAIRED) {
+            em = s_nb[nb_index(mx, my, mz)];
+            const int km = em.y & 3;
+            vm = (km == K_MULTI || km == K_LEAF) && (!near_seg || km == K_LEAF);
+            if (vm && static_cast<unsigned>(em.x) >= static_cast<unsigned>(p.n_nodes)) {
+                report(p.status, 2, item);
+                vm = false;
+            }
+        }
+        if (!__any_sync(0xffffffffu, vp || vm)) continue;
         double lb[16];
-        if (valid) {
-            const double* src = p.Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + tcell;
+        if (vp) {
+            const double* src = p.Lrbar + static_cast<size_t>(ep.x) * NRED * NCELL + (px & 7) + 8 * (py & 7) +
+                                64 * (pz & 7);
 #pragma unroll
             for (int q = 0; q < 16; ++q) lb[q] = __ldg(src + q * NCELL);
         } else {
@@ -262,10 +323,43 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
         double d[36];
         if (MULTI) {
             load_row(d, p.Dt, row);
-            ot_multi_adj(g, lb, d);
+            if (PAIRED) {
+                double lm[16];
+                if (vm) {
+                    const double* src = p.Lrbar + static_cast<size_t>(em.x) * NRED * NCELL + (mx & 7) +
+                                        8 * (my & 7) + 64 * (mz & 7);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) lm[q] = __ldg(src + q * NCELL);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) lm[q] = 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const double t = lb[q];
+                    lb[q] = t + lm[q];
+                    lm[q] = t - lm[q];
+                }
+                ot_multi_adj_pair(g, lb, lm, d);
+            } else {
+                ot_multi_adj(g, lb, d);
+            }
         } else {
             load_row16(d, p.Dt, row);
             ot_mono_adj(g4, lb, d);
+            if (PAIRED) {
+                double lm[16];
+                if (vm) {
+                    const double* src = p.Lrbar + static_cast<size_t>(em.x) * NRED * NCELL + (mx & 7) +
+                                        8 * (my & 7) + 64 * (mz & 7);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) lm[q] = __ldg(src + q * NCELL);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) lm[q] = 0.0;
+                }
+                ot_mono_adj_neg(g4, lm, d);
+            }
         }
     }
 }
@@ -314,8 +408,14 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
         for (int q = 0; q < 4; ++q) g4[q] = 0.0;
         if (skind == K_MULTI) {
             if ((MODE & 1) && p.Mbar != nullptr) {
-                walk_adjoint<true>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
-                walk_adjoint<true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                if (level == 0) {
+                    walk_adjoint<true, true>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                } else {
+                    walk_adjoint<true, true>(l1, p.L.far_pairs, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                    walk_adjoint<true, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, sx, sy, sz, s_nb[warp],
+                                              p, g, g4, it);
+                }
+                walk_adjoint<true, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
                 // expand the traceless reduction and apply (-1)^m/m! * multiplicity * h^-m
                 double Mb[20];
                 Mb[0] = g[0];
@@ -344,8 +444,14 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
                 for (int q = 0; q < 20; ++q) out[q * NCELL] = Mb[q];
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
-            walk_adjoint<false>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
-            walk_adjoint<false>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
+            if (level == 0) {
+                walk_adjoint<false, true>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+            } else {
+                walk_adjoint<false, true>(l1, p.L.far_pairs, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                walk_adjoint<false, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, sx, sy, sz, s_nb[warp], p,
+                                           g, g4, it);
+            }
+            walk_adjoint<false, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
             const double v = (g4[0] + g4[1]) + (g4[2] + g4[3]);
             if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = v;
             else p.mbar[static_cast<size_t>(src) * NCELL + scell] = v;

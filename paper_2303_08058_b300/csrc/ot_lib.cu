@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
+#include <set>
 #include <new>
 #include <string>
 #include <tuple>
@@ -151,7 +153,7 @@ struct ot_grid {
     std::vector<int2> nbr, vnbr;
     std::vector<int> ninfo, vinfo;
     std::vector<int> lists;
-    int far_len = 0, near_len = 0, root_len = 0;
+    int far_len = 0, far_pairs = 0, near_len = 0, root_len = 0, far_offsets = 0;
     double hinv[MAXLEV];
 
     // device buffers
@@ -302,34 +304,66 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     for (int l = 0; l < MAXLEV; ++l) g->hinv[l] = std::ldexp(1.0, l) / desc->h0;
 
     // --- stencils -------------------------------------------------------------
+    // far[p]: well separated at this level, parents not; near: not well
+    // separated; root: well separated.  Each list is stored as entries o
+    // standing for the pair {o, -o} when both are in it (flag bit 24; the
+    // representative has the larger packed key), then the single offsets.
     const int c = 12;
-    std::vector<int> far[8], near, root;
+    auto key = [](int ox, int oy, int oz) { return ((oz + 8) << 16) | ((oy + 8) << 8) | (ox + 8); };
+    auto split = [&](const std::vector<std::array<int, 3>>& offs, std::vector<int>& pairs, std::vector<int>& singles) {
+        std::set<int> in;
+        for (auto& o : offs) in.insert(key(o[0], o[1], o[2]));
+        for (auto& o : offs) {
+            const int k = key(o[0], o[1], o[2]), kn = key(-o[0], -o[1], -o[2]);
+            if (in.count(kn)) {
+                if (k > kn) pairs.push_back(pack_offset(o[0], o[1], o[2]) | (1 << 24));
+            } else {
+                singles.push_back(pack_offset(o[0], o[1], o[2]));
+            }
+        }
+    };
+    std::vector<int> far_pair[8], far_single[8], near_pair, near_single, root_pair, root_single;
     for (int p = 0; p < 8; ++p) {
         const int px = p & 1, py = (p >> 1) & 1, pz = (p >> 2) & 1;
+        std::vector<std::array<int, 3>> offs;
         for (int oz = -7; oz <= 7; ++oz)
             for (int oy = -7; oy <= 7; ++oy)
                 for (int ox = -7; ox <= 7; ++ox) {
                     const int n2 = ox * ox + oy * oy + oz * oz;
                     const int qx = fdiv2(px + ox), qy = fdiv2(py + oy), qz = fdiv2(pz + oz);
-                    if (n2 > c && qx * qx + qy * qy + qz * qz <= c) far[p].push_back(pack_offset(ox, oy, oz));
+                    if (n2 > c && qx * qx + qy * qy + qz * qz <= c) offs.push_back({ox, oy, oz});
                 }
+        split(offs, far_pair[p], far_single[p]);
     }
-    for (int oz = -7; oz <= 7; ++oz)
-        for (int oy = -7; oy <= 7; ++oy)
-            for (int ox = -7; ox <= 7; ++ox) {
-                const int n2 = ox * ox + oy * oy + oz * oz;
-                if (n2 > 0 && n2 <= c) near.push_back(pack_offset(ox, oy, oz));
-                if (n2 > c) root.push_back(pack_offset(ox, oy, oz));
-            }
+    {
+        std::vector<std::array<int, 3>> nr, rt;
+        for (int oz = -7; oz <= 7; ++oz)
+            for (int oy = -7; oy <= 7; ++oy)
+                for (int ox = -7; ox <= 7; ++ox) {
+                    const int n2 = ox * ox + oy * oy + oz * oz;
+                    if (n2 > 0 && n2 <= c) nr.push_back({ox, oy, oz});
+                    if (n2 > c) rt.push_back({ox, oy, oz});
+                }
+        split(nr, near_pair, near_single);
+        split(rt, root_pair, root_single);
+    }
     for (int p = 1; p < 8; ++p)
-        if (far[p].size() != far[0].size()) return fail(OT_EINVAL, "internal: parity stencils differ in size");
-    g->far_len = static_cast<int>(far[0].size());
-    g->near_len = static_cast<int>(near.size());
-    g->root_len = static_cast<int>(root.size());
+        if (far_pair[p].size() != far_pair[0].size() || far_single[p].size() != far_single[0].size())
+            return fail(OT_EINVAL, "internal: parity stencils differ in shape");
+    if (!near_single.empty() || !root_single.empty())
+        return fail(OT_EINVAL, "internal: near/root stencils not closed under negation");
+    g->far_pairs = static_cast<int>(far_pair[0].size());
+    g->far_len = g->far_pairs + static_cast<int>(far_single[0].size());
+    g->near_len = static_cast<int>(near_pair.size());
+    g->root_len = static_cast<int>(root_pair.size());
     g->lists.clear();
-    for (int p = 0; p < 8; ++p) g->lists.insert(g->lists.end(), far[p].begin(), far[p].end());
-    g->lists.insert(g->lists.end(), near.begin(), near.end());
-    g->lists.insert(g->lists.end(), root.begin(), root.end());
+    for (int p = 0; p < 8; ++p) {
+        g->lists.insert(g->lists.end(), far_pair[p].begin(), far_pair[p].end());
+        g->lists.insert(g->lists.end(), far_single[p].begin(), far_single[p].end());
+    }
+    g->lists.insert(g->lists.end(), near_pair.begin(), near_pair.end());
+    g->lists.insert(g->lists.end(), root_pair.begin(), root_pair.end());
+    g->far_offsets = static_cast<int>(2 * far_pair[0].size() + far_single[0].size());
 
     // --- derivative table ----------------------------------------------------
     std::vector<double> Dt(static_cast<size_t>(NOFF) * DROW, 0.0);
@@ -420,12 +454,15 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         vmap.insert(vmap.end(), ent.begin(), ent.end());
     }
 
-    // --- exact pair counts and per-item costs --------------------------------
-    // lane patterns: for each (parity, half) and list entry, which of the 27
-    // neighbours the warp's 32 cells reach; per neighbour, how many cells.
+    // --- exact pair counts, FLOPs and per-item costs ------------------------
+    // For each (parity, half) warp pattern and list entry: which of the 27
+    // neighbours the warp's 32 cells reach (both sides of a paired entry), and
+    // per neighbour how many (cell, source) pairs land there, split by
+    // paired / single entries.  Segments: 0 far, 1 near, 2 root.
     const int seg_len[3] = {g->far_len, g->near_len, g->root_len};
     std::vector<uint32_t> mask[16][3];
-    long long cnt[3][27];
+    std::vector<uint8_t> pflag[16][3];
+    long long cnt[3][2][27];   // [segment][paired][neighbour]: pairs over all 512 cells
     std::memset(cnt, 0, sizeof(cnt));
     for (int ph = 0; ph < 16; ++ph) {
         const int par = ph >> 1, half = ph & 1;
@@ -433,24 +470,37 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             const int* lst = (sg == 0) ? &g->lists[par * g->far_len]
                            : (sg == 1) ? &g->lists[8 * g->far_len] : &g->lists[8 * g->far_len + g->near_len];
             mask[ph][sg].resize(seg_len[sg]);
+            pflag[ph][sg].resize(seg_len[sg]);
             for (int k = 0; k < seg_len[sg]; ++k) {
                 const int po = lst[k];
+                const int paired = (po >> 24) & 1;
                 const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
                 uint32_t m = 0;
                 for (int lane = 0; lane < 32; ++lane) {
                     const int tx = (par & 1) + 2 * (lane & 3), ty = ((par >> 1) & 1) + 2 * ((lane >> 2) & 3),
                               tz = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
-                    const int nb = ((tx + ox + 8) >> 3) + 3 * ((ty + oy + 8) >> 3) + 9 * ((tz + oz + 8) >> 3);
-                    m |= 1u << nb;
-                    cnt[sg][nb]++;
+                    for (int side = 0; side <= paired; ++side) {
+                        const int sgn = side ? -1 : 1;
+                        const int nb = ((tx + sgn * ox + 8) >> 3) + 3 * ((ty + sgn * oy + 8) >> 3) +
+                                       9 * ((tz + sgn * oz + 8) >> 3);
+                        m |= 1u << nb;
+                        cnt[sg][paired][nb]++;
+                    }
                 }
                 mask[ph][sg][k] = m;
+                pflag[ph][sg][k] = static_cast<uint8_t>(paired);
             }
         }
     }
-    // forward costs (FMAs per lane) and counts
-    long long pairs_multi = 0, pairs_mono = 0, pairs_virt = 0, padded = 0, flops_multi_ang = 0, fma_fwd = 0,
-              fma_adj = 0;
+    // algorithmic FLOPs per in-domain pair (2 per FMA, 1 per add):
+    //   point mass 32, or 17 in a paired entry (16 FMA + 2 adds per two pairs);
+    //   multipole 140 (200 with the angular term), or 86 (116) paired;
+    //   adjoint: point mass 32, multipole 140, or 86 paired.
+    // FP64 instructions per lane and active entry (empty lanes included):
+    //   forward point mass 16 | 18 paired; multipole 70 (+30) | 102 (+30);
+    //   adjoint point mass 16 | 32 paired; multipole 70 | 102 paired.
+    long long pairs_multi = 0, pairs_mono = 0, pairs_virt = 0, pairs_ang = 0, lanes = 0;
+    long long flops_fwd = 0, flops_adj = 0, ops_fwd = 0, ops_adj = 0;
     std::vector<std::pair<long long, int>> fwd[4];
     std::vector<int> node_order_items;
     g->node_item_start.assign(n + 1, 0);
@@ -465,34 +515,41 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         const bool leaf = g->is_leaf[i];
         const int s1 = (desc->level[i] == 0) ? 2 : 0;
         for (int j = 0; j < 27; ++j) {
-            // cnt[sg][j] already sums over all 512 target cells of a sub-grid
-            const long long c1 = cnt[s1][j];
-            const long long cn = leaf ? cnt[1][j] : 0;
-            if (mm >> j & 1u) {
-                pairs_multi += c1 + cn;
-                if (!leaf) flops_multi_ang += c1;
+            long long cp = cnt[s1][1][j], cs = cnt[s1][0][j];
+            if (leaf) {
+                cp += cnt[1][1][j];
+                cs += cnt[1][0][j];
             }
-            if (mo >> j & 1u) pairs_mono += c1 + cn;
-            if (mv >> j & 1u) pairs_virt += c1 + cn;
+            if (mm >> j & 1u) {
+                pairs_multi += cp + cs;
+                if (!leaf) {
+                    pairs_ang += cp + cs;
+                    flops_fwd += 116 * cp + 200 * cs;
+                } else {
+                    flops_fwd += 86 * cp + 140 * cs;
+                }
+            }
+            if (mo >> j & 1u) {
+                pairs_mono += cp + cs;
+                flops_fwd += 17 * cp + 32 * cs;
+            }
+            if (mv >> j & 1u) pairs_virt += cp + cs;
         }
         g->node_item_start[i] = static_cast<int>(node_order_items.size());
         for (int ph = 0; ph < 16; ++ph) {
-            const int par = ph >> 1;
-            long long cost[4] = {0, 0, 0, 0};   // by mode bit: [1] multi, [2] mono
-            long long lanes_m = 0, lanes_o = 0;
-            const int multi_fma = leaf ? 70 : 100;
+            long long cost[3] = {0, 0, 0};   // [1] multipole class, [2] point-mass class
             auto scan = [&](int sg) {
                 const std::vector<uint32_t>& mk = mask[ph][sg];
+                const std::vector<uint8_t>& pf = pflag[ph][sg];
                 for (size_t k = 0; k < mk.size(); ++k) {
-                    if (mk[k] & mm) { cost[1] += multi_fma; lanes_m += 32; }
-                    if (mk[k] & mo) { cost[2] += 16; lanes_o += 32; }
+                    if (mk[k] & mm) cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
+                    if (mk[k] & mo) cost[2] += pf[k] ? 18 : 16;
+                    if (mk[k] & (mm | mo)) lanes += 32;
                 }
             };
-            (void)par;
             scan(s1);
             if (leaf) scan(1);
-            padded += lanes_m + lanes_o;
-            fma_fwd += 32 * (cost[1] + cost[2]);
+            ops_fwd += 32 * (cost[1] + cost[2]);
             const int item = (i << 4) | ph;
             node_order_items.push_back(item);
             for (int mode = 1; mode <= 3; ++mode) {
@@ -507,21 +564,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                          [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
                              return a.first > b.first;
                          });
-    // adjoint items: real sources by class, virtual sources
+    // adjoint items: real sources by class, virtual sources (point masses)
     std::vector<std::pair<long long, int>> adj[4];
-    auto adj_cost = [&](const int2* tbl, int lvl, int per_pair, int ph) {
-        uint32_t tv = 0, tl = 0;
-        for (int j = 0; j < 27; ++j) {
-            const int k = tbl[j].y & 3;
-            if (k == K_MULTI || k == K_LEAF) tv |= 1u << j;
-            if (k == K_LEAF) tl |= 1u << j;
-        }
-        long long cst = 0;
-        const int s1 = (lvl == 0) ? 2 : 0;
-        for (uint32_t m : mask[ph][s1]) if (m & tv) cst += per_pair;
-        for (uint32_t m : mask[ph][1]) if (m & tl) cst += per_pair;
-        return cst;
-    };
     std::vector<int> adj_node[4];
     for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode].assign(n + g->nvirt + 1, 0);
     for (int i = 0; i < n + g->nvirt; ++i) {
@@ -529,12 +573,31 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         const bool leaf = virt || g->is_leaf[i];
         const int2* tbl = virt ? &g->vnbr[static_cast<size_t>(i - n) * 27] : &g->nbr[static_cast<size_t>(i) * 27];
         const int lvl = virt ? g->vinfo[i - n] : desc->level[i];
+        const int s1 = (lvl == 0) ? 2 : 0;
+        uint32_t tv = 0, tl = 0;
+        for (int j = 0; j < 27; ++j) {
+            const int k = tbl[j].y & 3;
+            if (k == K_MULTI || k == K_LEAF) tv |= 1u << j;
+            if (k == K_LEAF) tl |= 1u << j;
+        }
+        for (int j = 0; j < 27; ++j) {
+            long long cp = (tv >> j & 1u) ? cnt[s1][1][j] : 0, cs = (tv >> j & 1u) ? cnt[s1][0][j] : 0;
+            if (tl >> j & 1u) {
+                cp += cnt[1][1][j];
+                cs += cnt[1][0][j];
+            }
+            flops_adj += leaf ? 32 * (cp + cs) : 86 * cp + 140 * cs;
+        }
         const int bit = leaf ? 2 : 1;
         for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode][i] = static_cast<int>(adj_node[mode].size());
         for (int ph = 0; ph < 16; ++ph) {
-            const long long cst = adj_cost(tbl, lvl, leaf ? 16 : 70, ph);
+            long long cst = 0;
+            for (size_t k = 0; k < mask[ph][s1].size(); ++k)
+                if (mask[ph][s1][k] & tv) cst += leaf ? (pflag[ph][s1][k] ? 32 : 16) : (pflag[ph][s1][k] ? 102 : 70);
+            for (size_t k = 0; k < mask[ph][1].size(); ++k)
+                if (mask[ph][1][k] & tl) cst += leaf ? 32 : 102;
             if (cst == 0) continue;
-            fma_adj += 32 * cst;
+            ops_adj += 32 * cst;
             const int item = (i << 4) | ph;
             for (int mode = 1; mode <= 3; ++mode)
                 if (mode & bit) {
@@ -585,16 +648,18 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.n_subgrids = n;
     I.n_virtual = g->nvirt;
     I.max_level = g->max_level;
-    I.far_offsets = g->far_len;
-    I.near_offsets = g->near_len;
-    I.root_offsets = g->root_len;
+    I.far_offsets = g->far_offsets;
+    I.near_offsets = 2 * g->near_len;
+    I.root_offsets = 2 * g->root_len;
     I.pairs_multipole = pairs_multi;
     I.pairs_monopole = pairs_mono;
     I.pairs_virtual = pairs_virt;
-    I.pairs_angular = flops_multi_ang;
-    I.lanes_fwd = padded;
-    I.fma_fwd = fma_fwd;
-    I.fma_adj = fma_adj;
+    I.pairs_angular = pairs_ang;
+    I.lanes_fwd = lanes;
+    I.flops_fwd = flops_fwd;
+    I.flops_adj = flops_adj;
+    I.ops_fwd = ops_fwd;
+    I.ops_adj = ops_adj;
     for (int mode = 1; mode <= 3; ++mode)
         for (int w = 2; w <= 8; w *= 2) {
             g->maxb_fwd[mode][w] = forward_max_blocks_per_sm(mode, w);
@@ -668,6 +733,7 @@ static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, 
     p.Dt = g->d_Dt;
     p.L.lists = g->d_lists;
     p.L.far_len = g->far_len;
+    p.L.far_pairs = g->far_pairs;
     p.L.near_len = g->near_len;
     p.L.root_len = g->root_len;
     p.L.near_off = 8 * g->far_len;
@@ -746,6 +812,7 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     p.Dt = g->d_Dt;
     p.L.lists = g->d_lists;
     p.L.far_len = g->far_len;
+    p.L.far_pairs = g->far_pairs;
     p.L.near_len = g->near_len;
     p.L.root_len = g->root_len;
     p.L.near_off = 8 * g->far_len;
