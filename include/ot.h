@@ -166,6 +166,20 @@ ot_status ot_interactions(ot_grid* grid, const double* M, const double* m,
 ot_status ot_interactions_backward(ot_grid* grid, const double* Lbar, double* Mbar,
                                    double* mbar, void* stream);
 
+/* Local-expansion down-pass (L2L) completing the multilevel solve, in place
+ * on L [n][20][512]: level by level from the root, every cell of a sub-grid
+ * whose parent is present adds its parent cell's expansion shifted to its own
+ * centre (degree-3 Taylor shift, d = +-h/2 per axis):
+ *   L_child[J] += sum_{|J|+|I| <= 3} L_parent[J+I] d^I / I!.
+ * After moments, both passes and this call, L[:,0] of a leaf cell is the
+ * potential at its centre (without the cell's self-potential) and -L[:,1:4]
+ * the gravitational field. */
+ot_status ot_l2l(ot_grid* grid, double* L, void* stream);
+
+/* Adjoint of ot_l2l, in place on Lbar [n][20][512]: from the deepest level
+ * up, every parent cell adds the transposed shifts of its children's Lbar. */
+ot_status ot_l2l_backward(ot_grid* grid, double* Lbar, void* stream);
+
 /* Schedule and tile shape of later calls (forward and adjoint; the plain
  * schedule launches once per target sub-grid forward and once per source
  * sub-grid in the adjoint).  warps_per_block in {2,4,8},

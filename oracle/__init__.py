@@ -64,7 +64,7 @@ def _load():
     lib.oracle_pass_adjoint_targets.restype = ctypes.c_longlong
     lib.oracle_l2l.argtypes = [P, P, P]
     lib.oracle_l2l.restype = None
-    lib.oracle_full_solve.argtypes = [I, P, P, P, ctypes.c_double, P, P]
+    lib.oracle_full_solve.argtypes = [I, P, P, P, ctypes.c_double, P, P, P]
     lib.oracle_full_solve.restype = I
     lib.oracle_set_threads.argtypes = [I]
     lib.oracle_set_threads.restype = None
@@ -194,10 +194,12 @@ def l2l(Lp, d) -> np.ndarray:
     return out
 
 
-def full_solve(tree, rho) -> np.ndarray:
-    """[n, 20, 512] total local expansion of every cell (potential = [:, 0])."""
+def full_solve(tree, rho, with_s: bool = False):
+    """[n, 20, 512] total local expansion of every cell (potential = [:, 0]);
+    with ``with_s`` also the matching sums of |terms|."""
     level, coord, leaf = _tree_args(tree)
     rho = np.ascontiguousarray(rho, dtype=np.float64)
     L = np.zeros((tree.n, NCOMP, NCELL))
-    _load().oracle_full_solve(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(rho), _p(L))
-    return L
+    S = np.zeros((tree.n, NCOMP, NCELL)) if with_s else None
+    _load().oracle_full_solve(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(rho), _p(L), _p(S))
+    return (L, S) if with_s else L

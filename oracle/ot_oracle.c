@@ -541,9 +541,11 @@ void oracle_l2l(const double* Lp, const double* d, double* Lc) {
 
 /* Full solve: moments (leaf cubes + M2M), both passes at every level, L2L from
  * each parent cell down to its children, level by level from the root.
- * Ltot [n][20][512] receives the total local expansion of every cell. */
+ * Ltot [n][20][512] receives the total local expansion of every cell; Stot
+ * (same shape, may be NULL) the sum of |terms| behind each coefficient: the
+ * passes' sums, carried down by the same shift with |d|. */
 int oracle_full_solve(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
-                      const double* rho, double* Ltot) {
+                      const double* rho, double* Ltot, double* Stot) {
     otree t;
     tree_init(&t, n, level, coord, is_leaf, h0);
     size_t nn = (size_t)n * NCOMP * NCELL;
@@ -552,16 +554,21 @@ int oracle_full_solve(int n, const int* level, const int* coord, const uint8_t* 
     double* L1 = (double*)malloc(sizeof(double) * (size_t)n * NCELL * NCOMP);
     double* L2 = (double*)malloc(sizeof(double) * (size_t)n * NCELL * NCOMP);
     double* S = (double*)malloc(sizeof(double) * (size_t)n * NCELL * NCOMP);
+    double* S2 = (double*)malloc(sizeof(double) * (size_t)n * NCELL * NCOMP);
     oracle_moments(n, level, coord, is_leaf, h0, rho, M);
     for (int i = 0; i < n; i++)
         for (int a = 0; a < NCELL; a++) m[(size_t)i * NCELL + a] = M[((size_t)i * NCOMP) * NCELL + a];
     oracle_pass(n, level, coord, is_leaf, h0, M, m, 1, 0, NULL, L1, NULL, S, NULL);
-    oracle_pass(n, level, coord, is_leaf, h0, M, m, 2, 0, NULL, L2, NULL, S, NULL);
+    oracle_pass(n, level, coord, is_leaf, h0, M, m, 2, 0, NULL, L2, NULL, S2, NULL);
     for (int i = 0; i < n; i++)
         for (int a = 0; a < NCELL; a++)
-            for (int c = 0; c < NCOMP; c++)
+            for (int c = 0; c < NCOMP; c++) {
                 Ltot[((size_t)i * NCOMP + c) * NCELL + a] =
                     L1[((size_t)i * NCELL + a) * NCOMP + c] + L2[((size_t)i * NCELL + a) * NCOMP + c];
+                if (Stot)
+                    Stot[((size_t)i * NCOMP + c) * NCELL + a] =
+                        S[((size_t)i * NCELL + a) * NCOMP + c] + S2[((size_t)i * NCELL + a) * NCOMP + c];
+            }
     for (int l = 1; l <= t.max_level; l++) {
         double h = h0 / pow(2.0, l);
         for (int i = 0; i < n; i++) {
@@ -579,10 +586,16 @@ int oracle_full_solve(int n, const int* level, const int* coord, const uint8_t* 
                 for (int ax = 0; ax < 3; ax++) d[ax] = ((g[ax] & 1) - 0.5) * h;
                 oracle_l2l(Lp, d, Lc);
                 for (int c = 0; c < NCOMP; c++) Ltot[((size_t)i * NCOMP + c) * NCELL + a] += Lc[c];
+                if (Stot) {
+                    double Sp[NCOMP], Sc[NCOMP], ad[3] = {fabs(d[0]), fabs(d[1]), fabs(d[2])};
+                    for (int c = 0; c < NCOMP; c++) Sp[c] = Stot[((size_t)P * NCOMP + c) * NCELL + cp];
+                    oracle_l2l(Sp, ad, Sc);
+                    for (int c = 0; c < NCOMP; c++) Stot[((size_t)i * NCOMP + c) * NCELL + a] += Sc[c];
+                }
             }
         }
     }
-    free(M); free(m); free(L1); free(L2); free(S);
+    free(M); free(m); free(L1); free(L2); free(S); free(S2);
     tree_free(&t);
     return 0;
 }

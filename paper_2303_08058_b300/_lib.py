@@ -20,7 +20,8 @@ OT_SCHED_PERSISTENT, OT_SCHED_PER_SUBGRID = 0, 1
 EXPORTS = ["ot_grid_create", "ot_grid_destroy", "ot_grid_info", "ot_moments", "ot_moments_backward",
            "ot_multipole_interactions", "ot_monopole_interactions", "ot_interactions",
            "ot_interactions_backward", "ot_set_schedule", "ot_autotune", "ot_grid_check",
-           "ot_fp64_fma_probe", "ot_multipole_interactions_noalloc", "ot_last_error"]
+           "ot_fp64_fma_probe", "ot_multipole_interactions_noalloc", "ot_l2l", "ot_l2l_backward",
+           "ot_last_error"]
 
 
 class OTError(RuntimeError):
@@ -76,6 +77,8 @@ def load():
         "ot_grid_check": [P, P],
         "ot_fp64_fma_probe": [P, I, I, I, P],
         "ot_multipole_interactions_noalloc": [P, P, P, P, P],
+        "ot_l2l": [P, P, P],
+        "ot_l2l_backward": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -101,6 +101,10 @@ cudaError_t launch_m2m_adjoint(double* Mb, const int* parents, int n_list, const
                                const int* ninfo, const double* hinv, cudaStream_t s);
 cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nodes, int n_list,
                                 const int* ninfo, const double* hinv, cudaStream_t s);
+cudaError_t launch_l2l(double* L, const int* parents, int n_list, const int* children, const int* ninfo,
+                       const double* hinv, cudaStream_t s);
+cudaError_t launch_l2l_adjoint(double* Lb, const int* parents, int n_list, const int* children,
+                               const int* ninfo, const double* hinv, cudaStream_t s);
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, int variant, cudaStream_t s);
 int forward_max_blocks_per_sm(int mode, int wpb);
 int adjoint_max_blocks_per_sm(int mode, int wpb);

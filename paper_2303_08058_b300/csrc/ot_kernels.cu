@@ -636,6 +636,122 @@ __device__ __forceinline__ void shift1_t(Dense4& D, double d) {
         }
 }
 
+// One-dimensional Taylor shift of a degree-3 local expansion (coefficients
+// are derivatives): out[..a..] = sum_{k <= 3 - |rest| - a} in[..a+k..] d^k / k!
+template <int AXIS>
+__device__ __forceinline__ void lshift1(Dense4& D, double d) {
+    const double d2h = 0.5 * d * d, d3s = d * d * d / 6.0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; p + q < 4; ++q) {
+            double m[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a)
+                m[a] = (AXIS == 0) ? D.v[a][p][q] : (AXIS == 1) ? D.v[p][a][q] : D.v[p][q][a];
+            const int top = 3 - p - q;
+            double o[4];
+            o[0] = m[0] + (top >= 1 ? d * m[1] : 0.0) + (top >= 2 ? d2h * m[2] : 0.0) + (top >= 3 ? d3s * m[3] : 0.0);
+            o[1] = m[1] + (top >= 2 ? d * m[2] : 0.0) + (top >= 3 ? d2h * m[3] : 0.0);
+            o[2] = m[2] + (top >= 3 ? d * m[3] : 0.0);
+            o[3] = m[3];
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a) {
+                if (AXIS == 0) D.v[a][p][q] = o[a];
+                else if (AXIS == 1) D.v[p][a][q] = o[a];
+                else D.v[p][q][a] = o[a];
+            }
+        }
+}
+
+// transpose of lshift1
+template <int AXIS>
+__device__ __forceinline__ void lshift1_t(Dense4& D, double d) {
+    const double d2h = 0.5 * d * d, d3s = d * d * d / 6.0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; p + q < 4; ++q) {
+            double g[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a)
+                g[a] = (AXIS == 0) ? D.v[a][p][q] : (AXIS == 1) ? D.v[p][a][q] : D.v[p][q][a];
+            const int top = 3 - p - q;
+            double o[4];
+            o[0] = g[0];
+            o[1] = (top >= 1) ? g[1] + d * g[0] : 0.0;
+            o[2] = (top >= 2) ? g[2] + d * g[1] + d2h * g[0] : 0.0;
+            o[3] = (top >= 3) ? g[3] + d * g[2] + d2h * g[1] + d3s * g[0] : 0.0;
+#pragma unroll
+            for (int a = 0; a + p + q < 4; ++a) {
+                if (AXIS == 0) D.v[a][p][q] = o[a];
+                else if (AXIS == 1) D.v[p][a][q] = o[a];
+                else D.v[p][q][a] = o[a];
+            }
+        }
+}
+
+// L2L down-pass of one level: every child cell of the listed parents adds
+// the parent cell's local expansion shifted to its own centre
+__global__ void l2l_kernel(double* __restrict__ L, const int* __restrict__ parents, int n_list,
+                           const int* __restrict__ children, const int* __restrict__ ninfo,
+                           const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * 8 * NCELL) return;
+    const int k = t / (8 * NCELL);
+    const int oct = (t / NCELL) % 8, ccell = t % NCELL;
+    const int P = parents[k];
+    const int C = children[8 * k + oct];
+    const int cx = (oct & 1) * 8 + (ccell & 7), cy = ((oct >> 1) & 1) * 8 + ((ccell >> 3) & 7),
+              cz = (oct >> 2) * 8 + (ccell >> 6);
+    const int pcell = (cx >> 1) + 8 * (cy >> 1) + 64 * (cz >> 1);
+    const double hc = 0.5 / hinv[ninfo[P] & 0xff];
+    Dense4 v;
+    to_dense(L + static_cast<size_t>(P) * NCOMP * NCELL + pcell, v);
+    lshift1<0>(v, ((cx & 1) - 0.5) * hc);
+    lshift1<1>(v, ((cy & 1) - 0.5) * hc);
+    lshift1<2>(v, ((cz & 1) - 0.5) * hc);
+    from_dense(v, L + static_cast<size_t>(C) * NCOMP * NCELL + ccell, true);
+}
+
+// transpose of one level of the down-pass: every parent cell adds the
+// transposed shifts of its 8 child cells' adjoints
+__global__ void l2l_adjoint_kernel(double* __restrict__ Lb, const int* __restrict__ parents, int n_list,
+                                   const int* __restrict__ children, const int* __restrict__ ninfo,
+                                   const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * NCELL) return;
+    const int k = t / NCELL, cell = t % NCELL;
+    const int P = parents[k];
+    const int gx = cell & 7, gy = (cell >> 3) & 7, gz = cell >> 6;
+    const double hc = 0.5 / hinv[ninfo[P] & 0xff];
+    Dense4 acc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc.v[a][b][c] = 0.0;
+#pragma unroll 1
+    for (int b = 0; b < 8; ++b) {
+        const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+        const int cx = 2 * gx + bx, cy = 2 * gy + by, cz = 2 * gz + bz;
+        const int C = children[8 * k + (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
+        Dense4 v;
+        to_dense(Lb + static_cast<size_t>(C) * NCOMP * NCELL + (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7), v);
+        lshift1_t<2>(v, (bz - 0.5) * hc);
+        lshift1_t<1>(v, (by - 0.5) * hc);
+        lshift1_t<0>(v, (bx - 0.5) * hc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bb = 0; a + bb < 4; ++bb)
+#pragma unroll
+                for (int c = 0; a + bb + c < 4; ++c) acc.v[a][bb][c] += v.v[a][bb][c];
+    }
+    from_dense(acc, Lb + static_cast<size_t>(P) * NCOMP * NCELL + cell, true);
+}
+
 __global__ void cube_moments_kernel(const double* __restrict__ rho, double* __restrict__ M, double* __restrict__ m,
                                     const int* __restrict__ nodes, int n_list, const int* __restrict__ ninfo,
                                     const double* __restrict__ hinv) {
@@ -863,6 +979,21 @@ cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nod
                                 const double* hinv, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
     cube_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(Mb, rhobar, nodes, n_list, ninfo, hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2l(double* L, const int* parents, int n_list, const int* children, const int* ninfo,
+                       const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    l2l_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(L, parents, n_list, children, ninfo, hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2l_adjoint(double* Lb, const int* parents, int n_list, const int* children, const int* ninfo,
+                               const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    l2l_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(Lb, parents, n_list, children, ninfo,
+                                                                             hinv);
     return cudaGetLastError();
 }
 

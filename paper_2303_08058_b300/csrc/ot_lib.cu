@@ -1058,6 +1058,31 @@ ot_status ot_moments_backward(ot_grid* g, const double* Mbar, const double* mbar
     GUARD_END
 }
 
+ot_status ot_l2l(ot_grid* g, double* L, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(L, "L");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // m2m holds the parents deepest level first: walk it from the root down
+    for (auto it = g->m2m.rbegin(); it != g->m2m.rend(); ++it)
+        OT_CUDA(launch_l2l(L, it->d_parents, static_cast<int>(it->parents.size()), it->d_children, g->d_ninfo,
+                           g->d_hinv, s));
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_l2l_backward(ot_grid* g, double* Lbar, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(Lbar, "Lbar");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (auto& L : g->m2m)
+        OT_CUDA(launch_l2l_adjoint(Lbar, L.d_parents, static_cast<int>(L.parents.size()), L.d_children, g->d_ninfo,
+                                   g->d_hinv, s));
+    return OT_OK;
+    GUARD_END
+}
+
 ot_status ot_multipole_interactions(ot_grid* g, const double* M, const double* centres, double* L, double* Lc,
                                     void* stream) {
     GUARD_BEGIN

@@ -120,6 +120,21 @@ class OTGrid:
         _lib.check(self.lib.ot_interactions(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), _stream(stream)))
         return L, Lc
 
+    def l2l(self, L, stream=None):
+        """In-place down-pass: adds every parent's shifted expansion (ot_l2l)."""
+        return _l2l(self, L, stream)
+
+    def l2l_backward(self, Lbar, stream=None):
+        return _l2l_backward(self, Lbar, stream)
+
+    def solve(self, rho, stream=None):
+        """Full multilevel solve: moments, both passes, L2L.  Returns L (leaf
+        L[:,0] is the potential) and Lc."""
+        M, m = self.moments(rho, stream=stream)
+        L, Lc = self.interactions(M, m, stream=stream)
+        self.l2l(L, stream=stream)
+        return L, Lc
+
     def backward(self, Lbar, Mbar=None, mbar=None, want=(True, True), stream=None):
         if Mbar is None and want[0]:
             Mbar = self.zeros(self.n, NCOMP, NCELL)
@@ -130,33 +145,50 @@ class OTGrid:
         return Mbar, mbar
 
 
+def _l2l(grid, L, stream=None):
+    _lib.check(grid.lib.ot_l2l(grid.handle, _ptr(L), _stream(stream)))
+    return L
+
+
+def _l2l_backward(grid, Lbar, stream=None):
+    _lib.check(grid.lib.ot_l2l_backward(grid.handle, _ptr(Lbar), _stream(stream)))
+    return Lbar
+
+
 def fp64_fma_probe(out, blocks, iters, variant=0, stream=None):
     lib = _lib.load()
     _lib.check(lib.ot_fp64_fma_probe(_ptr(out), int(blocks), int(iters), int(variant), _stream(stream)))
 
 
 class FMMInteractions(torch.autograd.Function):
-    """rho [n, 512] -> L [n, 20, 512] (both passes, moments included).
+    """rho [n, 512] -> L [n, 20, 512]: moments and both passes, and with
+    ``full`` the L2L down-pass (the complete multilevel solve).
 
-    The backward runs the transposed stencil kernels and the adjoint of the
-    moment computation; nothing from the forward pass is stored (the maps are
+    The backward runs the adjoint kernels (L2L transposed, transposed stencil,
+    moments transposed); nothing from the forward pass is stored (every map is
     linear in rho, so the adjoint needs only the grid)."""
 
     @staticmethod
-    def forward(ctx, grid: OTGrid, rho):
+    def forward(ctx, grid: OTGrid, rho, full: bool = False):
         M, m = grid.moments(rho.contiguous())
         L, _ = grid.interactions(M, m, want_lc=False)
-        ctx.grid = grid
+        if full:
+            grid.l2l(L)
+        ctx.grid, ctx.full = grid, full
         return L
 
     @staticmethod
     def backward(ctx, Lbar):
         grid = ctx.grid
-        Mbar, mbar = grid.backward(Lbar.contiguous())
+        Lbar = Lbar.contiguous().clone() if ctx.full else Lbar.contiguous()
+        if ctx.full:
+            grid.l2l_backward(Lbar)
+        Mbar, mbar = grid.backward(Lbar)
         rhobar = grid.moments_backward(Mbar, mbar)
-        return None, rhobar
+        return None, rhobar, None
 
 
-def potential_and_gradient(grid: OTGrid, rho):
-    """Differentiable L (potential, gradient, ...) of every cell from rho."""
-    return FMMInteractions.apply(grid, rho)
+def potential_and_gradient(grid: OTGrid, rho, full: bool = False):
+    """Differentiable L (potential, gradient, ...) of every cell from rho;
+    ``full`` adds the L2L down-pass (the whole multilevel solve)."""
+    return FMMInteractions.apply(grid, rho, full)
