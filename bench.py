@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default=None, help="WxB: warps per block x blocks per SM (skips the autotuner)")
+    ap.add_argument("--workload", choices=["polytrope64", "adaptive", "binary"], default="polytrope64",
+                    help="polytrope64: the headline workload; adaptive: 4,641-sub-grid octree (levels 3-6); "
+                         "binary: rotating binary star, levels 3-7, a new octree every step")
     return ap.parse_args()
 
 
@@ -145,16 +148,29 @@ class ClockSampler:
 # the workload
 # ---------------------------------------------------------------------------
 
-def make_workload():
+WORKLOADS = {
+    "polytrope64": WORKLOAD,
+    "adaptive": ("adaptive octree, levels 3-6 (4,641 sub-grids, 4,061 leaves), n=1 polytrope with seeded centre, "
+                 "refined where rho > 1e-3 rho_c, 2:1 balanced; both passes in one batched launch, then the adjoint"),
+    "binary": ("rotating binary star: two n=1 polytropes (q=0.5, R=24 and 19, 60 apart), levels 3-7 "
+               "(~9,500 sub-grids, ~8,300 leaves, 4.25M leaf cells), rotated 0.01 rad per step, octree rebuilt "
+               "each step; both passes + adjoint per step"),
+}
+
+
+def make_workload(name="polytrope64", step=0):
     import synth
-    tree, rho = synth.config2()
-    rng = np.random.default_rng(4)
-    probes = synth.config4_probes()
-    # L-bar of the differentiation workload: dloss/dL0 at 1000 probe cells
-    # plus a seeded N(0,1) L-bar on all 20 components of every cell (so every
-    # adjoint lane does full work)
+    if name == "adaptive":
+        tree, rho, _ = synth.config3()
+    elif name == "binary":
+        tree, rho = synth.config5_step(step)
+    else:
+        tree, rho = synth.config2()
+    # a seeded N(0,1) L-bar on all 20 components of every cell, so every
+    # adjoint lane does full work
+    rng = np.random.default_rng(4 + step)
     Lbar = rng.standard_normal((tree.n, 20, 512))
-    return tree, rho, Lbar, probes
+    return tree, rho, Lbar, None
 
 
 def fwd_flops(info):
@@ -208,7 +224,9 @@ def run_ours(args, rank, world):
     import paper_2303_08058_b300 as ot
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    tree, rho_h, Lbar_h, _ = make_workload()
+    if args.workload == "binary":
+        return run_binary(args, rank, world)
+    tree, rho_h, Lbar_h, _ = make_workload(args.workload)
     g = ot.OTGrid.from_tree(tree)
     sched = ot.OT_SCHED_PER_SUBGRID if args.schedule == "per_subgrid" else ot.OT_SCHED_PERSISTENT
     g.set_schedule(sched, 4, 0, not args.no_graph)
@@ -310,7 +328,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded polytrope densities, seeded L-bar)",
-        "config": {"workload": WORKLOAD, "subgrids": tree.n, "cells": tree.n * 512,
+        "config": {"workload": WORKLOADS[args.workload], "subgrids": tree.n, "cells": tree.n * 512,
                    "pairs_fwd": pairs_fwd, "pairs_adj": pairs_fwd,
                    "pairs_multipole": info["pairs_multipole"], "pairs_monopole": info["pairs_monopole"],
                    "schedule": args.schedule, "graph": not args.no_graph,
@@ -336,6 +354,61 @@ def run_ours(args, rank, world):
         "wall_s": wall,
     }
     return res, tree, rho_h
+
+
+def run_binary(args, rank, world):
+    """Rotating binary star: each of `--steps` rotation steps builds its
+    octree (host, untimed), then runs the path (moments, both passes,
+    adjoint, moment adjoint) timed with events on the stream."""
+    import torch
+    import paper_2303_08058_b300 as ot
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    step_ms, pairs, setup_s, tile = [], 0, 0.0, None
+    sched = ot.OT_SCHED_PER_SUBGRID if args.schedule == "per_subgrid" else ot.OT_SCHED_PERSISTENT
+    clocks.start()
+    for k in range(-1, args.steps):        # step -1: warm-up (step 0 untimed)
+        t0 = time.perf_counter()
+        tree, rho_h, Lbar_h, _ = make_workload("binary", max(k, 0))
+        g = ot.OTGrid.from_tree(tree)
+        rho = torch.as_tensor(rho_h, device="cuda")
+        Lbar = torch.as_tensor(Lbar_h, device="cuda")
+        M, m = g.moments(rho)
+        L, Lc = g.zeros(tree.n, 20, 512), g.zeros(tree.n, 3, 512)
+        if tile is None and sched == ot.OT_SCHED_PERSISTENT and not args.tile:
+            tuned = g.autotune(M, m, L, Lc)
+            tile = (tuned["warps_per_block"], tuned["blocks_per_sm"])
+        elif args.tile:
+            tile = tuple(int(x) for x in args.tile.lower().split("x"))
+        g.set_schedule(sched, *(tile or (4, 0)), not args.no_graph)
+        Mb, mb, rb = g.zeros(tree.n, 20, 512), g.zeros(tree.n, 512), g.zeros(tree.n, 512)
+        g.interactions(M, m, L, Lc)          # records the graph (untimed)
+        g.backward(Lbar, Mb, mb)
+        torch.cuda.synchronize()
+        setup_s += time.perf_counter() - t0
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.moments(rho, M, m)
+        g.interactions(M, m, L, Lc)
+        g.backward(Lbar, Mb, mb)
+        g.moments_backward(Mb, mb, rb)
+        b.record(stream)
+        torch.cuda.synchronize()
+        g.check()
+        if k >= 0:
+            step_ms.append(a.elapsed_time(b))
+            info = g.info()
+            pairs += 2 * (info["pairs_multipole"] + info["pairs_monopole"])
+        g.close()
+    clk = clocks.stop()
+    value, ms_per_step = aggregate(world, args.steps, pairs / max(args.steps, 1), sum(step_ms) / 1e3)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": 1,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (analytic binary-star densities, seeded L-bar)",
+            "config": {"workload": WORKLOADS["binary"], "schedule": args.schedule, "graph": not args.no_graph,
+                       "tile": tile, "pairs_per_step": pairs / max(args.steps, 1),
+                       "host_setup_s_per_step": setup_s / (args.steps + 1)},
+            "step_ms": step_ms, "clocks": clk}, None, None
 
 
 def cpu_baseline(tree, rho_h, seconds, seed=7):
@@ -415,7 +488,7 @@ def main():
     rank, world = dist_init(args)
     res, tree, rho_h = run_ours(args, rank, world)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and tree is not None:
             res["cpu_baseline"] = cpu_baseline(tree, rho_h, args.cpu_seconds)
         print(json.dumps(res))
     if world > 1:
