@@ -161,8 +161,12 @@ ot_status ot_interactions(ot_grid* grid, const double* M, const double* m,
  *   Mbar = (d L / d M)^T Lbar  for the multipole pass  [n][20][512] overwritten,
  *   mbar = (d L / d m)^T Lbar  for the monopole pass   [n][512]     overwritten,
  * with virtual descendants' gradients restricted onto their coarse leaf.
- * Runs the transposed stencil (a gather over sources); stores nothing from
- * the forward pass.  Mbar / mbar may be NULL to skip that half. */
+ * Mbar comes from the transposed stencil (a gather over sources).  mbar comes
+ * by default from the target-ordered walk with atomic adds into mbar (fewer
+ * FP64 operations; summation order, hence the last bits, vary from run to
+ * run); after ot_set_deterministic(grid, 1) it also comes from the gather
+ * (fixed order, bit-reproducible).  Stores nothing from the forward pass.
+ * Mbar / mbar may be NULL to skip that half. */
 ot_status ot_interactions_backward(ot_grid* grid, const double* Lbar, double* Mbar,
                                    double* mbar, void* stream);
 
@@ -179,6 +183,10 @@ ot_status ot_l2l(ot_grid* grid, double* L, void* stream);
 /* Adjoint of ot_l2l, in place on Lbar [n][20][512]: from the deepest level
  * up, every parent cell adds the transposed shifts of its children's Lbar. */
 ot_status ot_l2l_backward(ot_grid* grid, double* Lbar, void* stream);
+
+/* 1: every adjoint result in a fixed summation order (bit-reproducible);
+ * 0 (default): the point-mass adjoint uses atomic adds (faster). */
+ot_status ot_set_deterministic(ot_grid* grid, int32_t on);
 
 /* Schedule and tile shape of later calls (forward and adjoint; the plain
  * schedule launches once per target sub-grid forward and once per source

@@ -21,6 +21,7 @@ EXPORTS = ["ot_grid_create", "ot_grid_destroy", "ot_grid_info", "ot_moments", "o
            "ot_multipole_interactions", "ot_monopole_interactions", "ot_interactions",
            "ot_interactions_backward", "ot_set_schedule", "ot_autotune", "ot_grid_check",
            "ot_fp64_fma_probe", "ot_multipole_interactions_noalloc", "ot_l2l", "ot_l2l_backward",
+           "ot_set_deterministic",
            "ot_last_error"]
 
 
@@ -79,6 +80,7 @@ def load():
         "ot_multipole_interactions_noalloc": [P, P, P, P, P],
         "ot_l2l": [P, P, P],
         "ot_l2l_backward": [P, P, P],
+        "ot_set_deterministic": [P, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

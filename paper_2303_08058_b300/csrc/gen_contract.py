@@ -166,6 +166,22 @@ def emit():
     for j in range(16):
         w(f"  g[{j % 4}] = fma(lb[{j}], d[{j}], g[{j % 4}]);\n")
     w("}\n\n")
+    # point-mass adjoint organised by target: even- and odd-order parts of
+    # <lb, d>; the source at t+o receives e+q, the one at t-o receives e-q
+    w("// 16 FP64 ops: e = even-order part, q = odd-order part of <lb, d>\n")
+    w("__device__ __forceinline__ void ot_mono_adj_split(double& e, double& q, const double (&lb)[16],\n"
+      "                                                  const double (&d)[36]) {\n")
+    first = {0: True, 1: True}
+    for j in range(16):
+        par = rank(IND16[j]) % 2
+        v = "e" if par == 0 else "q"
+        if first[par]:
+            w(f"  {v} = lb[{j}] * d[{j}];\n")
+            first[par] = False
+        else:
+            w(f"  {v} = fma(lb[{j}], d[{j}], {v});\n")
+    w("}\n\n")
+
     # the same with the row of -o: odd-order derivatives negated
     w("// 16 FMAs (derivatives of the negated offset)\n")
     w("__device__ __forceinline__ void ot_mono_adj_neg(double (&g)[4], const double (&lb)[16], const double (&d)[36]) {\n")

@@ -73,6 +73,22 @@ struct AdjParams {
     double hinv[MAXLEV];
 };
 
+// point-mass adjoint organised by target cells (the forward's walk) with the
+// contributions scattered into mbar by atomic adds
+struct ScatParams {
+    const int* items;      // forward work items (node << 4 | parity << 1 | half)
+    int n_items;
+    int* counter;
+    const int2* nbr;
+    const int* ninfo;
+    const double* Dt;
+    Lists L;
+    const double* Lrbar;   // [n][16][512]
+    double* mbar;          // [n][512], zeroed before the launch
+    int n_nodes;
+    int* status;
+};
+
 struct PrepParams {
     const double* src;     // M [n][20][512] (forward) or Lbar (adjoint)
     double* dst;           // [n][16][512]
@@ -106,6 +122,8 @@ cudaError_t launch_l2l(double* L, const int* parents, int n_list, const int* chi
 cudaError_t launch_l2l_adjoint(double* Lb, const int* parents, int n_list, const int* children,
                                const int* ninfo, const double* hinv, cudaStream_t s);
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, int variant, cudaStream_t s);
+cudaError_t launch_scatter_adjoint(const ScatParams& p, bool persistent, int wpb, int grid, cudaStream_t s);
+int scatter_max_blocks_per_sm(int wpb);
 int forward_max_blocks_per_sm(int mode, int wpb);
 int adjoint_max_blocks_per_sm(int mode, int wpb);
 

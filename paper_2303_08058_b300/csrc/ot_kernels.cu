@@ -364,6 +364,10 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
     }
 }
 
+template <class P>
+__device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
+                             int node, int par, int half, int lane, int it);
+
 template <int MODE>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
@@ -379,6 +383,13 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
         }
         if (it >= p.n_items) break;
         const int item = __ldg(p.items + it);
+        if ((MODE & 4) && ((item >> 30) & 1)) {       // point-mass adjoint by target (atomic adds)
+            const int tgt = item & 0x3fffffff;
+            scatter_item(p, p.nbr, p.ninfo, s_nb[warp], tgt >> 4, (tgt >> 1) & 7, tgt & 1, lane, it);
+            __syncwarp();
+            if (!persistent) break;
+            continue;
+        }
         const int src = item >> 4, par = (item >> 1) & 7, half = item & 1;
         const bool virt = src >= p.n_nodes;
         const int2* nbt = virt ? p.vnbr + static_cast<size_t>(src - p.n_nodes) * 27
@@ -456,6 +467,113 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
             if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = v;
             else p.mbar[static_cast<size_t>(src) * NCELL + scell] = v;
         }
+        __syncwarp();
+        if (!persistent) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// point-mass adjoint by target: mbar[B] += <Lrbar(A), d G(X_A - X_B)>
+// ---------------------------------------------------------------------------
+
+template <class P>
+__device__ __forceinline__ void scatter_mass(const P& p, int2 e, int kind, int sx, int sy, int sz, double v) {
+    if (kind == K_LEAF) {
+        atomicAdd(p.mbar + static_cast<size_t>(e.x) * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7), v);
+    } else if (kind == K_VIRT) {
+        const unsigned meta = static_cast<unsigned>(e.y);
+        const int d = (meta >> 2) & 7;
+        const int vx = static_cast<int>(((meta >> 8) & 0xffu) + (sx & 7)) >> d;
+        const int vy = static_cast<int>(((meta >> 16) & 0xffu) + (sy & 7)) >> d;
+        const int vz = static_cast<int>((meta >> 24) + (sz & 7)) >> d;
+        atomicAdd(p.mbar + static_cast<size_t>(e.x) * NCELL + vx + 8 * vy + 64 * vz, v * pow2i(-3 * d));
+    }
+}
+
+// A paired entry o: with e, q the even- and odd-order parts of <lb, row(o)>,
+// the source at t+o (pair offset R = -o) receives e + q and the source at
+// t-o (R = +o, odd orders change sign) receives e - q.
+template <bool PAIRED, class P>
+__device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                             const int2* __restrict__ s_nb, const P& p,
+                                             const double (&lb)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        const int px = tx + ox, py = ty + oy, pz = tz + oz;
+        const int mx = tx - ox, my = ty - oy, mz = tz - oz;
+        const int2 ep = s_nb[nb_index(px, py, pz)];
+        int kp = ep.y & 3;
+        if (kp != K_NONE && static_cast<unsigned>(ep.x) >= static_cast<unsigned>(p.n_nodes)) {
+            report(p.status, 3, item);
+            kp = K_NONE;
+        }
+        int2 em = make_int2(-1, 0);
+        int km = K_NONE;
+        if (PAIRED) {
+            em = s_nb[nb_index(mx, my, mz)];
+            km = em.y & 3;
+            if (km != K_NONE && static_cast<unsigned>(em.x) >= static_cast<unsigned>(p.n_nodes)) {
+                report(p.status, 3, item);
+                km = K_NONE;
+            }
+        }
+        if (!__any_sync(0xffffffffu, kp >= K_LEAF || km >= K_LEAF)) continue;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(ox, oy, oz));
+        double e, q;
+        ot_mono_adj_split(e, q, lb, d);
+        scatter_mass(p, ep, kp, px, py, pz, e + q);
+        if (PAIRED) scatter_mass(p, em, km, mx, my, mz, e - q);
+    }
+}
+
+// one scatter work item: the warp's 32 target cells of `node` push their
+// point-mass adjoint contributions into mbar
+template <class P>
+__device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
+                             int node, int par, int half, int lane, int it) {
+    int tx, ty, tz;
+    lane_cell(lane, par, half, tx, ty, tz);
+    double lb[16];
+    const double* src = p.Lrbar + static_cast<size_t>(node) * NRED * NCELL + tx + 8 * ty + 64 * tz;
+    bool nz = false;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        lb[q] = __ldg(src + q * NCELL);
+        nz |= lb[q] != 0.0;
+    }
+    if (!__any_sync(0xffffffffu, nz)) return;     // targets without an adjoint contribute nothing
+    if (lane < 27) s_nb[lane] = __ldg(nbr + static_cast<size_t>(node) * 27 + lane);
+    __syncwarp();
+    const int info = __ldg(ninfo + node);
+    const int level = info & 0xff;
+    const bool leafT = (info >> 8) & 1;
+    if (level == 0) {
+        walk_scatter<true>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, lb, it);
+    } else {
+        const int* lf = p.L.lists + par * p.L.far_len;
+        walk_scatter<true>(lf, p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
+        walk_scatter<false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
+    }
+    if (leafT) walk_scatter<true>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, it);
+}
+
+__global__ void __launch_bounds__(256) scatter_adjoint_kernel(const ScatParams p, int persistent) {
+    __shared__ int2 s_nb[8][27];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    int it = blockIdx.x * wpb + warp;
+    for (;;) {
+        if (persistent) {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(p.counter, 1);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= p.n_items) break;
+        const int item = __ldg(p.items + it);
+        scatter_item(p, p.nbr, p.ninfo, s_nb[warp], item >> 4, (item >> 1) & 7, item & 1, lane, it);
         __syncwarp();
         if (!persistent) break;
     }
@@ -906,9 +1024,23 @@ cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wp
     switch (mode) {
         case 1: adjoint_kernel<1><<<grid, block, 0, s>>>(p, per); break;
         case 2: adjoint_kernel<2><<<grid, block, 0, s>>>(p, per); break;
+        case 4: adjoint_kernel<4><<<grid, block, 0, s>>>(p, per); break;
+        case 5: adjoint_kernel<5><<<grid, block, 0, s>>>(p, per); break;
         default: adjoint_kernel<3><<<grid, block, 0, s>>>(p, per); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_adjoint(const ScatParams& p, bool persistent, int wpb, int grid, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    scatter_adjoint_kernel<<<grid, 32 * wpb, 0, s>>>(p, persistent ? 1 : 0);
+    return cudaGetLastError();
+}
+
+int scatter_max_blocks_per_sm(int wpb) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)scatter_adjoint_kernel, 32 * wpb, 0);
+    return n;
 }
 
 int forward_max_blocks_per_sm(int mode, int wpb) {
@@ -922,7 +1054,9 @@ int forward_max_blocks_per_sm(int mode, int wpb) {
 int adjoint_max_blocks_per_sm(int mode, int wpb) {
     int n = 0;
     const void* f = (mode == 1) ? (const void*)adjoint_kernel<1>
-                  : (mode == 2) ? (const void*)adjoint_kernel<2> : (const void*)adjoint_kernel<3>;
+                  : (mode == 2) ? (const void*)adjoint_kernel<2>
+                  : (mode == 4) ? (const void*)adjoint_kernel<4>
+                  : (mode == 5) ? (const void*)adjoint_kernel<5> : (const void*)adjoint_kernel<3>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
     return n;
 }

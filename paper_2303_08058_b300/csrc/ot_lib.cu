@@ -172,9 +172,15 @@ struct ot_grid {
     int* d_items_adj[4] = {nullptr, nullptr, nullptr, nullptr};
     int n_items_adj[4] = {0, 0, 0, 0};
     int* d_items_adj_node[4] = {nullptr, nullptr, nullptr, nullptr};   // source order (plain path)
+    int* d_items_adj_fast[2] = {nullptr, nullptr};    // [0]: point-mass scatter items only, [1]: + multipole gather
+    int n_items_adj_fast[2] = {0, 0};
     std::vector<int> adj_item_start[4];                                // [n + nvirt + 1]
     int maxb_fwd[4][9] = {};
     int maxb_adj[4][9] = {};
+    int maxb_scat[9] = {};
+    int maxb_fast5[9] = {};
+    int deterministic = 0;              // 1: point-mass adjoint as a gather (fixed summation order)
+    long long flops_adj_det = 0, ops_adj_det = 0, flops_adj_fast = 0, ops_adj_fast = 0;
     int* d_nonleaf = nullptr;
     int n_nonleaf = 0;
     int* d_all = nullptr;
@@ -187,7 +193,7 @@ struct ot_grid {
     double* d_Lrbar = nullptr;
     double* d_vbar = nullptr;
     double* d_Mb = nullptr;
-    int* d_counters = nullptr;       // [0] forward, [1] adjoint
+    int* d_counters = nullptr;       // [0] forward, [1] adjoint gather, [2] adjoint scatter
     int* d_status = nullptr;         // [2]
     cudaStream_t cap_stream = nullptr;
 
@@ -501,6 +507,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     //   adjoint point mass 16 | 32 paired; multipole 70 | 102 paired.
     long long pairs_multi = 0, pairs_mono = 0, pairs_virt = 0, pairs_ang = 0, lanes = 0;
     long long flops_fwd = 0, flops_adj = 0, ops_fwd = 0, ops_adj = 0;
+    long long flops_adj_scat = 0, ops_adj_scat = 0, count_single_mono = 0;
+    long long flops_adj_multi = 0, ops_adj_multi = 0;
     std::vector<std::pair<long long, int>> fwd[4];
     std::vector<int> node_order_items;
     g->node_item_start.assign(n + 1, 0);
@@ -532,6 +540,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             if (mo >> j & 1u) {
                 pairs_mono += cp + cs;
                 flops_fwd += 17 * cp + 32 * cs;
+                flops_adj_scat += 16 * cp + 32 * cs;
             }
             if (mv >> j & 1u) pairs_virt += cp + cs;
         }
@@ -543,13 +552,20 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 const std::vector<uint8_t>& pf = pflag[ph][sg];
                 for (size_t k = 0; k < mk.size(); ++k) {
                     if (mk[k] & mm) cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
-                    if (mk[k] & mo) cost[2] += pf[k] ? 18 : 16;
+                    if (mk[k] & mo) {
+                        cost[2] += pf[k] ? 18 : 16;
+                        if (!pf[k]) count_single_mono -= 1;    // 17 ops single in the scatter
+                    }
                     if (mk[k] & (mm | mo)) lanes += 32;
                 }
             };
             scan(s1);
             if (leaf) scan(1);
             ops_fwd += 32 * (cost[1] + cost[2]);
+            // the point-mass adjoint organised by target walks the same active
+            // entries: 16 products + 2 adds per paired entry, 16 + 1 single
+            ops_adj_scat += 32 * (cost[2] - count_single_mono);
+            count_single_mono = 0;
             const int item = (i << 4) | ph;
             node_order_items.push_back(item);
             for (int mode = 1; mode <= 3; ++mode) {
@@ -587,6 +603,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 cs += cnt[1][0][j];
             }
             flops_adj += leaf ? 32 * (cp + cs) : 86 * cp + 140 * cs;
+            if (!leaf) flops_adj_multi += 86 * cp + 140 * cs;
         }
         const int bit = leaf ? 2 : 1;
         for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode][i] = static_cast<int>(adj_node[mode].size());
@@ -598,6 +615,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 if (mask[ph][1][k] & tl) cst += leaf ? 32 : 102;
             if (cst == 0) continue;
             ops_adj += 32 * cst;
+            if (!leaf) ops_adj_multi += 32 * cst;
             const int item = (i << 4) | ph;
             for (int mode = 1; mode <= 3; ++mode)
                 if (mode & bit) {
@@ -612,7 +630,21 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                          [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
                              return a.first > b.first;
                          });
-    if (static_cast<long long>(n + g->nvirt) >= (1LL << 27)) return fail(OT_EINVAL, "too many sub-grids");
+    if (static_cast<long long>(n + g->nvirt) >= (1LL << 26)) return fail(OT_EINVAL, "too many sub-grids");
+    // the default adjoint: point-mass scatter items (forward items of the
+    // point-mass class, flagged with bit 30) merged with the multipole gather
+    // items, longest first, in one persistent launch
+    std::vector<std::pair<long long, int>> fast[2];
+    for (auto& pr : fwd[2]) {
+        fast[0].emplace_back(pr.first, pr.second | (1 << 30));
+        fast[1].emplace_back(pr.first, pr.second | (1 << 30));
+    }
+    for (auto& pr : adj[1]) fast[1].push_back(pr);
+    for (int k = 0; k < 2; ++k)
+        std::stable_sort(fast[k].begin(), fast[k].end(),
+                         [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
+                             return a.first > b.first;
+                         });
 
     // --- M2M schedule ---------------------------------------------------------
     std::vector<int> nonleaf, all(n), cube;
@@ -657,9 +689,18 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.pairs_angular = pairs_ang;
     I.lanes_fwd = lanes;
     I.flops_fwd = flops_fwd;
-    I.flops_adj = flops_adj;
+    g->flops_adj_det = flops_adj;
+    g->ops_adj_det = ops_adj;
+    g->flops_adj_fast = flops_adj_multi + flops_adj_scat;
+    g->ops_adj_fast = ops_adj_multi + ops_adj_scat;
+    I.flops_adj = g->flops_adj_fast;
     I.ops_fwd = ops_fwd;
-    I.ops_adj = ops_adj;
+    I.ops_adj = g->ops_adj_fast;
+    for (int w = 2; w <= 8; w *= 2) {
+        g->maxb_scat[w] = scatter_max_blocks_per_sm(w);
+        g->maxb_adj[4 - 4][w] = adjoint_max_blocks_per_sm(4, w);   // slot 0: fused, point masses only
+        g->maxb_fast5[w] = adjoint_max_blocks_per_sm(5, w);
+    }
     for (int mode = 1; mode <= 3; ++mode)
         for (int w = 2; w <= 8; w *= 2) {
             g->maxb_fwd[mode][w] = forward_max_blocks_per_sm(mode, w);
@@ -690,6 +731,12 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         UP(g->d_items_adj_node[mode], adj_node[mode]);
     }
     UP(g->d_items_fwd_node, node_order_items);
+    for (int k = 0; k < 2; ++k) {
+        std::vector<int> items;
+        for (auto& pr : fast[k]) items.push_back(pr.second);
+        g->n_items_adj_fast[k] = static_cast<int>(items.size());
+        UP(g->d_items_adj_fast[k], items);
+    }
     g->n_nonleaf = static_cast<int>(nonleaf.size());
     UP(g->d_nonleaf, nonleaf);
     UP(g->d_all, all);
@@ -786,9 +833,44 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
     return OT_OK;
 }
 
+static ot_status enqueue_scatter(ot_grid* g, double* mbar, cudaStream_t s) {
+    ScatParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.counter = g->d_counters + 2;
+    p.nbr = g->d_nbr;
+    p.ninfo = g->d_ninfo;
+    p.Dt = g->d_Dt;
+    p.L.lists = g->d_lists;
+    p.L.far_len = g->far_len;
+    p.L.far_pairs = g->far_pairs;
+    p.L.near_len = g->near_len;
+    p.L.root_len = g->root_len;
+    p.L.near_off = 8 * g->far_len;
+    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.Lrbar = g->d_Lrbar;
+    p.mbar = mbar;
+    p.n_nodes = g->n;
+    p.status = g->d_status;
+    if (g->schedule == OT_SCHED_PER_SUBGRID) {
+        for (int i = 0; i < g->n; ++i) {
+            ScatParams q = p;
+            q.items = g->d_items_fwd_node + g->node_item_start[i];
+            q.n_items = g->node_item_start[i + 1] - g->node_item_start[i];
+            OT_CUDA(launch_scatter_adjoint(q, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s));
+        }
+    } else {
+        p.items = g->d_items_fwd[2];
+        p.n_items = g->n_items_fwd[2];
+        OT_CUDA(cudaMemsetAsync(g->d_counters + 2, 0, sizeof(int), s));
+        OT_CUDA(launch_scatter_adjoint(p, true, g->wpb, grid_blocks(g, g->maxb_scat[g->wpb]), s));
+    }
+    return OT_OK;
+}
+
 static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, double* mbar, cudaStream_t s) {
-    const int mode = (Mbar ? 1 : 0) | (mbar ? 2 : 0);
+    int mode = (Mbar ? 1 : 0) | (mbar ? 2 : 0);
     if (mode == 0) return OT_OK;
+    const bool scatter = !g->deterministic && mbar != nullptr;
     PrepParams pp;
     std::memset(&pp, 0, sizeof(pp));
     pp.src = Lbar;
@@ -800,6 +882,12 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     OT_CUDA(launch_prescale_adjoint(pp, s));
     if (Mbar) OT_CUDA(cudaMemsetAsync(Mbar, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
     if (mbar) OT_CUDA(cudaMemsetAsync(mbar, 0, static_cast<size_t>(g->n) * NCELL * sizeof(double), s));
+    if (scatter && g->schedule == OT_SCHED_PER_SUBGRID) {
+        ot_status st = enqueue_scatter(g, mbar, s);
+        if (st != OT_OK) return st;
+        mode &= 1;               // multipole sources still gather
+        if (mode == 0) return OT_OK;
+    }
     AdjParams p;
     std::memset(&p, 0, sizeof(p));
     p.items = g->d_items_adj[mode];
@@ -834,11 +922,21 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
             if (q.n_items == 0) continue;
             OT_CUDA(launch_adjoint(q, mode, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s));
         }
+    } else if (scatter) {
+        // one persistent launch: multipole gather items (if Mbar) and
+        // point-mass scatter items, longest first
+        const int k = (mode & 1) ? 1 : 0;
+        p.items = g->d_items_adj_fast[k];
+        p.n_items = g->n_items_adj_fast[k];
+        OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
+        const int maxb = k ? g->maxb_fast5[g->wpb] : g->maxb_adj[0][g->wpb];
+        OT_CUDA(launch_adjoint(p, k ? 5 : 4, true, g->wpb, grid_blocks(g, maxb), s));
     } else {
         OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
         OT_CUDA(launch_adjoint(p, mode, true, g->wpb, grid_blocks(g, g->maxb_adj[mode][g->wpb]), s));
     }
-    if (mbar && g->vmap_rows > 0) OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
+    if (!scatter && mbar && g->vmap_rows > 0)
+        OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
     return OT_OK;
 }
 
@@ -1026,6 +1124,17 @@ ot_status ot_set_schedule(ot_grid* g, int32_t schedule, int32_t warps_per_block,
     GUARD_END
 }
 
+ot_status ot_set_deterministic(ot_grid* g, int32_t on) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (on != 0 && on != 1) return fail(OT_EINVAL, "on must be 0 or 1");
+    g->deterministic = on;
+    g->info.flops_adj = on ? g->flops_adj_det : g->flops_adj_fast;
+    g->info.ops_adj = on ? g->ops_adj_det : g->ops_adj_fast;
+    return OT_OK;
+    GUARD_END
+}
+
 ot_status ot_moments(ot_grid* g, const double* rho, double* M, double* m, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
@@ -1128,7 +1237,7 @@ ot_status ot_interactions_backward(ot_grid* g, const double* Lbar, double* Mbar,
     if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
     if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{4, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps};
+    GraphKey key{4 + 8 * g->deterministic, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_backward(g, Lbar, Mbar, mbar, st); });
     GUARD_END
 }

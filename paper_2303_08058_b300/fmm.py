@@ -81,6 +81,10 @@ class OTGrid:
         _lib.check(self.lib.ot_set_schedule(self.handle, int(schedule), int(warps_per_block), int(blocks_per_sm),
                                             int(bool(use_graph))))
 
+    def set_deterministic(self, on=True):
+        """Fixed-order (bit-reproducible) adjoint instead of the atomic one."""
+        _lib.check(self.lib.ot_set_deterministic(self.handle, int(bool(on))))
+
     def autotune(self, M, m, L, Lc=None, stream=None):
         w, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
         _lib.check(self.lib.ot_autotune(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), _stream(stream),

@@ -216,6 +216,7 @@ def test_schedules_are_bitwise_identical(ot):
     for sched in [(0, 4, 0, True), (0, 2, 1, False), (1, 4, 0, False), (0, 8, 0, True)]:
         g = ot.OTGrid.from_tree(tree)
         g.set_schedule(*sched)
+        g.set_deterministic(True)
         M, m = g.moments(dev(rho))
         for _ in range(2):   # second call replays the graph
             L, Lc = g.interactions(M, m)
@@ -253,13 +254,15 @@ def test_adjoint_dense_single_subgrid(ot, orc):
     assert np.all(host(mb) == 0)
 
 
+@pytest.mark.parametrize("deterministic", [False, True])
 @pytest.mark.parametrize("which", ["uniform_tree", "adaptive", "leaf_level"])
-def test_adjoint_matches_oracle_transposed_sum(ot, orc, which):
+def test_adjoint_matches_oracle_transposed_sum(ot, orc, which, deterministic):
     tree = {"uniform_tree": lambda: synth.uniform_tree(1, 1.0),
             "adaptive": _small_adaptive,
             "leaf_level": lambda: synth.uniform_level(1, 1.0)}[which]()
     Lbar, tg = _sparse_lbar(tree, 300, 51)
     g = ot.OTGrid.from_tree(tree)
+    g.set_deterministic(deterministic)
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
     Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg)
@@ -267,6 +270,22 @@ def test_adjoint_matches_oracle_transposed_sum(ot, orc, which):
     assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
     assert_parity(host(mb), mo, Sm, what="mbar")
     assert np.max(np.abs(mo)) > 0
+
+
+def test_atomic_adjoint_equals_fixed_order_adjoint(ot):
+    """The default point-mass adjoint (target-ordered, atomic adds) and the
+    fixed-order gather agree to rounding on a dense L-bar; the multipole
+    half is the same gather in both modes (bitwise equal)."""
+    tree = _small_adaptive()
+    Lbar = dev(np.random.default_rng(55).standard_normal((tree.n, 20, 512)))
+    g = ot.OTGrid.from_tree(tree)
+    Mb1, mb1 = g.backward(Lbar)
+    g.set_deterministic(True)
+    Mb2, mb2 = g.backward(Lbar)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(Mb1), host(Mb2))
+    a, b = host(mb1), host(mb2)
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
 
 
 def test_adjoint_dot_product_gpu(ot):
