@@ -184,6 +184,20 @@ ot_status ot_l2l(ot_grid* grid, double* L, void* stream);
  * up, every parent cell adds the transposed shifts of its children's Lbar. */
 ot_status ot_l2l_backward(ot_grid* grid, double* Lbar, void* stream);
 
+/* Arithmetic of the point-mass contractions of the forward passes.
+ * OT_PREC_FP64 (default): FP64 FMAs throughout.
+ * OT_PREC_DF64_POINT_MASS: point-mass pairs are contracted in double-float
+ *   arithmetic on the FP32 pipe -- every value an unevaluated sum hi + lo of
+ *   two FP32 numbers (48-bit significand), products split exactly with FMAs,
+ *   sums by two-sum -- and moved into FP64 accumulators every 16 offsets, so
+ *   each coefficient stays within ~2e-13 of the sum of |terms| of its FP64
+ *   value.  Requires point masses m with |m| in [2^-100, 2^100] or m = 0 and
+ *   derivative-table values in the same range (true for cell sizes within
+ *   2^-10 .. 2^10 of level 0's).  Multipole pairs and the adjoints stay FP64. */
+#define OT_PREC_FP64 0
+#define OT_PREC_DF64_POINT_MASS 1
+ot_status ot_set_precision(ot_grid* grid, int32_t mode);
+
 /* 1: every adjoint result in a fixed summation order (bit-reproducible);
  * 0 (default): the point-mass adjoint uses atomic adds (faster). */
 ot_status ot_set_deterministic(ot_grid* grid, int32_t on);

@@ -15,13 +15,14 @@ OT_OK, OT_EINVAL, OT_ENOMEM, OT_ECUDA, OT_ETIMEOUT, OT_ESTATE, OT_ENOTSUP, OT_ED
 STATUS_NAMES = ["OT_OK", "OT_EINVAL", "OT_ENOMEM", "OT_ECUDA", "OT_ETIMEOUT", "OT_ESTATE", "OT_ENOTSUP",
                 "OT_EDEVICE"]
 OT_SCHED_PERSISTENT, OT_SCHED_PER_SUBGRID = 0, 1
+OT_PREC_FP64, OT_PREC_DF64_POINT_MASS = 0, 1
 
 # every entry point declared in include/ot.h
 EXPORTS = ["ot_grid_create", "ot_grid_destroy", "ot_grid_info", "ot_moments", "ot_moments_backward",
            "ot_multipole_interactions", "ot_monopole_interactions", "ot_interactions",
            "ot_interactions_backward", "ot_set_schedule", "ot_autotune", "ot_grid_check",
            "ot_fp64_fma_probe", "ot_multipole_interactions_noalloc", "ot_l2l", "ot_l2l_backward",
-           "ot_set_deterministic",
+           "ot_set_deterministic", "ot_set_precision",
            "ot_last_error"]
 
 
@@ -81,6 +82,7 @@ def load():
         "ot_l2l": [P, P, P],
         "ot_l2l_backward": [P, P, P],
         "ot_set_deterministic": [P, I],
+        "ot_set_precision": [P, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -26,6 +26,10 @@ cost 16 FMAs + 2 adds, two multipole pairs 70 FMAs + 32 adds (+ 30 FMAs for
 the angular term, whose derivatives are all of order 4); the multipole
 adjoint pairs the same way on the two targets' L-bar.
 
+Double-float variants (FP32 pairs hi + lo, see ot_kernels.cu) of the
+point-mass contractions read a second table of 32 floats per offset: the
+hi parts of the 16 IND16 derivatives, then their lo parts.
+
 Derivative-table row layout (36 doubles per integer offset):
   [0..15]  the IND16 components of ranks 0..3
   [16..19] zz, xzz, yzz, zzz
@@ -180,6 +184,24 @@ def emit():
             first[par] = False
         else:
             w(f"  {v} = fma(lb[{j}], d[{j}], {v});\n")
+    w("}\n\n")
+
+    # double-float (FP32 hi + lo) point-mass contraction, paired form:
+    # a[J] += x * D[J] with x = s (even order) or dm (odd order); the row
+    # holds hi[0..15] then lo[0..15]
+    w("// double-float: 16 products for two point-mass pairs (x = s or dm by order parity)\n")
+    w("__device__ __forceinline__ void ot_mono_fwd_pair_df(float (&ah)[16], float (&al)[16], float sh, float sl,\n"
+      "                                                    float dh, float dl, const float (&r)[32]) {\n")
+    for j in range(16):
+        even = rank(IND16[j]) % 2 == 0
+        xh, xl = ("sh", "sl") if even else ("dh", "dl")
+        w(f"  df_fma(ah[{j}], al[{j}], {xh}, {xl}, r[{j}], r[{16 + j}]);\n")
+    w("}\n\n")
+    w("// double-float: 16 products for one point-mass pair\n")
+    w("__device__ __forceinline__ void ot_mono_fwd_df(float (&ah)[16], float (&al)[16], float mh, float ml,\n"
+      "                                               const float (&r)[32]) {\n")
+    for j in range(16):
+        w(f"  df_fma(ah[{j}], al[{j}], mh, ml, r[{j}], r[{16 + j}]);\n")
     w("}\n\n")
 
     # the same with the row of -o: odd-order derivatives negated

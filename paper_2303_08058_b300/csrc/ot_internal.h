@@ -46,6 +46,8 @@ struct FwdParams {
     Lists L;
     const double* Mhat;    // [n][16][512] reduced scaled moments (non-leaf nodes)
     const double* m;       // [n][512]
+    const float2* mf;      // [n][512] masses as double-float (hi, lo), or null for FP64
+    const float* Dt32;     // [NOFF][32] hi then lo parts of the 16 point-mass derivatives
     double* Lout;          // [n][20][512]
     double* Lc;            // [n][3][512] or null
     int accumulate;
@@ -124,7 +126,8 @@ cudaError_t launch_l2l_adjoint(double* Lb, const int* parents, int n_list, const
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, int variant, cudaStream_t s);
 cudaError_t launch_scatter_adjoint(const ScatParams& p, bool persistent, int wpb, int grid, cudaStream_t s);
 int scatter_max_blocks_per_sm(int wpb);
-int forward_max_blocks_per_sm(int mode, int wpb);
+int forward_max_blocks_per_sm(int mode, int wpb);   // mode 6/7: double-float point masses
+cudaError_t launch_split_masses(const double* m, float2* mf, size_t n, cudaStream_t s);
 int adjoint_max_blocks_per_sm(int mode, int wpb);
 
 }  // namespace otk

@@ -19,6 +19,40 @@
 
 namespace otk {
 
+// ---------------------------------------------------------------------------
+// double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi)/2, 48 significant bits).  The _rn intrinsics are
+// never contracted into FMAs, which the error-free transformations need.
+// ---------------------------------------------------------------------------
+
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (ah, al) += (xh, xl) * (yh, yl): the high product is split exactly with an
+// FMA, the cross terms go to the low part, xl * yl is dropped
+__device__ __forceinline__ void df_fma(float& ah, float& al, float xh, float xl, float yh, float yl) {
+    const float ph = __fmul_rn(xh, yh);
+    const float pe = __fmaf_rn(xh, yh, -ph);
+    const float pl = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, pe));
+    float sh, se;
+    two_sum(ah, ph, sh, se);
+    al = __fadd_rn(al, __fadd_rn(se, pl));
+    ah = sh;
+}
+
+// (sh, sl) = (ah, al) + (bh, bl), renormalized
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+
 #include "ot_contract.inc"
 
 __device__ __forceinline__ void report(int* status, int code, int item) {
@@ -47,6 +81,18 @@ __device__ __forceinline__ void load_row(double (&d)[36], const double* __restri
         const double2 v = __ldg(p + i);
         d[2 * i] = v.x;
         d[2 * i + 1] = v.y;
+    }
+}
+
+__device__ __forceinline__ void load_row32f(float (&r)[32], const float* __restrict__ Dt32, int row) {
+    const float4* p = reinterpret_cast<const float4*>(Dt32 + static_cast<size_t>(row) * 32);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 v = __ldg(p + i);
+        r[4 * i] = v.x;
+        r[4 * i + 1] = v.y;
+        r[4 * i + 2] = v.z;
+        r[4 * i + 3] = v.w;
     }
 }
 
@@ -80,6 +126,28 @@ __device__ __forceinline__ double source_mass(const FwdParams& p, int2 e, int ki
     return 0.0;
 }
 
+// the same point mass as a double-float pair (hi, lo) from the split masses
+__device__ __forceinline__ void source_mass_df(const FwdParams& p, int2 e, int kind, int sx, int sy, int sz,
+                                               float& mh, float& ml) {
+    mh = 0.0f;
+    ml = 0.0f;
+    if (kind == K_LEAF) {
+        const float2 v = __ldg(p.mf + static_cast<size_t>(e.x) * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7));
+        mh = v.x;
+        ml = v.y;
+    } else if (kind == K_VIRT) {
+        const unsigned meta = static_cast<unsigned>(e.y);
+        const int d = (meta >> 2) & 7;
+        const int vx = static_cast<int>(((meta >> 8) & 0xffu) + (sx & 7)) >> d;
+        const int vy = static_cast<int>(((meta >> 16) & 0xffu) + (sy & 7)) >> d;
+        const int vz = static_cast<int>((meta >> 24) + (sz & 7)) >> d;
+        const float2 v = __ldg(p.mf + static_cast<size_t>(e.x) * NCELL + vx + 8 * vy + 64 * vz);
+        const float sc = __int_as_float((127 - 3 * d) << 23);      // 8^-d exactly
+        mh = __fmul_rn(v.x, sc);
+        ml = __fmul_rn(v.y, sc);
+    }
+}
+
 __device__ __forceinline__ void source_moments(const FwdParams& p, int2 e, bool multi, int sx, int sy, int sz,
                                                double (&r)[16]) {
     if (multi) {
@@ -107,11 +175,23 @@ __device__ __forceinline__ int nb_index(int sx, int sy, int sz) {
 
 // PAIRED: each entry o stands for the offsets o and -o (sources at t + o and
 // t - o share the table row of o, with odd-order derivatives negated for -o).
-template <int MODE, bool PAIRED>
+// (ah, al) double-float partial sums of the point-mass contributions, moved
+// into the FP64 accumulators every 16 entries (bounds their rounding error)
+__device__ __forceinline__ void df_flush(double (&a)[16], float (&ah)[16], float (&al)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a[j] += static_cast<double>(ah[j]) + static_cast<double>(al[j]);
+        ah[j] = 0.0f;
+        al[j] = 0.0f;
+    }
+}
+
+template <int MODE, bool PAIRED, bool EMU>
 __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
                                              int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                              const FwdParams& p, double (&a)[16], double (&c)[3],
-                                             double (&t4)[9], int item) {
+                                             double (&t4)[9], float (&ah)[16], float (&al)[16], int& nacc,
+                                             int item) {
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
@@ -129,14 +209,34 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
         if (MODE & 2) {
             const bool mono = kp >= K_LEAF || km >= K_LEAF;
             if (__any_sync(0xffffffffu, mono)) {
-                const double mp = source_mass(p, ep, kp, px, py, pz);
-                double d[36];
-                load_row16(d, p.Dt, row);
-                if (PAIRED) {
-                    const double mm = source_mass(p, em, km, mx, my, mz);
-                    ot_mono_fwd_pair(a, mp + mm, mp - mm, d);
+                if (EMU) {
+                    float mh, ml;
+                    source_mass_df(p, ep, kp, px, py, pz, mh, ml);
+                    float r[32];
+                    load_row32f(r, p.Dt32, row);
+                    if (PAIRED) {
+                        float nh, nl, sh, sl, dh, dl;
+                        source_mass_df(p, em, km, mx, my, mz, nh, nl);
+                        df_add(mh, ml, nh, nl, sh, sl);
+                        df_add(mh, ml, -nh, -nl, dh, dl);
+                        ot_mono_fwd_pair_df(ah, al, sh, sl, dh, dl, r);
+                    } else {
+                        ot_mono_fwd_df(ah, al, mh, ml, r);
+                    }
+                    if (++nacc == 16) {
+                        df_flush(a, ah, al);
+                        nacc = 0;
+                    }
                 } else {
-                    ot_mono_fwd(a, mp, d);
+                    const double mp = source_mass(p, ep, kp, px, py, pz);
+                    double d[36];
+                    load_row16(d, p.Dt, row);
+                    if (PAIRED) {
+                        const double mm = source_mass(p, em, km, mx, my, mz);
+                        ot_mono_fwd_pair(a, mp + mm, mp - mm, d);
+                    } else {
+                        ot_mono_fwd(a, mp, d);
+                    }
                 }
             }
         }
@@ -224,7 +324,7 @@ __device__ __forceinline__ void store_forward(const FwdParams& p, int node, int 
     }
 }
 
-template <int MODE>
+template <int MODE, bool EMU>
 __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
     const int lane = threadIdx.x & 31;
@@ -248,24 +348,32 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
         int tx, ty, tz;
         lane_cell(lane, par, half, tx, ty, tz);
         double a[16], c[3], t4[9];
+        float ah[16], al[16];
+        int nacc = 0;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) a[q] = 0.0;
+        for (int q = 0; q < 16; ++q) {
+            a[q] = 0.0;
+            ah[q] = 0.0f;
+            al[q] = 0.0f;
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) c[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) t4[q] = 0.0;
         if (level == 0) {
-            walk_forward<MODE, true>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, tx, ty, tz, s_nb[warp], p, a,
-                                     c, t4, it);
+            walk_forward<MODE, true, EMU>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, tx, ty, tz, s_nb[warp], p,
+                                          a, c, t4, ah, al, nacc, it);
         } else {
             const int* lf = p.L.lists + par * p.L.far_len;
-            walk_forward<MODE, true>(lf, p.L.far_pairs, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, it);
-            walk_forward<MODE, false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, tx, ty, tz,
-                                      s_nb[warp], p, a, c, t4, it);
+            walk_forward<MODE, true, EMU>(lf, p.L.far_pairs, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, ah, al,
+                                          nacc, it);
+            walk_forward<MODE, false, EMU>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, tx, ty, tz,
+                                           s_nb[warp], p, a, c, t4, ah, al, nacc, it);
         }
         if (leafT)
-            walk_forward<MODE, true>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p, a,
-                                     c, t4, it);
+            walk_forward<MODE, true, EMU>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p,
+                                          a, c, t4, ah, al, nacc, it);
+        if (EMU) df_flush(a, ah, al);
         store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
         __syncwarp();
         if (!persistent) break;
@@ -1009,11 +1117,32 @@ cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wp
     if (p.n_items == 0) return cudaSuccess;
     const dim3 block(32 * wpb);
     const int per = persistent ? 1 : 0;
+    const bool emu = p.mf != nullptr;
     switch (mode) {
-        case 1: forward_kernel<1><<<grid, block, 0, s>>>(p, per); break;
-        case 2: forward_kernel<2><<<grid, block, 0, s>>>(p, per); break;
-        default: forward_kernel<3><<<grid, block, 0, s>>>(p, per); break;
+        case 1: forward_kernel<1, false><<<grid, block, 0, s>>>(p, per); break;
+        case 2:
+            if (emu) forward_kernel<2, true><<<grid, block, 0, s>>>(p, per);
+            else forward_kernel<2, false><<<grid, block, 0, s>>>(p, per);
+            break;
+        default:
+            if (emu) forward_kernel<3, true><<<grid, block, 0, s>>>(p, per);
+            else forward_kernel<3, false><<<grid, block, 0, s>>>(p, per);
+            break;
     }
+    return cudaGetLastError();
+}
+
+__global__ void split_masses_kernel(const double* __restrict__ m, float2* __restrict__ mf, size_t n) {
+    const size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double v = m[t];
+    const float hi = __double2float_rn(v);
+    mf[t] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+}
+
+cudaError_t launch_split_masses(const double* m, float2* mf, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    split_masses_kernel<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(m, mf, n);
     return cudaGetLastError();
 }
 
@@ -1045,8 +1174,10 @@ int scatter_max_blocks_per_sm(int wpb) {
 
 int forward_max_blocks_per_sm(int mode, int wpb) {
     int n = 0;
-    const void* f = (mode == 1) ? (const void*)forward_kernel<1>
-                  : (mode == 2) ? (const void*)forward_kernel<2> : (const void*)forward_kernel<3>;
+    const void* f = (mode == 1) ? (const void*)forward_kernel<1, false>
+                  : (mode == 2) ? (const void*)forward_kernel<2, false>
+                  : (mode == 3) ? (const void*)forward_kernel<3, false>
+                  : (mode == 6) ? (const void*)forward_kernel<2, true> : (const void*)forward_kernel<3, true>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
     return n;
 }

@@ -163,6 +163,9 @@ struct ot_grid {
     int* d_ninfo = nullptr;
     int* d_vinfo = nullptr;
     double* d_Dt = nullptr;
+    float* d_Dt32 = nullptr;            // double-float split of the point-mass derivatives
+    float2* d_mf = nullptr;             // masses as double-float pairs (scratch)
+    int precision = 0;                  // 0: FP64; 1: double-float point-mass contractions
     int* d_lists = nullptr;
     double* d_hinv = nullptr;
     int* d_items_fwd[4] = {nullptr, nullptr, nullptr, nullptr};     // LPT order, by mode
@@ -179,6 +182,7 @@ struct ot_grid {
     int maxb_adj[4][9] = {};
     int maxb_scat[9] = {};
     int maxb_fast5[9] = {};
+    int maxb_emu[4][9] = {};            // forward with double-float point masses, modes 2 and 3
     int deterministic = 0;              // 1: point-mass adjoint as a gather (fixed summation order)
     long long flops_adj_det = 0, ops_adj_det = 0, flops_adj_fast = 0, ops_adj_fast = 0;
     int* d_nonleaf = nullptr;
@@ -697,6 +701,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.ops_fwd = ops_fwd;
     I.ops_adj = g->ops_adj_fast;
     for (int w = 2; w <= 8; w *= 2) {
+        g->maxb_emu[2][w] = forward_max_blocks_per_sm(6, w);
+        g->maxb_emu[3][w] = forward_max_blocks_per_sm(7, w);
         g->maxb_scat[w] = scatter_max_blocks_per_sm(w);
         g->maxb_adj[4 - 4][w] = adjoint_max_blocks_per_sm(4, w);   // slot 0: fused, point masses only
         g->maxb_fast5[w] = adjoint_max_blocks_per_sm(5, w);
@@ -716,6 +722,17 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_ninfo, g->ninfo);
     UP(g->d_vinfo, g->vinfo);
     UP(g->d_Dt, Dt);
+    {
+        std::vector<float> Dt32(static_cast<size_t>(NOFF) * 32, 0.0f);
+        for (int r = 0; r < NOFF; ++r)
+            for (int j = 0; j < 16; ++j) {
+                const double v = Dt[static_cast<size_t>(r) * DROW + j];
+                const float hi = static_cast<float>(v);
+                Dt32[static_cast<size_t>(r) * 32 + j] = hi;
+                Dt32[static_cast<size_t>(r) * 32 + 16 + j] = static_cast<float>(v - static_cast<double>(hi));
+            }
+        UP(g->d_Dt32, Dt32);
+    }
     UP(g->d_lists, g->lists);
     std::vector<double> hv(g->hinv, g->hinv + MAXLEV);
     UP(g->d_hinv, hv);
@@ -752,6 +769,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_mf, static_cast<size_t>(n) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_counters, 4)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_status, 2)) != OT_OK) return st;
     OT_CUDA(cudaMemsetAsync(g->d_status, 0, 2 * sizeof(int), s));
@@ -814,6 +832,12 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
     if (!accumulate) OT_CUDA(cudaMemsetAsync(L, 0, nL * sizeof(double), s));
     if ((mode & 1) && Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
     FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
+    const bool emu = g->precision == 1 && (mode & 2);
+    if (emu) {
+        OT_CUDA(launch_split_masses(m, g->d_mf, static_cast<size_t>(g->n) * NCELL, s));
+        p.mf = g->d_mf;
+        p.Dt32 = g->d_Dt32;
+    }
     // zeroed above, so the kernel always accumulates
     if (g->schedule == OT_SCHED_PER_SUBGRID) {
         p.items = g->d_items_fwd_node;
@@ -828,7 +852,8 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         p.items = g->d_items_fwd[mode];
         p.n_items = g->n_items_fwd[mode];
         OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
-        OT_CUDA(launch_forward(p, mode, true, g->wpb, grid_blocks(g, g->maxb_fwd[mode][g->wpb]), s));
+        const int maxb = emu ? g->maxb_emu[mode][g->wpb] : g->maxb_fwd[mode][g->wpb];
+        OT_CUDA(launch_forward(p, mode, true, g->wpb, grid_blocks(g, maxb), s));
     }
     return OT_OK;
 }
@@ -1124,6 +1149,16 @@ ot_status ot_set_schedule(ot_grid* g, int32_t schedule, int32_t warps_per_block,
     GUARD_END
 }
 
+ot_status ot_set_precision(ot_grid* g, int32_t mode) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (mode != OT_PREC_FP64 && mode != OT_PREC_DF64_POINT_MASS)
+        return fail(OT_EINVAL, "unknown precision mode %d", mode);
+    g->precision = mode;
+    return OT_OK;
+    GUARD_END
+}
+
 ot_status ot_set_deterministic(ot_grid* g, int32_t on) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
@@ -1212,7 +1247,7 @@ ot_status ot_monopole_interactions(ot_grid* g, const double* m, double* L, void*
     CHECK_PTR(m, "m");
     CHECK_PTR(L, "L");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{2, nullptr, m, L, nullptr, g->wpb, g->bps};
+    GraphKey key{2 + 16 * g->precision, nullptr, m, L, nullptr, g->wpb, g->bps};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward(g, 2, nullptr, m, L, nullptr, 1, st); });
     GUARD_END
 }
@@ -1225,7 +1260,7 @@ ot_status ot_interactions(ot_grid* g, const double* M, const double* m, double* 
     CHECK_PTR(L, "L");
     if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{3, M, m, L, Lc, g->wpb, g->bps};
+    GraphKey key{3 + 16 * g->precision, M, m, L, Lc, g->wpb, g->bps};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward(g, 3, M, m, L, Lc, 0, st); });
     GUARD_END
 }

@@ -81,6 +81,11 @@ class OTGrid:
         _lib.check(self.lib.ot_set_schedule(self.handle, int(schedule), int(warps_per_block), int(blocks_per_sm),
                                             int(bool(use_graph))))
 
+    def set_precision(self, mode=_lib.OT_PREC_FP64):
+        """OT_PREC_FP64, or OT_PREC_DF64_POINT_MASS (double-float point-mass
+        contractions on the FP32 pipe, see include/ot.h)."""
+        _lib.check(self.lib.ot_set_precision(self.handle, int(mode)))
+
     def set_deterministic(self, on=True):
         """Fixed-order (bit-reproducible) adjoint instead of the atomic one."""
         _lib.check(self.lib.ot_set_deterministic(self.handle, int(bool(on))))

@@ -1,0 +1,84 @@
+"""Double-float point-mass contractions (OT_PREC_DF64_POINT_MASS) against the
+oracle: the same 1e-12 bound on each coefficient as the FP64 path."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import assert_parity, oracle_threads, sample_targets
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ot():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2303_08058_b300 as ot
+    ot.load()
+    return ot
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    oracle_threads(oracle)
+    return oracle
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def _small_adaptive():
+    def refine(l, c, h0):
+        return l == 1 and tuple(c) in {(0, 0, 0), (1, 1, 0)}
+    return synth.adaptive_tree(refine, 1, 2, 16.0)
+
+
+@pytest.mark.parametrize("which", ["leaf_level", "root_leaf", "adaptive", "uniform_tree"])
+def test_df64_all_cells(ot, orc, which):
+    tree = {"leaf_level": lambda: synth.uniform_level(1, 1.0),
+            "root_leaf": lambda: synth.single_subgrid(0, 1.0, leaf=True),
+            "adaptive": _small_adaptive,
+            "uniform_tree": lambda: synth.uniform_tree(1, 1.0)}[which]()
+    rho = synth.uniform_random_density(tree, seed=81)
+    g = ot.OTGrid.from_tree(tree)
+    g.set_precision(ot.OT_PREC_DF64_POINT_MASS)
+    M, m = g.moments(dev(rho))
+    L, Lc = g.interactions(M, m)
+    torch.cuda.synchronize()
+    g.check()
+    Mh, mh = host(M), host(m)
+    tg = np.stack(np.meshgrid(np.arange(tree.n), np.arange(512), indexing="ij"), -1).reshape(-1, 2).astype(np.int32)
+    r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
+    r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
+    got = host(L)[tg[:, 0], :, tg[:, 1]]
+    assert_parity(got, r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
+    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], r1["Sc"], what="Lc", block_axis=1)
+
+
+@pytest.mark.parametrize("cfg", ["config2", "config5"])
+def test_df64_full_size_sampled(ot, orc, cfg):
+    tree, rho = synth.config2() if cfg == "config2" else synth.config5_step(3)
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L64, _ = g.interactions(M, m, want_lc=False)
+    L64 = host(L64)
+    g.set_precision(ot.OT_PREC_DF64_POINT_MASS)
+    Ldf, _ = g.interactions(M, m, want_lc=False)
+    torch.cuda.synchronize()
+    Ldf = host(Ldf)
+    tg = sample_targets(tree, 200, 82)
+    r2 = orc.run_pass(tree, "monopole", m=host(m), targets=tg)
+    r1 = orc.run_pass(tree, "multipole", M=host(M), targets=tg)
+    assert_parity(Ldf[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
+    # every cell: double-float within 1e-12 of the FP64 path relative to the
+    # coefficient-order block magnitude of the FP64 result
+    scale = np.max(np.abs(L64), axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(Ldf - L64) / scale) < 1e-12
