@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default=None, help="WxB: warps per block x blocks per SM (skips the autotuner)")
-    ap.add_argument("--workload", choices=["polytrope64", "adaptive", "binary"], default="polytrope64",
+    ap.add_argument("--workload", choices=["polytrope64", "adaptive", "binary", "integration"], default="polytrope64",
                     help="polytrope64: the headline workload; adaptive: 4,641-sub-grid octree (levels 3-6); "
                          "binary: rotating binary star, levels 3-7, a new octree every step")
     return ap.parse_args()
@@ -226,6 +226,8 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", torch.cuda.current_device())
     if args.workload == "binary":
         return run_binary(args, rank, world)
+    if args.workload == "integration":
+        return run_integration(args, rank, world)
     tree, rho_h, Lbar_h, _ = make_workload(args.workload)
     g = ot.OTGrid.from_tree(tree)
     sched = ot.OT_SCHED_PER_SUBGRID if args.schedule == "per_subgrid" else ot.OT_SCHED_PERSISTENT
@@ -424,6 +426,35 @@ def run_binary(args, rank, world):
                        "tile": tile, "pairs_per_step": pairs / max(args.steps, 1),
                        "host_setup_s_per_step": setup_s / (args.steps + 1)},
             "step_ms": step_ms, "clocks": clk}, None, None
+
+
+def run_integration(args, rank, world):
+    """The completion-notification study on the 64^3 and adaptive workloads:
+    per-sub-grid forward launches over 1-32 streams with completions seen by
+    stream sync, host callbacks or event polling, against one batched
+    persistent launch (median of --steps repetitions)."""
+    import torch
+    import paper_2303_08058_b300 as ot
+    names = {0: "stream_sync", 1: "host_callback", 2: "event_polling", 3: "batched_persistent"}
+    out = {}
+    for wl in ("polytrope64", "adaptive"):
+        tree, rho_h, _, _ = make_workload(wl)
+        g = ot.OTGrid.from_tree(tree)
+        g.set_schedule(ot.OT_SCHED_PERSISTENT, 4, 2, False)
+        M, m = g.moments(torch.as_tensor(rho_h, device="cuda"))
+        rows = []
+        for mech in (0, 1, 2, 3):
+            for ns in ((1,) if mech == 3 else (1, 4, 16, 32)):
+                g.completion_study(M, m, mech, ns)            # warm-up
+                runs = [g.completion_study(M, m, mech, ns)[0] for _ in range(max(args.steps, 1))]
+                med = sorted(runs, key=lambda r: r["wall_ms"])[len(runs) // 2]
+                rows.append({"mechanism": names[mech], "streams": ns, "wall_ms": med["wall_ms"],
+                             "mean_latency_us": med["mean_latency_us"], "max_latency_us": med["max_latency_us"],
+                             "launches": med["launches"]})
+        out[wl] = {"subgrids": tree.n, "rows": rows}
+        g.close()
+    return {"metric": "completion notification of per-sub-grid launches (wall ms per forward pass)",
+            "workload": "integration study", "impl": "ours", "results": out, "steps": args.steps}, None, None
 
 
 def cpu_baseline(tree, rho_h, seconds, seed=7):

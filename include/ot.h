@@ -243,6 +243,31 @@ ot_status ot_autotune(ot_grid* grid, const double* M, const double* m, double* L
 ot_status ot_multipole_interactions_noalloc(ot_grid* grid, const double* M, double* L, double* Lc,
                                             void* stream);
 
+/* Completion-notification study.  The paper's integration question: when a
+ * task runtime launches many small per-sub-grid kernels, how does each
+ * kernel's completion reach the host tasks waiting on it (Sec. 3.2: SYCL
+ * host tasks versus event polling inside the scheduler)?  This runs the
+ * forward interactions of every sub-grid as its own launch, round-robin over
+ * `n_streams` streams, and signals each completion by
+ *   0: cudaStreamSynchronize after the launch (no integration: synchronous),
+ *   1: a cudaLaunchHostFunc callback (the host-task analogue),
+ *   2: an event polled by the launching thread between submissions and
+ *      afterwards (the event-polling analogue),
+ *   3: one batched persistent launch over all sub-grids, one event.
+ * L, Lc are overwritten with the forward result.  Outputs: wall time from
+ * the first submission to the last completion, mean and max latency from a
+ * sub-grid's submission to its completion being seen on the host.  Host
+ * waits give up after `timeout_s` with OT_ETIMEOUT.  Synchronizes the device. */
+typedef struct {
+    double wall_ms;
+    double mean_latency_us;
+    double max_latency_us;
+    int64_t launches;
+} ot_completion_stats;
+ot_status ot_completion_study(ot_grid* grid, const double* M, const double* m, double* L, double* Lc,
+                              int32_t mechanism, int32_t n_streams, double timeout_s,
+                              ot_completion_stats* out);
+
 /* Reads and clears the device status word (synchronizes `stream`): OT_OK, or
  * OT_EDEVICE with the failing work item in ot_last_error(). */
 ot_status ot_grid_check(ot_grid* grid, void* stream);

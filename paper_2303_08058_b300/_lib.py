@@ -22,7 +22,7 @@ EXPORTS = ["ot_grid_create", "ot_grid_destroy", "ot_grid_info", "ot_moments", "o
            "ot_multipole_interactions", "ot_monopole_interactions", "ot_interactions",
            "ot_interactions_backward", "ot_set_schedule", "ot_autotune", "ot_grid_check",
            "ot_fp64_fma_probe", "ot_multipole_interactions_noalloc", "ot_l2l", "ot_l2l_backward",
-           "ot_set_deterministic", "ot_set_precision",
+           "ot_set_deterministic", "ot_set_precision", "ot_completion_study",
            "ot_last_error"]
 
 
@@ -50,6 +50,11 @@ class GridInfo(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class CompletionStats(ctypes.Structure):
+    _fields_ = [("wall_ms", ctypes.c_double), ("mean_latency_us", ctypes.c_double),
+                ("max_latency_us", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -83,6 +88,7 @@ def load():
         "ot_l2l_backward": [P, P, P],
         "ot_set_deterministic": [P, I],
         "ot_set_precision": [P, I],
+        "ot_completion_study": [P, P, P, P, P, I, I, ctypes.c_double, ctypes.POINTER(CompletionStats)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

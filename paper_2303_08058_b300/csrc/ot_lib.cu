@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <atomic>
+#include <chrono>
 #include <map>
 #include <set>
 #include <new>
@@ -1145,6 +1147,174 @@ ot_status ot_set_schedule(ot_grid* g, int32_t schedule, int32_t warps_per_block,
     g->info.warps_per_block = warps_per_block;
     g->info.blocks_per_sm = blocks_per_sm;
     g->info.graphs_enabled = use_graph;
+    return OT_OK;
+    GUARD_END
+}
+
+// ---------------------------------------------------------------------------
+// completion-notification study: many small per-sub-grid launches whose
+// completions reach the host by different mechanisms
+// ---------------------------------------------------------------------------
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct CompletionSlot {
+    Clock::time_point submitted;
+    Clock::time_point done;
+    std::atomic<int> flag{0};
+    std::atomic<int>* counter = nullptr;
+};
+
+void CUDART_CB host_completion(void* arg) {    // runs on a CUDA runtime thread: no CUDA calls
+    CompletionSlot* s = static_cast<CompletionSlot*>(arg);
+    s->done = Clock::now();
+    s->flag.store(1, std::memory_order_release);
+    s->counter->fetch_add(1, std::memory_order_acq_rel);
+}
+
+}  // namespace
+
+ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, double* L, double* Lc, int32_t mechanism,
+                              int32_t n_streams, double timeout_s, ot_completion_stats* out) {
+    GUARD_BEGIN
+    if (!g || !out) return fail(OT_EINVAL, "grid and out must not be NULL");
+    CHECK_PTR(M, "M");
+    CHECK_PTR(m, "m");
+    CHECK_PTR(L, "L");
+    if (mechanism < 0 || mechanism > 3) return fail(OT_EINVAL, "mechanism must be 0..3");
+    if (n_streams < 1 || n_streams > 128) return fail(OT_EINVAL, "n_streams must be in [1, 128]");
+    if (!(timeout_s > 0.0)) return fail(OT_EINVAL, "timeout_s must be positive");
+    std::memset(out, 0, sizeof(*out));
+    // set-up (untimed): pre-scaled moments, zeroed outputs
+    std::vector<cudaStream_t> streams(n_streams, nullptr);
+    for (auto& st : streams) OT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct StreamGuard {
+        std::vector<cudaStream_t>& v;
+        ~StreamGuard() {
+            for (auto st : v)
+                if (st) cudaStreamDestroy(st);
+        }
+    } guard{streams};
+    const int save_sched = g->schedule;
+    g->schedule = OT_SCHED_PERSISTENT;
+    ot_status st0 = enqueue_forward(g, 3, M, m, L, Lc, 0, streams[0]);    // warm-up, fills Mhat
+    g->schedule = save_sched;
+    if (st0 != OT_OK) return st0;
+    OT_CUDA(cudaMemsetAsync(L, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), streams[0]));
+    OT_CUDA(cudaDeviceSynchronize());
+    FwdParams p = fwd_params(g, m, L, Lc, 1);
+    const int n = g->n;
+    std::vector<CompletionSlot> slots(n);
+    std::atomic<int> done_count{0};
+    std::vector<cudaEvent_t> events;
+    if (mechanism == 2) {
+        events.resize(n, nullptr);
+        for (auto& e : events) OT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    struct EventGuard {
+        std::vector<cudaEvent_t>& v;
+        ~EventGuard() {
+            for (auto e : v)
+                if (e) cudaEventDestroy(e);
+        }
+    } eguard{events};
+    const Clock::time_point t0 = Clock::now();
+    const auto deadline = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+    bool timed_out = false;
+    long long launches = 0;
+    if (mechanism == 3) {
+        // one batched persistent launch over every sub-grid, one completion
+        g->schedule = OT_SCHED_PERSISTENT;
+        for (auto& sl : slots) sl.submitted = Clock::now();
+        ot_status st = enqueue_forward(g, 3, M, m, L, Lc, 0, streams[0]);   // zeroes L itself
+        g->schedule = save_sched;
+        if (st != OT_OK) return st;
+        launches = 1;
+        cudaEvent_t ev;
+        OT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        OT_CUDA(cudaEventRecord(ev, streams[0]));
+        cudaError_t q;
+        while ((q = cudaEventQuery(ev)) == cudaErrorNotReady) {
+            if (Clock::now() > deadline) {
+                timed_out = true;
+                break;
+            }
+        }
+        const Clock::time_point t = Clock::now();
+        cudaEventDestroy(ev);
+        if (!timed_out && q != cudaSuccess) return fail(OT_ECUDA, "event query: %s", cudaGetErrorString(q));
+        for (auto& sl : slots) sl.done = t;
+    } else {
+        std::vector<int> pending;
+        pending.reserve(n);
+        auto poll = [&]() {
+            size_t w = 0;
+            for (size_t k = 0; k < pending.size(); ++k) {
+                const int i = pending[k];
+                const cudaError_t q = cudaEventQuery(events[i]);
+                if (q == cudaSuccess) {
+                    slots[i].done = Clock::now();
+                } else {
+                    pending[w++] = i;
+                }
+            }
+            pending.resize(w);
+        };
+        for (int i = 0; i < n; ++i) {
+            cudaStream_t s = streams[i % n_streams];
+            FwdParams q = p;
+            q.items = g->d_items_fwd_node + g->node_item_start[i];
+            q.n_items = g->node_item_start[i + 1] - g->node_item_start[i];
+            slots[i].counter = &done_count;
+            slots[i].submitted = Clock::now();
+            OT_CUDA(launch_forward(q, 3, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s));
+            ++launches;
+            if (mechanism == 0) {
+                OT_CUDA(cudaStreamSynchronize(s));
+                slots[i].done = Clock::now();
+            } else if (mechanism == 1) {
+                OT_CUDA(cudaLaunchHostFunc(s, host_completion, &slots[i]));
+            } else {
+                OT_CUDA(cudaEventRecord(events[i], s));
+                pending.push_back(i);
+                poll();                      // between submissions, like a scheduler between tasks
+            }
+        }
+        if (mechanism == 1) {
+            while (done_count.load(std::memory_order_acquire) < n) {
+                if (Clock::now() > deadline) {
+                    timed_out = true;
+                    break;
+                }
+            }
+        } else if (mechanism == 2) {
+            while (!pending.empty()) {
+                poll();
+                if (Clock::now() > deadline) {
+                    timed_out = true;
+                    break;
+                }
+            }
+        }
+    }
+    const Clock::time_point t1 = Clock::now();
+    if (timed_out) {
+        cudaDeviceSynchronize();             // let the queued work finish before the slots go away
+        return fail(OT_ETIMEOUT, "completions did not all arrive within %.1f s", timeout_s);
+    }
+    double sum = 0.0, mx = 0.0;
+    for (auto& sl : slots) {
+        const double us = std::chrono::duration<double, std::micro>(sl.done - sl.submitted).count();
+        sum += us;
+        mx = std::max(mx, us);
+    }
+    out->wall_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    out->mean_latency_us = sum / n;
+    out->max_latency_us = mx;
+    out->launches = launches;
+    OT_CUDA(cudaDeviceSynchronize());
     return OT_OK;
     GUARD_END
 }

@@ -96,6 +96,16 @@ class OTGrid:
                                         ctypes.byref(w), ctypes.byref(b), ctypes.byref(ms)))
         return dict(warps_per_block=w.value, blocks_per_sm=b.value, ms=ms.value)
 
+    def completion_study(self, M, m, mechanism, n_streams=1, timeout_s=60.0, L=None, Lc=None):
+        """Per-sub-grid launches with completion signalled by mechanism 0 (stream
+        sync), 1 (host callback), 2 (event polling) or 3 (one batched launch)."""
+        L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
+        Lc = Lc if Lc is not None else self.zeros(self.n, 3, NCELL)
+        out = _lib.CompletionStats()
+        _lib.check(self.lib.ot_completion_study(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), int(mechanism),
+                                                int(n_streams), float(timeout_s), ctypes.byref(out)))
+        return {name: getattr(out, name) for name, _ in out._fields_}, L, Lc
+
     # -- the path ------------------------------------------------------------------
     def moments(self, rho, M=None, m=None, stream=None):
         M = M if M is not None else self.zeros(self.n, NCOMP, NCELL)

@@ -432,3 +432,22 @@ def test_fp64_probe_runs(ot):
         ot.fp64_fma_probe(out, 148, 100, variant)
         torch.cuda.synchronize()
         assert np.all(np.isfinite(host(out))) and np.all(host(out) > 0)
+
+
+@pytest.mark.parametrize("mechanism", [0, 1, 2, 3])
+def test_completion_study_results_and_stats(ot, mechanism):
+    """Per-sub-grid launches over 4 streams, whatever signals their
+    completion, give the batched launch's result; the stats are sane."""
+    tree = _small_adaptive()
+    rho = synth.uniform_random_density(tree, seed=90)
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L_ref, Lc_ref = g.interactions(M, m)
+    stats, L, Lc = g.completion_study(M, m, mechanism, n_streams=4)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(Lc), host(Lc_ref))
+    scale = np.max(np.abs(host(L_ref)))
+    assert np.max(np.abs(host(L) - host(L_ref))) <= 1e-13 * scale
+    assert stats["launches"] == (1 if mechanism == 3 else tree.n)
+    assert 0 < stats["mean_latency_us"] <= stats["max_latency_us"]
+    assert stats["wall_ms"] > 0
