@@ -62,6 +62,12 @@ def _load():
     lib.oracle_pass_adjoint.restype = I
     lib.oracle_pass_adjoint_targets.argtypes = [I, P, P, P, ctypes.c_double, I, P, P, P, P, I, P]
     lib.oracle_pass_adjoint_targets.restype = ctypes.c_longlong
+    lib.oracle_moments_com.argtypes = [I, P, P, P, ctypes.c_double, P, P, P]
+    lib.oracle_moments_com.restype = I
+    lib.oracle_pass_centres.argtypes = [I, P, P, P, ctypes.c_double, P, P, P, I, I, P, P, P, P, P]
+    lib.oracle_pass_centres.restype = ctypes.c_longlong
+    lib.oracle_full_solve_com.argtypes = [I, P, P, P, ctypes.c_double, P, I, P, P]
+    lib.oracle_full_solve_com.restype = I
     lib.oracle_l2l.argtypes = [P, P, P]
     lib.oracle_l2l.restype = None
     lib.oracle_full_solve.argtypes = [I, P, P, P, ctypes.c_double, P, P, P]
@@ -122,7 +128,17 @@ def moments(tree, rho) -> np.ndarray:
     return M
 
 
-def run_pass(tree, pass_kind: str, M=None, m=None, targets=None):
+def moments_com(tree, rho):
+    """(M [n,20,512], C [n,3,512]): moments about centre-of-mass expansion centres."""
+    level, coord, leaf = _tree_args(tree)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    M = np.zeros((tree.n, NCOMP, NCELL))
+    C = np.zeros((tree.n, 3, NCELL))
+    _load().oracle_moments_com(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(rho), _p(M), _p(C))
+    return M, C
+
+
+def run_pass(tree, pass_kind: str, M=None, m=None, targets=None, centres=None):
     """Evaluate one pass for the listed targets ([k, 2] node, cell) or all cells.
 
     Returns dict(L=[k,20], S=[k,20], npairs=int) plus Lc, Sc ([k,3]) for the
@@ -147,17 +163,18 @@ def run_pass(tree, pass_kind: str, M=None, m=None, targets=None):
     S = np.zeros((nt, NCOMP))
     Lc = np.zeros((nt, 3))
     Sc = np.zeros((nt, 3))
-    npairs = _load().oracle_pass(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Mv), _p(mv), kind,
-                                 nt, _p(tg), _p(L), _p(Lc), _p(S), _p(Sc))
+    Cv = np.ascontiguousarray(centres, dtype=np.float64) if centres is not None else None
+    npairs = _load().oracle_pass_centres(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Mv), _p(mv), _p(Cv),
+                                         kind, nt, _p(tg), _p(L), _p(Lc), _p(S), _p(Sc))
     out = dict(L=L, S=S, npairs=int(npairs))
     if kind == 1:
         out.update(Lc=Lc, Sc=Sc)
     return out
 
 
-def run_pass_grid(tree, pass_kind, M=None, m=None):
+def run_pass_grid(tree, pass_kind, M=None, m=None, centres=None):
     """All cells; returns L [n,20,512] (and Lc [n,3,512]) in the library layout."""
-    r = run_pass(tree, pass_kind, M=M, m=m)
+    r = run_pass(tree, pass_kind, M=M, m=m, centres=centres)
     n = tree.n
     out = dict(L=r["L"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(),
                S=r["S"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(), npairs=r["npairs"])
@@ -194,12 +211,14 @@ def l2l(Lp, d) -> np.ndarray:
     return out
 
 
-def full_solve(tree, rho, with_s: bool = False):
+def full_solve(tree, rho, with_s: bool = False, com: bool = False):
     """[n, 20, 512] total local expansion of every cell (potential = [:, 0]);
-    with ``with_s`` also the matching sums of |terms|."""
+    with ``with_s`` also the matching sums of |terms|; ``com`` uses
+    centre-of-mass expansion centres (expansions about the cells' centres of
+    mass, shifted between them)."""
     level, coord, leaf = _tree_args(tree)
     rho = np.ascontiguousarray(rho, dtype=np.float64)
     L = np.zeros((tree.n, NCOMP, NCELL))
     S = np.zeros((tree.n, NCOMP, NCELL)) if with_s else None
-    _load().oracle_full_solve(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(rho), _p(L), _p(S))
+    _load().oracle_full_solve_com(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(rho), int(com), _p(L), _p(S))
     return (L, S) if with_s else L

@@ -311,15 +311,100 @@ int oracle_moments(int n, const int* level, const int* coord, const uint8_t* is_
     return 0;
 }
 
+/* Centre-of-mass variant: C [n][3][512] receives every cell's expansion
+ * centre -- the geometric centre for a childless node's uniform cube, the
+ * mass-weighted mean of the 8 children's centres otherwise (geometric if the
+ * mass is zero) -- and M the moments about it (exact binomial shift of the
+ * children's moments by d = C_child - C_parent). */
+int oracle_moments_com(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
+                       const double* rho, double* M, double* C) {
+    otree t;
+    tree_init(&t, n, level, coord, is_leaf, h0);
+    for (int l = t.max_level; l >= 0; l--) {
+        double h = h0 / pow(2.0, l);
+        for (int i = 0; i < n; i++) {
+            if (level[i] != l) continue;
+            int child[8], nchild = 0;
+            for (int b = 0; b < 8; b++) {
+                child[b] = tree_find(&t, l + 1, 2L * coord[3 * i] + (b & 1), 2L * coord[3 * i + 1] + ((b >> 1) & 1),
+                                     2L * coord[3 * i + 2] + ((b >> 2) & 1));
+                if (child[b] >= 0) nchild++;
+            }
+            for (int a = 0; a < NCELL; a++) {
+                long gP[3] = {8L * coord[3 * i] + (a & 7), 8L * coord[3 * i + 1] + ((a >> 3) & 7),
+                              8L * coord[3 * i + 2] + (a >> 6)};
+                double* out = M + ((size_t)i * NCOMP) * NCELL + a;
+                double* cen = C + ((size_t)i * 3) * NCELL + a;
+                if (nchild < 8) {
+                    for (int ax = 0; ax < 3; ax++) cen[(size_t)ax * NCELL] = (gP[ax] + 0.5) * h;
+                    for (int c = 0; c < NCOMP; c++) {
+                        double v = rho[(size_t)i * NCELL + a];
+                        for (int ax = 0; ax < 3; ax++) v *= cube_axis_moment(comp_exp[c][ax], h);
+                        out[(size_t)c * NCELL] = v;
+                    }
+                    continue;
+                }
+                /* children cells: positions, masses, centres */
+                int cn[8], cc[8];
+                double mass = 0.0, wsum[3] = {0.0, 0.0, 0.0};
+                for (int b = 0; b < 8; b++) {
+                    long gc[3] = {2 * gP[0] + (b & 1), 2 * gP[1] + ((b >> 1) & 1), 2 * gP[2] + ((b >> 2) & 1)};
+                    cn[b] = tree_find(&t, l + 1, gc[0] >> 3, gc[1] >> 3, gc[2] >> 3);
+                    cc[b] = (int)((gc[0] & 7) + 8 * (gc[1] & 7) + 64 * (gc[2] & 7));
+                    double mc = M[((size_t)cn[b] * NCOMP) * NCELL + cc[b]];
+                    mass += mc;
+                    for (int ax = 0; ax < 3; ax++) wsum[ax] += mc * C[((size_t)cn[b] * 3 + ax) * NCELL + cc[b]];
+                }
+                double XP[3];
+                for (int ax = 0; ax < 3; ax++) XP[ax] = (mass != 0.0) ? wsum[ax] / mass : (gP[ax] + 0.5) * h;
+                double acc[NCOMP];
+                for (int c = 0; c < NCOMP; c++) acc[c] = 0.0;
+                for (int b = 0; b < 8; b++) {
+                    const double* Mc = M + (size_t)cn[b] * NCOMP * NCELL + cc[b];
+                    double d[3];
+                    for (int ax = 0; ax < 3; ax++) d[ax] = C[((size_t)cn[b] * 3 + ax) * NCELL + cc[b]] - XP[ax];
+                    for (int K = 0; K < NCOMP; K++) {
+                        const int* e = comp_exp[K];
+                        for (int I = 0; I < NCOMP; I++) {
+                            const int* f = comp_exp[I];
+                            if (f[0] > e[0] || f[1] > e[1] || f[2] > e[2]) continue;
+                            double term = Mc[(size_t)I * NCELL];
+                            for (int ax = 0; ax < 3; ax++)
+                                term *= binom(e[ax], f[ax]) * pow(d[ax], e[ax] - f[ax]);
+                            acc[K] += term;
+                        }
+                    }
+                }
+                for (int c = 0; c < NCOMP; c++) out[(size_t)c * NCELL] = acc[c];
+                for (int ax = 0; ax < 3; ax++) cen[(size_t)ax * NCELL] = XP[ax];
+            }
+        }
+    }
+    tree_free(&t);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* interaction passes                                                        */
 /* ------------------------------------------------------------------------ */
+
+/* expansion centre of a source found by source_lookup: from C for real
+ * cells, the geometric centre of the virtual cell otherwise */
+static void source_centre(const otree* t, int cls, int B, int cb, int l, const long* q, const double* C,
+                          double* XB) {
+    if (cls == 3 || !C) {
+        double h = t->h0 / pow(2.0, l);
+        for (int ax = 0; ax < 3; ax++) XB[ax] = (q[ax] + 0.5) * h;
+        return;
+    }
+    for (int ax = 0; ax < 3; ax++) XB[ax] = C[((size_t)B * 3 + ax) * NCELL + cb];
+}
 
 static const double INV_FACT[4] = {1.0, 1.0, 0.5, 1.0 / 6.0};
 
 /* One target cell of one pass.  pass 1: multipole sources (M), pass 2: point
  * masses (m).  Writes L[20] (+ Lc[3] for pass 1), S = sum of |terms|. */
-static long long target_pass(const otree* t, int pass, const double* M, const double* m,
+static long long target_pass(const otree* t, int pass, const double* M, const double* m, const double* C,
                              int T, int a, double* L, double* Lc, double* S, double* Sc) {
     int l = t->level[T];
     double h = t->h0 / pow(2.0, l);
@@ -344,6 +429,11 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                 if (pass == 1 && cls != 1) continue;
                 if (pass == 2 && cls != 2 && cls != 3) continue;
                 double R[3] = {-o[0] * h, -o[1] * h, -o[2] * h};   /* X_A - X_B */
+                if (C) {
+                    double XB[3];
+                    source_centre(t, cls, B, cb, l, q, C, XB);
+                    for (int ax = 0; ax < 3; ax++) R[ax] = C[((size_t)T * 3 + ax) * NCELL + a] - XB[ax];
+                }
                 double D[NCOMP4];
                 oracle_D(R, D);
                 npairs++;
@@ -400,9 +490,21 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
 
 /* targets: [nt][2] (node, cell) or NULL for every cell of every node in order.
  * L, S: [nt][20]; Lc, Sc: [nt][3] (pass 1 only; may be NULL). */
+long long oracle_pass_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
+                              const double* M, const double* m, const double* C, int pass, int nt,
+                              const int* targets, double* L, double* Lc, double* S, double* Sc);
+
 long long oracle_pass(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
                       const double* M, const double* m, int pass, int nt, const int* targets,
                       double* L, double* Lc, double* S, double* Sc) {
+    return oracle_pass_centres(n, level, coord, is_leaf, h0, M, m, NULL, pass, nt, targets, L, Lc, S, Sc);
+}
+
+/* The same with expansion centres C [n][3][512] (NULL: geometric): the pair
+ * set is unchanged, R = C_A - C_B. */
+long long oracle_pass_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
+                              const double* M, const double* m, const double* C, int pass, int nt,
+                              const int* targets, double* L, double* Lc, double* S, double* Sc) {
     otree t;
     tree_init(&t, n, level, coord, is_leaf, h0);
     if (!targets) nt = n * NCELL;
@@ -412,7 +514,7 @@ long long oracle_pass(int n, const int* level, const int* coord, const uint8_t* 
         int T = targets ? targets[2 * k] : k / NCELL;
         int a = targets ? targets[2 * k + 1] : k % NCELL;
         double lc[3], sc[3];
-        total += target_pass(&t, pass, M, m, T, a, L + (size_t)k * NCOMP, lc, S + (size_t)k * NCOMP, sc);
+        total += target_pass(&t, pass, M, m, C, T, a, L + (size_t)k * NCOMP, lc, S + (size_t)k * NCOMP, sc);
         if (Lc) for (int i = 0; i < 3; i++) Lc[(size_t)k * 3 + i] = lc[i];
         if (Sc) for (int i = 0; i < 3; i++) Sc[(size_t)k * 3 + i] = sc[i];
     }
@@ -544,8 +646,18 @@ void oracle_l2l(const double* Lp, const double* d, double* Lc) {
  * Ltot [n][20][512] receives the total local expansion of every cell; Stot
  * (same shape, may be NULL) the sum of |terms| behind each coefficient: the
  * passes' sums, carried down by the same shift with |d|. */
+int oracle_full_solve_com(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
+                          const double* rho, int com, double* Ltot, double* Stot);
+
 int oracle_full_solve(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
                       const double* rho, double* Ltot, double* Stot) {
+    return oracle_full_solve_com(n, level, coord, is_leaf, h0, rho, 0, Ltot, Stot);
+}
+
+/* com = 1: centre-of-mass expansion centres (moments, passes and the L2L
+ * shifts between them); com = 0: geometric centres. */
+int oracle_full_solve_com(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
+                          const double* rho, int com, double* Ltot, double* Stot) {
     otree t;
     tree_init(&t, n, level, coord, is_leaf, h0);
     size_t nn = (size_t)n * NCOMP * NCELL;
@@ -555,11 +667,13 @@ int oracle_full_solve(int n, const int* level, const int* coord, const uint8_t* 
     double* L2 = (double*)malloc(sizeof(double) * (size_t)n * NCELL * NCOMP);
     double* S = (double*)malloc(sizeof(double) * (size_t)n * NCELL * NCOMP);
     double* S2 = (double*)malloc(sizeof(double) * (size_t)n * NCELL * NCOMP);
-    oracle_moments(n, level, coord, is_leaf, h0, rho, M);
+    double* C = com ? (double*)malloc(sizeof(double) * (size_t)n * 3 * NCELL) : NULL;
+    if (com) oracle_moments_com(n, level, coord, is_leaf, h0, rho, M, C);
+    else oracle_moments(n, level, coord, is_leaf, h0, rho, M);
     for (int i = 0; i < n; i++)
         for (int a = 0; a < NCELL; a++) m[(size_t)i * NCELL + a] = M[((size_t)i * NCOMP) * NCELL + a];
-    oracle_pass(n, level, coord, is_leaf, h0, M, m, 1, 0, NULL, L1, NULL, S, NULL);
-    oracle_pass(n, level, coord, is_leaf, h0, M, m, 2, 0, NULL, L2, NULL, S2, NULL);
+    oracle_pass_centres(n, level, coord, is_leaf, h0, M, m, C, 1, 0, NULL, L1, NULL, S, NULL);
+    oracle_pass_centres(n, level, coord, is_leaf, h0, M, m, C, 2, 0, NULL, L2, NULL, S2, NULL);
     for (int i = 0; i < n; i++)
         for (int a = 0; a < NCELL; a++)
             for (int c = 0; c < NCOMP; c++) {
@@ -583,7 +697,9 @@ int oracle_full_solve(int n, const int* level, const int* coord, const uint8_t* 
                 double Lp[NCOMP], Lc[NCOMP];
                 for (int c = 0; c < NCOMP; c++) Lp[c] = Ltot[((size_t)P * NCOMP + c) * NCELL + cp];
                 double d[3];
-                for (int ax = 0; ax < 3; ax++) d[ax] = ((g[ax] & 1) - 0.5) * h;
+                for (int ax = 0; ax < 3; ax++)
+                    d[ax] = com ? C[((size_t)i * 3 + ax) * NCELL + a] - C[((size_t)P * 3 + ax) * NCELL + cp]
+                                : ((g[ax] & 1) - 0.5) * h;
                 oracle_l2l(Lp, d, Lc);
                 for (int c = 0; c < NCOMP; c++) Ltot[((size_t)i * NCOMP + c) * NCELL + a] += Lc[c];
                 if (Stot) {
@@ -595,7 +711,7 @@ int oracle_full_solve(int n, const int* level, const int* coord, const uint8_t* 
             }
         }
     }
-    free(M); free(m); free(L1); free(L2); free(S); free(S2);
+    free(M); free(m); free(L1); free(L2); free(S); free(S2); free(C);
     tree_free(&t);
     return 0;
 }

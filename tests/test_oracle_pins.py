@@ -508,3 +508,85 @@ def test_virtual_descendants_equal_refined_leaves(orc):
     r2 = orc.run_pass(ref, "monopole", m=m2, targets=targets)
     assert r1["npairs"] == r2["npairs"]
     np.testing.assert_allclose(r1["L"], r2["L"], rtol=0, atol=1e-14 * np.max(r1["S"]))
+
+
+# ---------------------------------------------------------------------------
+# centre-of-mass expansion centres
+# ---------------------------------------------------------------------------
+
+def test_com_moments_exact(orc):
+    """Root cells of a two-level tree: the centre is the mass-weighted mean of
+    the 8 child cubes' centres, the dipole vanishes, and every moment equals
+    the exact integral of the piecewise-constant density about that centre."""
+    tree = synth.uniform_tree(1, h_leaf=1.0)
+    rng = np.random.default_rng(21)
+    rho = rng.integers(1, 9, size=(tree.n, 512)).astype(float) / 4.0   # exact in binary
+    M, C = orc.moments_com(tree, rho)
+    idx = tree.index()
+    root = idx[(0, 0, 0, 0)]
+    for cell in (0, 77, 300, 511):
+        gp = np.array([cell % 8, (cell // 8) % 8, cell // 64])
+        kids = []
+        for b in itertools.product((0, 1), repeat=3):
+            gc = 2 * gp + np.array(b)
+            node = idx[(1, *(gc // 8))]
+            kids.append((Fraction(rho[node, int((gc % 8) @ np.array([1, 8, 64]))]), gc))
+        mass = sum(r for r, _ in kids)
+        X = [sum(r * (Fraction(int(gc[a])) + Fraction(1, 2)) for r, gc in kids) / mass for a in range(3)]
+        np.testing.assert_allclose(C[root, :, cell], [float(x) for x in X], rtol=1e-15)
+        exact = np.zeros(20)
+        for c, e in enumerate(EXP20):
+            v = Fraction(0)
+            for r, gc in kids:
+                t = r
+                for a in range(3):
+                    t *= _axis_int(e[a], Fraction(int(gc[a])) - X[a], Fraction(int(gc[a]) + 1) - X[a])
+                v += t
+            exact[c] = float(v)
+        scale = exact[0] * np.array([1.0] + [1.0] * 3 + [1.0] * 6 + [1.0] * 10)
+        np.testing.assert_allclose(M[root, :, cell], exact, rtol=0, atol=1e-13 * scale.max())
+        assert np.max(np.abs(M[root, 1:4, cell])) <= 1e-14 * exact[0]
+
+
+def test_off_centre_expansions_taylor_order(orc):
+    """Target and source expansions about arbitrary points inside their cells:
+    the local model of a random point cluster still errs as O(s^4)."""
+    tree = _single_node_tree()
+    rng = np.random.default_rng(22)
+    mu, u = _cluster(rng)
+    A, B = (0, 0, 0), (4, 1, 0)
+    XA = np.array(A) + 0.5 + rng.uniform(-0.3, 0.3, 3)
+    XB = np.array(B) + 0.5 + rng.uniform(-0.3, 0.3, 3)
+    dirs = rng.standard_normal((6, 3))
+    errs, scales = [], [0.4, 0.2, 0.1, 0.05]
+    for s in scales:
+        M = np.zeros((1, 20, 512))
+        C = synth.cell_centres(tree, 0).T.reshape(1, 3, 512).copy()
+        C[0, :, _cell(*A)] = XA
+        C[0, :, _cell(*B)] = XB
+        pos = XB + s * u
+        M[0, :, _cell(*B)] = point_cluster_moments(mu, pos, XB)
+        r = orc.run_pass(tree, "multipole", M=M, targets=[[0, _cell(*A)]], centres=C)
+        L = r["L"][0]
+        e = 0.0
+        for d in dirs:
+            delta = s * d / np.linalg.norm(d)
+            exact = -np.sum(mu / np.linalg.norm(XA + delta - pos, axis=1))
+            e = max(e, abs(taylor(L, delta) - exact))
+        errs.append(e)
+    order = _order(errs, scales)
+    assert 3.7 < order < 4.4, (errs, order)
+
+
+def test_com_full_solve_matches_direct_sum(orc):
+    tree = synth.uniform_tree(1, 1.0)
+    rng = np.random.default_rng(23)
+    rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    L = orc.full_solve(tree, rho, com=True)
+    pos, ids = _leaf_cells(tree)
+    m = rho[ids[:, 0], ids[:, 1]]
+    for k in rng.choice(len(pos), 200, replace=False):
+        d = np.linalg.norm(pos - pos[k], axis=1)
+        d[k] = np.inf
+        exact = -np.sum(m / d)
+        assert abs(L[ids[k, 0], 0, ids[k, 1]] - exact) < 2e-4 * abs(exact)
