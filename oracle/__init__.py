@@ -62,6 +62,8 @@ def _load():
     lib.oracle_pass_adjoint.restype = I
     lib.oracle_pass_adjoint_targets.argtypes = [I, P, P, P, ctypes.c_double, I, P, P, P, P, I, P]
     lib.oracle_pass_adjoint_targets.restype = ctypes.c_longlong
+    lib.oracle_pass_adjoint_centres.argtypes = [I, P, P, P, ctypes.c_double, P, I, P, P, P, P, I, P]
+    lib.oracle_pass_adjoint_centres.restype = ctypes.c_longlong
     lib.oracle_moments_com.argtypes = [I, P, P, P, ctypes.c_double, P, P, P]
     lib.oracle_moments_com.restype = I
     lib.oracle_pass_centres.argtypes = [I, P, P, P, ctypes.c_double, P, P, P, I, I, P, P, P, P, P]
@@ -184,10 +186,11 @@ def run_pass_grid(tree, pass_kind, M=None, m=None, centres=None):
     return out
 
 
-def pass_adjoint(tree, pass_kind: str, Lbar, with_s: bool = False, targets=None):
+def pass_adjoint(tree, pass_kind: str, Lbar, with_s: bool = False, targets=None, centres=None):
     """Transposed sum of a pass: Mbar [n,20,512] (multipole) or mbar [n,512];
     with ``with_s`` also the matching sum of |terms|.  ``targets`` ([k, 2]
-    node, cell) restricts the scatter to those target cells."""
+    node, cell) restricts the scatter to those target cells; ``centres``
+    ([n, 3, 512]) are expansion centres held fixed (default geometric)."""
     level, coord, leaf = _tree_args(tree)
     kind = {"multipole": 1, "monopole": 2}[pass_kind]
     Lbar = np.ascontiguousarray(Lbar, dtype=np.float64)
@@ -195,8 +198,10 @@ def pass_adjoint(tree, pass_kind: str, Lbar, with_s: bool = False, targets=None)
     mbar = np.zeros((tree.n, NCELL))
     S = np.zeros_like(Mbar if kind == 1 else mbar)
     tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int32).reshape(-1, 2)
-    npairs = _load().oracle_pass_adjoint_targets(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, kind, _p(Lbar),
-                                        _p(Mbar), _p(mbar), _p(S), 0 if tg is None else tg.shape[0], _p(tg))
+    Cv = None if centres is None else np.ascontiguousarray(centres, dtype=np.float64)
+    npairs = _load().oracle_pass_adjoint_centres(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Cv), kind,
+                                                 _p(Lbar), _p(Mbar), _p(mbar), _p(S),
+                                                 0 if tg is None else tg.shape[0], _p(tg))
     out = Mbar if kind == 1 else mbar
     if with_s == "pairs":
         return out, int(npairs)

@@ -537,11 +537,24 @@ int oracle_pass_adjoint(int n, const int* level, const int* coord, const uint8_t
     return 0;
 }
 
+long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf,
+                                      double h0, const double* C, int pass, const double* Lbar, double* Mbar,
+                                      double* mbar, double* Sbar, int nt, const int* targets);
+
 /* Same, scattering only from the listed target cells ([nt][2] node, cell);
  * returns the number of pairs walked. */
 long long oracle_pass_adjoint_targets(int n, const int* level, const int* coord, const uint8_t* is_leaf,
                                       double h0, int pass, const double* Lbar, double* Mbar, double* mbar,
                                       double* Sbar, int nt, const int* targets) {
+    return oracle_pass_adjoint_centres(n, level, coord, is_leaf, h0, NULL, pass, Lbar, Mbar, mbar, Sbar, nt,
+                                       targets);
+}
+
+/* The same with expansion centres C [n][3][512] held fixed (NULL: geometric):
+ * the pairs are those of the forward pass, R = C_A - C_B as there. */
+long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf,
+                                      double h0, const double* C, int pass, const double* Lbar, double* Mbar,
+                                      double* mbar, double* Sbar, int nt, const int* targets) {
     otree t;
     long long npairs = 0;
     tree_init(&t, n, level, coord, is_leaf, h0);
@@ -574,6 +587,11 @@ long long oracle_pass_adjoint_targets(int n, const int* level, const int* coord,
                         if (pass == 2 && cls != 2 && cls != 3) continue;
                         npairs++;
                         double R[3] = {-o[0] * h, -o[1] * h, -o[2] * h};
+                        if (C) {
+                            double XB[3];
+                            source_centre(&t, cls, B, cb, l, q, C, XB);
+                            for (int ax = 0; ax < 3; ax++) R[ax] = C[((size_t)T * 3 + ax) * NCELL + a] - XB[ax];
+                        }
                         double D[NCOMP4];
                         oracle_D(R, D);
                         if (pass == 2) {
