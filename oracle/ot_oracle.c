@@ -262,6 +262,9 @@ int oracle_moments(int n, const int* level, const int* coord, const uint8_t* is_
     tree_init(&t, n, level, coord, is_leaf, h0);
     for (int l = t.max_level; l >= 0; l--) {
         double h = h0 / pow(2.0, l);
+        /* the nodes of one level are independent (each reads only the
+         * finished level below and writes only its own cells) */
+#pragma omp parallel for schedule(dynamic, 1)
         for (int i = 0; i < n; i++) {
             if (level[i] != l) continue;
             int nchild = 0;
@@ -322,6 +325,9 @@ int oracle_moments_com(int n, const int* level, const int* coord, const uint8_t*
     tree_init(&t, n, level, coord, is_leaf, h0);
     for (int l = t.max_level; l >= 0; l--) {
         double h = h0 / pow(2.0, l);
+        /* the nodes of one level are independent (each reads only the
+         * finished level below and writes only its own cells) */
+#pragma omp parallel for schedule(dynamic, 1)
         for (int i = 0; i < n; i++) {
             if (level[i] != l) continue;
             int child[8], nchild = 0;
