@@ -50,11 +50,11 @@ def test_df64_all_cells(ot, orc, which):
     rho = synth.uniform_random_density(tree, seed=81)
     g = ot.OTGrid.from_tree(tree)
     g.set_precision(ot.OT_PREC_DF64_POINT_MASS)
-    M, m = g.moments(dev(rho))
-    L, Lc = g.interactions(M, m)
+    Mh = orc.moments(tree, rho)            # oracle inputs never come from the GPU
+    mh = np.ascontiguousarray(Mh[:, 0, :])
+    L, Lc = g.interactions(dev(Mh), dev(mh))
     torch.cuda.synchronize()
     g.check()
-    Mh, mh = host(M), host(m)
     tg = np.stack(np.meshgrid(np.arange(tree.n), np.arange(512), indexing="ij"), -1).reshape(-1, 2).astype(np.int32)
     r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
     r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
@@ -67,7 +67,9 @@ def test_df64_all_cells(ot, orc, which):
 def test_df64_full_size_sampled(ot, orc, cfg):
     tree, rho = synth.config2() if cfg == "config2" else synth.config5_step(3)
     g = ot.OTGrid.from_tree(tree)
-    M, m = g.moments(dev(rho))
+    Mh = orc.moments(tree, rho)
+    mh = np.ascontiguousarray(Mh[:, 0, :])
+    M, m = dev(Mh), dev(mh)
     L64, _ = g.interactions(M, m, want_lc=False)
     L64 = host(L64)
     g.set_precision(ot.OT_PREC_DF64_POINT_MASS)
@@ -75,8 +77,8 @@ def test_df64_full_size_sampled(ot, orc, cfg):
     torch.cuda.synchronize()
     Ldf = host(Ldf)
     tg = sample_targets(tree, 200, 82)
-    r2 = orc.run_pass(tree, "monopole", m=host(m), targets=tg)
-    r1 = orc.run_pass(tree, "multipole", M=host(M), targets=tg)
+    r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
+    r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
     assert_parity(Ldf[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
     # every cell: double-float within 1e-12 of the FP64 path relative to the
     # coefficient-order block magnitude of the FP64 result

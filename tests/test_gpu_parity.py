@@ -39,10 +39,19 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def gpu_fused(ot, tree, rho=None, M=None, m=None, schedule=None):
+def oracle_moments(orc, tree, rho):
+    """(M, m) from the oracle: inputs of the pass parity tests never come from
+    the GPU (the GPU moments are checked against these separately)."""
+    M = orc.moments(tree, rho)
+    return M, np.ascontiguousarray(M[:, 0, :])
+
+
+def gpu_fused(ot, tree, rho=None, M=None, m=None, schedule=None, orc=None):
     g = ot.OTGrid.from_tree(tree)
     if schedule is not None:
         g.set_schedule(*schedule)
+    if M is None and orc is not None:
+        M, m = oracle_moments(orc, tree, rho)
     if M is None:
         Md, md = g.moments(dev(rho))
     else:
@@ -111,10 +120,10 @@ def test_config1_multipole_all_cells(ot, orc):
     """One isolated sub-grid of multipole cells (monopole + quadrupole moments)."""
     tree, rho = synth.config1()
     g = ot.OTGrid.from_tree(tree)
-    M, m = g.moments(dev(rho))
-    L, Lc = g.multipole(M)
+    M, _ = oracle_moments(orc, tree, rho)
+    L, Lc = g.multipole(dev(M))
     torch.cuda.synchronize()
-    r = orc.run_pass_grid(tree, "multipole", M=host(M))
+    r = orc.run_pass_grid(tree, "multipole", M=M)
     assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
     assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
     assert g.info()["pairs_multipole"] == r["npairs"]
@@ -163,7 +172,7 @@ def test_monopole_uniform_level(ot, orc):
 def test_fused_uniform_tree_with_coarse_levels(ot, orc):
     tree = synth.uniform_tree(1, 1.0)
     rho = synth.uniform_random_density(tree, seed=45)
-    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
     tg = all_targets(tree)
     Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
     assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
@@ -184,7 +193,7 @@ def test_fused_adaptive_virtual_descendants(ot, orc):
     pairs with refined (multipole) neighbours, mixed-class warps."""
     tree = _small_adaptive()
     rho = synth.uniform_random_density(tree, seed=46)
-    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
     info = g.info()
     assert info["pairs_virtual"] > 0 and info["n_virtual"] > 0
     tg = all_targets(tree)
@@ -341,7 +350,7 @@ def test_autograd_matches_central_differences(ot):
 
 def test_config2_full_size_sampled(ot, orc):
     tree, rho = synth.config2()
-    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
     tg = np.concatenate([sample_targets(tree, 96, 61, levels=[3]), sample_targets(tree, 48, 62, levels=[0, 1, 2])])
     Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
     assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
@@ -388,7 +397,7 @@ def test_adaptive_workloads_sampled(ot, orc, cfg):
         tree, rho, _ = synth.config3()
     else:
         tree, rho = synth.config5_step(0)
-    g, M, m, L, Lc = gpu_fused(ot, tree, rho)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
     info = g.info()
     assert info["pairs_virtual"] > 0
     tg = sample_targets(tree, 160, 65)
@@ -419,9 +428,12 @@ def test_abi_rejects_bad_input(ot):
     st = lib.ot_multipole_interactions(g.handle, ctypes.c_void_p(M.data_ptr() + 8), None,
                                        ctypes.c_void_p(L.data_ptr()), None, None)
     assert st == _lib.OT_EINVAL and b"aligned" in lib.ot_last_error()
-    st = lib.ot_multipole_interactions(g.handle, ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(M.data_ptr()),
+    st = lib.ot_multipole_interactions(g.handle, ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(M.data_ptr() + 8),
                                        ctypes.c_void_p(L.data_ptr()), None, None)
-    assert st == _lib.OT_ENOTSUP
+    assert st == _lib.OT_EINVAL and b"C is not 16-byte aligned" in lib.ot_last_error()
+    st = lib.ot_interactions_com(g.handle, None, None, ctypes.c_void_p(M.data_ptr()),
+                                 ctypes.c_void_p(L.data_ptr()), None, None)
+    assert st == _lib.OT_EINVAL and b"both NULL" in lib.ot_last_error()
     assert lib.ot_interactions(None, None, None, None, None, None) == _lib.OT_EINVAL
     g.check()
 
