@@ -111,6 +111,9 @@ typedef struct {
     int32_t warps_per_block;       /* tile shape in use */
     int32_t blocks_per_sm;
     int32_t graphs_enabled;
+    int64_t flops_fwd_com;         /* algorithmic FLOPs of ot_interactions_com (both passes, with Lc):
+                                      per pair the derivative evaluation plus the contraction */
+    int64_t flops_adj_com;         /* the same for ot_interactions_backward_com */
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the
@@ -142,7 +145,9 @@ ot_status ot_moments_backward(ot_grid* grid, const double* Mbar, const double* m
  * Lc [n][3][512] (angular-momentum correction, non-leaf targets with
  * non-zero mass, multipole sources only; may be NULL) overwritten:
  *   Lc_A[i] = -(1/6) sum_B sum_{jkl} (M3_B - (m_B/m_A) M3_A)[jkl] d^{ijkl} G.
- * `centres` must be NULL (geometric cell centres), else OT_ENOTSUP. */
+ * `centres` NULL: geometric cell centres.  Non-NULL: explicit expansion
+ * centres [n][3][512], the same as ot_interactions_com(grid, M, NULL,
+ * centres, L, Lc, stream). */
 ot_status ot_multipole_interactions(ot_grid* grid, const double* M, const double* centres,
                                     double* L, double* Lc, void* stream);
 
@@ -183,6 +188,47 @@ ot_status ot_l2l(ot_grid* grid, double* L, void* stream);
 /* Adjoint of ot_l2l, in place on Lbar [n][20][512]: from the deepest level
  * up, every parent cell adds the transposed shifts of its children's Lbar. */
 ot_status ot_l2l_backward(ot_grid* grid, double* Lbar, void* stream);
+
+/* Centre-of-mass expansion centres (the octree FMM of Sec. 2.1 expands
+ * every cell about its centre of mass).  Moments and Taylor coefficients are
+ * then taken about per-cell centres C [n][3][512] (x, y, z planes; positions
+ * in the units of h0) instead of the geometric centres; the pair set of both
+ * passes is unchanged, and every pair evaluates the derivatives of G at
+ * R = C_A - C_B itself (sqrt, division and the order 0..4 polynomials) rather
+ * than reading the integer-offset table.  Point-mass sources sit at their
+ * geometric cell centres (a uniform cube's centre of mass), virtual
+ * descendants at their virtual cells' centres.
+ *
+ * ot_moments_com: rho [n][512] -> M [n][20][512], m [n][512], C [n][3][512]
+ * (all overwritten).  A node without all 8 children: C = geometric centre,
+ * M = uniform-cube moments (as ot_moments).  A node with 8 children, from the
+ * deepest level up: C = mass-weighted mean of the 8 child cells' centres
+ * (the geometric centre where that mass is exactly 0), M = the children's
+ * moments shifted binomially to C. */
+ot_status ot_moments_com(ot_grid* grid, const double* rho, double* M, double* m, double* C,
+                         void* stream);
+
+/* Both passes (or one: M or m NULL, not both) with explicit centres C, in one
+ * persistent launch (graph-replayed when graphs are enabled).  L [n][20][512]
+ * OVERWRITTEN with the sum of the passes run; Lc [n][3][512] (may be NULL;
+ * multipole pass only) overwritten, as in ot_multipole_interactions.  Always
+ * the persistent schedule; FP64 throughout (ot_set_precision does not apply).
+ * Pairs closer than the opening rule admits are the caller's concern: C
+ * must keep every pair's |R| > 0 (true for centres inside their cells). */
+ot_status ot_interactions_com(ot_grid* grid, const double* M, const double* m, const double* C,
+                              double* L, double* Lc, void* stream);
+
+/* Adjoint of ot_interactions_com with the centres held fixed (a partial
+ * gradient: the dependence of C on the densities is not differentiated).
+ * Mbar [n][20][512], mbar [n][512] overwritten (either may be NULL to skip);
+ * always the fixed-order gather, bit-reproducible. */
+ot_status ot_interactions_backward_com(ot_grid* grid, const double* Lbar, const double* C,
+                                       double* Mbar, double* mbar, void* stream);
+
+/* Down-pass with explicit centres, in place on L: d = C_child - C_parent per
+ * child cell (otherwise as ot_l2l); and its adjoint with C fixed. */
+ot_status ot_l2l_com(ot_grid* grid, const double* C, double* L, void* stream);
+ot_status ot_l2l_com_backward(ot_grid* grid, const double* C, double* Lbar, void* stream);
 
 /* Arithmetic of the point-mass contractions of the forward passes.
  * OT_PREC_FP64 (default): FP64 FMAs throughout.

@@ -23,7 +23,8 @@ EXPORTS = ["ot_grid_create", "ot_grid_destroy", "ot_grid_info", "ot_moments", "o
            "ot_interactions_backward", "ot_set_schedule", "ot_autotune", "ot_grid_check",
            "ot_fp64_fma_probe", "ot_multipole_interactions_noalloc", "ot_l2l", "ot_l2l_backward",
            "ot_set_deterministic", "ot_set_precision", "ot_completion_study",
-           "ot_last_error"]
+           "ot_moments_com", "ot_interactions_com", "ot_interactions_backward_com", "ot_l2l_com",
+           "ot_l2l_com_backward", "ot_last_error"]
 
 
 class OTError(RuntimeError):
@@ -46,7 +47,8 @@ class GridInfo(ctypes.Structure):
                 ("pairs_monopole", ctypes.c_int64), ("pairs_virtual", ctypes.c_int64),
                 ("pairs_angular", ctypes.c_int64), ("lanes_fwd", ctypes.c_int64), ("flops_fwd", ctypes.c_int64),
                 ("flops_adj", ctypes.c_int64), ("ops_fwd", ctypes.c_int64), ("ops_adj", ctypes.c_int64), ("schedule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("graphs_enabled", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("graphs_enabled", ctypes.c_int32),
+                ("flops_fwd_com", ctypes.c_int64), ("flops_adj_com", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -89,6 +91,11 @@ def load():
         "ot_set_deterministic": [P, I],
         "ot_set_precision": [P, I],
         "ot_completion_study": [P, P, P, P, P, I, I, ctypes.c_double, ctypes.POINTER(CompletionStats)],
+        "ot_moments_com": [P, P, P, P, P, P],
+        "ot_interactions_com": [P, P, P, P, P, P, P],
+        "ot_interactions_backward_com": [P, P, P, P, P, P],
+        "ot_l2l_com": [P, P, P, P],
+        "ot_l2l_com_backward": [P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -77,6 +77,81 @@ def t4_expr(e):
     return f"(-{t4_expr(add(base, (2, 0, 0)))} - {t4_expr(add(base, (0, 2, 0)))})"
 
 
+def _flops(e):
+    """Algorithmic FLOPs of a sympy expression as the emitted code evaluates
+    it: n-1 per n-ary sum or product (a factor -1 is a sign, not a product),
+    k-1 products for an integer power k."""
+    import sympy
+    if e.is_Atom:
+        return 0
+    sub = sum(_flops(a) for a in e.args)
+    if e.is_Add:
+        return sub + len(e.args) - 1
+    if e.is_Mul:
+        factors = [a for a in e.args if a != -1]
+        return sub + max(len(factors) - 1, 0)
+    if e.is_Pow and e.exp.is_Integer and e.exp > 1:
+        return _flops(e.base) + int(e.exp) - 1
+    raise ValueError(f"unexpected node {e.func}")
+
+
+def deriv_flops(ncomp):
+    """FLOPs of one call of the generated derivative routine for the first
+    `ncomp` components: r^2 (5), 1/sqrt (2), r^-2 and the powers r^-(2k+1),
+    the cse'd polynomials and one scaling product per component."""
+    import sympy
+    polys, repl, reduced = _deriv_polys(ncomp)
+    kmax = max(k for k, _ in polys)
+    return 5 + 2 + 1 + kmax + sum(_flops(v) for _, v in repl) + sum(_flops(P) for P in reduced) + ncomp
+
+
+def _deriv_polys(ncomp):
+    import sympy
+    x, y, z = sympy.symbols("x y z", real=True)
+    r2 = x * x + y * y + z * z
+    G = -1 / sympy.sqrt(r2)
+    polys = []
+    for e in ROW[:ncomp]:
+        k = rank(e)
+        expr = sympy.diff(G, x, e[0], y, e[1], z, e[2]) if k else G
+        P = sympy.expand(sympy.simplify(expr * r2 ** sympy.Rational(2 * k + 1, 2)))
+        assert P.is_polynomial(x, y, z), (e, P)
+        polys.append((k, P))
+    repl, reduced = sympy.cse([P for _, P in polys], symbols=sympy.numbered_symbols("t"))
+    return polys, repl, reduced
+
+
+def deriv_code(name, ncomp):
+    """Straight-line code for the first `ncomp` row-layout derivatives of
+    G = -1/r at R = (x, y, z): with sympy, d^K G = P_K(x, y, z) r^-(2k+1) for
+    a polynomial P_K of degree k; the polynomials share subexpressions (cse)."""
+    import sympy
+    polys, repl, reduced = _deriv_polys(ncomp)
+    lines = [f"__device__ __forceinline__ void {name}(double x, double y, double z, double (&d)[36]) {{\n",
+             "  const double r2 = fma(x, x, fma(y, y, z * z));\n",
+             "  const double ir = 1.0 / sqrt(r2);\n",
+             "  const double ir2 = ir * ir;\n",
+             "  const double s0 = ir;\n"]
+    for k in range(1, max(k for k, _ in polys) + 1):
+        lines.append(f"  const double s{k} = s{k - 1} * ir2;\n")
+    import re
+
+    def cc(e):
+        # integer powers as products (no pow calls), integer constants as doubles
+        t = sympy.ccode(e)
+        t = re.sub(r"pow\((\w+), 4\)", r"((\1 * \1) * (\1 * \1))", t)
+        t = re.sub(r"pow\((\w+), 3\)", r"(\1 * \1 * \1)", t)
+        t = re.sub(r"pow\((\w+), 2\)", r"(\1 * \1)", t)
+        assert "pow" not in t, t
+        return re.sub(r"(?<![\w.])(\d+)(?![\w.])", r"\1.0", t)
+    for sym, val in repl:
+        lines.append(f"  const double {sym} = {cc(val)};\n")
+    for q, ((k, _), P) in enumerate(zip(polys, reduced)):
+        lines.append(f"  d[{q}] = ({cc(P)}) * s{k};\n")
+    lines.append("}\n\n")
+    return "".join(lines)
+
+
 def emit():
     out = []
     w = out.append
@@ -203,6 +278,15 @@ def emit():
     for j in range(16):
         w(f"  df_fma(ah[{j}], al[{j}], mh, ml, r[{j}], r[{16 + j}]);\n")
     w("}\n\n")
+
+    # derivatives at an arbitrary separation (centre-of-mass expansion centres)
+    w("// derivatives of -1/r of orders 0..4 (row layout) at R = (x, y, z)\n")
+    w(deriv_code("ot_deriv_at", 35))
+    w("// orders 0..3 only (point-mass sources)\n")
+    w(deriv_code("ot_deriv16_at", 16))
+    w("// algorithmic FLOPs of one call of each (sqrt and the division count one each)\n")
+    w(f"constexpr int OT_DERIV35_FLOPS = {deriv_flops(35)};\n")
+    w(f"constexpr int OT_DERIV16_FLOPS = {deriv_flops(16)};\n\n")
 
     # the same with the row of -o: odd-order derivatives negated
     w("// 16 FMAs (derivatives of the negated offset)\n")

@@ -1084,6 +1084,392 @@ __global__ void cube_adjoint_kernel(const double* __restrict__ Mb, double* __res
 }
 
 // ---------------------------------------------------------------------------
+// centre-of-mass expansion centres: moments, L2L, and the passes with the
+// derivatives computed per pair from R = C_A - C_B
+// ---------------------------------------------------------------------------
+
+__global__ void geometric_centres_kernel(double* __restrict__ C, const int* __restrict__ nodes, int n_list,
+                                         const int* __restrict__ ninfo, const int* __restrict__ ncoord,
+                                         const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * NCELL) return;
+    const int node = nodes[t / NCELL], cell = t % NCELL;
+    const double h = 1.0 / hinv[ninfo[node] & 0xff];
+    const int loc[3] = {cell & 7, (cell >> 3) & 7, cell >> 6};
+    for (int a = 0; a < 3; ++a)
+        C[(static_cast<size_t>(node) * 3 + a) * NCELL + cell] = (8.0 * ncoord[3 * node + a] + loc[a] + 0.5) * h;
+}
+
+// parent cell: centre = mass-weighted mean of the 8 children's centres
+// (geometric if the mass is zero), moments = children's moments shifted there
+__global__ void m2m_com_kernel(double* __restrict__ M, double* __restrict__ m, double* __restrict__ C,
+                               const int* __restrict__ parents, int n_list, const int* __restrict__ children,
+                               const int* __restrict__ ninfo, const int* __restrict__ ncoord,
+                               const double* __restrict__ hinv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * NCELL) return;
+    const int k = t / NCELL, cell = t % NCELL;
+    const int P = parents[k];
+    const int g[3] = {cell & 7, (cell >> 3) & 7, cell >> 6};
+    int cn[8], cc[8];
+    double mass = 0.0, w[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+    for (int b = 0; b < 8; ++b) {
+        const int cx = 2 * g[0] + (b & 1), cy = 2 * g[1] + ((b >> 1) & 1), cz = 2 * g[2] + (b >> 2);
+        cn[b] = children[8 * k + (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
+        cc[b] = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
+        const double mc = M[static_cast<size_t>(cn[b]) * NCOMP * NCELL + cc[b]];
+        mass += mc;
+        for (int a = 0; a < 3; ++a) w[a] = fma(mc, C[(static_cast<size_t>(cn[b]) * 3 + a) * NCELL + cc[b]], w[a]);
+    }
+    double X[3];
+    const double h = 1.0 / hinv[ninfo[P] & 0xff];
+    for (int a = 0; a < 3; ++a) X[a] = (mass != 0.0) ? w[a] / mass : (8.0 * ncoord[3 * P + a] + g[a] + 0.5) * h;
+    Dense4 acc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc.v[a][b][c] = 0.0;
+#pragma unroll 1
+    for (int b = 0; b < 8; ++b) {
+        Dense4 v;
+        to_dense(M + static_cast<size_t>(cn[b]) * NCOMP * NCELL + cc[b], v);
+        const double* Cc = C + static_cast<size_t>(cn[b]) * 3 * NCELL + cc[b];
+        shift1<0>(v, Cc[0] - X[0]);
+        shift1<1>(v, Cc[NCELL] - X[1]);
+        shift1<2>(v, Cc[2 * NCELL] - X[2]);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bb = 0; a + bb < 4; ++bb)
+#pragma unroll
+                for (int c = 0; a + bb + c < 4; ++c) acc.v[a][bb][c] += v.v[a][bb][c];
+    }
+    from_dense(acc, M + static_cast<size_t>(P) * NCOMP * NCELL + cell, false);
+    m[static_cast<size_t>(P) * NCELL + cell] = acc.v[0][0][0];
+    for (int a = 0; a < 3; ++a) C[(static_cast<size_t>(P) * 3 + a) * NCELL + cell] = X[a];
+}
+
+__global__ void l2l_com_kernel(double* __restrict__ L, const double* __restrict__ C, const int* __restrict__ parents,
+                               int n_list, const int* __restrict__ children) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * 8 * NCELL) return;
+    const int k = t / (8 * NCELL);
+    const int oct = (t / NCELL) % 8, ccell = t % NCELL;
+    const int P = parents[k];
+    const int Cn = children[8 * k + oct];
+    const int cx = (oct & 1) * 8 + (ccell & 7), cy = ((oct >> 1) & 1) * 8 + ((ccell >> 3) & 7),
+              cz = (oct >> 2) * 8 + (ccell >> 6);
+    const int pcell = (cx >> 1) + 8 * (cy >> 1) + 64 * (cz >> 1);
+    const double* Cc = C + static_cast<size_t>(Cn) * 3 * NCELL + ccell;
+    const double* Cp = C + static_cast<size_t>(P) * 3 * NCELL + pcell;
+    Dense4 v;
+    to_dense(L + static_cast<size_t>(P) * NCOMP * NCELL + pcell, v);
+    lshift1<0>(v, Cc[0] - Cp[0]);
+    lshift1<1>(v, Cc[NCELL] - Cp[NCELL]);
+    lshift1<2>(v, Cc[2 * NCELL] - Cp[2 * NCELL]);
+    from_dense(v, L + static_cast<size_t>(Cn) * NCOMP * NCELL + ccell, true);
+}
+
+// transpose of l2l_com_kernel: every parent cell adds the transposed shifts
+// of its 8 child cells' adjoints (centres held fixed)
+__global__ void l2l_com_adjoint_kernel(double* __restrict__ Lb, const double* __restrict__ C,
+                                       const int* __restrict__ parents, int n_list,
+                                       const int* __restrict__ children) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_list * NCELL) return;
+    const int k = t / NCELL, cell = t % NCELL;
+    const int P = parents[k];
+    const int gx = cell & 7, gy = (cell >> 3) & 7, gz = cell >> 6;
+    const double* Cp = C + static_cast<size_t>(P) * 3 * NCELL + cell;
+    const double xp = Cp[0], yp = Cp[NCELL], zp = Cp[2 * NCELL];
+    Dense4 acc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc.v[a][b][c] = 0.0;
+#pragma unroll 1
+    for (int b = 0; b < 8; ++b) {
+        const int cx = 2 * gx + (b & 1), cy = 2 * gy + ((b >> 1) & 1), cz = 2 * gz + (b >> 2);
+        const int Cn = children[8 * k + (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
+        const int ccell = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
+        const double* Cc = C + static_cast<size_t>(Cn) * 3 * NCELL + ccell;
+        Dense4 v;
+        to_dense(Lb + static_cast<size_t>(Cn) * NCOMP * NCELL + ccell, v);
+        lshift1_t<2>(v, Cc[2 * NCELL] - zp);
+        lshift1_t<1>(v, Cc[NCELL] - yp);
+        lshift1_t<0>(v, Cc[0] - xp);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bb = 0; a + bb < 4; ++bb)
+#pragma unroll
+                for (int c = 0; a + bb + c < 4; ++c) acc.v[a][bb][c] += v.v[a][bb][c];
+    }
+    from_dense(acc, Lb + static_cast<size_t>(P) * NCOMP * NCELL + cell, true);
+}
+
+// source expansion centre seen from a target sub-grid at `org` (its first
+// cell's global position) through neighbour entry e: explicit for real
+// cells, the geometric centre of a virtual descendant's cell
+__device__ __forceinline__ void com_source_centre(const double* __restrict__ C, int2 e, int kind, const int (&org)[3],
+                                                  int sx, int sy, int sz, double h, double (&X)[3]) {
+    if (kind == K_LEAF || kind == K_MULTI) {
+        const double* c = C + static_cast<size_t>(e.x) * 3 * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+        X[0] = c[0];
+        X[1] = c[NCELL];
+        X[2] = c[2 * NCELL];
+    } else {
+        X[0] = (org[0] + sx + 0.5) * h;
+        X[1] = (org[1] + sy + 0.5) * h;
+        X[2] = (org[2] + sz + 0.5) * h;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void com_pair(const FwdParams& p, int2 e, int kind, const int (&org)[3], int sx, int sy,
+                                         int sz, double h, const double (&XA)[3], bool angular, double (&a)[16],
+                                         double (&c)[3], double (&t4)[9]) {
+    const bool mono = (MODE & 2) && kind >= K_LEAF;
+    const bool multi = (MODE & 1) && kind == K_MULTI;
+    const bool any_mono = __any_sync(0xffffffffu, mono);
+    const bool any_multi = __any_sync(0xffffffffu, multi);
+    if (!any_mono && !any_multi) return;
+    double X[3];
+    if (kind == K_NONE) {            // no source: any finite separation (its terms are zero)
+        X[0] = XA[0];
+        X[1] = XA[1];
+        X[2] = XA[2] + h;
+    } else {
+        com_source_centre(p.C, e, kind, org, sx, sy, sz, h, X);
+    }
+    double d[36];
+    if (any_multi) ot_deriv_at(XA[0] - X[0], XA[1] - X[1], XA[2] - X[2], d);
+    else ot_deriv16_at(XA[0] - X[0], XA[1] - X[1], XA[2] - X[2], d);
+    if (any_mono) ot_mono_fwd(a, source_mass(p, e, kind, sx, sy, sz), d);
+    if (any_multi) {
+        double r[16];
+        source_moments(p, e, multi, sx, sy, sz, r);
+        ot_multi_fwd(a, r, d);
+        if (angular) ot_angular_fwd(c, t4, r, r[0], d);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, int len, bool angular, bool paired,
+                                                 int tx, int ty, int tz, const int2* __restrict__ s_nb,
+                                                 const FwdParams& p, const int (&org)[3], double h,
+                                                 const double (&XA)[3], double (&a)[16], double (&c)[3],
+                                                 double (&t4)[9], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        for (int side = 0; side < (paired ? 2 : 1); ++side) {
+            const int sg = side ? -1 : 1;
+            const int sx = tx + sg * ox, sy = ty + sg * oy, sz = tz + sg * oz;
+            const int2 e = s_nb[nb_index(sx, sy, sz)];
+            const int kind = checked_kind(p, e, item);
+            com_pair<MODE>(p, e, kind, org, sx, sy, sz, h, XA, angular, a, c, t4);
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
+    __shared__ int2 s_nb[8][27];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(p.counter, 1);
+        const int it = __shfl_sync(0xffffffffu, v, 0);
+        if (it >= p.n_items) break;
+        const int item = __ldg(p.items + it);
+        const int node = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        if (lane < 27) s_nb[warp][lane] = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
+        __syncwarp();
+        const int info = __ldg(p.ninfo + node);
+        const int level = info & 0xff;
+        const bool leafT = (info >> 8) & 1;
+        const double h = p.hreal[level];
+        const int org[3] = {8 * __ldg(p.ncoord + 3 * node), 8 * __ldg(p.ncoord + 3 * node + 1),
+                            8 * __ldg(p.ncoord + 3 * node + 2)};
+        int tx, ty, tz;
+        lane_cell(lane, par, half, tx, ty, tz);
+        const int tcell = tx + 8 * ty + 64 * tz;
+        const double* ca = p.C + static_cast<size_t>(node) * 3 * NCELL + tcell;
+        const double XA[3] = {ca[0], ca[NCELL], ca[2 * NCELL]};
+        double a[16], c[3], t4[9];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) c[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) t4[q] = 0.0;
+        if (level == 0) {
+            walk_forward_com<MODE>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, true, tx, ty, tz, s_nb[warp], p,
+                                   org, h, XA, a, c, t4, it);
+        } else {
+            const int* lf = p.L.lists + par * p.L.far_len;
+            walk_forward_com<MODE>(lf, p.L.far_pairs, !leafT, true, tx, ty, tz, s_nb[warp], p, org, h, XA, a, c, t4,
+                                   it);
+            walk_forward_com<MODE>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, false, tx, ty, tz,
+                                   s_nb[warp], p, org, h, XA, a, c, t4, it);
+        }
+        if (leafT)
+            walk_forward_com<MODE>(p.L.lists + p.L.near_off, p.L.near_len, false, true, tx, ty, tz, s_nb[warp], p,
+                                   org, h, XA, a, c, t4, it);
+        store_forward<MODE>(p, node, level, leafT, tcell, a, c, t4);
+        __syncwarp();
+    }
+}
+
+// adjoint gather with fixed centres: source B collects from targets A
+template <bool MULTI>
+__device__ __forceinline__ void walk_adjoint_com(const int* __restrict__ list, int len, bool near_seg, bool paired,
+                                                 int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
+                                                 const AdjParams& p, const double (&XB)[3], double (&g)[16],
+                                                 double (&g4)[4], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        for (int side = 0; side < (paired ? 2 : 1); ++side) {
+            const int sg = side ? -1 : 1;
+            const int tx = sx0 + sg * ox, ty = sy0 + sg * oy, tz = sz0 + sg * oz;
+            const int2 e = s_nb[nb_index(tx, ty, tz)];
+            const int kind = e.y & 3;
+            bool valid = (kind == K_MULTI || kind == K_LEAF) && (!near_seg || kind == K_LEAF);
+            if (valid && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
+                report(p.status, 4, item);
+                valid = false;
+            }
+            if (!__any_sync(0xffffffffu, valid)) continue;
+            const int tcell = (tx & 7) + 8 * (ty & 7) + 64 * (tz & 7);
+            double lb[16], XA[3] = {XB[0], XB[1], XB[2] + 1.0};   // dummy separation for lanes without a target
+            if (valid) {
+                const double* src = p.Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + tcell;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) lb[q] = __ldg(src + q * NCELL);
+                const double* ca = p.C + static_cast<size_t>(e.x) * 3 * NCELL + tcell;
+                XA[0] = ca[0];
+                XA[1] = ca[NCELL];
+                XA[2] = ca[2 * NCELL];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) lb[q] = 0.0;
+            }
+            double d[36];
+            if (MULTI) {
+                ot_deriv_at(XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2], d);
+                ot_multi_adj(g, lb, d);
+            } else {
+                ot_deriv16_at(XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2], d);
+                ot_mono_adj(g4, lb, d);
+            }
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
+    __shared__ int2 s_nb[8][27];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(p.counter, 1);
+        const int it = __shfl_sync(0xffffffffu, v, 0);
+        if (it >= p.n_items) break;
+        const int item = __ldg(p.items + it);
+        const int src = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        const bool virt = src >= p.n_nodes;
+        const int2* nbt = virt ? p.vnbr + static_cast<size_t>(src - p.n_nodes) * 27
+                               : p.nbr + static_cast<size_t>(src) * 27;
+        if (lane < 27) s_nb[warp][lane] = __ldg(nbt + lane);
+        __syncwarp();
+        int level, skind;
+        const int* crd;
+        if (virt) {
+            level = __ldg(p.vinfo + (src - p.n_nodes));
+            skind = K_VIRT;
+            crd = p.vcoord + 3 * (src - p.n_nodes);
+        } else {
+            const int info = __ldg(p.ninfo + src);
+            level = info & 0xff;
+            skind = ((info >> 8) & 1) ? K_LEAF : K_MULTI;
+            crd = p.ncoord + 3 * src;
+        }
+        int sx, sy, sz;
+        lane_cell(lane, par, half, sx, sy, sz);
+        const int scell = sx + 8 * sy + 64 * sz;
+        double XB[3];
+        if (virt) {
+            const double h = p.hreal[level];
+            XB[0] = (8.0 * crd[0] + sx + 0.5) * h;
+            XB[1] = (8.0 * crd[1] + sy + 0.5) * h;
+            XB[2] = (8.0 * crd[2] + sz + 0.5) * h;
+        } else {
+            const double* cb = p.C + static_cast<size_t>(src) * 3 * NCELL + scell;
+            XB[0] = cb[0];
+            XB[1] = cb[NCELL];
+            XB[2] = cb[2 * NCELL];
+        }
+        const int* l1 = (level == 0) ? p.L.lists + p.L.root_off : p.L.lists + par * p.L.far_len;
+        const int* l2 = p.L.lists + p.L.near_off;
+        double g[16], g4[4];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) g[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g4[q] = 0.0;
+        const int np = (level == 0) ? p.L.root_len : p.L.far_pairs;
+        const int ns = (level == 0) ? 0 : p.L.far_len - p.L.far_pairs;
+        if (skind == K_MULTI) {
+            if ((MODE & 1) && p.Mbar != nullptr) {
+                walk_adjoint_com<true>(l1, np, false, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
+                walk_adjoint_com<true>(l1 + np, ns, false, false, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
+                walk_adjoint_com<true>(l2, p.L.near_len, true, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
+                double Mb[20];
+                Mb[0] = g[0];
+                Mb[1] = -g[1];
+                Mb[2] = -g[2];
+                Mb[3] = -g[3];
+                Mb[4] = 0.5 * g[4];
+                Mb[5] = g[5];
+                Mb[6] = g[6];
+                Mb[7] = 0.5 * g[7];
+                Mb[8] = g[8];
+                Mb[9] = -0.5 * (g[4] + g[7]);
+                Mb[10] = -g[9] / 6.0;
+                Mb[11] = -0.5 * g[10];
+                Mb[12] = -0.5 * g[11];
+                Mb[13] = -0.5 * g[12];
+                Mb[14] = -g[13];
+                Mb[15] = 0.5 * (g[9] + g[12]);
+                Mb[16] = -g[14] / 6.0;
+                Mb[17] = -0.5 * g[15];
+                Mb[18] = 0.5 * (g[10] + g[14]);
+                Mb[19] = (g[11] + g[15]) / 6.0;
+                double* out = p.Mbar + static_cast<size_t>(src) * NCOMP * NCELL + scell;
+#pragma unroll
+                for (int q = 0; q < 20; ++q) out[q * NCELL] = Mb[q];
+            }
+        } else if ((MODE & 2) && p.mbar != nullptr) {
+            walk_adjoint_com<false>(l1, np, false, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
+            walk_adjoint_com<false>(l1 + np, ns, false, false, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
+            walk_adjoint_com<false>(l2, p.L.near_len, true, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
+            const double val = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+            if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = val;
+            else p.mbar[static_cast<size_t>(src) * NCELL + scell] = val;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 FMA throughput probe
 // ---------------------------------------------------------------------------
 
@@ -1245,6 +1631,74 @@ cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nod
     if (n_list == 0) return cudaSuccess;
     cube_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(Mb, rhobar, nodes, n_list, ninfo, hinv);
     return cudaGetLastError();
+}
+
+cudaError_t launch_geometric_centres(double* C, const int* nodes, int n_list, const int* ninfo, const int* ncoord,
+                                     const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    geometric_centres_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(C, nodes, n_list, ninfo, ncoord,
+                                                                                    hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2m_com(double* M, double* m, double* C, const int* parents, int n_list, const int* children,
+                           const int* ninfo, const int* ncoord, const double* hinv, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    m2m_com_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(M, m, C, parents, n_list, children, ninfo,
+                                                                          ncoord, hinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2l_com(double* L, const double* C, const int* parents, int n_list, const int* children,
+                           cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    l2l_com_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(L, C, parents, n_list, children);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2l_com_adjoint(double* Lb, const double* C, const int* parents, int n_list, const int* children,
+                                   cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    l2l_com_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(Lb, C, parents, n_list, children);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_com(const FwdParams& p, int mode, int wpb, int grid, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    switch (mode) {
+        case 1: forward_com_kernel<1><<<grid, 32 * wpb, 0, s>>>(p); break;
+        case 2: forward_com_kernel<2><<<grid, 32 * wpb, 0, s>>>(p); break;
+        default: forward_com_kernel<3><<<grid, 32 * wpb, 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_com(const AdjParams& p, int mode, int wpb, int grid, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    switch (mode) {
+        case 1: adjoint_com_kernel<1><<<grid, 32 * wpb, 0, s>>>(p); break;
+        case 2: adjoint_com_kernel<2><<<grid, 32 * wpb, 0, s>>>(p); break;
+        default: adjoint_com_kernel<3><<<grid, 32 * wpb, 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+int deriv_flops(int ncomp) { return ncomp == 35 ? OT_DERIV35_FLOPS : OT_DERIV16_FLOPS; }
+
+int forward_com_max_blocks_per_sm(int mode, int wpb) {
+    int n = 0;
+    const void* f = (mode == 1) ? (const void*)forward_com_kernel<1>
+                  : (mode == 2) ? (const void*)forward_com_kernel<2> : (const void*)forward_com_kernel<3>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
+    return n;
+}
+
+int adjoint_com_max_blocks_per_sm(int mode, int wpb) {
+    int n = 0;
+    const void* f = (mode == 1) ? (const void*)adjoint_com_kernel<1>
+                  : (mode == 2) ? (const void*)adjoint_com_kernel<2> : (const void*)adjoint_com_kernel<3>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
+    return n;
 }
 
 cudaError_t launch_l2l(double* L, const int* parents, int n_list, const int* children, const int* ninfo,

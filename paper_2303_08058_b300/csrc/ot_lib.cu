@@ -135,8 +135,9 @@ struct GraphKey {
     const void* c;
     const void* d;
     int w, bps;
+    const void* e;
     bool operator<(const GraphKey& o) const {
-        return std::tie(op, a, b, c, d, w, bps) < std::tie(o.op, o.a, o.b, o.c, o.d, o.w, o.bps);
+        return std::tie(op, a, b, c, d, w, bps, e) < std::tie(o.op, o.a, o.b, o.c, o.d, o.w, o.bps, o.e);
     }
 };
 
@@ -164,6 +165,8 @@ struct ot_grid {
     int2* d_vnbr = nullptr;
     int* d_ninfo = nullptr;
     int* d_vinfo = nullptr;
+    int* d_ncoord = nullptr;            // [n][3] sub-grid positions (explicit-centre kernels)
+    int* d_vcoord = nullptr;            // [nvirt][3]
     double* d_Dt = nullptr;
     float* d_Dt32 = nullptr;            // double-float split of the point-mass derivatives
     float2* d_mf = nullptr;             // masses as double-float pairs (scratch)
@@ -185,6 +188,8 @@ struct ot_grid {
     int maxb_scat[9] = {};
     int maxb_fast5[9] = {};
     int maxb_emu[4][9] = {};            // forward with double-float point masses, modes 2 and 3
+    int maxb_com_fwd[4][9] = {};        // explicit expansion centres
+    int maxb_com_adj[4][9] = {};
     int deterministic = 0;              // 1: point-mass adjoint as a gather (fixed summation order)
     long long flops_adj_det = 0, ops_adj_det = 0, flops_adj_fast = 0, ops_adj_fast = 0;
     int* d_nonleaf = nullptr;
@@ -419,6 +424,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     g->nvirt = static_cast<int>(vnodes.size());
     g->vnbr.assign(static_cast<size_t>(std::max(g->nvirt, 1)) * 27, int2{-1, K_NONE});
     g->vinfo.assign(std::max(g->nvirt, 1), 0);
+    std::vector<int> vcoord(static_cast<size_t>(std::max(g->nvirt, 1)) * 3, 0);
+    for (int v = 0; v < g->nvirt; ++v)
+        for (int a = 0; a < 3; ++a) vcoord[3 * v + a] = static_cast<int>(vnodes[v].q[a]);
     std::vector<std::pair<int, int>> vrows;   // (P*512 + pcell, entry)
     for (int v = 0; v < g->nvirt; ++v) {
         const VNode& V = vnodes[v];
@@ -702,6 +710,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.flops_adj = g->flops_adj_fast;
     I.ops_fwd = ops_fwd;
     I.ops_adj = g->ops_adj_fast;
+    // explicit centres: every pair evaluates its derivatives (no pairing)
+    I.flops_fwd_com = pairs_multi * (deriv_flops(35) + 140) + pairs_ang * 60 + pairs_mono * (deriv_flops(16) + 32);
+    I.flops_adj_com = pairs_multi * (deriv_flops(35) + 140) + pairs_mono * (deriv_flops(16) + 32);
     for (int w = 2; w <= 8; w *= 2) {
         g->maxb_emu[2][w] = forward_max_blocks_per_sm(6, w);
         g->maxb_emu[3][w] = forward_max_blocks_per_sm(7, w);
@@ -713,6 +724,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         for (int w = 2; w <= 8; w *= 2) {
             g->maxb_fwd[mode][w] = forward_max_blocks_per_sm(mode, w);
             g->maxb_adj[mode][w] = adjoint_max_blocks_per_sm(mode, w);
+            g->maxb_com_fwd[mode][w] = forward_com_max_blocks_per_sm(mode, w);
+            g->maxb_com_adj[mode][w] = adjoint_com_max_blocks_per_sm(mode, w);
         }
 
     // --- uploads ----------------------------------------------------------------
@@ -723,6 +736,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_vnbr, g->vnbr);
     UP(g->d_ninfo, g->ninfo);
     UP(g->d_vinfo, g->vinfo);
+    UP(g->d_vcoord, vcoord);
+    {
+        std::vector<int> nc(desc->coord, desc->coord + 3 * static_cast<size_t>(n));
+        UP(g->d_ncoord, nc);
+    }
     UP(g->d_Dt, Dt);
     {
         std::vector<float> Dt32(static_cast<size_t>(NOFF) * 32, 0.0f);
@@ -964,6 +982,91 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     }
     if (!scatter && mbar && g->vmap_rows > 0)
         OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
+    return OT_OK;
+}
+
+// --- explicit expansion centres ---------------------------------------------
+// Moments about arbitrary centres carry their own units, so nothing is
+// pre-scaled by h (hinv = 1 in the prescale kernels and the epilogue), and the
+// derivatives are evaluated per pair at R = C_A - C_B.  Always the persistent
+// schedule (LPT-ordered items, one launch).
+
+static ot_status enqueue_forward_com(ot_grid* g, int mode, const double* M, const double* m, const double* C,
+                                     double* L, double* Lc, cudaStream_t s) {
+    if (mode & 1) {
+        PrepParams pp;
+        std::memset(&pp, 0, sizeof(pp));
+        pp.src = M;
+        pp.dst = g->d_Mhat;
+        pp.nodes = g->d_nonleaf;
+        pp.n_list = g->n_nonleaf;
+        pp.ninfo = g->d_ninfo;
+        for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = 1.0;
+        OT_CUDA(launch_prescale_moments(pp, s));
+    }
+    OT_CUDA(cudaMemsetAsync(L, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
+    if ((mode & 1) && Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
+    FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
+    for (int l = 0; l < MAXLEV; ++l) {
+        p.hinv[l] = 1.0;
+        p.hreal[l] = 1.0 / g->hinv[l];
+    }
+    p.C = C;
+    p.ncoord = g->d_ncoord;
+    p.items = g->d_items_fwd[mode];
+    p.n_items = g->n_items_fwd[mode];
+    OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
+    OT_CUDA(launch_forward_com(p, mode, g->wpb, grid_blocks(g, g->maxb_com_fwd[mode][g->wpb]), s));
+    return OT_OK;
+}
+
+static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const double* C, double* Mbar, double* mbar,
+                                      cudaStream_t s) {
+    const int mode = (Mbar ? 1 : 0) | (mbar ? 2 : 0);
+    if (mode == 0) return OT_OK;
+    PrepParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.src = Lbar;
+    pp.dst = g->d_Lrbar;
+    pp.nodes = g->d_all;
+    pp.n_list = g->n;
+    pp.ninfo = g->d_ninfo;
+    for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = 1.0;
+    OT_CUDA(launch_prescale_adjoint(pp, s));
+    if (Mbar) OT_CUDA(cudaMemsetAsync(Mbar, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
+    if (mbar) OT_CUDA(cudaMemsetAsync(mbar, 0, static_cast<size_t>(g->n) * NCELL * sizeof(double), s));
+    AdjParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.items = g->d_items_adj[mode];
+    p.n_items = g->n_items_adj[mode];
+    p.counter = g->d_counters + 1;
+    p.nbr = g->d_nbr;
+    p.vnbr = g->d_vnbr;
+    p.ninfo = g->d_ninfo;
+    p.vinfo = g->d_vinfo;
+    p.L.lists = g->d_lists;
+    p.L.far_len = g->far_len;
+    p.L.far_pairs = g->far_pairs;
+    p.L.near_len = g->near_len;
+    p.L.root_len = g->root_len;
+    p.L.near_off = 8 * g->far_len;
+    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.Lrbar = g->d_Lrbar;
+    p.Mbar = Mbar;
+    p.mbar = mbar;
+    p.vbar = g->d_vbar;
+    p.n_nodes = g->n;
+    p.status = g->d_status;
+    for (int l = 0; l < MAXLEV; ++l) {
+        p.hinv[l] = 1.0;
+        p.hreal[l] = 1.0 / g->hinv[l];
+    }
+    p.C = C;
+    p.ncoord = g->d_ncoord;
+    p.vcoord = g->d_vcoord;
+    OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
+    OT_CUDA(launch_adjoint_com(p, mode, g->wpb, grid_blocks(g, g->maxb_com_adj[mode][g->wpb]), s));
+    if (mbar && g->vmap_rows > 0) OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
     return OT_OK;
 }
 
@@ -1401,7 +1504,7 @@ ot_status ot_multipole_interactions(ot_grid* g, const double* M, const double* c
                                     void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
-    if (centres) return fail(OT_ENOTSUP, "explicit expansion centres are not built (pass NULL)");
+    if (centres) return ot_interactions_com(g, M, nullptr, centres, L, Lc, stream);
     CHECK_PTR(M, "M");
     CHECK_PTR(L, "L");
     if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
@@ -1444,6 +1547,78 @@ ot_status ot_interactions_backward(ot_grid* g, const double* Lbar, double* Mbar,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     GraphKey key{4 + 8 * g->deterministic, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_backward(g, Lbar, Mbar, mbar, st); });
+    GUARD_END
+}
+
+ot_status ot_moments_com(ot_grid* g, const double* rho, double* M, double* m, double* C, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(rho, "rho");
+    CHECK_PTR(M, "M");
+    CHECK_PTR(m, "m");
+    CHECK_PTR(C, "C");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OT_CUDA(launch_cube_moments(rho, M, m, g->d_cube, g->n_cube, g->d_ninfo, g->d_hinv, s));
+    OT_CUDA(launch_geometric_centres(C, g->d_cube, g->n_cube, g->d_ninfo, g->d_ncoord, g->d_hinv, s));
+    for (auto& L : g->m2m)
+        OT_CUDA(launch_m2m_com(M, m, C, L.d_parents, static_cast<int>(L.parents.size()), L.d_children, g->d_ninfo,
+                               g->d_ncoord, g->d_hinv, s));
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_interactions_com(ot_grid* g, const double* M, const double* m, const double* C, double* L, double* Lc,
+                              void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!M && !m) return fail(OT_EINVAL, "M and m are both NULL");
+    if (M && !aligned16(M)) return fail(OT_EINVAL, "M is not 16-byte aligned");
+    if (m && !aligned16(m)) return fail(OT_EINVAL, "m is not 16-byte aligned");
+    CHECK_PTR(C, "C");
+    CHECK_PTR(L, "L");
+    if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
+    const int mode = (M ? 1 : 0) | (m ? 2 : 0);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GraphKey key{32 + mode, M, m, L, Lc, g->wpb, g->bps, C};
+    return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward_com(g, mode, M, m, C, L, Lc, st); });
+    GUARD_END
+}
+
+ot_status ot_interactions_backward_com(ot_grid* g, const double* Lbar, const double* C, double* Mbar, double* mbar,
+                                       void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(Lbar, "Lbar");
+    CHECK_PTR(C, "C");
+    if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
+    if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GraphKey key{40, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps, C};
+    return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_backward_com(g, Lbar, C, Mbar, mbar, st); });
+    GUARD_END
+}
+
+ot_status ot_l2l_com(ot_grid* g, const double* C, double* L, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(C, "C");
+    CHECK_PTR(L, "L");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (auto it = g->m2m.rbegin(); it != g->m2m.rend(); ++it)
+        OT_CUDA(launch_l2l_com(L, C, it->d_parents, static_cast<int>(it->parents.size()), it->d_children, s));
+    return OT_OK;
+    GUARD_END
+}
+
+ot_status ot_l2l_com_backward(ot_grid* g, const double* C, double* Lbar, void* stream) {
+    GUARD_BEGIN
+    if (!g) return fail(OT_EINVAL, "grid is NULL");
+    CHECK_PTR(C, "C");
+    CHECK_PTR(Lbar, "Lbar");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (auto& L : g->m2m)
+        OT_CUDA(launch_l2l_com_adjoint(Lbar, C, L.d_parents, static_cast<int>(L.parents.size()), L.d_children, s));
+    return OT_OK;
     GUARD_END
 }
 

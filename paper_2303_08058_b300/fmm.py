@@ -119,11 +119,11 @@ class OTGrid:
                                                 _stream(stream)))
         return rhobar
 
-    def multipole(self, M, L=None, Lc=None, want_lc=True, stream=None):
+    def multipole(self, M, L=None, Lc=None, want_lc=True, centres=None, stream=None):
         L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
         if Lc is None and want_lc:
             Lc = self.zeros(self.n, 3, NCELL)
-        _lib.check(self.lib.ot_multipole_interactions(self.handle, _ptr(M), None, _ptr(L), _ptr(Lc),
+        _lib.check(self.lib.ot_multipole_interactions(self.handle, _ptr(M), _ptr(centres), _ptr(L), _ptr(Lc),
                                                       _stream(stream)))
         return L, Lc
 
@@ -138,6 +138,49 @@ class OTGrid:
             Lc = self.zeros(self.n, 3, NCELL)
         _lib.check(self.lib.ot_interactions(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), _stream(stream)))
         return L, Lc
+
+    # -- centre-of-mass expansion centres ----------------------------------------
+    def moments_com(self, rho, M=None, m=None, C=None, stream=None):
+        """(M, m, C): moments about the cells' centres of mass (ot_moments_com)."""
+        M = M if M is not None else self.zeros(self.n, NCOMP, NCELL)
+        m = m if m is not None else self.zeros(self.n, NCELL)
+        C = C if C is not None else self.zeros(self.n, 3, NCELL)
+        _lib.check(self.lib.ot_moments_com(self.handle, _ptr(rho), _ptr(M), _ptr(m), _ptr(C), _stream(stream)))
+        return M, m, C
+
+    def interactions_com(self, M, m, C, L=None, Lc=None, want_lc=True, stream=None):
+        """Both passes (either source may be None) about explicit centres C."""
+        L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
+        if Lc is None and want_lc and M is not None:
+            Lc = self.zeros(self.n, 3, NCELL)
+        _lib.check(self.lib.ot_interactions_com(self.handle, _ptr(M), _ptr(m), _ptr(C), _ptr(L), _ptr(Lc),
+                                                _stream(stream)))
+        return L, Lc
+
+    def backward_com(self, Lbar, C, Mbar=None, mbar=None, want=(True, True), stream=None):
+        """Adjoint of interactions_com with the centres held fixed."""
+        if Mbar is None and want[0]:
+            Mbar = self.zeros(self.n, NCOMP, NCELL)
+        if mbar is None and want[1]:
+            mbar = self.zeros(self.n, NCELL)
+        _lib.check(self.lib.ot_interactions_backward_com(self.handle, _ptr(Lbar), _ptr(C), _ptr(Mbar), _ptr(mbar),
+                                                         _stream(stream)))
+        return Mbar, mbar
+
+    def l2l_com(self, L, C, stream=None):
+        _lib.check(self.lib.ot_l2l_com(self.handle, _ptr(C), _ptr(L), _stream(stream)))
+        return L
+
+    def l2l_com_backward(self, Lbar, C, stream=None):
+        _lib.check(self.lib.ot_l2l_com_backward(self.handle, _ptr(C), _ptr(Lbar), _stream(stream)))
+        return Lbar
+
+    def solve_com(self, rho, stream=None):
+        """Full multilevel solve about centres of mass: (L, Lc, C)."""
+        M, m, C = self.moments_com(rho, stream=stream)
+        L, Lc = self.interactions_com(M, m, C, stream=stream)
+        self.l2l_com(L, C, stream=stream)
+        return L, Lc, C
 
     def l2l(self, L, stream=None):
         """In-place down-pass: adds every parent's shifted expansion (ot_l2l)."""
