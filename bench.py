@@ -307,6 +307,27 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     df_ms = statistics.median(a.elapsed_time(b) for a, b in de)
     g.set_precision(ot.OT_PREC_FP64)
+    # the same passes about centres of mass (derivatives evaluated per pair)
+    Mc, mc, Cc = g.moments_com(rho)
+    g.interactions_com(Mc, mc, Cc, L, Lc)
+    g.backward_com(Lbar, Cc, Mb, mb)
+    ce = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in ce:
+        flush.zero_()
+        a.record(stream)
+        g.interactions_com(Mc, mc, Cc, L, Lc)
+        b.record(stream)
+    cb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in cb:
+        flush.zero_()
+        a.record(stream)
+        g.backward_com(Lbar, Cc, Mb, mb)
+        b.record(stream)
+    torch.cuda.synchronize()
+    g.check()
+    com_fwd_ms = statistics.median(a.elapsed_time(b) for a, b in ce)
+    com_adj_ms = statistics.median(a.elapsed_time(b) for a, b in cb)
+    del Mc, mc, Cc
     clk = clocks.stop()
 
     # -- FP64 FMA peak, measured on this GPU at the clocks it runs now --------
@@ -354,6 +375,14 @@ def run_ours(args, rank, world):
         "fwd_df64_point_mass": {"value": pairs_fwd / (df_ms * 1e-3), "unit": UNIT, "ms": df_ms,
                                 "note": "point-mass pairs in double-float on the FP32 pipe (within 1e-12 of "
                                         "the FP64 result); reported beside the FP64 numbers, not as them"},
+        "com": {"fwd": {"value": pairs_fwd / (com_fwd_ms * 1e-3), "unit": UNIT, "ms": com_fwd_ms,
+                        "tflops": info["flops_fwd_com"] / (com_fwd_ms * 1e-3) / 1e12,
+                        "frac": info["flops_fwd_com"] / (com_fwd_ms * 1e-3) / 1e12 / peak},
+                "adjoint": {"value": pairs_fwd / (com_adj_ms * 1e-3), "unit": UNIT, "ms": com_adj_ms,
+                            "tflops": info["flops_adj_com"] / (com_adj_ms * 1e-3) / 1e12,
+                            "frac": info["flops_adj_com"] / (com_adj_ms * 1e-3) / 1e12 / peak},
+                "note": "centre-of-mass expansion centres: the same pairs, derivatives of G evaluated "
+                        "per pair at R = C_A - C_B; fractions of the same FP64 peak"},
         "roofline": {"bound": "alu", "kernel": "forward_kernel<3> (both passes, one launch)",
                      "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                      "peak_source": (f"nominal B300 FP64 {NOMINAL_FP64_TFLOPS} TFLOP/s at {NOMINAL_SM_MHZ:.0f} MHz, "

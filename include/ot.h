@@ -190,14 +190,15 @@ ot_status ot_l2l(ot_grid* grid, double* L, void* stream);
 ot_status ot_l2l_backward(ot_grid* grid, double* Lbar, void* stream);
 
 /* Centre-of-mass expansion centres (the octree FMM of Sec. 2.1 expands
- * every cell about its centre of mass).  Moments and Taylor coefficients are
- * then taken about per-cell centres C [n][3][512] (x, y, z planes; positions
- * in the units of h0) instead of the geometric centres; the pair set of both
- * passes is unchanged, and every pair evaluates the derivatives of G at
- * R = C_A - C_B itself (sqrt, division and the order 0..4 polynomials) rather
- * than reading the integer-offset table.  Point-mass sources sit at their
- * geometric cell centres (a uniform cube's centre of mass), virtual
- * descendants at their virtual cells' centres.
+ * every cell about its centre of mass).  Cells of non-leaf sub-grids are
+ * expanded about per-cell centres C [n][3][512] (x, y, z planes; positions in
+ * the units of h0); cells of leaf sub-grids are uniform cubes and stay at
+ * their geometric centres, as do virtual descendants -- C is never read for
+ * leaf sub-grids.  The pair set of both passes is unchanged.  A pair whose
+ * two centres are geometric (a leaf target and a point-mass source) sits at
+ * an integer offset and uses the derivative table; every other pair
+ * evaluates the derivatives of G at its own R = C_A - C_B (one sqrt and one
+ * division, the order 0..4 polynomials it needs).
  *
  * ot_moments_com: rho [n][512] -> M [n][20][512], m [n][512], C [n][3][512]
  * (all overwritten).  A node without all 8 children: C = geometric centre,
@@ -213,20 +214,22 @@ ot_status ot_moments_com(ot_grid* grid, const double* rho, double* M, double* m,
  * OVERWRITTEN with the sum of the passes run; Lc [n][3][512] (may be NULL;
  * multipole pass only) overwritten, as in ot_multipole_interactions.  Always
  * the persistent schedule; FP64 throughout (ot_set_precision does not apply).
- * Pairs closer than the opening rule admits are the caller's concern: C
- * must keep every pair's |R| > 0 (true for centres inside their cells). */
+ * Every pair must keep |C_A - C_B| > 0, which holds for centres inside their
+ * cells (any centre of mass of non-negative densities). */
 ot_status ot_interactions_com(ot_grid* grid, const double* M, const double* m, const double* C,
                               double* L, double* Lc, void* stream);
 
 /* Adjoint of ot_interactions_com with the centres held fixed (a partial
  * gradient: the dependence of C on the densities is not differentiated).
- * Mbar [n][20][512], mbar [n][512] overwritten (either may be NULL to skip);
- * always the fixed-order gather, bit-reproducible. */
+ * Mbar [n][20][512], mbar [n][512] overwritten (either may be NULL to skip).
+ * As ot_interactions_backward: mbar by atomic adds from the targets by
+ * default, by the fixed-order gather after ot_set_deterministic(grid, 1). */
 ot_status ot_interactions_backward_com(ot_grid* grid, const double* Lbar, const double* C,
                                        double* Mbar, double* mbar, void* stream);
 
-/* Down-pass with explicit centres, in place on L: d = C_child - C_parent per
- * child cell (otherwise as ot_l2l); and its adjoint with C fixed. */
+/* Down-pass with explicit centres, in place on L: d = X_child - X_parent per
+ * child cell, X the centre as above (C for non-leaf sub-grids, geometric for
+ * leaf sub-grids); otherwise as ot_l2l.  And its adjoint with C fixed. */
 ot_status ot_l2l_com(ot_grid* grid, const double* C, double* L, void* stream);
 ot_status ot_l2l_com_backward(ot_grid* grid, const double* C, double* Lbar, void* stream);
 

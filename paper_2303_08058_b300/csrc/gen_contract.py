@@ -95,23 +95,34 @@ def _flops(e):
     raise ValueError(f"unexpected node {e.func}")
 
 
-def deriv_flops(ncomp):
-    """FLOPs of one call of the generated derivative routine for the first
-    `ncomp` components: r^2 (5), 1/sqrt (2), r^-2 and the powers r^-(2k+1),
-    the cse'd polynomials and one scaling product per component."""
-    import sympy
-    polys, repl, reduced = _deriv_polys(ncomp)
+# Derivative components each per-pair routine produces (row layout): the
+# point-mass contractions read orders 0-3 of the reduced basis (0..15), the
+# multipole contractions orders 0-3 with three extra traces (0..18), the
+# angular term 12 of the order-4 components (20..28, 30..32).
+DERIV_SETS = {
+    "ot_deriv16_at": list(range(16)),
+    "ot_deriv19_at": list(range(19)),
+    "ot_deriv31_at": list(range(19)) + list(range(20, 29)) + [30, 31, 32],
+}
+
+
+def deriv_flops(name):
+    """FLOPs of one call of a generated derivative routine: r^2 (5), 1/sqrt
+    (2), r^-2 and the powers r^-(2k+1), the cse'd polynomials and one
+    scaling product per component."""
+    polys, repl, reduced = _deriv_polys(DERIV_SETS[name])
     kmax = max(k for k, _ in polys)
-    return 5 + 2 + 1 + kmax + sum(_flops(v) for _, v in repl) + sum(_flops(P) for P in reduced) + ncomp
+    return 5 + 2 + 1 + kmax + sum(_flops(v) for _, v in repl) + sum(_flops(P) for P in reduced) + len(polys)
 
 
-def _deriv_polys(ncomp):
+def _deriv_polys(indices):
     import sympy
     x, y, z = sympy.symbols("x y z", real=True)
     r2 = x * x + y * y + z * z
     G = -1 / sympy.sqrt(r2)
     polys = []
-    for e in ROW[:ncomp]:
+    for q in indices:
+        e = ROW[q]
         k = rank(e)
         expr = sympy.diff(G, x, e[0], y, e[1], z, e[2]) if k else G
         P = sympy.expand(sympy.simplify(expr * r2 ** sympy.Rational(2 * k + 1, 2)))
@@ -121,12 +132,16 @@ def _deriv_polys(ncomp):
     return polys, repl, reduced
 
 
-def deriv_code(name, ncomp):
-    """Straight-line code for the first `ncomp` row-layout derivatives of
+def deriv_code(name):
+    """Straight-line code for the derivative components DERIV_SETS[name] of
     G = -1/r at R = (x, y, z): with sympy, d^K G = P_K(x, y, z) r^-(2k+1) for
-    a polynomial P_K of degree k; the polynomials share subexpressions (cse)."""
+    a polynomial P_K of degree k; the polynomials share subexpressions (cse).
+    Entries of d outside the set are left untouched."""
+    import re
+
     import sympy
-    polys, repl, reduced = _deriv_polys(ncomp)
+    indices = DERIV_SETS[name]
+    polys, repl, reduced = _deriv_polys(indices)
     lines = [f"__device__ __forceinline__ void {name}(double x, double y, double z, double (&d)[36]) {{\n",
              "  const double r2 = fma(x, x, fma(y, y, z * z));\n",
              "  const double ir = 1.0 / sqrt(r2);\n",
@@ -134,7 +149,6 @@ def deriv_code(name, ncomp):
              "  const double s0 = ir;\n"]
     for k in range(1, max(k for k, _ in polys) + 1):
         lines.append(f"  const double s{k} = s{k - 1} * ir2;\n")
-    import re
 
     def cc(e):
         # integer powers as products (no pow calls), integer constants as doubles
@@ -146,7 +160,7 @@ def deriv_code(name, ncomp):
         return re.sub(r"(?<![\w.])(\d+)(?![\w.])", r"\1.0", t)
     for sym, val in repl:
         lines.append(f"  const double {sym} = {cc(val)};\n")
-    for q, ((k, _), P) in enumerate(zip(polys, reduced)):
+    for q, (k, _), P in zip(indices, polys, reduced):
         lines.append(f"  d[{q}] = ({cc(P)}) * s{k};\n")
     lines.append("}\n\n")
     return "".join(lines)
@@ -280,13 +294,16 @@ def emit():
     w("}\n\n")
 
     # derivatives at an arbitrary separation (centre-of-mass expansion centres)
-    w("// derivatives of -1/r of orders 0..4 (row layout) at R = (x, y, z)\n")
-    w(deriv_code("ot_deriv_at", 35))
-    w("// orders 0..3 only (point-mass sources)\n")
-    w(deriv_code("ot_deriv16_at", 16))
+    w("// derivatives of -1/r (row layout) at R = (x, y, z), the components each\n")
+    w("// contraction reads: point masses, multipole sources, multipole sources\n")
+    w("// with the angular term\n")
+    for name in DERIV_SETS:
+        w(deriv_code(name))
     w("// algorithmic FLOPs of one call of each (sqrt and the division count one each)\n")
-    w(f"constexpr int OT_DERIV35_FLOPS = {deriv_flops(35)};\n")
-    w(f"constexpr int OT_DERIV16_FLOPS = {deriv_flops(16)};\n\n")
+    for name in DERIV_SETS:
+        w(f"constexpr int {name.upper().replace('OT_DERIV', 'OT_DERIV').replace('_AT', '')}_FLOPS = "
+          f"{deriv_flops(name)};\n")
+    w("\n")
 
     # the same with the row of -o: odd-order derivatives negated
     w("// 16 FMAs (derivatives of the negated offset)\n")

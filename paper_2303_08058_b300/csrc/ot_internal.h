@@ -53,7 +53,7 @@ struct FwdParams {
     int accumulate;
     int n_nodes;
     int* status;           // [2]: first error code, its item
-    double hinv[MAXLEV];   // 1 / h_l (all 1 for explicit centres: nothing is pre-scaled by h)
+    double hinv[MAXLEV];   // 1 / h_l
     // explicit expansion centres (centre-of-mass mode)
     const double* C;       // [n][3][512] or null
     const int* ncoord;     // [n][3] node positions
@@ -120,17 +120,18 @@ cudaError_t launch_restrict_virtual(const double* vbar, const int* vmap, int n_p
 cudaError_t launch_cube_moments(const double* rho, double* M, double* m, const int* nodes, int n_list,
                                 const int* ninfo, const double* hinv, cudaStream_t s);
 cudaError_t launch_geometric_centres(double* C, const int* nodes, int n_list, const int* ninfo, const int* ncoord,
-                                     const double* hinv, cudaStream_t s);
+                                     double h0, cudaStream_t s);
 cudaError_t launch_m2m_com(double* M, double* m, double* C, const int* parents, int n_list, const int* children,
-                           const int* ninfo, const int* ncoord, const double* hinv, cudaStream_t s);
+                           const int* ninfo, const int* ncoord, double h0, cudaStream_t s);
 cudaError_t launch_l2l_com(double* L, const double* C, const int* parents, int n_list, const int* children,
-                           cudaStream_t s);
+                           const int* ninfo, const int* ncoord, double h0, cudaStream_t s);
 cudaError_t launch_l2l_com_adjoint(double* Lb, const double* C, const int* parents, int n_list, const int* children,
-                                   cudaStream_t s);
+                                   const int* ninfo, const int* ncoord, double h0, cudaStream_t s);
 cudaError_t launch_forward_com(const FwdParams& p, int mode, int wpb, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_com(const AdjParams& p, int mode, int wpb, int grid, cudaStream_t s);
 int forward_com_max_blocks_per_sm(int mode, int wpb);
-int deriv_flops(int ncomp);   // algorithmic FLOPs of one per-pair derivative evaluation (35 or 16 components)
+int adjoint_com_max_blocks_per_sm(int mode, int wpb);
+int deriv_flops(int ncomp);   // algorithmic FLOPs of one per-pair derivative evaluation (16, 19 or 31 components)
 int adjoint_com_max_blocks_per_sm(int mode, int wpb);
 cudaError_t launch_m2m(double* M, double* m, const int* parents, int n_list, const int* children,
                        const int* ninfo, const double* hinv, cudaStream_t s);

@@ -472,6 +472,38 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
     }
 }
 
+// M-bar of one source cell from the gathered g (reduced, h-scaled): expand
+// the traceless reduction and apply (-1)^m/m! * multiplicity * h^-m
+__device__ __forceinline__ void store_mbar(double* __restrict__ Mbar, int src, int scell, double h1,
+                                           const double (&g)[16]) {
+    const double h2 = h1 * h1, h3 = h2 * h1;
+    double Mb[20];
+    Mb[0] = g[0];
+    Mb[1] = -h1 * g[1];
+    Mb[2] = -h1 * g[2];
+    Mb[3] = -h1 * g[3];
+    Mb[4] = 0.5 * h2 * g[4];
+    Mb[5] = h2 * g[5];
+    Mb[6] = h2 * g[6];
+    Mb[7] = 0.5 * h2 * g[7];
+    Mb[8] = h2 * g[8];
+    Mb[9] = -0.5 * h2 * (g[4] + g[7]);
+    const double s6 = -h3 / 6.0, s2 = -0.5 * h3;
+    Mb[10] = s6 * g[9];
+    Mb[11] = s2 * g[10];
+    Mb[12] = s2 * g[11];
+    Mb[13] = s2 * g[12];
+    Mb[14] = -h3 * g[13];
+    Mb[15] = -s2 * (g[9] + g[12]);
+    Mb[16] = s6 * g[14];
+    Mb[17] = s2 * g[15];
+    Mb[18] = -s2 * (g[10] + g[14]);
+    Mb[19] = -s6 * (g[11] + g[15]);
+    double* out = Mbar + static_cast<size_t>(src) * NCOMP * NCELL + scell;
+#pragma unroll
+    for (int q = 0; q < 20; ++q) out[q * NCELL] = Mb[q];
+}
+
 template <class P>
 __device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
                              int node, int par, int half, int lane, int it);
@@ -519,7 +551,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
         const int* l1 = (level == 0) ? p.L.lists + p.L.root_off : p.L.lists + par * p.L.far_len;
         const int n1 = (level == 0) ? p.L.root_len : p.L.far_len;
         const int* l2 = p.L.lists + p.L.near_off;
-        const double h1 = p.hinv[level], h2 = h1 * h1, h3 = h2 * h1;
+        const double h1 = p.hinv[level];
         double g[16], g4[4];
 #pragma unroll
         for (int q = 0; q < 16; ++q) g[q] = 0.0;
@@ -535,32 +567,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
                                               p, g, g4, it);
                 }
                 walk_adjoint<true, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
-                // expand the traceless reduction and apply (-1)^m/m! * multiplicity * h^-m
-                double Mb[20];
-                Mb[0] = g[0];
-                Mb[1] = -h1 * g[1];
-                Mb[2] = -h1 * g[2];
-                Mb[3] = -h1 * g[3];
-                Mb[4] = 0.5 * h2 * g[4];
-                Mb[5] = h2 * g[5];
-                Mb[6] = h2 * g[6];
-                Mb[7] = 0.5 * h2 * g[7];
-                Mb[8] = h2 * g[8];
-                Mb[9] = -0.5 * h2 * (g[4] + g[7]);
-                const double s6 = -h3 / 6.0, s2 = -0.5 * h3;
-                Mb[10] = s6 * g[9];
-                Mb[11] = s2 * g[10];
-                Mb[12] = s2 * g[11];
-                Mb[13] = s2 * g[12];
-                Mb[14] = -h3 * g[13];
-                Mb[15] = -s2 * (g[9] + g[12]);
-                Mb[16] = s6 * g[14];
-                Mb[17] = s2 * g[15];
-                Mb[18] = -s2 * (g[10] + g[14]);
-                Mb[19] = -s6 * (g[11] + g[15]);
-                double* out = p.Mbar + static_cast<size_t>(src) * NCOMP * NCELL + scell;
-#pragma unroll
-                for (int q = 0; q < 20; ++q) out[q * NCELL] = Mb[q];
+                store_mbar(p.Mbar, src, scell, h1, g);
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
             if (level == 0) {
@@ -1084,47 +1091,56 @@ __global__ void cube_adjoint_kernel(const double* __restrict__ Mb, double* __res
 }
 
 // ---------------------------------------------------------------------------
-// centre-of-mass expansion centres: moments, L2L, and the passes with the
-// derivatives computed per pair from R = C_A - C_B
+// explicit (centre-of-mass) expansion centres
+//
+// Cells of non-leaf sub-grids are expanded about the centres C; cells of leaf
+// sub-grids and virtual descendants are uniform cubes about their geometric
+// centres (C is never read for them).  The passes work in the units of the
+// target level's h exactly as the table path does (same prescaling, same
+// epilogue): a pair whose two centres are geometric is at an integer offset
+// and reads the derivative table; any other pair evaluates the derivatives
+// at its own R/h.
 // ---------------------------------------------------------------------------
 
+// geometric centre coordinate of local cell s (in [-8, 16)) of a sub-grid
+// whose first cell is at integer position org: (org + s + 1/2) h
+__device__ __forceinline__ double geo_centre(int org, int s, double h) { return (org + s + 0.5) * h; }
+
 __global__ void geometric_centres_kernel(double* __restrict__ C, const int* __restrict__ nodes, int n_list,
-                                         const int* __restrict__ ninfo, const int* __restrict__ ncoord,
-                                         const double* __restrict__ hinv) {
+                                         const int* __restrict__ ninfo, const int* __restrict__ ncoord, double h0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_list * NCELL) return;
     const int node = nodes[t / NCELL], cell = t % NCELL;
-    const double h = 1.0 / hinv[ninfo[node] & 0xff];
+    const double h = ldexp(h0, -(ninfo[node] & 0xff));
     const int loc[3] = {cell & 7, (cell >> 3) & 7, cell >> 6};
     for (int a = 0; a < 3; ++a)
-        C[(static_cast<size_t>(node) * 3 + a) * NCELL + cell] = (8.0 * ncoord[3 * node + a] + loc[a] + 0.5) * h;
+        C[(static_cast<size_t>(node) * 3 + a) * NCELL + cell] = geo_centre(8 * ncoord[3 * node + a], loc[a], h);
 }
 
 // parent cell: centre = mass-weighted mean of the 8 children's centres
-// (geometric if the mass is zero), moments = children's moments shifted there
+// (geometric if the mass is exactly zero), moments = the children's moments
+// shifted binomially to it
 __global__ void m2m_com_kernel(double* __restrict__ M, double* __restrict__ m, double* __restrict__ C,
                                const int* __restrict__ parents, int n_list, const int* __restrict__ children,
-                               const int* __restrict__ ninfo, const int* __restrict__ ncoord,
-                               const double* __restrict__ hinv) {
+                               const int* __restrict__ ninfo, const int* __restrict__ ncoord, double h0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_list * NCELL) return;
     const int k = t / NCELL, cell = t % NCELL;
     const int P = parents[k];
     const int g[3] = {cell & 7, (cell >> 3) & 7, cell >> 6};
-    int cn[8], cc[8];
     double mass = 0.0, w[3] = {0.0, 0.0, 0.0};
 #pragma unroll 1
     for (int b = 0; b < 8; ++b) {
         const int cx = 2 * g[0] + (b & 1), cy = 2 * g[1] + ((b >> 1) & 1), cz = 2 * g[2] + (b >> 2);
-        cn[b] = children[8 * k + (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
-        cc[b] = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
-        const double mc = M[static_cast<size_t>(cn[b]) * NCOMP * NCELL + cc[b]];
+        const int cn = children[8 * k + (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
+        const int cc = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
+        const double mc = M[static_cast<size_t>(cn) * NCOMP * NCELL + cc];
         mass += mc;
-        for (int a = 0; a < 3; ++a) w[a] = fma(mc, C[(static_cast<size_t>(cn[b]) * 3 + a) * NCELL + cc[b]], w[a]);
+        for (int a = 0; a < 3; ++a) w[a] += mc * C[(static_cast<size_t>(cn) * 3 + a) * NCELL + cc];
     }
     double X[3];
-    const double h = 1.0 / hinv[ninfo[P] & 0xff];
-    for (int a = 0; a < 3; ++a) X[a] = (mass != 0.0) ? w[a] / mass : (8.0 * ncoord[3 * P + a] + g[a] + 0.5) * h;
+    const double h = ldexp(h0, -(ninfo[P] & 0xff));
+    for (int a = 0; a < 3; ++a) X[a] = (mass != 0.0) ? w[a] / mass : geo_centre(8 * ncoord[3 * P + a], g[a], h);
     Dense4 acc;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1134,9 +1150,12 @@ __global__ void m2m_com_kernel(double* __restrict__ M, double* __restrict__ m, d
             for (int c = 0; c < 4; ++c) acc.v[a][b][c] = 0.0;
 #pragma unroll 1
     for (int b = 0; b < 8; ++b) {
+        const int cx = 2 * g[0] + (b & 1), cy = 2 * g[1] + ((b >> 1) & 1), cz = 2 * g[2] + (b >> 2);
+        const int cn = children[8 * k + (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
+        const int cc = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
         Dense4 v;
-        to_dense(M + static_cast<size_t>(cn[b]) * NCOMP * NCELL + cc[b], v);
-        const double* Cc = C + static_cast<size_t>(cn[b]) * 3 * NCELL + cc[b];
+        to_dense(M + static_cast<size_t>(cn) * NCOMP * NCELL + cc, v);
+        const double* Cc = C + static_cast<size_t>(cn) * 3 * NCELL + cc;
         shift1<0>(v, Cc[0] - X[0]);
         shift1<1>(v, Cc[NCELL] - X[1]);
         shift1<2>(v, Cc[2 * NCELL] - X[2]);
@@ -1152,8 +1171,27 @@ __global__ void m2m_com_kernel(double* __restrict__ M, double* __restrict__ m, d
     for (int a = 0; a < 3; ++a) C[(static_cast<size_t>(P) * 3 + a) * NCELL + cell] = X[a];
 }
 
+// centre of one cell of `node`: C for non-leaf sub-grids, geometric otherwise
+__device__ __forceinline__ void cell_centre(const double* __restrict__ C, const int* __restrict__ ninfo,
+                                            const int* __restrict__ ncoord, double h0, int node, int cell,
+                                            double (&X)[3]) {
+    const int info = ninfo[node];
+    if ((info >> 8) & 1) {
+        const double h = ldexp(h0, -(info & 0xff));
+        X[0] = geo_centre(8 * ncoord[3 * node], cell & 7, h);
+        X[1] = geo_centre(8 * ncoord[3 * node + 1], (cell >> 3) & 7, h);
+        X[2] = geo_centre(8 * ncoord[3 * node + 2], cell >> 6, h);
+    } else {
+        const double* c = C + static_cast<size_t>(node) * 3 * NCELL + cell;
+        X[0] = c[0];
+        X[1] = c[NCELL];
+        X[2] = c[2 * NCELL];
+    }
+}
+
 __global__ void l2l_com_kernel(double* __restrict__ L, const double* __restrict__ C, const int* __restrict__ parents,
-                               int n_list, const int* __restrict__ children) {
+                               int n_list, const int* __restrict__ children, const int* __restrict__ ninfo,
+                               const int* __restrict__ ncoord, double h0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_list * 8 * NCELL) return;
     const int k = t / (8 * NCELL);
@@ -1163,28 +1201,29 @@ __global__ void l2l_com_kernel(double* __restrict__ L, const double* __restrict_
     const int cx = (oct & 1) * 8 + (ccell & 7), cy = ((oct >> 1) & 1) * 8 + ((ccell >> 3) & 7),
               cz = (oct >> 2) * 8 + (ccell >> 6);
     const int pcell = (cx >> 1) + 8 * (cy >> 1) + 64 * (cz >> 1);
-    const double* Cc = C + static_cast<size_t>(Cn) * 3 * NCELL + ccell;
-    const double* Cp = C + static_cast<size_t>(P) * 3 * NCELL + pcell;
+    double Xc[3], Xp[3];
+    cell_centre(C, ninfo, ncoord, h0, Cn, ccell, Xc);
+    cell_centre(C, ninfo, ncoord, h0, P, pcell, Xp);
     Dense4 v;
     to_dense(L + static_cast<size_t>(P) * NCOMP * NCELL + pcell, v);
-    lshift1<0>(v, Cc[0] - Cp[0]);
-    lshift1<1>(v, Cc[NCELL] - Cp[NCELL]);
-    lshift1<2>(v, Cc[2 * NCELL] - Cp[2 * NCELL]);
+    lshift1<0>(v, Xc[0] - Xp[0]);
+    lshift1<1>(v, Xc[1] - Xp[1]);
+    lshift1<2>(v, Xc[2] - Xp[2]);
     from_dense(v, L + static_cast<size_t>(Cn) * NCOMP * NCELL + ccell, true);
 }
 
-// transpose of l2l_com_kernel: every parent cell adds the transposed shifts
-// of its 8 child cells' adjoints (centres held fixed)
+// transpose of l2l_com_kernel (centres held fixed)
 __global__ void l2l_com_adjoint_kernel(double* __restrict__ Lb, const double* __restrict__ C,
                                        const int* __restrict__ parents, int n_list,
-                                       const int* __restrict__ children) {
+                                       const int* __restrict__ children, const int* __restrict__ ninfo,
+                                       const int* __restrict__ ncoord, double h0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_list * NCELL) return;
     const int k = t / NCELL, cell = t % NCELL;
     const int P = parents[k];
     const int gx = cell & 7, gy = (cell >> 3) & 7, gz = cell >> 6;
-    const double* Cp = C + static_cast<size_t>(P) * 3 * NCELL + cell;
-    const double xp = Cp[0], yp = Cp[NCELL], zp = Cp[2 * NCELL];
+    double Xp[3];
+    cell_centre(C, ninfo, ncoord, h0, P, cell, Xp);
     Dense4 acc;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1197,12 +1236,13 @@ __global__ void l2l_com_adjoint_kernel(double* __restrict__ Lb, const double* __
         const int cx = 2 * gx + (b & 1), cy = 2 * gy + ((b >> 1) & 1), cz = 2 * gz + (b >> 2);
         const int Cn = children[8 * k + (cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
         const int ccell = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
-        const double* Cc = C + static_cast<size_t>(Cn) * 3 * NCELL + ccell;
+        double Xc[3];
+        cell_centre(C, ninfo, ncoord, h0, Cn, ccell, Xc);
         Dense4 v;
         to_dense(Lb + static_cast<size_t>(Cn) * NCOMP * NCELL + ccell, v);
-        lshift1_t<2>(v, Cc[2 * NCELL] - zp);
-        lshift1_t<1>(v, Cc[NCELL] - yp);
-        lshift1_t<0>(v, Cc[0] - xp);
+        lshift1_t<2>(v, Xc[2] - Xp[2]);
+        lshift1_t<1>(v, Xc[1] - Xp[1]);
+        lshift1_t<0>(v, Xc[0] - Xp[0]);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1213,67 +1253,96 @@ __global__ void l2l_com_adjoint_kernel(double* __restrict__ Lb, const double* __
     from_dense(acc, Lb + static_cast<size_t>(P) * NCOMP * NCELL + cell, true);
 }
 
-// source expansion centre seen from a target sub-grid at `org` (its first
-// cell's global position) through neighbour entry e: explicit for real
-// cells, the geometric centre of a virtual descendant's cell
-__device__ __forceinline__ void com_source_centre(const double* __restrict__ C, int2 e, int kind, const int (&org)[3],
-                                                  int sx, int sy, int sz, double h, double (&X)[3]) {
-    if (kind == K_LEAF || kind == K_MULTI) {
-        const double* c = C + static_cast<size_t>(e.x) * 3 * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
-        X[0] = c[0];
-        X[1] = c[NCELL];
-        X[2] = c[2 * NCELL];
+// R/h for a pair whose source sits at X: lanes without a source of the class
+// being contracted get a unit separation (their terms are zero)
+__device__ __forceinline__ void scaled_sep(bool has, const double (&XA)[3], const double (&X)[3], double hinv,
+                                           double& rx, double& ry, double& rz) {
+    if (has) {
+        rx = (XA[0] - X[0]) * hinv;
+        ry = (XA[1] - X[1]) * hinv;
+        rz = (XA[2] - X[2]) * hinv;
     } else {
-        X[0] = (org[0] + sx + 0.5) * h;
-        X[1] = (org[1] + sy + 0.5) * h;
-        X[2] = (org[2] + sz + 0.5) * h;
+        rx = 0.0;
+        ry = 0.0;
+        rz = 1.0;
     }
 }
 
-template <int MODE>
-__device__ __forceinline__ void com_pair(const FwdParams& p, int2 e, int kind, const int (&org)[3], int sx, int sy,
-                                         int sz, double h, const double (&XA)[3], bool angular, double (&a)[16],
-                                         double (&c)[3], double (&t4)[9]) {
-    const bool mono = (MODE & 2) && kind >= K_LEAF;
-    const bool multi = (MODE & 1) && kind == K_MULTI;
-    const bool any_mono = __any_sync(0xffffffffu, mono);
-    const bool any_multi = __any_sync(0xffffffffu, multi);
-    if (!any_mono && !any_multi) return;
-    double X[3];
-    if (kind == K_NONE) {            // no source: any finite separation (its terms are zero)
-        X[0] = XA[0];
-        X[1] = XA[1];
-        X[2] = XA[2] + h;
-    } else {
-        com_source_centre(p.C, e, kind, org, sx, sy, sz, h, X);
-    }
-    double d[36];
-    if (any_multi) ot_deriv_at(XA[0] - X[0], XA[1] - X[1], XA[2] - X[2], d);
-    else ot_deriv16_at(XA[0] - X[0], XA[1] - X[1], XA[2] - X[2], d);
-    if (any_mono) ot_mono_fwd(a, source_mass(p, e, kind, sx, sy, sz), d);
-    if (any_multi) {
-        double r[16];
-        source_moments(p, e, multi, sx, sy, sz, r);
-        ot_multi_fwd(a, r, d);
-        if (angular) ot_angular_fwd(c, t4, r, r[0], d);
-    }
-}
-
-template <int MODE>
-__device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, int len, bool angular, bool paired,
+// One stencil segment of a target with explicit centres.  PAIRED: each entry
+// o stands for the sources at t + o and t - o.
+template <int MODE, bool PAIRED>
+__device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, int len, bool angular, bool leafT,
                                                  int tx, int ty, int tz, const int2* __restrict__ s_nb,
-                                                 const FwdParams& p, const int (&org)[3], double h,
+                                                 const FwdParams& p, const int (&org)[3], double h, double hinv,
                                                  const double (&XA)[3], double (&a)[16], double (&c)[3],
                                                  double (&t4)[9], int item) {
+    constexpr int NS = PAIRED ? 2 : 1;
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
-        for (int side = 0; side < (paired ? 2 : 1); ++side) {
-            const int sg = side ? -1 : 1;
-            const int sx = tx + sg * ox, sy = ty + sg * oy, sz = tz + sg * oz;
-            const int2 e = s_nb[nb_index(sx, sy, sz)];
-            const int kind = checked_kind(p, e, item);
-            com_pair<MODE>(p, e, kind, org, sx, sy, sz, h, XA, angular, a, c, t4);
+        int sx[NS], sy[NS], sz[NS], kd[NS];
+        int2 e[NS];
+#pragma unroll
+        for (int sd = 0; sd < NS; ++sd) {
+            const int sg = sd ? -1 : 1;
+            sx[sd] = tx + sg * ox;
+            sy[sd] = ty + sg * oy;
+            sz[sd] = tz + sg * oz;
+            e[sd] = s_nb[nb_index(sx[sd], sy[sd], sz[sd])];
+            kd[sd] = checked_kind(p, e[sd], item);
+        }
+        if (MODE & 2) {
+            if (leafT) {
+                // both centres geometric: R/h = -o, the table row (paired as on the table path)
+                bool mono = kd[0] >= K_LEAF;
+                if (PAIRED) mono = mono || kd[NS - 1] >= K_LEAF;
+                if (__any_sync(0xffffffffu, mono)) {
+                    const double mp = source_mass(p, e[0], kd[0], sx[0], sy[0], sz[0]);
+                    double d[36];
+                    load_row16(d, p.Dt, offset_row(ox, oy, oz));
+                    if (PAIRED) {
+                        const double mm = source_mass(p, e[NS - 1], kd[NS - 1], sx[NS - 1], sy[NS - 1], sz[NS - 1]);
+                        ot_mono_fwd_pair(a, mp + mm, mp - mm, d);
+                    } else {
+                        ot_mono_fwd(a, mp, d);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int sd = 0; sd < NS; ++sd) {
+                    const bool mono = kd[sd] >= K_LEAF;
+                    if (!__any_sync(0xffffffffu, mono)) continue;
+                    const double X[3] = {geo_centre(org[0], sx[sd], h), geo_centre(org[1], sy[sd], h),
+                                         geo_centre(org[2], sz[sd], h)};
+                    double rx, ry, rz, d[36];
+                    scaled_sep(mono, XA, X, hinv, rx, ry, rz);
+                    ot_deriv16_at(rx, ry, rz, d);
+                    ot_mono_fwd(a, source_mass(p, e[sd], kd[sd], sx[sd], sy[sd], sz[sd]), d);
+                }
+            }
+        }
+        if (MODE & 1) {
+#pragma unroll
+            for (int sd = 0; sd < NS; ++sd) {
+                const bool multi = kd[sd] == K_MULTI;
+                if (!__any_sync(0xffffffffu, multi)) continue;
+                double X[3] = {0.0, 0.0, 0.0};
+                if (multi) {
+                    const double* cb = p.C + static_cast<size_t>(e[sd].x) * 3 * NCELL + (sx[sd] & 7) +
+                                       8 * (sy[sd] & 7) + 64 * (sz[sd] & 7);
+                    X[0] = cb[0];
+                    X[1] = cb[NCELL];
+                    X[2] = cb[2 * NCELL];
+                }
+                double rx, ry, rz, d[36];
+                scaled_sep(multi, XA, X, hinv, rx, ry, rz);
+                if (angular) ot_deriv31_at(rx, ry, rz, d);
+                else ot_deriv19_at(rx, ry, rz, d);
+                double r[16];
+                source_moments(p, e[sd], multi, sx[sd], sy[sd], sz[sd], r);
+                ot_multi_fwd(a, r, d);
+                if (angular) ot_angular_fwd(c, t4, r, r[0], d);
+            }
         }
     }
 }
@@ -1295,14 +1364,23 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
         const int info = __ldg(p.ninfo + node);
         const int level = info & 0xff;
         const bool leafT = (info >> 8) & 1;
-        const double h = p.hreal[level];
+        const double h = p.hreal[level], hinv = p.hinv[level];
         const int org[3] = {8 * __ldg(p.ncoord + 3 * node), 8 * __ldg(p.ncoord + 3 * node + 1),
                             8 * __ldg(p.ncoord + 3 * node + 2)};
         int tx, ty, tz;
         lane_cell(lane, par, half, tx, ty, tz);
         const int tcell = tx + 8 * ty + 64 * tz;
-        const double* ca = p.C + static_cast<size_t>(node) * 3 * NCELL + tcell;
-        const double XA[3] = {ca[0], ca[NCELL], ca[2 * NCELL]};
+        double XA[3];
+        if (leafT) {
+            XA[0] = geo_centre(org[0], tx, h);
+            XA[1] = geo_centre(org[1], ty, h);
+            XA[2] = geo_centre(org[2], tz, h);
+        } else {
+            const double* ca = p.C + static_cast<size_t>(node) * 3 * NCELL + tcell;
+            XA[0] = ca[0];
+            XA[1] = ca[NCELL];
+            XA[2] = ca[2 * NCELL];
+        }
         double a[16], c[3], t4[9];
 #pragma unroll
         for (int q = 0; q < 16; ++q) a[q] = 0.0;
@@ -1311,34 +1389,39 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) t4[q] = 0.0;
         if (level == 0) {
-            walk_forward_com<MODE>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, true, tx, ty, tz, s_nb[warp], p,
-                                   org, h, XA, a, c, t4, it);
+            walk_forward_com<MODE, true>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, leafT, tx, ty, tz,
+                                         s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
         } else {
             const int* lf = p.L.lists + par * p.L.far_len;
-            walk_forward_com<MODE>(lf, p.L.far_pairs, !leafT, true, tx, ty, tz, s_nb[warp], p, org, h, XA, a, c, t4,
-                                   it);
-            walk_forward_com<MODE>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, false, tx, ty, tz,
-                                   s_nb[warp], p, org, h, XA, a, c, t4, it);
+            walk_forward_com<MODE, true>(lf, p.L.far_pairs, !leafT, leafT, tx, ty, tz, s_nb[warp], p, org, h, hinv,
+                                         XA, a, c, t4, it);
+            walk_forward_com<MODE, false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, leafT, tx, ty,
+                                          tz, s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
         }
         if (leafT)
-            walk_forward_com<MODE>(p.L.lists + p.L.near_off, p.L.near_len, false, true, tx, ty, tz, s_nb[warp], p,
-                                   org, h, XA, a, c, t4, it);
+            walk_forward_com<MODE, true>(p.L.lists + p.L.near_off, p.L.near_len, false, true, tx, ty, tz,
+                                         s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
         store_forward<MODE>(p, node, level, leafT, tcell, a, c, t4);
         __syncwarp();
     }
 }
 
-// adjoint gather with fixed centres: source B collects from targets A
-template <bool MULTI>
-__device__ __forceinline__ void walk_adjoint_com(const int* __restrict__ list, int len, bool near_seg, bool paired,
-                                                 int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
-                                                 const AdjParams& p, const double (&XB)[3], double (&g)[16],
-                                                 double (&g4)[4], int item) {
+// Adjoint gather with fixed centres: source cell B collects from the targets
+// of its transposed stencil (target = source + sg * o, sg = +1, and -1 too
+// when PAIRED).  MULTI: multipole source, derivatives per pair.  Otherwise a
+// point-mass source: a leaf target is at an integer offset (the table row of
+// R/h = sg * o), a non-leaf target uses its own centre.
+template <bool MULTI, bool PAIRED>
+__device__ __forceinline__ void walk_adjoint_com(const int* __restrict__ list, int len, bool near_seg, int sx0,
+                                                 int sy0, int sz0, const int2* __restrict__ s_nb, const AdjParams& p,
+                                                 const int (&org)[3], double h, double hinv, const double (&XB)[3],
+                                                 double (&g)[16], double (&g4)[4], int item) {
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
-        for (int side = 0; side < (paired ? 2 : 1); ++side) {
-            const int sg = side ? -1 : 1;
+#pragma unroll
+        for (int sd = 0; sd < (PAIRED ? 2 : 1); ++sd) {
+            const int sg = sd ? -1 : 1;
             const int tx = sx0 + sg * ox, ty = sy0 + sg * oy, tz = sz0 + sg * oz;
             const int2 e = s_nb[nb_index(tx, ty, tz)];
             const int kind = e.y & 3;
@@ -1349,31 +1432,118 @@ __device__ __forceinline__ void walk_adjoint_com(const int* __restrict__ list, i
             }
             if (!__any_sync(0xffffffffu, valid)) continue;
             const int tcell = (tx & 7) + 8 * (ty & 7) + 64 * (tz & 7);
-            double lb[16], XA[3] = {XB[0], XB[1], XB[2] + 1.0};   // dummy separation for lanes without a target
+            double lb[16];
             if (valid) {
                 const double* src = p.Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + tcell;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) lb[q] = __ldg(src + q * NCELL);
-                const double* ca = p.C + static_cast<size_t>(e.x) * 3 * NCELL + tcell;
-                XA[0] = ca[0];
-                XA[1] = ca[NCELL];
-                XA[2] = ca[2 * NCELL];
             } else {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) lb[q] = 0.0;
             }
             double d[36];
             if (MULTI) {
-                ot_deriv_at(XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2], d);
+                double XA[3] = {0.0, 0.0, 0.0};
+                if (valid) {
+                    if (kind == K_MULTI) {
+                        const double* ca = p.C + static_cast<size_t>(e.x) * 3 * NCELL + tcell;
+                        XA[0] = ca[0];
+                        XA[1] = ca[NCELL];
+                        XA[2] = ca[2 * NCELL];
+                    } else {
+                        XA[0] = geo_centre(org[0], tx, h);
+                        XA[1] = geo_centre(org[1], ty, h);
+                        XA[2] = geo_centre(org[2], tz, h);
+                    }
+                }
+                double rx, ry, rz;
+                scaled_sep(valid, XA, XB, hinv, rx, ry, rz);
+                ot_deriv19_at(rx, ry, rz, d);
                 ot_multi_adj(g, lb, d);
             } else {
-                ot_deriv16_at(XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2], d);
+                // the table row of R/h = sg * o is that of the offset -sg * o
+                const int row = sd ? offset_row(ox, oy, oz) : NOFF - 1 - offset_row(ox, oy, oz);
+                load_row16(d, p.Dt, row);
+                const bool own = valid && kind == K_MULTI;
+                if (__any_sync(0xffffffffu, own) && own) {
+                    const double* ca = p.C + static_cast<size_t>(e.x) * 3 * NCELL + tcell;
+                    const double XA[3] = {ca[0], ca[NCELL], ca[2 * NCELL]};
+                    double rx, ry, rz;
+                    scaled_sep(true, XA, XB, hinv, rx, ry, rz);
+                    ot_deriv16_at(rx, ry, rz, d);
+                }
                 ot_mono_adj(g4, lb, d);
             }
         }
     }
 }
 
+// point-mass adjoint by a non-leaf target (centre from C): every point-mass
+// source of its stencil receives <lb, dG(R/h)> by atomic add
+template <bool PAIRED>
+__device__ __forceinline__ void walk_scatter_com(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                 const int2* __restrict__ s_nb, const AdjParams& p,
+                                                 const int (&org)[3], double h, double hinv, const double (&XA)[3],
+                                                 const double (&lb)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+#pragma unroll
+        for (int sd = 0; sd < (PAIRED ? 2 : 1); ++sd) {
+            const int sg = sd ? -1 : 1;
+            const int sx = tx + sg * ox, sy = ty + sg * oy, sz = tz + sg * oz;
+            const int2 e = s_nb[nb_index(sx, sy, sz)];
+            int kind = e.y & 3;
+            if (kind != K_NONE && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
+                report(p.status, 3, item);
+                kind = K_NONE;
+            }
+            const bool mono = kind >= K_LEAF;
+            if (!__any_sync(0xffffffffu, mono)) continue;
+            const double X[3] = {geo_centre(org[0], sx, h), geo_centre(org[1], sy, h), geo_centre(org[2], sz, h)};
+            double rx, ry, rz, d[36];
+            scaled_sep(mono, XA, X, hinv, rx, ry, rz);
+            ot_deriv16_at(rx, ry, rz, d);
+            double ev, od;
+            ot_mono_adj_split(ev, od, lb, d);
+            scatter_mass(p, e, kind, sx, sy, sz, ev + od);
+        }
+    }
+}
+
+__device__ void scatter_item_com(const AdjParams& p, int2* s_nb, int node, int par, int half, int lane, int it) {
+    int tx, ty, tz;
+    lane_cell(lane, par, half, tx, ty, tz);
+    const int tcell = tx + 8 * ty + 64 * tz;
+    double lb[16];
+    const double* src = p.Lrbar + static_cast<size_t>(node) * NRED * NCELL + tcell;
+    bool nz = false;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        lb[q] = __ldg(src + q * NCELL);
+        nz |= lb[q] != 0.0;
+    }
+    if (!__any_sync(0xffffffffu, nz)) return;
+    if (lane < 27) s_nb[lane] = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
+    __syncwarp();
+    const int level = __ldg(p.ninfo + node) & 0xff;
+    const double h = p.hreal[level], hinv = p.hinv[level];
+    const int org[3] = {8 * __ldg(p.ncoord + 3 * node), 8 * __ldg(p.ncoord + 3 * node + 1),
+                        8 * __ldg(p.ncoord + 3 * node + 2)};
+    const double* ca = p.C + static_cast<size_t>(node) * 3 * NCELL + tcell;
+    const double XA[3] = {ca[0], ca[NCELL], ca[2 * NCELL]};
+    if (level == 0) {
+        walk_scatter_com<true>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, org, h, hinv, XA, lb, it);
+    } else {
+        const int* lf = p.L.lists + par * p.L.far_len;
+        walk_scatter_com<true>(lf, p.L.far_pairs, tx, ty, tz, s_nb, p, org, h, hinv, XA, lb, it);
+        walk_scatter_com<false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, tx, ty, tz, s_nb, p, org, h, hinv,
+                                XA, lb, it);
+    }
+}
+
+// MODE bits: 1 multipole sources (gather), 2 point-mass sources (gather),
+// 4 point-mass adjoint by target (items with bit 30 set, atomic adds)
 template <int MODE>
 __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
     __shared__ int2 s_nb[8][27];
@@ -1385,6 +1555,17 @@ __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
         const int it = __shfl_sync(0xffffffffu, v, 0);
         if (it >= p.n_items) break;
         const int item = __ldg(p.items + it);
+        if ((MODE & 4) && ((item >> 30) & 1)) {
+            const int tgt = item & 0x3fffffff;
+            const int node = tgt >> 4;
+            // a leaf target has a geometric centre: the table path's scatter
+            if ((__ldg(p.ninfo + node) >> 8) & 1)
+                scatter_item(p, p.nbr, p.ninfo, s_nb[warp], node, (tgt >> 1) & 7, tgt & 1, lane, it);
+            else
+                scatter_item_com(p, s_nb[warp], node, (tgt >> 1) & 7, tgt & 1, lane, it);
+            __syncwarp();
+            continue;
+        }
         const int src = item >> 4, par = (item >> 1) & 7, half = item & 1;
         const bool virt = src >= p.n_nodes;
         const int2* nbt = virt ? p.vnbr + static_cast<size_t>(src - p.n_nodes) * 27
@@ -1403,64 +1584,45 @@ __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
             skind = ((info >> 8) & 1) ? K_LEAF : K_MULTI;
             crd = p.ncoord + 3 * src;
         }
+        const double h = p.hreal[level], hinv = p.hinv[level];
+        const int org[3] = {8 * __ldg(crd), 8 * __ldg(crd + 1), 8 * __ldg(crd + 2)};
         int sx, sy, sz;
         lane_cell(lane, par, half, sx, sy, sz);
         const int scell = sx + 8 * sy + 64 * sz;
         double XB[3];
-        if (virt) {
-            const double h = p.hreal[level];
-            XB[0] = (8.0 * crd[0] + sx + 0.5) * h;
-            XB[1] = (8.0 * crd[1] + sy + 0.5) * h;
-            XB[2] = (8.0 * crd[2] + sz + 0.5) * h;
-        } else {
+        if (skind == K_MULTI) {
             const double* cb = p.C + static_cast<size_t>(src) * 3 * NCELL + scell;
             XB[0] = cb[0];
             XB[1] = cb[NCELL];
             XB[2] = cb[2 * NCELL];
+        } else {
+            XB[0] = geo_centre(org[0], sx, h);
+            XB[1] = geo_centre(org[1], sy, h);
+            XB[2] = geo_centre(org[2], sz, h);
         }
         const int* l1 = (level == 0) ? p.L.lists + p.L.root_off : p.L.lists + par * p.L.far_len;
         const int* l2 = p.L.lists + p.L.near_off;
+        const int np = (level == 0) ? p.L.root_len : p.L.far_pairs;
+        const int ns = (level == 0) ? 0 : p.L.far_len - p.L.far_pairs;
         double g[16], g4[4];
 #pragma unroll
         for (int q = 0; q < 16; ++q) g[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) g4[q] = 0.0;
-        const int np = (level == 0) ? p.L.root_len : p.L.far_pairs;
-        const int ns = (level == 0) ? 0 : p.L.far_len - p.L.far_pairs;
         if (skind == K_MULTI) {
             if ((MODE & 1) && p.Mbar != nullptr) {
-                walk_adjoint_com<true>(l1, np, false, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
-                walk_adjoint_com<true>(l1 + np, ns, false, false, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
-                walk_adjoint_com<true>(l2, p.L.near_len, true, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
-                double Mb[20];
-                Mb[0] = g[0];
-                Mb[1] = -g[1];
-                Mb[2] = -g[2];
-                Mb[3] = -g[3];
-                Mb[4] = 0.5 * g[4];
-                Mb[5] = g[5];
-                Mb[6] = g[6];
-                Mb[7] = 0.5 * g[7];
-                Mb[8] = g[8];
-                Mb[9] = -0.5 * (g[4] + g[7]);
-                Mb[10] = -g[9] / 6.0;
-                Mb[11] = -0.5 * g[10];
-                Mb[12] = -0.5 * g[11];
-                Mb[13] = -0.5 * g[12];
-                Mb[14] = -g[13];
-                Mb[15] = 0.5 * (g[9] + g[12]);
-                Mb[16] = -g[14] / 6.0;
-                Mb[17] = -0.5 * g[15];
-                Mb[18] = 0.5 * (g[10] + g[14]);
-                Mb[19] = (g[11] + g[15]) / 6.0;
-                double* out = p.Mbar + static_cast<size_t>(src) * NCOMP * NCELL + scell;
-#pragma unroll
-                for (int q = 0; q < 20; ++q) out[q * NCELL] = Mb[q];
+                walk_adjoint_com<true, true>(l1, np, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4, it);
+                walk_adjoint_com<true, false>(l1 + np, ns, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4,
+                                              it);
+                walk_adjoint_com<true, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g,
+                                             g4, it);
+                store_mbar(p.Mbar, src, scell, hinv, g);
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
-            walk_adjoint_com<false>(l1, np, false, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
-            walk_adjoint_com<false>(l1 + np, ns, false, false, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
-            walk_adjoint_com<false>(l2, p.L.near_len, true, true, sx, sy, sz, s_nb[warp], p, XB, g, g4, it);
+            walk_adjoint_com<false, true>(l1, np, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4, it);
+            walk_adjoint_com<false, false>(l1 + np, ns, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4, it);
+            walk_adjoint_com<false, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4,
+                                          it);
             const double val = (g4[0] + g4[1]) + (g4[2] + g4[3]);
             if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = val;
             else p.mbar[static_cast<size_t>(src) * NCELL + scell] = val;
@@ -1634,32 +1796,34 @@ cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nod
 }
 
 cudaError_t launch_geometric_centres(double* C, const int* nodes, int n_list, const int* ninfo, const int* ncoord,
-                                     const double* hinv, cudaStream_t s) {
+                                     double h0, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
     geometric_centres_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(C, nodes, n_list, ninfo, ncoord,
-                                                                                    hinv);
+                                                                                    h0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2m_com(double* M, double* m, double* C, const int* parents, int n_list, const int* children,
-                           const int* ninfo, const int* ncoord, const double* hinv, cudaStream_t s) {
+                           const int* ninfo, const int* ncoord, double h0, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
     m2m_com_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(M, m, C, parents, n_list, children, ninfo,
-                                                                          ncoord, hinv);
+                                                                          ncoord, h0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_l2l_com(double* L, const double* C, const int* parents, int n_list, const int* children,
-                           cudaStream_t s) {
+                           const int* ninfo, const int* ncoord, double h0, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
-    l2l_com_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(L, C, parents, n_list, children);
+    l2l_com_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(L, C, parents, n_list, children, ninfo,
+                                                                              ncoord, h0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_l2l_com_adjoint(double* Lb, const double* C, const int* parents, int n_list, const int* children,
-                                   cudaStream_t s) {
+                                   const int* ninfo, const int* ncoord, double h0, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
-    l2l_com_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(Lb, C, parents, n_list, children);
+    l2l_com_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(Lb, C, parents, n_list, children,
+                                                                                  ninfo, ncoord, h0);
     return cudaGetLastError();
 }
 
@@ -1678,12 +1842,16 @@ cudaError_t launch_adjoint_com(const AdjParams& p, int mode, int wpb, int grid, 
     switch (mode) {
         case 1: adjoint_com_kernel<1><<<grid, 32 * wpb, 0, s>>>(p); break;
         case 2: adjoint_com_kernel<2><<<grid, 32 * wpb, 0, s>>>(p); break;
-        default: adjoint_com_kernel<3><<<grid, 32 * wpb, 0, s>>>(p); break;
+        case 3: adjoint_com_kernel<3><<<grid, 32 * wpb, 0, s>>>(p); break;
+        case 4: adjoint_com_kernel<4><<<grid, 32 * wpb, 0, s>>>(p); break;
+        default: adjoint_com_kernel<5><<<grid, 32 * wpb, 0, s>>>(p); break;
     }
     return cudaGetLastError();
 }
 
-int deriv_flops(int ncomp) { return ncomp == 35 ? OT_DERIV35_FLOPS : OT_DERIV16_FLOPS; }
+int deriv_flops(int ncomp) {
+    return ncomp == 31 ? OT_DERIV31_FLOPS : ncomp == 19 ? OT_DERIV19_FLOPS : OT_DERIV16_FLOPS;
+}
 
 int forward_com_max_blocks_per_sm(int mode, int wpb) {
     int n = 0;
@@ -1695,8 +1863,11 @@ int forward_com_max_blocks_per_sm(int mode, int wpb) {
 
 int adjoint_com_max_blocks_per_sm(int mode, int wpb) {
     int n = 0;
-    const void* f = (mode == 1) ? (const void*)adjoint_com_kernel<1>
-                  : (mode == 2) ? (const void*)adjoint_com_kernel<2> : (const void*)adjoint_com_kernel<3>;
+    const void* f = (mode == 1)   ? (const void*)adjoint_com_kernel<1>
+                    : (mode == 2) ? (const void*)adjoint_com_kernel<2>
+                    : (mode == 3) ? (const void*)adjoint_com_kernel<3>
+                    : (mode == 4) ? (const void*)adjoint_com_kernel<4>
+                                  : (const void*)adjoint_com_kernel<5>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
     return n;
 }

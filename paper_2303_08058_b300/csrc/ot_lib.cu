@@ -189,7 +189,7 @@ struct ot_grid {
     int maxb_fast5[9] = {};
     int maxb_emu[4][9] = {};            // forward with double-float point masses, modes 2 and 3
     int maxb_com_fwd[4][9] = {};        // explicit expansion centres
-    int maxb_com_adj[4][9] = {};
+    int maxb_com_adj[6][9] = {};        // modes 1-3 gather, 4-5 with point-mass items by target
     int deterministic = 0;              // 1: point-mass adjoint as a gather (fixed summation order)
     long long flops_adj_det = 0, ops_adj_det = 0, flops_adj_fast = 0, ops_adj_fast = 0;
     int* d_nonleaf = nullptr;
@@ -523,6 +523,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     long long flops_fwd = 0, flops_adj = 0, ops_fwd = 0, ops_adj = 0;
     long long flops_adj_scat = 0, ops_adj_scat = 0, count_single_mono = 0;
     long long flops_adj_multi = 0, ops_adj_multi = 0;
+    long long flops_fwd_com = 0, flops_adj_com = 0;   // explicit centres (see ot_interactions_com)
     std::vector<std::pair<long long, int>> fwd[4];
     std::vector<int> node_order_items;
     g->node_item_start.assign(n + 1, 0);
@@ -550,11 +551,17 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 } else {
                     flops_fwd += 86 * cp + 140 * cs;
                 }
+                // explicit centres: every multipole pair evaluates its derivatives
+                flops_fwd_com += (cp + cs) * (leaf ? deriv_flops(19) + 140 : deriv_flops(31) + 200);
+                flops_adj_com += (cp + cs) * (deriv_flops(19) + 140);
             }
             if (mo >> j & 1u) {
                 pairs_mono += cp + cs;
                 flops_fwd += 17 * cp + 32 * cs;
                 flops_adj_scat += 16 * cp + 32 * cs;
+                // explicit centres: a leaf target reads the table, a non-leaf one evaluates
+                flops_fwd_com += leaf ? 17 * cp + 32 * cs : (cp + cs) * (deriv_flops(16) + 32);
+                flops_adj_com += leaf ? 16 * cp + 32 * cs : (cp + cs) * (deriv_flops(16) + 32);
             }
             if (mv >> j & 1u) pairs_virt += cp + cs;
         }
@@ -710,9 +717,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.flops_adj = g->flops_adj_fast;
     I.ops_fwd = ops_fwd;
     I.ops_adj = g->ops_adj_fast;
-    // explicit centres: every pair evaluates its derivatives (no pairing)
-    I.flops_fwd_com = pairs_multi * (deriv_flops(35) + 140) + pairs_ang * 60 + pairs_mono * (deriv_flops(16) + 32);
-    I.flops_adj_com = pairs_multi * (deriv_flops(35) + 140) + pairs_mono * (deriv_flops(16) + 32);
+    I.flops_fwd_com = flops_fwd_com;
+    I.flops_adj_com = flops_adj_com;
     for (int w = 2; w <= 8; w *= 2) {
         g->maxb_emu[2][w] = forward_max_blocks_per_sm(6, w);
         g->maxb_emu[3][w] = forward_max_blocks_per_sm(7, w);
@@ -726,6 +732,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             g->maxb_adj[mode][w] = adjoint_max_blocks_per_sm(mode, w);
             g->maxb_com_fwd[mode][w] = forward_com_max_blocks_per_sm(mode, w);
             g->maxb_com_adj[mode][w] = adjoint_com_max_blocks_per_sm(mode, w);
+            if (mode <= 2) g->maxb_com_adj[3 + mode][w] = adjoint_com_max_blocks_per_sm(3 + mode, w);
         }
 
     // --- uploads ----------------------------------------------------------------
@@ -986,10 +993,16 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
 }
 
 // --- explicit expansion centres ---------------------------------------------
-// Moments about arbitrary centres carry their own units, so nothing is
-// pre-scaled by h (hinv = 1 in the prescale kernels and the epilogue), and the
-// derivatives are evaluated per pair at R = C_A - C_B.  Always the persistent
-// schedule (LPT-ordered items, one launch).
+// The same units as the table path (sources prescaled by h^-m, coefficients
+// by h^-(n+1)); pairs involving a centre from C evaluate their derivatives at
+// R/h.  Always the persistent schedule (LPT-ordered items, one launch).
+
+static void com_scales(ot_grid* g, double* hinv, double* hreal) {
+    for (int l = 0; l < MAXLEV; ++l) {
+        hinv[l] = g->hinv[l];
+        hreal[l] = std::ldexp(g->h0, -l);
+    }
+}
 
 static ot_status enqueue_forward_com(ot_grid* g, int mode, const double* M, const double* m, const double* C,
                                      double* L, double* Lc, cudaStream_t s) {
@@ -1001,16 +1014,13 @@ static ot_status enqueue_forward_com(ot_grid* g, int mode, const double* M, cons
         pp.nodes = g->d_nonleaf;
         pp.n_list = g->n_nonleaf;
         pp.ninfo = g->d_ninfo;
-        for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = 1.0;
+        for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = g->hinv[l];
         OT_CUDA(launch_prescale_moments(pp, s));
     }
     OT_CUDA(cudaMemsetAsync(L, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
     if ((mode & 1) && Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
     FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
-    for (int l = 0; l < MAXLEV; ++l) {
-        p.hinv[l] = 1.0;
-        p.hreal[l] = 1.0 / g->hinv[l];
-    }
+    com_scales(g, p.hinv, p.hreal);
     p.C = C;
     p.ncoord = g->d_ncoord;
     p.items = g->d_items_fwd[mode];
@@ -1024,6 +1034,7 @@ static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const doub
                                       cudaStream_t s) {
     const int mode = (Mbar ? 1 : 0) | (mbar ? 2 : 0);
     if (mode == 0) return OT_OK;
+    const bool scatter = !g->deterministic && mbar != nullptr;
     PrepParams pp;
     std::memset(&pp, 0, sizeof(pp));
     pp.src = Lbar;
@@ -1031,19 +1042,18 @@ static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const doub
     pp.nodes = g->d_all;
     pp.n_list = g->n;
     pp.ninfo = g->d_ninfo;
-    for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = 1.0;
+    for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = g->hinv[l];
     OT_CUDA(launch_prescale_adjoint(pp, s));
     if (Mbar) OT_CUDA(cudaMemsetAsync(Mbar, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
     if (mbar) OT_CUDA(cudaMemsetAsync(mbar, 0, static_cast<size_t>(g->n) * NCELL * sizeof(double), s));
     AdjParams p;
     std::memset(&p, 0, sizeof(p));
-    p.items = g->d_items_adj[mode];
-    p.n_items = g->n_items_adj[mode];
     p.counter = g->d_counters + 1;
     p.nbr = g->d_nbr;
     p.vnbr = g->d_vnbr;
     p.ninfo = g->d_ninfo;
     p.vinfo = g->d_vinfo;
+    p.Dt = g->d_Dt;
     p.L.lists = g->d_lists;
     p.L.far_len = g->far_len;
     p.L.far_pairs = g->far_pairs;
@@ -1057,16 +1067,25 @@ static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const doub
     p.vbar = g->d_vbar;
     p.n_nodes = g->n;
     p.status = g->d_status;
-    for (int l = 0; l < MAXLEV; ++l) {
-        p.hinv[l] = 1.0;
-        p.hreal[l] = 1.0 / g->hinv[l];
-    }
+    com_scales(g, p.hinv, p.hreal);
     p.C = C;
     p.ncoord = g->d_ncoord;
     p.vcoord = g->d_vcoord;
+    int kmode = mode;
+    if (scatter) {
+        // one launch: multipole gather items (if Mbar) and point-mass items by target
+        const int k = (mode & 1) ? 1 : 0;
+        p.items = g->d_items_adj_fast[k];
+        p.n_items = g->n_items_adj_fast[k];
+        kmode = k ? 5 : 4;
+    } else {
+        p.items = g->d_items_adj[mode];
+        p.n_items = g->n_items_adj[mode];
+    }
     OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
-    OT_CUDA(launch_adjoint_com(p, mode, g->wpb, grid_blocks(g, g->maxb_com_adj[mode][g->wpb]), s));
-    if (mbar && g->vmap_rows > 0) OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
+    OT_CUDA(launch_adjoint_com(p, kmode, g->wpb, grid_blocks(g, g->maxb_com_adj[kmode][g->wpb]), s));
+    if (!scatter && mbar && g->vmap_rows > 0)
+        OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
     return OT_OK;
 }
 
@@ -1559,10 +1578,10 @@ ot_status ot_moments_com(ot_grid* g, const double* rho, double* M, double* m, do
     CHECK_PTR(C, "C");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     OT_CUDA(launch_cube_moments(rho, M, m, g->d_cube, g->n_cube, g->d_ninfo, g->d_hinv, s));
-    OT_CUDA(launch_geometric_centres(C, g->d_cube, g->n_cube, g->d_ninfo, g->d_ncoord, g->d_hinv, s));
+    OT_CUDA(launch_geometric_centres(C, g->d_cube, g->n_cube, g->d_ninfo, g->d_ncoord, g->h0, s));
     for (auto& L : g->m2m)
         OT_CUDA(launch_m2m_com(M, m, C, L.d_parents, static_cast<int>(L.parents.size()), L.d_children, g->d_ninfo,
-                               g->d_ncoord, g->d_hinv, s));
+                               g->d_ncoord, g->h0, s));
     return OT_OK;
     GUARD_END
 }
@@ -1593,7 +1612,7 @@ ot_status ot_interactions_backward_com(ot_grid* g, const double* Lbar, const dou
     if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
     if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{40, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps, C};
+    GraphKey key{40 + 8 * g->deterministic, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps, C};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_backward_com(g, Lbar, C, Mbar, mbar, st); });
     GUARD_END
 }
@@ -1605,7 +1624,8 @@ ot_status ot_l2l_com(ot_grid* g, const double* C, double* L, void* stream) {
     CHECK_PTR(L, "L");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (auto it = g->m2m.rbegin(); it != g->m2m.rend(); ++it)
-        OT_CUDA(launch_l2l_com(L, C, it->d_parents, static_cast<int>(it->parents.size()), it->d_children, s));
+        OT_CUDA(launch_l2l_com(L, C, it->d_parents, static_cast<int>(it->parents.size()), it->d_children,
+                               g->d_ninfo, g->d_ncoord, g->h0, s));
     return OT_OK;
     GUARD_END
 }
@@ -1617,7 +1637,8 @@ ot_status ot_l2l_com_backward(ot_grid* g, const double* C, double* Lbar, void* s
     CHECK_PTR(Lbar, "Lbar");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (auto& L : g->m2m)
-        OT_CUDA(launch_l2l_com_adjoint(Lbar, C, L.d_parents, static_cast<int>(L.parents.size()), L.d_children, s));
+        OT_CUDA(launch_l2l_com_adjoint(Lbar, C, L.d_parents, static_cast<int>(L.parents.size()), L.d_children,
+                                       g->d_ninfo, g->d_ncoord, g->h0, s));
     return OT_OK;
     GUARD_END
 }

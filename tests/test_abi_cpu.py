@@ -122,7 +122,8 @@ def test_generated_trees_are_2to1_balanced():
 def test_generated_pair_derivatives_match_sympy(tmp_path):
     """The per-pair derivative routines of the explicit-centre kernels,
     compiled as host C++ (they use only fma, sqrt and division), against
-    sympy's exact derivatives of -1/r at integer and fractional separations."""
+    sympy's exact derivatives of -1/r at integer and fractional separations,
+    for exactly the components each routine promises."""
     import shutil
     import subprocess
 
@@ -139,12 +140,13 @@ def test_generated_pair_derivatives_match_sympy(tmp_path):
     def routine(name):
         start = text.index(f"__device__ __forceinline__ void {name}(")
         return text[start:text.index("\n}\n", start) + 3]
-    src = ("#include <cmath>\nusing std::fma; using std::sqrt;\n#define __device__\n#define __forceinline__ inline\n"
-           + routine("ot_deriv_at") + routine("ot_deriv16_at")
-           + 'extern "C" void d35(double x, double y, double z, double* o) { double d[36]; ot_deriv_at(x, y, z, d);'
-             ' for (int i = 0; i < 35; ++i) o[i] = d[i]; }\n'
-           + 'extern "C" void d16(double x, double y, double z, double* o) { double d[36]; ot_deriv16_at(x, y, z, d);'
-             ' for (int i = 0; i < 16; ++i) o[i] = d[i]; }\n')
+    names = list(gen_contract.DERIV_SETS)
+    src = "#include <cmath>\nusing std::fma; using std::sqrt;\n#define __device__\n#define __forceinline__ inline\n"
+    for name in names:
+        src += routine(name)
+        src += (f'extern "C" void c_{name}(double x, double y, double z, double* o) {{ double d[36];'
+                f' for (int i = 0; i < 36; ++i) d[i] = 1e300; {name}(x, y, z, d);'
+                f' for (int i = 0; i < 36; ++i) o[i] = d[i]; }}\n')
     (tmp_path / "d.cpp").write_text(src)
     so = str(tmp_path / "d.so")
     subprocess.run(["g++", "-O1", "-ffp-contract=off", "-shared", "-fPIC", "-o", so, str(tmp_path / "d.cpp")],
@@ -153,15 +155,18 @@ def test_generated_pair_derivatives_match_sympy(tmp_path):
     x, y, z = sympy.symbols("x y z", real=True)
     G = -1 / sympy.sqrt(x * x + y * y + z * z)
     for R in [(3, -4, 12), (1.25, 0.5, -2.75), (-0.3, 2.2, 0.9), (0, 0, 5), (7, 1, 1)]:
-        out35 = (ctypes.c_double * 35)()
-        out16 = (ctypes.c_double * 16)()
-        lib.d35(ctypes.c_double(R[0]), ctypes.c_double(R[1]), ctypes.c_double(R[2]), out35)
-        lib.d16(ctypes.c_double(R[0]), ctypes.c_double(R[1]), ctypes.c_double(R[2]), out16)
         sub = {x: sympy.Rational(R[0]), y: sympy.Rational(R[1]), z: sympy.Rational(R[2])}
         r = float(np.linalg.norm(R))
-        for q, e in enumerate(gen_contract.ROW[:35]):
-            exact = float(sympy.N(sympy.diff(G, x, e[0], y, e[1], z, e[2]).subs(sub), 40))
-            scale = 1.0 / r ** (sum(e) + 1)
-            assert abs(out35[q] - exact) <= 1e-14 * max(abs(exact), scale), (R, e, out35[q], exact)
-            if q < 16:
-                assert abs(out16[q] - exact) <= 1e-14 * max(abs(exact), scale), (R, e, out16[q], exact)
+        exact = [float(sympy.N(sympy.diff(G, x, e[0], y, e[1], z, e[2]).subs(sub), 40))
+                 for e in gen_contract.ROW[:35]]
+        for name in names:
+            out = (ctypes.c_double * 36)()
+            getattr(lib, f"c_{name}")(ctypes.c_double(R[0]), ctypes.c_double(R[1]), ctypes.c_double(R[2]), out)
+            want = set(gen_contract.DERIV_SETS[name])
+            for q in range(36):
+                if q not in want:
+                    assert out[q] == 1e300, (name, q)      # untouched
+                    continue
+                e = gen_contract.ROW[q]
+                scale = 1.0 / r ** (sum(e) + 1)
+                assert abs(out[q] - exact[q]) <= 1e-14 * max(abs(exact[q]), scale), (name, R, e, out[q], exact[q])

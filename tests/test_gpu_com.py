@@ -114,7 +114,9 @@ def test_com_passes_all_cells(ot, orc, which):
     rho = synth.uniform_random_density(tree, seed=92)
     M, m, C = oracle_com_inputs(orc, tree, rho)
     g = ot.OTGrid.from_tree(tree)
-    L, Lc = g.interactions_com(dev(M), dev(m), dev(C))
+    Cg = C.copy()
+    Cg[tree.is_leaf == 1] = np.nan      # never read: leaf cells sit at their geometric centres
+    L, Lc = g.interactions_com(dev(M), dev(m), dev(Cg))
     torch.cuda.synchronize()
     g.check()
     tg = all_targets(tree)
@@ -195,14 +197,18 @@ def _sparse_lbar(tree, count, seed):
     return Lbar, tg.astype(np.int32)
 
 
+@pytest.mark.parametrize("deterministic", [False, True])
 @pytest.mark.parametrize("which", ["uniform", "adaptive", "leaf_level"])
-def test_com_adjoint_matches_oracle(ot, orc, which):
+def test_com_adjoint_matches_oracle(ot, orc, which, deterministic):
     tree = TREES[which]()
     rho = synth.uniform_random_density(tree, seed=97)
     _, _, C = oracle_com_inputs(orc, tree, rho)
     Lbar, tg = _sparse_lbar(tree, 300, 98)
     g = ot.OTGrid.from_tree(tree)
-    Mb, mb = g.backward_com(dev(Lbar), dev(C))
+    g.set_deterministic(deterministic)
+    Cg = C.copy()
+    Cg[tree.is_leaf == 1] = np.nan
+    Mb, mb = g.backward_com(dev(Lbar), dev(Cg))
     torch.cuda.synchronize()
     g.check()
     Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg, centres=C)
@@ -234,6 +240,21 @@ def test_com_adjoint_dot_product_binary_star(ot, orc):
 # ---------------------------------------------------------------------------
 # down-pass and the full solve
 # ---------------------------------------------------------------------------
+
+def test_com_atomic_adjoint_equals_fixed_order(ot, orc):
+    tree, rho = synth.config5_step(3)
+    _, _, C = oracle_com_inputs(orc, tree, rho)
+    Lbar = dev(np.random.default_rng(106).standard_normal((tree.n, 20, 512)))
+    g = ot.OTGrid.from_tree(tree)
+    Cd = dev(C)
+    Mb1, mb1 = g.backward_com(Lbar, Cd)
+    g.set_deterministic(True)
+    Mb2, mb2 = g.backward_com(Lbar, Cd)
+    torch.cuda.synchronize()
+    assert torch.equal(Mb1, Mb2)
+    scale = float(mb2.abs().max())
+    assert float((mb1 - mb2).abs().max()) <= 1e-13 * scale
+
 
 def test_com_l2l_adjoint_dot_product(ot, orc):
     tree = _small_adaptive()
