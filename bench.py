@@ -183,6 +183,12 @@ def adj_flops(info):
     return info["flops_adj"]
 
 
+# DRAM bytes (read + written) of one forward_kernel<3> launch on the 64^3
+# polytrope workload with the 8x1 tile, from an ncu capture of that kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum = 55.70 MB + 4.40 MB).
+# Reported only for that workload; None once the kernel changes.
+FORWARD_DRAM_BYTES_POLYTROPE64 = 60_100_608
+
 # Nominal FP64 rate of a B300 (1.25 TFLOP/s) at its maximum SM clock (2032 MHz):
 # 1.25e12 / (148 SMs * 2.032e9) = 4.16 FP64 flop per clock per SM.
 NOMINAL_FP64_TFLOPS = 1.25
@@ -384,7 +390,9 @@ def run_ours(args, rank, world):
                 "note": "centre-of-mass expansion centres: the same pairs, derivatives of G evaluated "
                         "per pair at R = C_A - C_B; fractions of the same FP64 peak"},
         "roofline": {"bound": "alu", "kernel": "forward_kernel<3> (both passes, one launch)",
-                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "traffic": (FORWARD_DRAM_BYTES_POLYTROPE64 if args.workload == "polytrope64" else None),
+                     "traffic_unit": "bytes per launch (ncu, 8x1 tile)",
                      "peak_source": (f"nominal B300 FP64 {NOMINAL_FP64_TFLOPS} TFLOP/s at {NOMINAL_SM_MHZ:.0f} MHz, "
                                      f"scaled to the median SM clock sampled in this run ({sm_mhz:.0f} MHz)"),
                      "probe_tflops": peak_tflops, "probe": probe_cfg,
