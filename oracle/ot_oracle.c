@@ -408,6 +408,28 @@ static void source_centre(const otree* t, int cls, int B, int cb, int l, const l
 
 static const double INV_FACT[4] = {1.0, 1.0, 0.5, 1.0 / 6.0};
 
+/* Coarse leaf target next to a refined region: a leaf target cell at global
+ * position g (level l) whose near source q is a cell of a refined sub-grid
+ * is itself refined virtually.  Its 8 children (level l+1, each holding an
+ * eighth of the cell) meet the 8 children of q as point masses one level
+ * down, and the target's coefficients are the mean of its children's.
+ * child_s[cs], child_R[cs][cv][3]: the source children's (node, cell) and
+ * the separations X_v - X_s (geometric centres, exact in binary). */
+static void refined_pairs(const otree* t, int l, const long* g, const long* q, int (*child_s)[2],
+                          double (*child_R)[8][3]) {
+    double hc = t->h0 / pow(2.0, l + 1);
+    for (int cs = 0; cs < 8; cs++) {
+        long qs[3] = {2 * q[0] + (cs & 1), 2 * q[1] + ((cs >> 1) & 1), 2 * q[2] + (cs >> 2)};
+        double sc;
+        /* in a 2:1-balanced tree these children are leaf cells */
+        source_lookup(t, l + 1, qs, &child_s[cs][0], &child_s[cs][1], &sc);
+        for (int cv = 0; cv < 8; cv++) {
+            long gv[3] = {2 * g[0] + (cv & 1), 2 * g[1] + ((cv >> 1) & 1), 2 * g[2] + (cv >> 2)};
+            for (int ax = 0; ax < 3; ax++) child_R[cs][cv][ax] = (double)(gv[ax] - qs[ax]) * hc;
+        }
+    }
+}
+
 /* One target cell of one pass.  pass 1: multipole sources (M), pass 2: point
  * masses (m).  Writes L[20] (+ Lc[3] for pass 1), S = sum of |terms|. */
 static long long target_pass(const otree* t, int pass, const double* M, const double* m, const double* C,
@@ -432,8 +454,30 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                 int B, cb;
                 double scale;
                 int cls = source_lookup(t, l, q, &B, &cb, &scale);
-                if (pass == 1 && cls != 1) continue;
-                if (pass == 2 && cls != 2 && cls != 3) continue;
+                int refined = leafT && !is_far && cls == 1;
+                if (pass == 1 && (cls != 1 || refined)) continue;
+                if (pass == 2 && cls != 2 && cls != 3 && !refined) continue;
+                if (refined) {
+                    /* pass 2: the mean over the target's virtual children of the
+                     * point-mass contributions of the source's children */
+                    int cs_[8][2];
+                    double Rc[8][8][3];
+                    refined_pairs(t, l, g, q, cs_, Rc);
+                    npairs += 8;
+                    for (int cs = 0; cs < 8; cs++) {
+                        double ms = m[(size_t)cs_[cs][0] * NCELL + cs_[cs][1]];
+                        for (int cv = 0; cv < 8; cv++) {
+                            double D[NCOMP4];
+                            oracle_D(Rc[cs][cv], D);
+                            for (int J = 0; J < NCOMP; J++) {
+                                double term = 0.125 * ms * D[J];
+                                L[J] += term;
+                                S[J] += fabs(term);
+                            }
+                        }
+                    }
+                    continue;
+                }
                 double R[3] = {-o[0] * h, -o[1] * h, -o[2] * h};   /* X_A - X_B */
                 if (C) {
                     double XB[3];
@@ -589,8 +633,29 @@ long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord,
                         int B, cb;
                         double scale;
                         int cls = source_lookup(&t, l, q, &B, &cb, &scale);
-                        if (pass == 1 && cls != 1) continue;
-                        if (pass == 2 && cls != 2 && cls != 3) continue;
+                        int refined = leafT && !is_far && cls == 1;
+                        if (pass == 1 && (cls != 1 || refined)) continue;
+                        if (pass == 2 && cls != 2 && cls != 3 && !refined) continue;
+                        if (refined) {
+                            int cs_[8][2];
+                            double Rc[8][8][3];
+                            refined_pairs(&t, l, g, q, cs_, Rc);
+                            npairs += 8;
+                            for (int cs = 0; cs < 8; cs++) {
+                                double acc = 0.0, sacc = 0.0;
+                                for (int cv = 0; cv < 8; cv++) {
+                                    double D[NCOMP4];
+                                    oracle_D(Rc[cs][cv], D);
+                                    for (int J = 0; J < NCOMP; J++) {
+                                        acc += 0.125 * LA[(size_t)J * NCELL] * D[J];
+                                        sacc += fabs(0.125 * LA[(size_t)J * NCELL] * D[J]);
+                                    }
+                                }
+                                mbar[(size_t)cs_[cs][0] * NCELL + cs_[cs][1]] += acc;
+                                if (Sbar) Sbar[(size_t)cs_[cs][0] * NCELL + cs_[cs][1]] += sacc;
+                            }
+                            continue;
+                        }
                         npairs++;
                         double R[3] = {-o[0] * h, -o[1] * h, -o[2] * h};
                         if (C) {

@@ -614,3 +614,55 @@ def test_com_adjoint_dot_product(orc, pass_kind):
     # and the centres matter: the geometric-centre adjoint differs
     geo = orc.pass_adjoint(tree, pass_kind, Lbar)
     assert np.max(np.abs(geo - bar)) > 1e-6 * np.max(np.abs(bar))
+
+
+# ---------------------------------------------------------------------------
+# coarse leaf targets next to refined sub-grids (virtual refinement)
+# ---------------------------------------------------------------------------
+
+def test_newton_third_law_adaptive_tree(orc):
+    """On a 2:1-balanced adaptive tree every pair of both passes appears from
+    both sides -- fine cells see a coarse leaf's virtual children, and the
+    coarse leaf, refined virtually, sees the fine cells -- so the expansion
+    forces of all cells of all levels sum to zero to rounding."""
+    tree = _small_adaptive()
+    rng = np.random.default_rng(26)
+    rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    M = orc.moments(tree, rho)
+    m = np.ascontiguousarray(M[:, 0, :])
+    r1 = orc.run_pass_grid(tree, "multipole", M=M)
+    r2 = orc.run_pass_grid(tree, "monopole", m=m)
+    L = r1["L"] + r2["L"]
+    F = np.array([_force(M[i, :, a], L[i, :, a], r1["Lc"][i, :, a]) for i in range(tree.n) for a in range(512)])
+    scale = np.sum(np.abs(F))
+    assert np.max(np.abs(F.sum(axis=0))) <= 1e-13 * scale, (F.sum(axis=0), scale)
+
+
+def test_coarse_target_sees_fine_mass_through_virtual_children(orc):
+    """One unit mass in a fine cell next to a coarse leaf: a coarse cell whose
+    refined neighbour is near gets the mean over its 8 virtual children of
+    -1/r and of its gradient R/r^3; a coarse cell farther away gets nothing
+    from the point-mass pass (it sees the refined cell's multipole)."""
+    tree = _small_adaptive()
+    idx = tree.index()
+    assert tree.is_leaf[idx[(1, 0, 1, 0)]] == 1 and tree.is_leaf[idx[(1, 0, 0, 0)]] == 0
+    m = np.zeros((tree.n, 512))
+    fine = np.array([3, 15, 3])                                   # level-2 global cell
+    m[idx[(2, *(fine // 8))], _cell(*(fine % 8))] = 1.0
+    hc = tree.h0 / 4.0
+    coarse = idx[(1, 0, 1, 0)]
+    for g in ((1, 8, 1), (1, 9, 1), (1, 12, 1)):                  # level-1 global cells
+        near = np.sum((np.array(g) - fine // 2) ** 2) <= 12
+        r = orc.run_pass(tree, "monopole", m=m, targets=[[coarse, _cell(*(np.array(g) % 8))]])
+        L = r["L"][0]
+        if not near:
+            assert np.all(L == 0.0)
+            continue
+        want0, want1 = 0.0, np.zeros(3)
+        for cv in itertools.product((0, 1), repeat=3):
+            R = (2 * np.array(g) + np.array(cv) - fine) * hc          # X_v - X_s
+            d = np.linalg.norm(R)
+            want0 += -1.0 / d / 8.0
+            want1 += R / d ** 3 / 8.0
+        assert L[0] == pytest.approx(want0, rel=1e-14)
+        np.testing.assert_allclose(L[1:4], want1, rtol=1e-14)
