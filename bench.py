@@ -313,6 +313,18 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     df_ms = statistics.median(a.elapsed_time(b) for a, b in de)
     g.set_precision(ot.OT_PREC_FP64)
+    # each variant as its own launch: the multipole pass, the point-mass pass
+    variant_ms = {}
+    for name, call in (("multipole", lambda: g.multipole(M, L, Lc)), ("monopole", lambda: g.monopole(m, L))):
+        call()
+        ve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in ve:
+            flush.zero_()
+            a.record(stream)
+            call()
+            b.record(stream)
+        torch.cuda.synchronize()
+        variant_ms[name] = statistics.median(a.elapsed_time(b) for a, b in ve)
     # the same passes about centres of mass (derivatives evaluated per pair)
     Mc, mc, Cc = g.moments_com(rho)
     g.interactions_com(Mc, mc, Cc, L, Lc)
@@ -376,7 +388,18 @@ def run_ours(args, rank, world):
                    "tile": {"warps_per_block": info["warps_per_block"], "blocks_per_sm": info["blocks_per_sm"]},
                    "autotuned": tuned, "l2": "flushed between steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
-        "fwd": {"value": pairs_fwd / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
+        "fwd": {"value": pairs_fwd / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms,
+                "pairs_in_domain": pairs_fwd, "pairs_padded": info["lanes_fwd"]},
+        "variants": {
+            "multipole": {"value": info["pairs_multipole"] / (variant_ms["multipole"] * 1e-3), "unit": UNIT,
+                          "ms": variant_ms["multipole"], "pairs": info["pairs_multipole"],
+                          "pairs_with_angular_term": info["pairs_angular"]},
+            "monopole": {"value": info["pairs_monopole"] / (variant_ms["monopole"] * 1e-3), "unit": UNIT,
+                         "ms": variant_ms["monopole"], "pairs": info["pairs_monopole"]},
+            "boundary": {"pairs": info["pairs_virtual"],
+                         "note": "point-mass pairs whose source is a virtual descendant of a coarser leaf; "
+                                 "they run inside the monopole launch"},
+            "note": "separate launches of one pass each; the fused launch (fwd) runs both"},
         "adjoint": {"value": pairs_fwd / (adj_ms * 1e-3), "unit": UNIT, "ms": adj_ms},
         "fwd_df64_point_mass": {"value": pairs_fwd / (df_ms * 1e-3), "unit": UNIT, "ms": df_ms,
                                 "note": "point-mass pairs in double-float on the FP32 pipe (within 1e-12 of "
@@ -513,9 +536,28 @@ def cpu_baseline(tree, rho_h, seconds, seed=7):
         t_used += time.perf_counter() - t0
         pairs += r1["npairs"] + r2["npairs"]
         ntg += len(tg)
+    # the same oracle on one thread, a shorter sample
+    oracle.set_threads(1)
+    pairs1, t1 = 0, 0.0
+    while t1 < max(2.0, seconds / 6):
+        tg = np.stack([rng.integers(0, tree.n, 64), rng.integers(0, 512, 64)], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        r1 = oracle.run_pass(tree, "multipole", M=M, targets=tg)
+        r2 = oracle.run_pass(tree, "monopole", m=m, targets=tg)
+        t1 += time.perf_counter() - t0
+        pairs1 += r1["npairs"] + r2["npairs"]
+    oracle.set_threads(cores)
+    cpu = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            cpu = next((ln.split(":", 1)[1].strip() for ln in f if ln.startswith("model name")), "")
+    except OSError:
+        pass
     return {"value": pairs / t_used, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
             "sample": f"forward of both passes for {ntg} random target cells of the workload "
-                      f"({pairs} pairs, {t_used:.1f} s)"}
+                      f"({pairs} pairs, {t_used:.1f} s)",
+            "single_thread": {"value": pairs1 / t1, "unit": UNIT, "sample": f"{pairs1} pairs, {t1:.1f} s"},
+            "cpu": cpu}
 
 
 def run_reference(args, rank, world):

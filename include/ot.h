@@ -27,6 +27,12 @@
  *     leaf nodes are point masses; a same-level position with no node but
  *     covered by a coarser leaf is a virtual descendant holding 8^-d of that
  *     leaf's cell mass (coarse-fine boundary); anything else is empty.
+ *   Coarse leaf targets (the other side of that boundary): a leaf target's
+ *     near source that is a cell of a refined node is not contracted as a
+ *     multipole.  The target cell is refined virtually instead -- its 8
+ *     children, an eighth of the cell each, meet the source cell's 8 children
+ *     (leaf cells one level down) as point masses -- and takes the mean of
+ *     its children's coefficients.  This is part of the monopole pass.
  *
  * Memory and ownership.  Every array argument is a DEVICE pointer owned by
  * the caller, 16-byte aligned, densely packed in the layout given, and must
@@ -114,12 +120,18 @@ typedef struct {
     int64_t flops_fwd_com;         /* algorithmic FLOPs of ot_interactions_com (both passes, with Lc):
                                       per pair the derivative evaluation plus the contraction */
     int64_t flops_adj_com;         /* the same for ot_interactions_backward_com */
+    int64_t pairs_refined;         /* near pairs of a leaf target and a cell of a refined
+                                      sub-grid, evaluated through the leaf's virtual children
+                                      (each counted as 8 point-mass pairs in pairs_monopole) */
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the
  * scratch arena on the current device.  `stream` orders the uploads.
- * Errors: OT_EINVAL (bad description), OT_ENOMEM, OT_ECUDA, OT_ENOTSUP
- * (stencil_c other than 12, flags other than geometric centres). */
+ * Errors: OT_EINVAL (bad description; also a tree that is not 2:1 balanced
+ * in the sense the coarse-leaf rule needs: a child of a refined neighbour of
+ * a leaf sub-grid that touches the leaf must itself be a leaf), OT_ENOMEM,
+ * OT_ECUDA, OT_ENOTSUP (stencil_c other than 12, flags other than geometric
+ * centres). */
 ot_status ot_grid_create(const ot_grid_desc* desc, void* stream, ot_grid** out);
 
 /* Frees everything the handle owns (synchronizes the device first). NULL is OK. */

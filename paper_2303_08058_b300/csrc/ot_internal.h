@@ -12,6 +12,7 @@ constexpr int NCOMP = 20;         // moments / Taylor coefficients of orders 0..
 constexpr int NRED = 16;          // traceless-reduced components
 constexpr int DROW = 36;          // doubles per derivative-table row
 constexpr int NOFF = 15 * 15 * 15;  // integer offsets in [-7, 7]^3
+constexpr int NVROW = 14 * 14 * 14; // rows of the virtual-child table: q = 2o + c in [-6, 7]^3
 constexpr int MAXLEV = 21;        // levels 0..20
 
 // Neighbour-table entry (one per 3x3x3 neighbour of a sub-grid at its own level).
@@ -58,6 +59,9 @@ struct FwdParams {
     const double* C;       // [n][3][512] or null
     const int* ncoord;     // [n][3] node positions
     double hreal[MAXLEV];  // h_l
+    // coarse leaf targets refined virtually next to refined sub-grids
+    const int* child_of;   // [n][8] child node per octant (x fastest), -1 for leaves
+    const double* Dv;      // [NVROW][16] virtual-child mean rows (built by build_grid)
 };
 
 struct AdjParams {
@@ -81,6 +85,8 @@ struct AdjParams {
     const int* ncoord;     // [n][3]
     const int* vcoord;     // [nvirt][3] positions of virtual sub-grids at their level
     double hreal[MAXLEV];
+    const int* child_of;   // as in FwdParams
+    const double* Dv;
 };
 
 // point-mass adjoint organised by target cells (the forward's walk) with the
@@ -97,6 +103,8 @@ struct ScatParams {
     double* mbar;          // [n][512], zeroed before the launch
     int n_nodes;
     int* status;
+    const int* child_of;   // as in FwdParams
+    const double* Dv;
 };
 
 struct PrepParams {

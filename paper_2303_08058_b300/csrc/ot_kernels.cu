@@ -173,6 +173,116 @@ __device__ __forceinline__ int nb_index(int sx, int sy, int sz) {
     return ((sx + 8) >> 3) + 3 * ((sy + 8) >> 3) + 9 * ((sz + 8) >> 3);
 }
 
+// ---------------------------------------------------------------------------
+// coarse leaf targets next to refined sub-grids
+//
+// A leaf target cell a whose near source b (offset o) is a cell of a refined
+// sub-grid is refined virtually: its 8 children (an eighth of the cell each)
+// meet b's 8 children s (offset cs in {0,1}^3; leaf cells one level down) as
+// point masses, and a takes the mean of its children's coefficients.  In
+// units of the target level's h the child pair (cv, cs) has the table row of
+// q - cv, q = 2o + cs, and the child level's h^-(n+1) is 2^(n+1) times the
+// target level's, so the mean over the target's children is one row per q:
+//   Dv[q][j] = 2^(n_j+1) / 8 * sum_cv row(q - cv)[j],
+// and b contributes sum_cs m_s Dv[2o + cs].  The partner source at -o uses
+// the same rows with its child 7 - cs and odd orders negated.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int vrow_index(int ox, int oy, int oz, int cs) {
+    return (2 * ox + (cs & 1) + 6) + 14 * (2 * oy + ((cs >> 1) & 1) + 6) + 196 * (2 * oz + (cs >> 2) + 6);
+}
+
+__device__ __forceinline__ void load_vrow16(double (&d)[36], const double* __restrict__ Dv, int r) {
+    const double2* src = reinterpret_cast<const double2*>(Dv + static_cast<size_t>(r) * 16);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const double2 v = __ldg(src + q);
+        d[2 * q] = v.x;
+        d[2 * q + 1] = v.y;
+    }
+}
+
+// child cs of the cell at local position (sx, sy, sz) of the refined node
+// `node`: returns the child node (or -1 after reporting a bad table entry)
+// and its cell
+template <class P>
+__device__ __forceinline__ int child_cell(const P& p, int node, int sx, int sy, int sz, int cs, int& cell, int item) {
+    const int fx = 2 * (sx & 7) + (cs & 1), fy = 2 * (sy & 7) + ((cs >> 1) & 1), fz = 2 * (sz & 7) + (cs >> 2);
+    const int c = __ldg(p.child_of + 8 * node + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3));
+    cell = (fx & 7) + 8 * (fy & 7) + 64 * (fz & 7);
+    if (static_cast<unsigned>(c) >= static_cast<unsigned>(p.n_nodes)) {
+        report(p.status, 5, item);
+        return -1;
+    }
+    return c;
+}
+
+// forward: refined near sources at t + o (vp) and t - o (vm) of one entry
+__device__ __forceinline__ void refined_near_fwd(const FwdParams& p, int ox, int oy, int oz, int2 ep, bool vp, int px,
+                                                 int py, int pz, int2 em, bool vm, int mx, int my, int mz,
+                                                 double (&a)[16], int item) {
+    const int bx = 2 * (px & 7), by = 2 * (py & 7), bz = 2 * (pz & 7);
+    const int cx = 2 * (mx & 7), cy = 2 * (my & 7), cz = 2 * (mz & 7);
+    const int* chp = p.child_of + 8 * (vp ? ep.x : 0);
+    const int* chm = p.child_of + 8 * (vm ? em.x : 0);
+#pragma unroll 1
+    for (int cs = 0; cs < 8; ++cs) {
+        double mp = 0.0, mm = 0.0;
+        if (vp) {
+            const int fx = bx + (cs & 1), fy = by + ((cs >> 1) & 1), fz = bz + (cs >> 2);
+            const int c = __ldg(chp + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3));
+            if (static_cast<unsigned>(c) < static_cast<unsigned>(p.n_nodes))
+                mp = __ldg(p.m + static_cast<size_t>(c) * NCELL + (fx & 7) + 8 * (fy & 7) + 64 * (fz & 7));
+            else report(p.status, 5, item);
+        }
+        if (vm) {
+            const int k = 7 - cs;
+            const int fx = cx + (k & 1), fy = cy + ((k >> 1) & 1), fz = cz + (k >> 2);
+            const int c = __ldg(chm + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3));
+            if (static_cast<unsigned>(c) < static_cast<unsigned>(p.n_nodes))
+                mm = __ldg(p.m + static_cast<size_t>(c) * NCELL + (fx & 7) + 8 * (fy & 7) + 64 * (fz & 7));
+            else report(p.status, 5, item);
+        }
+        // even orders take the sum, odd orders the difference (the partner's
+        // rows are the same with odd orders negated)
+        const double* row = p.Dv + static_cast<size_t>(vrow_index(ox, oy, oz, cs)) * 16;
+        const double sm = mp + mm, df = mp - mm;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int n = j == 0 ? 0 : j < 4 ? 1 : j < 9 ? 2 : 3;
+            a[j] = fma((n & 1) ? df : sm, __ldg(row + j), a[j]);
+        }
+    }
+}
+
+// the transpose, by target: the children of the refined sources receive
+// their share of the target's adjoint by atomic adds
+template <class P>
+__device__ __forceinline__ void refined_near_scatter(const P& p, int ox, int oy, int oz, int2 ep, bool vp, int px,
+                                                     int py, int pz, int2 em, bool vm, int mx, int my, int mz,
+                                                     const double (&lb)[16], int item) {
+#pragma unroll 1
+    for (int cs = 0; cs < 8; ++cs) {
+        double d[36];
+        load_vrow16(d, p.Dv, vrow_index(ox, oy, oz, cs));
+        double e, q;
+        ot_mono_adj_split(e, q, lb, d);
+        int cell;
+        if (vp) {
+            const int c = child_cell(p, ep.x, px, py, pz, cs, cell, item);
+            if (c >= 0) atomicAdd(p.mbar + static_cast<size_t>(c) * NCELL + cell, e + q);
+        }
+        if (vm) {
+            const int c = child_cell(p, em.x, mx, my, mz, 7 - cs, cell, item);
+            if (c >= 0) atomicAdd(p.mbar + static_cast<size_t>(c) * NCELL + cell, e - q);
+        }
+    }
+}
+
+// the order scale 2^(n+1)/8 of the reduced components, for the adjoint
+// gather from a coarse leaf's virtual children
+__device__ __forceinline__ double vchild_scale(int j) { return j == 0 ? 0.25 : j < 4 ? 0.5 : j < 9 ? 1.0 : 2.0; }
+
 // PAIRED: each entry o stands for the offsets o and -o (sources at t + o and
 // t - o share the table row of o, with odd-order derivatives negated for -o).
 // (ah, al) double-float partial sums of the point-mass contributions, moved
@@ -186,7 +296,7 @@ __device__ __forceinline__ void df_flush(double (&a)[16], float (&ah)[16], float
     }
 }
 
-template <int MODE, bool PAIRED, bool EMU>
+template <int MODE, bool PAIRED, bool EMU, bool NEAR = false>
 __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
                                              int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                              const FwdParams& p, double (&a)[16], double (&c)[3],
@@ -240,7 +350,13 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
                 }
             }
         }
-        if (MODE & 1) {
+        if ((MODE & 2) && NEAR) {
+            // near sources in refined sub-grids: the target refined virtually
+            const bool rp = kp == K_MULTI, rm = km == K_MULTI;
+            if (__any_sync(0xffffffffu, rp || rm))
+                refined_near_fwd(p, ox, oy, oz, ep, rp, px, py, pz, em, rm, mx, my, mz, a, item);
+        }
+        if ((MODE & 1) && !NEAR) {
             const bool multi = kp == K_MULTI || km == K_MULTI;
             if (__any_sync(0xffffffffu, multi)) {
                 double r[16];
@@ -371,7 +487,7 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
                                            s_nb[warp], p, a, c, t4, ah, al, nacc, it);
         }
         if (leafT)
-            walk_forward<MODE, true, EMU>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p,
+            walk_forward<MODE, true, EMU, true>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p,
                                           a, c, t4, ah, al, nacc, it);
         if (EMU) df_flush(a, ah, al);
         store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
@@ -388,8 +504,38 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
 // list of parity p (far pairs are symmetric under o -> -o with the parities
 // swapped), with the table row of the forward offset o = -o'.  A paired
 // entry o' also gathers from A = B - o' (row of o', odd orders negated).
+// lb of one adjoint target: a real cell's reduced L-bar, or for a virtual
+// child of a coarse leaf (depth 1; the coarse leaf refined as a target) the
+// covering cell's, times 2^(n+1)/8 (the mean over the children, in the
+// finer level's h units)
+__device__ __forceinline__ void adjoint_target_lb(const AdjParams& p, int2 e, bool real, bool vchild, int tx, int ty,
+                                                  int tz, double (&lb)[16]) {
+    if (real) {
+        const double* src = p.Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + (tx & 7) + 8 * (ty & 7) + 64 * (tz & 7);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) lb[q] = __ldg(src + q * NCELL);
+    } else if (vchild) {
+        const unsigned meta = static_cast<unsigned>(e.y);
+        const int vx = static_cast<int>(((meta >> 8) & 0xffu) + (tx & 7)) >> 1;
+        const int vy = static_cast<int>(((meta >> 16) & 0xffu) + (ty & 7)) >> 1;
+        const int vz = static_cast<int>((meta >> 24) + (tz & 7)) >> 1;
+        const double* src = p.Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + vx + 8 * vy + 64 * vz;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) lb[q] = vchild_scale(q) * __ldg(src + q * NCELL);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) lb[q] = 0.0;
+    }
+}
+
+// a depth-1 virtual descendant (the child of a coarse leaf cell) as a target
+// of a real point-mass source
+__device__ __forceinline__ bool virtual_child_target(int2 e, bool virt_t) {
+    return virt_t && (e.y & 3) == K_VIRT && ((static_cast<unsigned>(e.y) >> 2) & 7u) == 1u;
+}
+
 template <bool MULTI, bool PAIRED>
-__device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int len, bool near_seg,
+__device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int len, bool near_seg, bool virt_t,
                                              int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
                                              const AdjParams& p, double (&g)[16], double (&g4)[4],
                                              int item) {
@@ -401,32 +547,26 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
         const int2 ep = s_nb[nb_index(px, py, pz)];
         int kp = ep.y & 3;
         bool vp = (kp == K_MULTI || kp == K_LEAF) && (!near_seg || kp == K_LEAF);
-        if (vp && static_cast<unsigned>(ep.x) >= static_cast<unsigned>(p.n_nodes)) {
+        bool wp = !MULTI && virtual_child_target(ep, virt_t);
+        if ((vp || wp) && static_cast<unsigned>(ep.x) >= static_cast<unsigned>(p.n_nodes)) {
             report(p.status, 2, item);
-            vp = false;
+            vp = wp = false;
         }
         int2 em = make_int2(-1, 0);
-        bool vm = false;
+        bool vm = false, wm = false;
         if (PAIRED) {
             em = s_nb[nb_index(mx, my, mz)];
             const int km = em.y & 3;
             vm = (km == K_MULTI || km == K_LEAF) && (!near_seg || km == K_LEAF);
-            if (vm && static_cast<unsigned>(em.x) >= static_cast<unsigned>(p.n_nodes)) {
+            wm = !MULTI && virtual_child_target(em, virt_t);
+            if ((vm || wm) && static_cast<unsigned>(em.x) >= static_cast<unsigned>(p.n_nodes)) {
                 report(p.status, 2, item);
-                vm = false;
+                vm = wm = false;
             }
         }
-        if (!__any_sync(0xffffffffu, vp || vm)) continue;
+        if (!__any_sync(0xffffffffu, vp || vm || wp || wm)) continue;
         double lb[16];
-        if (vp) {
-            const double* src = p.Lrbar + static_cast<size_t>(ep.x) * NRED * NCELL + (px & 7) + 8 * (py & 7) +
-                                64 * (pz & 7);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) lb[q] = __ldg(src + q * NCELL);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) lb[q] = 0.0;
-        }
+        adjoint_target_lb(p, ep, vp, wp, px, py, pz, lb);
         const int row = NOFF - 1 - offset_row(ox, oy, oz);
         double d[36];
         if (MULTI) {
@@ -457,15 +597,7 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
             ot_mono_adj(g4, lb, d);
             if (PAIRED) {
                 double lm[16];
-                if (vm) {
-                    const double* src = p.Lrbar + static_cast<size_t>(em.x) * NRED * NCELL + (mx & 7) +
-                                        8 * (my & 7) + 64 * (mz & 7);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) lm[q] = __ldg(src + q * NCELL);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) lm[q] = 0.0;
-                }
+                adjoint_target_lb(p, em, vm, wm, mx, my, mz, lm);
                 ot_mono_adj_neg(g4, lm, d);
             }
         }
@@ -558,26 +690,28 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
 #pragma unroll
         for (int q = 0; q < 4; ++q) g4[q] = 0.0;
         if (skind == K_MULTI) {
+            // targets of the transposed far (root) stencil; near leaf targets
+            // of a refined cell see its children instead
             if ((MODE & 1) && p.Mbar != nullptr) {
                 if (level == 0) {
-                    walk_adjoint<true, true>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                    walk_adjoint<true, true>(l1, n1, false, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
                 } else {
-                    walk_adjoint<true, true>(l1, p.L.far_pairs, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
-                    walk_adjoint<true, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, sx, sy, sz, s_nb[warp],
-                                              p, g, g4, it);
+                    walk_adjoint<true, true>(l1, p.L.far_pairs, false, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                    walk_adjoint<true, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, false, sx, sy, sz,
+                                              s_nb[warp], p, g, g4, it);
                 }
-                walk_adjoint<true, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
                 store_mbar(p.Mbar, src, scell, h1, g);
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
+            const bool vt = skind == K_LEAF;   // real leaf cells also feed coarse leaves' virtual children
             if (level == 0) {
-                walk_adjoint<false, true>(l1, n1, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                walk_adjoint<false, true>(l1, n1, false, vt, sx, sy, sz, s_nb[warp], p, g, g4, it);
             } else {
-                walk_adjoint<false, true>(l1, p.L.far_pairs, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
-                walk_adjoint<false, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, sx, sy, sz, s_nb[warp], p,
-                                           g, g4, it);
+                walk_adjoint<false, true>(l1, p.L.far_pairs, false, vt, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                walk_adjoint<false, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, vt, sx, sy, sz, s_nb[warp],
+                                           p, g, g4, it);
             }
-            walk_adjoint<false, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, g, g4, it);
+            walk_adjoint<false, true>(l2, p.L.near_len, true, vt, sx, sy, sz, s_nb[warp], p, g, g4, it);
             const double v = (g4[0] + g4[1]) + (g4[2] + g4[3]);
             if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = v;
             else p.mbar[static_cast<size_t>(src) * NCELL + scell] = v;
@@ -608,9 +742,9 @@ __device__ __forceinline__ void scatter_mass(const P& p, int2 e, int kind, int s
 // A paired entry o: with e, q the even- and odd-order parts of <lb, row(o)>,
 // the source at t+o (pair offset R = -o) receives e + q and the source at
 // t-o (R = +o, odd orders change sign) receives e - q.
-template <bool PAIRED, class P>
-__device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int len, int tx, int ty, int tz,
-                                             const int2* __restrict__ s_nb, const P& p,
+template <bool PAIRED, bool NEAR, class P>
+__device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int len, int tx, int ty,
+                                             int tz, const int2* __restrict__ s_nb, const P& p,
                                              const double (&lb)[16], int item) {
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
@@ -632,6 +766,13 @@ __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int l
                 report(p.status, 3, item);
                 km = K_NONE;
             }
+        }
+        if (NEAR) {
+            // near sources in refined sub-grids: their children, through the
+            // target's virtual children
+            const bool rp = kp == K_MULTI, rm = km == K_MULTI;
+            if (__any_sync(0xffffffffu, rp || rm))
+                refined_near_scatter(p, ox, oy, oz, ep, rp, px, py, pz, em, rm, mx, my, mz, lb, item);
         }
         if (!__any_sync(0xffffffffu, kp >= K_LEAF || km >= K_LEAF)) continue;
         double d[36];
@@ -665,13 +806,13 @@ __device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int
     const int level = info & 0xff;
     const bool leafT = (info >> 8) & 1;
     if (level == 0) {
-        walk_scatter<true>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, lb, it);
+        walk_scatter<true, false>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, lb, it);
     } else {
         const int* lf = p.L.lists + par * p.L.far_len;
-        walk_scatter<true>(lf, p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
-        walk_scatter<false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
+        walk_scatter<true, false>(lf, p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
+        walk_scatter<false, false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
     }
-    if (leafT) walk_scatter<true>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, it);
+    if (leafT) walk_scatter<true, true>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, it);
 }
 
 __global__ void __launch_bounds__(256) scatter_adjoint_kernel(const ScatParams p, int persistent) {
@@ -1270,7 +1411,7 @@ __device__ __forceinline__ void scaled_sep(bool has, const double (&XA)[3], cons
 
 // One stencil segment of a target with explicit centres.  PAIRED: each entry
 // o stands for the sources at t + o and t - o.
-template <int MODE, bool PAIRED>
+template <int MODE, bool PAIRED, bool NEAR = false>
 __device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, int len, bool angular, bool leafT,
                                                  int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                                  const FwdParams& p, const int (&org)[3], double h, double hinv,
@@ -1307,6 +1448,13 @@ __device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, i
                         ot_mono_fwd(a, mp, d);
                     }
                 }
+                if (PAIRED && NEAR) {
+                    // near sources in refined sub-grids (all centres geometric)
+                    const bool rp = kd[0] == K_MULTI, rm = kd[NS - 1] == K_MULTI;
+                    if (__any_sync(0xffffffffu, rp || rm))
+                        refined_near_fwd(p, ox, oy, oz, e[0], rp, sx[0], sy[0], sz[0], e[NS - 1], rm, sx[NS - 1],
+                                         sy[NS - 1], sz[NS - 1], a, item);
+                }
             } else {
 #pragma unroll
                 for (int sd = 0; sd < NS; ++sd) {
@@ -1321,7 +1469,7 @@ __device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, i
                 }
             }
         }
-        if (MODE & 1) {
+        if ((MODE & 1) && !NEAR) {
 #pragma unroll
             for (int sd = 0; sd < NS; ++sd) {
                 const bool multi = kd[sd] == K_MULTI;
@@ -1393,13 +1541,14 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
                                          s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
         } else {
             const int* lf = p.L.lists + par * p.L.far_len;
-            walk_forward_com<MODE, true>(lf, p.L.far_pairs, !leafT, leafT, tx, ty, tz, s_nb[warp], p, org, h, hinv,
+            walk_forward_com<MODE, true>(lf, p.L.far_pairs, !leafT, leafT, tx, ty, tz, s_nb[warp], p, org, h,
+                                         hinv,
                                          XA, a, c, t4, it);
             walk_forward_com<MODE, false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, leafT, tx, ty,
                                           tz, s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
         }
         if (leafT)
-            walk_forward_com<MODE, true>(p.L.lists + p.L.near_off, p.L.near_len, false, true, tx, ty, tz,
+            walk_forward_com<MODE, true, true>(p.L.lists + p.L.near_off, p.L.near_len, false, true, tx, ty, tz,
                                          s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
         store_forward<MODE>(p, node, level, leafT, tcell, a, c, t4);
         __syncwarp();
@@ -1412,8 +1561,9 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
 // point-mass source: a leaf target is at an integer offset (the table row of
 // R/h = sg * o), a non-leaf target uses its own centre.
 template <bool MULTI, bool PAIRED>
-__device__ __forceinline__ void walk_adjoint_com(const int* __restrict__ list, int len, bool near_seg, int sx0,
-                                                 int sy0, int sz0, const int2* __restrict__ s_nb, const AdjParams& p,
+__device__ __forceinline__ void walk_adjoint_com(const int* __restrict__ list, int len, bool near_seg, bool virt_t,
+                                                 int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
+                                                 const AdjParams& p,
                                                  const int (&org)[3], double h, double hinv, const double (&XB)[3],
                                                  double (&g)[16], double (&g4)[4], int item) {
     for (int k = 0; k < len; ++k) {
@@ -1426,21 +1576,15 @@ __device__ __forceinline__ void walk_adjoint_com(const int* __restrict__ list, i
             const int2 e = s_nb[nb_index(tx, ty, tz)];
             const int kind = e.y & 3;
             bool valid = (kind == K_MULTI || kind == K_LEAF) && (!near_seg || kind == K_LEAF);
-            if (valid && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
+            bool vchild = !MULTI && virtual_child_target(e, virt_t);
+            if ((valid || vchild) && static_cast<unsigned>(e.x) >= static_cast<unsigned>(p.n_nodes)) {
                 report(p.status, 4, item);
-                valid = false;
+                valid = vchild = false;
             }
-            if (!__any_sync(0xffffffffu, valid)) continue;
+            if (!__any_sync(0xffffffffu, valid || vchild)) continue;
             const int tcell = (tx & 7) + 8 * (ty & 7) + 64 * (tz & 7);
             double lb[16];
-            if (valid) {
-                const double* src = p.Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + tcell;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) lb[q] = __ldg(src + q * NCELL);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) lb[q] = 0.0;
-            }
+            adjoint_target_lb(p, e, valid, vchild, tx, ty, tz, lb);
             double d[36];
             if (MULTI) {
                 double XA[3] = {0.0, 0.0, 0.0};
@@ -1610,19 +1754,22 @@ __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) g4[q] = 0.0;
         if (skind == K_MULTI) {
+            // targets of the transposed far (root) stencil; near leaf targets
+            // of a refined cell see its children instead
             if ((MODE & 1) && p.Mbar != nullptr) {
-                walk_adjoint_com<true, true>(l1, np, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4, it);
-                walk_adjoint_com<true, false>(l1 + np, ns, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4,
-                                              it);
-                walk_adjoint_com<true, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g,
-                                             g4, it);
+                walk_adjoint_com<true, true>(l1, np, false, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4,
+                                             it);
+                walk_adjoint_com<true, false>(l1 + np, ns, false, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB,
+                                              g, g4, it);
                 store_mbar(p.Mbar, src, scell, hinv, g);
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
-            walk_adjoint_com<false, true>(l1, np, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4, it);
-            walk_adjoint_com<false, false>(l1 + np, ns, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4, it);
-            walk_adjoint_com<false, true>(l2, p.L.near_len, true, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4,
-                                          it);
+            const bool vt = skind == K_LEAF;
+            walk_adjoint_com<false, true>(l1, np, false, vt, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4, it);
+            walk_adjoint_com<false, false>(l1 + np, ns, false, vt, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4,
+                                           it);
+            walk_adjoint_com<false, true>(l2, p.L.near_len, true, vt, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g,
+                                          g4, it);
             const double val = (g4[0] + g4[1]) + (g4[2] + g4[3]);
             if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = val;
             else p.mbar[static_cast<size_t>(src) * NCELL + scell] = val;

@@ -167,6 +167,8 @@ struct ot_grid {
     int* d_vinfo = nullptr;
     int* d_ncoord = nullptr;            // [n][3] sub-grid positions (explicit-centre kernels)
     int* d_vcoord = nullptr;            // [nvirt][3]
+    int* d_child_of = nullptr;          // [n][8] children (coarse leaves refined virtually as targets)
+    double* d_Dv = nullptr;             // [NVROW][16] virtual-child mean rows
     double* d_Dt = nullptr;
     float* d_Dt32 = nullptr;            // double-float split of the point-mass derivatives
     float2* d_mf = nullptr;             // masses as double-float pairs (scratch)
@@ -519,7 +521,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // FP64 instructions per lane and active entry (empty lanes included):
     //   forward point mass 16 | 18 paired; multipole 70 (+30) | 102 (+30);
     //   adjoint point mass 16 | 32 paired; multipole 70 | 102 paired.
-    long long pairs_multi = 0, pairs_mono = 0, pairs_virt = 0, pairs_ang = 0, lanes = 0;
+    //   refined near entries (a leaf target's near source in a refined
+    //   sub-grid): 8 point-mass contractions from the virtual-child table,
+    //   counted as 8 interactions (the source cell's children).
+    long long pairs_multi = 0, pairs_mono = 0, pairs_virt = 0, pairs_ang = 0, pairs_ref = 0, lanes = 0;
     long long flops_fwd = 0, flops_adj = 0, ops_fwd = 0, ops_adj = 0;
     long long flops_adj_scat = 0, ops_adj_scat = 0, count_single_mono = 0;
     long long flops_adj_multi = 0, ops_adj_multi = 0;
@@ -538,22 +543,27 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         const bool leaf = g->is_leaf[i];
         const int s1 = (desc->level[i] == 0) ? 2 : 0;
         for (int j = 0; j < 27; ++j) {
-            long long cp = cnt[s1][1][j], cs = cnt[s1][0][j];
-            if (leaf) {
-                cp += cnt[1][1][j];
-                cs += cnt[1][0][j];
-            }
+            const long long cpf = cnt[s1][1][j], csf = cnt[s1][0][j];                 // far / root
+            const long long cpn = leaf ? cnt[1][1][j] : 0, csn = leaf ? cnt[1][0][j] : 0;   // near
+            const long long cp = cpf + cpn, cs = csf + csn;
             if (mm >> j & 1u) {
-                pairs_multi += cp + cs;
+                pairs_multi += cpf + csf;
                 if (!leaf) {
-                    pairs_ang += cp + cs;
-                    flops_fwd += 116 * cp + 200 * cs;
+                    pairs_ang += cpf + csf;
+                    flops_fwd += 116 * cpf + 200 * csf;
                 } else {
-                    flops_fwd += 86 * cp + 140 * cs;
+                    flops_fwd += 86 * cpf + 140 * csf;
                 }
                 // explicit centres: every multipole pair evaluates its derivatives
-                flops_fwd_com += (cp + cs) * (leaf ? deriv_flops(19) + 140 : deriv_flops(31) + 200);
-                flops_adj_com += (cp + cs) * (deriv_flops(19) + 140);
+                flops_fwd_com += (cpf + csf) * (leaf ? deriv_flops(19) + 140 : deriv_flops(31) + 200);
+                flops_adj_com += (cpf + csf) * (deriv_flops(19) + 140);
+                // near sources in the refined sub-grid: its cells' children
+                pairs_ref += cpn + csn;
+                pairs_mono += 8 * (cpn + csn);
+                flops_fwd += 8 * (17 * cpn + 32 * csn);
+                flops_fwd_com += 8 * (17 * cpn + 32 * csn);
+                flops_adj_scat += 8 * (16 * cpn + 32 * csn);
+                flops_adj_com += 8 * (16 * cpn + 32 * csn);
             }
             if (mo >> j & 1u) {
                 pairs_mono += cp + cs;
@@ -572,7 +582,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 const std::vector<uint32_t>& mk = mask[ph][sg];
                 const std::vector<uint8_t>& pf = pflag[ph][sg];
                 for (size_t k = 0; k < mk.size(); ++k) {
-                    if (mk[k] & mm) cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
+                    if (mk[k] & mm) {
+                        if (sg == 1) cost[2] += 8 * 18;     // refined near source: 8 paired contractions
+                        else cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
+                    }
                     if (mk[k] & mo) {
                         cost[2] += pf[k] ? 18 : 16;
                         if (!pf[k]) count_single_mono -= 1;    // 17 ops single in the scatter
@@ -611,15 +624,19 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         const int2* tbl = virt ? &g->vnbr[static_cast<size_t>(i - n) * 27] : &g->nbr[static_cast<size_t>(i) * 27];
         const int lvl = virt ? g->vinfo[i - n] : desc->level[i];
         const int s1 = (lvl == 0) ? 2 : 0;
-        uint32_t tv = 0, tl = 0;
+        // targets: multipole or leaf cells (far / root), leaf cells (near, for
+        // point-mass sources only), and for real leaf sources the virtual
+        // children of coarse leaves (depth 1), far and near
+        uint32_t tv = 0, tl = 0, tw = 0;
         for (int j = 0; j < 27; ++j) {
             const int k = tbl[j].y & 3;
             if (k == K_MULTI || k == K_LEAF) tv |= 1u << j;
             if (k == K_LEAF) tl |= 1u << j;
+            if (!virt && leaf && k == K_VIRT && ((static_cast<unsigned>(tbl[j].y) >> 2) & 7u) == 1u) tw |= 1u << j;
         }
         for (int j = 0; j < 27; ++j) {
-            long long cp = (tv >> j & 1u) ? cnt[s1][1][j] : 0, cs = (tv >> j & 1u) ? cnt[s1][0][j] : 0;
-            if (tl >> j & 1u) {
+            long long cp = ((tv | tw) >> j & 1u) ? cnt[s1][1][j] : 0, cs = ((tv | tw) >> j & 1u) ? cnt[s1][0][j] : 0;
+            if (leaf && ((tl | tw) >> j & 1u)) {
                 cp += cnt[1][1][j];
                 cs += cnt[1][0][j];
             }
@@ -631,9 +648,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         for (int ph = 0; ph < 16; ++ph) {
             long long cst = 0;
             for (size_t k = 0; k < mask[ph][s1].size(); ++k)
-                if (mask[ph][s1][k] & tv) cst += leaf ? (pflag[ph][s1][k] ? 32 : 16) : (pflag[ph][s1][k] ? 102 : 70);
-            for (size_t k = 0; k < mask[ph][1].size(); ++k)
-                if (mask[ph][1][k] & tl) cst += leaf ? 32 : 102;
+                if (mask[ph][s1][k] & (tv | tw))
+                    cst += leaf ? (pflag[ph][s1][k] ? 32 : 16) : (pflag[ph][s1][k] ? 102 : 70);
+            if (leaf)
+                for (size_t k = 0; k < mask[ph][1].size(); ++k)
+                    if (mask[ph][1][k] & (tl | tw)) cst += 32;
             if (cst == 0) continue;
             ops_adj += 32 * cst;
             if (!leaf) ops_adj_multi += 32 * cst;
@@ -666,6 +685,58 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                          [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
                              return a.first > b.first;
                          });
+
+    // --- coarse leaf targets next to refined sub-grids ------------------------
+    // A leaf's near sources in a refined neighbour are replaced by that
+    // cell's children one level down (seen from the leaf's virtual
+    // children); they must be leaf cells, which 2:1 balance guarantees: every
+    // child of a refined neighbour that touches the leaf must be a leaf.
+    std::vector<int> child_of(static_cast<size_t>(n) * 8, -1);
+    for (int i = 0; i < n; ++i)
+        for (int b = 0; b < 8; ++b)
+            child_of[static_cast<size_t>(i) * 8 + b] =
+                B.find(desc->level[i] + 1, 2L * desc->coord[3 * i] + (b & 1),
+                       2L * desc->coord[3 * i + 1] + ((b >> 1) & 1), 2L * desc->coord[3 * i + 2] + (b >> 2));
+    for (int i = 0; i < n; ++i) {
+        if (!g->is_leaf[i]) continue;
+        for (int j = 0; j < 27; ++j) {
+            const int2 e = g->nbr[static_cast<size_t>(i) * 27 + j];
+            if ((e.y & 3) != K_MULTI) continue;
+            for (int b = 0; b < 8; ++b) {
+                const int c = child_of[static_cast<size_t>(e.x) * 8 + b];
+                if (c < 0 || g->is_leaf[c]) continue;
+                bool touch = true;
+                for (int a = 0; a < 3; ++a) {
+                    const long cc = 2L * desc->coord[3 * e.x + a] + ((b >> a) & 1);
+                    const long lo = 2L * desc->coord[3 * i + a];
+                    touch = touch && cc >= lo - 1 && cc <= lo + 2;
+                }
+                if (touch)
+                    return fail(OT_EINVAL,
+                                "tree is not 2:1 balanced: leaf sub-grid %d (level %d) touches refined sub-grid %d "
+                                "of its neighbour's children",
+                                i, desc->level[i], c);
+            }
+        }
+    }
+    // virtual-child mean rows: Dv[q][j] = 2^(n_j+1)/8 * sum_cv Dt[row(q - cv)][j],
+    // q = 2o + cs in [-6, 7]^3 (row(o) holds the derivatives at -o)
+    std::vector<double> Dv(static_cast<size_t>(NVROW) * 16, 0.0);
+    {
+        const double fo[4] = {0.25, 0.5, 1.0, 2.0};
+        const int ord[16] = {0, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3};
+        for (int qz = -6; qz <= 7; ++qz)
+            for (int qy = -6; qy <= 7; ++qy)
+                for (int qx = -6; qx <= 7; ++qx) {
+                    double* out = &Dv[static_cast<size_t>((qx + 6) + 14 * (qy + 6) + 196 * (qz + 6)) * 16];
+                    for (int cv = 0; cv < 8; ++cv) {
+                        const int rx = qx - (cv & 1), ry = qy - ((cv >> 1) & 1), rz = qz - (cv >> 2);
+                        const double* row = &Dt[static_cast<size_t>((rx + 7) + 15 * (ry + 7) + 225 * (rz + 7)) * DROW];
+                        for (int j = 0; j < 16; ++j) out[j] += row[j];
+                    }
+                    for (int j = 0; j < 16; ++j) out[j] *= fo[ord[j]];
+                }
+    }
 
     // --- M2M schedule ---------------------------------------------------------
     std::vector<int> nonleaf, all(n), cube;
@@ -707,6 +778,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.pairs_multipole = pairs_multi;
     I.pairs_monopole = pairs_mono;
     I.pairs_virtual = pairs_virt;
+    I.pairs_refined = pairs_ref;
     I.pairs_angular = pairs_ang;
     I.lanes_fwd = lanes;
     I.flops_fwd = flops_fwd;
@@ -744,6 +816,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_ninfo, g->ninfo);
     UP(g->d_vinfo, g->vinfo);
     UP(g->d_vcoord, vcoord);
+    UP(g->d_child_of, child_of);
+    UP(g->d_Dv, Dv);
     {
         std::vector<int> nc(desc->coord, desc->coord + 3 * static_cast<size_t>(n));
         UP(g->d_ncoord, nc);
@@ -837,6 +911,8 @@ static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, 
     p.accumulate = accumulate;
     p.n_nodes = g->n;
     p.status = g->d_status;
+    p.child_of = g->d_child_of;
+    p.Dv = g->d_Dv;
     for (int l = 0; l < MAXLEV; ++l) p.hinv[l] = g->hinv[l];
     return p;
 }
@@ -903,6 +979,8 @@ static ot_status enqueue_scatter(ot_grid* g, double* mbar, cudaStream_t s) {
     p.mbar = mbar;
     p.n_nodes = g->n;
     p.status = g->d_status;
+    p.child_of = g->d_child_of;
+    p.Dv = g->d_Dv;
     if (g->schedule == OT_SCHED_PER_SUBGRID) {
         for (int i = 0; i < g->n; ++i) {
             ScatParams q = p;
@@ -963,6 +1041,8 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     p.vbar = g->d_vbar;
     p.n_nodes = g->n;
     p.status = g->d_status;
+    p.child_of = g->d_child_of;
+    p.Dv = g->d_Dv;
     for (int l = 0; l < MAXLEV; ++l) p.hinv[l] = g->hinv[l];
     if (g->schedule == OT_SCHED_PER_SUBGRID) {
         // one launch per source sub-grid (real and virtual)
@@ -1067,6 +1147,8 @@ static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const doub
     p.vbar = g->d_vbar;
     p.n_nodes = g->n;
     p.status = g->d_status;
+    p.child_of = g->d_child_of;
+    p.Dv = g->d_Dv;
     com_scales(g, p.hinv, p.hreal);
     p.C = C;
     p.ncoord = g->d_ncoord;
