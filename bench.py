@@ -389,16 +389,19 @@ def run_ours(args, rank, world):
                    "autotuned": tuned, "l2": "flushed between steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "fwd": {"value": pairs_fwd / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms,
-                "pairs_in_domain": pairs_fwd, "pairs_padded": info["lanes_fwd"]},
+                "pairs_in_domain": pairs_fwd, "pairs_padded": info["pairs_padded_fwd"]},
         "variants": {
             "multipole": {"value": info["pairs_multipole"] / (variant_ms["multipole"] * 1e-3), "unit": UNIT,
                           "ms": variant_ms["multipole"], "pairs": info["pairs_multipole"],
                           "pairs_with_angular_term": info["pairs_angular"]},
             "monopole": {"value": info["pairs_monopole"] / (variant_ms["monopole"] * 1e-3), "unit": UNIT,
                          "ms": variant_ms["monopole"], "pairs": info["pairs_monopole"]},
-            "boundary": {"pairs": info["pairs_virtual"],
-                         "note": "point-mass pairs whose source is a virtual descendant of a coarser leaf; "
-                                 "they run inside the monopole launch"},
+            "boundary": {"pairs": info["pairs_virtual"] + info["pairs_refined"],
+                         "pairs_virtual_source": info["pairs_virtual"],
+                         "pairs_refined_target": info["pairs_refined"],
+                         "note": "coarse-fine pairs: point masses that are virtual descendants of a coarser "
+                                 "leaf, and coarse leaf targets refined virtually against a refined neighbour's "
+                                 "children; both run inside the monopole launch"},
             "note": "separate launches of one pass each; the fused launch (fwd) runs both"},
         "adjoint": {"value": pairs_fwd / (adj_ms * 1e-3), "unit": UNIT, "ms": adj_ms},
         "fwd_df64_point_mass": {"value": pairs_fwd / (df_ms * 1e-3), "unit": UNIT, "ms": df_ms,

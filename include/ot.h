@@ -122,7 +122,9 @@ typedef struct {
     int64_t flops_adj_com;         /* the same for ot_interactions_backward_com */
     int64_t pairs_refined;         /* near pairs of a leaf target and a cell of a refined
                                       sub-grid, evaluated through the leaf's virtual children
-                                      (each counted as 8 point-mass pairs in pairs_monopole) */
+                                      (each counted once in pairs_monopole) */
+    int64_t pairs_padded_fwd;      /* pairs the forward's lanes run, sources outside the domain
+                                      included (a paired entry runs two per lane) */
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the

@@ -463,7 +463,7 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                     int cs_[8][2];
                     double Rc[8][8][3];
                     refined_pairs(t, l, g, q, cs_, Rc);
-                    npairs += 8;
+                    npairs += 1;   /* one stencil pair */
                     for (int cs = 0; cs < 8; cs++) {
                         double ms = m[(size_t)cs_[cs][0] * NCELL + cs_[cs][1]];
                         for (int cv = 0; cv < 8; cv++) {
@@ -640,7 +640,7 @@ long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord,
                             int cs_[8][2];
                             double Rc[8][8][3];
                             refined_pairs(&t, l, g, q, cs_, Rc);
-                            npairs += 8;
+                            npairs += 1;   /* one stencil pair */
                             for (int cs = 0; cs < 8; cs++) {
                                 double acc = 0.0, sacc = 0.0;
                                 for (int cv = 0; cv < 8; cv++) {

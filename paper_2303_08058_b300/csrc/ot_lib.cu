@@ -523,8 +523,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     //   adjoint point mass 16 | 32 paired; multipole 70 | 102 paired.
     //   refined near entries (a leaf target's near source in a refined
     //   sub-grid): 8 point-mass contractions from the virtual-child table,
-    //   counted as 8 interactions (the source cell's children).
+    //   counted as one interaction (one stencil pair).
     long long pairs_multi = 0, pairs_mono = 0, pairs_virt = 0, pairs_ang = 0, pairs_ref = 0, lanes = 0;
+    long long padded = 0;   // pairs the lanes run, out-of-domain sources included
     long long flops_fwd = 0, flops_adj = 0, ops_fwd = 0, ops_adj = 0;
     long long flops_adj_scat = 0, ops_adj_scat = 0, count_single_mono = 0;
     long long flops_adj_multi = 0, ops_adj_multi = 0;
@@ -559,7 +560,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 flops_adj_com += (cpf + csf) * (deriv_flops(19) + 140);
                 // near sources in the refined sub-grid: its cells' children
                 pairs_ref += cpn + csn;
-                pairs_mono += 8 * (cpn + csn);
+                pairs_mono += cpn + csn;
                 flops_fwd += 8 * (17 * cpn + 32 * csn);
                 flops_fwd_com += 8 * (17 * cpn + 32 * csn);
                 flops_adj_scat += 8 * (16 * cpn + 32 * csn);
@@ -590,7 +591,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         cost[2] += pf[k] ? 18 : 16;
                         if (!pf[k]) count_single_mono -= 1;    // 17 ops single in the scatter
                     }
-                    if (mk[k] & (mm | mo)) lanes += 32;
+                    if (mk[k] & (mm | mo)) {
+                        lanes += 32;
+                        padded += 32 * (pf[k] ? 2 : 1);
+                    }
                 }
             };
             scan(s1);
@@ -781,6 +785,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.pairs_refined = pairs_ref;
     I.pairs_angular = pairs_ang;
     I.lanes_fwd = lanes;
+    I.pairs_padded_fwd = padded;
     I.flops_fwd = flops_fwd;
     g->flops_adj_det = flops_adj;
     g->ops_adj_det = ops_adj;

@@ -125,3 +125,42 @@ def test_config5_binary_star_steps(ot, orc, step):
     assert lhs == pytest.approx(rhs, rel=1e-11)
     g.check()
     g.close()
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_mirror_symmetry_full_size(ot, axis):
+    """The 64^3 workload with its density mirrored across the x (or z)
+    mid-plane: the GPU's coefficients of both passes mirror, with the
+    components of odd order along that axis negated.  Exercises the +-o
+    pairing, the parity-dependent lists and the z-halves of the warp layout."""
+    tree, rho = synth.config2()
+    rho = rho * (1.0 + 0.3 * np.random.default_rng(120 + axis).random(rho.shape))   # break the star's symmetry
+    idx = tree.index()
+    exps = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1),
+            (0, 0, 2), (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1),
+            (0, 1, 2), (0, 0, 3)]
+
+    def mirror(field):
+        out = np.empty_like(field)
+        for (l, x, y, z), i in idx.items():
+            c = [x, y, z]
+            c[axis] = 2 ** l - 1 - c[axis]
+            j = idx[(l, *c)]
+            f = field[j].reshape(field.shape[1:-1] + (8, 8, 8))            # [..., z, y, x]
+            out[i] = np.flip(f, axis=f.ndim - 1 - axis).reshape(field.shape[1:])
+        return out
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L, Lc = g.interactions(M, m)
+    Mm, mm = g.moments(dev(mirror(rho)))
+    Lm, Lcm = g.interactions(Mm, mm)
+    torch.cuda.synchronize()
+    sign = np.array([-1.0 if e[axis] % 2 else 1.0 for e in exps])[None, :, None]
+    want = sign * mirror(host(L))
+    scale = np.max(np.abs(host(L)), axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(host(Lm) - want) / scale) < 1e-12
+    # the angular term is a force: its component along the axis flips
+    sc = np.array([-1.0 if a == axis else 1.0 for a in range(3)])[None, :, None]
+    want_c = sc * mirror(host(Lc))
+    scale_c = np.max(np.abs(host(Lc)), axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(host(Lcm) - want_c) / scale_c) < 1e-12

@@ -666,3 +666,30 @@ def test_coarse_target_sees_fine_mass_through_virtual_children(orc):
             want1 += R / d ** 3 / 8.0
         assert L[0] == pytest.approx(want0, rel=1e-14)
         np.testing.assert_allclose(L[1:4], want1, rtol=1e-14)
+
+
+def test_mirror_symmetry(orc):
+    """Mirroring the density of a uniform tree across the x mid-plane mirrors
+    the coefficients of both passes: L'(x) = S L(X - x), S negating the
+    components of odd x-order (D(-R) = (-1)^k D(R) and the mirror-symmetric
+    stencils)."""
+    tree = synth.uniform_tree(1, 1.0)
+    rng = np.random.default_rng(27)
+    rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    idx = tree.index()
+
+    def mirror(field):
+        out = np.empty_like(field)
+        for (l, x, y, z), i in idx.items():
+            j = idx[(l, 2 ** l - 1 - x, y, z)]
+            f = field[j].reshape(field.shape[1:-1] + (8, 8, 8))    # [..., z, y, x]
+            out[i] = f[..., ::-1].reshape(field.shape[1:])
+        return out
+    rho_m = mirror(rho)
+    M, Mm = orc.moments(tree, rho), orc.moments(tree, rho_m)
+    L = orc.run_pass_grid(tree, "multipole", M=M)["L"] + orc.run_pass_grid(tree, "monopole", m=M[:, 0])["L"]
+    Lm = orc.run_pass_grid(tree, "multipole", M=Mm)["L"] + orc.run_pass_grid(tree, "monopole", m=Mm[:, 0])["L"]
+    sign = np.array([-1.0 if e[0] % 2 else 1.0 for e in EXP20])[None, :, None]
+    want = sign * mirror(L)
+    scale = np.max(np.abs(L), axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(Lm - want) / scale) < 1e-13
