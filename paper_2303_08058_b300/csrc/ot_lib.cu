@@ -10,6 +10,7 @@
 #include <atomic>
 #include <chrono>
 #include <map>
+#include <mutex>
 #include <set>
 #include <new>
 #include <string>
@@ -243,6 +244,16 @@ struct ot_grid {
         if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };
+
+// Live handles: every entry point checks its handle against this set, so a
+// destroyed or foreign pointer is refused (OT_EINVAL) instead of used.
+static std::mutex g_handles_mu;
+static std::set<const ot_grid*> g_handles;
+
+static bool grid_live(const ot_grid* g) {
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    return g_handles.count(g) != 0;
+}
 
 // ---------------------------------------------------------------------------
 // geometry
@@ -1181,10 +1192,12 @@ static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const doub
 // The scratch covers the node-index span of the non-leaf sub-grids only;
 // nothing on this path allocates memory.
 ot_status otk_set_error(ot_status code, const char* msg) { return fail(code, "%s", msg); }
+bool otk_grid_live(const ot_grid* g) { return grid_live(g); }
 
 ot_status otk_multipole_with_scratch(ot_grid* g, const double* M, double* L, double* Lc, double* scratch,
                                      size_t scratch_doubles, cudaStream_t s) {
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     if (!M || !aligned16(M)) return fail(OT_EINVAL, "M is NULL or not 16-byte aligned");
     if (!L || !aligned16(L)) return fail(OT_EINVAL, "L is NULL or not 16-byte aligned");
     if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
@@ -1314,6 +1327,10 @@ ot_status ot_grid_create(const ot_grid_desc* desc, void* stream, ot_grid** out) 
     g->info.warps_per_block = g->wpb;
     g->info.blocks_per_sm = g->bps;
     g->info.graphs_enabled = g->use_graph;
+    {
+        std::lock_guard<std::mutex> lk(g_handles_mu);
+        g_handles.insert(g);
+    }
     *out = g;
     return OT_OK;
     GUARD_END
@@ -1322,6 +1339,10 @@ ot_status ot_grid_create(const ot_grid_desc* desc, void* stream, ot_grid** out) 
 ot_status ot_grid_destroy(ot_grid* grid) {
     GUARD_BEGIN
     if (!grid) return OT_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_handles_mu);
+        if (!g_handles.erase(grid)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
+    }
     cudaDeviceSynchronize();
     delete grid;
     return OT_OK;
@@ -1330,6 +1351,7 @@ ot_status ot_grid_destroy(ot_grid* grid) {
 
 ot_status ot_grid_info(const ot_grid* grid, ot_grid_info_t* info) {
     if (!grid || !info) return fail(OT_EINVAL, "grid and info must not be NULL");
+    if (!grid_live(grid)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     *info = grid->info;
     return OT_OK;
 }
@@ -1338,6 +1360,7 @@ ot_status ot_set_schedule(ot_grid* g, int32_t schedule, int32_t warps_per_block,
                           int32_t use_graph) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     if (schedule != OT_SCHED_PERSISTENT && schedule != OT_SCHED_PER_SUBGRID)
         return fail(OT_EINVAL, "unknown schedule %d", schedule);
     if (warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8)
@@ -1531,6 +1554,7 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
 ot_status ot_set_precision(ot_grid* g, int32_t mode) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     if (mode != OT_PREC_FP64 && mode != OT_PREC_DF64_POINT_MASS)
         return fail(OT_EINVAL, "unknown precision mode %d", mode);
     g->precision = mode;
@@ -1541,6 +1565,7 @@ ot_status ot_set_precision(ot_grid* g, int32_t mode) {
 ot_status ot_set_deterministic(ot_grid* g, int32_t on) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     if (on != 0 && on != 1) return fail(OT_EINVAL, "on must be 0 or 1");
     g->deterministic = on;
     g->info.flops_adj = on ? g->flops_adj_det : g->flops_adj_fast;
@@ -1552,6 +1577,7 @@ ot_status ot_set_deterministic(ot_grid* g, int32_t on) {
 ot_status ot_moments(ot_grid* g, const double* rho, double* M, double* m, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(rho, "rho");
     CHECK_PTR(M, "M");
     CHECK_PTR(m, "m");
@@ -1567,6 +1593,7 @@ ot_status ot_moments(ot_grid* g, const double* rho, double* M, double* m, void* 
 ot_status ot_moments_backward(ot_grid* g, const double* Mbar, const double* mbar, double* rhobar, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(rhobar, "rhobar");
     if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
     if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
@@ -1584,6 +1611,7 @@ ot_status ot_moments_backward(ot_grid* g, const double* Mbar, const double* mbar
 ot_status ot_l2l(ot_grid* g, double* L, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(L, "L");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // m2m holds the parents deepest level first: walk it from the root down
@@ -1597,6 +1625,7 @@ ot_status ot_l2l(ot_grid* g, double* L, void* stream) {
 ot_status ot_l2l_backward(ot_grid* g, double* Lbar, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(Lbar, "Lbar");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (auto& L : g->m2m)
@@ -1610,6 +1639,7 @@ ot_status ot_multipole_interactions(ot_grid* g, const double* M, const double* c
                                     void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     if (centres) return ot_interactions_com(g, M, nullptr, centres, L, Lc, stream);
     CHECK_PTR(M, "M");
     CHECK_PTR(L, "L");
@@ -1623,6 +1653,7 @@ ot_status ot_multipole_interactions(ot_grid* g, const double* M, const double* c
 ot_status ot_monopole_interactions(ot_grid* g, const double* m, double* L, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(m, "m");
     CHECK_PTR(L, "L");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1634,6 +1665,7 @@ ot_status ot_monopole_interactions(ot_grid* g, const double* m, double* L, void*
 ot_status ot_interactions(ot_grid* g, const double* M, const double* m, double* L, double* Lc, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(M, "M");
     CHECK_PTR(m, "m");
     CHECK_PTR(L, "L");
@@ -1647,6 +1679,7 @@ ot_status ot_interactions(ot_grid* g, const double* M, const double* m, double* 
 ot_status ot_interactions_backward(ot_grid* g, const double* Lbar, double* Mbar, double* mbar, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(Lbar, "Lbar");
     if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
     if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
@@ -1659,6 +1692,7 @@ ot_status ot_interactions_backward(ot_grid* g, const double* Lbar, double* Mbar,
 ot_status ot_moments_com(ot_grid* g, const double* rho, double* M, double* m, double* C, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(rho, "rho");
     CHECK_PTR(M, "M");
     CHECK_PTR(m, "m");
@@ -1677,6 +1711,7 @@ ot_status ot_interactions_com(ot_grid* g, const double* M, const double* m, cons
                               void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     if (!M && !m) return fail(OT_EINVAL, "M and m are both NULL");
     if (M && !aligned16(M)) return fail(OT_EINVAL, "M is not 16-byte aligned");
     if (m && !aligned16(m)) return fail(OT_EINVAL, "m is not 16-byte aligned");
@@ -1694,6 +1729,7 @@ ot_status ot_interactions_backward_com(ot_grid* g, const double* Lbar, const dou
                                        void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(Lbar, "Lbar");
     CHECK_PTR(C, "C");
     if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
@@ -1707,6 +1743,7 @@ ot_status ot_interactions_backward_com(ot_grid* g, const double* Lbar, const dou
 ot_status ot_l2l_com(ot_grid* g, const double* C, double* L, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(C, "C");
     CHECK_PTR(L, "L");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1720,6 +1757,7 @@ ot_status ot_l2l_com(ot_grid* g, const double* C, double* L, void* stream) {
 ot_status ot_l2l_com_backward(ot_grid* g, const double* C, double* Lbar, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(C, "C");
     CHECK_PTR(Lbar, "Lbar");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1734,6 +1772,7 @@ ot_status ot_autotune(ot_grid* g, const double* M, const double* m, double* L, d
                       int32_t* best_warps, int32_t* best_blocks, double* best_ms) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     CHECK_PTR(M, "M");
     CHECK_PTR(m, "m");
     CHECK_PTR(L, "L");
@@ -1791,6 +1830,7 @@ ot_status ot_autotune(ot_grid* g, const double* M, const double* m, double* L, d
 ot_status ot_grid_check(ot_grid* g, void* stream) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
+    if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int h[2] = {0, 0};
     OT_CUDA(cudaMemcpyAsync(h, g->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));

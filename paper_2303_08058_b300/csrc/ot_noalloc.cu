@@ -16,11 +16,12 @@
 #include "../../include/ot.h"
 #include "ot_internal.h"
 
-// defined in ot_lib.cu: the multipole pass with caller-supplied scratch, and
-// the setter of the calling thread's error message
+// defined in ot_lib.cu: the multipole pass with caller-supplied scratch, the
+// setter of the calling thread's error message, and the live-handle check
 ot_status otk_multipole_with_scratch(ot_grid* g, const double* M, double* L, double* Lc, double* scratch,
                                      size_t scratch_doubles, cudaStream_t s);
 ot_status otk_set_error(ot_status code, const char* msg);
+bool otk_grid_live(const ot_grid* g);
 
 namespace {
 
@@ -56,6 +57,7 @@ ot_status scratch_address(int dev, double** out) {
 extern "C" ot_status ot_multipole_interactions_noalloc(ot_grid* grid, const double* M, double* L, double* Lc,
                                                        void* stream) {
     if (!grid) return otk_set_error(OT_EINVAL, "grid is NULL");
+    if (!otk_grid_live(grid)) return otk_set_error(OT_EINVAL, "grid handle is not live (destroyed or never created)");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();

@@ -5,6 +5,9 @@ interaction path (moments, both passes, adjoints) runs in libotfmm's kernels.
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
+import os
 
 import numpy as np
 import torch
@@ -66,6 +69,17 @@ class OTGrid:
             pass
 
     # -- helpers -------------------------------------------------------------------
+    def _p(self, t, comps):
+        """Pointer of a [n][comps][512] float64 tensor on this grid's device;
+        the library cannot check sizes, so the binding does."""
+        if t is None:
+            return None
+        if t.numel() != self.n * comps * NCELL:
+            raise ValueError(f"expected {self.n} x {comps} x {NCELL} elements, got shape {tuple(t.shape)}")
+        if t.device != self.device:
+            raise ValueError(f"tensor on {t.device}, grid on {self.device}")
+        return _ptr(t)
+
     def zeros(self, *shape):
         return torch.zeros(*shape, dtype=torch.float64, device=self.device)
 
@@ -90,11 +104,42 @@ class OTGrid:
         """Fixed-order (bit-reproducible) adjoint instead of the atomic one."""
         _lib.check(self.lib.ot_set_deterministic(self.handle, int(bool(on))))
 
-    def autotune(self, M, m, L, Lc=None, stream=None):
+    def config_key(self) -> str:
+        """Hash of the tree and the device: the key of a tuned tile shape."""
+        h = hashlib.sha1()
+        for a in (self.level, self.coord, self.is_leaf, np.float64(self.h0)):
+            h.update(np.ascontiguousarray(a).tobytes())
+        h.update(torch.cuda.get_device_name(self.device).encode())
+        return h.hexdigest()
+
+    def autotune(self, M, m, L, Lc=None, stream=None, cache=None):
+        """Time the fused launch over tile shapes and keep the fastest.  With
+        ``cache`` (a JSON file path) a shape tuned before for the same tree on
+        the same device is applied without timing, and new results are added."""
+        key = self.config_key()
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                hit = json.load(f).get(key)
+            if hit is not None:
+                self.set_schedule(_lib.OT_SCHED_PERSISTENT, hit["warps_per_block"], hit["blocks_per_sm"],
+                                  bool(self.info()["graphs_enabled"]))
+                return dict(hit, cached=True)
         w, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-        _lib.check(self.lib.ot_autotune(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), _stream(stream),
-                                        ctypes.byref(w), ctypes.byref(b), ctypes.byref(ms)))
-        return dict(warps_per_block=w.value, blocks_per_sm=b.value, ms=ms.value)
+        _lib.check(self.lib.ot_autotune(self.handle, self._p(M, NCOMP), self._p(m, 1), self._p(L, NCOMP),
+                                        self._p(Lc, 3), _stream(stream), ctypes.byref(w), ctypes.byref(b),
+                                        ctypes.byref(ms)))
+        out = dict(warps_per_block=w.value, blocks_per_sm=b.value, ms=ms.value)
+        if cache is not None:
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    table = json.load(f)
+            table[key] = out
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1)
+            os.replace(tmp, cache)
+        return dict(out, cached=False)
 
     def completion_study(self, M, m, mechanism, n_streams=1, timeout_s=60.0, L=None, Lc=None):
         """Per-sub-grid launches with completion signalled by mechanism 0 (stream
@@ -102,41 +147,44 @@ class OTGrid:
         L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
         Lc = Lc if Lc is not None else self.zeros(self.n, 3, NCELL)
         out = _lib.CompletionStats()
-        _lib.check(self.lib.ot_completion_study(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), int(mechanism),
-                                                int(n_streams), float(timeout_s), ctypes.byref(out)))
+        _lib.check(self.lib.ot_completion_study(self.handle, self._p(M, NCOMP), self._p(m, 1), self._p(L, NCOMP),
+                                                self._p(Lc, 3), int(mechanism), int(n_streams), float(timeout_s),
+                                                ctypes.byref(out)))
         return {name: getattr(out, name) for name, _ in out._fields_}, L, Lc
 
     # -- the path ------------------------------------------------------------------
     def moments(self, rho, M=None, m=None, stream=None):
         M = M if M is not None else self.zeros(self.n, NCOMP, NCELL)
         m = m if m is not None else self.zeros(self.n, NCELL)
-        _lib.check(self.lib.ot_moments(self.handle, _ptr(rho), _ptr(M), _ptr(m), _stream(stream)))
+        _lib.check(self.lib.ot_moments(self.handle, self._p(rho, 1), self._p(M, NCOMP), self._p(m, 1),
+                                       _stream(stream)))
         return M, m
 
     def moments_backward(self, Mbar=None, mbar=None, rhobar=None, stream=None):
         rhobar = rhobar if rhobar is not None else self.zeros(self.n, NCELL)
-        _lib.check(self.lib.ot_moments_backward(self.handle, _ptr(Mbar), _ptr(mbar), _ptr(rhobar),
-                                                _stream(stream)))
+        _lib.check(self.lib.ot_moments_backward(self.handle, self._p(Mbar, NCOMP), self._p(mbar, 1),
+                                                self._p(rhobar, 1), _stream(stream)))
         return rhobar
 
     def multipole(self, M, L=None, Lc=None, want_lc=True, centres=None, stream=None):
         L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
         if Lc is None and want_lc:
             Lc = self.zeros(self.n, 3, NCELL)
-        _lib.check(self.lib.ot_multipole_interactions(self.handle, _ptr(M), _ptr(centres), _ptr(L), _ptr(Lc),
-                                                      _stream(stream)))
+        _lib.check(self.lib.ot_multipole_interactions(self.handle, self._p(M, NCOMP), self._p(centres, 3),
+                                                      self._p(L, NCOMP), self._p(Lc, 3), _stream(stream)))
         return L, Lc
 
     def monopole(self, m, L=None, stream=None):
         L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
-        _lib.check(self.lib.ot_monopole_interactions(self.handle, _ptr(m), _ptr(L), _stream(stream)))
+        _lib.check(self.lib.ot_monopole_interactions(self.handle, self._p(m, 1), self._p(L, NCOMP), _stream(stream)))
         return L
 
     def interactions(self, M, m, L=None, Lc=None, want_lc=True, stream=None):
         L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
         if Lc is None and want_lc:
             Lc = self.zeros(self.n, 3, NCELL)
-        _lib.check(self.lib.ot_interactions(self.handle, _ptr(M), _ptr(m), _ptr(L), _ptr(Lc), _stream(stream)))
+        _lib.check(self.lib.ot_interactions(self.handle, self._p(M, NCOMP), self._p(m, 1), self._p(L, NCOMP),
+                                            self._p(Lc, 3), _stream(stream)))
         return L, Lc
 
     # -- centre-of-mass expansion centres ----------------------------------------
@@ -145,7 +193,8 @@ class OTGrid:
         M = M if M is not None else self.zeros(self.n, NCOMP, NCELL)
         m = m if m is not None else self.zeros(self.n, NCELL)
         C = C if C is not None else self.zeros(self.n, 3, NCELL)
-        _lib.check(self.lib.ot_moments_com(self.handle, _ptr(rho), _ptr(M), _ptr(m), _ptr(C), _stream(stream)))
+        _lib.check(self.lib.ot_moments_com(self.handle, self._p(rho, 1), self._p(M, NCOMP), self._p(m, 1),
+                                           self._p(C, 3), _stream(stream)))
         return M, m, C
 
     def interactions_com(self, M, m, C, L=None, Lc=None, want_lc=True, stream=None):
@@ -153,8 +202,8 @@ class OTGrid:
         L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
         if Lc is None and want_lc and M is not None:
             Lc = self.zeros(self.n, 3, NCELL)
-        _lib.check(self.lib.ot_interactions_com(self.handle, _ptr(M), _ptr(m), _ptr(C), _ptr(L), _ptr(Lc),
-                                                _stream(stream)))
+        _lib.check(self.lib.ot_interactions_com(self.handle, self._p(M, NCOMP), self._p(m, 1), self._p(C, 3),
+                                                self._p(L, NCOMP), self._p(Lc, 3), _stream(stream)))
         return L, Lc
 
     def backward_com(self, Lbar, C, Mbar=None, mbar=None, want=(True, True), stream=None):
@@ -163,16 +212,16 @@ class OTGrid:
             Mbar = self.zeros(self.n, NCOMP, NCELL)
         if mbar is None and want[1]:
             mbar = self.zeros(self.n, NCELL)
-        _lib.check(self.lib.ot_interactions_backward_com(self.handle, _ptr(Lbar), _ptr(C), _ptr(Mbar), _ptr(mbar),
-                                                         _stream(stream)))
+        _lib.check(self.lib.ot_interactions_backward_com(self.handle, self._p(Lbar, NCOMP), self._p(C, 3),
+                                                         self._p(Mbar, NCOMP), self._p(mbar, 1), _stream(stream)))
         return Mbar, mbar
 
     def l2l_com(self, L, C, stream=None):
-        _lib.check(self.lib.ot_l2l_com(self.handle, _ptr(C), _ptr(L), _stream(stream)))
+        _lib.check(self.lib.ot_l2l_com(self.handle, self._p(C, 3), self._p(L, NCOMP), _stream(stream)))
         return L
 
     def l2l_com_backward(self, Lbar, C, stream=None):
-        _lib.check(self.lib.ot_l2l_com_backward(self.handle, _ptr(C), _ptr(Lbar), _stream(stream)))
+        _lib.check(self.lib.ot_l2l_com_backward(self.handle, self._p(C, 3), self._p(Lbar, NCOMP), _stream(stream)))
         return Lbar
 
     def solve_com(self, rho, stream=None):
@@ -202,23 +251,26 @@ class OTGrid:
             Mbar = self.zeros(self.n, NCOMP, NCELL)
         if mbar is None and want[1]:
             mbar = self.zeros(self.n, NCELL)
-        _lib.check(self.lib.ot_interactions_backward(self.handle, _ptr(Lbar), _ptr(Mbar), _ptr(mbar),
-                                                     _stream(stream)))
+        _lib.check(self.lib.ot_interactions_backward(self.handle, self._p(Lbar, NCOMP), self._p(Mbar, NCOMP),
+                                                     self._p(mbar, 1), _stream(stream)))
         return Mbar, mbar
 
 
 def _l2l(grid, L, stream=None):
-    _lib.check(grid.lib.ot_l2l(grid.handle, _ptr(L), _stream(stream)))
+    _lib.check(grid.lib.ot_l2l(grid.handle, grid._p(L, NCOMP), _stream(stream)))
     return L
 
 
 def _l2l_backward(grid, Lbar, stream=None):
-    _lib.check(grid.lib.ot_l2l_backward(grid.handle, _ptr(Lbar), _stream(stream)))
+    _lib.check(grid.lib.ot_l2l_backward(grid.handle, grid._p(Lbar, NCOMP), _stream(stream)))
     return Lbar
 
 
 def fp64_fma_probe(out, blocks, iters, variant=0, stream=None):
+    """FP64 FMA probe: writes blocks x 256 doubles into ``out``."""
     lib = _lib.load()
+    if out.numel() < int(blocks) * 256:
+        raise ValueError(f"out holds {out.numel()} doubles, the probe writes {int(blocks) * 256}")
     _lib.check(lib.ot_fp64_fma_probe(_ptr(out), int(blocks), int(iters), int(variant), _stream(stream)))
 
 

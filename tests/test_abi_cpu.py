@@ -68,6 +68,13 @@ def test_host_argument_checks_without_device(lib):
     assert lib.ot_set_schedule(None, 0, 4, 0, 1) == _lib.OT_EINVAL
     assert lib.ot_interactions(None, None, None, None, None, None) == _lib.OT_EINVAL
     assert lib.ot_fp64_fma_probe(None, 1, 1, 0, None) == _lib.OT_EINVAL
+    # a pointer that is not a live grid handle is refused before any use
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.ot_grid_destroy(fake) == _lib.OT_EINVAL
+    assert b"not live" in lib.ot_last_error()
+    assert lib.ot_grid_info(fake, ctypes.byref(_lib.GridInfo())) == _lib.OT_EINVAL
+    assert lib.ot_interactions(fake, None, None, None, None, None) == _lib.OT_EINVAL
+    assert lib.ot_multipole_interactions_noalloc(fake, None, None, None, None) == _lib.OT_EINVAL
 
 
 def test_generated_contraction_code_is_current():

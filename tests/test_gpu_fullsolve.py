@@ -124,7 +124,7 @@ def test_full_solve_autograd_central_differences(ot):
         with torch.no_grad():
             Lr = ot.potential_and_gradient(g, dev(r), full=True)
             return float((Lr[probes[:, 0], 0, probes[:, 1]] ** 2).sum())
-    loss0 = float(loss)
+    loss0 = float(loss.detach())
     for n, c in zip(rng.choice(leaf_nodes, 12), rng.integers(0, 512, 12)):
         step = 1e-6 * max(rho0[n, c], 1e-3)
         rp, rm = rho0.copy(), rho0.copy()

@@ -436,6 +436,25 @@ def test_abi_rejects_bad_input(ot):
     assert st == _lib.OT_EINVAL and b"both NULL" in lib.ot_last_error()
     assert lib.ot_interactions(None, None, None, None, None, None) == _lib.OT_EINVAL
     g.check()
+    # a destroyed handle is refused, not used
+    g2 = ot.OTGrid.from_tree(tree)
+    h = ctypes.c_void_p(g2.handle.value)
+    g2.close()
+    assert lib.ot_multipole_interactions(h, ctypes.c_void_p(M.data_ptr()), None, ctypes.c_void_p(L.data_ptr()),
+                                         None, None) == _lib.OT_EINVAL
+    assert b"not live" in lib.ot_last_error()
+    assert lib.ot_grid_destroy(h) == _lib.OT_EINVAL
+    # the binding checks element counts and devices (the library cannot)
+    with pytest.raises(ValueError, match="elements"):
+        g.multipole(torch.zeros(20 * 512 - 1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError, match="elements"):
+        g.interactions(torch.zeros(1, 20, 512, dtype=torch.float64, device="cuda"),
+                       torch.zeros(1, 512, dtype=torch.float64, device="cuda"),
+                       L=torch.zeros(1, 3, 512, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError, match="float64"):
+        g.moments(torch.zeros(1, 512, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError, match="probe writes"):
+        ot.fp64_fma_probe(torch.zeros(100, dtype=torch.float64, device="cuda"), 1, 10)
 
 
 def test_fp64_probe_runs(ot):
@@ -463,3 +482,27 @@ def test_completion_study_results_and_stats(ot, mechanism):
     assert stats["launches"] == (1 if mechanism == 3 else tree.n)
     assert 0 < stats["mean_latency_us"] <= stats["max_latency_us"]
     assert stats["wall_ms"] > 0
+
+
+def test_autotune_cache(ot, tmp_path):
+    """A tuned tile shape is stored under the tree's and device's key and
+    applied without timing by the next grid on the same tree."""
+    tree = synth.uniform_tree(1, 1.0)
+    rho = synth.uniform_random_density(tree, seed=130)
+    cache = str(tmp_path / "tiles.json")
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L, Lc = g.zeros(tree.n, 20, 512), g.zeros(tree.n, 3, 512)
+    first = g.autotune(M, m, L, Lc, cache=cache)
+    assert not first["cached"]
+    g2 = ot.OTGrid.from_tree(tree)
+    second = g2.autotune(M, m, L, Lc, cache=cache)
+    assert second["cached"]
+    info = g2.info()
+    assert (info["warps_per_block"], info["blocks_per_sm"]) == (first["warps_per_block"], first["blocks_per_sm"])
+    L2, _ = g2.interactions(M, m)
+    L1, _ = g.interactions(M, m)
+    torch.cuda.synchronize()
+    assert torch.equal(L1, L2)
+    other = ot.OTGrid.from_tree(synth.uniform_tree(2, 1.0))
+    assert other.config_key() != g.config_key()

@@ -71,7 +71,7 @@ def test_config4_probe_loss_gradient(ot, orc):
         with torch.no_grad():
             Lr = ot.potential_and_gradient(g, dev(r))
             return float((Lr[pn, 0, pc] ** 2).sum())
-    loss0 = float(loss)
+    loss0 = float(loss.detach())
     for (k, c) in pick:
         n = leaf_nodes[k]
         step = 1e-6 * rho_h[n, c]
