@@ -247,18 +247,25 @@ ot_status ot_interactions_backward_com(ot_grid* grid, const double* Lbar, const 
 ot_status ot_l2l_com(ot_grid* grid, const double* C, double* L, void* stream);
 ot_status ot_l2l_com_backward(ot_grid* grid, const double* C, double* Lbar, void* stream);
 
-/* Arithmetic of the point-mass contractions of the forward passes.
+/* Arithmetic of the contractions of the forward passes (the table path;
+ * ot_interactions_com and the adjoints stay FP64).
  * OT_PREC_FP64 (default): FP64 FMAs throughout.
  * OT_PREC_DF64_POINT_MASS: point-mass pairs are contracted in double-float
  *   arithmetic on the FP32 pipe -- every value an unevaluated sum hi + lo of
  *   two FP32 numbers (48-bit significand), products split exactly with FMAs,
- *   sums by two-sum -- and moved into FP64 accumulators every 16 offsets, so
- *   each coefficient stays within ~2e-13 of the sum of |terms| of its FP64
+ *   accumulated by two-sums with renormalization -- and the partial sums move
+ *   into FP64 accumulators before any of them holds more than 64 products, so
+ *   each coefficient stays within ~7e-13 of the sum of |terms| of its FP64
  *   value.  Requires point masses m with |m| in [2^-100, 2^100] or m = 0 and
  *   derivative-table values in the same range (true for cell sizes within
- *   2^-10 .. 2^10 of level 0's).  Multipole pairs and the adjoints stay FP64. */
+ *   2^-10 .. 2^10 of level 0's).
+ * OT_PREC_DF64: the multipole contractions too (the 70-product contraction
+ *   and the angular term, with the reduced moments split into double-float
+ *   pairs once per call), under the same 64-product rule and bound.  The same
+ *   range requirement holds for the reduced moments (mass-scaled, so O(mass)). */
 #define OT_PREC_FP64 0
 #define OT_PREC_DF64_POINT_MASS 1
+#define OT_PREC_DF64 2
 ot_status ot_set_precision(ot_grid* grid, int32_t mode);
 
 /* 1: every adjoint result in a fixed summation order (bit-reproducible);

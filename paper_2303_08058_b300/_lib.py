@@ -15,7 +15,7 @@ OT_OK, OT_EINVAL, OT_ENOMEM, OT_ECUDA, OT_ETIMEOUT, OT_ESTATE, OT_ENOTSUP, OT_ED
 STATUS_NAMES = ["OT_OK", "OT_EINVAL", "OT_ENOMEM", "OT_ECUDA", "OT_ETIMEOUT", "OT_ESTATE", "OT_ENOTSUP",
                 "OT_EDEVICE"]
 OT_SCHED_PERSISTENT, OT_SCHED_PER_SUBGRID = 0, 1
-OT_PREC_FP64, OT_PREC_DF64_POINT_MASS = 0, 1
+OT_PREC_FP64, OT_PREC_DF64_POINT_MASS, OT_PREC_DF64 = 0, 1, 2
 
 # every entry point declared in include/ot.h
 EXPORTS = ["ot_grid_create", "ot_grid_destroy", "ot_grid_info", "ot_moments", "ot_moments_backward",

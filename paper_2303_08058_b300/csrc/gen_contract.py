@@ -293,6 +293,55 @@ def emit():
         w(f"  df_fma(ah[{j}], al[{j}], mh, ml, r[{j}], r[{16 + j}]);\n")
     w("}\n\n")
 
+    # double-float multipole contractions.  The table row is a float2 pair
+    # (hi, lo) per derivative component, read from L1 as each component is
+    # needed; terms are grouped by component so its pair dies after its terms.
+    by_di = {}
+    for (j, k, di) in terms:
+        by_di.setdefault(di, []).append((j, k))
+    w("// double-float, paired: 70 products for two multipole pairs (rs = r+ + r-, rd = r+ - r-)\n")
+    w("__device__ __forceinline__ void ot_multi_fwd_pair_df(float (&ah)[16], float (&al)[16], const float (&rsh)[16],\n"
+      "                                                     const float (&rsl)[16], const float (&rdh)[16],\n"
+      "                                                     const float (&rdl)[16], const float2* __restrict__ row) {\n")
+    for di in sorted(by_di):
+        w(f"  {{\n    const float2 d = __ldg(row + {di});\n")
+        src = "rs" if rank(ROW[di]) % 2 == 0 else "rd"
+        for (j, k) in by_di[di]:
+            w(f"    df_fma(ah[{j}], al[{j}], {src}h[{k}], {src}l[{k}], d.x, d.y);\n")
+        w("  }\n")
+    w("}\n\n")
+    w("// double-float: 70 products for one multipole pair\n")
+    w("__device__ __forceinline__ void ot_multi_fwd_df(float (&ah)[16], float (&al)[16], const float (&rh)[16],\n"
+      "                                                const float (&rl)[16], const float2* __restrict__ row) {\n")
+    for di in sorted(by_di):
+        w(f"  {{\n    const float2 d = __ldg(row + {di});\n")
+        for (j, k) in by_di[di]:
+            w(f"    df_fma(ah[{j}], al[{j}], rh[{k}], rl[{k}], d.x, d.y);\n")
+        w("  }\n")
+    w("}\n\n")
+    # angular term in double-float: c[i] += sum_{K in R3} r[K] d[e_i + K];
+    # t4[q] += mB d[q] (rank-4 components: even, so paired entries use sums)
+    ang = {}
+    for i in range(3):
+        ei = tuple(1 if a == i else 0 for a in range(3))
+        for k in R3:
+            ang.setdefault(ROWIDX[add(ei, IND16[k])], []).append(("c", i, k))
+    for q, e in enumerate(T4):
+        ang.setdefault(ROWIDX[e], []).append(("t", q, None))
+    w("// double-float angular term: 21 + 9 products\n")
+    w("__device__ __forceinline__ void ot_angular_fwd_df(float (&ch)[3], float (&cl)[3], float (&th)[9], float (&tl)[9],\n"
+      "                                                  const float (&rh)[16], const float (&rl)[16],\n"
+      "                                                  const float2* __restrict__ row) {\n")
+    for di in sorted(ang):
+        w(f"  {{\n    const float2 d = __ldg(row + {di});\n")
+        for (kind, i, k) in ang[di]:
+            if kind == "c":
+                w(f"    df_fma(ch[{i}], cl[{i}], rh[{k}], rl[{k}], d.x, d.y);\n")
+            else:
+                w(f"    df_fma(th[{i}], tl[{i}], rh[0], rl[0], d.x, d.y);\n")
+        w("  }\n")
+    w("}\n\n")
+
     # derivatives at an arbitrary separation (centre-of-mass expansion centres)
     w("// derivatives of -1/r (row layout) at R = (x, y, z), the components each\n")
     w("// contraction reads: point masses, multipole sources, multipole sources\n")

@@ -49,6 +49,8 @@ struct FwdParams {
     const double* m;       // [n][512]
     const float2* mf;      // [n][512] masses as double-float (hi, lo), or null for FP64
     const float* Dt32;     // [NOFF][32] hi then lo parts of the 16 point-mass derivatives
+    const float2* Mf;      // [n][16][512] reduced moments as (hi, lo) pairs, or null (FP64 multipole pass)
+    const float2* Dt2;     // [NOFF][DROW] the derivative table as (hi, lo) pairs
     double* Lout;          // [n][20][512]
     double* Lc;            // [n][3][512] or null
     int accumulate;
@@ -157,6 +159,7 @@ cudaError_t launch_fp64_probe(double* out, int blocks, int iters, int variant, c
 cudaError_t launch_scatter_adjoint(const ScatParams& p, bool persistent, int wpb, int grid, cudaStream_t s);
 int scatter_max_blocks_per_sm(int wpb);
 int forward_max_blocks_per_sm(int mode, int wpb);   // mode 6/7: double-float point masses
+cudaError_t launch_split_moments(const double* Mhat, float2* Mf, const int* nodes, int n_list, cudaStream_t s);
 cudaError_t launch_split_masses(const double* m, float2* mf, size_t n, cudaStream_t s);
 int adjoint_max_blocks_per_sm(int mode, int wpb);
 

@@ -32,16 +32,21 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// (ah, al) += (xh, xl) * (yh, yl): the high product is split exactly with an
-// FMA, the cross terms go to the low part, xl * yl is dropped
+// (ah, al) += (xh, xl) * (yh, yl), accurate double-word accumulation: the
+// high product is split exactly with an FMA, the cross terms and the split's
+// error go to the low part (xl * yl is dropped), the high parts are summed by
+// two-sum, and (ah, al) is renormalized by a second two-sum, so that
+// |al| <= ulp(ah) / 2 after every call.  With u = 2^-24, k calls on one
+// accumulator err by at most about (3k + 6) u^2 times the sum of |products|
+// (the low-part roundings are u times quantities of order u * |partial sum|).
 __device__ __forceinline__ void df_fma(float& ah, float& al, float xh, float xl, float yh, float yl) {
     const float ph = __fmul_rn(xh, yh);
     const float pe = __fmaf_rn(xh, yh, -ph);
     const float pl = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, pe));
     float sh, se;
     two_sum(ah, ph, sh, se);
-    al = __fadd_rn(al, __fadd_rn(se, pl));
-    ah = sh;
+    const float t = __fadd_rn(__fadd_rn(al, pl), se);
+    two_sum(sh, t, ah, al);
 }
 
 // (sh, sl) = (ah, al) + (bh, bl), renormalized
@@ -283,25 +288,111 @@ __device__ __forceinline__ void refined_near_scatter(const P& p, int ox, int oy,
 // gather from a coarse leaf's virtual children
 __device__ __forceinline__ double vchild_scale(int j) { return j == 0 ? 0.25 : j < 4 ? 0.5 : j < 9 ? 1.0 : 2.0; }
 
-// PAIRED: each entry o stands for the offsets o and -o (sources at t + o and
-// t - o share the table row of o, with odd-order derivatives negated for -o).
-// (ah, al) double-float partial sums of the point-mass contributions, moved
-// into the FP64 accumulators every 16 entries (bounds their rounding error)
-__device__ __forceinline__ void df_flush(double (&a)[16], float (&ah)[16], float (&al)[16]) {
+// Double-float accumulators of one lane: the 16 coefficients and, when the
+// multipole contractions run in double-float too, the angular term's source
+// and target parts.  They move into the FP64 accumulators by groups -- the
+// coefficients of orders 0, 1, 2, 3, the angular source part, the angular
+// target part -- each as soon as its next entry would take it past DF_MAX
+// products since its last move (the error bound of df_fma then stays below
+// (3 * 64 + 6) 2^-48 ~ 7e-13 of the sum of |products|).  Per entry a
+// multipole source adds 16, 9, 4, 1 products to the four coefficient groups
+// (and 7 and 1 to the angular ones), a point mass 1 to each coefficient group.
+constexpr int DF_MAX = 64;
+
+struct DFAcc {
+    float ah[16], al[16];
+    float ch[3], cl[3];
+    float th[9], tl[9];
+    int cnt[6];
+};
+
+__device__ __forceinline__ void df_zero(DFAcc& f) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        a[j] += static_cast<double>(ah[j]) + static_cast<double>(al[j]);
-        ah[j] = 0.0f;
-        al[j] = 0.0f;
+        f.ah[j] = 0.0f;
+        f.al[j] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        f.ch[i] = 0.0f;
+        f.cl[i] = 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        f.th[q] = 0.0f;
+        f.tl[q] = 0.0f;
+    }
+#pragma unroll
+    for (int g = 0; g < 6; ++g) f.cnt[g] = 0;
+}
+
+template <int LO, int HI>
+__device__ __forceinline__ void df_move(double* a, float* h, float* l) {
+#pragma unroll
+    for (int j = LO; j < HI; ++j) {
+        a[j] += static_cast<double>(h[j]) + static_cast<double>(l[j]);
+        h[j] = 0.0f;
+        l[j] = 0.0f;
     }
 }
 
-template <int MODE, bool PAIRED, bool EMU, bool NEAR = false>
+// make room for an entry adding inc[g] products to group g
+__device__ __forceinline__ void df_reserve(double (&a)[16], double (&c)[3], double (&t4)[9], DFAcc& f, int i0, int i1,
+                                           int i2, int i3, int i4, int i5) {
+    if (f.cnt[0] + i0 > DF_MAX) { df_move<0, 1>(a, f.ah, f.al); f.cnt[0] = 0; }
+    if (f.cnt[1] + i1 > DF_MAX) { df_move<1, 4>(a, f.ah, f.al); f.cnt[1] = 0; }
+    if (f.cnt[2] + i2 > DF_MAX) { df_move<4, 9>(a, f.ah, f.al); f.cnt[2] = 0; }
+    if (f.cnt[3] + i3 > DF_MAX) { df_move<9, 16>(a, f.ah, f.al); f.cnt[3] = 0; }
+    if (f.cnt[4] + i4 > DF_MAX) { df_move<0, 3>(c, f.ch, f.cl); f.cnt[4] = 0; }
+    if (f.cnt[5] + i5 > DF_MAX) { df_move<0, 9>(t4, f.th, f.tl); f.cnt[5] = 0; }
+    f.cnt[0] += i0;
+    f.cnt[1] += i1;
+    f.cnt[2] += i2;
+    f.cnt[3] += i3;
+    f.cnt[4] += i4;
+    f.cnt[5] += i5;
+}
+
+template <bool ANG>
+__device__ __forceinline__ void df_flush_all(double (&a)[16], double (&c)[3], double (&t4)[9], DFAcc& f) {
+    df_move<0, 16>(a, f.ah, f.al);
+    if (ANG) {
+        df_move<0, 3>(c, f.ch, f.cl);
+        df_move<0, 9>(t4, f.th, f.tl);
+    }
+#pragma unroll
+    for (int g = 0; g < 6; ++g) f.cnt[g] = 0;
+}
+
+// reduced moments of a multipole source as double-float pairs
+__device__ __forceinline__ void source_moments_df(const FwdParams& p, int2 e, bool multi, int sx, int sy, int sz,
+                                                  float (&rh)[16], float (&rl)[16]) {
+    if (multi) {
+        const float2* src = p.Mf + static_cast<size_t>(e.x) * NRED * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float2 v = __ldg(src + q * NCELL);
+            rh[q] = v.x;
+            rl[q] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            rh[q] = 0.0f;
+            rl[q] = 0.0f;
+        }
+    }
+}
+
+// PAIRED: each entry o stands for the offsets o and -o (sources at t + o and
+// t - o share the table row of o, with odd-order derivatives negated for -o).
+// EMU bits: 1 point-mass contractions in double-float (the partial sums in
+// DFAcc), 2 multipole ones too
+template <int MODE, bool PAIRED, int EMU, bool NEAR = false>
 __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
                                              int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                              const FwdParams& p, double (&a)[16], double (&c)[3],
-                                             double (&t4)[9], float (&ah)[16], float (&al)[16], int& nacc,
-                                             int item) {
+                                             double (&t4)[9], DFAcc& f, int item) {
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
@@ -319,7 +410,8 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
         if (MODE & 2) {
             const bool mono = kp >= K_LEAF || km >= K_LEAF;
             if (__any_sync(0xffffffffu, mono)) {
-                if (EMU) {
+                if (EMU & 1) {
+                    df_reserve(a, c, t4, f, 1, 1, 1, 1, 0, 0);
                     float mh, ml;
                     source_mass_df(p, ep, kp, px, py, pz, mh, ml);
                     float r[32];
@@ -329,13 +421,9 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
                         source_mass_df(p, em, km, mx, my, mz, nh, nl);
                         df_add(mh, ml, nh, nl, sh, sl);
                         df_add(mh, ml, -nh, -nl, dh, dl);
-                        ot_mono_fwd_pair_df(ah, al, sh, sl, dh, dl, r);
+                        ot_mono_fwd_pair_df(f.ah, f.al, sh, sl, dh, dl, r);
                     } else {
-                        ot_mono_fwd_df(ah, al, mh, ml, r);
-                    }
-                    if (++nacc == 16) {
-                        df_flush(a, ah, al);
-                        nacc = 0;
+                        ot_mono_fwd_df(f.ah, f.al, mh, ml, r);
                     }
                 } else {
                     const double mp = source_mass(p, ep, kp, px, py, pz);
@@ -356,7 +444,34 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
             if (__any_sync(0xffffffffu, rp || rm))
                 refined_near_fwd(p, ox, oy, oz, ep, rp, px, py, pz, em, rm, mx, my, mz, a, item);
         }
-        if ((MODE & 1) && !NEAR) {
+        if ((MODE & 1) && !NEAR && (EMU & 2)) {
+            const bool multi = kp == K_MULTI || km == K_MULTI;
+            if (__any_sync(0xffffffffu, multi)) {
+                df_reserve(a, c, t4, f, 16, 9, 4, 1, angular ? 7 : 0, angular ? 1 : 0);
+                float rh[16], rl[16];
+                source_moments_df(p, ep, kp == K_MULTI, px, py, pz, rh, rl);
+                const float2* drow = p.Dt2 + static_cast<size_t>(row) * DROW;
+                if (PAIRED) {
+                    float mh[16], ml[16];
+                    source_moments_df(p, em, km == K_MULTI, mx, my, mz, mh, ml);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        float sh, sl, dh, dl;
+                        df_add(rh[q], rl[q], mh[q], ml[q], sh, sl);       // sum
+                        df_add(rh[q], rl[q], -mh[q], -ml[q], dh, dl);     // difference
+                        rh[q] = sh;
+                        rl[q] = sl;
+                        mh[q] = dh;
+                        ml[q] = dl;
+                    }
+                    ot_multi_fwd_pair_df(f.ah, f.al, rh, rl, mh, ml, drow);
+                } else {
+                    ot_multi_fwd_df(f.ah, f.al, rh, rl, drow);
+                }
+                if (angular) ot_angular_fwd_df(f.ch, f.cl, f.th, f.tl, rh, rl, drow);
+            }
+        }
+        if ((MODE & 1) && !NEAR && !(EMU & 2)) {
             const bool multi = kp == K_MULTI || km == K_MULTI;
             if (__any_sync(0xffffffffu, multi)) {
                 double r[16];
@@ -440,7 +555,7 @@ __device__ __forceinline__ void store_forward(const FwdParams& p, int node, int 
     }
 }
 
-template <int MODE, bool EMU>
+template <int MODE, int EMU>
 __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
     const int lane = threadIdx.x & 31;
@@ -464,32 +579,27 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
         int tx, ty, tz;
         lane_cell(lane, par, half, tx, ty, tz);
         double a[16], c[3], t4[9];
-        float ah[16], al[16];
-        int nacc = 0;
+        DFAcc f;
+        df_zero(f);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            a[q] = 0.0;
-            ah[q] = 0.0f;
-            al[q] = 0.0f;
-        }
+        for (int q = 0; q < 16; ++q) a[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 3; ++q) c[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) t4[q] = 0.0;
         if (level == 0) {
             walk_forward<MODE, true, EMU>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, tx, ty, tz, s_nb[warp], p,
-                                          a, c, t4, ah, al, nacc, it);
+                                          a, c, t4, f, it);
         } else {
             const int* lf = p.L.lists + par * p.L.far_len;
-            walk_forward<MODE, true, EMU>(lf, p.L.far_pairs, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, ah, al,
-                                          nacc, it);
+            walk_forward<MODE, true, EMU>(lf, p.L.far_pairs, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
             walk_forward<MODE, false, EMU>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, tx, ty, tz,
-                                           s_nb[warp], p, a, c, t4, ah, al, nacc, it);
+                                           s_nb[warp], p, a, c, t4, f, it);
         }
         if (leafT)
             walk_forward<MODE, true, EMU, true>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p,
-                                          a, c, t4, ah, al, nacc, it);
-        if (EMU) df_flush(a, ah, al);
+                                          a, c, t4, f, it);
+        if (EMU) df_flush_all<(EMU & 2) != 0>(a, c, t4, f);
         store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
         __syncwarp();
         if (!persistent) break;
@@ -1812,18 +1922,37 @@ cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wp
     if (p.n_items == 0) return cudaSuccess;
     const dim3 block(32 * wpb);
     const int per = persistent ? 1 : 0;
-    const bool emu = p.mf != nullptr;
-    switch (mode) {
-        case 1: forward_kernel<1, false><<<grid, block, 0, s>>>(p, per); break;
-        case 2:
-            if (emu) forward_kernel<2, true><<<grid, block, 0, s>>>(p, per);
-            else forward_kernel<2, false><<<grid, block, 0, s>>>(p, per);
-            break;
-        default:
-            if (emu) forward_kernel<3, true><<<grid, block, 0, s>>>(p, per);
-            else forward_kernel<3, false><<<grid, block, 0, s>>>(p, per);
-            break;
+    // double-float point masses when split masses are given, multipole
+    // contractions too when split moments are given
+    const int emu = (p.mf != nullptr && (mode & 2) ? 1 : 0) | (p.Mf != nullptr && (mode & 1) ? 2 : 0);
+    switch (mode * 4 + emu) {
+        case 4: forward_kernel<1, 0><<<grid, block, 0, s>>>(p, per); break;
+        case 6: forward_kernel<1, 2><<<grid, block, 0, s>>>(p, per); break;
+        case 8: forward_kernel<2, 0><<<grid, block, 0, s>>>(p, per); break;
+        case 9: forward_kernel<2, 1><<<grid, block, 0, s>>>(p, per); break;
+        case 12: forward_kernel<3, 0><<<grid, block, 0, s>>>(p, per); break;
+        case 13: forward_kernel<3, 1><<<grid, block, 0, s>>>(p, per); break;
+        case 15: forward_kernel<3, 3><<<grid, block, 0, s>>>(p, per); break;
+        default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// reduced moments of the listed nodes as double-float pairs (hi, lo)
+__global__ void split_moments_kernel(const double* __restrict__ Mhat, float2* __restrict__ Mf,
+                                     const int* __restrict__ nodes, int n_list) {
+    const size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= static_cast<size_t>(n_list) * NRED * NCELL) return;
+    const size_t off = static_cast<size_t>(nodes[t / (NRED * NCELL)]) * NRED * NCELL + t % (NRED * NCELL);
+    const double v = Mhat[off];
+    const float hi = __double2float_rn(v);
+    Mf[off] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+}
+
+cudaError_t launch_split_moments(const double* Mhat, float2* Mf, const int* nodes, int n_list, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    const long long n = 1LL * n_list * NRED * NCELL;
+    split_moments_kernel<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(Mhat, Mf, nodes, n_list);
     return cudaGetLastError();
 }
 
@@ -1867,12 +1996,17 @@ int scatter_max_blocks_per_sm(int wpb) {
     return n;
 }
 
+// mode 1-3 FP64; 6, 7 double-float point masses (modes 2, 3); 5, 8 double-float
+// multipole contractions too (modes 1, 3)
 int forward_max_blocks_per_sm(int mode, int wpb) {
     int n = 0;
-    const void* f = (mode == 1) ? (const void*)forward_kernel<1, false>
-                  : (mode == 2) ? (const void*)forward_kernel<2, false>
-                  : (mode == 3) ? (const void*)forward_kernel<3, false>
-                  : (mode == 6) ? (const void*)forward_kernel<2, true> : (const void*)forward_kernel<3, true>;
+    const void* f = (mode == 1)   ? (const void*)forward_kernel<1, 0>
+                    : (mode == 2) ? (const void*)forward_kernel<2, 0>
+                    : (mode == 3) ? (const void*)forward_kernel<3, 0>
+                    : (mode == 5) ? (const void*)forward_kernel<1, 2>
+                    : (mode == 6) ? (const void*)forward_kernel<2, 1>
+                    : (mode == 7) ? (const void*)forward_kernel<3, 1>
+                                  : (const void*)forward_kernel<3, 3>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
     return n;
 }

@@ -173,7 +173,10 @@ struct ot_grid {
     double* d_Dt = nullptr;
     float* d_Dt32 = nullptr;            // double-float split of the point-mass derivatives
     float2* d_mf = nullptr;             // masses as double-float pairs (scratch)
-    int precision = 0;                  // 0: FP64; 1: double-float point-mass contractions
+    int precision = 0;                  // OT_PREC_*: 0 FP64; 1 double-float point masses; 2 both passes
+    float2* d_Mf = nullptr;             // reduced moments as double-float pairs (scratch)
+    float2* d_Dt2 = nullptr;            // the derivative table as double-float pairs
+    int maxb_emu2[4][9] = {};           // forward with double-float multipole contractions, modes 1 and 3
     int* d_lists = nullptr;
     double* d_hinv = nullptr;
     int* d_items_fwd[4] = {nullptr, nullptr, nullptr, nullptr};     // LPT order, by mode
@@ -810,6 +813,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     for (int w = 2; w <= 8; w *= 2) {
         g->maxb_emu[2][w] = forward_max_blocks_per_sm(6, w);
         g->maxb_emu[3][w] = forward_max_blocks_per_sm(7, w);
+        g->maxb_emu2[1][w] = forward_max_blocks_per_sm(5, w);
+        g->maxb_emu2[3][w] = forward_max_blocks_per_sm(8, w);
         g->maxb_scat[w] = scatter_max_blocks_per_sm(w);
         g->maxb_adj[4 - 4][w] = adjoint_max_blocks_per_sm(4, w);   // slot 0: fused, point masses only
         g->maxb_fast5[w] = adjoint_max_blocks_per_sm(5, w);
@@ -849,6 +854,12 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 Dt32[static_cast<size_t>(r) * 32 + 16 + j] = static_cast<float>(v - static_cast<double>(hi));
             }
         UP(g->d_Dt32, Dt32);
+        std::vector<float2> Dt2(static_cast<size_t>(NOFF) * DROW);
+        for (size_t i = 0; i < Dt2.size(); ++i) {
+            const float hi = static_cast<float>(Dt[i]);
+            Dt2[i] = make_float2(hi, static_cast<float>(Dt[i] - static_cast<double>(hi)));
+        }
+        UP(g->d_Dt2, Dt2);
     }
     UP(g->d_lists, g->lists);
     std::vector<double> hv(g->hinv, g->hinv + MAXLEV);
@@ -887,6 +898,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_mf, static_cast<size_t>(n) * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Mf, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_counters, 4)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_status, 2)) != OT_OK) return st;
     OT_CUDA(cudaMemsetAsync(g->d_status, 0, 2 * sizeof(int), s));
@@ -951,11 +963,17 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
     if (!accumulate) OT_CUDA(cudaMemsetAsync(L, 0, nL * sizeof(double), s));
     if ((mode & 1) && Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
     FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
-    const bool emu = g->precision == 1 && (mode & 2);
+    const bool emu = g->precision >= 1 && (mode & 2);       // double-float point masses
+    const bool emu2 = g->precision == 2 && (mode & 1);      // double-float multipole contractions
     if (emu) {
         OT_CUDA(launch_split_masses(m, g->d_mf, static_cast<size_t>(g->n) * NCELL, s));
         p.mf = g->d_mf;
         p.Dt32 = g->d_Dt32;
+    }
+    if (emu2) {
+        OT_CUDA(launch_split_moments(g->d_Mhat, g->d_Mf, g->d_nonleaf, g->n_nonleaf, s));
+        p.Mf = g->d_Mf;
+        p.Dt2 = g->d_Dt2;
     }
     // zeroed above, so the kernel always accumulates
     if (g->schedule == OT_SCHED_PER_SUBGRID) {
@@ -971,7 +989,8 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         p.items = g->d_items_fwd[mode];
         p.n_items = g->n_items_fwd[mode];
         OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
-        const int maxb = emu ? g->maxb_emu[mode][g->wpb] : g->maxb_fwd[mode][g->wpb];
+        const int maxb = emu2 ? g->maxb_emu2[mode][g->wpb]
+                         : emu ? g->maxb_emu[mode][g->wpb] : g->maxb_fwd[mode][g->wpb];
         OT_CUDA(launch_forward(p, mode, true, g->wpb, grid_blocks(g, maxb), s));
     }
     return OT_OK;
@@ -1555,7 +1574,7 @@ ot_status ot_set_precision(ot_grid* g, int32_t mode) {
     GUARD_BEGIN
     if (!g) return fail(OT_EINVAL, "grid is NULL");
     if (!grid_live(g)) return fail(OT_EINVAL, "grid handle is not live (destroyed or never created)");
-    if (mode != OT_PREC_FP64 && mode != OT_PREC_DF64_POINT_MASS)
+    if (mode != OT_PREC_FP64 && mode != OT_PREC_DF64_POINT_MASS && mode != OT_PREC_DF64)
         return fail(OT_EINVAL, "unknown precision mode %d", mode);
     g->precision = mode;
     return OT_OK;
@@ -1645,7 +1664,7 @@ ot_status ot_multipole_interactions(ot_grid* g, const double* M, const double* c
     CHECK_PTR(L, "L");
     if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{1, M, nullptr, L, Lc, g->wpb, g->bps};
+    GraphKey key{1 + 16 * g->precision, M, nullptr, L, Lc, g->wpb, g->bps};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward(g, 1, M, nullptr, L, Lc, 0, st); });
     GUARD_END
 }
@@ -1720,7 +1739,7 @@ ot_status ot_interactions_com(ot_grid* g, const double* M, const double* m, cons
     if (Lc && !aligned16(Lc)) return fail(OT_EINVAL, "Lc is not 16-byte aligned");
     const int mode = (M ? 1 : 0) | (m ? 2 : 0);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{32 + mode, M, m, L, Lc, g->wpb, g->bps, C};
+    GraphKey key{100 + mode, M, m, L, Lc, g->wpb, g->bps, C};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_forward_com(g, mode, M, m, C, L, Lc, st); });
     GUARD_END
 }
@@ -1735,7 +1754,7 @@ ot_status ot_interactions_backward_com(ot_grid* g, const double* Lbar, const dou
     if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
     if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{40 + 8 * g->deterministic, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps, C};
+    GraphKey key{110 + g->deterministic, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps, C};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_backward_com(g, Lbar, C, Mbar, mbar, st); });
     GUARD_END
 }

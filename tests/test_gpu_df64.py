@@ -1,5 +1,7 @@
-"""Double-float point-mass contractions (OT_PREC_DF64_POINT_MASS) against the
-oracle: the same 1e-12 bound on each coefficient as the FP64 path."""
+"""Double-float contractions against the oracle: point masses only
+(OT_PREC_DF64_POINT_MASS) and the multipole contractions with the angular
+term too (OT_PREC_DF64), under the same 1e-12 bound on each coefficient as
+the FP64 path."""
 import numpy as np
 import pytest
 import torch
@@ -41,15 +43,23 @@ def _small_adaptive():
     return synth.adaptive_tree(refine, 1, 2, 16.0)
 
 
+PRECS = ["point_mass", "both"]
+
+
+def _prec(ot, name):
+    return ot.OT_PREC_DF64_POINT_MASS if name == "point_mass" else ot.OT_PREC_DF64
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("which", ["leaf_level", "root_leaf", "adaptive", "uniform_tree"])
-def test_df64_all_cells(ot, orc, which):
+def test_df64_all_cells(ot, orc, which, prec):
     tree = {"leaf_level": lambda: synth.uniform_level(1, 1.0),
             "root_leaf": lambda: synth.single_subgrid(0, 1.0, leaf=True),
             "adaptive": _small_adaptive,
             "uniform_tree": lambda: synth.uniform_tree(1, 1.0)}[which]()
     rho = synth.uniform_random_density(tree, seed=81)
     g = ot.OTGrid.from_tree(tree)
-    g.set_precision(ot.OT_PREC_DF64_POINT_MASS)
+    g.set_precision(_prec(ot, prec))
     Mh = orc.moments(tree, rho)            # oracle inputs never come from the GPU
     mh = np.ascontiguousarray(Mh[:, 0, :])
     L, Lc = g.interactions(dev(Mh), dev(mh))
@@ -63,8 +73,9 @@ def test_df64_all_cells(ot, orc, which):
     assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], r1["Sc"], what="Lc", block_axis=1)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("cfg", ["config2", "config5"])
-def test_df64_full_size_sampled(ot, orc, cfg):
+def test_df64_full_size_sampled(ot, orc, cfg, prec):
     tree, rho = synth.config2() if cfg == "config2" else synth.config5_step(3)
     g = ot.OTGrid.from_tree(tree)
     Mh = orc.moments(tree, rho)
@@ -72,7 +83,7 @@ def test_df64_full_size_sampled(ot, orc, cfg):
     M, m = dev(Mh), dev(mh)
     L64, _ = g.interactions(M, m, want_lc=False)
     L64 = host(L64)
-    g.set_precision(ot.OT_PREC_DF64_POINT_MASS)
+    g.set_precision(_prec(ot, prec))
     Ldf, _ = g.interactions(M, m, want_lc=False)
     torch.cuda.synchronize()
     Ldf = host(Ldf)
@@ -84,3 +95,39 @@ def test_df64_full_size_sampled(ot, orc, cfg):
     # coefficient-order block magnitude of the FP64 result
     scale = np.max(np.abs(L64), axis=(0, 2), keepdims=True)
     assert np.max(np.abs(Ldf - L64) / scale) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [140, 141])
+def test_df64_random_moments_every_term(ot, orc, seed):
+    """Random moments of every order through the double-float multipole
+    contraction and angular term (single sub-grid: root, far pairs, paired and
+    single entries)."""
+    tree = synth.single_subgrid(1, 0.5)
+    M = synth.random_moments(tree, seed=seed)
+    g = ot.OTGrid.from_tree(tree)
+    g.set_precision(ot.OT_PREC_DF64)
+    L, Lc = g.multipole(dev(M))
+    torch.cuda.synchronize()
+    g.check()
+    r = orc.run_pass_grid(tree, "multipole", M=M)
+    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
+    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
+
+
+def test_df64_multipole_pass_differs_from_fp64_by_rounding_only(ot):
+    """The double-float mode really runs a different arithmetic (results not
+    bitwise equal to FP64) yet stays within the bound of the FP64 result."""
+    tree, rho = synth.config2()
+    g = ot.OTGrid.from_tree(tree)
+    M, m = g.moments(dev(rho))
+    L64, Lc64 = g.interactions(M, m)
+    L64, Lc64 = host(L64), host(Lc64)
+    g.set_precision(ot.OT_PREC_DF64)
+    Ldf, Lcdf = g.interactions(M, m)
+    torch.cuda.synchronize()
+    Ldf, Lcdf = host(Ldf), host(Lcdf)
+    assert not np.array_equal(Ldf, L64)
+    scale = np.max(np.abs(L64), axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(Ldf - L64) / scale) < 1e-12
+    scale_c = np.max(np.abs(Lc64), axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(Lcdf - Lc64) / scale_c) < 1e-11
