@@ -59,3 +59,40 @@ def sample_targets(tree, count, seed, levels=None):
     pick = rng.choice(nodes, size=count, replace=True)
     cells = rng.integers(0, 512, size=count)
     return np.stack([pick, cells], axis=1).astype(np.int32)
+
+
+def oracle_full_solve_at(orc, tree, M, m, cells):
+    """The oracle's full multilevel solve at the given leaf cells only: each
+    cell's own passes plus its ancestors' passes, shifted down level by level
+    (the local-expansion shift between geometric cell centres); S follows the
+    same chain with |d|.  Returns (L, S) [k, 20]."""
+    idx = tree.index()
+    chains, need = [], {}
+    for node, cell in cells:
+        lv = int(tree.level[node])
+        g = 8 * tree.coord[node] + np.array([cell % 8, (cell // 8) % 8, cell // 64])
+        chain = []
+        for l in range(lv + 1):
+            gl = g >> (lv - l)
+            nd = idx[(l, *(gl // 8))]
+            cc = int(gl[0] % 8 + 8 * (gl[1] % 8) + 64 * (gl[2] % 8))
+            chain.append((nd, cc, gl, l))
+            need[(nd, cc)] = None
+        chains.append(chain)
+    tg = np.array(list(need), dtype=np.int32)
+    r1 = orc.run_pass(tree, "multipole", M=M, targets=tg)
+    r2 = orc.run_pass(tree, "monopole", m=m, targets=tg)
+    Lp = {k: r1["L"][i] + r2["L"][i] for i, k in enumerate(need)}
+    Sp = {k: r1["S"][i] + r2["S"][i] for i, k in enumerate(need)}
+    L, S = [], []
+    for chain in chains:
+        nd, cc, gl, l = chain[0]
+        acc, sacc = Lp[(nd, cc)].copy(), Sp[(nd, cc)].copy()
+        for (nd, cc, gl, l), (_, _, gp, lp) in zip(chain[1:], chain[:-1]):
+            h, hp = tree.h0 / 2 ** l, tree.h0 / 2 ** lp
+            d = (gl + 0.5) * h - (gp + 0.5) * hp
+            acc = Lp[(nd, cc)] + orc.l2l(acc, d)
+            sacc = Sp[(nd, cc)] + orc.l2l(sacc, np.abs(d))
+        L.append(acc)
+        S.append(sacc)
+    return np.array(L), np.array(S)

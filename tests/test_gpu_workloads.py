@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import synth
-from helpers import assert_parity, oracle_threads, sample_targets
+from helpers import assert_parity, oracle_full_solve_at, oracle_threads, sample_targets
 
 pytestmark = pytest.mark.gpu
 
@@ -164,3 +164,46 @@ def test_mirror_symmetry_full_size(ot, axis):
     want_c = sc * mirror(host(Lc))
     scale_c = np.max(np.abs(host(Lc)), axis=(0, 2), keepdims=True)
     assert np.max(np.abs(host(Lcm) - want_c) / scale_c) < 1e-12
+
+
+def test_config4_full_solve_probe_loss_gradient(ot, orc):
+    """The differentiation workload on the full multilevel potential: loss =
+    sum over the 1000 probe cells of Phi^2, Phi = L0 after moments, both
+    passes and the down-pass; the gradient for all leaf densities through the
+    adjoint chain (down-pass, passes, moments transposed).  Phi at the probes
+    against the oracle's full solve there; the gradient against central
+    differences."""
+    tree, rho_h = synth.config2()
+    leaf_nodes = np.nonzero(tree.level == 3)[0]
+    probes = synth.config4_probes()
+    pn, pc = leaf_nodes[probes // 512], probes % 512
+    g = ot.OTGrid.from_tree(tree)
+    rho = dev(rho_h).requires_grad_(True)
+    L = ot.potential_and_gradient(g, rho, full=True)
+    loss = (L[pn, 0, pc] ** 2).sum()
+    loss.backward()
+    grad = host(rho.grad)
+    g.check()
+
+    Mo = orc.moments(tree, rho_h)
+    Lo, So = oracle_full_solve_at(orc, tree, Mo, np.ascontiguousarray(Mo[:, 0, :]), list(zip(pn, pc)))
+    assert_parity(host(L)[pn, :, pc], Lo, So, what="full-solve L at the probes", block_axis=1)
+
+    rng = np.random.default_rng(6)
+    inside = np.argwhere(rho_h[leaf_nodes] > 1e-3)
+    pick = inside[rng.choice(len(inside), 48, replace=False)]
+
+    def f(r):
+        with torch.no_grad():
+            Lr = ot.potential_and_gradient(g, dev(r), full=True)
+            return float((Lr[pn, 0, pc] ** 2).sum())
+    loss0 = float(loss.detach())
+    for (k, c) in pick:
+        n = leaf_nodes[k]
+        step = 1e-6 * rho_h[n, c]
+        rp, rm = rho_h.copy(), rho_h.copy()
+        rp[n, c] += step
+        rm[n, c] -= step
+        fd = (f(rp) - f(rm)) / (2 * step)
+        noise = np.finfo(np.float64).eps * abs(loss0) / step
+        assert abs(grad[n, c] - fd) <= 1e-4 * abs(fd) + noise, (n, c, grad[n, c], fd, noise)

@@ -693,3 +693,19 @@ def test_mirror_symmetry(orc):
     want = sign * mirror(L)
     scale = np.max(np.abs(L), axis=(0, 2), keepdims=True)
     assert np.max(np.abs(Lm - want) / scale) < 1e-13
+
+
+def test_sampled_full_solve_helper_matches_whole_grid(orc):
+    """The tests' per-cell full solve (own passes plus the ancestors' passes
+    shifted down) reproduces the oracle's whole-grid full solve."""
+    from helpers import oracle_full_solve_at
+    tree = synth.uniform_tree(1, 1.0)
+    rng = np.random.default_rng(28)
+    rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    L, S = orc.full_solve(tree, rho, with_s=True)
+    M = orc.moments(tree, rho)
+    cells = [(int(i), int(c)) for i in np.nonzero(tree.is_leaf)[0][:3] for c in (0, 77, 511)]
+    Lc, Sc = oracle_full_solve_at(orc, tree, M, np.ascontiguousarray(M[:, 0, :]), cells)
+    for k, (i, c) in enumerate(cells):
+        np.testing.assert_allclose(Lc[k], L[i, :, c], rtol=0, atol=1e-13 * np.max(S[i, :, c]))
+        np.testing.assert_allclose(Sc[k], S[i, :, c], rtol=1e-12)
