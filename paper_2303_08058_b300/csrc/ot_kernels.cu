@@ -1,6 +1,9 @@
-// FP64 CUDA kernels for sm_103a: the stencil walk of the multipole and
-// monopole interaction passes, its transposed (adjoint) walk, cell moments
-// with their M2M shift, and the FP64 FMA probe.
+// CUDA kernels for sm_103a: the stencil walk of the multipole and monopole
+// interaction passes (with the coarse-fine boundary rules on both sides), its
+// transposed (adjoint) walk, cell moments with their M2M shift, the L2L
+// down-pass and its adjoint, the same passes about explicit (centre-of-mass)
+// expansion centres, double-float variants of the forward contractions, and
+// the FP64 FMA probe.
 //
 // Design (B300): the interaction passes are bound by the FP64 FMA pipe, which
 // on this part runs at a small fraction of the FP32 rate; memory traffic per
@@ -610,10 +613,6 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
 // adjoint (transposed) stencil walk: a gather over source cells
 // ---------------------------------------------------------------------------
 
-// Source B of parity p gathers from targets A = B + o' for o' in the forward
-// list of parity p (far pairs are symmetric under o -> -o with the parities
-// swapped), with the table row of the forward offset o = -o'.  A paired
-// entry o' also gathers from A = B - o' (row of o', odd orders negated).
 // lb of one adjoint target: a real cell's reduced L-bar, or for a virtual
 // child of a coarse leaf (depth 1; the coarse leaf refined as a target) the
 // covering cell's, times 2^(n+1)/8 (the mean over the children, in the
@@ -644,6 +643,12 @@ __device__ __forceinline__ bool virtual_child_target(int2 e, bool virt_t) {
     return virt_t && (e.y & 3) == K_VIRT && ((static_cast<unsigned>(e.y) >> 2) & 7u) == 1u;
 }
 
+// Source B of parity p gathers from targets A = B + o' for o' in the forward
+// list of parity p (far pairs are symmetric under o -> -o with the parities
+// swapped), with the table row of the forward offset o = -o'.  A paired
+// entry o' also gathers from A = B - o' (row of o', odd orders negated).
+// virt_t: a real leaf source also gathers from depth-1 virtual children of
+// coarse leaves (the transpose of the coarse-target refinement).
 template <bool MULTI, bool PAIRED>
 __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int len, bool near_seg, bool virt_t,
                                              int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
