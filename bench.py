@@ -367,15 +367,15 @@ def run_ours(args, rank, world):
     Lbar_pin = torch.as_tensor(Lbar_h).pin_memory()
     L_out = torch.empty((tree.n, 20, 512), dtype=torch.float64).pin_memory()
     rb_out = torch.empty((tree.n, 512), dtype=torch.float64).pin_memory()
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    # one step through OTGrid.step_host: the copies of L-bar (in) and L (out)
+    # overlap the forward and the adjoint on a side stream
+    work = {}
+    g.step_host(rho_pin, Lbar_pin, L_out, rb_out, work)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
     for a, b in e2e_ev:
         flush.zero_()
         a.record(stream)
-        rho.copy_(rho_pin, non_blocking=True)
-        Lbar.copy_(Lbar_pin, non_blocking=True)
-        step()
-        L_out.copy_(L, non_blocking=True)
-        rb_out.copy_(rb, non_blocking=True)
+        g.step_host(rho_pin, Lbar_pin, L_out, rb_out, work)
         b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = statistics.median(a.elapsed_time(b) for a, b in e2e_ev)

@@ -246,6 +246,53 @@ class OTGrid:
         self.l2l(L, stream=stream)
         return L, Lc
 
+    def step_host(self, rho_h, Lbar_h, L_h, rhobar_h, work=None, stream=None):
+        """One forward + adjoint step between pinned host buffers: rho_h [n, 512]
+        and Lbar_h [n, 20, 512] in; L_h [n, 20, 512] (both passes) and rhobar_h
+        [n, 512] (the density adjoint of Lbar through both passes and the
+        moments) out; the angular term is computed (work["Lc"]) but stays on
+        the device.  The large copies run on a side stream, overlapped with
+        the kernels: Lbar uploads during the moments and the forward, L
+        downloads during the adjoint.  ``work`` (a dict this method fills on
+        first use) keeps the device buffers between calls.  Asynchronous on
+        ``stream``; the outputs are ready when it completes."""
+        main = stream if stream is not None else torch.cuda.current_stream()
+        if work is None:
+            work = {}
+        if not work:
+            work["copy"] = torch.cuda.Stream(device=self.device)
+            work["rho"] = self.zeros(self.n, NCELL)
+            work["Lbar"] = self.zeros(self.n, NCOMP, NCELL)
+            work["M"] = self.zeros(self.n, NCOMP, NCELL)
+            work["m"] = self.zeros(self.n, NCELL)
+            work["L"] = self.zeros(self.n, NCOMP, NCELL)
+            work["Lc"] = self.zeros(self.n, 3, NCELL)
+            work["Mb"] = self.zeros(self.n, NCOMP, NCELL)
+            work["mb"] = self.zeros(self.n, NCELL)
+            work["rb"] = self.zeros(self.n, NCELL)
+        cp = work["copy"]
+        start, lbar_in, fwd_done = (torch.cuda.Event() for _ in range(3))
+        start.record(main)
+        cp.wait_event(start)                      # the previous step has released the buffers
+        with torch.cuda.stream(cp):
+            work["Lbar"].copy_(Lbar_h, non_blocking=True)
+            lbar_in.record(cp)
+        with torch.cuda.stream(main):
+            work["rho"].copy_(rho_h, non_blocking=True)
+        self.moments(work["rho"], work["M"], work["m"], stream=main)
+        self.interactions(work["M"], work["m"], work["L"], work["Lc"], stream=main)
+        fwd_done.record(main)
+        with torch.cuda.stream(cp):
+            cp.wait_event(fwd_done)
+            L_h.copy_(work["L"], non_blocking=True)
+        main.wait_event(lbar_in)
+        self.backward(work["Lbar"], work["Mb"], work["mb"], stream=main)
+        self.moments_backward(work["Mb"], work["mb"], work["rb"], stream=main)
+        with torch.cuda.stream(main):
+            rhobar_h.copy_(work["rb"], non_blocking=True)
+        main.wait_stream(cp)
+        return work
+
     def backward(self, Lbar, Mbar=None, mbar=None, want=(True, True), stream=None):
         if Mbar is None and want[0]:
             Mbar = self.zeros(self.n, NCOMP, NCELL)
