@@ -106,23 +106,46 @@ DERIV_SETS = {
 }
 
 
+def _deriv_plan(indices):
+    """Which components of DERIV_SETS' index list are evaluated as polynomials
+    and which follow from the Laplace identity d_zz = -d_xx - d_yy: a
+    component with two or more z derivatives is -(K + (2,0,-2)) - (K + (0,2,-2)),
+    recursively, so only components with at most one z are polynomials."""
+    direct, derived = set(), []
+
+    def need(e):
+        if e[2] < 2:
+            direct.add(e)
+            return
+        for sub in ((e[0] + 2, e[1], e[2] - 2), (e[0], e[1] + 2, e[2] - 2)):
+            need(sub)
+        if e not in derived:
+            derived.append(e)
+    for q in indices:
+        need(ROW[q])
+    derived.sort(key=lambda e: e[2])          # fewer z first: operands come before their users
+    return sorted(direct, key=lambda e: (sum(e), e)), derived
+
+
 def deriv_flops(name):
     """FLOPs of one call of a generated derivative routine: r^2 (5), 1/sqrt
-    (2), r^-2 and the powers r^-(2k+1), the cse'd polynomials and one
-    scaling product per component."""
-    polys, repl, reduced = _deriv_polys(DERIV_SETS[name])
+    (2), r^-2 and the powers r^-(2k+1), the cse'd polynomials, one scaling
+    product per polynomial component, two per component from the Laplace
+    identity."""
+    direct, derived = _deriv_plan(DERIV_SETS[name])
+    polys, repl, reduced = _deriv_polys(direct)
     kmax = max(k for k, _ in polys)
-    return 5 + 2 + 1 + kmax + sum(_flops(v) for _, v in repl) + sum(_flops(P) for P in reduced) + len(polys)
+    return (5 + 2 + 1 + kmax + sum(_flops(v) for _, v in repl) + sum(_flops(P) for P in reduced) + len(polys)
+            + 2 * len(derived))
 
 
-def _deriv_polys(indices):
+def _deriv_polys(exps):
     import sympy
     x, y, z = sympy.symbols("x y z", real=True)
     r2 = x * x + y * y + z * z
     G = -1 / sympy.sqrt(r2)
     polys = []
-    for q in indices:
-        e = ROW[q]
+    for e in exps:
         k = rank(e)
         expr = sympy.diff(G, x, e[0], y, e[1], z, e[2]) if k else G
         P = sympy.expand(sympy.simplify(expr * r2 ** sympy.Rational(2 * k + 1, 2)))
@@ -135,13 +158,16 @@ def _deriv_polys(indices):
 def deriv_code(name):
     """Straight-line code for the derivative components DERIV_SETS[name] of
     G = -1/r at R = (x, y, z): with sympy, d^K G = P_K(x, y, z) r^-(2k+1) for
-    a polynomial P_K of degree k; the polynomials share subexpressions (cse).
-    Entries of d outside the set are left untouched."""
+    a polynomial P_K of degree k (components with at most one z derivative;
+    the polynomials share subexpressions, cse), and the components with two
+    or more z derivatives from the Laplace identity.  Entries of d outside
+    the set are left untouched."""
     import re
 
     import sympy
     indices = DERIV_SETS[name]
-    polys, repl, reduced = _deriv_polys(indices)
+    direct, derived = _deriv_plan(indices)
+    polys, repl, reduced = _deriv_polys(direct)
     lines = [f"__device__ __forceinline__ void {name}(double x, double y, double z, double (&d)[36]) {{\n",
              "  const double r2 = fma(x, x, fma(y, y, z * z));\n",
              "  const double ir = 1.0 / sqrt(r2);\n",
@@ -158,10 +184,18 @@ def deriv_code(name):
         t = re.sub(r"pow\((\w+), 2\)", r"(\1 * \1)", t)
         assert "pow" not in t, t
         return re.sub(r"(?<![\w.])(\d+)(?![\w.])", r"\1.0", t)
+
+    def var(e):
+        return f"k{e[0]}{e[1]}{e[2]}"
     for sym, val in repl:
         lines.append(f"  const double {sym} = {cc(val)};\n")
-    for q, (k, _), P in zip(indices, polys, reduced):
-        lines.append(f"  d[{q}] = ({cc(P)}) * s{k};\n")
+    for e, (k, _), P in zip(direct, polys, reduced):
+        lines.append(f"  const double {var(e)} = ({cc(P)}) * s{k};\n")
+    for e in derived:
+        a, b = (e[0] + 2, e[1], e[2] - 2), (e[0], e[1] + 2, e[2] - 2)
+        lines.append(f"  const double {var(e)} = -({var(a)} + {var(b)});\n")
+    for q in indices:
+        lines.append(f"  d[{q}] = {var(ROW[q])};\n")
     lines.append("}\n\n")
     return "".join(lines)
 
