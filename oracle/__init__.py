@@ -11,8 +11,9 @@ See ``ot_oracle.c`` for the formulas and the passage of the paper each follows.
 Parity pins (tests/test_oracle_*.py) check it against sympy derivatives,
 exact polynomial integrals, brute-force point-mass sums, closed-form
 potentials and conservation invariants.  The angular-momentum correction is
-pinned only by its antisymmetry (Newton III) and by its being the missing
-order-(1,3) gradient term: parity unpinned beyond that.
+pinned by its antisymmetry (Newton III), by its being the missing order-(1,3)
+gradient term, and by the exact cancellation of the total torque for masses
+and octupoles; that it is the cited method's exact expression is a reading.
 """
 from __future__ import annotations
 

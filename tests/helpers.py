@@ -96,3 +96,54 @@ def oracle_full_solve_at(orc, tree, M, m, cells):
         L.append(acc)
         S.append(sacc)
     return np.array(L), np.array(S)
+
+
+# stored components: 0; x y z; xx xy xz yy yz zz; xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+_E20 = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1),
+        (0, 0, 2), (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1),
+        (0, 1, 2), (0, 0, 3)]
+_C20 = {e: c for c, e in enumerate(_E20)}
+
+
+def _k(*idx):
+    e = [0, 0, 0]
+    for a in idx:
+        e[a] += 1
+    return _C20[tuple(e)]
+
+
+def expansion_forces(M, L, Lc=None):
+    """[k, 3] forces on k cells with moments M [k, 20] in fields L [k, 20]:
+    F_i = -(M0 L_i + sum_j M_j L_ij + 1/2 sum_jk M_jk L_ijk) - M0 Lc_i."""
+    F = np.zeros((M.shape[0], 3))
+    for i in range(3):
+        f = M[:, 0] * L[:, _k(i)]
+        for j in range(3):
+            f = f + M[:, _k(j)] * L[:, _k(i, j)]
+            for l in range(3):
+                f = f + 0.5 * M[:, _k(j, l)] * L[:, _k(i, j, l)]
+        if Lc is not None:
+            f = f + M[:, 0] * Lc[:, i]
+        F[:, i] = -f
+    return F
+
+
+def spin_torques(M, L):
+    """[k, 3] torques of the local fields on the cells' mass distributions
+    about their centres: tau_i = -eps_ijk sum_I L[k + I] M[j + I] / I!."""
+    eps = np.zeros((3, 3, 3))
+    eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1.0
+    eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1.0
+    tau = np.zeros((M.shape[0], 3))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                if eps[i, j, k] == 0:
+                    continue
+                acc = L[:, _k(k)] * M[:, _k(j)]
+                for a in range(3):
+                    acc = acc + L[:, _k(k, a)] * M[:, _k(j, a)]
+                    for b in range(3):
+                        acc = acc + 0.5 * L[:, _k(k, a, b)] * M[:, _k(j, a, b)]
+                tau[:, i] -= eps[i, j, k] * acc
+    return tau

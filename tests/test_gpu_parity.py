@@ -534,3 +534,27 @@ def test_step_host_matches_separate_calls(ot):
     g.step_host(rho_pin, Lbar_pin, L_out, rb_out, work)
     torch.cuda.synchronize()
     assert torch.equal(L_out, L.cpu()) and torch.equal(rb_out, rb.cpu())
+
+
+@pytest.mark.parametrize("seed", [160, 161])
+def test_angular_term_conserves_angular_momentum_gpu(ot, seed):
+    """The GPU's multipole pass with its angular term on masses and
+    octupoles: the total torque (orbital plus spin) over an isolated sub-grid
+    vanishes to rounding; without Lc it is O(1)."""
+    from helpers import expansion_forces, spin_torques
+    tree = synth.single_subgrid(1, 1.0)
+    M = synth.random_moments(tree, seed=seed)
+    M[0, 1:10, :] = 0.0
+    g = ot.OTGrid.from_tree(tree)
+    L, Lc = g.multipole(dev(M))
+    torch.cuda.synchronize()
+    Mc, Lh, Lch = M[0].T, host(L)[0].T, host(Lc)[0].T
+    X = synth.cell_centres(tree, 0)
+    tau = spin_torques(Mc, Lh)
+    F0 = expansion_forces(Mc, Lh)
+    F1 = expansion_forces(Mc, Lh, Lch)
+    scale = np.sum(np.abs(np.cross(X, F0)))
+    T0 = np.linalg.norm(np.sum(np.cross(X, F0) + tau, axis=0))
+    T1 = np.linalg.norm(np.sum(np.cross(X, F1) + tau, axis=0))
+    assert T0 > 1e-5 * scale
+    assert T1 <= 1e-13 * scale, (T0, T1, scale)

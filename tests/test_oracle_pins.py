@@ -709,3 +709,59 @@ def test_sampled_full_solve_helper_matches_whole_grid(orc):
     for k, (i, c) in enumerate(cells):
         np.testing.assert_allclose(Lc[k], L[i, :, c], rtol=0, atol=1e-13 * np.max(S[i, :, c]))
         np.testing.assert_allclose(Sc[k], S[i, :, c], rtol=1e-12)
+
+
+_EPS = np.zeros((3, 3, 3))
+_EPS[0, 1, 2] = _EPS[1, 2, 0] = _EPS[2, 0, 1] = 1.0
+_EPS[0, 2, 1] = _EPS[2, 1, 0] = _EPS[1, 0, 2] = -1.0
+
+
+def _spin_torque(Mt, L):
+    """Torque of the local field on a cell's mass distribution about its
+    centre: tau_i = -eps_ijk sum_I L[k + I] M[j + I] / I! (full index sums,
+    |I| <= 2)."""
+    comp = {e: c for c, e in enumerate(EXP20)}
+
+    def key(*idx):
+        e = [0, 0, 0]
+        for a in idx:
+            e[a] += 1
+        return comp[tuple(e)]
+    tau = np.zeros(3)
+    for i, j, k in itertools.product(range(3), repeat=3):
+        if _EPS[i, j, k] == 0:
+            continue
+        acc = L[key(k)] * Mt[key(j)]
+        for a in range(3):
+            acc += L[key(k, a)] * Mt[key(j, a)]
+        for a, b in itertools.product(range(3), repeat=2):
+            acc += 0.5 * L[key(k, a, b)] * Mt[key(j, a, b)]
+        tau[i] -= _EPS[i, j, k] * acc
+    return tau
+
+
+@pytest.mark.parametrize("seed", [20, 21, 22])
+def test_angular_term_conserves_angular_momentum(orc, seed):
+    """Masses and octupoles only (the case the angular term is for): over an
+    isolated sub-grid the total torque of the expansion forces about the
+    origin, orbital X x F plus the spin torque, is O(1) without Lc and
+    vanishes to rounding with it -- which fixes the term's sign and form."""
+    tree = _single_node_tree()
+    M = synth.random_moments(tree, seed=seed)
+    M[0, 1:10, :] = 0.0
+    r = orc.run_pass_grid(tree, "multipole", M=M)
+    L, Lc = r["L"][0].T, r["Lc"][0].T
+    X = synth.cell_centres(tree, 0)
+
+    def torque(with_lc):
+        T, scale = np.zeros(3), 0.0
+        for a in range(512):
+            F = _force(M[0, :, a], L[a], Lc[a] if with_lc else None)
+            t = np.cross(X[a], F) + _spin_torque(M[0, :, a], L[a])
+            T += t
+            scale += np.sum(np.abs(np.cross(X[a], F)))
+        return np.linalg.norm(T), scale
+    t0, scale = torque(False)
+    t1, _ = torque(True)
+    assert t0 > 1e-5 * scale
+    assert t1 <= 1e-14 * scale, (t0, t1, scale)
