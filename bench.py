@@ -323,6 +323,15 @@ def run_ours(args, rank, world):
         b.record(stream)
     torch.cuda.synchronize()
     df2_ms = statistics.median(a.elapsed_time(b) for a, b in de2)
+    g.backward(Lbar, Mb, mb)
+    da = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in da:
+        flush.zero_()
+        a.record(stream)
+        g.backward(Lbar, Mb, mb)
+        b.record(stream)
+    torch.cuda.synchronize()
+    dfa_ms = statistics.median(a.elapsed_time(b) for a, b in da)
     g.set_precision(ot.OT_PREC_FP64)
     # each variant as its own launch: the multipole pass, the point-mass pass
     variant_ms = {}
@@ -422,6 +431,10 @@ def run_ours(args, rank, world):
                      "note": "point-mass and multipole contractions (with the angular term) in double-float "
                              "on the FP32 pipe, within 1e-12 of the oracle's sum of |terms|; beside the FP64 "
                              "numbers, not as them"},
+        "adjoint_df64": {"value": pairs_fwd / (dfa_ms * 1e-3), "unit": UNIT, "ms": dfa_ms,
+                         "fwd_plus_adjoint": 2 * pairs_fwd / ((df2_ms + dfa_ms) * 1e-3),
+                         "note": "the adjoint's multipole gather and point-mass scatter in double-float "
+                                 "(OT_PREC_DF64); beside the FP64 numbers, not as them"},
         "com": {"fwd": {"value": pairs_fwd / (com_fwd_ms * 1e-3), "unit": UNIT, "ms": com_fwd_ms,
                         "tflops": info["flops_fwd_com"] / (com_fwd_ms * 1e-3) / 1e12,
                         "frac": info["flops_fwd_com"] / (com_fwd_ms * 1e-3) / 1e12 / peak},

@@ -247,8 +247,8 @@ ot_status ot_interactions_backward_com(ot_grid* grid, const double* Lbar, const 
 ot_status ot_l2l_com(ot_grid* grid, const double* C, double* L, void* stream);
 ot_status ot_l2l_com_backward(ot_grid* grid, const double* C, double* Lbar, void* stream);
 
-/* Arithmetic of the contractions of the forward passes (the table path;
- * ot_interactions_com and the adjoints stay FP64).
+/* Arithmetic of the contractions of the table path (ot_interactions_com
+ * stays FP64).
  * OT_PREC_FP64 (default): FP64 FMAs throughout.
  * OT_PREC_DF64_POINT_MASS: point-mass pairs are contracted in double-float
  *   arithmetic on the FP32 pipe -- every value an unevaluated sum hi + lo of
@@ -261,8 +261,13 @@ ot_status ot_l2l_com_backward(ot_grid* grid, const double* C, double* Lbar, void
  *   2^-10 .. 2^10 of level 0's).
  * OT_PREC_DF64: the multipole contractions too (the 70-product contraction
  *   and the angular term, with the reduced moments split into double-float
- *   pairs once per call), under the same 64-product rule and bound.  The same
- *   range requirement holds for the reduced moments (mass-scaled, so O(mass)). */
+ *   pairs once per call), under the same 64-product rule and bound, and the
+ *   default adjoint (persistent schedule, not deterministic): the multipole
+ *   gather under the same rule, each point-mass contribution as a fresh
+ *   double-float dot product added to mbar in FP64.  The same range
+ *   requirement holds for the reduced moments and L-bar (scaled by h, so of
+ *   the order of the mass and L-bar).  With ot_set_deterministic or the
+ *   per-sub-grid schedule the adjoint stays FP64. */
 #define OT_PREC_FP64 0
 #define OT_PREC_DF64_POINT_MASS 1
 #define OT_PREC_DF64 2

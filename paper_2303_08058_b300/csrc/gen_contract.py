@@ -376,6 +376,38 @@ def emit():
         w("  }\n")
     w("}\n\n")
 
+    # double-float adjoint contractions (transposes of the above)
+    w("// double-float adjoint, paired: g[K] += sum_J (even order of J+K ? ls[J] : ld[J]) * d[J+K]\n")
+    w("__device__ __forceinline__ void ot_multi_adj_pair_df(float (&gh)[16], float (&gl)[16], const float (&lsh)[16],\n"
+      "                                                     const float (&lsl)[16], const float (&ldh)[16],\n"
+      "                                                     const float (&ldl)[16], const float2* __restrict__ row) {\n")
+    for di in sorted(by_di):
+        w(f"  {{\n    const float2 d = __ldg(row + {di});\n")
+        src = "ls" if rank(ROW[di]) % 2 == 0 else "ld"
+        for (j, k) in by_di[di]:
+            w(f"    df_fma(gh[{k}], gl[{k}], {src}h[{j}], {src}l[{j}], d.x, d.y);\n")
+        w("  }\n")
+    w("}\n\n")
+    w("// double-float adjoint, one target: g[K] += sum_J lb[J] d[J+K]\n")
+    w("__device__ __forceinline__ void ot_multi_adj_df(float (&gh)[16], float (&gl)[16], const float (&lh)[16],\n"
+      "                                                const float (&ll)[16], const float2* __restrict__ row) {\n")
+    for di in sorted(by_di):
+        w(f"  {{\n    const float2 d = __ldg(row + {di});\n")
+        for (j, k) in by_di[di]:
+            w(f"    df_fma(gh[{k}], gl[{k}], lh[{j}], ll[{j}], d.x, d.y);\n")
+        w("  }\n")
+    w("}\n\n")
+    w("// double-float point-mass adjoint of one entry: the even- and odd-order\n"
+      "// parts (e, q) of <lb, d> in fresh double-float accumulators\n")
+    w("__device__ __forceinline__ void ot_mono_adj_split_df(float& eh, float& el, float& qh, float& ql,\n"
+      "                                                     const float (&lh)[16], const float (&ll)[16],\n"
+      "                                                     const float (&r)[32]) {\n")
+    w("  eh = 0.0f;\n  el = 0.0f;\n  qh = 0.0f;\n  ql = 0.0f;\n")
+    for j in range(16):
+        v = "e" if rank(IND16[j]) % 2 == 0 else "q"
+        w(f"  df_fma({v}h, {v}l, lh[{j}], ll[{j}], r[{j}], r[{16 + j}]);\n")
+    w("}\n\n")
+
     # derivatives at an arbitrary separation (centre-of-mass expansion centres)
     w("// derivatives of -1/r (row layout) at R = (x, y, z), the components each\n")
     w("// contraction reads: point masses, multipole sources, multipole sources\n")

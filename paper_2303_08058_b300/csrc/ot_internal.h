@@ -89,6 +89,10 @@ struct AdjParams {
     double hreal[MAXLEV];
     const int* child_of;   // as in FwdParams
     const double* Dv;
+    // double-float adjoint
+    const float2* Lf;      // [n][16][512] reduced L-bar as (hi, lo) pairs
+    const float2* Dt2;     // [NOFF][DROW] the derivative table as (hi, lo) pairs
+    const float* Dt32;     // [NOFF][32] hi then lo parts of the 16 point-mass derivatives
 };
 
 // point-mass adjoint organised by target cells (the forward's walk) with the

@@ -637,6 +637,26 @@ __device__ __forceinline__ void adjoint_target_lb(const AdjParams& p, int2 e, bo
     }
 }
 
+// the reduced L-bar of a real target cell as double-float pairs (or zeros)
+__device__ __forceinline__ void adjoint_target_lb_df(const AdjParams& p, int2 e, bool real, int tx, int ty, int tz,
+                                                     float (&lh)[16], float (&ll)[16]) {
+    if (real) {
+        const float2* src = p.Lf + static_cast<size_t>(e.x) * NRED * NCELL + (tx & 7) + 8 * (ty & 7) + 64 * (tz & 7);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float2 v = __ldg(src + q * NCELL);
+            lh[q] = v.x;
+            ll[q] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            lh[q] = 0.0f;
+            ll[q] = 0.0f;
+        }
+    }
+}
+
 // a depth-1 virtual descendant (the child of a coarse leaf cell) as a target
 // of a real point-mass source
 __device__ __forceinline__ bool virtual_child_target(int2 e, bool virt_t) {
@@ -649,11 +669,13 @@ __device__ __forceinline__ bool virtual_child_target(int2 e, bool virt_t) {
 // entry o' also gathers from A = B - o' (row of o', odd orders negated).
 // virt_t: a real leaf source also gathers from depth-1 virtual children of
 // coarse leaves (the transpose of the coarse-target refinement).
-template <bool MULTI, bool PAIRED>
+// EMU (multipole sources only): the contraction in double-float into f,
+// moved into g by coefficient-order groups (at most 64 products each)
+template <bool MULTI, bool PAIRED, bool EMU = false>
 __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int len, bool near_seg, bool virt_t,
                                              int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
                                              const AdjParams& p, double (&g)[16], double (&g4)[4],
-                                             int item) {
+                                             DFAcc& f, int item) {
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
@@ -680,9 +702,34 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
             }
         }
         if (!__any_sync(0xffffffffu, vp || vm || wp || wm)) continue;
+        const int row = NOFF - 1 - offset_row(ox, oy, oz);
+        if constexpr (MULTI && EMU) {
+            double dc[3], dt[9];     // the angular groups are not used here
+            df_reserve(g, dc, dt, f, 16, 9, 4, 1, 0, 0);
+            float lh[16], ll[16];
+            adjoint_target_lb_df(p, ep, vp, px, py, pz, lh, ll);
+            const float2* drow = p.Dt2 + static_cast<size_t>(row) * DROW;
+            if (PAIRED) {
+                float mh[16], ml[16];
+                adjoint_target_lb_df(p, em, vm, mx, my, mz, mh, ml);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    float sh, sl, dh, dl;
+                    df_add(lh[q], ll[q], mh[q], ml[q], sh, sl);
+                    df_add(lh[q], ll[q], -mh[q], -ml[q], dh, dl);
+                    lh[q] = sh;
+                    ll[q] = sl;
+                    mh[q] = dh;
+                    ml[q] = dl;
+                }
+                ot_multi_adj_pair_df(f.ah, f.al, lh, ll, mh, ml, drow);
+            } else {
+                ot_multi_adj_df(f.ah, f.al, lh, ll, drow);
+            }
+            continue;
+        }
         double lb[16];
         adjoint_target_lb(p, ep, vp, wp, px, py, pz, lb);
-        const int row = NOFF - 1 - offset_row(ox, oy, oz);
         double d[36];
         if (MULTI) {
             load_row(d, p.Dt, row);
@@ -751,11 +798,12 @@ __device__ __forceinline__ void store_mbar(double* __restrict__ Mbar, int src, i
     for (int q = 0; q < 20; ++q) out[q * NCELL] = Mb[q];
 }
 
-template <class P>
+template <bool EMU = false, class P>
 __device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
                              int node, int par, int half, int lane, int it);
 
-template <int MODE>
+// EMU: double-float multipole gather and point-mass scatter (MODE 1, 4, 5)
+template <int MODE, bool EMU = false>
 __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
     const int lane = threadIdx.x & 31;
@@ -772,7 +820,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
         const int item = __ldg(p.items + it);
         if ((MODE & 4) && ((item >> 30) & 1)) {       // point-mass adjoint by target (atomic adds)
             const int tgt = item & 0x3fffffff;
-            scatter_item(p, p.nbr, p.ninfo, s_nb[warp], tgt >> 4, (tgt >> 1) & 7, tgt & 1, lane, it);
+            scatter_item<EMU>(p, p.nbr, p.ninfo, s_nb[warp], tgt >> 4, (tgt >> 1) & 7, tgt & 1, lane, it);
             __syncwarp();
             if (!persistent) break;
             continue;
@@ -800,6 +848,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
         const int* l2 = p.L.lists + p.L.near_off;
         const double h1 = p.hinv[level];
         double g[16], g4[4];
+        DFAcc f;
+        if (EMU) df_zero(f);
 #pragma unroll
         for (int q = 0; q < 16; ++q) g[q] = 0.0;
 #pragma unroll
@@ -809,24 +859,29 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
             // of a refined cell see its children instead
             if ((MODE & 1) && p.Mbar != nullptr) {
                 if (level == 0) {
-                    walk_adjoint<true, true>(l1, n1, false, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                    walk_adjoint<true, true, EMU>(l1, n1, false, false, sx, sy, sz, s_nb[warp], p, g, g4, f, it);
                 } else {
-                    walk_adjoint<true, true>(l1, p.L.far_pairs, false, false, sx, sy, sz, s_nb[warp], p, g, g4, it);
-                    walk_adjoint<true, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, false, sx, sy, sz,
-                                              s_nb[warp], p, g, g4, it);
+                    walk_adjoint<true, true, EMU>(l1, p.L.far_pairs, false, false, sx, sy, sz, s_nb[warp], p, g, g4,
+                                                  f, it);
+                    walk_adjoint<true, false, EMU>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, false, sx, sy, sz,
+                                                   s_nb[warp], p, g, g4, f, it);
+                }
+                if (EMU) {
+                    double dc[3], dt[9];
+                    df_flush_all<false>(g, dc, dt, f);
                 }
                 store_mbar(p.Mbar, src, scell, h1, g);
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
             const bool vt = skind == K_LEAF;   // real leaf cells also feed coarse leaves' virtual children
             if (level == 0) {
-                walk_adjoint<false, true>(l1, n1, false, vt, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                walk_adjoint<false, true>(l1, n1, false, vt, sx, sy, sz, s_nb[warp], p, g, g4, f, it);
             } else {
-                walk_adjoint<false, true>(l1, p.L.far_pairs, false, vt, sx, sy, sz, s_nb[warp], p, g, g4, it);
+                walk_adjoint<false, true>(l1, p.L.far_pairs, false, vt, sx, sy, sz, s_nb[warp], p, g, g4, f, it);
                 walk_adjoint<false, false>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, vt, sx, sy, sz, s_nb[warp],
-                                           p, g, g4, it);
+                                           p, g, g4, f, it);
             }
-            walk_adjoint<false, true>(l2, p.L.near_len, true, vt, sx, sy, sz, s_nb[warp], p, g, g4, it);
+            walk_adjoint<false, true>(l2, p.L.near_len, true, vt, sx, sy, sz, s_nb[warp], p, g, g4, f, it);
             const double v = (g4[0] + g4[1]) + (g4[2] + g4[3]);
             if (virt) p.vbar[static_cast<size_t>(src - p.n_nodes) * NCELL + scell] = v;
             else p.mbar[static_cast<size_t>(src) * NCELL + scell] = v;
@@ -857,10 +912,16 @@ __device__ __forceinline__ void scatter_mass(const P& p, int2 e, int kind, int s
 // A paired entry o: with e, q the even- and odd-order parts of <lb, row(o)>,
 // the source at t+o (pair offset R = -o) receives e + q and the source at
 // t-o (R = +o, odd orders change sign) receives e - q.
-template <bool PAIRED, bool NEAR, class P>
+// EMU: the target's L-bar as double-float pairs (lbh, lbl; lb unused), each
+// entry's dot product in fresh double-float accumulators (at most 8 products
+// each, error below 30 * 2^-48 of its |terms|), added in FP64.  The pairs are
+// loaded, not split here: a split the compiler may recompute inside the loop
+// would put FP64 work back on the slow pipe.
+template <bool PAIRED, bool NEAR, bool EMU = false, class P>
 __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int len, int tx, int ty,
                                              int tz, const int2* __restrict__ s_nb, const P& p,
-                                             const double (&lb)[16], int item) {
+                                             const double (&lb)[16], const float (&lbh)[16], const float (&lbl)[16],
+                                             int item) {
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
         const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
@@ -886,33 +947,64 @@ __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int l
             // near sources in refined sub-grids: their children, through the
             // target's virtual children
             const bool rp = kp == K_MULTI, rm = km == K_MULTI;
-            if (__any_sync(0xffffffffu, rp || rm))
-                refined_near_scatter(p, ox, oy, oz, ep, rp, px, py, pz, em, rm, mx, my, mz, lb, item);
+            if (__any_sync(0xffffffffu, rp || rm)) {
+                if constexpr (EMU) {
+                    double lbd[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) lbd[q] = static_cast<double>(lbh[q]) + static_cast<double>(lbl[q]);
+                    refined_near_scatter(p, ox, oy, oz, ep, rp, px, py, pz, em, rm, mx, my, mz, lbd, item);
+                } else {
+                    refined_near_scatter(p, ox, oy, oz, ep, rp, px, py, pz, em, rm, mx, my, mz, lb, item);
+                }
+            }
         }
         if (!__any_sync(0xffffffffu, kp >= K_LEAF || km >= K_LEAF)) continue;
-        double d[36];
-        load_row16(d, p.Dt, offset_row(ox, oy, oz));
-        double e, q;
-        ot_mono_adj_split(e, q, lb, d);
-        scatter_mass(p, ep, kp, px, py, pz, e + q);
-        if (PAIRED) scatter_mass(p, em, km, mx, my, mz, e - q);
+        if constexpr (EMU) {
+            float r[32];
+            load_row32f(r, p.Dt32, offset_row(ox, oy, oz));
+            float eh, el, qh, ql, sh, sl, dh, dl;
+            ot_mono_adj_split_df(eh, el, qh, ql, lbh, lbl, r);
+            df_add(eh, el, qh, ql, sh, sl);
+            df_add(eh, el, -qh, -ql, dh, dl);
+            scatter_mass(p, ep, kp, px, py, pz, static_cast<double>(sh) + static_cast<double>(sl));
+            if (PAIRED) scatter_mass(p, em, km, mx, my, mz, static_cast<double>(dh) + static_cast<double>(dl));
+        } else {
+            double d[36];
+            load_row16(d, p.Dt, offset_row(ox, oy, oz));
+            double e, q;
+            ot_mono_adj_split(e, q, lb, d);
+            scatter_mass(p, ep, kp, px, py, pz, e + q);
+            if (PAIRED) scatter_mass(p, em, km, mx, my, mz, e - q);
+        }
     }
 }
 
 // one scatter work item: the warp's 32 target cells of `node` push their
 // point-mass adjoint contributions into mbar
-template <class P>
+template <bool EMU, class P>
 __device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
                              int node, int par, int half, int lane, int it) {
     int tx, ty, tz;
     lane_cell(lane, par, half, tx, ty, tz);
     double lb[16];
-    const double* src = p.Lrbar + static_cast<size_t>(node) * NRED * NCELL + tx + 8 * ty + 64 * tz;
+    float lbh[16], lbl[16];
     bool nz = false;
+    if constexpr (EMU) {
+        const float2* src = p.Lf + static_cast<size_t>(node) * NRED * NCELL + tx + 8 * ty + 64 * tz;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        lb[q] = __ldg(src + q * NCELL);
-        nz |= lb[q] != 0.0;
+        for (int q = 0; q < 16; ++q) {
+            const float2 v = __ldg(src + q * NCELL);
+            lbh[q] = v.x;
+            lbl[q] = v.y;
+            nz |= v.x != 0.0f;
+        }
+    } else {
+        const double* src = p.Lrbar + static_cast<size_t>(node) * NRED * NCELL + tx + 8 * ty + 64 * tz;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            lb[q] = __ldg(src + q * NCELL);
+            nz |= lb[q] != 0.0;
+        }
     }
     if (!__any_sync(0xffffffffu, nz)) return;     // targets without an adjoint contribute nothing
     if (lane < 27) s_nb[lane] = __ldg(nbr + static_cast<size_t>(node) * 27 + lane);
@@ -921,13 +1013,15 @@ __device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int
     const int level = info & 0xff;
     const bool leafT = (info >> 8) & 1;
     if (level == 0) {
-        walk_scatter<true, false>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, lb, it);
+        walk_scatter<true, false, EMU>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
     } else {
         const int* lf = p.L.lists + par * p.L.far_len;
-        walk_scatter<true, false>(lf, p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
-        walk_scatter<false, false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, tx, ty, tz, s_nb, p, lb, it);
+        walk_scatter<true, false, EMU>(lf, p.L.far_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        walk_scatter<false, false, EMU>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, tx, ty, tz, s_nb, p, lb, lbh,
+                                        lbl, it);
     }
-    if (leafT) walk_scatter<true, true>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, it);
+    if (leafT) walk_scatter<true, true, EMU>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, lbh,
+                                            lbl, it);
 }
 
 __global__ void __launch_bounds__(256) scatter_adjoint_kernel(const ScatParams p, int persistent) {
@@ -1979,6 +2073,15 @@ cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wp
     if (p.n_items == 0) return cudaSuccess;
     const dim3 block(32 * wpb);
     const int per = persistent ? 1 : 0;
+    if (p.Dt32 != nullptr) {           // double-float (split L-bar and tables given)
+        switch (mode) {
+            case 1: adjoint_kernel<1, true><<<grid, block, 0, s>>>(p, per); break;
+            case 4: adjoint_kernel<4, true><<<grid, block, 0, s>>>(p, per); break;
+            case 5: adjoint_kernel<5, true><<<grid, block, 0, s>>>(p, per); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (mode) {
         case 1: adjoint_kernel<1><<<grid, block, 0, s>>>(p, per); break;
         case 2: adjoint_kernel<2><<<grid, block, 0, s>>>(p, per); break;
@@ -2016,12 +2119,17 @@ int forward_max_blocks_per_sm(int mode, int wpb) {
     return n;
 }
 
+// mode 1-5 FP64; 9, 12, 13: the double-float variants of modes 1, 4, 5
 int adjoint_max_blocks_per_sm(int mode, int wpb) {
     int n = 0;
-    const void* f = (mode == 1) ? (const void*)adjoint_kernel<1>
-                  : (mode == 2) ? (const void*)adjoint_kernel<2>
-                  : (mode == 4) ? (const void*)adjoint_kernel<4>
-                  : (mode == 5) ? (const void*)adjoint_kernel<5> : (const void*)adjoint_kernel<3>;
+    const void* f = (mode == 1)    ? (const void*)adjoint_kernel<1>
+                    : (mode == 2)  ? (const void*)adjoint_kernel<2>
+                    : (mode == 4)  ? (const void*)adjoint_kernel<4>
+                    : (mode == 5)  ? (const void*)adjoint_kernel<5>
+                    : (mode == 9)  ? (const void*)adjoint_kernel<1, true>
+                    : (mode == 12) ? (const void*)adjoint_kernel<4, true>
+                    : (mode == 13) ? (const void*)adjoint_kernel<5, true>
+                                   : (const void*)adjoint_kernel<3>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
     return n;
 }

@@ -177,6 +177,7 @@ struct ot_grid {
     float2* d_Mf = nullptr;             // reduced moments as double-float pairs (scratch)
     float2* d_Dt2 = nullptr;            // the derivative table as double-float pairs
     int maxb_emu2[4][9] = {};           // forward with double-float multipole contractions, modes 1 and 3
+    int maxb_adj_emu[14][9] = {};       // double-float adjoint, modes 9, 12, 13 (= 1, 4, 5 + 8)
     int* d_lists = nullptr;
     double* d_hinv = nullptr;
     int* d_items_fwd[4] = {nullptr, nullptr, nullptr, nullptr};     // LPT order, by mode
@@ -815,6 +816,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         g->maxb_emu[3][w] = forward_max_blocks_per_sm(7, w);
         g->maxb_emu2[1][w] = forward_max_blocks_per_sm(5, w);
         g->maxb_emu2[3][w] = forward_max_blocks_per_sm(8, w);
+        for (int m : {9, 12, 13}) g->maxb_adj_emu[m][w] = adjoint_max_blocks_per_sm(m, w);
         g->maxb_scat[w] = scatter_max_blocks_per_sm(w);
         g->maxb_adj[4 - 4][w] = adjoint_max_blocks_per_sm(4, w);   // slot 0: fused, point masses only
         g->maxb_fast5[w] = adjoint_max_blocks_per_sm(5, w);
@@ -1095,12 +1097,29 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
         const int k = (mode & 1) ? 1 : 0;
         p.items = g->d_items_adj_fast[k];
         p.n_items = g->n_items_adj_fast[k];
+        int maxb = k ? g->maxb_fast5[g->wpb] : g->maxb_adj[0][g->wpb];
+        if (g->precision == OT_PREC_DF64) {
+            // double-float: L-bar split into (hi, lo) pairs in the moments'
+            // scratch (calls on one grid are serialized)
+            OT_CUDA(launch_split_moments(g->d_Lrbar, g->d_Mf, g->d_all, g->n, s));
+            p.Lf = g->d_Mf;
+            p.Dt2 = g->d_Dt2;
+            p.Dt32 = g->d_Dt32;
+            maxb = g->maxb_adj_emu[k ? 13 : 12][g->wpb];
+        }
         OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
-        const int maxb = k ? g->maxb_fast5[g->wpb] : g->maxb_adj[0][g->wpb];
         OT_CUDA(launch_adjoint(p, k ? 5 : 4, true, g->wpb, grid_blocks(g, maxb), s));
     } else {
+        int maxb = g->maxb_adj[mode][g->wpb];
+        if (g->precision == OT_PREC_DF64 && mode == 1) {
+            OT_CUDA(launch_split_moments(g->d_Lrbar, g->d_Mf, g->d_all, g->n, s));
+            p.Lf = g->d_Mf;
+            p.Dt2 = g->d_Dt2;
+            p.Dt32 = g->d_Dt32;
+            maxb = g->maxb_adj_emu[9][g->wpb];
+        }
         OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
-        OT_CUDA(launch_adjoint(p, mode, true, g->wpb, grid_blocks(g, g->maxb_adj[mode][g->wpb]), s));
+        OT_CUDA(launch_adjoint(p, mode, true, g->wpb, grid_blocks(g, maxb), s));
     }
     if (!scatter && mbar && g->vmap_rows > 0)
         OT_CUDA(launch_restrict_virtual(g->d_vbar, g->d_vmap, g->vmap_rows, mbar, s));
@@ -1703,7 +1722,7 @@ ot_status ot_interactions_backward(ot_grid* g, const double* Lbar, double* Mbar,
     if (Mbar && !aligned16(Mbar)) return fail(OT_EINVAL, "Mbar is not 16-byte aligned");
     if (mbar && !aligned16(mbar)) return fail(OT_EINVAL, "mbar is not 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    GraphKey key{4 + 8 * g->deterministic, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps};
+    GraphKey key{4 + 8 * g->deterministic + 16 * g->precision, Lbar, Mbar, mbar, nullptr, g->wpb, g->bps};
     return run_graphed(g, key, s, [&](cudaStream_t st) { return enqueue_backward(g, Lbar, Mbar, mbar, st); });
     GUARD_END
 }

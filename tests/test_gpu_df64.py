@@ -131,3 +131,51 @@ def test_df64_multipole_pass_differs_from_fp64_by_rounding_only(ot):
     assert np.max(np.abs(Ldf - L64) / scale) < 1e-12
     scale_c = np.max(np.abs(Lc64), axis=(0, 2), keepdims=True)
     assert np.max(np.abs(Lcdf - Lc64) / scale_c) < 1e-11
+
+
+def _sparse_lbar(tree, count, seed):
+    rng = np.random.default_rng(seed)
+    tg = np.unique(np.stack([rng.integers(0, tree.n, count), rng.integers(0, 512, count)], 1), axis=0)
+    Lbar = np.zeros((tree.n, 20, 512))
+    Lbar[tg[:, 0], :, tg[:, 1]] = rng.standard_normal((len(tg), 20))
+    return Lbar, tg.astype(np.int32)
+
+
+@pytest.mark.parametrize("which", ["uniform_tree", "adaptive", "leaf_level"])
+def test_df64_adjoint_matches_oracle(ot, orc, which):
+    """The double-float adjoint (multipole gather and point-mass scatter)
+    against the oracle's transposed sums under the same 1e-12 bound."""
+    tree = {"leaf_level": lambda: synth.uniform_level(1, 1.0),
+            "adaptive": _small_adaptive,
+            "uniform_tree": lambda: synth.uniform_tree(1, 1.0)}[which]()
+    Lbar, tg = _sparse_lbar(tree, 300, 142)
+    g = ot.OTGrid.from_tree(tree)
+    g.set_precision(ot.OT_PREC_DF64)
+    Mb, mb = g.backward(dev(Lbar))
+    Mb1, _ = g.backward(dev(Lbar), want=(True, False))      # the multipole half alone
+    torch.cuda.synchronize()
+    g.check()
+    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg)
+    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
+    assert_parity(host(Mb1), Mo, SM, what="Mbar (alone)", block_axis=1)
+    assert_parity(host(mb), mo, Sm, what="mbar")
+
+
+@pytest.mark.parametrize("cfg", ["config2", "config5"])
+def test_df64_adjoint_full_size_close_to_fp64(ot, cfg):
+    """Dense N(0,1) L-bar on the full-size grids: the double-float adjoint
+    within 1e-12 of the FP64 adjoint relative to each component's largest
+    magnitude, and really a different arithmetic."""
+    tree, _ = synth.config2() if cfg == "config2" else synth.config5_step(2)
+    Lbar = dev(np.random.default_rng(143).standard_normal((tree.n, 20, 512)))
+    g = ot.OTGrid.from_tree(tree)
+    Mb64, mb64 = g.backward(Lbar)
+    g.set_precision(ot.OT_PREC_DF64)
+    Mbd, mbd = g.backward(Lbar)
+    torch.cuda.synchronize()
+    Mb64, mb64, Mbd, mbd = host(Mb64), host(mb64), host(Mbd), host(mbd)
+    assert not np.array_equal(Mbd, Mb64)
+    sM = np.max(np.abs(Mb64), axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(Mbd - Mb64) / np.where(sM > 0, sM, 1.0)) < 1e-12
+    assert np.max(np.abs(mbd - mb64)) < 1e-12 * np.max(np.abs(mb64))
