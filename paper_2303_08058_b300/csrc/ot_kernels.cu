@@ -339,15 +339,18 @@ __device__ __forceinline__ void df_move(double* a, float* h, float* l) {
     }
 }
 
-// make room for an entry adding inc[g] products to group g
+// make room for an entry adding inc[g] products to group g.  The counts are
+// warp-uniform; the __syncwarp() keeps each move a real (rarely taken) branch:
+// if-converted into predicated code, the moves' FP64 conversions and adds
+// would issue on the FP64 pipe at every entry.
 __device__ __forceinline__ void df_reserve(double (&a)[16], double (&c)[3], double (&t4)[9], DFAcc& f, int i0, int i1,
                                            int i2, int i3, int i4, int i5) {
-    if (f.cnt[0] + i0 > DF_MAX) { df_move<0, 1>(a, f.ah, f.al); f.cnt[0] = 0; }
-    if (f.cnt[1] + i1 > DF_MAX) { df_move<1, 4>(a, f.ah, f.al); f.cnt[1] = 0; }
-    if (f.cnt[2] + i2 > DF_MAX) { df_move<4, 9>(a, f.ah, f.al); f.cnt[2] = 0; }
-    if (f.cnt[3] + i3 > DF_MAX) { df_move<9, 16>(a, f.ah, f.al); f.cnt[3] = 0; }
-    if (f.cnt[4] + i4 > DF_MAX) { df_move<0, 3>(c, f.ch, f.cl); f.cnt[4] = 0; }
-    if (f.cnt[5] + i5 > DF_MAX) { df_move<0, 9>(t4, f.th, f.tl); f.cnt[5] = 0; }
+    if (f.cnt[0] + i0 > DF_MAX) { __syncwarp(); df_move<0, 1>(a, f.ah, f.al); f.cnt[0] = 0; }
+    if (f.cnt[1] + i1 > DF_MAX) { __syncwarp(); df_move<1, 4>(a, f.ah, f.al); f.cnt[1] = 0; }
+    if (f.cnt[2] + i2 > DF_MAX) { __syncwarp(); df_move<4, 9>(a, f.ah, f.al); f.cnt[2] = 0; }
+    if (f.cnt[3] + i3 > DF_MAX) { __syncwarp(); df_move<9, 16>(a, f.ah, f.al); f.cnt[3] = 0; }
+    if (f.cnt[4] + i4 > DF_MAX) { __syncwarp(); df_move<0, 3>(c, f.ch, f.cl); f.cnt[4] = 0; }
+    if (f.cnt[5] + i5 > DF_MAX) { __syncwarp(); df_move<0, 9>(t4, f.th, f.tl); f.cnt[5] = 0; }
     f.cnt[0] += i0;
     f.cnt[1] += i1;
     f.cnt[2] += i2;
