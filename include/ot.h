@@ -125,6 +125,9 @@ typedef struct {
                                       (each counted once in pairs_monopole) */
     int64_t pairs_padded_fwd;      /* pairs the forward's lanes run, sources outside the domain
                                       included (a paired entry runs two per lane) */
+    int32_t chunked_subgrids;      /* sub-grids whose multipole work items run as several
+                                      list chunks (summed in chunk order by the last one) */
+    int32_t reserved0;
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the

@@ -46,10 +46,12 @@ class GridInfo(ctypes.Structure):
                 ("root_offsets", ctypes.c_int32), ("pairs_multipole", ctypes.c_int64),
                 ("pairs_monopole", ctypes.c_int64), ("pairs_virtual", ctypes.c_int64),
                 ("pairs_angular", ctypes.c_int64), ("lanes_fwd", ctypes.c_int64), ("flops_fwd", ctypes.c_int64),
-                ("flops_adj", ctypes.c_int64), ("ops_fwd", ctypes.c_int64), ("ops_adj", ctypes.c_int64), ("schedule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("flops_adj", ctypes.c_int64), ("ops_fwd", ctypes.c_int64), ("ops_adj", ctypes.c_int64),
+                ("schedule", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("graphs_enabled", ctypes.c_int32),
                 ("flops_fwd_com", ctypes.c_int64), ("flops_adj_com", ctypes.c_int64),
-                ("pairs_refined", ctypes.c_int64), ("pairs_padded_fwd", ctypes.c_int64)]
+                ("pairs_refined", ctypes.c_int64), ("pairs_padded_fwd", ctypes.c_int64),
+                ("chunked_subgrids", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -14,6 +14,24 @@ constexpr int DROW = 36;          // doubles per derivative-table row
 constexpr int NOFF = 15 * 15 * 15;  // integer offsets in [-7, 7]^3
 constexpr int NVROW = 14 * 14 * 14; // rows of the virtual-child table: q = 2o + c in [-6, 7]^3
 constexpr int MAXLEV = 21;        // levels 0..20
+constexpr int PART_VALS = 28;     // accumulators of a chunk: 16 coefficients, 3 + 9 angular
+
+// Parity pattern of reduced component q (bit 0: x, bit 1: y, bit 2: z order
+// odd).  Reduced order: 0; x y z; xx xy xz yy yz; xxx xxy xxz xyy xyz yyy yyz.
+__host__ __device__ constexpr int comp_parity(int q) {
+    return static_cast<int>((0x4271421605304210ULL >> (4 * q)) & 0xfULL);
+}
+// FP64 instructions per lane of a reflection class with zero pattern Z: the
+// Walsh-Hadamard transform over the d = 3 - |Z| sign axes (d 2^d adds) and one
+// FMA per component whose parity avoids Z (the others are exactly zero).
+__host__ __device__ constexpr int class_fmas(int Z) {
+    int n = 0;
+    for (int q = 0; q < NRED; ++q) n += (comp_parity(q) & Z) == 0;
+    return n;
+}
+__host__ __device__ constexpr int class_adds(int Z) {
+    return (3 - ((Z & 1) + ((Z >> 1) & 1) + ((Z >> 2) & 1))) << (3 - ((Z & 1) + ((Z >> 1) & 1) + ((Z >> 2) & 1)));
+}
 
 // Neighbour-table entry (one per 3x3x3 neighbour of a sub-grid at its own level).
 //   x: node index (real node, or the coarse leaf of a virtual descendant)
@@ -31,10 +49,24 @@ enum Kind : int { K_NONE = 0, K_MULTI = 1, K_LEAF = 2, K_VIRT = 3 };
 // Each far list holds far_pairs entries standing for an offset o and its
 // negation -o (both in the list), then far_len - far_pairs single offsets.
 // The near and root lists are closed under negation: every entry is paired.
+//
+// Point masses at leaf targets walk the same far and near offsets grouped by
+// reflection class: the offsets (±a, ±b, ±c) of one list, a, b, c >= 0.  A
+// class entry is a | b << 8 | c << 16 | members << 24, member bit i standing
+// for the offset with x negated if i & 1, y if i & 2, z if i & 4 (for a zero
+// component only the bit-clear member).  Entries are grouped by the zero
+// pattern Z (bit 0: a == 0, bit 1: b == 0, bit 2: c == 0): group Z spans
+// [zoff[Z], zoff[Z + 1]).  Offsets of classes that would cost more than their
+// +-o pairs and singles follow as pairs, then singles.  The far class list of
+// parity p is the far list of parity 0 reflected on the axes set in p, so
+// every parity has the same class counts.
 struct Lists {
-    const int* lists;      // far[8][far_len] | near[near_len] | root[root_len]
+    const int* lists;      // far[8][far_len] | near[near_len] | root[root_len] | cfar[8][cf_stride] | cnear
     int far_len, far_pairs, near_len, root_len;
     int near_off, root_off;
+    int cf_off, cf_stride, cf_pairs, cf_singles;   // far classes; leftover pairs and singles follow zoff[7]
+    int cn_off, cn_pairs;                          // near classes, then leftover pairs
+    int cf_z[8], cn_z[8];                          // class group bounds by zero pattern
 };
 
 struct FwdParams {
@@ -64,6 +96,10 @@ struct FwdParams {
     // coarse leaf targets refined virtually next to refined sub-grids
     const int* child_of;   // [n][8] child node per octant (x fastest), -1 for leaves
     const double* Dv;      // [NVROW][16] virtual-child mean rows (built by build_grid)
+    // chunked items (item bits 26-29: chunk index); null: every item is whole
+    const int2* cinfo;     // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
+    double* part;          // [slots][PART_VALS][32] chunk accumulators
+    int* chunk_ctr;        // [counters] chunks finished per (node, parity, half), zeroed per launch
 };
 
 struct AdjParams {

@@ -394,7 +394,90 @@ __device__ __forceinline__ void source_moments_df(const FwdParams& p, int2 e, bo
 // t - o share the table row of o, with odd-order derivatives negated for -o).
 // EMU bits: 1 point-mass contractions in double-float (the partial sums in
 // DFAcc), 2 multipole ones too
-template <int MODE, bool PAIRED, int EMU, bool NEAR = false>
+// ---------------------------------------------------------------------------
+// point masses by reflection class (leaf targets)
+//
+// The sources at t + s*o (s in {+1, -1}^3 per axis, o = (a, b, c) >= 0) share
+// one table row up to signs: D^(kx,ky,kz) at -s*o is sx^kx sy^ky sz^kz times
+// its value at -o, since G is even in every coordinate.  So a target adds
+// row_q * W[pi(q)] to reduced coefficient q, W the Walsh-Hadamard transform
+// of the members' masses over the sign axes, W[pi] = sum_i (-1)^|i & pi| m_i
+// (member i negated on the axes set in i), pi(q) the parity pattern of q.
+// Eight point-mass pairs then cost 24 adds + 16 FMAs instead of four +-o
+// entries of 2 adds + 16 FMAs each.  An axis with o = 0 holds one member and
+// no odd orders on it (their table entries are exactly zero): class Z skips
+// those axes and components.  The adjoint by target is the transpose: the
+// partial dot products of L-bar and the row by parity pattern, transformed
+// the same way (the transform is symmetric), give each member's share.
+// ---------------------------------------------------------------------------
+
+template <int Z>
+__device__ __forceinline__ void class_transform(double (&w)[8]) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        if ((Z >> b) & 1) continue;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (((i >> b) & 1) || (i & Z)) continue;
+            const double u = w[i], v = w[i | (1 << b)];
+            w[i] = u + v;
+            w[i | (1 << b)] = u - v;
+        }
+    }
+}
+
+// local position of member i of class (a, b, c) seen from target t
+__device__ __forceinline__ void class_member(int i, int a, int b, int c, int tx, int ty, int tz, int& sx, int& sy,
+                                             int& sz) {
+    sx = (i & 1) ? tx - a : tx + a;
+    sy = (i & 2) ? ty - b : ty + b;
+    sz = (i & 4) ? tz - c : tz + c;
+}
+
+template <int Z>
+__device__ __forceinline__ void walk_classes_fwd(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                 const int2* __restrict__ s_nb, const FwdParams& p,
+                                                 double (&acc)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        double w[8];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            w[i] = 0.0;
+            if (i & Z) continue;
+            if ((members >> i) & 1u) {
+                int sx, sy, sz;
+                class_member(i, a, b, c, tx, ty, tz, sx, sy, sz);
+                const int2 es = s_nb[nb_index(sx, sy, sz)];
+                const int ks = checked_kind(p, es, item);
+                any |= ks >= K_LEAF;
+                w[i] = source_mass(p, es, ks, sx, sy, sz);
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(a, b, c));
+        class_transform<Z>(w);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (!(comp_parity(q) & Z)) acc[q] = fma(w[comp_parity(q)], d[q], acc[q]);
+    }
+}
+
+// the seven zero patterns of a class list (Z = 7 would be the self pair)
+template <int Z = 0, class CH>
+__device__ __forceinline__ void walk_classes_fwd_all(const int* __restrict__ list, const int* zoff, const CH& ch,
+                                                     int tx, int ty, int tz, const int2* __restrict__ s_nb,
+                                                     const FwdParams& p, double (&acc)[16], int item) {
+    const int len = zoff[Z + 1] - zoff[Z];
+    walk_classes_fwd<Z>(list + zoff[Z] + ch.lo(len), ch.n(len), tx, ty, tz, s_nb, p, acc, item);
+    if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, ch, tx, ty, tz, s_nb, p, acc, item);
+}
+
+template <int MODE, bool PAIRED, int EMU, bool NEAR = false, bool PM = true>
 __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
                                              int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                              const FwdParams& p, double (&a)[16], double (&c)[3],
@@ -413,7 +496,7 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
             km = checked_kind(p, em, item);
         }
         const int row = offset_row(ox, oy, oz);
-        if (MODE & 2) {
+        if ((MODE & 2) && PM) {
             const bool mono = kp >= K_LEAF || km >= K_LEAF;
             if (__any_sync(0xffffffffu, mono)) {
                 if (EMU & 1) {
@@ -561,6 +644,51 @@ __device__ __forceinline__ void store_forward(const FwdParams& p, int node, int 
     }
 }
 
+// chunk c of k of a work item walks entries [len c / k, len (c + 1) / k) of
+// every list
+struct Chunk {
+    int c, k;
+    __device__ __forceinline__ int lo(int len) const { return len * c / k; }
+    __device__ __forceinline__ int n(int len) const { return len * (c + 1) / k - len * c / k; }
+};
+
+// the chunk's accumulators into its partial slot; true for the last chunk of
+// the (node, parity, half) to finish, which then holds the sum of all chunks
+// in chunk order (the same bits whichever chunk finishes last)
+__device__ __forceinline__ bool chunk_combine(const FwdParams& p, int2 ci, int ph, Chunk ch, int lane,
+                                              double (&a)[16], double (&c)[3], double (&t4)[9]) {
+    double* slot = p.part + static_cast<size_t>(ci.x + ph * ch.k + ch.c) * PART_VALS * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) __stcg(slot + q * 32, a[q]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) __stcg(slot + (16 + q) * 32, c[q]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) __stcg(slot + (19 + q) * 32, t4[q]);
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(p.chunk_ctr + (ci.y >> 4) + ph, 1) == ch.k - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) a[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) c[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) t4[q] = 0.0;
+    for (int j = 0; j < ch.k; ++j) {
+        const double* src = p.part + static_cast<size_t>(ci.x + ph * ch.k + j) * PART_VALS * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] += __ldcg(src + q * 32);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) c[q] += __ldcg(src + (16 + q) * 32);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) t4[q] += __ldcg(src + (19 + q) * 32);
+    }
+    return true;
+}
+
 template <int MODE, int EMU>
 __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
@@ -576,7 +704,18 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
         }
         if (it >= p.n_items) break;
         const int item = __ldg(p.items + it);
-        const int node = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        const int node = (item >> 4) & 0x3fffff, par = (item >> 1) & 7, half = item & 1;
+        Chunk ch{(item >> 26) & 15, 1};
+        int2 ci = make_int2(-1, 0);
+        if (p.cinfo != nullptr) {
+            ci = __ldg(p.cinfo + node);
+            if (ci.x >= 0) ch.k = (ci.y & 15) + 1;
+        }
+        if (ch.c >= ch.k) {        // a chunk index the node does not have
+            report(p.status, 6, it);
+            if (!persistent) break;
+            continue;
+        }
         if (lane < 27) s_nb[warp][lane] = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
         __syncwarp();
         const int info = __ldg(p.ninfo + node);
@@ -593,20 +732,55 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
         for (int q = 0; q < 3; ++q) c[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) t4[q] = 0.0;
-        if (level == 0) {
-            walk_forward<MODE, true, EMU>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, tx, ty, tz, s_nb[warp], p,
-                                          a, c, t4, f, it);
+        if ((MODE & 2) && level > 0 && leafT && !(EMU & 1)) {
+            // leaf target, FP64 point masses: by reflection class over the far
+            // and near offsets; multipole sources (refined neighbours) over the
+            // full far list, refined near sources over the near list
+            const int2* nb = s_nb[warp];
+            const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
+            walk_classes_fwd_all(cf, p.L.cf_z, ch, tx, ty, tz, nb, p, a, it);
+            cf += p.L.cf_z[7];
+            walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
+                                       t4, f, it);
+            cf += p.L.cf_pairs;
+            walk_forward<2, false, EMU>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
+                                        c, t4, f, it);
+            const int* cn = p.L.lists + p.L.cn_off;
+            walk_classes_fwd_all(cn, p.L.cn_z, ch, tx, ty, tz, nb, p, a, it);
+            cn += p.L.cn_z[7];
+            walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
+                                       t4, f, it);
+            if (__any_sync(0xffffffffu, lane < 27 && (nb[lane < 27 ? lane : 0].y & 3) == K_MULTI)) {
+                if (MODE & 1) {
+                    const int* lf = p.L.lists + par * p.L.far_len;
+                    const int ns = p.L.far_len - p.L.far_pairs;
+                    walk_forward<1, true, EMU>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), false, tx, ty, tz, nb,
+                                               p, a, c, t4, f, it);
+                    walk_forward<1, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), false, tx, ty, tz, nb, p, a,
+                                                c, t4, f, it);
+                }
+                walk_forward<2, true, EMU, true, false>(p.L.lists + p.L.near_off + ch.lo(p.L.near_len),
+                                                        ch.n(p.L.near_len), false, tx, ty, tz, nb, p, a, c, t4, f, it);
+            }
         } else {
-            const int* lf = p.L.lists + par * p.L.far_len;
-            walk_forward<MODE, true, EMU>(lf, p.L.far_pairs, !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
-            walk_forward<MODE, false, EMU>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, tx, ty, tz,
-                                           s_nb[warp], p, a, c, t4, f, it);
+            if (level == 0) {
+                walk_forward<MODE, true, EMU>(p.L.lists + p.L.root_off + ch.lo(p.L.root_len), ch.n(p.L.root_len),
+                                              !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
+            } else {
+                const int* lf = p.L.lists + par * p.L.far_len;
+                const int ns = p.L.far_len - p.L.far_pairs;
+                walk_forward<MODE, true, EMU>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), !leafT, tx, ty, tz,
+                                              s_nb[warp], p, a, c, t4, f, it);
+                walk_forward<MODE, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), !leafT, tx, ty, tz,
+                                               s_nb[warp], p, a, c, t4, f, it);
+            }
+            if (leafT)
+                walk_forward<MODE, true, EMU, true>(p.L.lists + p.L.near_off + ch.lo(p.L.near_len), ch.n(p.L.near_len),
+                                                    false, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
         }
-        if (leafT)
-            walk_forward<MODE, true, EMU, true>(p.L.lists + p.L.near_off, p.L.near_len, false, tx, ty, tz, s_nb[warp], p,
-                                          a, c, t4, f, it);
         if (EMU) df_flush_all<(EMU & 2) != 0>(a, c, t4, f);
-        store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
+        if (ch.k == 1 || chunk_combine(p, ci, item & 15, ch, lane, a, c, t4))
+            store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
         __syncwarp();
         if (!persistent) break;
     }
@@ -920,7 +1094,70 @@ __device__ __forceinline__ void scatter_mass(const P& p, int2 e, int kind, int s
 // each, error below 30 * 2^-48 of its |terms|), added in FP64.  The pairs are
 // loaded, not split here: a split the compiler may recompute inside the loop
 // would put FP64 work back on the slow pipe.
-template <bool PAIRED, bool NEAR, bool EMU = false, class P>
+// the point-mass adjoint by target over a class list (see walk_classes_fwd):
+// member i of a class receives sum_pi (-1)^|i & pi| P[pi], P[pi] the partial
+// dot product of the target's L-bar and the row over the components of
+// parity pattern pi
+template <int Z, class P>
+__device__ __forceinline__ void walk_classes_scatter(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                     const int2* __restrict__ s_nb, const P& p,
+                                                     const double (&lb)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        int2 es[8];
+        int ks[8];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            ks[i] = K_NONE;
+            es[i] = make_int2(-1, 0);
+            if (i & Z) continue;
+            if ((members >> i) & 1u) {
+                int sx, sy, sz;
+                class_member(i, a, b, c, tx, ty, tz, sx, sy, sz);
+                es[i] = s_nb[nb_index(sx, sy, sz)];
+                int kind = es[i].y & 3;
+                if (kind != K_NONE && static_cast<unsigned>(es[i].x) >= static_cast<unsigned>(p.n_nodes)) {
+                    report(p.status, 3, item);
+                    kind = K_NONE;
+                }
+                ks[i] = kind;
+                any |= kind >= K_LEAF;
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(a, b, c));
+        double w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (!(comp_parity(q) & Z)) w[comp_parity(q)] = fma(lb[q], d[q], w[comp_parity(q)]);
+        class_transform<Z>(w);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i & Z) continue;
+            if (ks[i] >= K_LEAF) {
+                int sx, sy, sz;
+                class_member(i, a, b, c, tx, ty, tz, sx, sy, sz);
+                scatter_mass(p, es[i], ks[i], sx, sy, sz, w[i]);
+            }
+        }
+    }
+}
+
+template <int Z = 0, class P>
+__device__ __forceinline__ void walk_classes_scatter_all(const int* __restrict__ list, const int* zoff, int tx,
+                                                         int ty, int tz, const int2* __restrict__ s_nb, const P& p,
+                                                         const double (&lb)[16], int item) {
+    walk_classes_scatter<Z>(list + zoff[Z], zoff[Z + 1] - zoff[Z], tx, ty, tz, s_nb, p, lb, item);
+    if constexpr (Z < 6) walk_classes_scatter_all<Z + 1>(list, zoff, tx, ty, tz, s_nb, p, lb, item);
+}
+
+template <bool PAIRED, bool NEAR, bool EMU = false, bool PM = true, class P>
 __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int len, int tx, int ty,
                                              int tz, const int2* __restrict__ s_nb, const P& p,
                                              const double (&lb)[16], const float (&lbh)[16], const float (&lbl)[16],
@@ -961,7 +1198,7 @@ __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int l
                 }
             }
         }
-        if (!__any_sync(0xffffffffu, kp >= K_LEAF || km >= K_LEAF)) continue;
+        if (!PM || !__any_sync(0xffffffffu, kp >= K_LEAF || km >= K_LEAF)) continue;
         if constexpr (EMU) {
             float r[32];
             load_row32f(r, p.Dt32, offset_row(ox, oy, oz));
@@ -1015,6 +1252,21 @@ __device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int
     const int info = __ldg(ninfo + node);
     const int level = info & 0xff;
     const bool leafT = (info >> 8) & 1;
+    if (!EMU && level > 0 && leafT) {
+        // by reflection class (see the forward); refined near sources over the near list
+        const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
+        walk_classes_scatter_all(cf, p.L.cf_z, tx, ty, tz, s_nb, p, lb, it);
+        cf += p.L.cf_z[7];
+        walk_scatter<true, false, EMU>(cf, p.L.cf_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        const int* cn = p.L.lists + p.L.cn_off;
+        walk_classes_scatter_all(cn, p.L.cn_z, tx, ty, tz, s_nb, p, lb, it);
+        walk_scatter<true, false, EMU>(cn + p.L.cn_z[7], p.L.cn_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        if (__any_sync(0xffffffffu, lane < 27 && (s_nb[lane < 27 ? lane : 0].y & 3) == K_MULTI))
+            walk_scatter<true, true, EMU, false>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, lbh,
+                                                 lbl, it);
+        return;
+    }
     if (level == 0) {
         walk_scatter<true, false, EMU>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
     } else {

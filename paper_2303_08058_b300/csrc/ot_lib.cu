@@ -158,6 +158,7 @@ struct ot_grid {
     std::vector<int> ninfo, vinfo;
     std::vector<int> lists;
     int far_len = 0, far_pairs = 0, near_len = 0, root_len = 0, far_offsets = 0;
+    Lists Lh = {};                      // list layout; Lh.lists is set to d_lists after the upload
     double hinv[MAXLEV];
 
     // device buffers
@@ -183,6 +184,16 @@ struct ot_grid {
     int* d_items_fwd[4] = {nullptr, nullptr, nullptr, nullptr};     // LPT order, by mode
     int n_items_fwd[4] = {0, 0, 0, 0};
     int* d_items_fwd_node = nullptr;                                 // node order (plain path)
+    // chunked items of the multipole and fused passes (table path)
+    std::vector<int> itemsc_fwd[4], itemsc_node, itemc_node_start;
+    std::vector<int2> cinfo;            // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
+    int n_part_slots = 0, n_chunk_ctrs = 0;
+    int* d_itemsc_fwd[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n_itemsc_fwd[4] = {0, 0, 0, 0};
+    int* d_itemsc_node = nullptr;
+    int2* d_cinfo = nullptr;
+    double* d_part = nullptr;           // [slots][28][32] chunk accumulators
+    int* d_chunk_ctr = nullptr;         // [counters] chunks finished per (node, parity, half)
     std::vector<int> node_item_start;                                // [n + 1] into d_items_fwd_node
     int* d_items_adj[4] = {nullptr, nullptr, nullptr, nullptr};
     int n_items_adj[4] = {0, 0, 0, 0};
@@ -357,9 +368,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         }
     };
     std::vector<int> far_pair[8], far_single[8], near_pair, near_single, root_pair, root_single;
+    std::vector<std::array<int, 3>> far_offs[8], near_offs;
     for (int p = 0; p < 8; ++p) {
         const int px = p & 1, py = (p >> 1) & 1, pz = (p >> 2) & 1;
-        std::vector<std::array<int, 3>> offs;
+        std::vector<std::array<int, 3>>& offs = far_offs[p];
         for (int oz = -7; oz <= 7; ++oz)
             for (int oy = -7; oy <= 7; ++oy)
                 for (int ox = -7; ox <= 7; ++ox) {
@@ -380,6 +392,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 }
         split(nr, near_pair, near_single);
         split(rt, root_pair, root_single);
+        near_offs = nr;
     }
     for (int p = 1; p < 8; ++p)
         if (far_pair[p].size() != far_pair[0].size() || far_single[p].size() != far_single[0].size())
@@ -398,6 +411,73 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     g->lists.insert(g->lists.end(), near_pair.begin(), near_pair.end());
     g->lists.insert(g->lists.end(), root_pair.begin(), root_pair.end());
     g->far_offsets = static_cast<int>(2 * far_pair[0].size() + far_single[0].size());
+
+    // reflection classes of the far (per parity) and near offsets, for point
+    // masses at leaf targets: a class is kept where its FP64 instructions per
+    // lane (class_adds + class_fmas) are fewer than those of its +-o pairs
+    // (18) and singles (16); its offsets are walked as pairs and singles
+    // otherwise
+    auto class_split = [&](const std::vector<std::array<int, 3>>& offs, std::vector<int> (&cls)[8],
+                           std::vector<int>& pairs, std::vector<int>& singles) {
+        std::map<int, std::vector<std::array<int, 3>>> byrep;
+        for (auto& o : offs) byrep[std::abs(o[0]) | (std::abs(o[1]) << 8) | (std::abs(o[2]) << 16)].push_back(o);
+        for (auto& kv : byrep) {
+            const int a = kv.first & 0xff, b = (kv.first >> 8) & 0xff, cc = kv.first >> 16;
+            const int Z = (a == 0 ? 1 : 0) | (b == 0 ? 2 : 0) | (cc == 0 ? 4 : 0);
+            int members = 0;
+            for (auto& o : kv.second) members |= 1 << ((o[0] < 0 ? 1 : 0) | (o[1] < 0 ? 2 : 0) | (o[2] < 0 ? 4 : 0));
+            std::vector<int> pp, ss;
+            split(kv.second, pp, ss);
+            if (class_adds(Z) + class_fmas(Z) < static_cast<int>(18 * pp.size() + 16 * ss.size())) {
+                cls[Z].push_back(kv.first | (members << 24));
+            } else {
+                pairs.insert(pairs.end(), pp.begin(), pp.end());
+                singles.insert(singles.end(), ss.begin(), ss.end());
+            }
+        }
+    };
+    std::vector<int> cfar[8][8], cfar_pair[8], cfar_single[8], cnear[8], cnear_pair, cnear_single;
+    for (int p = 0; p < 8; ++p) class_split(far_offs[p], cfar[p], cfar_pair[p], cfar_single[p]);
+    class_split(near_offs, cnear, cnear_pair, cnear_single);
+    for (int p = 1; p < 8; ++p) {
+        bool same = cfar_pair[p].size() == cfar_pair[0].size() && cfar_single[p].size() == cfar_single[0].size();
+        for (int z = 0; z < 8; ++z) same = same && cfar[p][z].size() == cfar[0][z].size();
+        if (!same) return fail(OT_EINVAL, "internal: parity class stencils differ in shape");
+    }
+    if (!cnear_single.empty()) return fail(OT_EINVAL, "internal: near class stencil not closed under negation");
+    Lists& Lh = g->Lh;
+    std::memset(&Lh, 0, sizeof(Lh));
+    Lh.far_len = g->far_len;
+    Lh.far_pairs = g->far_pairs;
+    Lh.near_len = g->near_len;
+    Lh.root_len = g->root_len;
+    Lh.near_off = 8 * g->far_len;
+    Lh.root_off = 8 * g->far_len + g->near_len;
+    Lh.cf_z[0] = 0;
+    for (int z = 0; z < 7; ++z) Lh.cf_z[z + 1] = Lh.cf_z[z] + static_cast<int>(cfar[0][z].size());
+    Lh.cf_pairs = static_cast<int>(cfar_pair[0].size());
+    Lh.cf_singles = static_cast<int>(cfar_single[0].size());
+    Lh.cf_stride = Lh.cf_z[7] + Lh.cf_pairs + Lh.cf_singles;
+    Lh.cf_off = static_cast<int>(g->lists.size());
+    for (int p = 0; p < 8; ++p) {
+        for (int z = 0; z < 7; ++z) g->lists.insert(g->lists.end(), cfar[p][z].begin(), cfar[p][z].end());
+        g->lists.insert(g->lists.end(), cfar_pair[p].begin(), cfar_pair[p].end());
+        g->lists.insert(g->lists.end(), cfar_single[p].begin(), cfar_single[p].end());
+    }
+    Lh.cn_z[0] = 0;
+    for (int z = 0; z < 7; ++z) Lh.cn_z[z + 1] = Lh.cn_z[z] + static_cast<int>(cnear[z].size());
+    Lh.cn_pairs = static_cast<int>(cnear_pair.size());
+    Lh.cn_off = static_cast<int>(g->lists.size());
+    for (int z = 0; z < 7; ++z) g->lists.insert(g->lists.end(), cnear[z].begin(), cnear[z].end());
+    g->lists.insert(g->lists.end(), cnear_pair.begin(), cnear_pair.end());
+    {
+        // every far and near offset exactly once
+        long long nf = 2LL * Lh.cf_pairs + Lh.cf_singles, nn = 2LL * Lh.cn_pairs;
+        for (int k = 0; k < Lh.cf_z[7]; ++k) nf += __builtin_popcount(static_cast<unsigned>(g->lists[Lh.cf_off + k]) >> 24);
+        for (int k = 0; k < Lh.cn_z[7]; ++k) nn += __builtin_popcount(static_cast<unsigned>(g->lists[Lh.cn_off + k]) >> 24);
+        if (nf != g->far_offsets || nn != 2LL * g->near_len)
+            return fail(OT_EINVAL, "internal: class stencils do not cover the offsets");
+    }
 
     // --- derivative table ----------------------------------------------------
     std::vector<double> Dt(static_cast<size_t>(NOFF) * DROW, 0.0);
@@ -529,8 +609,74 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             }
         }
     }
+    // The class lists of leaf targets (point masses): per warp pattern and
+    // entry the neighbours its members reach; per entry its FP64 instructions
+    // per lane (forward, scatter adjoint), members and FLOPs; per neighbour
+    // the FLOPs of the pairs landing there over all 512 cells, an entry's
+    // FLOPs shared equally by its members.
+    const int cseg_len[2] = {g->Lh.cf_stride, g->Lh.cn_z[7] + g->Lh.cn_pairs};
+    std::vector<uint32_t> cmask[16][2];
+    std::vector<int> ccost_f[2], ccost_s[2], cmem[2];
+    double cfl_f[2][27], cfl_s[2][27];
+    std::memset(cfl_f, 0, sizeof(cfl_f));
+    std::memset(cfl_s, 0, sizeof(cfl_s));
+    for (int cg = 0; cg < 2; ++cg) {
+        const int nz = cg == 0 ? g->Lh.cf_z[7] : g->Lh.cn_z[7];
+        const int npair = cg == 0 ? g->Lh.cf_pairs : g->Lh.cn_pairs;
+        ccost_f[cg].resize(cseg_len[cg]);
+        ccost_s[cg].resize(cseg_len[cg]);
+        cmem[cg].resize(cseg_len[cg]);
+        for (int ph = 0; ph < 16; ++ph) {
+            const int par = ph >> 1, half = ph & 1;
+            const int* lst = &g->lists[cg == 0 ? g->Lh.cf_off + par * g->Lh.cf_stride : g->Lh.cn_off];
+            cmask[ph][cg].resize(cseg_len[cg]);
+            for (int k = 0; k < cseg_len[cg]; ++k) {
+                const int e = lst[k];
+                std::vector<std::array<int, 3>> mem;
+                int cf, cs, fl_f, fl_s;
+                if (k < nz) {
+                    const int a = e & 0xff, b = (e >> 8) & 0xff, cc = (e >> 16) & 0xff;
+                    const int Z = (a == 0 ? 1 : 0) | (b == 0 ? 2 : 0) | (cc == 0 ? 4 : 0);
+                    for (int t = 0; t < 8; ++t)
+                        if ((static_cast<unsigned>(e) >> 24 >> t) & 1u)
+                            mem.push_back({t & 1 ? -a : a, t & 2 ? -b : b, t & 4 ? -cc : cc});
+                    cf = cs = class_adds(Z) + class_fmas(Z);
+                    fl_f = fl_s = class_adds(Z) + 2 * class_fmas(Z);
+                } else {
+                    const int ox = (e & 0xff) - 8, oy = ((e >> 8) & 0xff) - 8, oz = ((e >> 16) & 0xff) - 8;
+                    mem.push_back({ox, oy, oz});
+                    if (k < nz + npair) {
+                        mem.push_back({-ox, -oy, -oz});
+                        cf = cs = 18;
+                        fl_f = fl_s = 34;
+                    } else {
+                        cf = 16;
+                        cs = 17;
+                        fl_f = fl_s = 32;
+                    }
+                }
+                ccost_f[cg][k] = cf;
+                ccost_s[cg][k] = cs;
+                cmem[cg][k] = static_cast<int>(mem.size());
+                uint32_t m = 0;
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int tx = (par & 1) + 2 * (lane & 3), ty = ((par >> 1) & 1) + 2 * ((lane >> 2) & 3),
+                              tz = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
+                    for (auto& o : mem) {
+                        const int nb = ((tx + o[0] + 8) >> 3) + 3 * ((ty + o[1] + 8) >> 3) + 9 * ((tz + o[2] + 8) >> 3);
+                        m |= 1u << nb;
+                        cfl_f[cg][nb] += static_cast<double>(fl_f) / mem.size();
+                        cfl_s[cg][nb] += static_cast<double>(fl_s) / mem.size();
+                    }
+                }
+                cmask[ph][cg][k] = m;
+            }
+        }
+    }
     // algorithmic FLOPs per in-domain pair (2 per FMA, 1 per add):
     //   point mass 32, or 17 in a paired entry (16 FMA + 2 adds per two pairs);
+    //   point masses at leaf targets (level > 0) by class: class_adds +
+    //   2 class_fmas per class entry, shared by its members;
     //   multipole 140 (200 with the angular term), or 86 (116) paired;
     //   adjoint: point mass 32, multipole 140, or 86 paired.
     // FP64 instructions per lane and active entry (empty lanes included):
@@ -547,6 +693,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     long long flops_fwd_com = 0, flops_adj_com = 0;   // explicit centres (see ot_interactions_com)
     std::vector<std::pair<long long, int>> fwd[4];
     std::vector<int> node_order_items;
+    std::vector<long long> node_cost(n, 0);   // largest item of the node (both passes)
+    long long total_cost = 0;
     g->node_item_start.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) {
         uint32_t mm = 0, mo = 0, mv = 0;
@@ -558,6 +706,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         }
         const bool leaf = g->is_leaf[i];
         const int s1 = (desc->level[i] == 0) ? 2 : 0;
+        const bool by_class = leaf && desc->level[i] > 0;   // point masses by reflection class
         for (int j = 0; j < 27; ++j) {
             const long long cpf = cnt[s1][1][j], csf = cnt[s1][0][j];                 // far / root
             const long long cpn = leaf ? cnt[1][1][j] : 0, csn = leaf ? cnt[1][0][j] : 0;   // near
@@ -583,8 +732,13 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             }
             if (mo >> j & 1u) {
                 pairs_mono += cp + cs;
-                flops_fwd += 17 * cp + 32 * cs;
-                flops_adj_scat += 16 * cp + 32 * cs;
+                if (by_class) {
+                    flops_fwd += std::llround(cfl_f[0][j] + cfl_f[1][j]);
+                    flops_adj_scat += std::llround(cfl_s[0][j] + cfl_s[1][j]);
+                } else {
+                    flops_fwd += 17 * cp + 32 * cs;
+                    flops_adj_scat += 16 * cp + 32 * cs;
+                }
                 // explicit centres: a leaf target reads the table, a non-leaf one evaluates
                 flops_fwd_com += leaf ? 17 * cp + 32 * cs : (cp + cs) * (deriv_flops(16) + 32);
                 flops_adj_com += leaf ? 16 * cp + 32 * cs : (cp + cs) * (deriv_flops(16) + 32);
@@ -612,12 +766,32 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     }
                 }
             };
-            scan(s1);
-            if (leaf) scan(1);
+            if (by_class) {
+                // multipole sources (refined neighbours) by the full lists, point
+                // masses by class
+                const uint32_t mo_keep = mo;
+                mo = 0;
+                scan(s1);
+                scan(1);
+                mo = mo_keep;
+                long long cost_s = cost[2];    // refined near sources
+                for (int cg = 0; cg < 2; ++cg)
+                    for (size_t k = 0; k < cmask[ph][cg].size(); ++k)
+                        if (cmask[ph][cg][k] & mo) {
+                            cost[2] += ccost_f[cg][k];
+                            cost_s += ccost_s[cg][k];
+                            lanes += 32;
+                            padded += 32 * cmem[cg][k];
+                        }
+                ops_adj_scat += 32 * cost_s;
+            } else {
+                scan(s1);
+                if (leaf) scan(1);
+                // the point-mass adjoint organised by target walks the same active
+                // entries: 16 products + 2 adds per paired entry, 16 + 1 single
+                ops_adj_scat += 32 * (cost[2] - count_single_mono);
+            }
             ops_fwd += 32 * (cost[1] + cost[2]);
-            // the point-mass adjoint organised by target walks the same active
-            // entries: 16 products + 2 adds per paired entry, 16 + 1 single
-            ops_adj_scat += 32 * (cost[2] - count_single_mono);
             count_single_mono = 0;
             const int item = (i << 4) | ph;
             node_order_items.push_back(item);
@@ -625,6 +799,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 long long cst = ((mode & 1) ? cost[1] : 0) + ((mode & 2) ? cost[2] : 0);
                 if (cst > 0) fwd[mode].emplace_back(cst, item);
             }
+            node_cost[i] = std::max(node_cost[i], cost[1] + cost[2]);
+            total_cost += cost[1] + cost[2];
         }
     }
     g->node_item_start[n] = static_cast<int>(node_order_items.size());
@@ -633,6 +809,53 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                          [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
                              return a.first > b.first;
                          });
+    // Long items split into list chunks.  A warp shares its scheduler's FP64
+    // unit with the other resident warps for the whole launch, so an item
+    // whose work is a large share of one SM's (the root's walk of its 3196
+    // offsets, the coarse levels' far lists) would finish last by a wide
+    // margin.  Items of a node whose largest item exceeds
+    // cap = total / (SMs * 32) run as K = ceil(largest / cap) <= 16 chunks
+    // (every walked list cut into K equal ranges); each chunk leaves its
+    // accumulators in a partial slot and the node's last chunk to finish sums
+    // the K slots in chunk order and stores (the same bits whatever the
+    // schedule).  The multipole and fused passes use the chunked lists; the
+    // point-mass pass and its adjoint keep whole items.
+    {
+        const long long cap = std::max<long long>(1024, total_cost / (32LL * std::max(g->num_sms, 1)));
+        std::vector<int> nchunk(n, 1);
+        g->cinfo.assign(n, int2{-1, 0});
+        int slots = 0, ctrs = 0;
+        for (int i = 0; i < n; ++i) {
+            const long long k = (node_cost[i] + cap - 1) / cap;
+            nchunk[i] = static_cast<int>(std::min<long long>(16, std::max<long long>(1, k)));
+            if (nchunk[i] > 1) {
+                g->cinfo[i] = int2{slots, (ctrs << 4) | (nchunk[i] - 1)};
+                slots += 16 * nchunk[i];
+                ctrs += 16;
+            }
+        }
+        g->n_part_slots = slots;
+        g->n_chunk_ctrs = ctrs;
+        for (int mode = 1; mode <= 3; mode += 2) {
+            std::vector<std::pair<long long, int>> v;
+            for (auto& pr : fwd[mode]) {
+                const int k = nchunk[pr.second >> 4];
+                for (int c = 0; c < k; ++c) v.emplace_back(pr.first / k, pr.second | (c << 26));
+            }
+            std::stable_sort(v.begin(), v.end(), [](const std::pair<long long, int>& a,
+                                                    const std::pair<long long, int>& b) { return a.first > b.first; });
+            g->itemsc_fwd[mode].clear();
+            for (auto& pr : v) g->itemsc_fwd[mode].push_back(pr.second);
+        }
+        g->itemc_node_start.assign(n + 1, 0);
+        g->itemsc_node.clear();
+        for (int i = 0; i < n; ++i) {
+            g->itemc_node_start[i] = static_cast<int>(g->itemsc_node.size());
+            for (int ph = 0; ph < 16; ++ph)
+                for (int c = 0; c < nchunk[i]; ++c) g->itemsc_node.push_back((i << 4) | ph | (c << 26));
+        }
+        g->itemc_node_start[n] = static_cast<int>(g->itemsc_node.size());
+    }
     // adjoint items: real sources by class, virtual sources (point masses)
     std::vector<std::pair<long long, int>> adj[4];
     std::vector<int> adj_node[4];
@@ -689,7 +912,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                          [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
                              return a.first > b.first;
                          });
-    if (static_cast<long long>(n + g->nvirt) >= (1LL << 26)) return fail(OT_EINVAL, "too many sub-grids");
+    // forward items hold the node in bits 4-25 (chunk index in 26-29), adjoint
+    // items the source in bits 4-29
+    if (n >= (1 << 22) || static_cast<long long>(n + g->nvirt) >= (1LL << 26))
+        return fail(OT_EINVAL, "too many sub-grids");
     // the default adjoint: point-mass scatter items (forward items of the
     // point-mass class, flagged with bit 30) merged with the multipole gather
     // items, longest first, in one persistent launch
@@ -801,6 +1027,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.pairs_angular = pairs_ang;
     I.lanes_fwd = lanes;
     I.pairs_padded_fwd = padded;
+    I.chunked_subgrids = g->n_chunk_ctrs / 16;
     I.flops_fwd = flops_fwd;
     g->flops_adj_det = flops_adj;
     g->ops_adj_det = ops_adj;
@@ -864,6 +1091,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         UP(g->d_Dt2, Dt2);
     }
     UP(g->d_lists, g->lists);
+    g->Lh.lists = g->d_lists;
     std::vector<double> hv(g->hinv, g->hinv + MAXLEV);
     UP(g->d_hinv, hv);
     for (int mode = 1; mode <= 3; ++mode) {
@@ -878,6 +1106,12 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         UP(g->d_items_adj_node[mode], adj_node[mode]);
     }
     UP(g->d_items_fwd_node, node_order_items);
+    for (int mode = 1; mode <= 3; mode += 2) {
+        g->n_itemsc_fwd[mode] = static_cast<int>(g->itemsc_fwd[mode].size());
+        UP(g->d_itemsc_fwd[mode], g->itemsc_fwd[mode]);
+    }
+    UP(g->d_itemsc_node, g->itemsc_node);
+    UP(g->d_cinfo, g->cinfo);
     for (int k = 0; k < 2; ++k) {
         std::vector<int> items;
         for (auto& pr : fast[k]) items.push_back(pr.second);
@@ -902,6 +1136,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if ((st = g->alloc(&g->d_mf, static_cast<size_t>(n) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mf, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_counters, 4)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_part, static_cast<size_t>(std::max(g->n_part_slots, 1)) * PART_VALS * 32)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_chunk_ctr, static_cast<size_t>(std::max(g->n_chunk_ctrs, 1)))) != OT_OK) return st;
     if ((st = g->alloc(&g->d_status, 2)) != OT_OK) return st;
     OT_CUDA(cudaMemsetAsync(g->d_status, 0, 2 * sizeof(int), s));
     OT_CUDA(cudaMemsetAsync(g->d_counters, 0, 4 * sizeof(int), s));
@@ -927,13 +1163,7 @@ static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, 
     p.nbr = g->d_nbr;
     p.ninfo = g->d_ninfo;
     p.Dt = g->d_Dt;
-    p.L.lists = g->d_lists;
-    p.L.far_len = g->far_len;
-    p.L.far_pairs = g->far_pairs;
-    p.L.near_len = g->near_len;
-    p.L.root_len = g->root_len;
-    p.L.near_off = 8 * g->far_len;
-    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.L = g->Lh;
     p.Mhat = g->d_Mhat;
     p.m = m;
     p.Lout = L;
@@ -978,18 +1208,27 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         p.Dt2 = g->d_Dt2;
     }
     // zeroed above, so the kernel always accumulates
+    const bool chunked = (mode & 1) != 0;     // the multipole and fused passes run chunked items
+    if (chunked) {
+        p.cinfo = g->d_cinfo;
+        p.part = g->d_part;
+        p.chunk_ctr = g->d_chunk_ctr;
+        if (g->n_chunk_ctrs > 0)
+            OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs) * sizeof(int), s));
+    }
     if (g->schedule == OT_SCHED_PER_SUBGRID) {
-        p.items = g->d_items_fwd_node;
+        const int* base = chunked ? g->d_itemsc_node : g->d_items_fwd_node;
+        const std::vector<int>& start = chunked ? g->itemc_node_start : g->node_item_start;
         for (int i = 0; i < g->n; ++i) {
             FwdParams q = p;
-            q.items = g->d_items_fwd_node + g->node_item_start[i];
-            q.n_items = g->node_item_start[i + 1] - g->node_item_start[i];
+            q.items = base + start[i];
+            q.n_items = start[i + 1] - start[i];
             const int blocks = (q.n_items + g->wpb - 1) / g->wpb;
             OT_CUDA(launch_forward(q, mode, false, g->wpb, blocks, s));
         }
     } else {
-        p.items = g->d_items_fwd[mode];
-        p.n_items = g->n_items_fwd[mode];
+        p.items = chunked ? g->d_itemsc_fwd[mode] : g->d_items_fwd[mode];
+        p.n_items = chunked ? g->n_itemsc_fwd[mode] : g->n_items_fwd[mode];
         OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
         const int maxb = emu2 ? g->maxb_emu2[mode][g->wpb]
                          : emu ? g->maxb_emu[mode][g->wpb] : g->maxb_fwd[mode][g->wpb];
@@ -1005,13 +1244,7 @@ static ot_status enqueue_scatter(ot_grid* g, double* mbar, cudaStream_t s) {
     p.nbr = g->d_nbr;
     p.ninfo = g->d_ninfo;
     p.Dt = g->d_Dt;
-    p.L.lists = g->d_lists;
-    p.L.far_len = g->far_len;
-    p.L.far_pairs = g->far_pairs;
-    p.L.near_len = g->near_len;
-    p.L.root_len = g->root_len;
-    p.L.near_off = 8 * g->far_len;
-    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.L = g->Lh;
     p.Lrbar = g->d_Lrbar;
     p.mbar = mbar;
     p.n_nodes = g->n;
@@ -1065,13 +1298,7 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     p.ninfo = g->d_ninfo;
     p.vinfo = g->d_vinfo;
     p.Dt = g->d_Dt;
-    p.L.lists = g->d_lists;
-    p.L.far_len = g->far_len;
-    p.L.far_pairs = g->far_pairs;
-    p.L.near_len = g->near_len;
-    p.L.root_len = g->root_len;
-    p.L.near_off = 8 * g->far_len;
-    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.L = g->Lh;
     p.Lrbar = g->d_Lrbar;
     p.Mbar = Mbar;
     p.mbar = mbar;
@@ -1188,13 +1415,7 @@ static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const doub
     p.ninfo = g->d_ninfo;
     p.vinfo = g->d_vinfo;
     p.Dt = g->d_Dt;
-    p.L.lists = g->d_lists;
-    p.L.far_len = g->far_len;
-    p.L.far_pairs = g->far_pairs;
-    p.L.near_len = g->near_len;
-    p.L.root_len = g->root_len;
-    p.L.near_off = 8 * g->far_len;
-    p.L.root_off = 8 * g->far_len + g->near_len;
+    p.L = g->Lh;
     p.Lrbar = g->d_Lrbar;
     p.Mbar = Mbar;
     p.mbar = mbar;
@@ -1457,7 +1678,10 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     if (n_streams < 1 || n_streams > 128) return fail(OT_EINVAL, "n_streams must be in [1, 128]");
     if (!(timeout_s > 0.0)) return fail(OT_EINVAL, "timeout_s must be positive");
     std::memset(out, 0, sizeof(*out));
-    // set-up (untimed): pre-scaled moments, zeroed outputs
+    // set-up (untimed): pre-scaled moments, zeroed outputs.  The study runs on
+    // streams of its own that do not order after the caller's: work already
+    // queued on this grid (its scratch, queue and chunk counters) finishes first.
+    OT_CUDA(cudaDeviceSynchronize());
     std::vector<cudaStream_t> streams(n_streams, nullptr);
     for (auto& st : streams) OT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     struct StreamGuard {
@@ -1475,6 +1699,15 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     OT_CUDA(cudaMemsetAsync(L, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), streams[0]));
     OT_CUDA(cudaDeviceSynchronize());
     FwdParams p = fwd_params(g, m, L, Lc, 1);
+    // the per-sub-grid launches run the batched launch's chunked items (the
+    // same summation order); chunk counters zeroed once, each node owns its own
+    p.cinfo = g->d_cinfo;
+    p.part = g->d_part;
+    p.chunk_ctr = g->d_chunk_ctr;
+    if (g->n_chunk_ctrs > 0) {
+        OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs) * sizeof(int), streams[0]));
+        OT_CUDA(cudaStreamSynchronize(streams[0]));
+    }
     const int n = g->n;
     std::vector<CompletionSlot> slots(n);
     std::atomic<int> done_count{0};
@@ -1535,8 +1768,8 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
         for (int i = 0; i < n; ++i) {
             cudaStream_t s = streams[i % n_streams];
             FwdParams q = p;
-            q.items = g->d_items_fwd_node + g->node_item_start[i];
-            q.n_items = g->node_item_start[i + 1] - g->node_item_start[i];
+            q.items = g->d_itemsc_node + g->itemc_node_start[i];
+            q.n_items = g->itemc_node_start[i + 1] - g->itemc_node_start[i];
             slots[i].counter = &done_count;
             slots[i].submitted = Clock::now();
             OT_CUDA(launch_forward(q, 3, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s));
