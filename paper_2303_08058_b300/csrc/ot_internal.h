@@ -129,6 +129,11 @@ struct AdjParams {
     const float2* Lf;      // [n][16][512] reduced L-bar as (hi, lo) pairs
     const float2* Dt2;     // [NOFF][DROW] the derivative table as (hi, lo) pairs
     const float* Dt32;     // [NOFF][32] hi then lo parts of the 16 point-mass derivatives
+    // chunked multipole gather items (bit 31 set: source in bits 4-25, chunk
+    // index in bits 26-29); null: every item is whole
+    const int2* cinfo;     // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
+    double* part;          // [slots][NRED][32] chunk accumulators
+    int* chunk_ctr;        // [counters] chunks finished per (source, parity, half), zeroed per launch
 };
 
 // point-mass adjoint organised by target cells (the forward's walk) with the

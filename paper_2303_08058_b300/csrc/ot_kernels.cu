@@ -652,40 +652,52 @@ struct Chunk {
     __device__ __forceinline__ int n(int len) const { return len * (c + 1) / k - len * c / k; }
 };
 
-// the chunk's accumulators into its partial slot; true for the last chunk of
-// the (node, parity, half) to finish, which then holds the sum of all chunks
-// in chunk order (the same bits whichever chunk finishes last)
-__device__ __forceinline__ bool chunk_combine(const FwdParams& p, int2 ci, int ph, Chunk ch, int lane,
-                                              double (&a)[16], double (&c)[3], double (&t4)[9]) {
-    double* slot = p.part + static_cast<size_t>(ci.x + ph * ch.k + ch.c) * PART_VALS * 32 + lane;
+// the chunk's NV accumulators into its partial slot; true for the last chunk
+// of the (node, parity, half) to finish, which then holds the sum of all
+// chunks in chunk order (the same bits whichever chunk finishes last).  Each
+// lane's stores are fenced before lane 0 counts the chunk; the last chunk
+// fences again before it reads the slots (L1 bypassed).  Nothing waits.
+template <int NV>
+__device__ __forceinline__ bool chunk_combine(double* part, int* ctr, int2 ci, int ph, Chunk ch, int lane,
+                                              double (&v)[NV]) {
+    double* slot = part + static_cast<size_t>(ci.x + ph * ch.k + ch.c) * NV * 32 + lane;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) __stcg(slot + q * 32, a[q]);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) __stcg(slot + (16 + q) * 32, c[q]);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) __stcg(slot + (19 + q) * 32, t4[q]);
+    for (int q = 0; q < NV; ++q) __stcg(slot + q * 32, v[q]);
     __threadfence();
     __syncwarp();
     int last = 0;
-    if (lane == 0) last = atomicAdd(p.chunk_ctr + (ci.y >> 4) + ph, 1) == ch.k - 1;
+    if (lane == 0) last = atomicAdd(ctr + (ci.y >> 4) + ph, 1) == ch.k - 1;
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return false;
     __threadfence();
 #pragma unroll
-    for (int q = 0; q < 16; ++q) a[q] = 0.0;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) c[q] = 0.0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) t4[q] = 0.0;
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
     for (int j = 0; j < ch.k; ++j) {
-        const double* src = p.part + static_cast<size_t>(ci.x + ph * ch.k + j) * PART_VALS * 32 + lane;
+        const double* src = part + static_cast<size_t>(ci.x + ph * ch.k + j) * NV * 32 + lane;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) a[q] += __ldcg(src + q * 32);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) c[q] += __ldcg(src + (16 + q) * 32);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) t4[q] += __ldcg(src + (19 + q) * 32);
+        for (int q = 0; q < NV; ++q) v[q] += __ldcg(src + q * 32);
     }
+    return true;
+}
+
+// the forward's accumulators: the 16 coefficients, the angular term's source
+// and target parts
+__device__ __forceinline__ bool chunk_combine_fwd(const FwdParams& p, int2 ci, int ph, Chunk ch, int lane,
+                                                  double (&a)[16], double (&c)[3], double (&t4)[9]) {
+    double v[PART_VALS];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = a[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[16 + q] = c[q];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[19 + q] = t4[q];
+    if (!chunk_combine(p.part, p.chunk_ctr, ci, ph, ch, lane, v)) return false;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) a[q] = v[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) c[q] = v[16 + q];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) t4[q] = v[19 + q];
     return true;
 }
 
@@ -779,7 +791,7 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
                                                     false, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
         }
         if (EMU) df_flush_all<(EMU & 2) != 0>(a, c, t4, f);
-        if (ch.k == 1 || chunk_combine(p, ci, item & 15, ch, lane, a, c, t4))
+        if (ch.k == 1 || chunk_combine_fwd(p, ci, item & 15, ch, lane, a, c, t4))
             store_forward<MODE>(p, node, level, leafT, tx + 8 * ty + 64 * tz, a, c, t4);
         __syncwarp();
         if (!persistent) break;
@@ -1002,7 +1014,23 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
             if (!persistent) break;
             continue;
         }
-        const int src = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        Chunk ch{0, 1};
+        int2 ci = make_int2(-1, 0);
+        int src = item >> 4;
+        if (item < 0) {            // a chunk of a multipole gather item
+            src = (item >> 4) & 0x3fffff;
+            ch.c = (item >> 26) & 15;
+            if (p.cinfo != nullptr && src < p.n_nodes) {
+                ci = __ldg(p.cinfo + src);
+                if (ci.x >= 0) ch.k = (ci.y & 15) + 1;
+            }
+            if (ch.c >= ch.k) {
+                report(p.status, 6, it);
+                if (!persistent) break;
+                continue;
+            }
+        }
+        const int par = (item >> 1) & 7, half = item & 1;
         const bool virt = src >= p.n_nodes;
         const int2* nbt = virt ? p.vnbr + static_cast<size_t>(src - p.n_nodes) * 27
                                : p.nbr + static_cast<size_t>(src) * 27;
@@ -1036,18 +1064,21 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
             // of a refined cell see its children instead
             if ((MODE & 1) && p.Mbar != nullptr) {
                 if (level == 0) {
-                    walk_adjoint<true, true, EMU>(l1, n1, false, false, sx, sy, sz, s_nb[warp], p, g, g4, f, it);
+                    walk_adjoint<true, true, EMU>(l1 + ch.lo(n1), ch.n(n1), false, false, sx, sy, sz, s_nb[warp], p, g,
+                                                  g4, f, it);
                 } else {
-                    walk_adjoint<true, true, EMU>(l1, p.L.far_pairs, false, false, sx, sy, sz, s_nb[warp], p, g, g4,
-                                                  f, it);
-                    walk_adjoint<true, false, EMU>(l1 + p.L.far_pairs, n1 - p.L.far_pairs, false, false, sx, sy, sz,
+                    const int ns = n1 - p.L.far_pairs;
+                    walk_adjoint<true, true, EMU>(l1 + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), false, false, sx,
+                                                  sy, sz, s_nb[warp], p, g, g4, f, it);
+                    walk_adjoint<true, false, EMU>(l1 + p.L.far_pairs + ch.lo(ns), ch.n(ns), false, false, sx, sy, sz,
                                                    s_nb[warp], p, g, g4, f, it);
                 }
                 if (EMU) {
                     double dc[3], dt[9];
                     df_flush_all<false>(g, dc, dt, f);
                 }
-                store_mbar(p.Mbar, src, scell, h1, g);
+                if (ch.k == 1 || chunk_combine(p.part, p.chunk_ctr, ci, item & 15, ch, lane, g))
+                    store_mbar(p.Mbar, src, scell, h1, g);
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
             const bool vt = skind == K_LEAF;   // real leaf cells also feed coarse leaves' virtual children

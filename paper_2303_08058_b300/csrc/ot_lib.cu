@@ -194,6 +194,17 @@ struct ot_grid {
     int2* d_cinfo = nullptr;
     double* d_part = nullptr;           // [slots][28][32] chunk accumulators
     int* d_chunk_ctr = nullptr;         // [counters] chunks finished per (node, parity, half)
+    // chunked multipole gather items of the adjoint (modes 1 and 3, and the
+    // default adjoint's merged list); they share d_part and d_chunk_ctr
+    std::vector<int> itemsc_adj[4], itemsc_adj_node[4], itemc_adj_start[4], itemsc_adj_fast1;
+    std::vector<int2> cinfo_adj;
+    int n_part_slots_adj = 0, n_chunk_ctrs_adj = 0;
+    int* d_itemsc_adj[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n_itemsc_adj[4] = {0, 0, 0, 0};
+    int* d_itemsc_adj_node[4] = {nullptr, nullptr, nullptr, nullptr};
+    int* d_itemsc_adj_fast1 = nullptr;
+    int n_itemsc_adj_fast1 = 0;
+    int2* d_cinfo_adj = nullptr;
     std::vector<int> node_item_start;                                // [n + 1] into d_items_fwd_node
     int* d_items_adj[4] = {nullptr, nullptr, nullptr, nullptr};
     int n_items_adj[4] = {0, 0, 0, 0};
@@ -859,6 +870,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // adjoint items: real sources by class, virtual sources (point masses)
     std::vector<std::pair<long long, int>> adj[4];
     std::vector<int> adj_node[4];
+    std::vector<long long> adj_node_cost(n, 0);   // largest multipole gather item of a real non-leaf source
+    long long total_adj_cost = 0;
     for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode].assign(n + g->nvirt + 1, 0);
     for (int i = 0; i < n + g->nvirt; ++i) {
         const bool virt = i >= n;
@@ -897,7 +910,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     if (mask[ph][1][k] & (tl | tw)) cst += 32;
             if (cst == 0) continue;
             ops_adj += 32 * cst;
-            if (!leaf) ops_adj_multi += 32 * cst;
+            if (!leaf) {
+                ops_adj_multi += 32 * cst;
+                adj_node_cost[i] = std::max(adj_node_cost[i], cst);
+                total_adj_cost += cst;
+            }
             const int item = (i << 4) | ph;
             for (int mode = 1; mode <= 3; ++mode)
                 if (mode & bit) {
@@ -930,6 +947,64 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                          [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
                              return a.first > b.first;
                          });
+    // Multipole gather items split into list chunks as the forward's are
+    // (a source's gather walks the transposed stencil: the same long lists
+    // at the root and the coarse levels).  A chunked item sets bit 31 and
+    // holds the source in bits 4-25, the chunk index in bits 26-29.
+    {
+        const long long cap = std::max<long long>(1024, total_adj_cost / (32LL * std::max(g->num_sms, 1)));
+        std::vector<int> nchunk(n, 1);
+        g->cinfo_adj.assign(n, int2{-1, 0});
+        int slots = 0, ctrs = 0;
+        for (int i = 0; i < n; ++i) {
+            const long long k = (adj_node_cost[i] + cap - 1) / cap;
+            nchunk[i] = static_cast<int>(std::min<long long>(16, std::max<long long>(1, k)));
+            if (nchunk[i] > 1) {
+                g->cinfo_adj[i] = int2{slots, (ctrs << 4) | (nchunk[i] - 1)};
+                slots += 16 * nchunk[i];
+                ctrs += 16;
+            }
+        }
+        g->n_part_slots_adj = slots;
+        g->n_chunk_ctrs_adj = ctrs;
+        auto chunk_list = [&](const std::vector<std::pair<long long, int>>& in, std::vector<int>& out) {
+            std::vector<std::pair<long long, int>> v;
+            for (auto& pr : in) {
+                const int src = (pr.second >> 4) & 0x3ffffff;
+                const bool gather = !((pr.second >> 30) & 1) && src < n;
+                const int k = gather ? nchunk[src] : 1;
+                if (k == 1) {
+                    v.push_back(pr);
+                } else {
+                    for (int c = 0; c < k; ++c)
+                        v.emplace_back(pr.first / k, static_cast<int>(0x80000000u | static_cast<unsigned>(
+                                                                         (src << 4) | (pr.second & 15) | (c << 26))));
+                }
+            }
+            std::stable_sort(v.begin(), v.end(), [](const std::pair<long long, int>& a,
+                                                    const std::pair<long long, int>& b) { return a.first > b.first; });
+            out.clear();
+            for (auto& pr : v) out.push_back(pr.second);
+        };
+        for (int mode = 1; mode <= 3; mode += 2) {
+            chunk_list(adj[mode], g->itemsc_adj[mode]);
+            // source order (plain path)
+            g->itemc_adj_start[mode].assign(n + g->nvirt + 1, 0);
+            g->itemsc_adj_node[mode].clear();
+            for (int i = 0; i < n + g->nvirt; ++i) {
+                g->itemc_adj_start[mode][i] = static_cast<int>(g->itemsc_adj_node[mode].size());
+                for (int t = g->adj_item_start[mode][i]; t < g->adj_item_start[mode][i + 1]; ++t) {
+                    const int item = adj_node[mode][t];
+                    const int k = i < n ? nchunk[i] : 1;
+                    for (int c = 0; c < k; ++c)
+                        g->itemsc_adj_node[mode].push_back(
+                            k == 1 ? item : static_cast<int>(0x80000000u | static_cast<unsigned>(item | (c << 26))));
+                }
+            }
+            g->itemc_adj_start[mode][n + g->nvirt] = static_cast<int>(g->itemsc_adj_node[mode].size());
+        }
+        chunk_list(fast[1], g->itemsc_adj_fast1);
+    }
 
     // --- coarse leaf targets next to refined sub-grids ------------------------
     // A leaf's near sources in a refined neighbour are replaced by that
@@ -1112,6 +1187,14 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     }
     UP(g->d_itemsc_node, g->itemsc_node);
     UP(g->d_cinfo, g->cinfo);
+    for (int mode = 1; mode <= 3; mode += 2) {
+        g->n_itemsc_adj[mode] = static_cast<int>(g->itemsc_adj[mode].size());
+        UP(g->d_itemsc_adj[mode], g->itemsc_adj[mode]);
+        UP(g->d_itemsc_adj_node[mode], g->itemsc_adj_node[mode]);
+    }
+    g->n_itemsc_adj_fast1 = static_cast<int>(g->itemsc_adj_fast1.size());
+    UP(g->d_itemsc_adj_fast1, g->itemsc_adj_fast1);
+    UP(g->d_cinfo_adj, g->cinfo_adj);
     for (int k = 0; k < 2; ++k) {
         std::vector<int> items;
         for (auto& pr : fast[k]) items.push_back(pr.second);
@@ -1136,8 +1219,13 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if ((st = g->alloc(&g->d_mf, static_cast<size_t>(n) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mf, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_counters, 4)) != OT_OK) return st;
-    if ((st = g->alloc(&g->d_part, static_cast<size_t>(std::max(g->n_part_slots, 1)) * PART_VALS * 32)) != OT_OK) return st;
-    if ((st = g->alloc(&g->d_chunk_ctr, static_cast<size_t>(std::max(g->n_chunk_ctrs, 1)))) != OT_OK) return st;
+    {
+        const size_t part = std::max<size_t>({static_cast<size_t>(g->n_part_slots) * PART_VALS,
+                                              static_cast<size_t>(g->n_part_slots_adj) * NRED, 1});
+        const size_t ctrs = std::max({g->n_chunk_ctrs, g->n_chunk_ctrs_adj, 1});
+        if ((st = g->alloc(&g->d_part, part * 32)) != OT_OK) return st;
+        if ((st = g->alloc(&g->d_chunk_ctr, ctrs)) != OT_OK) return st;
+    }
     if ((st = g->alloc(&g->d_status, 2)) != OT_OK) return st;
     OT_CUDA(cudaMemsetAsync(g->d_status, 0, 2 * sizeof(int), s));
     OT_CUDA(cudaMemsetAsync(g->d_counters, 0, 4 * sizeof(int), s));
@@ -1290,8 +1378,18 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     }
     AdjParams p;
     std::memset(&p, 0, sizeof(p));
-    p.items = g->d_items_adj[mode];
-    p.n_items = g->n_items_adj[mode];
+    // multipole gathers (modes 1 and 3, and the merged default list) run the
+    // chunked items
+    const bool chunked = (mode & 1) != 0;
+    p.items = chunked ? g->d_itemsc_adj[mode] : g->d_items_adj[mode];
+    p.n_items = chunked ? g->n_itemsc_adj[mode] : g->n_items_adj[mode];
+    if (chunked) {
+        p.cinfo = g->d_cinfo_adj;
+        p.part = g->d_part;
+        p.chunk_ctr = g->d_chunk_ctr;
+        if (g->n_chunk_ctrs_adj > 0)
+            OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs_adj) * sizeof(int), s));
+    }
     p.counter = g->d_counters + 1;
     p.nbr = g->d_nbr;
     p.vnbr = g->d_vnbr;
@@ -1310,10 +1408,11 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     for (int l = 0; l < MAXLEV; ++l) p.hinv[l] = g->hinv[l];
     if (g->schedule == OT_SCHED_PER_SUBGRID) {
         // one launch per source sub-grid (real and virtual)
-        const std::vector<int>& st = g->adj_item_start[mode];
+        const std::vector<int>& st = chunked ? g->itemc_adj_start[mode] : g->adj_item_start[mode];
+        const int* base = chunked ? g->d_itemsc_adj_node[mode] : g->d_items_adj_node[mode];
         for (int i = 0; i + 1 < static_cast<int>(st.size()); ++i) {
             AdjParams q = p;
-            q.items = g->d_items_adj_node[mode] + st[i];
+            q.items = base + st[i];
             q.n_items = st[i + 1] - st[i];
             if (q.n_items == 0) continue;
             OT_CUDA(launch_adjoint(q, mode, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s));
@@ -1322,8 +1421,8 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
         // one persistent launch: multipole gather items (if Mbar) and
         // point-mass scatter items, longest first
         const int k = (mode & 1) ? 1 : 0;
-        p.items = g->d_items_adj_fast[k];
-        p.n_items = g->n_items_adj_fast[k];
+        p.items = k ? g->d_itemsc_adj_fast1 : g->d_items_adj_fast[0];
+        p.n_items = k ? g->n_itemsc_adj_fast1 : g->n_items_adj_fast[0];
         int maxb = k ? g->maxb_fast5[g->wpb] : g->maxb_adj[0][g->wpb];
         if (g->precision == OT_PREC_DF64) {
             // double-float: L-bar split into (hi, lo) pairs in the moments'
