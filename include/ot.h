@@ -287,10 +287,13 @@ ot_status ot_set_deterministic(ot_grid* grid, int32_t on);
 ot_status ot_set_schedule(ot_grid* grid, int32_t schedule, int32_t warps_per_block,
                           int32_t blocks_per_sm, int32_t use_graph);
 
-/* Times every tile shape of the persistent schedule on the given buffers
- * (which it overwrites) with CUDA events and keeps the fastest; writes the
- * chosen (warps_per_block, blocks_per_sm) and its time in ms to the outputs.
- * Synchronizes `stream`. */
+/* Times every tile shape of the persistent schedule with CUDA events and
+ * keeps the fastest: one step of the forward (both passes, on the given
+ * buffers, which it overwrites) and the adjoint (reading L as L-bar, writing
+ * library scratch).  A shape's blocks_per_sm is capped per kernel by its
+ * resident limit, so a shape can give the adjoint more warps than the
+ * forward.  Writes the chosen (warps_per_block, blocks_per_sm) and its step
+ * time in ms to the outputs.  Synchronizes `stream`. */
 ot_status ot_autotune(ot_grid* grid, const double* M, const double* m, double* L, double* Lc,
                       void* stream, int32_t* best_warps, int32_t* best_blocks, double* best_ms);
 

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libotfmm.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("ot_kernels.cu", "ot_lib.cu", "ot_noalloc.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("ot_internal.h", "ot_contract.inc", "gen_contract.py")] + \
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("ot_internal.h", "ot_contract.inc", "ot_contract_counts.h",
+                                                  "gen_contract.py")] + \
     [os.path.join(ROOT, "include", "ot.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -37,7 +38,8 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     inc = os.path.join(CSRC, "ot_contract.inc")
     gen = os.path.join(CSRC, "gen_contract.py")
-    if force or _stale(inc, [gen]):
+    counts = os.path.join(CSRC, "ot_contract_counts.h")
+    if force or _stale(inc, [gen]) or _stale(counts, [gen]):
         subprocess.run([sys.executable, gen], check=True)
     if not (force or _stale(LIB, DEPS)):
         return LIB

@@ -200,6 +200,100 @@ def deriv_code(name):
     return "".join(lines)
 
 
+# ---------------------------------------------------------------------------
+# reflection classes of multipole sources
+#
+# The sources at t + s*o (s in {+1, -1}^3 per axis, o >= 0) see one table row
+# up to signs: d^K G at -s*o is s^K d^K G at -o, s^K = prod_a s_a^K_a, whose
+# value depends only on the parity pattern pi(K) of K.  A term
+# a[J] += r_s[K] d[J + K] summed over the members becomes
+# d[J + K] * W_K[pi(J) ^ pi(K)], W_K the Walsh-Hadamard transform of the
+# members' K-th moments over the sign axes (W_K[pi] = sum_i (-1)^|i & pi|
+# r_i[K], member i negated on the axes set in i).  Each source component
+# needs only the transform outputs its terms use; an axis with a zero offset
+# component (bit set in Z) has one member and its odd-order derivatives are
+# exactly zero, so terms with pi & Z drop out.
+# ---------------------------------------------------------------------------
+
+def parity(e):
+    return (e[0] & 1) | ((e[1] & 1) << 1) | ((e[2] & 1) << 2)
+
+
+def mclass_terms(Z, ang):
+    """per source component k: [(output pi, target kind, index, row index)]"""
+    out = {k: [] for k in range(16)}
+    for j, ej in enumerate(IND16):
+        for k, ek in enumerate(IND16):
+            if rank(ej) + rank(ek) <= 3:
+                e = add(ej, ek)
+                if not (parity(e) & Z):
+                    out[k].append((parity(e), "a", j, ROWIDX[e]))
+    if ang:
+        for i in range(3):
+            ei = tuple(1 if a == i else 0 for a in range(3))
+            for k in R3:
+                e = add(ei, IND16[k])
+                if not (parity(e) & Z):
+                    out[k].append((parity(e), "c", i, ROWIDX[e]))
+        for q, e in enumerate(T4):
+            if not (parity(e) & Z):
+                out[0].append((parity(e), "t4", q, ROWIDX[e]))
+    return out
+
+
+def transform_plan(Z, need):
+    """butterflies computing the transform outputs `need` of the members
+    {i : i & Z == 0}: the stage order with the fewest adds.  Returns (ops,
+    final names) with ops = [(stage, index, op, lhs index, rhs index)]."""
+    bits = [b for b in range(3) if not (Z >> b) & 1]
+    best = None
+    for order in itertools.permutations(bits):
+        needed = [None] * (len(order) + 1)
+        needed[len(order)] = set(need)
+        for t in range(len(order), 0, -1):
+            b = 1 << order[t - 1]
+            prev = set()
+            for x in needed[t]:
+                prev |= {x & ~b, x | b}
+            needed[t - 1] = prev
+        ops = []
+        for t in range(1, len(order) + 1):
+            b = 1 << order[t - 1]
+            for x in sorted(needed[t]):
+                lo, hi = x & ~b, x | b
+                ops.append((t, x, "+" if x == lo else "-", lo, hi))
+        if best is None or len(ops) < len(best[0]):
+            best = (ops, len(order))
+    return best
+
+
+def mclass_fwd_code(Z, ang):
+    name = f"ot_mclass_fwd_z{Z}" + ("_ang" if ang else "")
+    lines = [f"__device__ __forceinline__ void {name}(double (&a)[16], double (&c)[3], double (&t4)[9],\n"
+             f"    const double* const (&src)[8], const double* __restrict__ row) {{\n"]
+    members = [i for i in range(8) if not (i & Z)]
+    terms = mclass_terms(Z, ang)
+    n_add = n_fma = 0
+    for k in range(16):
+        if not terms[k]:
+            continue
+        lines.append("  {\n")
+        for i in members:
+            lines.append(f"    const double v0_{i} = src[{i}] ? __ldg(src[{i}] + {k} * NCELL) : 0.0;\n")
+        need = sorted({pi for (pi, _, _, _) in terms[k]})
+        ops, nst = transform_plan(Z, need)
+        for (t, x, op, lo, hi) in ops:
+            lines.append(f"    const double v{t}_{x} = v{t - 1}_{lo} {op} v{t - 1}_{hi};\n")
+        n_add += len(ops)
+        for (pi, kind, idx, di) in terms[k]:
+            w = f"v{nst}_{pi}"
+            lines.append(f"    {kind}[{idx}] = fma({w}, __ldg(row + {di}), {kind}[{idx}]);\n")
+            n_fma += 1
+        lines.append("  }\n")
+    lines.append("}\n\n")
+    return name, "".join(lines), n_add, n_fma
+
+
 def emit():
     out = []
     w = out.append
@@ -408,6 +502,24 @@ def emit():
         w(f"  df_fma({v}h, {v}l, lh[{j}], ll[{j}], r[{j}], r[{16 + j}]);\n")
     w("}\n\n")
 
+    # multipole sources by reflection class
+    w("// multipole sources of one reflection class, zero pattern Z (see\n"
+      "// gen_contract.py): src[i] the reduced moments of member i (stride NCELL)\n"
+      "// or null, row the table row of the class's representative offset\n")
+    for Z in range(7):
+        for ang in (False, True):
+            name, code, n_add, n_fma = mclass_fwd_code(Z, ang)
+            w(f"// {n_add} adds + {n_fma} FMAs\n")
+            w(code)
+    w("template <int Z, bool ANG>\n"
+      "__device__ __forceinline__ void ot_mclass_fwd(double (&a)[16], double (&c)[3], double (&t4)[9],\n"
+      "                                              const double* const (&src)[8], const double* __restrict__ row) {\n")
+    for Z in range(7):
+        w(f"  {'if' if Z == 0 else 'else if'} constexpr (Z == {Z}) {{\n"
+          f"    if constexpr (ANG) ot_mclass_fwd_z{Z}_ang(a, c, t4, src, row);\n"
+          f"    else ot_mclass_fwd_z{Z}(a, c, t4, src, row);\n  }}\n")
+    w("}\n\n")
+
     # derivatives at an arbitrary separation (centre-of-mass expansion centres)
     w("// derivatives of -1/r (row layout) at R = (x, y, z), the components each\n")
     w("// contraction reads: point masses, multipole sources, multipole sources\n")
@@ -430,7 +542,26 @@ def emit():
     return "".join(out)
 
 
+def emit_counts():
+    """ot_contract_counts.h: operation counts of the generated routines that
+    the host code's cost model and FLOP accounting use"""
+    out = ["// Generated by gen_contract.py -- do not edit.\n",
+           "// Operation counts of generated contractions (host and device).\n",
+           "#pragma once\n\n",
+           "// FP64 adds and FMAs of ot_mclass_fwd_z<Z>[_ang], indexed [ang][Z]\n"]
+    adds, fmas = {}, {}
+    for Z in range(7):
+        for ang in (False, True):
+            _, _, adds[ang, Z], fmas[ang, Z] = mclass_fwd_code(Z, ang)
+    for name, tab in (("OT_MCLASS_ADDS", adds), ("OT_MCLASS_FMAS", fmas)):
+        out.append(f"constexpr int {name}[2][7] = {{" + ", ".join(
+            "{" + ", ".join(str(tab[ang, Z]) for Z in range(7)) + "}" for ang in (False, True)) + "};\n")
+    return "".join(out)
+
+
 if __name__ == "__main__":
     here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "ot_contract.inc"), "w") as f:
         f.write(emit())
+    with open(os.path.join(here, "ot_contract_counts.h"), "w") as f:
+        f.write(emit_counts())

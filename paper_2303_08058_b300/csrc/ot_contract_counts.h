@@ -1,0 +1,7 @@
+// Generated by gen_contract.py -- do not edit.
+// Operation counts of generated contractions (host and device).
+#pragma once
+
+// FP64 adds and FMAs of ot_mclass_fwd_z<Z>[_ang], indexed [ang][Z]
+constexpr int OT_MCLASS_ADDS[2][7] = {{232, 70, 70, 16, 70, 16, 16}, {309, 95, 95, 22, 95, 22, 22}};
+constexpr int OT_MCLASS_FMAS[2][7] = {{70, 40, 40, 22, 40, 22, 22}, {100, 56, 56, 31, 56, 31, 31}};

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ot_contract_counts.h"
+
 namespace otk {
 
 constexpr int NCELL = 512;        // cells per 8^3 sub-grid
@@ -50,8 +52,9 @@ enum Kind : int { K_NONE = 0, K_MULTI = 1, K_LEAF = 2, K_VIRT = 3 };
 // negation -o (both in the list), then far_len - far_pairs single offsets.
 // The near and root lists are closed under negation: every entry is paired.
 //
-// Point masses at leaf targets walk the same far and near offsets grouped by
-// reflection class: the offsets (±a, ±b, ±c) of one list, a, b, c >= 0.  A
+// Point masses at leaf targets (and multipole sources at non-leaf targets)
+// walk the same far, near and root offsets grouped by reflection class: the
+// offsets (±a, ±b, ±c) of one list, a, b, c >= 0.  A
 // class entry is a | b << 8 | c << 16 | members << 24, member bit i standing
 // for the offset with x negated if i & 1, y if i & 2, z if i & 4 (for a zero
 // component only the bit-clear member).  Entries are grouped by the zero
@@ -59,14 +62,19 @@ enum Kind : int { K_NONE = 0, K_MULTI = 1, K_LEAF = 2, K_VIRT = 3 };
 // [zoff[Z], zoff[Z + 1]).  Offsets of classes that would cost more than their
 // +-o pairs and singles follow as pairs, then singles.  The far class list of
 // parity p is the far list of parity 0 reflected on the axes set in p, so
-// every parity has the same class counts.
+// every parity has the same class counts.  The point-mass and multipole
+// class lists differ only in which classes stay pairs and singles (their
+// costs differ).
 struct Lists {
-    const int* lists;      // far[8][far_len] | near[near_len] | root[root_len] | cfar[8][cf_stride] | cnear
+    const int* lists;      // far[8][far_len] | near | root | cfar[8][cf_stride] | cnear | mfar[8][mf_stride] | mroot
     int far_len, far_pairs, near_len, root_len;
     int near_off, root_off;
     int cf_off, cf_stride, cf_pairs, cf_singles;   // far classes; leftover pairs and singles follow zoff[7]
     int cn_off, cn_pairs;                          // near classes, then leftover pairs
     int cf_z[8], cn_z[8];                          // class group bounds by zero pattern
+    // multipole sources by class: far lists per parity and the root list
+    int mf_off, mf_stride, mf_pairs, mf_singles, mf_z[8];
+    int mr_off, mr_pairs, mr_z[8];
 };
 
 struct FwdParams {

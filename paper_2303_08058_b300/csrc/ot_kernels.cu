@@ -477,6 +477,48 @@ __device__ __forceinline__ void walk_classes_fwd_all(const int* __restrict__ lis
     if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, ch, tx, ty, tz, s_nb, p, acc, item);
 }
 
+// multipole sources by reflection class (non-leaf targets): the members'
+// reduced moments feed the class contraction (see gen_contract.py), which
+// transforms them over the sign axes component by component
+template <int Z, bool ANG>
+__device__ __forceinline__ void walk_mclasses_fwd(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                  const int2* __restrict__ s_nb, const FwdParams& p,
+                                                  double (&acc)[16], double (&c)[3], double (&t4)[9], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int ox = e & 0xff, oy = (e >> 8) & 0xff, oz = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        const double* src[8];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            src[i] = nullptr;
+            if (i & Z) continue;
+            if ((members >> i) & 1u) {
+                int sx, sy, sz;
+                class_member(i, ox, oy, oz, tx, ty, tz, sx, sy, sz);
+                const int2 es = s_nb[nb_index(sx, sy, sz)];
+                if (checked_kind(p, es, item) == K_MULTI) {
+                    src[i] = p.Mhat + static_cast<size_t>(es.x) * NRED * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+                    any = true;
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        ot_mclass_fwd<Z, ANG>(acc, c, t4, src, p.Dt + static_cast<size_t>(offset_row(ox, oy, oz)) * DROW);
+    }
+}
+
+template <bool ANG, int Z = 0, class CH>
+__device__ __forceinline__ void walk_mclasses_fwd_all(const int* __restrict__ list, const int (&zoff)[8], const CH& ch,
+                                                      int tx, int ty, int tz, const int2* __restrict__ s_nb,
+                                                      const FwdParams& p, double (&acc)[16], double (&c)[3],
+                                                      double (&t4)[9], int item) {
+    const int len = zoff[Z + 1] - zoff[Z];
+    walk_mclasses_fwd<Z, ANG>(list + zoff[Z] + ch.lo(len), ch.n(len), tx, ty, tz, s_nb, p, acc, c, t4, item);
+    if constexpr (Z < 6) walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, ch, tx, ty, tz, s_nb, p, acc, c, t4, item);
+}
+
 template <int MODE, bool PAIRED, int EMU, bool NEAR = false, bool PM = true>
 __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
                                              int tx, int ty, int tz, const int2* __restrict__ s_nb,
@@ -773,6 +815,33 @@ __global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int per
                 }
                 walk_forward<2, true, EMU, true, false>(p.L.lists + p.L.near_off + ch.lo(p.L.near_len),
                                                         ch.n(p.L.near_len), false, tx, ty, tz, nb, p, a, c, t4, f, it);
+            }
+        } else if (!leafT && !(EMU & 2)) {
+            // non-leaf target, FP64 multipole contractions: multipole sources
+            // by reflection class (root or far list), the classes' leftover
+            // pairs and singles; point masses (leaf neighbours of an adaptive
+            // tree) over the far list
+            const int2* nb = s_nb[warp];
+            if (MODE & 1) {
+                const bool root = level == 0;
+                int zo[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) zo[q] = root ? p.L.mr_z[q] : p.L.mf_z[q];
+                const int* ml = p.L.lists + (root ? p.L.mr_off : p.L.mf_off + par * p.L.mf_stride);
+                walk_mclasses_fwd_all<true>(ml, zo, ch, tx, ty, tz, nb, p, a, c, t4, it);
+                ml += zo[7];
+                const int np = root ? p.L.mr_pairs : p.L.mf_pairs, ns = root ? 0 : p.L.mf_singles;
+                walk_forward<1, true, EMU>(ml + ch.lo(np), ch.n(np), true, tx, ty, tz, nb, p, a, c, t4, f, it);
+                walk_forward<1, false, EMU>(ml + np + ch.lo(ns), ch.n(ns), true, tx, ty, tz, nb, p, a, c, t4, f, it);
+            }
+            if ((MODE & 2) && level > 0 &&
+                __any_sync(0xffffffffu, lane < 27 && (nb[lane < 27 ? lane : 0].y & 3) >= K_LEAF)) {
+                const int* lf = p.L.lists + par * p.L.far_len;
+                const int ns = p.L.far_len - p.L.far_pairs;
+                walk_forward<2, true, EMU>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), true, tx, ty, tz, nb, p,
+                                           a, c, t4, f, it);
+                walk_forward<2, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), true, tx, ty, tz, nb, p, a, c,
+                                            t4, f, it);
             }
         } else {
             if (level == 0) {

@@ -379,7 +379,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         }
     };
     std::vector<int> far_pair[8], far_single[8], near_pair, near_single, root_pair, root_single;
-    std::vector<std::array<int, 3>> far_offs[8], near_offs;
+    std::vector<std::array<int, 3>> far_offs[8], near_offs, root_offs;
     for (int p = 0; p < 8; ++p) {
         const int px = p & 1, py = (p >> 1) & 1, pz = (p >> 2) & 1;
         std::vector<std::array<int, 3>>& offs = far_offs[p];
@@ -404,6 +404,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         split(nr, near_pair, near_single);
         split(rt, root_pair, root_single);
         near_offs = nr;
+        root_offs = rt;
     }
     for (int p = 1; p < 8; ++p)
         if (far_pair[p].size() != far_pair[0].size() || far_single[p].size() != far_single[0].size())
@@ -429,7 +430,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // (18) and singles (16); its offsets are walked as pairs and singles
     // otherwise
     auto class_split = [&](const std::vector<std::array<int, 3>>& offs, std::vector<int> (&cls)[8],
-                           std::vector<int>& pairs, std::vector<int>& singles) {
+                           std::vector<int>& pairs, std::vector<int>& singles, bool multipole) {
         std::map<int, std::vector<std::array<int, 3>>> byrep;
         for (auto& o : offs) byrep[std::abs(o[0]) | (std::abs(o[1]) << 8) | (std::abs(o[2]) << 16)].push_back(o);
         for (auto& kv : byrep) {
@@ -439,7 +440,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             for (auto& o : kv.second) members |= 1 << ((o[0] < 0 ? 1 : 0) | (o[1] < 0 ? 2 : 0) | (o[2] < 0 ? 4 : 0));
             std::vector<int> pp, ss;
             split(kv.second, pp, ss);
-            if (class_adds(Z) + class_fmas(Z) < static_cast<int>(18 * pp.size() + 16 * ss.size())) {
+            // FP64 instructions per lane: point masses 18 per pair, 16 per
+            // single; multipole sources with the angular term 132 and 100
+            const int ccost = multipole ? OT_MCLASS_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z] : class_adds(Z) + class_fmas(Z);
+            const int pcost = multipole ? 132 : 18, scost = multipole ? 100 : 16;
+            if (ccost < static_cast<int>(pcost * pp.size() + scost * ss.size())) {
                 cls[Z].push_back(kv.first | (members << 24));
             } else {
                 pairs.insert(pairs.end(), pp.begin(), pp.end());
@@ -448,8 +453,18 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         }
     };
     std::vector<int> cfar[8][8], cfar_pair[8], cfar_single[8], cnear[8], cnear_pair, cnear_single;
-    for (int p = 0; p < 8; ++p) class_split(far_offs[p], cfar[p], cfar_pair[p], cfar_single[p]);
-    class_split(near_offs, cnear, cnear_pair, cnear_single);
+    for (int p = 0; p < 8; ++p) class_split(far_offs[p], cfar[p], cfar_pair[p], cfar_single[p], false);
+    class_split(near_offs, cnear, cnear_pair, cnear_single, false);
+    // the same for multipole sources: far lists and the root list
+    std::vector<int> mfar[8][8], mfar_pair[8], mfar_single[8], mroot[8], mroot_pair, mroot_single;
+    for (int p = 0; p < 8; ++p) class_split(far_offs[p], mfar[p], mfar_pair[p], mfar_single[p], true);
+    class_split(root_offs, mroot, mroot_pair, mroot_single, true);
+    for (int p = 1; p < 8; ++p) {
+        bool same = mfar_pair[p].size() == mfar_pair[0].size() && mfar_single[p].size() == mfar_single[0].size();
+        for (int z = 0; z < 8; ++z) same = same && mfar[p][z].size() == mfar[0][z].size();
+        if (!same) return fail(OT_EINVAL, "internal: parity class stencils differ in shape");
+    }
+    if (!mroot_single.empty()) return fail(OT_EINVAL, "internal: root class stencil not closed under negation");
     for (int p = 1; p < 8; ++p) {
         bool same = cfar_pair[p].size() == cfar_pair[0].size() && cfar_single[p].size() == cfar_single[0].size();
         for (int z = 0; z < 8; ++z) same = same && cfar[p][z].size() == cfar[0][z].size();
@@ -481,12 +496,32 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     Lh.cn_off = static_cast<int>(g->lists.size());
     for (int z = 0; z < 7; ++z) g->lists.insert(g->lists.end(), cnear[z].begin(), cnear[z].end());
     g->lists.insert(g->lists.end(), cnear_pair.begin(), cnear_pair.end());
+    Lh.mf_z[0] = 0;
+    for (int z = 0; z < 7; ++z) Lh.mf_z[z + 1] = Lh.mf_z[z] + static_cast<int>(mfar[0][z].size());
+    Lh.mf_pairs = static_cast<int>(mfar_pair[0].size());
+    Lh.mf_singles = static_cast<int>(mfar_single[0].size());
+    Lh.mf_stride = Lh.mf_z[7] + Lh.mf_pairs + Lh.mf_singles;
+    Lh.mf_off = static_cast<int>(g->lists.size());
+    for (int p = 0; p < 8; ++p) {
+        for (int z = 0; z < 7; ++z) g->lists.insert(g->lists.end(), mfar[p][z].begin(), mfar[p][z].end());
+        g->lists.insert(g->lists.end(), mfar_pair[p].begin(), mfar_pair[p].end());
+        g->lists.insert(g->lists.end(), mfar_single[p].begin(), mfar_single[p].end());
+    }
+    Lh.mr_z[0] = 0;
+    for (int z = 0; z < 7; ++z) Lh.mr_z[z + 1] = Lh.mr_z[z] + static_cast<int>(mroot[z].size());
+    Lh.mr_pairs = static_cast<int>(mroot_pair.size());
+    Lh.mr_off = static_cast<int>(g->lists.size());
+    for (int z = 0; z < 7; ++z) g->lists.insert(g->lists.end(), mroot[z].begin(), mroot[z].end());
+    g->lists.insert(g->lists.end(), mroot_pair.begin(), mroot_pair.end());
     {
         // every far and near offset exactly once
         long long nf = 2LL * Lh.cf_pairs + Lh.cf_singles, nn = 2LL * Lh.cn_pairs;
         for (int k = 0; k < Lh.cf_z[7]; ++k) nf += __builtin_popcount(static_cast<unsigned>(g->lists[Lh.cf_off + k]) >> 24);
         for (int k = 0; k < Lh.cn_z[7]; ++k) nn += __builtin_popcount(static_cast<unsigned>(g->lists[Lh.cn_off + k]) >> 24);
-        if (nf != g->far_offsets || nn != 2LL * g->near_len)
+        long long mf = 2LL * Lh.mf_pairs + Lh.mf_singles, mr = 2LL * Lh.mr_pairs;
+        for (int k = 0; k < Lh.mf_z[7]; ++k) mf += __builtin_popcount(static_cast<unsigned>(g->lists[Lh.mf_off + k]) >> 24);
+        for (int k = 0; k < Lh.mr_z[7]; ++k) mr += __builtin_popcount(static_cast<unsigned>(g->lists[Lh.mr_off + k]) >> 24);
+        if (nf != g->far_offsets || nn != 2LL * g->near_len || mf != g->far_offsets || mr != 2LL * g->root_len)
             return fail(OT_EINVAL, "internal: class stencils do not cover the offsets");
     }
 
@@ -625,21 +660,28 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // per lane (forward, scatter adjoint), members and FLOPs; per neighbour
     // the FLOPs of the pairs landing there over all 512 cells, an entry's
     // FLOPs shared equally by its members.
-    const int cseg_len[2] = {g->Lh.cf_stride, g->Lh.cn_z[7] + g->Lh.cn_pairs};
-    std::vector<uint32_t> cmask[16][2];
-    std::vector<int> ccost_f[2], ccost_s[2], cmem[2];
-    double cfl_f[2][27], cfl_s[2][27];
+    // Class segments: 0 point masses, far (per parity); 1 point masses,
+    // near; 2 multipole sources with the angular term, far (per parity);
+    // 3 the same, root.
+    const int cseg_len[4] = {g->Lh.cf_stride, g->Lh.cn_z[7] + g->Lh.cn_pairs, g->Lh.mf_stride,
+                             g->Lh.mr_z[7] + g->Lh.mr_pairs};
+    std::vector<uint32_t> cmask[16][4];
+    std::vector<int> ccost_f[4], ccost_s[4], cmem[4];
+    double cfl_f[4][27], cfl_s[4][27];
     std::memset(cfl_f, 0, sizeof(cfl_f));
     std::memset(cfl_s, 0, sizeof(cfl_s));
-    for (int cg = 0; cg < 2; ++cg) {
-        const int nz = cg == 0 ? g->Lh.cf_z[7] : g->Lh.cn_z[7];
-        const int npair = cg == 0 ? g->Lh.cf_pairs : g->Lh.cn_pairs;
+    for (int cg = 0; cg < 4; ++cg) {
+        const int nz = cg == 0 ? g->Lh.cf_z[7] : cg == 1 ? g->Lh.cn_z[7] : cg == 2 ? g->Lh.mf_z[7] : g->Lh.mr_z[7];
+        const int npair = cg == 0 ? g->Lh.cf_pairs : cg == 1 ? g->Lh.cn_pairs : cg == 2 ? g->Lh.mf_pairs : g->Lh.mr_pairs;
+        const bool multi = cg >= 2;
         ccost_f[cg].resize(cseg_len[cg]);
         ccost_s[cg].resize(cseg_len[cg]);
         cmem[cg].resize(cseg_len[cg]);
         for (int ph = 0; ph < 16; ++ph) {
             const int par = ph >> 1, half = ph & 1;
-            const int* lst = &g->lists[cg == 0 ? g->Lh.cf_off + par * g->Lh.cf_stride : g->Lh.cn_off];
+            const int off = cg == 0 ? g->Lh.cf_off + par * g->Lh.cf_stride : cg == 1 ? g->Lh.cn_off
+                          : cg == 2 ? g->Lh.mf_off + par * g->Lh.mf_stride : g->Lh.mr_off;
+            const int* lst = &g->lists[off];
             cmask[ph][cg].resize(cseg_len[cg]);
             for (int k = 0; k < cseg_len[cg]; ++k) {
                 const int e = lst[k];
@@ -651,19 +693,24 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     for (int t = 0; t < 8; ++t)
                         if ((static_cast<unsigned>(e) >> 24 >> t) & 1u)
                             mem.push_back({t & 1 ? -a : a, t & 2 ? -b : b, t & 4 ? -cc : cc});
-                    cf = cs = class_adds(Z) + class_fmas(Z);
-                    fl_f = fl_s = class_adds(Z) + 2 * class_fmas(Z);
+                    if (multi) {
+                        cf = cs = OT_MCLASS_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z];
+                        fl_f = fl_s = OT_MCLASS_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z];
+                    } else {
+                        cf = cs = class_adds(Z) + class_fmas(Z);
+                        fl_f = fl_s = class_adds(Z) + 2 * class_fmas(Z);
+                    }
                 } else {
                     const int ox = (e & 0xff) - 8, oy = ((e >> 8) & 0xff) - 8, oz = ((e >> 16) & 0xff) - 8;
                     mem.push_back({ox, oy, oz});
                     if (k < nz + npair) {
                         mem.push_back({-ox, -oy, -oz});
-                        cf = cs = 18;
-                        fl_f = fl_s = 34;
+                        cf = cs = multi ? 132 : 18;
+                        fl_f = fl_s = multi ? 232 : 34;
                     } else {
-                        cf = 16;
-                        cs = 17;
-                        fl_f = fl_s = 32;
+                        cf = multi ? 100 : 16;
+                        cs = multi ? 100 : 17;
+                        fl_f = fl_s = multi ? 200 : 32;
                     }
                 }
                 ccost_f[cg][k] = cf;
@@ -689,6 +736,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     //   point masses at leaf targets (level > 0) by class: class_adds +
     //   2 class_fmas per class entry, shared by its members;
     //   multipole 140 (200 with the angular term), or 86 (116) paired;
+    //   multipole sources at non-leaf targets by class: OT_MCLASS_ADDS +
+    //   2 OT_MCLASS_FMAS (angular) per class entry, shared by its members;
     //   adjoint: point mass 32, multipole 140, or 86 paired.
     // FP64 instructions per lane and active entry (empty lanes included):
     //   forward point mass 16 | 18 paired; multipole 70 (+30) | 102 (+30);
@@ -726,7 +775,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 pairs_multi += cpf + csf;
                 if (!leaf) {
                     pairs_ang += cpf + csf;
-                    flops_fwd += 116 * cpf + 200 * csf;
+                    flops_fwd += std::llround(cfl_f[desc->level[i] == 0 ? 3 : 2][j]);
                 } else {
                     flops_fwd += 86 * cpf + 140 * csf;
                 }
@@ -795,9 +844,24 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                             padded += 32 * cmem[cg][k];
                         }
                 ops_adj_scat += 32 * cost_s;
+            } else if (!leaf) {
+                // multipole sources by class, point masses (leaf neighbours)
+                // over the far list
+                const int cgm = desc->level[i] == 0 ? 3 : 2;
+                for (size_t k = 0; k < cmask[ph][cgm].size(); ++k)
+                    if (cmask[ph][cgm][k] & mm) {
+                        cost[1] += ccost_f[cgm][k];
+                        lanes += 32;
+                        padded += 32 * cmem[cgm][k];
+                    }
+                const uint32_t mm_keep = mm;
+                mm = 0;
+                scan(s1);
+                mm = mm_keep;
+                ops_adj_scat += 32 * (cost[2] - count_single_mono);
             } else {
                 scan(s1);
-                if (leaf) scan(1);
+                scan(1);
                 // the point-mass adjoint organised by target walks the same active
                 // entries: 16 products + 2 adds per paired entry, 16 + 1 single
                 ops_adj_scat += 32 * (cost[2] - count_single_mono);
@@ -2156,18 +2220,30 @@ ot_status ot_autotune(ot_grid* g, const double* M, const double* m, double* L, d
     double best = 1e30;
     int bw = save_w, bb = save_b;
     const int ws[3] = {2, 4, 8};
+    // the adjoint's m-bar output (its M-bar goes to the grid's scratch)
+    double* mbar = nullptr;
+    OT_CUDA(cudaMalloc(&mbar, static_cast<size_t>(g->n) * NCELL * sizeof(double)));
+    struct Free {
+        double* q;
+        ~Free() { cudaFree(q); }
+    } free_mbar{mbar};
     for (int wi = 0; wi < 3; ++wi) {
         const int w = ws[wi];
-        const int maxb = g->maxb_fwd[3][w];
+        const int maxb = std::max(g->maxb_fwd[3][w], g->maxb_fast5[w]);
         for (int b = 1; b <= std::min(maxb, 16); ++b) {
             g->wpb = w;
             g->bps = b;
-            ot_status st = enqueue_forward(g, 3, M, m, L, Lc, 0, s);   // warm-up
+            auto step = [&]() -> ot_status {
+                ot_status st = enqueue_forward(g, 3, M, m, L, Lc, 0, s);
+                if (st != OT_OK) return st;
+                return enqueue_backward(g, L, g->d_Mb, mbar, s);
+            };
+            ot_status st = step();   // warm-up
             if (st != OT_OK) return st;
             float best_run = 1e30f;
             for (int r = 0; r < 2; ++r) {
                 OT_CUDA(cudaEventRecord(e0, s));
-                st = enqueue_forward(g, 3, M, m, L, Lc, 0, s);
+                st = step();
                 if (st != OT_OK) return st;
                 OT_CUDA(cudaEventRecord(e1, s));
                 OT_CUDA(cudaEventSynchronize(e1));

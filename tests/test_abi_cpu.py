@@ -85,6 +85,7 @@ def test_generated_contraction_code_is_current():
         sys.path.pop(0)
     text = gen_contract.emit()
     assert text == open(os.path.join(PKG, "csrc", "ot_contract.inc")).read()
+    assert gen_contract.emit_counts() == open(os.path.join(PKG, "csrc", "ot_contract_counts.h")).read()
     body = text.split("ot_multi_fwd")[1].split("}")[0]
     assert body.count("fma(") == 70
     body = text.split("ot_mono_fwd")[1].split("}")[0]
@@ -177,3 +178,84 @@ def test_generated_pair_derivatives_match_sympy(tmp_path):
                 e = gen_contract.ROW[q]
                 scale = 1.0 / r ** (sum(e) + 1)
                 assert abs(out[q] - exact[q]) <= 1e-14 * max(abs(exact[q]), scale), (name, R, e, out[q], exact[q])
+
+
+def test_multipole_class_contraction_matches_its_members(tmp_path):
+    """The reflection-class contraction of multipole sources, compiled as host
+    C++, against the per-source contraction (ot_multi_fwd + ot_angular_fwd)
+    of each member with the derivatives at its own offset, for every zero
+    pattern, with and without the angular term, and with members missing."""
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    text = open(os.path.join(PKG, "csrc", "ot_contract.inc")).read()
+
+    def routine(name):
+        start = text.index(f"__device__ __forceinline__ void {name}(")
+        return text[start:text.index("\n}\n", start) + 3]
+    src = ("#include <cmath>\nusing std::fma; using std::sqrt;\n#define __device__\n#define __forceinline__ inline\n"
+           "#define __restrict__\n#define __ldg(p) (*(p))\nconstexpr int NCELL = 1;\n")
+    for name in ["ot_multi_fwd", "ot_angular_fwd", "ot_deriv31_at"]:
+        src += routine(name)
+    for Z in range(7):
+        for ang in ("", "_ang"):
+            src += routine(f"ot_mclass_fwd_z{Z}{ang}")
+    src += "typedef void (*cls_fn)(double (&)[16], double (&)[3], double (&)[9], const double* const (&)[8], const double*);\n"
+    src += "static cls_fn table[2][7] = {{" + ", ".join(f"ot_mclass_fwd_z{Z}" for Z in range(7)) + "}, {" + \
+        ", ".join(f"ot_mclass_fwd_z{Z}_ang" for Z in range(7)) + "}};\n"
+    src += r'''
+extern "C" void run_class(int Z, int ang, const double* r, int mask, const double* row, double* out) {
+    double a[16] = {0}, c[3] = {0}, t4[9] = {0};
+    const double* p[8];
+    for (int i = 0; i < 8; ++i) p[i] = ((mask >> i) & 1) ? r + 16 * i : nullptr;
+    table[ang][Z](a, c, t4, p, row);
+    for (int i = 0; i < 16; ++i) out[i] = a[i];
+    for (int i = 0; i < 3; ++i) out[16 + i] = c[i];
+    for (int i = 0; i < 9; ++i) out[19 + i] = t4[i];
+}
+extern "C" void run_members(int ox, int oy, int oz, int ang, const double* r, int mask, double* out) {
+    double a[16] = {0}, c[3] = {0}, t4[9] = {0};
+    for (int i = 0; i < 8; ++i) {
+        if (!((mask >> i) & 1)) continue;
+        double d[36] = {0};
+        const int sx = (i & 1) ? -ox : ox, sy = (i & 2) ? -oy : oy, sz = (i & 4) ? -oz : oz;
+        ot_deriv31_at(-1.0 * sx, -1.0 * sy, -1.0 * sz, d);
+        double rr[16];
+        for (int q = 0; q < 16; ++q) rr[q] = r[16 * i + q];
+        ot_multi_fwd(a, rr, d);
+        if (ang) ot_angular_fwd(c, t4, rr, rr[0], d);
+    }
+    for (int i = 0; i < 16; ++i) out[i] = a[i];
+    for (int i = 0; i < 3; ++i) out[16 + i] = c[i];
+    for (int i = 0; i < 9; ++i) out[19 + i] = t4[i];
+}
+extern "C" void row_at(int ox, int oy, int oz, double* out) {
+    double d[36] = {0};
+    ot_deriv31_at(-1.0 * ox, -1.0 * oy, -1.0 * oz, d);
+    for (int q = 0; q < 36; ++q) out[q] = d[q];
+}
+'''
+    (tmp_path / "c.cpp").write_text(src)
+    so = str(tmp_path / "c.so")
+    subprocess.run(["g++", "-O1", "-ffp-contract=off", "-shared", "-fPIC", "-o", so, str(tmp_path / "c.cpp")],
+                   check=True)
+    lib = ctypes.CDLL(so)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rng = np.random.default_rng(7)
+    for (ox, oy, oz) in [(3, 2, 5), (0, 4, 1), (2, 0, 3), (3, 1, 0), (0, 0, 5), (0, 6, 0), (4, 0, 0), (7, 7, 7)]:
+        Z = (ox == 0) | ((oy == 0) << 1) | ((oz == 0) << 2)
+        allowed = [i for i in range(8) if not (i & Z)]
+        row = np.zeros(36)
+        lib.row_at(ox, oy, oz, row.ctypes.data_as(dp))
+        for ang in (0, 1):
+            for trial in range(4):
+                mask = sum(1 << i for i in allowed if trial == 0 or rng.random() < 0.6)
+                r = rng.standard_normal((8, 16))
+                got, want = np.zeros(28), np.zeros(28)
+                lib.run_class(Z, ang, r.ctypes.data_as(dp), mask, row.ctypes.data_as(dp), got.ctypes.data_as(dp))
+                lib.run_members(ox, oy, oz, ang, r.ctypes.data_as(dp), mask, want.ctypes.data_as(dp))
+                scale = np.max(np.abs(want)) + 1e-300
+                assert np.max(np.abs(got - want)) <= 1e-13 * scale, ((ox, oy, oz), ang, mask, got - want)
+                if not ang:
+                    assert np.all(got[16:] == 0)
