@@ -294,6 +294,41 @@ def mclass_fwd_code(Z, ang):
     return name, "".join(lines), n_add, n_fma
 
 
+def mclass_adj_code(Z):
+    """the transpose (multipole gather by source): the members are targets,
+    per target component j the transform of their reduced L-bar feeds
+    g[k] += W_j[pi(j + k)] d[j + k]"""
+    name = f"ot_mclass_adj_z{Z}"
+    lines = [f"__device__ __forceinline__ void {name}(double (&g)[16], const double* const (&src)[8],\n"
+             f"    const double* __restrict__ row) {{\n"]
+    members = [i for i in range(8) if not (i & Z)]
+    terms = {j: [] for j in range(16)}
+    for j, ej in enumerate(IND16):
+        for k, ek in enumerate(IND16):
+            if rank(ej) + rank(ek) <= 3:
+                e = add(ej, ek)
+                if not (parity(e) & Z):
+                    terms[j].append((parity(e), k, ROWIDX[e]))
+    n_add = n_fma = 0
+    for j in range(16):
+        if not terms[j]:
+            continue
+        lines.append("  {\n")
+        for i in members:
+            lines.append(f"    const double v0_{i} = src[{i}] ? __ldg(src[{i}] + {j} * NCELL) : 0.0;\n")
+        need = sorted({pi for (pi, _, _) in terms[j]})
+        ops, nst = transform_plan(Z, need)
+        for (t, x, op, lo, hi) in ops:
+            lines.append(f"    const double v{t}_{x} = v{t - 1}_{lo} {op} v{t - 1}_{hi};\n")
+        n_add += len(ops)
+        for (pi, k, di) in terms[j]:
+            lines.append(f"    g[{k}] = fma(v{nst}_{pi}, __ldg(row + {di}), g[{k}]);\n")
+            n_fma += 1
+        lines.append("  }\n")
+    lines.append("}\n\n")
+    return name, "".join(lines), n_add, n_fma
+
+
 def emit():
     out = []
     w = out.append
@@ -511,6 +546,16 @@ def emit():
             name, code, n_add, n_fma = mclass_fwd_code(Z, ang)
             w(f"// {n_add} adds + {n_fma} FMAs\n")
             w(code)
+    for Z in range(7):
+        name, code, n_add, n_fma = mclass_adj_code(Z)
+        w(f"// adjoint: {n_add} adds + {n_fma} FMAs\n")
+        w(code)
+    w("template <int Z>\n"
+      "__device__ __forceinline__ void ot_mclass_adj(double (&g)[16], const double* const (&src)[8],\n"
+      "                                              const double* __restrict__ row) {\n")
+    for Z in range(7):
+        w(f"  {'if' if Z == 0 else 'else if'} constexpr (Z == {Z}) ot_mclass_adj_z{Z}(g, src, row);\n")
+    w("}\n\n")
     w("template <int Z, bool ANG>\n"
       "__device__ __forceinline__ void ot_mclass_fwd(double (&a)[16], double (&c)[3], double (&t4)[9],\n"
       "                                              const double* const (&src)[8], const double* __restrict__ row) {\n")
@@ -556,6 +601,10 @@ def emit_counts():
     for name, tab in (("OT_MCLASS_ADDS", adds), ("OT_MCLASS_FMAS", fmas)):
         out.append(f"constexpr int {name}[2][7] = {{" + ", ".join(
             "{" + ", ".join(str(tab[ang, Z]) for Z in range(7)) + "}" for ang in (False, True)) + "};\n")
+    out.append("// FP64 adds and FMAs of ot_mclass_adj_z<Z>\n")
+    cnt = [mclass_adj_code(Z)[2:] for Z in range(7)]
+    out.append("constexpr int OT_MCLASS_ADJ_ADDS[7] = {" + ", ".join(str(a) for a, _ in cnt) + "};\n")
+    out.append("constexpr int OT_MCLASS_ADJ_FMAS[7] = {" + ", ".join(str(f) for _, f in cnt) + "};\n")
     return "".join(out)
 
 

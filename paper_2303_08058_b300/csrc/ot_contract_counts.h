@@ -5,3 +5,6 @@
 // FP64 adds and FMAs of ot_mclass_fwd_z<Z>[_ang], indexed [ang][Z]
 constexpr int OT_MCLASS_ADDS[2][7] = {{232, 70, 70, 16, 70, 16, 16}, {309, 95, 95, 22, 95, 22, 22}};
 constexpr int OT_MCLASS_FMAS[2][7] = {{70, 40, 40, 22, 40, 22, 22}, {100, 56, 56, 31, 56, 31, 31}};
+// FP64 adds and FMAs of ot_mclass_adj_z<Z>
+constexpr int OT_MCLASS_ADJ_ADDS[7] = {232, 70, 70, 16, 70, 16, 16};
+constexpr int OT_MCLASS_ADJ_FMAS[7] = {70, 40, 40, 22, 40, 22, 22};

@@ -1024,6 +1024,54 @@ __device__ __forceinline__ void walk_adjoint(const int* __restrict__ list, int l
     }
 }
 
+// the multipole gather by reflection class: the members are the targets
+// B + s*o of source B (multipole or leaf cells of B's level, as in
+// walk_adjoint), whose reduced L-bar feed the transposed class contraction
+// (see gen_contract.py) with the table row of -o
+template <int Z>
+__device__ __forceinline__ void walk_mclasses_adj(const int* __restrict__ list, int len, int sx0, int sy0, int sz0,
+                                                  const int2* __restrict__ s_nb, const AdjParams& p,
+                                                  double (&g)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int ox = e & 0xff, oy = (e >> 8) & 0xff, oz = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        const double* src[8];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            src[i] = nullptr;
+            if (i & Z) continue;
+            if ((members >> i) & 1u) {
+                int tx, ty, tz;
+                class_member(i, ox, oy, oz, sx0, sy0, sz0, tx, ty, tz);
+                const int2 et = s_nb[nb_index(tx, ty, tz)];
+                const int kt = et.y & 3;
+                if (kt == K_MULTI || kt == K_LEAF) {
+                    if (static_cast<unsigned>(et.x) >= static_cast<unsigned>(p.n_nodes)) {
+                        report(p.status, 2, item);
+                    } else {
+                        src[i] = p.Lrbar + static_cast<size_t>(et.x) * NRED * NCELL + (tx & 7) + 8 * (ty & 7) +
+                                 64 * (tz & 7);
+                        any = true;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        ot_mclass_adj<Z>(g, src, p.Dt + static_cast<size_t>(NOFF - 1 - offset_row(ox, oy, oz)) * DROW);
+    }
+}
+
+template <int Z = 0, class CH>
+__device__ __forceinline__ void walk_mclasses_adj_all(const int* __restrict__ list, const int (&zoff)[8], const CH& ch,
+                                                      int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
+                                                      const AdjParams& p, double (&g)[16], int item) {
+    const int len = zoff[Z + 1] - zoff[Z];
+    walk_mclasses_adj<Z>(list + zoff[Z] + ch.lo(len), ch.n(len), sx0, sy0, sz0, s_nb, p, g, item);
+    if constexpr (Z < 6) walk_mclasses_adj_all<Z + 1>(list, zoff, ch, sx0, sy0, sz0, s_nb, p, g, item);
+}
+
 // M-bar of one source cell from the gathered g (reduced, h-scaled): expand
 // the traceless reduction and apply (-1)^m/m! * multiplicity * h^-m
 __device__ __forceinline__ void store_mbar(double* __restrict__ Mbar, int src, int scell, double h1,
@@ -1057,12 +1105,12 @@ __device__ __forceinline__ void store_mbar(double* __restrict__ Mbar, int src, i
 }
 
 template <bool EMU = false, class P>
-__device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
+__device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
                              int node, int par, int half, int lane, int it);
 
 // EMU: double-float multipole gather and point-mass scatter (MODE 1, 4, 5)
 template <int MODE, bool EMU = false>
-__global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int persistent) {
+__global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1132,7 +1180,22 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjParams p, int per
             // targets of the transposed far (root) stencil; near leaf targets
             // of a refined cell see its children instead
             if ((MODE & 1) && p.Mbar != nullptr) {
-                if (level == 0) {
+                if (!EMU) {
+                    // by reflection class (root or far list of the source's
+                    // parity), then the classes' leftover pairs and singles
+                    const bool root = level == 0;
+                    int zo[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) zo[q] = root ? p.L.mr_z[q] : p.L.mf_z[q];
+                    const int* ml = p.L.lists + (root ? p.L.mr_off : p.L.mf_off + par * p.L.mf_stride);
+                    walk_mclasses_adj_all(ml, zo, ch, sx, sy, sz, s_nb[warp], p, g, it);
+                    ml += zo[7];
+                    const int np = root ? p.L.mr_pairs : p.L.mf_pairs, ns = root ? 0 : p.L.mf_singles;
+                    walk_adjoint<true, true>(ml + ch.lo(np), ch.n(np), false, false, sx, sy, sz, s_nb[warp], p, g, g4,
+                                             f, it);
+                    walk_adjoint<true, false>(ml + np + ch.lo(ns), ch.n(ns), false, false, sx, sy, sz, s_nb[warp], p,
+                                              g, g4, f, it);
+                } else if (level == 0) {
                     walk_adjoint<true, true, EMU>(l1 + ch.lo(n1), ch.n(n1), false, false, sx, sy, sz, s_nb[warp], p, g,
                                                   g4, f, it);
                 } else {
@@ -1322,7 +1385,7 @@ __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int l
 // one scatter work item: the warp's 32 target cells of `node` push their
 // point-mass adjoint contributions into mbar
 template <bool EMU, class P>
-__device__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
+__device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
                              int node, int par, int half, int lane, int it) {
     int tx, ty, tz;
     lane_cell(lane, par, half, tx, ty, tz);

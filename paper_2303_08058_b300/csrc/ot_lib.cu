@@ -18,7 +18,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/ot.h"
+#include "ot.h"
 #include "ot_internal.h"
 
 using namespace otk;
@@ -693,9 +693,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     for (int t = 0; t < 8; ++t)
                         if ((static_cast<unsigned>(e) >> 24 >> t) & 1u)
                             mem.push_back({t & 1 ? -a : a, t & 2 ? -b : b, t & 4 ? -cc : cc});
-                    if (multi) {
-                        cf = cs = OT_MCLASS_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z];
-                        fl_f = fl_s = OT_MCLASS_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z];
+                    if (multi) {   // forward with the angular term; the adjoint's gather
+                        cf = OT_MCLASS_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z];
+                        cs = OT_MCLASS_ADJ_ADDS[Z] + OT_MCLASS_ADJ_FMAS[Z];
+                        fl_f = OT_MCLASS_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z];
+                        fl_s = OT_MCLASS_ADJ_ADDS[Z] + 2 * OT_MCLASS_ADJ_FMAS[Z];
                     } else {
                         cf = cs = class_adds(Z) + class_fmas(Z);
                         fl_f = fl_s = class_adds(Z) + 2 * class_fmas(Z);
@@ -705,12 +707,15 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     mem.push_back({ox, oy, oz});
                     if (k < nz + npair) {
                         mem.push_back({-ox, -oy, -oz});
-                        cf = cs = multi ? 132 : 18;
-                        fl_f = fl_s = multi ? 232 : 34;
+                        cf = multi ? 132 : 18;
+                        cs = multi ? 102 : 18;
+                        fl_f = multi ? 232 : 34;
+                        fl_s = multi ? 172 : 34;
                     } else {
                         cf = multi ? 100 : 16;
-                        cs = multi ? 100 : 17;
-                        fl_f = fl_s = multi ? 200 : 32;
+                        cs = multi ? 70 : 17;
+                        fl_f = multi ? 200 : 32;
+                        fl_s = multi ? 140 : 32;
                     }
                 }
                 ccost_f[cg][k] = cf;
@@ -738,6 +743,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     //   multipole 140 (200 with the angular term), or 86 (116) paired;
     //   multipole sources at non-leaf targets by class: OT_MCLASS_ADDS +
     //   2 OT_MCLASS_FMAS (angular) per class entry, shared by its members;
+    //   the adjoint's multipole gather by class likewise (OT_MCLASS_ADJ_*);
     //   adjoint: point mass 32, multipole 140, or 86 paired.
     // FP64 instructions per lane and active entry (empty lanes included):
     //   forward point mass 16 | 18 paired; multipole 70 (+30) | 102 (+30);
@@ -959,16 +965,27 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 cp += cnt[1][1][j];
                 cs += cnt[1][0][j];
             }
-            flops_adj += leaf ? 32 * (cp + cs) : 86 * cp + 140 * cs;
-            if (!leaf) flops_adj_multi += 86 * cp + 140 * cs;
+            if (leaf) {
+                flops_adj += 32 * (cp + cs);
+            } else if (((tv | tw) >> j) & 1u) {
+                // multipole gather by class (segment 2 far, 3 root)
+                const long long fl = std::llround(cfl_s[lvl == 0 ? 3 : 2][j]);
+                flops_adj += fl;
+                flops_adj_multi += fl;
+            }
         }
         const int bit = leaf ? 2 : 1;
         for (int mode = 1; mode <= 3; ++mode) g->adj_item_start[mode][i] = static_cast<int>(adj_node[mode].size());
         for (int ph = 0; ph < 16; ++ph) {
             long long cst = 0;
-            for (size_t k = 0; k < mask[ph][s1].size(); ++k)
-                if (mask[ph][s1][k] & (tv | tw))
-                    cst += leaf ? (pflag[ph][s1][k] ? 32 : 16) : (pflag[ph][s1][k] ? 102 : 70);
+            if (leaf) {
+                for (size_t k = 0; k < mask[ph][s1].size(); ++k)
+                    if (mask[ph][s1][k] & (tv | tw)) cst += pflag[ph][s1][k] ? 32 : 16;
+            } else {
+                const int cgm = lvl == 0 ? 3 : 2;
+                for (size_t k = 0; k < cmask[ph][cgm].size(); ++k)
+                    if (cmask[ph][cgm][k] & tv) cst += ccost_s[cgm][k];
+            }
             if (leaf)
                 for (size_t k = 0; k < mask[ph][1].size(); ++k)
                     if (mask[ph][1][k] & (tl | tw)) cst += 32;

@@ -13,7 +13,7 @@
 #include <cstddef>
 #include <mutex>
 
-#include "../../include/ot.h"
+#include "ot.h"
 #include "ot_internal.h"
 
 // defined in ot_lib.cu: the multipole pass with caller-supplied scratch, the

@@ -184,7 +184,8 @@ def test_multipole_class_contraction_matches_its_members(tmp_path):
     """The reflection-class contraction of multipole sources, compiled as host
     C++, against the per-source contraction (ot_multi_fwd + ot_angular_fwd)
     of each member with the derivatives at its own offset, for every zero
-    pattern, with and without the angular term, and with members missing."""
+    pattern, with and without the angular term, and with members missing;
+    the same for the transposed gather (ot_multi_adj per target member)."""
     import shutil
     import subprocess
     if shutil.which("g++") is None:
@@ -196,11 +197,14 @@ def test_multipole_class_contraction_matches_its_members(tmp_path):
         return text[start:text.index("\n}\n", start) + 3]
     src = ("#include <cmath>\nusing std::fma; using std::sqrt;\n#define __device__\n#define __forceinline__ inline\n"
            "#define __restrict__\n#define __ldg(p) (*(p))\nconstexpr int NCELL = 1;\n")
-    for name in ["ot_multi_fwd", "ot_angular_fwd", "ot_deriv31_at"]:
+    for name in ["ot_multi_fwd", "ot_angular_fwd", "ot_multi_adj", "ot_deriv31_at"]:
         src += routine(name)
     for Z in range(7):
         for ang in ("", "_ang"):
             src += routine(f"ot_mclass_fwd_z{Z}{ang}")
+        src += routine(f"ot_mclass_adj_z{Z}")
+    src += "typedef void (*adj_fn)(double (&)[16], const double* const (&)[8], const double*);\n"
+    src += "static adj_fn adj_table[7] = {" + ", ".join(f"ot_mclass_adj_z{Z}" for Z in range(7)) + "};\n"
     src += "typedef void (*cls_fn)(double (&)[16], double (&)[3], double (&)[9], const double* const (&)[8], const double*);\n"
     src += "static cls_fn table[2][7] = {{" + ", ".join(f"ot_mclass_fwd_z{Z}" for Z in range(7)) + "}, {" + \
         ", ".join(f"ot_mclass_fwd_z{Z}_ang" for Z in range(7)) + "}};\n"
@@ -229,6 +233,26 @@ extern "C" void run_members(int ox, int oy, int oz, int ang, const double* r, in
     for (int i = 0; i < 16; ++i) out[i] = a[i];
     for (int i = 0; i < 3; ++i) out[16 + i] = c[i];
     for (int i = 0; i < 9; ++i) out[19 + i] = t4[i];
+}
+extern "C" void run_class_adj(int Z, const double* r, int mask, const double* row, double* out) {
+    double g[16] = {0};
+    const double* p[8];
+    for (int i = 0; i < 8; ++i) p[i] = ((mask >> i) & 1) ? r + 16 * i : nullptr;
+    adj_table[Z](g, p, row);
+    for (int i = 0; i < 16; ++i) out[i] = g[i];
+}
+extern "C" void run_members_adj(int ox, int oy, int oz, const double* r, int mask, double* out) {
+    double g[16] = {0};
+    for (int i = 0; i < 8; ++i) {
+        if (!((mask >> i) & 1)) continue;
+        double d[36] = {0};
+        const int sx = (i & 1) ? -ox : ox, sy = (i & 2) ? -oy : oy, sz = (i & 4) ? -oz : oz;
+        ot_deriv31_at(1.0 * sx, 1.0 * sy, 1.0 * sz, d);     // target at +s*o from the source
+        double lb[16];
+        for (int q = 0; q < 16; ++q) lb[q] = r[16 * i + q];
+        ot_multi_adj(g, lb, d);
+    }
+    for (int i = 0; i < 16; ++i) out[i] = g[i];
 }
 extern "C" void row_at(int ox, int oy, int oz, double* out) {
     double d[36] = {0};
@@ -259,3 +283,13 @@ extern "C" void row_at(int ox, int oy, int oz, double* out) {
                 assert np.max(np.abs(got - want)) <= 1e-13 * scale, ((ox, oy, oz), ang, mask, got - want)
                 if not ang:
                     assert np.all(got[16:] == 0)
+        # the gather by source: targets at +s*o, the table row of -o
+        mrow = np.zeros(36)
+        lib.row_at(-ox, -oy, -oz, mrow.ctypes.data_as(dp))
+        for trial in range(4):
+            mask = sum(1 << i for i in allowed if trial == 0 or rng.random() < 0.6)
+            r = rng.standard_normal((8, 16))
+            got, want = np.zeros(16), np.zeros(16)
+            lib.run_class_adj(Z, r.ctypes.data_as(dp), mask, mrow.ctypes.data_as(dp), got.ctypes.data_as(dp))
+            lib.run_members_adj(ox, oy, oz, r.ctypes.data_as(dp), mask, want.ctypes.data_as(dp))
+            assert np.max(np.abs(got - want)) <= 1e-13 * (np.max(np.abs(want)) + 1e-300), ((ox, oy, oz), mask)
