@@ -179,10 +179,6 @@ def fwd_flops(info):
     return info["flops_fwd"]
 
 
-def adj_flops(info):
-    return info["flops_adj"]
-
-
 # DRAM bytes (read + written) of one forward_kernel<3> launch on the 64^3
 # polytrope workload with the 8x1 tile, from an ncu capture of that kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum = 55.63 MB + 26.38 MB).
@@ -395,6 +391,8 @@ def run_ours(args, rank, world):
     sm_mhz = clk.get("sm_mhz") or NOMINAL_SM_MHZ
     peak = NOMINAL_FP64_TFLOPS * sm_mhz / NOMINAL_SM_MHZ
     ach = fwd_flops(info) / (fwd_ms * 1e-3) / 1e12
+    peak_ops = peak / 2                       # FP64 pipe slots: one per FMA
+    ach_ops = info["fp64_ops_fwd"] / (fwd_ms * 1e-3) / 1e12
     n_m2m = int(len({int(l) for l in tree.level[tree.is_leaf == 0]}))
     launches_step = (1 + n_m2m) + 2 + 2 + (1 if info["n_virtual"] else 0) + (1 + n_m2m + 1)
     res = {
@@ -444,16 +442,22 @@ def run_ours(args, rank, world):
                 "note": "centre-of-mass expansion centres: the same pairs, derivatives of G evaluated "
                         "per pair at R = C_A - C_B; fractions of the same FP64 peak"},
         "roofline": {"bound": "alu", "kernel": "forward_kernel<3> (both passes, one launch)",
-                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "achieved": ach_ops, "peak": peak_ops, "unit": "Tinst/s", "frac": ach_ops / peak_ops,
                      "traffic": (FORWARD_DRAM_BYTES_POLYTROPE64 if args.workload == "polytrope64" else None),
                      "traffic_unit": "bytes per launch (ncu, 8x1 tile)",
-                     "peak_source": (f"nominal B300 FP64 {NOMINAL_FP64_TFLOPS} TFLOP/s at {NOMINAL_SM_MHZ:.0f} MHz, "
+                     "unit_note": ("FP64 pipe thread-instructions per second (an FMA or an add is one pipe slot); "
+                                   "achieved: the algorithmic FP64 instructions of the in-domain pairs per "
+                                   "launch (library count) over the launch's CUDA-event time"),
+                     "peak_source": (f"nominal B300 FP64 {NOMINAL_FP64_TFLOPS} TFLOP/s = "
+                                     f"{NOMINAL_FP64_TFLOPS / 2} T FMA/s at {NOMINAL_SM_MHZ:.0f} MHz, "
                                      f"scaled to the median SM clock sampled in this run ({sm_mhz:.0f} MHz)"),
+                     "flops": {"achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                               "note": "algorithmic FLOPs of the algorithm run (2 per FMA, 1 per add)"},
                      "probe_tflops": peak_tflops, "probe": probe_cfg,
-                     "fp64_pipe_busy": info["ops_fwd"] / (fwd_ms * 1e-3) / (peak * 1e12 / 2),
-                     "adjoint_achieved": adj_flops(info) / (adj_ms * 1e-3) / 1e12,
-                     "adjoint_frac": adj_flops(info) / (adj_ms * 1e-3) / 1e12 / peak,
-                     "adjoint_fp64_pipe_busy": info["ops_adj"] / (adj_ms * 1e-3) / (peak * 1e12 / 2)},
+                     "fp64_pipe_busy": info["ops_fwd"] / (fwd_ms * 1e-3) / (peak_ops * 1e12),
+                     "adjoint_achieved": info["fp64_ops_adj"] / (adj_ms * 1e-3) / 1e12,
+                     "adjoint_frac": info["fp64_ops_adj"] / (adj_ms * 1e-3) / 1e12 / peak_ops,
+                     "adjoint_fp64_pipe_busy": info["ops_adj"] / (adj_ms * 1e-3) / (peak_ops * 1e12)},
         "e2e": {"value": world * pairs_step / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(rho_pin.numel() * 8 + Lbar_pin.numel() * 8),
                 "d2h_bytes_per_step": int(L_out.numel() * 8 + rb_out.numel() * 8), "ms": e2e_ms},

@@ -128,6 +128,10 @@ typedef struct {
     int32_t chunked_subgrids;      /* sub-grids whose multipole work items run as several
                                       list chunks (summed in chunk order by the last one) */
     int32_t reserved0;
+    int64_t fp64_ops_fwd;          /* algorithmic FP64 instructions (one per FMA or add) of one
+                                      forward launch over the in-domain pairs: the FP64 pipe's
+                                      work (a class or +-o entry's shared by its members) */
+    int64_t fp64_ops_adj;          /* the same for the adjoint in use */
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the

@@ -51,7 +51,8 @@ class GridInfo(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("graphs_enabled", ctypes.c_int32),
                 ("flops_fwd_com", ctypes.c_int64), ("flops_adj_com", ctypes.c_int64),
                 ("pairs_refined", ctypes.c_int64), ("pairs_padded_fwd", ctypes.c_int64),
-                ("chunked_subgrids", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("chunked_subgrids", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("fp64_ops_fwd", ctypes.c_int64), ("fp64_ops_adj", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

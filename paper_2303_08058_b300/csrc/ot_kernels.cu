@@ -744,7 +744,7 @@ __device__ __forceinline__ bool chunk_combine_fwd(const FwdParams& p, int2 ci, i
 }
 
 template <int MODE, int EMU>
-__global__ void __launch_bounds__(256) forward_kernel(const FwdParams p, int persistent) {
+__global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;

@@ -221,6 +221,7 @@ struct ot_grid {
     int maxb_com_adj[6][9] = {};        // modes 1-3 gather, 4-5 with point-mass items by target
     int deterministic = 0;              // 1: point-mass adjoint as a gather (fixed summation order)
     long long flops_adj_det = 0, ops_adj_det = 0, flops_adj_fast = 0, ops_adj_fast = 0;
+    long long fp64_ops_adj_det = 0, fp64_ops_adj_fast = 0;
     int* d_nonleaf = nullptr;
     int n_nonleaf = 0;
     int* d_all = nullptr;
@@ -667,9 +668,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                              g->Lh.mr_z[7] + g->Lh.mr_pairs};
     std::vector<uint32_t> cmask[16][4];
     std::vector<int> ccost_f[4], ccost_s[4], cmem[4];
-    double cfl_f[4][27], cfl_s[4][27];
+    double cfl_f[4][27], cfl_s[4][27], cop_f[4][27], cop_s[4][27];   // FLOPs; FP64 instructions
     std::memset(cfl_f, 0, sizeof(cfl_f));
     std::memset(cfl_s, 0, sizeof(cfl_s));
+    std::memset(cop_f, 0, sizeof(cop_f));
+    std::memset(cop_s, 0, sizeof(cop_s));
     for (int cg = 0; cg < 4; ++cg) {
         const int nz = cg == 0 ? g->Lh.cf_z[7] : cg == 1 ? g->Lh.cn_z[7] : cg == 2 ? g->Lh.mf_z[7] : g->Lh.mr_z[7];
         const int npair = cg == 0 ? g->Lh.cf_pairs : cg == 1 ? g->Lh.cn_pairs : cg == 2 ? g->Lh.mf_pairs : g->Lh.mr_pairs;
@@ -730,6 +733,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         m |= 1u << nb;
                         cfl_f[cg][nb] += static_cast<double>(fl_f) / mem.size();
                         cfl_s[cg][nb] += static_cast<double>(fl_s) / mem.size();
+                        cop_f[cg][nb] += static_cast<double>(cf) / mem.size();
+                        cop_s[cg][nb] += static_cast<double>(cs) / mem.size();
                     }
                 }
                 cmask[ph][cg][k] = m;
@@ -757,6 +762,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     long long flops_adj_scat = 0, ops_adj_scat = 0, count_single_mono = 0;
     long long flops_adj_multi = 0, ops_adj_multi = 0;
     long long flops_fwd_com = 0, flops_adj_com = 0;   // explicit centres (see ot_interactions_com)
+    // algorithmic FP64 instructions (one per FMA or add) of the in-domain
+    // pairs, shared per entry like the FLOPs: the FP64 pipe's work
+    double alg_fwd = 0.0, alg_adj_scat = 0.0, alg_adj_multi = 0.0, alg_adj_det = 0.0;
     std::vector<std::pair<long long, int>> fwd[4];
     std::vector<int> node_order_items;
     std::vector<long long> node_cost(n, 0);   // largest item of the node (both passes)
@@ -782,8 +790,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 if (!leaf) {
                     pairs_ang += cpf + csf;
                     flops_fwd += std::llround(cfl_f[desc->level[i] == 0 ? 3 : 2][j]);
+                    alg_fwd += cop_f[desc->level[i] == 0 ? 3 : 2][j];
                 } else {
                     flops_fwd += 86 * cpf + 140 * csf;
+                    alg_fwd += 51.0 * cpf + 70.0 * csf;
                 }
                 // explicit centres: every multipole pair evaluates its derivatives
                 flops_fwd_com += (cpf + csf) * (leaf ? deriv_flops(19) + 140 : deriv_flops(31) + 200);
@@ -792,8 +802,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 pairs_ref += cpn + csn;
                 pairs_mono += cpn + csn;
                 flops_fwd += 8 * (17 * cpn + 32 * csn);
+                alg_fwd += 8 * (9.0 * cpn + 16.0 * csn);
                 flops_fwd_com += 8 * (17 * cpn + 32 * csn);
                 flops_adj_scat += 8 * (16 * cpn + 32 * csn);
+                alg_adj_scat += 8 * (9.0 * cpn + 16.0 * csn);
                 flops_adj_com += 8 * (16 * cpn + 32 * csn);
             }
             if (mo >> j & 1u) {
@@ -801,9 +813,13 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 if (by_class) {
                     flops_fwd += std::llround(cfl_f[0][j] + cfl_f[1][j]);
                     flops_adj_scat += std::llround(cfl_s[0][j] + cfl_s[1][j]);
+                    alg_fwd += cop_f[0][j] + cop_f[1][j];
+                    alg_adj_scat += cop_s[0][j] + cop_s[1][j];
                 } else {
                     flops_fwd += 17 * cp + 32 * cs;
                     flops_adj_scat += 16 * cp + 32 * cs;
+                    alg_fwd += 9.0 * cp + 16.0 * cs;
+                    alg_adj_scat += 9.0 * cp + 17.0 * cs;
                 }
                 // explicit centres: a leaf target reads the table, a non-leaf one evaluates
                 flops_fwd_com += leaf ? 17 * cp + 32 * cs : (cp + cs) * (deriv_flops(16) + 32);
@@ -967,11 +983,14 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             }
             if (leaf) {
                 flops_adj += 32 * (cp + cs);
+                alg_adj_det += 16.0 * (cp + cs);
             } else if (((tv | tw) >> j) & 1u) {
                 // multipole gather by class (segment 2 far, 3 root)
                 const long long fl = std::llround(cfl_s[lvl == 0 ? 3 : 2][j]);
                 flops_adj += fl;
                 flops_adj_multi += fl;
+                alg_adj_det += cop_s[lvl == 0 ? 3 : 2][j];
+                alg_adj_multi += cop_s[lvl == 0 ? 3 : 2][j];
             }
         }
         const int bit = leaf ? 2 : 1;
@@ -1185,6 +1204,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.pairs_padded_fwd = padded;
     I.chunked_subgrids = g->n_chunk_ctrs / 16;
     I.flops_fwd = flops_fwd;
+    I.fp64_ops_fwd = std::llround(alg_fwd);
+    g->fp64_ops_adj_det = std::llround(alg_adj_det);
+    g->fp64_ops_adj_fast = std::llround(alg_adj_multi + alg_adj_scat);
+    I.fp64_ops_adj = g->fp64_ops_adj_fast;
     g->flops_adj_det = flops_adj;
     g->ops_adj_det = ops_adj;
     g->flops_adj_fast = flops_adj_multi + flops_adj_scat;
@@ -2020,6 +2043,7 @@ ot_status ot_set_deterministic(ot_grid* g, int32_t on) {
     if (on != 0 && on != 1) return fail(OT_EINVAL, "on must be 0 or 1");
     g->deterministic = on;
     g->info.flops_adj = on ? g->flops_adj_det : g->flops_adj_fast;
+    g->info.fp64_ops_adj = on ? g->fp64_ops_adj_det : g->fp64_ops_adj_fast;
     g->info.ops_adj = on ? g->ops_adj_det : g->ops_adj_fast;
     return OT_OK;
     GUARD_END
