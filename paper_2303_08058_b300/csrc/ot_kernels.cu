@@ -2038,7 +2038,7 @@ __device__ __forceinline__ void scaled_sep(bool has, const double (&XA)[3], cons
 
 // One stencil segment of a target with explicit centres.  PAIRED: each entry
 // o stands for the sources at t + o and t - o.
-template <int MODE, bool PAIRED, bool NEAR = false>
+template <int MODE, bool PAIRED, bool NEAR = false, bool PM = true>
 __device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, int len, bool angular, bool leafT,
                                                  int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                                  const FwdParams& p, const int (&org)[3], double h, double hinv,
@@ -2064,7 +2064,7 @@ __device__ __forceinline__ void walk_forward_com(const int* __restrict__ list, i
                 // both centres geometric: R/h = -o, the table row (paired as on the table path)
                 bool mono = kd[0] >= K_LEAF;
                 if (PAIRED) mono = mono || kd[NS - 1] >= K_LEAF;
-                if (__any_sync(0xffffffffu, mono)) {
+                if (PM && __any_sync(0xffffffffu, mono)) {
                     const double mp = source_mass(p, e[0], kd[0], sx[0], sy[0], sz[0]);
                     double d[36];
                     load_row16(d, p.Dt, offset_row(ox, oy, oz));
@@ -2133,7 +2133,17 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
         const int it = __shfl_sync(0xffffffffu, v, 0);
         if (it >= p.n_items) break;
         const int item = __ldg(p.items + it);
-        const int node = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        const int node = (item >> 4) & 0x3fffff, par = (item >> 1) & 7, half = item & 1;
+        Chunk ch{(item >> 26) & 15, 1};
+        int2 ci = make_int2(-1, 0);
+        if (p.cinfo != nullptr) {
+            ci = __ldg(p.cinfo + node);
+            if (ci.x >= 0) ch.k = (ci.y & 15) + 1;
+        }
+        if (ch.c >= ch.k) {
+            report(p.status, 6, it);
+            continue;
+        }
         if (lane < 27) s_nb[warp][lane] = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
         __syncwarp();
         const int info = __ldg(p.ninfo + node);
@@ -2163,21 +2173,55 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
         for (int q = 0; q < 3; ++q) c[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) t4[q] = 0.0;
-        if (level == 0) {
-            walk_forward_com<MODE, true>(p.L.lists + p.L.root_off, p.L.root_len, !leafT, leafT, tx, ty, tz,
-                                         s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
+        if ((MODE & 2) && leafT && level > 0) {
+            // leaf target: its point masses have geometric centres, so they run
+            // the table path's class walk; multipole sources (refined
+            // neighbours) and refined near sources keep the explicit-centre walk
+            const int2* nb = s_nb[warp];
+            DFAcc f;
+            df_zero(f);
+            const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
+            walk_classes_fwd_all(cf, p.L.cf_z, ch, tx, ty, tz, nb, p, a, it);
+            cf += p.L.cf_z[7];
+            walk_forward<2, true, 0>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
+                                     t4, f, it);
+            cf += p.L.cf_pairs;
+            walk_forward<2, false, 0>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
+                                      c, t4, f, it);
+            const int* cn = p.L.lists + p.L.cn_off;
+            walk_classes_fwd_all(cn, p.L.cn_z, ch, tx, ty, tz, nb, p, a, it);
+            cn += p.L.cn_z[7];
+            walk_forward<2, true, 0>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
+                                     t4, f, it);
+            if (__any_sync(0xffffffffu, lane < 27 && (nb[lane < 27 ? lane : 0].y & 3) == K_MULTI)) {
+                if constexpr ((MODE & 1) != 0) {
+                    const int* lf = p.L.lists + par * p.L.far_len;
+                    const int ns = p.L.far_len - p.L.far_pairs;
+                    walk_forward_com<1, true>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), false, true, tx, ty,
+                                              tz, nb, p, org, h, hinv, XA, a, c, t4, it);
+                    walk_forward_com<1, false>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), false, true, tx, ty, tz,
+                                               nb, p, org, h, hinv, XA, a, c, t4, it);
+                }
+                walk_forward_com<2, true, true, false>(p.L.lists + p.L.near_off + ch.lo(p.L.near_len),
+                                                       ch.n(p.L.near_len), false, true, tx, ty, tz, nb, p, org, h,
+                                                       hinv, XA, a, c, t4, it);
+            }
+        } else if (level == 0) {
+            walk_forward_com<MODE, true>(p.L.lists + p.L.root_off + ch.lo(p.L.root_len), ch.n(p.L.root_len), !leafT,
+                                         leafT, tx, ty, tz, s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
         } else {
             const int* lf = p.L.lists + par * p.L.far_len;
-            walk_forward_com<MODE, true>(lf, p.L.far_pairs, !leafT, leafT, tx, ty, tz, s_nb[warp], p, org, h,
-                                         hinv,
-                                         XA, a, c, t4, it);
-            walk_forward_com<MODE, false>(lf + p.L.far_pairs, p.L.far_len - p.L.far_pairs, !leafT, leafT, tx, ty,
-                                          tz, s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
-        }
-        if (leafT)
-            walk_forward_com<MODE, true, true>(p.L.lists + p.L.near_off, p.L.near_len, false, true, tx, ty, tz,
+            const int ns = p.L.far_len - p.L.far_pairs;
+            walk_forward_com<MODE, true>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), !leafT, leafT, tx, ty, tz,
                                          s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
-        store_forward<MODE>(p, node, level, leafT, tcell, a, c, t4);
+            walk_forward_com<MODE, false>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), !leafT, leafT, tx, ty, tz,
+                                          s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
+        }
+        if (leafT && !((MODE & 2) && level > 0))
+            walk_forward_com<MODE, true, true>(p.L.lists + p.L.near_off + ch.lo(p.L.near_len), ch.n(p.L.near_len),
+                                               false, true, tx, ty, tz, s_nb[warp], p, org, h, hinv, XA, a, c, t4, it);
+        if (ch.k == 1 || chunk_combine_fwd(p, ci, item & 15, ch, lane, a, c, t4))
+            store_forward<MODE>(p, node, level, leafT, tcell, a, c, t4);
         __syncwarp();
     }
 }
@@ -2337,7 +2381,22 @@ __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
             __syncwarp();
             continue;
         }
-        const int src = item >> 4, par = (item >> 1) & 7, half = item & 1;
+        Chunk ch{0, 1};
+        int2 ci = make_int2(-1, 0);
+        int src = item >> 4;
+        if (item < 0) {            // a chunk of a multipole gather item (as on the table path)
+            src = (item >> 4) & 0x3fffff;
+            ch.c = (item >> 26) & 15;
+            if (p.cinfo != nullptr && src < p.n_nodes) {
+                ci = __ldg(p.cinfo + src);
+                if (ci.x >= 0) ch.k = (ci.y & 15) + 1;
+            }
+            if (ch.c >= ch.k) {
+                report(p.status, 6, it);
+                continue;
+            }
+        }
+        const int par = (item >> 1) & 7, half = item & 1;
         const bool virt = src >= p.n_nodes;
         const int2* nbt = virt ? p.vnbr + static_cast<size_t>(src - p.n_nodes) * 27
                                : p.nbr + static_cast<size_t>(src) * 27;
@@ -2384,11 +2443,12 @@ __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
             // targets of the transposed far (root) stencil; near leaf targets
             // of a refined cell see its children instead
             if ((MODE & 1) && p.Mbar != nullptr) {
-                walk_adjoint_com<true, true>(l1, np, false, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB, g, g4,
-                                             it);
-                walk_adjoint_com<true, false>(l1 + np, ns, false, false, sx, sy, sz, s_nb[warp], p, org, h, hinv, XB,
-                                              g, g4, it);
-                store_mbar(p.Mbar, src, scell, hinv, g);
+                walk_adjoint_com<true, true>(l1 + ch.lo(np), ch.n(np), false, false, sx, sy, sz, s_nb[warp], p, org,
+                                             h, hinv, XB, g, g4, it);
+                walk_adjoint_com<true, false>(l1 + np + ch.lo(ns), ch.n(ns), false, false, sx, sy, sz, s_nb[warp], p,
+                                              org, h, hinv, XB, g, g4, it);
+                if (ch.k == 1 || chunk_combine(p.part, p.chunk_ctr, ci, item & 15, ch, lane, g))
+                    store_mbar(p.Mbar, src, scell, hinv, g);
             }
         } else if ((MODE & 2) && p.mbar != nullptr) {
             const bool vt = skind == K_LEAF;

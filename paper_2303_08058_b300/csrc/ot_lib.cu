@@ -1587,8 +1587,17 @@ static ot_status enqueue_forward_com(ot_grid* g, int mode, const double* M, cons
     com_scales(g, p.hinv, p.hreal);
     p.C = C;
     p.ncoord = g->d_ncoord;
-    p.items = g->d_items_fwd[mode];
-    p.n_items = g->n_items_fwd[mode];
+    // the multipole and fused passes run the table path's chunked items
+    const bool chunked = (mode & 1) != 0;
+    if (chunked) {
+        p.cinfo = g->d_cinfo;
+        p.part = g->d_part;
+        p.chunk_ctr = g->d_chunk_ctr;
+        if (g->n_chunk_ctrs > 0)
+            OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs) * sizeof(int), s));
+    }
+    p.items = chunked ? g->d_itemsc_fwd[mode] : g->d_items_fwd[mode];
+    p.n_items = chunked ? g->n_itemsc_fwd[mode] : g->n_items_fwd[mode];
     OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
     OT_CUDA(launch_forward_com(p, mode, g->wpb, grid_blocks(g, g->maxb_com_fwd[mode][g->wpb]), s));
     return OT_OK;
@@ -1632,15 +1641,24 @@ static ot_status enqueue_backward_com(ot_grid* g, const double* Lbar, const doub
     p.ncoord = g->d_ncoord;
     p.vcoord = g->d_vcoord;
     int kmode = mode;
+    // the multipole gathers run the table path's chunked items (long sources
+    // as list chunks, combined in chunk order)
+    if (mode & 1) {
+        p.cinfo = g->d_cinfo_adj;
+        p.part = g->d_part;
+        p.chunk_ctr = g->d_chunk_ctr;
+        if (g->n_chunk_ctrs_adj > 0)
+            OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs_adj) * sizeof(int), s));
+    }
     if (scatter) {
         // one launch: multipole gather items (if Mbar) and point-mass items by target
         const int k = (mode & 1) ? 1 : 0;
-        p.items = g->d_items_adj_fast[k];
-        p.n_items = g->n_items_adj_fast[k];
+        p.items = k ? g->d_itemsc_adj_fast1 : g->d_items_adj_fast[0];
+        p.n_items = k ? g->n_itemsc_adj_fast1 : g->n_items_adj_fast[0];
         kmode = k ? 5 : 4;
     } else {
-        p.items = g->d_items_adj[mode];
-        p.n_items = g->n_items_adj[mode];
+        p.items = (mode & 1) ? g->d_itemsc_adj[mode] : g->d_items_adj[mode];
+        p.n_items = (mode & 1) ? g->n_itemsc_adj[mode] : g->n_items_adj[mode];
     }
     OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
     OT_CUDA(launch_adjoint_com(p, kmode, g->wpb, grid_blocks(g, g->maxb_com_adj[kmode][g->wpb]), s));
