@@ -241,13 +241,17 @@ def mclass_terms(Z, ang):
     return out
 
 
-def transform_plan(Z, need):
+def transform_plan(Z, need, first=None):
     """butterflies computing the transform outputs `need` of the members
-    {i : i & Z == 0}: the stage order with the fewest adds.  Returns (ops,
-    final names) with ops = [(stage, index, op, lhs index, rhs index)]."""
+    {i : i & Z == 0}: the stage order with the fewest adds (with `first`, the
+    orders starting with that axis; the caller then loads stage 1 instead of
+    computing it).  Returns (ops, number of stages) with ops = [(stage,
+    index, op, lhs index, rhs index)]."""
     bits = [b for b in range(3) if not (Z >> b) & 1]
     best = None
     for order in itertools.permutations(bits):
+        if first is not None and order[0] != first:
+            continue
         needed = [None] * (len(order) + 1)
         needed[len(order)] = set(need)
         for t in range(len(order), 0, -1):
@@ -262,9 +266,10 @@ def transform_plan(Z, need):
             for x in sorted(needed[t]):
                 lo, hi = x & ~b, x | b
                 ops.append((t, x, "+" if x == lo else "-", lo, hi))
-        if best is None or len(ops) < len(best[0]):
-            best = (ops, len(order))
-    return best
+        cost = len([op for op in ops if first is None or op[0] > 1])
+        if best is None or cost < best[2]:
+            best = (ops, len(order), cost)
+    return best[0], best[1]
 
 
 def mclass_fwd_code(Z, ang):
@@ -288,6 +293,40 @@ def mclass_fwd_code(Z, ang):
         for (pi, kind, idx, di) in terms[k]:
             w = f"v{nst}_{pi}"
             lines.append(f"    {kind}[{idx}] = fma({w}, __ldg(row + {di}), {kind}[{idx}]);\n")
+            n_fma += 1
+        lines.append("  }\n")
+    lines.append("}\n\n")
+    return name, "".join(lines), n_add, n_fma
+
+
+def mclass_fwd_x_code(Z, ang):
+    """ot_mclass_fwd_code with the x stage prebuilt: for a class with a > 0
+    (Z without bit 0) the members' x butterflies r(q + a x) +- r(q - a x) at
+    the four positions q = t + (0, +-b, +-c) are read from a table built once
+    per call (pos[q] points at component 0's sum; its difference and the
+    other components follow at stride NCELL)"""
+    assert not (Z & 1)
+    name = f"ot_mclass_fwd_x_z{Z}" + ("_ang" if ang else "")
+    lines = [f"__device__ __forceinline__ void {name}(double (&a)[16], double (&c)[3], double (&t4)[9],\n"
+             f"    const double* const (&pos)[4], const double* __restrict__ row) {{\n"]
+    terms = mclass_terms(Z, ang)
+    n_add = n_fma = n_ld = 0
+    for k in range(16):
+        if not terms[k]:
+            continue
+        lines.append("  {\n")
+        need = sorted({pi for (pi, _, _, _) in terms[k]})
+        ops, nst = transform_plan(Z, need, first=0)
+        for (t, x, op, lo, hi) in ops:
+            if t == 1:
+                q = (x >> 1) & 3
+                lines.append(f"    const double v1_{x} = pos[{q}] ? __ldg(pos[{q}] + {2 * k + (x & 1)} * NCELL) : 0.0;\n")
+                n_ld += 1
+            else:
+                lines.append(f"    const double v{t}_{x} = v{t - 1}_{lo} {op} v{t - 1}_{hi};\n")
+                n_add += 1
+        for (pi, kind, idx, di) in terms[k]:
+            lines.append(f"    {kind}[{idx}] = fma(v{nst}_{pi}, __ldg(row + {di}), {kind}[{idx}]);\n")
             n_fma += 1
         lines.append("  }\n")
     lines.append("}\n\n")
@@ -546,6 +585,19 @@ def emit():
             name, code, n_add, n_fma = mclass_fwd_code(Z, ang)
             w(f"// {n_add} adds + {n_fma} FMAs\n")
             w(code)
+    for Z in (0, 2, 4, 6):
+        for ang in (False, True):
+            name, code, n_add, n_fma = mclass_fwd_x_code(Z, ang)
+            w(f"// x stage prebuilt: {n_add} adds + {n_fma} FMAs\n")
+            w(code)
+    w("template <int Z, bool ANG>\n"
+      "__device__ __forceinline__ void ot_mclass_fwd_x(double (&a)[16], double (&c)[3], double (&t4)[9],\n"
+      "                                                const double* const (&pos)[4], const double* __restrict__ row) {\n")
+    for i, Z in enumerate((0, 2, 4, 6)):
+        w(f"  {'if' if i == 0 else 'else if'} constexpr (Z == {Z}) {{\n"
+          f"    if constexpr (ANG) ot_mclass_fwd_x_z{Z}_ang(a, c, t4, pos, row);\n"
+          f"    else ot_mclass_fwd_x_z{Z}(a, c, t4, pos, row);\n  }}\n")
+    w("}\n\n")
     for Z in range(7):
         name, code, n_add, n_fma = mclass_adj_code(Z)
         w(f"// adjoint: {n_add} adds + {n_fma} FMAs\n")
@@ -601,6 +653,10 @@ def emit_counts():
     for name, tab in (("OT_MCLASS_ADDS", adds), ("OT_MCLASS_FMAS", fmas)):
         out.append(f"constexpr int {name}[2][7] = {{" + ", ".join(
             "{" + ", ".join(str(tab[ang, Z]) for Z in range(7)) + "}" for ang in (False, True)) + "};\n")
+    out.append("// FP64 adds of ot_mclass_fwd_x_z<Z>[_ang] (x stage prebuilt; 0 for Z with bit 0), [ang][Z]\n")
+    xa = {(ang, Z): (mclass_fwd_x_code(Z, ang)[2] if not (Z & 1) else 0) for ang in (False, True) for Z in range(7)}
+    out.append("constexpr int OT_MCLASS_X_ADDS[2][7] = {" + ", ".join(
+        "{" + ", ".join(str(xa[ang, Z]) for Z in range(7)) + "}" for ang in (False, True)) + "};\n")
     out.append("// FP64 adds and FMAs of ot_mclass_adj_z<Z>\n")
     cnt = [mclass_adj_code(Z)[2:] for Z in range(7)]
     out.append("constexpr int OT_MCLASS_ADJ_ADDS[7] = {" + ", ".join(str(a) for a, _ in cnt) + "};\n")

@@ -75,6 +75,10 @@ struct Lists {
     // multipole sources by class: far lists per parity and the root list
     int mf_off, mf_stride, mf_pairs, mf_singles, mf_z[8];
     int mr_off, mr_pairs, mr_z[8];
+    // per group Z with a > 0: the number of x-complete entries at its start
+    // (both or neither x member at every (y, z) sign), which may read their
+    // first transform stage from the prebuilt x butterflies
+    int cf_x[8], cn_x[8], mf_x[8], mr_x[8];
 };
 
 struct FwdParams {
@@ -108,6 +112,11 @@ struct FwdParams {
     const int2* cinfo;     // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
     double* part;          // [slots][PART_VALS][32] chunk accumulators
     int* chunk_ctr;        // [counters] chunks finished per (node, parity, half), zeroed per launch
+    // prebuilt x butterflies (null: not built for this launch); a node's slot
+    // in its kind's table is xslot[node]
+    const double* Sx;      // [non-leaf slot][7][16][2][512]: Mhat(c + a x) +- Mhat(c - a x), multipole cells
+    const double* Sm;      // [leaf slot][7][2][512]: the same for the point masses
+    const int* xslot;      // [n]
 };
 
 struct AdjParams {
@@ -171,12 +180,23 @@ struct PrepParams {
     double hinv[MAXLEV];
 };
 
+// node info bits (ninfo): level (0-7), leaf (8), and whether the node's
+// classes may read the prebuilt x butterflies: bit 9 multipole sources (a
+// non-leaf node whose 26 neighbours are all multipole or empty), bit 10
+// point masses (a leaf node whose neighbours are all leaf or empty)
+constexpr int NI_XMULTI = 1 << 9;
+constexpr int NI_XMASS = 1 << 10;
+
 // launchers (ot_kernels.cu)
 cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid,
                            cudaStream_t s);
 cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wpb, int grid,
                            cudaStream_t s);
 cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s);
+cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* nbr, const double* Mhat, int n_nodes,
+                                      double* Sx, cudaStream_t s);
+cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
+                                     double* Sm, cudaStream_t s);
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);
 cudaError_t launch_restrict_virtual(const double* vbar, const int* vmap, int n_pairs_map,
                                     double* mbar, cudaStream_t s);

@@ -467,14 +467,84 @@ __device__ __forceinline__ void walk_classes_fwd(const int* __restrict__ list, i
     }
 }
 
-// the seven zero patterns of a class list (Z = 7 would be the self pair)
+// the transform stages after the x stage (y and z axes not in Z)
+template <int Z>
+__device__ __forceinline__ void class_transform_yz(double (&w)[8]) {
+#pragma unroll
+    for (int b = 1; b < 3; ++b) {
+        if ((Z >> b) & 1) continue;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (((i >> b) & 1) || (i & Z)) continue;
+            const double u = w[i], v = w[i | (1 << b)];
+            w[i] = u + v;
+            w[i | (1 << b)] = u - v;
+        }
+    }
+}
+
+// x-complete point-mass classes of a node whose neighbours are all leaf or
+// empty: the first transform stage comes from the prebuilt x butterflies of
+// the masses at the positions t + (0, +-b, +-c)
+template <int Z>
+__device__ __forceinline__ void walk_classes_fwd_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                   const int2* __restrict__ s_nb, const FwdParams& p,
+                                                   double (&acc)[16], int item) {
+    static_assert((Z & 1) == 0, "the x stage needs a > 0");
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        double w[8];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            w[2 * q] = 0.0;
+            w[2 * q + 1] = 0.0;
+            if ((2 * q) & Z) continue;
+            if ((members >> (2 * q)) & 1u) {
+                const int sy = (q & 1) ? ty - b : ty + b, sz = (q & 2) ? tz - c : tz + c;
+                const int2 es = s_nb[nb_index(tx, sy, sz)];
+                const int ks = checked_kind(p, es, item);
+                if (ks == K_LEAF) {
+                    const double* src = p.Sm + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + a - 1) * 2 * NCELL +
+                                        (tx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+                    w[2 * q] = __ldg(src);
+                    w[2 * q + 1] = __ldg(src + NCELL);
+                    any = true;
+                } else if (ks != K_NONE) {
+                    report(p.status, 7, item);    // the node's flag promised leaf or empty neighbours
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(a, b, c));
+        class_transform_yz<Z>(w);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (!(comp_parity(q) & Z)) acc[q] = fma(w[comp_parity(q)], d[q], acc[q]);
+    }
+}
+
+// the seven zero patterns of a class list (Z = 7 would be the self pair);
+// with xpath, each group's x-complete head (xc[Z] entries, Z without bit 0)
+// takes the prebuilt x butterflies
 template <int Z = 0, class CH>
-__device__ __forceinline__ void walk_classes_fwd_all(const int* __restrict__ list, const int* zoff, const CH& ch,
-                                                     int tx, int ty, int tz, const int2* __restrict__ s_nb,
-                                                     const FwdParams& p, double (&acc)[16], int item) {
+__device__ __forceinline__ void walk_classes_fwd_all(const int* __restrict__ list, const int* zoff, const int* xc,
+                                                     bool xpath, const CH& ch, int tx, int ty, int tz,
+                                                     const int2* __restrict__ s_nb, const FwdParams& p,
+                                                     double (&acc)[16], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
-    walk_classes_fwd<Z>(list + zoff[Z] + ch.lo(len), ch.n(len), tx, ty, tz, s_nb, p, acc, item);
-    if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, ch, tx, ty, tz, s_nb, p, acc, item);
+    int nx = 0;
+    if constexpr ((Z & 1) == 0) {
+        if (xpath) {
+            nx = xc[Z];
+            walk_classes_fwd_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, p, acc, item);
+        }
+    }
+    walk_classes_fwd<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, item);
+    if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, p, acc, item);
 }
 
 // multipole sources by reflection class (non-leaf targets): the members'
@@ -509,14 +579,59 @@ __device__ __forceinline__ void walk_mclasses_fwd(const int* __restrict__ list, 
     }
 }
 
+// x-complete multipole classes of a node whose neighbours are all multipole
+// or empty: the first transform stage of every source component comes from
+// the prebuilt x butterflies at the positions t + (0, +-b, +-c)
+template <int Z, bool ANG>
+__device__ __forceinline__ void walk_mclasses_fwd_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                    const int2* __restrict__ s_nb, const FwdParams& p,
+                                                    double (&acc)[16], double (&c)[3], double (&t4)[9], int item) {
+    static_assert((Z & 1) == 0, "the x stage needs a > 0");
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int ox = e & 0xff, oy = (e >> 8) & 0xff, oz = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        const double* pos[4];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pos[q] = nullptr;
+            if ((2 * q) & Z) continue;
+            if ((members >> (2 * q)) & 1u) {
+                const int sy = (q & 1) ? ty - oy : ty + oy, sz = (q & 2) ? tz - oz : tz + oz;
+                const int2 es = s_nb[nb_index(tx, sy, sz)];
+                const int ks = checked_kind(p, es, item);
+                if (ks == K_MULTI) {
+                    pos[q] = p.Sx + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + ox - 1) * 32 * NCELL + (tx & 7) +
+                             8 * (sy & 7) + 64 * (sz & 7);
+                    any = true;
+                } else if (ks != K_NONE) {
+                    report(p.status, 7, item);    // the node's flag promised multipole or empty neighbours
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        ot_mclass_fwd_x<Z, ANG>(acc, c, t4, pos, p.Dt + static_cast<size_t>(offset_row(ox, oy, oz)) * DROW);
+    }
+}
+
 template <bool ANG, int Z = 0, class CH>
-__device__ __forceinline__ void walk_mclasses_fwd_all(const int* __restrict__ list, const int (&zoff)[8], const CH& ch,
-                                                      int tx, int ty, int tz, const int2* __restrict__ s_nb,
-                                                      const FwdParams& p, double (&acc)[16], double (&c)[3],
-                                                      double (&t4)[9], int item) {
+__device__ __forceinline__ void walk_mclasses_fwd_all(const int* __restrict__ list, const int (&zoff)[8],
+                                                      const int (&xc)[8], bool xpath, const CH& ch, int tx, int ty,
+                                                      int tz, const int2* __restrict__ s_nb, const FwdParams& p,
+                                                      double (&acc)[16], double (&c)[3], double (&t4)[9], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
-    walk_mclasses_fwd<Z, ANG>(list + zoff[Z] + ch.lo(len), ch.n(len), tx, ty, tz, s_nb, p, acc, c, t4, item);
-    if constexpr (Z < 6) walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, ch, tx, ty, tz, s_nb, p, acc, c, t4, item);
+    int nx = 0;
+    if constexpr ((Z & 1) == 0) {
+        if (xpath) {
+            nx = xc[Z];
+            walk_mclasses_fwd_x<Z, ANG>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, p, acc, c, t4, item);
+        }
+    }
+    walk_mclasses_fwd<Z, ANG>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, c, t4,
+                              item);
+    if constexpr (Z < 6)
+        walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, p, acc, c, t4, item);
 }
 
 template <int MODE, bool PAIRED, int EMU, bool NEAR = false, bool PM = true>
@@ -791,8 +906,9 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             // and near offsets; multipole sources (refined neighbours) over the
             // full far list, refined near sources over the near list
             const int2* nb = s_nb[warp];
+            const bool xpath = p.Sm != nullptr && (info & NI_XMASS);
             const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-            walk_classes_fwd_all(cf, p.L.cf_z, ch, tx, ty, tz, nb, p, a, it);
+            walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, p, a, it);
             cf += p.L.cf_z[7];
             walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -800,7 +916,7 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             walk_forward<2, false, EMU>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
                                         c, t4, f, it);
             const int* cn = p.L.lists + p.L.cn_off;
-            walk_classes_fwd_all(cn, p.L.cn_z, ch, tx, ty, tz, nb, p, a, it);
+            walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -824,11 +940,15 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             const int2* nb = s_nb[warp];
             if (MODE & 1) {
                 const bool root = level == 0;
-                int zo[8];
+                int zo[8], xc[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) zo[q] = root ? p.L.mr_z[q] : p.L.mf_z[q];
+                for (int q = 0; q < 8; ++q) {
+                    zo[q] = root ? p.L.mr_z[q] : p.L.mf_z[q];
+                    xc[q] = root ? p.L.mr_x[q] : p.L.mf_x[q];
+                }
+                const bool xpath = p.Sx != nullptr && (info & NI_XMULTI);
                 const int* ml = p.L.lists + (root ? p.L.mr_off : p.L.mf_off + par * p.L.mf_stride);
-                walk_mclasses_fwd_all<true>(ml, zo, ch, tx, ty, tz, nb, p, a, c, t4, it);
+                walk_mclasses_fwd_all<true>(ml, zo, xc, xpath, ch, tx, ty, tz, nb, p, a, c, t4, it);
                 ml += zo[7];
                 const int np = root ? p.L.mr_pairs : p.L.mf_pairs, ns = root ? 0 : p.L.mf_singles;
                 walk_forward<1, true, EMU>(ml + ch.lo(np), ch.n(np), true, tx, ty, tz, nb, p, a, c, t4, f, it);
@@ -2181,7 +2301,7 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
             DFAcc f;
             df_zero(f);
             const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-            walk_classes_fwd_all(cf, p.L.cf_z, ch, tx, ty, tz, nb, p, a, it);
+            walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, false, ch, tx, ty, tz, nb, p, a, it);
             cf += p.L.cf_z[7];
             walk_forward<2, true, 0>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                      t4, f, it);
@@ -2189,7 +2309,7 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
             walk_forward<2, false, 0>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
                                       c, t4, f, it);
             const int* cn = p.L.lists + p.L.cn_off;
-            walk_classes_fwd_all(cn, p.L.cn_z, ch, tx, ty, tz, nb, p, a, it);
+            walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, false, ch, tx, ty, tz, nb, p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, 0>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
                                      t4, f, it);
@@ -2614,9 +2734,89 @@ int adjoint_max_blocks_per_sm(int mode, int wpb) {
 
 static inline int blocks_for(long long n, int per) { return static_cast<int>((n + per - 1) / per); }
 
+// x butterflies for the first transform stage of x-complete classes: for
+// every cell c of the listed nodes (slot = list index) and a = 1..7,
+// v(c + a x) + v(c - a x) and v(c + a x) - v(c - a x), v the value the pass
+// reads at that position (reduced moments of multipole cells; point masses
+// of leaf and virtual cells), 0 elsewhere
+__global__ void xbutterfly_moments_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
+                                          const double* __restrict__ Mhat, int n_nodes, double* __restrict__ Sx) {
+    const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (gid >= 7LL * NCELL * n_list) return;
+    const int cell = static_cast<int>(gid % NCELL);
+    const int a = static_cast<int>((gid / NCELL) % 7) + 1;
+    const int slot = static_cast<int>(gid / (7 * NCELL));
+    const int node = __ldg(nodes + slot);
+    const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const double* src[2] = {nullptr, nullptr};
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        const int sx = sd ? x - a : x + a;
+        const int2 e = __ldg(nbr + static_cast<size_t>(node) * 27 + nb_index(sx, y, z));
+        if ((e.y & 3) == K_MULTI && static_cast<unsigned>(e.x) < static_cast<unsigned>(n_nodes))
+            src[sd] = Mhat + static_cast<size_t>(e.x) * NRED * NCELL + (sx & 7) + 8 * y + 64 * z;
+    }
+    double* out = Sx + static_cast<size_t>(slot * 7 + a - 1) * 32 * NCELL + cell;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const double vp = src[0] ? __ldg(src[0] + k * NCELL) : 0.0;
+        const double vm = src[1] ? __ldg(src[1] + k * NCELL) : 0.0;
+        out[(2 * k) * NCELL] = vp + vm;
+        out[(2 * k + 1) * NCELL] = vp - vm;
+    }
+}
+
+__device__ __forceinline__ double mass_at(const double* __restrict__ m, int2 e, int n_nodes, int sx, int sy, int sz) {
+    const int kind = e.y & 3;
+    if (static_cast<unsigned>(e.x) >= static_cast<unsigned>(n_nodes)) return 0.0;
+    if (kind == K_LEAF) return __ldg(m + static_cast<size_t>(e.x) * NCELL + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7));
+    if (kind == K_VIRT) {
+        const unsigned meta = static_cast<unsigned>(e.y);
+        const int d = (meta >> 2) & 7;
+        const int vx = static_cast<int>(((meta >> 8) & 0xffu) + (sx & 7)) >> d;
+        const int vy = static_cast<int>(((meta >> 16) & 0xffu) + (sy & 7)) >> d;
+        const int vz = static_cast<int>((meta >> 24) + (sz & 7)) >> d;
+        return __ldg(m + static_cast<size_t>(e.x) * NCELL + vx + 8 * vy + 64 * vz) * pow2i(-3 * d);
+    }
+    return 0.0;
+}
+
+__global__ void xbutterfly_masses_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
+                                         const double* __restrict__ m, int n_nodes, double* __restrict__ Sm) {
+    const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (gid >= 7LL * NCELL * n_list) return;
+    const int cell = static_cast<int>(gid % NCELL);
+    const int a = static_cast<int>((gid / NCELL) % 7) + 1;
+    const int slot = static_cast<int>(gid / (7 * NCELL));
+    const int node = __ldg(nodes + slot);
+    const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const int2* nb = nbr + static_cast<size_t>(node) * 27;
+    const double vp = mass_at(m, __ldg(nb + nb_index(x + a, y, z)), n_nodes, x + a, y, z);
+    const double vm = mass_at(m, __ldg(nb + nb_index(x - a, y, z)), n_nodes, x - a, y, z);
+    double* out = Sm + static_cast<size_t>(slot * 7 + a - 1) * 2 * NCELL + cell;
+    out[0] = vp + vm;
+    out[NCELL] = vp - vm;
+}
+
 cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s) {
     if (p.n_list == 0) return cudaSuccess;
     prescale_moments_kernel<<<blocks_for(1LL * p.n_list * NCELL, 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* nbr, const double* Mhat, int n_nodes,
+                                      double* Sx, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    xbutterfly_moments_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Mhat,
+                                                                                        n_nodes, Sx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
+                                     double* Sm, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    xbutterfly_masses_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, m, n_nodes,
+                                                                                       Sm);
     return cudaGetLastError();
 }
 

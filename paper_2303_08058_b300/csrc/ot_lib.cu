@@ -116,6 +116,14 @@ void derivative_row(const double R[3], double* row) {
 
 inline int pack_offset(int ox, int oy, int oz) { return (ox + 8) | ((oy + 8) << 8) | ((oz + 8) << 16); }
 inline int fdiv2(int a) { return (a >= 0) ? a / 2 : -((1 - a) / 2); }   // floor(a / 2)
+// a class entry whose members come in x pairs: at every (y, z) sign both or
+// neither of the members with x = +a, -a
+inline bool x_complete(int e) {
+    const unsigned m = static_cast<unsigned>(e) >> 24;
+    for (int q = 0; q < 4; ++q)
+        if (((m >> (2 * q)) & 1u) != ((m >> (2 * q + 1)) & 1u)) return false;
+    return true;
+}
 
 inline uint64_t node_key(int l, int x, int y, int z) {
     return (static_cast<uint64_t>(l) << 60) | (static_cast<uint64_t>(x) << 40) |
@@ -194,6 +202,13 @@ struct ot_grid {
     int2* d_cinfo = nullptr;
     double* d_part = nullptr;           // [slots][28][32] chunk accumulators
     int* d_chunk_ctr = nullptr;         // [counters] chunks finished per (node, parity, half)
+    // prebuilt x butterflies of the classes' first transform stage
+    std::vector<int> xslot;             // [n]: slot among the non-leaf (leaf) nodes
+    int n_xnonleaf = 0, n_xleaf = 0;
+    int* d_xslot = nullptr;
+    int* d_leaf = nullptr;              // leaf nodes in slot order
+    double* d_Sx = nullptr;             // [non-leaf slot][7][16][2][512]
+    double* d_Sm = nullptr;             // [leaf slot][7][2][512]
     // chunked multipole gather items of the adjoint (modes 1 and 3, and the
     // default adjoint's merged list); they share d_part and d_chunk_ctr
     std::vector<int> itemsc_adj[4], itemsc_adj_node[4], itemc_adj_start[4], itemsc_adj_fast1;
@@ -452,6 +467,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 singles.insert(singles.end(), ss.begin(), ss.end());
             }
         }
+        // within a group with a > 0, the x-complete classes first (both or
+        // neither of the x members at every (y, z) sign): their first
+        // transform stage can come from the prebuilt x butterflies
+        for (int z = 0; z < 8; z += 2)
+            std::stable_partition(cls[z].begin(), cls[z].end(), [](int e) { return x_complete(e); });
     };
     std::vector<int> cfar[8][8], cfar_pair[8], cfar_single[8], cnear[8], cnear_pair, cnear_single;
     for (int p = 0; p < 8; ++p) class_split(far_offs[p], cfar[p], cfar_pair[p], cfar_single[p], false);
@@ -480,6 +500,21 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     Lh.root_len = g->root_len;
     Lh.near_off = 8 * g->far_len;
     Lh.root_off = 8 * g->far_len + g->near_len;
+    // x-complete entries at the start of each group (the same count for every parity)
+    auto xcount = [](const std::vector<int>& v) {
+        int c = 0;
+        while (c < static_cast<int>(v.size()) && x_complete(v[c])) ++c;
+        return c;
+    };
+    for (int z = 0; z < 8; ++z) {
+        Lh.cf_x[z] = (z & 1) ? 0 : xcount(cfar[0][z]);
+        Lh.cn_x[z] = (z & 1) ? 0 : xcount(cnear[z]);
+        Lh.mf_x[z] = (z & 1) ? 0 : xcount(mfar[0][z]);
+        Lh.mr_x[z] = (z & 1) ? 0 : xcount(mroot[z]);
+        for (int p = 1; p < 8; ++p)
+            if (((z & 1) == 0) && (xcount(cfar[p][z]) != Lh.cf_x[z] || xcount(mfar[p][z]) != Lh.mf_x[z]))
+                return fail(OT_EINVAL, "internal: parity class stencils differ in shape");
+    }
     Lh.cf_z[0] = 0;
     for (int z = 0; z < 7; ++z) Lh.cf_z[z + 1] = Lh.cf_z[z] + static_cast<int>(cfar[0][z].size());
     Lh.cf_pairs = static_cast<int>(cfar_pair[0].size());
@@ -618,6 +653,24 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         vmap.insert(vmap.end(), ent.begin(), ent.end());
     }
 
+    // --- prebuilt x butterflies ----------------------------------------------
+    // A node's classes may read their first transform stage from per-cell x
+    // butterflies when every position of its 27-neighbourhood lies in a node
+    // whose butterflies are built (multipole sources: non-leaf nodes; point
+    // masses: leaf nodes) or outside the domain.  Slots: index among the
+    // non-leaf, resp. leaf, nodes.
+    g->xslot.assign(n, -1);
+    g->n_xnonleaf = g->n_xleaf = 0;
+    for (int i = 0; i < n; ++i) g->xslot[i] = g->is_leaf[i] ? g->n_xleaf++ : g->n_xnonleaf++;
+    for (int i = 0; i < n; ++i) {
+        bool same = true;
+        for (int j = 0; j < 27 && same; ++j) {
+            const int k = g->nbr[static_cast<size_t>(i) * 27 + j].y & 3;
+            same = k == K_NONE || k == (g->is_leaf[i] ? K_LEAF : K_MULTI);
+        }
+        if (same) g->ninfo[i] |= g->is_leaf[i] ? NI_XMASS : NI_XMULTI;
+    }
+
     // --- exact pair counts, FLOPs and per-item costs ------------------------
     // For each (parity, half) warp pattern and list entry: which of the 27
     // neighbours the warp's 32 cells reach (both sides of a paired entry), and
@@ -669,17 +722,26 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     std::vector<uint32_t> cmask[16][4];
     std::vector<int> ccost_f[4], ccost_s[4], cmem[4];
     double cfl_f[4][27], cfl_s[4][27], cop_f[4][27], cop_s[4][27];   // FLOPs; FP64 instructions
+    // the forward's figures for a node whose x-complete classes read the
+    // prebuilt x butterflies (the x stage's adds gone)
+    double cfl_fx[4][27], cop_fx[4][27];
+    std::vector<int> ccost_fx[4];
     std::memset(cfl_f, 0, sizeof(cfl_f));
     std::memset(cfl_s, 0, sizeof(cfl_s));
     std::memset(cop_f, 0, sizeof(cop_f));
     std::memset(cop_s, 0, sizeof(cop_s));
+    std::memset(cfl_fx, 0, sizeof(cfl_fx));
+    std::memset(cop_fx, 0, sizeof(cop_fx));
     for (int cg = 0; cg < 4; ++cg) {
         const int nz = cg == 0 ? g->Lh.cf_z[7] : cg == 1 ? g->Lh.cn_z[7] : cg == 2 ? g->Lh.mf_z[7] : g->Lh.mr_z[7];
         const int npair = cg == 0 ? g->Lh.cf_pairs : cg == 1 ? g->Lh.cn_pairs : cg == 2 ? g->Lh.mf_pairs : g->Lh.mr_pairs;
         const bool multi = cg >= 2;
         ccost_f[cg].resize(cseg_len[cg]);
+        ccost_fx[cg].resize(cseg_len[cg]);
         ccost_s[cg].resize(cseg_len[cg]);
         cmem[cg].resize(cseg_len[cg]);
+        const int* zx = cg == 0 ? g->Lh.cf_x : cg == 1 ? g->Lh.cn_x : cg == 2 ? g->Lh.mf_x : g->Lh.mr_x;
+        const int* zz = cg == 0 ? g->Lh.cf_z : cg == 1 ? g->Lh.cn_z : cg == 2 ? g->Lh.mf_z : g->Lh.mr_z;
         for (int ph = 0; ph < 16; ++ph) {
             const int par = ph >> 1, half = ph & 1;
             const int off = cg == 0 ? g->Lh.cf_off + par * g->Lh.cf_stride : cg == 1 ? g->Lh.cn_off
@@ -689,21 +751,29 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             for (int k = 0; k < cseg_len[cg]; ++k) {
                 const int e = lst[k];
                 std::vector<std::array<int, 3>> mem;
-                int cf, cs, fl_f, fl_s;
+                int cf, cs, fl_f, fl_s, cfx, fl_fx;
                 if (k < nz) {
                     const int a = e & 0xff, b = (e >> 8) & 0xff, cc = (e >> 16) & 0xff;
                     const int Z = (a == 0 ? 1 : 0) | (b == 0 ? 2 : 0) | (cc == 0 ? 4 : 0);
                     for (int t = 0; t < 8; ++t)
                         if ((static_cast<unsigned>(e) >> 24 >> t) & 1u)
                             mem.push_back({t & 1 ? -a : a, t & 2 ? -b : b, t & 4 ? -cc : cc});
+                    const bool xe = !(Z & 1) && k - zz[Z] < zx[Z];     // x-complete head of its group
                     if (multi) {   // forward with the angular term; the adjoint's gather
                         cf = OT_MCLASS_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z];
                         cs = OT_MCLASS_ADJ_ADDS[Z] + OT_MCLASS_ADJ_FMAS[Z];
                         fl_f = OT_MCLASS_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z];
                         fl_s = OT_MCLASS_ADJ_ADDS[Z] + 2 * OT_MCLASS_ADJ_FMAS[Z];
+                        cfx = xe ? OT_MCLASS_X_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z] : cf;
+                        fl_fx = xe ? OT_MCLASS_X_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z] : fl_f;
                     } else {
                         cf = cs = class_adds(Z) + class_fmas(Z);
                         fl_f = fl_s = class_adds(Z) + 2 * class_fmas(Z);
+                        // without the x stage: (d - 1) 2^d adds
+                        const int xadds = xe ? class_adds(Z) - (class_adds(Z) / std::max(1, 3 - __builtin_popcount(Z)))
+                                             : class_adds(Z);
+                        cfx = xadds + class_fmas(Z);
+                        fl_fx = xadds + 2 * class_fmas(Z);
                     }
                 } else {
                     const int ox = (e & 0xff) - 8, oy = ((e >> 8) & 0xff) - 8, oz = ((e >> 16) & 0xff) - 8;
@@ -720,8 +790,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         fl_f = multi ? 200 : 32;
                         fl_s = multi ? 140 : 32;
                     }
+                    cfx = cf;
+                    fl_fx = fl_f;
                 }
                 ccost_f[cg][k] = cf;
+                ccost_fx[cg][k] = cfx;
                 ccost_s[cg][k] = cs;
                 cmem[cg][k] = static_cast<int>(mem.size());
                 uint32_t m = 0;
@@ -735,6 +808,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         cfl_s[cg][nb] += static_cast<double>(fl_s) / mem.size();
                         cop_f[cg][nb] += static_cast<double>(cf) / mem.size();
                         cop_s[cg][nb] += static_cast<double>(cs) / mem.size();
+                        cfl_fx[cg][nb] += static_cast<double>(fl_fx) / mem.size();
+                        cop_fx[cg][nb] += static_cast<double>(cfx) / mem.size();
                     }
                 }
                 cmask[ph][cg][k] = m;
@@ -781,6 +856,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         const bool leaf = g->is_leaf[i];
         const int s1 = (desc->level[i] == 0) ? 2 : 0;
         const bool by_class = leaf && desc->level[i] > 0;   // point masses by reflection class
+        // the node's classes read the prebuilt x butterflies
+        const bool xnode = (g->ninfo[i] & (leaf ? NI_XMASS : NI_XMULTI)) != 0;
+        const auto& CFL = xnode ? cfl_fx : cfl_f;
+        const auto& COP = xnode ? cop_fx : cop_f;
+        const std::vector<int>* CCF = xnode ? ccost_fx : ccost_f;
         for (int j = 0; j < 27; ++j) {
             const long long cpf = cnt[s1][1][j], csf = cnt[s1][0][j];                 // far / root
             const long long cpn = leaf ? cnt[1][1][j] : 0, csn = leaf ? cnt[1][0][j] : 0;   // near
@@ -789,8 +869,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 pairs_multi += cpf + csf;
                 if (!leaf) {
                     pairs_ang += cpf + csf;
-                    flops_fwd += std::llround(cfl_f[desc->level[i] == 0 ? 3 : 2][j]);
-                    alg_fwd += cop_f[desc->level[i] == 0 ? 3 : 2][j];
+                    flops_fwd += std::llround(CFL[desc->level[i] == 0 ? 3 : 2][j]);
+                    alg_fwd += COP[desc->level[i] == 0 ? 3 : 2][j];
                 } else {
                     flops_fwd += 86 * cpf + 140 * csf;
                     alg_fwd += 51.0 * cpf + 70.0 * csf;
@@ -811,9 +891,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             if (mo >> j & 1u) {
                 pairs_mono += cp + cs;
                 if (by_class) {
-                    flops_fwd += std::llround(cfl_f[0][j] + cfl_f[1][j]);
+                    flops_fwd += std::llround(CFL[0][j] + CFL[1][j]);
                     flops_adj_scat += std::llround(cfl_s[0][j] + cfl_s[1][j]);
-                    alg_fwd += cop_f[0][j] + cop_f[1][j];
+                    alg_fwd += COP[0][j] + COP[1][j];
                     alg_adj_scat += cop_s[0][j] + cop_s[1][j];
                 } else {
                     flops_fwd += 17 * cp + 32 * cs;
@@ -860,7 +940,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 for (int cg = 0; cg < 2; ++cg)
                     for (size_t k = 0; k < cmask[ph][cg].size(); ++k)
                         if (cmask[ph][cg][k] & mo) {
-                            cost[2] += ccost_f[cg][k];
+                            cost[2] += CCF[cg][k];
                             cost_s += ccost_s[cg][k];
                             lanes += 32;
                             padded += 32 * cmem[cg][k];
@@ -872,7 +952,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 const int cgm = desc->level[i] == 0 ? 3 : 2;
                 for (size_t k = 0; k < cmask[ph][cgm].size(); ++k)
                     if (cmask[ph][cgm][k] & mm) {
-                        cost[1] += ccost_f[cgm][k];
+                        cost[1] += CCF[cgm][k];
                         lanes += 32;
                         padded += 32 * cmem[cgm][k];
                     }
@@ -1310,6 +1390,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_all, all);
     g->n_cube = static_cast<int>(cube.size());
     UP(g->d_cube, cube);
+    UP(g->d_leaf, cube);
+    UP(g->d_xslot, g->xslot);
     for (auto& L : g->m2m) {
         UP(L.d_parents, L.parents);
         UP(L.d_children, L.children);
@@ -1317,6 +1399,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_vmap, vmap);
 #undef UP
     if ((st = g->alloc(&g->d_Mhat, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Sx, static_cast<size_t>(std::max(g->n_xnonleaf, 1)) * 7 * 32 * NCELL)) != OT_OK)
+        return st;
+    if ((st = g->alloc(&g->d_Sm, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
@@ -1365,6 +1450,7 @@ static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, 
     p.status = g->d_status;
     p.child_of = g->d_child_of;
     p.Dv = g->d_Dv;
+    p.xslot = g->d_xslot;
     for (int l = 0; l < MAXLEV; ++l) p.hinv[l] = g->hinv[l];
     return p;
 }
@@ -1387,6 +1473,15 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
     if (!accumulate) OT_CUDA(cudaMemsetAsync(L, 0, nL * sizeof(double), s));
     if ((mode & 1) && Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
     FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
+    // prebuilt x butterflies of the class transforms (FP64 contractions only)
+    if ((mode & 1) && g->precision != 2 && g->n_xnonleaf > 0) {
+        OT_CUDA(launch_xbutterfly_moments(g->d_nonleaf, g->n_nonleaf, g->d_nbr, g->d_Mhat, g->n, g->d_Sx, s));
+        p.Sx = g->d_Sx;
+    }
+    if ((mode & 2) && g->precision == 0 && g->n_xleaf > 0) {
+        OT_CUDA(launch_xbutterfly_masses(g->d_leaf, g->n_xleaf, g->d_nbr, m, g->n, g->d_Sm, s));
+        p.Sm = g->d_Sm;
+    }
     const bool emu = g->precision >= 1 && (mode & 2);       // double-float point masses
     const bool emu2 = g->precision == 2 && (mode & 1);      // double-float multipole contractions
     if (emu) {
@@ -1925,6 +2020,9 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     p.cinfo = g->d_cinfo;
     p.part = g->d_part;
     p.chunk_ctr = g->d_chunk_ctr;
+    // and the x butterflies the warm-up built from the same M and m
+    if (g->precision != 2 && g->n_xnonleaf > 0) p.Sx = g->d_Sx;
+    if (g->precision == 0 && g->n_xleaf > 0) p.Sm = g->d_Sm;
     if (g->n_chunk_ctrs > 0) {
         OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs) * sizeof(int), streams[0]));
         OT_CUDA(cudaStreamSynchronize(streams[0]));

@@ -185,7 +185,8 @@ def test_multipole_class_contraction_matches_its_members(tmp_path):
     C++, against the per-source contraction (ot_multi_fwd + ot_angular_fwd)
     of each member with the derivatives at its own offset, for every zero
     pattern, with and without the angular term, and with members missing;
-    the same for the transposed gather (ot_multi_adj per target member)."""
+    the variant with the x butterflies prebuilt; the same for the transposed
+    gather (ot_multi_adj per target member)."""
     import shutil
     import subprocess
     if shutil.which("g++") is None:
@@ -203,6 +204,12 @@ def test_multipole_class_contraction_matches_its_members(tmp_path):
         for ang in ("", "_ang"):
             src += routine(f"ot_mclass_fwd_z{Z}{ang}")
         src += routine(f"ot_mclass_adj_z{Z}")
+    for Z in (0, 2, 4, 6):
+        for ang in ("", "_ang"):
+            src += routine(f"ot_mclass_fwd_x_z{Z}{ang}")
+    src += "typedef void (*x_fn)(double (&)[16], double (&)[3], double (&)[9], const double* const (&)[4], const double*);\n"
+    src += "static x_fn x_table[2][4] = {{" + ", ".join(f"ot_mclass_fwd_x_z{Z}" for Z in (0, 2, 4, 6)) + "}, {" + \
+        ", ".join(f"ot_mclass_fwd_x_z{Z}_ang" for Z in (0, 2, 4, 6)) + "}};\n"
     src += "typedef void (*adj_fn)(double (&)[16], const double* const (&)[8], const double*);\n"
     src += "static adj_fn adj_table[7] = {" + ", ".join(f"ot_mclass_adj_z{Z}" for Z in range(7)) + "};\n"
     src += "typedef void (*cls_fn)(double (&)[16], double (&)[3], double (&)[9], const double* const (&)[8], const double*);\n"
@@ -230,6 +237,26 @@ extern "C" void run_members(int ox, int oy, int oz, int ang, const double* r, in
         ot_multi_fwd(a, rr, d);
         if (ang) ot_angular_fwd(c, t4, rr, rr[0], d);
     }
+    for (int i = 0; i < 16; ++i) out[i] = a[i];
+    for (int i = 0; i < 3; ++i) out[16 + i] = c[i];
+    for (int i = 0; i < 9; ++i) out[19 + i] = t4[i];
+}
+extern "C" void run_class_x(int Z, int ang, const double* r, int mask, const double* row, double* out) {
+    // the x butterflies of the members at the four (y, z) sign positions
+    double S[4][32];
+    const double* p[4];
+    for (int q = 0; q < 4; ++q) {
+        for (int k = 0; k < 16; ++k) {
+            const int ip = q << 1, im = (q << 1) | 1;
+            const double vp = ((mask >> ip) & 1) ? r[16 * ip + k] : 0.0;
+            const double vm = ((mask >> im) & 1) ? r[16 * im + k] : 0.0;
+            S[q][2 * k] = vp + vm;
+            S[q][2 * k + 1] = vp - vm;
+        }
+        p[q] = S[q];
+    }
+    double a[16] = {0}, c[3] = {0}, t4[9] = {0};
+    x_table[ang][Z >> 1](a, c, t4, p, row);
     for (int i = 0; i < 16; ++i) out[i] = a[i];
     for (int i = 0; i < 3; ++i) out[16 + i] = c[i];
     for (int i = 0; i < 9; ++i) out[19 + i] = t4[i];
@@ -283,6 +310,10 @@ extern "C" void row_at(int ox, int oy, int oz, double* out) {
                 assert np.max(np.abs(got - want)) <= 1e-13 * scale, ((ox, oy, oz), ang, mask, got - want)
                 if not ang:
                     assert np.all(got[16:] == 0)
+                if not (Z & 1):       # the x stage prebuilt
+                    gx = np.zeros(28)
+                    lib.run_class_x(Z, ang, r.ctypes.data_as(dp), mask, row.ctypes.data_as(dp), gx.ctypes.data_as(dp))
+                    assert np.max(np.abs(gx - want)) <= 1e-13 * scale, ((ox, oy, oz), ang, mask, "x")
         # the gather by source: targets at +s*o, the table row of -o
         mrow = np.zeros(36)
         lib.row_at(-ox, -oy, -oz, mrow.ctypes.data_as(dp))
