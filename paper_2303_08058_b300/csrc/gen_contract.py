@@ -368,6 +368,42 @@ def mclass_adj_code(Z):
     return name, "".join(lines), n_add, n_fma
 
 
+def mclass_adj_x_code(Z):
+    """ot_mclass_adj_code with the x stage prebuilt (the member targets'
+    L-bar x butterflies at the positions q = B + (0, +-b, +-c))"""
+    assert not (Z & 1)
+    name = f"ot_mclass_adj_x_z{Z}"
+    lines = [f"__device__ __forceinline__ void {name}(double (&g)[16], const double* const (&pos)[4],\n"
+             f"    const double* __restrict__ row) {{\n"]
+    terms = {j: [] for j in range(16)}
+    for j, ej in enumerate(IND16):
+        for k, ek in enumerate(IND16):
+            if rank(ej) + rank(ek) <= 3:
+                e = add(ej, ek)
+                if not (parity(e) & Z):
+                    terms[j].append((parity(e), k, ROWIDX[e]))
+    n_add = n_fma = 0
+    for j in range(16):
+        if not terms[j]:
+            continue
+        lines.append("  {\n")
+        need = sorted({pi for (pi, _, _) in terms[j]})
+        ops, nst = transform_plan(Z, need, first=0)
+        for (t, x, op, lo, hi) in ops:
+            if t == 1:
+                q = (x >> 1) & 3
+                lines.append(f"    const double v1_{x} = pos[{q}] ? __ldg(pos[{q}] + {2 * j + (x & 1)} * NCELL) : 0.0;\n")
+            else:
+                lines.append(f"    const double v{t}_{x} = v{t - 1}_{lo} {op} v{t - 1}_{hi};\n")
+                n_add += 1
+        for (pi, k, di) in terms[j]:
+            lines.append(f"    g[{k}] = fma(v{nst}_{pi}, __ldg(row + {di}), g[{k}]);\n")
+            n_fma += 1
+        lines.append("  }\n")
+    lines.append("}\n\n")
+    return name, "".join(lines), n_add, n_fma
+
+
 def emit():
     out = []
     w = out.append
@@ -602,6 +638,16 @@ def emit():
         name, code, n_add, n_fma = mclass_adj_code(Z)
         w(f"// adjoint: {n_add} adds + {n_fma} FMAs\n")
         w(code)
+    for Z in (0, 2, 4, 6):
+        name, code, n_add, n_fma = mclass_adj_x_code(Z)
+        w(f"// adjoint, x stage prebuilt: {n_add} adds + {n_fma} FMAs\n")
+        w(code)
+    w("template <int Z>\n"
+      "__device__ __forceinline__ void ot_mclass_adj_x(double (&g)[16], const double* const (&pos)[4],\n"
+      "                                                const double* __restrict__ row) {\n")
+    for i, Z in enumerate((0, 2, 4, 6)):
+        w(f"  {'if' if i == 0 else 'else if'} constexpr (Z == {Z}) ot_mclass_adj_x_z{Z}(g, pos, row);\n")
+    w("}\n\n")
     w("template <int Z>\n"
       "__device__ __forceinline__ void ot_mclass_adj(double (&g)[16], const double* const (&src)[8],\n"
       "                                              const double* __restrict__ row) {\n")
@@ -657,6 +703,9 @@ def emit_counts():
     xa = {(ang, Z): (mclass_fwd_x_code(Z, ang)[2] if not (Z & 1) else 0) for ang in (False, True) for Z in range(7)}
     out.append("constexpr int OT_MCLASS_X_ADDS[2][7] = {" + ", ".join(
         "{" + ", ".join(str(xa[ang, Z]) for Z in range(7)) + "}" for ang in (False, True)) + "};\n")
+    ax = [mclass_adj_x_code(Z)[2] if not (Z & 1) else 0 for Z in range(7)]
+    out.append("// FP64 adds of ot_mclass_adj_x_z<Z> (x stage prebuilt; 0 for Z with bit 0)\n")
+    out.append("constexpr int OT_MCLASS_ADJ_X_ADDS[7] = {" + ", ".join(str(a) for a in ax) + "};\n")
     out.append("// FP64 adds and FMAs of ot_mclass_adj_z<Z>\n")
     cnt = [mclass_adj_code(Z)[2:] for Z in range(7)]
     out.append("constexpr int OT_MCLASS_ADJ_ADDS[7] = {" + ", ".join(str(a) for a, _ in cnt) + "};\n")

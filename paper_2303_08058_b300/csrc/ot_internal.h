@@ -146,6 +146,9 @@ struct AdjParams {
     const float2* Lf;      // [n][16][512] reduced L-bar as (hi, lo) pairs
     const float2* Dt2;     // [NOFF][DROW] the derivative table as (hi, lo) pairs
     const float* Dt32;     // [NOFF][32] hi then lo parts of the 16 point-mass derivatives
+    // prebuilt x butterflies of the targets' reduced L-bar (null: not built)
+    const double* Tx;      // [tslot][7][16][2][512]: Lrbar(c + a x) +- Lrbar(c - a x) over real cells
+    const int* tslot;      // [n]: slot of a node at a level with non-leaf nodes, else -1
     // chunked multipole gather items (bit 31 set: source in bits 4-25, chunk
     // index in bits 26-29); null: every item is whole
     const int2* cinfo;     // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
@@ -186,6 +189,9 @@ struct PrepParams {
 // point masses (a leaf node whose neighbours are all leaf or empty)
 constexpr int NI_XMULTI = 1 << 9;
 constexpr int NI_XMASS = 1 << 10;
+// bit 11: a non-leaf source whose multipole gather may read the targets'
+// prebuilt L-bar x butterflies (no virtual neighbour)
+constexpr int NI_XGATHER = 1 << 11;
 
 // launchers (ot_kernels.cu)
 cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid,
@@ -195,6 +201,8 @@ cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wp
 cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s);
 cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* nbr, const double* Mhat, int n_nodes,
                                       double* Sx, cudaStream_t s);
+cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr, const double* Lrbar, int n_nodes,
+                                   double* Tx, cudaStream_t s);
 cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
                                      double* Sm, cudaStream_t s);
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);

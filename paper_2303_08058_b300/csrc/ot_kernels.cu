@@ -1183,13 +1183,62 @@ __device__ __forceinline__ void walk_mclasses_adj(const int* __restrict__ list, 
     }
 }
 
+// x-complete classes of a source whose neighbours are real or empty: the
+// first transform stage of every target component comes from the prebuilt
+// L-bar x butterflies at the positions B + (0, +-b, +-c)
+template <int Z>
+__device__ __forceinline__ void walk_mclasses_adj_x(const int* __restrict__ list, int len, int sx0, int sy0, int sz0,
+                                                    const int2* __restrict__ s_nb, const AdjParams& p,
+                                                    double (&g)[16], int item) {
+    static_assert((Z & 1) == 0, "the x stage needs a > 0");
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int ox = e & 0xff, oy = (e >> 8) & 0xff, oz = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        const double* pos[4];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pos[q] = nullptr;
+            if ((2 * q) & Z) continue;
+            if ((members >> (2 * q)) & 1u) {
+                const int ty = (q & 1) ? sy0 - oy : sy0 + oy, tz = (q & 2) ? sz0 - oz : sz0 + oz;
+                const int2 et = s_nb[nb_index(sx0, ty, tz)];
+                const int kt = et.y & 3;
+                if ((kt == K_MULTI || kt == K_LEAF) && static_cast<unsigned>(et.x) < static_cast<unsigned>(p.n_nodes)) {
+                    const int slot = __ldg(p.tslot + et.x);
+                    if (slot >= 0) {
+                        pos[q] = p.Tx + static_cast<size_t>(slot * 7 + ox - 1) * 32 * NCELL + (sx0 & 7) +
+                                 8 * (ty & 7) + 64 * (tz & 7);
+                        any = true;
+                    } else {
+                        report(p.status, 7, item);
+                    }
+                } else if (kt != K_NONE) {
+                    report(p.status, 7, item);    // the source's flag promised real or empty neighbours
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        ot_mclass_adj_x<Z>(g, pos, p.Dt + static_cast<size_t>(NOFF - 1 - offset_row(ox, oy, oz)) * DROW);
+    }
+}
+
 template <int Z = 0, class CH>
-__device__ __forceinline__ void walk_mclasses_adj_all(const int* __restrict__ list, const int (&zoff)[8], const CH& ch,
-                                                      int sx0, int sy0, int sz0, const int2* __restrict__ s_nb,
-                                                      const AdjParams& p, double (&g)[16], int item) {
+__device__ __forceinline__ void walk_mclasses_adj_all(const int* __restrict__ list, const int (&zoff)[8],
+                                                      const int (&xc)[8], bool xpath, const CH& ch, int sx0, int sy0,
+                                                      int sz0, const int2* __restrict__ s_nb, const AdjParams& p,
+                                                      double (&g)[16], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
-    walk_mclasses_adj<Z>(list + zoff[Z] + ch.lo(len), ch.n(len), sx0, sy0, sz0, s_nb, p, g, item);
-    if constexpr (Z < 6) walk_mclasses_adj_all<Z + 1>(list, zoff, ch, sx0, sy0, sz0, s_nb, p, g, item);
+    int nx = 0;
+    if constexpr ((Z & 1) == 0) {
+        if (xpath) {
+            nx = xc[Z];
+            walk_mclasses_adj_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), sx0, sy0, sz0, s_nb, p, g, item);
+        }
+    }
+    walk_mclasses_adj<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), sx0, sy0, sz0, s_nb, p, g, item);
+    if constexpr (Z < 6) walk_mclasses_adj_all<Z + 1>(list, zoff, xc, xpath, ch, sx0, sy0, sz0, s_nb, p, g, item);
 }
 
 // M-bar of one source cell from the gathered g (reduced, h-scaled): expand
@@ -1304,11 +1353,15 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int 
                     // by reflection class (root or far list of the source's
                     // parity), then the classes' leftover pairs and singles
                     const bool root = level == 0;
-                    int zo[8];
+                    int zo[8], xc[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) zo[q] = root ? p.L.mr_z[q] : p.L.mf_z[q];
+                    for (int q = 0; q < 8; ++q) {
+                        zo[q] = root ? p.L.mr_z[q] : p.L.mf_z[q];
+                        xc[q] = root ? p.L.mr_x[q] : p.L.mf_x[q];
+                    }
+                    const bool xpath = p.Tx != nullptr && (__ldg(p.ninfo + src) & NI_XGATHER);
                     const int* ml = p.L.lists + (root ? p.L.mr_off : p.L.mf_off + par * p.L.mf_stride);
-                    walk_mclasses_adj_all(ml, zo, ch, sx, sy, sz, s_nb[warp], p, g, it);
+                    walk_mclasses_adj_all(ml, zo, xc, xpath, ch, sx, sy, sz, s_nb[warp], p, g, it);
                     ml += zo[7];
                     const int np = root ? p.L.mr_pairs : p.L.mf_pairs, ns = root ? 0 : p.L.mf_singles;
                     walk_adjoint<true, true>(ml + ch.lo(np), ch.n(np), false, false, sx, sy, sz, s_nb[warp], p, g, g4,
@@ -2766,6 +2819,36 @@ __global__ void xbutterfly_moments_kernel(const int* __restrict__ nodes, int n_l
     }
 }
 
+// the same over the targets' reduced L-bar: multipole and leaf cells of the
+// node's level (the multipole gather's targets)
+__global__ void xbutterfly_lbar_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
+                                       const double* __restrict__ Lrbar, int n_nodes, double* __restrict__ Tx) {
+    const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (gid >= 7LL * NCELL * n_list) return;
+    const int cell = static_cast<int>(gid % NCELL);
+    const int a = static_cast<int>((gid / NCELL) % 7) + 1;
+    const int slot = static_cast<int>(gid / (7 * NCELL));
+    const int node = __ldg(nodes + slot);
+    const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const double* src[2] = {nullptr, nullptr};
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        const int sx = sd ? x - a : x + a;
+        const int2 e = __ldg(nbr + static_cast<size_t>(node) * 27 + nb_index(sx, y, z));
+        const int k = e.y & 3;
+        if ((k == K_MULTI || k == K_LEAF) && static_cast<unsigned>(e.x) < static_cast<unsigned>(n_nodes))
+            src[sd] = Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + (sx & 7) + 8 * y + 64 * z;
+    }
+    double* out = Tx + static_cast<size_t>(slot * 7 + a - 1) * 32 * NCELL + cell;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const double vp = src[0] ? __ldg(src[0] + k * NCELL) : 0.0;
+        const double vm = src[1] ? __ldg(src[1] + k * NCELL) : 0.0;
+        out[(2 * k) * NCELL] = vp + vm;
+        out[(2 * k + 1) * NCELL] = vp - vm;
+    }
+}
+
 __device__ __forceinline__ double mass_at(const double* __restrict__ m, int2 e, int n_nodes, int sx, int sy, int sz) {
     const int kind = e.y & 3;
     if (static_cast<unsigned>(e.x) >= static_cast<unsigned>(n_nodes)) return 0.0;
@@ -2809,6 +2892,14 @@ cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* 
     if (n_list == 0) return cudaSuccess;
     xbutterfly_moments_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Mhat,
                                                                                         n_nodes, Sx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr, const double* Lrbar, int n_nodes,
+                                   double* Tx, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    xbutterfly_lbar_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Lrbar, n_nodes,
+                                                                                     Tx);
     return cudaGetLastError();
 }
 

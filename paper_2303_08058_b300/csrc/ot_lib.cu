@@ -209,6 +209,10 @@ struct ot_grid {
     int* d_leaf = nullptr;              // leaf nodes in slot order
     double* d_Sx = nullptr;             // [non-leaf slot][7][16][2][512]
     double* d_Sm = nullptr;             // [leaf slot][7][2][512]
+    std::vector<int> tslot, tnodes;     // the gather's L-bar butterflies: slot per node, nodes per slot
+    int* d_tslot = nullptr;
+    int* d_tnodes = nullptr;
+    double* d_Tx = nullptr;             // [tslot][7][16][2][512]
     // chunked multipole gather items of the adjoint (modes 1 and 3, and the
     // default adjoint's merged list); they share d_part and d_chunk_ctr
     std::vector<int> itemsc_adj[4], itemsc_adj_node[4], itemc_adj_start[4], itemsc_adj_fast1;
@@ -670,6 +674,27 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         }
         if (same) g->ninfo[i] |= g->is_leaf[i] ? NI_XMASS : NI_XMULTI;
     }
+    // the adjoint's gather: butterflies of the targets' L-bar for every node
+    // of a level that has non-leaf nodes; a non-leaf source without virtual
+    // neighbours reads them
+    {
+        std::vector<char> lvl_nonleaf(MAXLEV, 0);
+        for (int i = 0; i < n; ++i)
+            if (!g->is_leaf[i]) lvl_nonleaf[desc->level[i]] = 1;
+        g->tslot.assign(n, -1);
+        g->tnodes.clear();
+        for (int i = 0; i < n; ++i)
+            if (lvl_nonleaf[desc->level[i]]) {
+                g->tslot[i] = static_cast<int>(g->tnodes.size());
+                g->tnodes.push_back(i);
+            }
+        for (int i = 0; i < n; ++i) {
+            if (g->is_leaf[i]) continue;
+            bool real = true;
+            for (int j = 0; j < 27 && real; ++j) real = (g->nbr[static_cast<size_t>(i) * 27 + j].y & 3) != K_VIRT;
+            if (real) g->ninfo[i] |= NI_XGATHER;
+        }
+    }
 
     // --- exact pair counts, FLOPs and per-item costs ------------------------
     // For each (parity, half) warp pattern and list entry: which of the 27
@@ -724,20 +749,23 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     double cfl_f[4][27], cfl_s[4][27], cop_f[4][27], cop_s[4][27];   // FLOPs; FP64 instructions
     // the forward's figures for a node whose x-complete classes read the
     // prebuilt x butterflies (the x stage's adds gone)
-    double cfl_fx[4][27], cop_fx[4][27];
-    std::vector<int> ccost_fx[4];
+    double cfl_fx[4][27], cop_fx[4][27], cfl_sx[4][27], cop_sx[4][27];
+    std::vector<int> ccost_fx[4], ccost_sx[4];
     std::memset(cfl_f, 0, sizeof(cfl_f));
     std::memset(cfl_s, 0, sizeof(cfl_s));
     std::memset(cop_f, 0, sizeof(cop_f));
     std::memset(cop_s, 0, sizeof(cop_s));
     std::memset(cfl_fx, 0, sizeof(cfl_fx));
     std::memset(cop_fx, 0, sizeof(cop_fx));
+    std::memset(cfl_sx, 0, sizeof(cfl_sx));
+    std::memset(cop_sx, 0, sizeof(cop_sx));
     for (int cg = 0; cg < 4; ++cg) {
         const int nz = cg == 0 ? g->Lh.cf_z[7] : cg == 1 ? g->Lh.cn_z[7] : cg == 2 ? g->Lh.mf_z[7] : g->Lh.mr_z[7];
         const int npair = cg == 0 ? g->Lh.cf_pairs : cg == 1 ? g->Lh.cn_pairs : cg == 2 ? g->Lh.mf_pairs : g->Lh.mr_pairs;
         const bool multi = cg >= 2;
         ccost_f[cg].resize(cseg_len[cg]);
         ccost_fx[cg].resize(cseg_len[cg]);
+        ccost_sx[cg].resize(cseg_len[cg]);
         ccost_s[cg].resize(cseg_len[cg]);
         cmem[cg].resize(cseg_len[cg]);
         const int* zx = cg == 0 ? g->Lh.cf_x : cg == 1 ? g->Lh.cn_x : cg == 2 ? g->Lh.mf_x : g->Lh.mr_x;
@@ -751,7 +779,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             for (int k = 0; k < cseg_len[cg]; ++k) {
                 const int e = lst[k];
                 std::vector<std::array<int, 3>> mem;
-                int cf, cs, fl_f, fl_s, cfx, fl_fx;
+                int cf, cs, fl_f, fl_s, cfx, fl_fx, csx, fl_sx;
                 if (k < nz) {
                     const int a = e & 0xff, b = (e >> 8) & 0xff, cc = (e >> 16) & 0xff;
                     const int Z = (a == 0 ? 1 : 0) | (b == 0 ? 2 : 0) | (cc == 0 ? 4 : 0);
@@ -766,6 +794,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         fl_s = OT_MCLASS_ADJ_ADDS[Z] + 2 * OT_MCLASS_ADJ_FMAS[Z];
                         cfx = xe ? OT_MCLASS_X_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z] : cf;
                         fl_fx = xe ? OT_MCLASS_X_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z] : fl_f;
+                        csx = xe ? OT_MCLASS_ADJ_X_ADDS[Z] + OT_MCLASS_ADJ_FMAS[Z] : cs;
+                        fl_sx = xe ? OT_MCLASS_ADJ_X_ADDS[Z] + 2 * OT_MCLASS_ADJ_FMAS[Z] : fl_s;
                     } else {
                         cf = cs = class_adds(Z) + class_fmas(Z);
                         fl_f = fl_s = class_adds(Z) + 2 * class_fmas(Z);
@@ -774,6 +804,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                                              : class_adds(Z);
                         cfx = xadds + class_fmas(Z);
                         fl_fx = xadds + 2 * class_fmas(Z);
+                        csx = cs;           // the scatter transforms on the output side: no x table
+                        fl_sx = fl_s;
                     }
                 } else {
                     const int ox = (e & 0xff) - 8, oy = ((e >> 8) & 0xff) - 8, oz = ((e >> 16) & 0xff) - 8;
@@ -792,9 +824,12 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     }
                     cfx = cf;
                     fl_fx = fl_f;
+                    csx = cs;
+                    fl_sx = fl_s;
                 }
                 ccost_f[cg][k] = cf;
                 ccost_fx[cg][k] = cfx;
+                ccost_sx[cg][k] = csx;
                 ccost_s[cg][k] = cs;
                 cmem[cg][k] = static_cast<int>(mem.size());
                 uint32_t m = 0;
@@ -810,6 +845,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         cop_s[cg][nb] += static_cast<double>(cs) / mem.size();
                         cfl_fx[cg][nb] += static_cast<double>(fl_fx) / mem.size();
                         cop_fx[cg][nb] += static_cast<double>(cfx) / mem.size();
+                        cfl_sx[cg][nb] += static_cast<double>(fl_sx) / mem.size();
+                        cop_sx[cg][nb] += static_cast<double>(csx) / mem.size();
                     }
                 }
                 cmask[ph][cg][k] = m;
@@ -1065,12 +1102,15 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 flops_adj += 32 * (cp + cs);
                 alg_adj_det += 16.0 * (cp + cs);
             } else if (((tv | tw) >> j) & 1u) {
-                // multipole gather by class (segment 2 far, 3 root)
-                const long long fl = std::llround(cfl_s[lvl == 0 ? 3 : 2][j]);
+                // multipole gather by class (segment 2 far, 3 root), with the
+                // targets' prebuilt x butterflies when the source is flagged
+                const bool xs = !virt && (g->ninfo[i] & NI_XGATHER);
+                const int sg = lvl == 0 ? 3 : 2;
+                const long long fl = std::llround(xs ? cfl_sx[sg][j] : cfl_s[sg][j]);
                 flops_adj += fl;
                 flops_adj_multi += fl;
-                alg_adj_det += cop_s[lvl == 0 ? 3 : 2][j];
-                alg_adj_multi += cop_s[lvl == 0 ? 3 : 2][j];
+                alg_adj_det += xs ? cop_sx[sg][j] : cop_s[sg][j];
+                alg_adj_multi += xs ? cop_sx[sg][j] : cop_s[sg][j];
             }
         }
         const int bit = leaf ? 2 : 1;
@@ -1082,8 +1122,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     if (mask[ph][s1][k] & (tv | tw)) cst += pflag[ph][s1][k] ? 32 : 16;
             } else {
                 const int cgm = lvl == 0 ? 3 : 2;
+                const bool xs = !virt && (g->ninfo[i] & NI_XGATHER);
                 for (size_t k = 0; k < cmask[ph][cgm].size(); ++k)
-                    if (cmask[ph][cgm][k] & tv) cst += ccost_s[cgm][k];
+                    if (cmask[ph][cgm][k] & tv) cst += xs ? ccost_sx[cgm][k] : ccost_s[cgm][k];
             }
             if (leaf)
                 for (size_t k = 0; k < mask[ph][1].size(); ++k)
@@ -1392,6 +1433,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_cube, cube);
     UP(g->d_leaf, cube);
     UP(g->d_xslot, g->xslot);
+    UP(g->d_tslot, g->tslot);
+    UP(g->d_tnodes, g->tnodes);
     for (auto& L : g->m2m) {
         UP(L.d_parents, L.parents);
         UP(L.d_children, L.children);
@@ -1402,6 +1445,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if ((st = g->alloc(&g->d_Sx, static_cast<size_t>(std::max(g->n_xnonleaf, 1)) * 7 * 32 * NCELL)) != OT_OK)
         return st;
     if ((st = g->alloc(&g->d_Sm, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Tx, static_cast<size_t>(std::max<size_t>(g->tnodes.size(), 1)) * 7 * 32 * NCELL)) !=
+        OT_OK)
+        return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
@@ -1588,7 +1634,14 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
         p.chunk_ctr = g->d_chunk_ctr;
         if (g->n_chunk_ctrs_adj > 0)
             OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs_adj) * sizeof(int), s));
+        // the targets' L-bar x butterflies for the FP64 multipole gather
+        if (g->precision != 2 && !g->tnodes.empty()) {
+            OT_CUDA(launch_xbutterfly_lbar(g->d_tnodes, static_cast<int>(g->tnodes.size()), g->d_nbr, g->d_Lrbar, g->n,
+                                           g->d_Tx, s));
+            p.Tx = g->d_Tx;
+        }
     }
+    p.tslot = g->d_tslot;
     p.counter = g->d_counters + 1;
     p.nbr = g->d_nbr;
     p.vnbr = g->d_vnbr;

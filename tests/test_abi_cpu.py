@@ -210,6 +210,10 @@ def test_multipole_class_contraction_matches_its_members(tmp_path):
     src += "typedef void (*x_fn)(double (&)[16], double (&)[3], double (&)[9], const double* const (&)[4], const double*);\n"
     src += "static x_fn x_table[2][4] = {{" + ", ".join(f"ot_mclass_fwd_x_z{Z}" for Z in (0, 2, 4, 6)) + "}, {" + \
         ", ".join(f"ot_mclass_fwd_x_z{Z}_ang" for Z in (0, 2, 4, 6)) + "}};\n"
+    for Z in (0, 2, 4, 6):
+        src += routine(f"ot_mclass_adj_x_z{Z}")
+    src += "typedef void (*adjx_fn)(double (&)[16], const double* const (&)[4], const double*);\n"
+    src += "static adjx_fn adjx_table[4] = {" + ", ".join(f"ot_mclass_adj_x_z{Z}" for Z in (0, 2, 4, 6)) + "};\n"
     src += "typedef void (*adj_fn)(double (&)[16], const double* const (&)[8], const double*);\n"
     src += "static adj_fn adj_table[7] = {" + ", ".join(f"ot_mclass_adj_z{Z}" for Z in range(7)) + "};\n"
     src += "typedef void (*cls_fn)(double (&)[16], double (&)[3], double (&)[9], const double* const (&)[8], const double*);\n"
@@ -268,6 +272,23 @@ extern "C" void run_class_adj(int Z, const double* r, int mask, const double* ro
     adj_table[Z](g, p, row);
     for (int i = 0; i < 16; ++i) out[i] = g[i];
 }
+extern "C" void run_class_adj_x(int Z, const double* r, int mask, const double* row, double* out) {
+    double S[4][32];
+    const double* p[4];
+    for (int q = 0; q < 4; ++q) {
+        for (int k = 0; k < 16; ++k) {
+            const int ip = q << 1, im = (q << 1) | 1;
+            const double vp = ((mask >> ip) & 1) ? r[16 * ip + k] : 0.0;
+            const double vm = ((mask >> im) & 1) ? r[16 * im + k] : 0.0;
+            S[q][2 * k] = vp + vm;
+            S[q][2 * k + 1] = vp - vm;
+        }
+        p[q] = S[q];
+    }
+    double g[16] = {0};
+    adjx_table[Z >> 1](g, p, row);
+    for (int i = 0; i < 16; ++i) out[i] = g[i];
+}
 extern "C" void run_members_adj(int ox, int oy, int oz, const double* r, int mask, double* out) {
     double g[16] = {0};
     for (int i = 0; i < 8; ++i) {
@@ -324,3 +345,7 @@ extern "C" void row_at(int ox, int oy, int oz, double* out) {
             lib.run_class_adj(Z, r.ctypes.data_as(dp), mask, mrow.ctypes.data_as(dp), got.ctypes.data_as(dp))
             lib.run_members_adj(ox, oy, oz, r.ctypes.data_as(dp), mask, want.ctypes.data_as(dp))
             assert np.max(np.abs(got - want)) <= 1e-13 * (np.max(np.abs(want)) + 1e-300), ((ox, oy, oz), mask)
+            if not (Z & 1):
+                gx = np.zeros(16)
+                lib.run_class_adj_x(Z, r.ctypes.data_as(dp), mask, mrow.ctypes.data_as(dp), gx.ctypes.data_as(dp))
+                assert np.max(np.abs(gx - want)) <= 1e-13 * (np.max(np.abs(want)) + 1e-300), ((ox, oy, oz), mask)
