@@ -149,6 +149,12 @@ struct AdjParams {
     // prebuilt x butterflies of the targets' reduced L-bar (null: not built)
     const double* Tx;      // [tslot][7][16][2][512]: Lrbar(c + a x) +- Lrbar(c - a x) over real cells
     const int* tslot;      // [n]: slot of a node at a level with non-leaf nodes, else -1
+    // the point-mass scatter's x stage deferred (null: scatter to mbar directly):
+    // a leaf target with leaf or empty neighbours adds its x-complete classes'
+    // two x channels at the positions t + (0, +-b, +-c), and a later pass
+    // (xbutterfly_masses_adjoint) forms the members' sums and differences
+    double* Sbar;          // [leaf slot][7][2][512], zeroed before the launch
+    const int* xslot;      // [n]: leaf slot
     // chunked multipole gather items (bit 31 set: source in bits 4-25, chunk
     // index in bits 26-29); null: every item is whole
     const int2* cinfo;     // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
@@ -172,6 +178,8 @@ struct ScatParams {
     int* status;
     const int* child_of;   // as in FwdParams
     const double* Dv;
+    double* Sbar;          // as in AdjParams (null here: the plain schedule scatters directly)
+    const int* xslot;
 };
 
 struct PrepParams {
@@ -203,6 +211,8 @@ cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* 
                                       double* Sx, cudaStream_t s);
 cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr, const double* Lrbar, int n_nodes,
                                    double* Tx, cudaStream_t s);
+cudaError_t launch_xbutterfly_masses_adjoint(const int* nodes, int n_list, const int2* nbr, const int* xslot,
+                                             const double* Sbar, int n_nodes, double* mbar, cudaStream_t s);
 cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
                                      double* Sm, cudaStream_t s);
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);

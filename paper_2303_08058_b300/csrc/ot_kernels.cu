@@ -1485,12 +1485,75 @@ __device__ __forceinline__ void walk_classes_scatter(const int* __restrict__ lis
     }
 }
 
+// x-complete classes of a leaf target with leaf or empty neighbours: the
+// partial dot products transformed over y and z only; for each (y, z) sign
+// the two x channels go to the deferred butterfly accumulators of the
+// position t + (0, +-b, +-c) (the members at +-a receive their sum and
+// difference in xbutterfly_masses_adjoint_kernel)
+template <int Z, class P>
+__device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                       const int2* __restrict__ s_nb, const P& p,
+                                                       const double (&lb)[16], int item) {
+    static_assert((Z & 1) == 0, "the x stage needs a > 0");
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        double* dst[4];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            dst[q] = nullptr;
+            if ((2 * q) & Z) continue;
+            if ((members >> (2 * q)) & 1u) {
+                const int sy = (q & 1) ? ty - b : ty + b, sz = (q & 2) ? tz - c : tz + c;
+                const int2 es = s_nb[nb_index(tx, sy, sz)];
+                const int ks = es.y & 3;
+                if (ks == K_LEAF && static_cast<unsigned>(es.x) < static_cast<unsigned>(p.n_nodes)) {
+                    dst[q] = p.Sbar + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + a - 1) * 2 * NCELL + (tx & 7) +
+                             8 * (sy & 7) + 64 * (sz & 7);
+                    any = true;
+                } else if (ks != K_NONE) {
+                    report(p.status, 7, item);    // the target's flag promised leaf or empty neighbours
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(a, b, c));
+        double w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (!(comp_parity(q) & Z)) w[comp_parity(q)] = fma(lb[q], d[q], w[comp_parity(q)]);
+        class_transform_yz<Z>(w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if ((2 * q) & Z) continue;
+            if (dst[q] != nullptr) {
+                atomicAdd(dst[q], w[2 * q]);
+                atomicAdd(dst[q] + NCELL, w[2 * q + 1]);
+            }
+        }
+    }
+}
+
 template <int Z = 0, class P>
-__device__ __forceinline__ void walk_classes_scatter_all(const int* __restrict__ list, const int* zoff, int tx,
-                                                         int ty, int tz, const int2* __restrict__ s_nb, const P& p,
+__device__ __forceinline__ void walk_classes_scatter_all(const int* __restrict__ list, const int* zoff, const int* xc,
+                                                         bool xpath, int tx, int ty, int tz,
+                                                         const int2* __restrict__ s_nb, const P& p,
                                                          const double (&lb)[16], int item) {
-    walk_classes_scatter<Z>(list + zoff[Z], zoff[Z + 1] - zoff[Z], tx, ty, tz, s_nb, p, lb, item);
-    if constexpr (Z < 6) walk_classes_scatter_all<Z + 1>(list, zoff, tx, ty, tz, s_nb, p, lb, item);
+    const int len = zoff[Z + 1] - zoff[Z];
+    int nx = 0;
+    if constexpr ((Z & 1) == 0) {
+        if (xpath) {
+            nx = xc[Z];
+            walk_classes_scatter_x<Z>(list + zoff[Z], nx, tx, ty, tz, s_nb, p, lb, item);
+        }
+    }
+    walk_classes_scatter<Z>(list + zoff[Z] + nx, len - nx, tx, ty, tz, s_nb, p, lb, item);
+    if constexpr (Z < 6) walk_classes_scatter_all<Z + 1>(list, zoff, xc, xpath, tx, ty, tz, s_nb, p, lb, item);
 }
 
 template <bool PAIRED, bool NEAR, bool EMU = false, bool PM = true, class P>
@@ -1590,13 +1653,14 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
     const bool leafT = (info >> 8) & 1;
     if (!EMU && level > 0 && leafT) {
         // by reflection class (see the forward); refined near sources over the near list
+        const bool xpath = p.Sbar != nullptr && (info & NI_XMASS);
         const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-        walk_classes_scatter_all(cf, p.L.cf_z, tx, ty, tz, s_nb, p, lb, it);
+        walk_classes_scatter_all(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, p, lb, it);
         cf += p.L.cf_z[7];
         walk_scatter<true, false, EMU>(cf, p.L.cf_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         const int* cn = p.L.lists + p.L.cn_off;
-        walk_classes_scatter_all(cn, p.L.cn_z, tx, ty, tz, s_nb, p, lb, it);
+        walk_classes_scatter_all(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, p, lb, it);
         walk_scatter<true, false, EMU>(cn + p.L.cn_z[7], p.L.cn_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         if (__any_sync(0xffffffffu, lane < 27 && (s_nb[lane < 27 ? lane : 0].y & 3) == K_MULTI))
             walk_scatter<true, true, EMU, false>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, lbh,
@@ -2864,6 +2928,35 @@ __device__ __forceinline__ double mass_at(const double* __restrict__ m, int2 e, 
     return 0.0;
 }
 
+// the transpose of xbutterfly_masses_kernel: each leaf cell c collects, for
+// a = 1..7, the deferred x channels (A, B) of the positions c - a x (c is
+// their +a member: A + B) and c + a x (their -a member: A - B)
+__global__ void xbutterfly_masses_adjoint_kernel(const int* __restrict__ nodes, int n_list,
+                                                 const int2* __restrict__ nbr, const int* __restrict__ xslot,
+                                                 const double* __restrict__ Sbar, int n_nodes,
+                                                 double* __restrict__ mbar) {
+    const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (gid >= 1LL * NCELL * n_list) return;
+    const int cell = static_cast<int>(gid % NCELL);
+    const int node = __ldg(nodes + static_cast<int>(gid / NCELL));
+    const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const int2* nb = nbr + static_cast<size_t>(node) * 27;
+    double acc = 0.0;
+    for (int a = 1; a <= 7; ++a) {
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            const int qx = sd ? x + a : x - a;         // the position whose member c is
+            const int2 e = __ldg(nb + nb_index(qx, y, z));
+            if ((e.y & 3) != K_LEAF || static_cast<unsigned>(e.x) >= static_cast<unsigned>(n_nodes)) continue;
+            const double* src = Sbar + static_cast<size_t>(__ldg(xslot + e.x) * 7 + a - 1) * 2 * NCELL + (qx & 7) +
+                                8 * y + 64 * z;
+            const double A = __ldg(src), B = __ldg(src + NCELL);
+            acc += sd ? A - B : A + B;
+        }
+    }
+    mbar[static_cast<size_t>(node) * NCELL + cell] += acc;
+}
+
 __global__ void xbutterfly_masses_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
                                          const double* __restrict__ m, int n_nodes, double* __restrict__ Sm) {
     const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -2892,6 +2985,14 @@ cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* 
     if (n_list == 0) return cudaSuccess;
     xbutterfly_moments_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Mhat,
                                                                                         n_nodes, Sx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xbutterfly_masses_adjoint(const int* nodes, int n_list, const int2* nbr, const int* xslot,
+                                             const double* Sbar, int n_nodes, double* mbar, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    xbutterfly_masses_adjoint_kernel<<<blocks_for(1LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, xslot,
+                                                                                             Sbar, n_nodes, mbar);
     return cudaGetLastError();
 }
 

@@ -213,6 +213,7 @@ struct ot_grid {
     int* d_tslot = nullptr;
     int* d_tnodes = nullptr;
     double* d_Tx = nullptr;             // [tslot][7][16][2][512]
+    double* d_Sbar = nullptr;           // [leaf slot][7][2][512]: the point-mass scatter's deferred x stage
     // chunked multipole gather items of the adjoint (modes 1 and 3, and the
     // default adjoint's merged list); they share d_part and d_chunk_ctr
     std::vector<int> itemsc_adj[4], itemsc_adj_node[4], itemc_adj_start[4], itemsc_adj_fast1;
@@ -804,8 +805,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                                              : class_adds(Z);
                         cfx = xadds + class_fmas(Z);
                         fl_fx = xadds + 2 * class_fmas(Z);
-                        csx = cs;           // the scatter transforms on the output side: no x table
-                        fl_sx = fl_s;
+                        csx = cfx;          // the scatter defers its x stage alike
+                        fl_sx = fl_fx;
                     }
                 } else {
                     const int ox = (e & 0xff) - 8, oy = ((e >> 8) & 0xff) - 8, oz = ((e >> 16) & 0xff) - 8;
@@ -929,9 +930,14 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 pairs_mono += cp + cs;
                 if (by_class) {
                     flops_fwd += std::llround(CFL[0][j] + CFL[1][j]);
-                    flops_adj_scat += std::llround(cfl_s[0][j] + cfl_s[1][j]);
                     alg_fwd += COP[0][j] + COP[1][j];
-                    alg_adj_scat += cop_s[0][j] + cop_s[1][j];
+                    if (xnode) {
+                        flops_adj_scat += std::llround(cfl_sx[0][j] + cfl_sx[1][j]);
+                        alg_adj_scat += cop_sx[0][j] + cop_sx[1][j];
+                    } else {
+                        flops_adj_scat += std::llround(cfl_s[0][j] + cfl_s[1][j]);
+                        alg_adj_scat += cop_s[0][j] + cop_s[1][j];
+                    }
                 } else {
                     flops_fwd += 17 * cp + 32 * cs;
                     flops_adj_scat += 16 * cp + 32 * cs;
@@ -978,7 +984,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     for (size_t k = 0; k < cmask[ph][cg].size(); ++k)
                         if (cmask[ph][cg][k] & mo) {
                             cost[2] += CCF[cg][k];
-                            cost_s += ccost_s[cg][k];
+                            cost_s += xnode ? ccost_sx[cg][k] : ccost_s[cg][k];
                             lanes += 32;
                             padded += 32 * cmem[cg][k];
                         }
@@ -1448,6 +1454,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if ((st = g->alloc(&g->d_Tx, static_cast<size_t>(std::max<size_t>(g->tnodes.size(), 1)) * 7 * 32 * NCELL)) !=
         OT_OK)
         return st;
+    if ((st = g->alloc(&g->d_Sbar, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
@@ -1685,8 +1692,19 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
             p.Dt32 = g->d_Dt32;
             maxb = g->maxb_adj_emu[k ? 13 : 12][g->wpb];
         }
+        // FP64 scatter: the x stage of x-complete classes deferred to a pass
+        // over the leaf cells
+        const bool defer = g->precision != OT_PREC_DF64 && g->n_xleaf > 0;
+        if (defer) {
+            OT_CUDA(cudaMemsetAsync(g->d_Sbar, 0, static_cast<size_t>(g->n_xleaf) * 7 * 2 * NCELL * sizeof(double), s));
+            p.Sbar = g->d_Sbar;
+            p.xslot = g->d_xslot;
+        }
         OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
         OT_CUDA(launch_adjoint(p, k ? 5 : 4, true, g->wpb, grid_blocks(g, maxb), s));
+        if (defer)
+            OT_CUDA(launch_xbutterfly_masses_adjoint(g->d_leaf, g->n_xleaf, g->d_nbr, g->d_xslot, g->d_Sbar, g->n,
+                                                     mbar, s));
     } else {
         int maxb = g->maxb_adj[mode][g->wpb];
         if (g->precision == OT_PREC_DF64 && mode == 1) {
