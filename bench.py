@@ -181,9 +181,9 @@ def fwd_flops(info):
 
 # DRAM bytes (read + written) of one forward_kernel<3> launch on the 64^3
 # polytrope workload with the 8x1 tile, from an ncu capture of that kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 55.63 MB + 26.38 MB).
+# (dram__bytes_read.sum + dram__bytes_write.sum = 155.31 MB + 44.76 MB).
 # Reported only for that workload; None once the kernel changes.
-FORWARD_DRAM_BYTES_POLYTROPE64 = 82_008_064
+FORWARD_DRAM_BYTES_POLYTROPE64 = 200_074_240
 
 # Nominal FP64 rate of a B300 (1.25 TFLOP/s) at its maximum SM clock (2032 MHz):
 # 1.25e12 / (148 SMs * 2.032e9) = 4.16 FP64 flop per clock per SM.
