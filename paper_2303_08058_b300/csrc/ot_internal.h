@@ -116,6 +116,7 @@ struct FwdParams {
     // in its kind's table is xslot[node]
     const double* Sx;      // [non-leaf slot][7][16][2][512]: Mhat(c + a x) +- Mhat(c - a x), multipole cells
     const double* Sm;      // [leaf slot][7][2][512]: the same for the point masses
+    const float2* Smf;     // the masses' table as double-float (hi, lo) pairs (double-float point masses)
     const int* xslot;      // [n]
 };
 

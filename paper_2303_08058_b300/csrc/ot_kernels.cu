@@ -527,6 +527,139 @@ __device__ __forceinline__ void walk_classes_fwd_x(const int* __restrict__ list,
     }
 }
 
+// Double-float point-mass classes (EMU bit 1): the members' masses as
+// (hi, lo) pairs, the transform by df_add, one df_fma per component into the
+// double-float accumulators.  The transform of up to eight masses errs by at
+// most 3 * 2^-48 of the sum of their magnitudes, so a product's error stays
+// within a few 2^-48 of the |terms| its members stand for, inside the grouped
+// accumulation's bound.
+template <int Z, int B0>
+__device__ __forceinline__ void class_transform_df(float (&wh)[8], float (&wl)[8]) {
+#pragma unroll
+    for (int b = B0; b < 3; ++b) {
+        if ((Z >> b) & 1) continue;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (((i >> b) & 1) || (i & Z)) continue;
+            const int j = i | (1 << b);
+            float sh, sl, dh, dl;
+            df_add(wh[i], wl[i], wh[j], wl[j], sh, sl);
+            df_add(wh[i], wl[i], -wh[j], -wl[j], dh, dl);
+            wh[i] = sh;
+            wl[i] = sl;
+            wh[j] = dh;
+            wl[j] = dl;
+        }
+    }
+}
+
+template <int Z>
+__device__ __forceinline__ void class_fma_df(DFAcc& f, const float (&wh)[8], const float (&wl)[8],
+                                             const float (&r)[32]) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if (!(comp_parity(q) & Z)) df_fma(f.ah[q], f.al[q], wh[comp_parity(q)], wl[comp_parity(q)], r[q], r[16 + q]);
+}
+
+template <int Z>
+__device__ __forceinline__ void walk_classes_fwd_df(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                    const int2* __restrict__ s_nb, const FwdParams& p,
+                                                    double (&acc)[16], double (&c)[3], double (&t4)[9], DFAcc& f,
+                                                    int item) {
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int a = e & 0xff, b = (e >> 8) & 0xff, cc = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        float wh[8], wl[8];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            wh[i] = 0.0f;
+            wl[i] = 0.0f;
+            if (i & Z) continue;
+            if ((members >> i) & 1u) {
+                int sx, sy, sz;
+                class_member(i, a, b, cc, tx, ty, tz, sx, sy, sz);
+                const int2 es = s_nb[nb_index(sx, sy, sz)];
+                const int ks = checked_kind(p, es, item);
+                any |= ks >= K_LEAF;
+                source_mass_df(p, es, ks, sx, sy, sz, wh[i], wl[i]);
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        df_reserve(acc, c, t4, f, 1, 1, 1, 1, 0, 0);
+        float r[32];
+        load_row32f(r, p.Dt32, offset_row(a, b, cc));
+        class_transform_df<Z, 0>(wh, wl);
+        class_fma_df<Z>(f, wh, wl, r);
+    }
+}
+
+// the same with the x stage from the prebuilt x butterflies of the masses,
+// split into (hi, lo) pairs
+template <int Z>
+__device__ __forceinline__ void walk_classes_fwd_df_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                      const int2* __restrict__ s_nb, const FwdParams& p,
+                                                      double (&acc)[16], double (&c)[3], double (&t4)[9], DFAcc& f,
+                                                      int item) {
+    static_assert((Z & 1) == 0, "the x stage needs a > 0");
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int a = e & 0xff, b = (e >> 8) & 0xff, cc = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        float wh[8], wl[8];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            wh[2 * q] = wl[2 * q] = wh[2 * q + 1] = wl[2 * q + 1] = 0.0f;
+            if ((2 * q) & Z) continue;
+            if ((members >> (2 * q)) & 1u) {
+                const int sy = (q & 1) ? ty - b : ty + b, sz = (q & 2) ? tz - cc : tz + cc;
+                const int2 es = s_nb[nb_index(tx, sy, sz)];
+                const int ks = checked_kind(p, es, item);
+                if (ks == K_LEAF) {
+                    const float2* src = p.Smf + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + a - 1) * 2 * NCELL +
+                                        (tx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+                    const float2 vp = __ldg(src), vm = __ldg(src + NCELL);
+                    wh[2 * q] = vp.x;
+                    wl[2 * q] = vp.y;
+                    wh[2 * q + 1] = vm.x;
+                    wl[2 * q + 1] = vm.y;
+                    any = true;
+                } else if (ks != K_NONE) {
+                    report(p.status, 7, item);
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        df_reserve(acc, c, t4, f, 1, 1, 1, 1, 0, 0);
+        float r[32];
+        load_row32f(r, p.Dt32, offset_row(a, b, cc));
+        class_transform_df<Z, 1>(wh, wl);
+        class_fma_df<Z>(f, wh, wl, r);
+    }
+}
+
+template <int Z = 0, class CH>
+__device__ __forceinline__ void walk_classes_fwd_df_all(const int* __restrict__ list, const int* zoff, const int* xc,
+                                                        bool xpath, const CH& ch, int tx, int ty, int tz,
+                                                        const int2* __restrict__ s_nb, const FwdParams& p,
+                                                        double (&acc)[16], double (&c)[3], double (&t4)[9], DFAcc& f,
+                                                        int item) {
+    const int len = zoff[Z + 1] - zoff[Z];
+    int nx = 0;
+    if constexpr ((Z & 1) == 0) {
+        if (xpath) {
+            nx = xc[Z];
+            walk_classes_fwd_df_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, p, acc, c, t4, f, item);
+        }
+    }
+    walk_classes_fwd_df<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, c, t4, f,
+                           item);
+    if constexpr (Z < 6)
+        walk_classes_fwd_df_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, p, acc, c, t4, f, item);
+}
+
 // the seven zero patterns of a class list (Z = 7 would be the self pair);
 // with xpath, each group's x-complete head (xc[Z] entries, Z without bit 0)
 // takes the prebuilt x butterflies
@@ -901,14 +1034,18 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
         for (int q = 0; q < 3; ++q) c[q] = 0.0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) t4[q] = 0.0;
-        if ((MODE & 2) && level > 0 && leafT && !(EMU & 1)) {
-            // leaf target, FP64 point masses: by reflection class over the far
-            // and near offsets; multipole sources (refined neighbours) over the
-            // full far list, refined near sources over the near list
+        if ((MODE & 2) && level > 0 && leafT) {
+            // leaf target, point masses: by reflection class over the far
+            // and near offsets (FP64, or double-float with EMU bit 1);
+            // multipole sources (refined neighbours) over the full far list,
+            // refined near sources over the near list
             const int2* nb = s_nb[warp];
-            const bool xpath = p.Sm != nullptr && (info & NI_XMASS);
+            const bool xpath = (EMU & 1) ? p.Smf != nullptr && (info & NI_XMASS) : p.Sm != nullptr && (info & NI_XMASS);
             const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-            walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, p, a, it);
+            if constexpr ((EMU & 1) != 0)
+                walk_classes_fwd_df_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, p, a, c, t4, f, it);
+            else
+                walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, p, a, it);
             cf += p.L.cf_z[7];
             walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -916,7 +1053,10 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             walk_forward<2, false, EMU>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
                                         c, t4, f, it);
             const int* cn = p.L.lists + p.L.cn_off;
-            walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, p, a, it);
+            if constexpr ((EMU & 1) != 0)
+                walk_classes_fwd_df_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, p, a, c, t4, f, it);
+            else
+                walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -1434,10 +1574,45 @@ __device__ __forceinline__ void scatter_mass(const P& p, int2 e, int kind, int s
 // member i of a class receives sum_pi (-1)^|i & pi| P[pi], P[pi] the partial
 // dot product of the target's L-bar and the row over the components of
 // parity pattern pi
-template <int Z, class P>
+// a class's eight member shares of a target's L-bar: the partial dot
+// products by parity pattern, transformed over the sign axes from B0 on (B0 =
+// 1: the x stage left to the deferred pass).  EMU: the partials and the
+// transform in double-float (at most 3 products per partial), each share
+// converted to FP64 once.
+template <int Z, int B0, bool EMU, class P>
+__device__ __forceinline__ void class_scatter_values(const P& p, int row, const double (&lb)[16],
+                                                     const float (&lbh)[16], const float (&lbl)[16], double (&w)[8]) {
+    if constexpr (EMU) {
+        float r[32];
+        load_row32f(r, p.Dt32, row);
+        float wh[8], wl[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wh[i] = wl[i] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (!(comp_parity(q) & Z)) df_fma(wh[comp_parity(q)], wl[comp_parity(q)], lbh[q], lbl[q], r[q], r[16 + q]);
+        class_transform_df<Z, B0>(wh, wl);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            w[i] = (i & Z) ? 0.0 : static_cast<double>(wh[i]) + static_cast<double>(wl[i]);
+    } else {
+        double d[36];
+        load_row16(d, p.Dt, row);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (!(comp_parity(q) & Z)) w[comp_parity(q)] = fma(lb[q], d[q], w[comp_parity(q)]);
+        if constexpr (B0 == 0) class_transform<Z>(w);
+        else class_transform_yz<Z>(w);
+    }
+}
+
+template <int Z, bool EMU, class P>
 __device__ __forceinline__ void walk_classes_scatter(const int* __restrict__ list, int len, int tx, int ty, int tz,
                                                      const int2* __restrict__ s_nb, const P& p,
-                                                     const double (&lb)[16], int item) {
+                                                     const double (&lb)[16], const float (&lbh)[16],
+                                                     const float (&lbl)[16], int item) {
     for (int k = 0; k < len; ++k) {
         const int e = __ldg(list + k);
         const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
@@ -1464,15 +1639,8 @@ __device__ __forceinline__ void walk_classes_scatter(const int* __restrict__ lis
             }
         }
         if (!__any_sync(0xffffffffu, any)) continue;
-        double d[36];
-        load_row16(d, p.Dt, offset_row(a, b, c));
         double w[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) w[i] = 0.0;
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-            if (!(comp_parity(q) & Z)) w[comp_parity(q)] = fma(lb[q], d[q], w[comp_parity(q)]);
-        class_transform<Z>(w);
+        class_scatter_values<Z, 0, EMU>(p, offset_row(a, b, c), lb, lbh, lbl, w);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (i & Z) continue;
@@ -1490,10 +1658,11 @@ __device__ __forceinline__ void walk_classes_scatter(const int* __restrict__ lis
 // the two x channels go to the deferred butterfly accumulators of the
 // position t + (0, +-b, +-c) (the members at +-a receive their sum and
 // difference in xbutterfly_masses_adjoint_kernel)
-template <int Z, class P>
+template <int Z, bool EMU, class P>
 __device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
                                                        const int2* __restrict__ s_nb, const P& p,
-                                                       const double (&lb)[16], int item) {
+                                                       const double (&lb)[16], const float (&lbh)[16],
+                                                       const float (&lbl)[16], int item) {
     static_assert((Z & 1) == 0, "the x stage needs a > 0");
     for (int k = 0; k < len; ++k) {
         const int e = __ldg(list + k);
@@ -1519,15 +1688,8 @@ __device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ l
             }
         }
         if (!__any_sync(0xffffffffu, any)) continue;
-        double d[36];
-        load_row16(d, p.Dt, offset_row(a, b, c));
         double w[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) w[i] = 0.0;
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-            if (!(comp_parity(q) & Z)) w[comp_parity(q)] = fma(lb[q], d[q], w[comp_parity(q)]);
-        class_transform_yz<Z>(w);
+        class_scatter_values<Z, 1, EMU>(p, offset_row(a, b, c), lb, lbh, lbl, w);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if ((2 * q) & Z) continue;
@@ -1539,21 +1701,23 @@ __device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ l
     }
 }
 
-template <int Z = 0, class P>
+template <bool EMU, int Z = 0, class P>
 __device__ __forceinline__ void walk_classes_scatter_all(const int* __restrict__ list, const int* zoff, const int* xc,
                                                          bool xpath, int tx, int ty, int tz,
                                                          const int2* __restrict__ s_nb, const P& p,
-                                                         const double (&lb)[16], int item) {
+                                                         const double (&lb)[16], const float (&lbh)[16],
+                                                         const float (&lbl)[16], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
     int nx = 0;
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
             nx = xc[Z];
-            walk_classes_scatter_x<Z>(list + zoff[Z], nx, tx, ty, tz, s_nb, p, lb, item);
+            walk_classes_scatter_x<Z, EMU>(list + zoff[Z], nx, tx, ty, tz, s_nb, p, lb, lbh, lbl, item);
         }
     }
-    walk_classes_scatter<Z>(list + zoff[Z] + nx, len - nx, tx, ty, tz, s_nb, p, lb, item);
-    if constexpr (Z < 6) walk_classes_scatter_all<Z + 1>(list, zoff, xc, xpath, tx, ty, tz, s_nb, p, lb, item);
+    walk_classes_scatter<Z, EMU>(list + zoff[Z] + nx, len - nx, tx, ty, tz, s_nb, p, lb, lbh, lbl, item);
+    if constexpr (Z < 6)
+        walk_classes_scatter_all<EMU, Z + 1>(list, zoff, xc, xpath, tx, ty, tz, s_nb, p, lb, lbh, lbl, item);
 }
 
 template <bool PAIRED, bool NEAR, bool EMU = false, bool PM = true, class P>
@@ -1651,16 +1815,16 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
     const int info = __ldg(ninfo + node);
     const int level = info & 0xff;
     const bool leafT = (info >> 8) & 1;
-    if (!EMU && level > 0 && leafT) {
+    if (level > 0 && leafT) {
         // by reflection class (see the forward); refined near sources over the near list
         const bool xpath = p.Sbar != nullptr && (info & NI_XMASS);
         const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-        walk_classes_scatter_all(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, p, lb, it);
+        walk_classes_scatter_all<EMU>(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         cf += p.L.cf_z[7];
         walk_scatter<true, false, EMU>(cf, p.L.cf_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         const int* cn = p.L.lists + p.L.cn_off;
-        walk_classes_scatter_all(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, p, lb, it);
+        walk_classes_scatter_all<EMU>(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         walk_scatter<true, false, EMU>(cn + p.L.cn_z[7], p.L.cn_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         if (__any_sync(0xffffffffu, lane < 27 && (s_nb[lane < 27 ? lane : 0].y & 3) == K_MULTI))
             walk_scatter<true, true, EMU, false>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, lbh,

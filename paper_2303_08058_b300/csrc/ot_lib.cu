@@ -209,6 +209,7 @@ struct ot_grid {
     int* d_leaf = nullptr;              // leaf nodes in slot order
     double* d_Sx = nullptr;             // [non-leaf slot][7][16][2][512]
     double* d_Sm = nullptr;             // [leaf slot][7][2][512]
+    float2* d_Smf = nullptr;            // the same as double-float pairs
     std::vector<int> tslot, tnodes;     // the gather's L-bar butterflies: slot per node, nodes per slot
     int* d_tslot = nullptr;
     int* d_tnodes = nullptr;
@@ -1455,6 +1456,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         OT_OK)
         return st;
     if ((st = g->alloc(&g->d_Sbar, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Smf, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
@@ -1511,6 +1513,15 @@ static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, 
 // enqueue one forward pass (mode 1, 2 or 3) on stream s
 static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const double* m, double* L, double* Lc,
                                  int accumulate, cudaStream_t s) {
+    if (mode == 3 && g->precision != 0 && g->schedule == OT_SCHED_PERSISTENT) {
+        // With double-float contractions both passes run as two launches:
+        // fused, the one kernel holds the FP64 or double-float multipole code
+        // and the double-float point-mass code at once, and the mix of the two
+        // item kinds on an SM ran 1.5-1.7x slower than the two launches.
+        ot_status st = enqueue_forward(g, 1, M, m, L, Lc, accumulate, s);
+        if (st != OT_OK) return st;
+        return enqueue_forward(g, 2, M, m, L, nullptr, 1, s);
+    }
     const size_t nL = static_cast<size_t>(g->n) * NCOMP * NCELL;
     if (mode & 1) {
         PrepParams pp;
@@ -1531,9 +1542,15 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         OT_CUDA(launch_xbutterfly_moments(g->d_nonleaf, g->n_nonleaf, g->d_nbr, g->d_Mhat, g->n, g->d_Sx, s));
         p.Sx = g->d_Sx;
     }
-    if ((mode & 2) && g->precision == 0 && g->n_xleaf > 0) {
+    if ((mode & 2) && g->n_xleaf > 0) {
         OT_CUDA(launch_xbutterfly_masses(g->d_leaf, g->n_xleaf, g->d_nbr, m, g->n, g->d_Sm, s));
-        p.Sm = g->d_Sm;
+        if (g->precision == 0) {
+            p.Sm = g->d_Sm;
+        } else {
+            // double-float point masses read the table as (hi, lo) pairs
+            OT_CUDA(launch_split_masses(g->d_Sm, g->d_Smf, static_cast<size_t>(g->n_xleaf) * 7 * 2 * NCELL, s));
+            p.Smf = g->d_Smf;
+        }
     }
     const bool emu = g->precision >= 1 && (mode & 2);       // double-float point masses
     const bool emu2 = g->precision == 2 && (mode & 1);      // double-float multipole contractions
@@ -1611,6 +1628,14 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
     int mode = (Mbar ? 1 : 0) | (mbar ? 2 : 0);
     if (mode == 0) return OT_OK;
     const bool scatter = !g->deterministic && mbar != nullptr;
+    if (mode == 3 && scatter && g->precision == OT_PREC_DF64 && g->schedule == OT_SCHED_PERSISTENT) {
+        // double-float: the gather and the scatter as two launches (one
+        // kernel holding both double-float walks ran 1.35x slower than the
+        // two launches on the 64^3 polytrope)
+        ot_status st = enqueue_backward(g, Lbar, Mbar, nullptr, s);
+        if (st != OT_OK) return st;
+        return enqueue_backward(g, Lbar, nullptr, mbar, s);
+    }
     PrepParams pp;
     std::memset(&pp, 0, sizeof(pp));
     pp.src = Lbar;
@@ -1694,7 +1719,7 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
         }
         // FP64 scatter: the x stage of x-complete classes deferred to a pass
         // over the leaf cells
-        const bool defer = g->precision != OT_PREC_DF64 && g->n_xleaf > 0;
+        const bool defer = g->n_xleaf > 0;
         if (defer) {
             OT_CUDA(cudaMemsetAsync(g->d_Sbar, 0, static_cast<size_t>(g->n_xleaf) * 7 * 2 * NCELL * sizeof(double), s));
             p.Sbar = g->d_Sbar;
@@ -2094,6 +2119,7 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     // and the x butterflies the warm-up built from the same M and m
     if (g->precision != 2 && g->n_xnonleaf > 0) p.Sx = g->d_Sx;
     if (g->precision == 0 && g->n_xleaf > 0) p.Sm = g->d_Sm;
+    if (g->precision != 0 && g->n_xleaf > 0) p.Smf = g->d_Smf;
     if (g->n_chunk_ctrs > 0) {
         OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs) * sizeof(int), streams[0]));
         OT_CUDA(cudaStreamSynchronize(streams[0]));
