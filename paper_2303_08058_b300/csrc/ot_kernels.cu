@@ -488,7 +488,7 @@ __device__ __forceinline__ void class_transform_yz(double (&w)[8]) {
 // the masses at the positions t + (0, +-b, +-c)
 template <int Z>
 __device__ __forceinline__ void walk_classes_fwd_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
-                                                   const int2* __restrict__ s_nb, const FwdParams& p,
+                                                   const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
                                                    double (&acc)[16], int item) {
     static_assert((Z & 1) == 0, "the x stage needs a > 0");
     for (int k = 0; k < len; ++k) {
@@ -507,7 +507,7 @@ __device__ __forceinline__ void walk_classes_fwd_x(const int* __restrict__ list,
                 const int2 es = s_nb[nb_index(tx, sy, sz)];
                 const int ks = checked_kind(p, es, item);
                 if (ks == K_LEAF) {
-                    const double* src = p.Sm + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + a - 1) * 2 * NCELL +
+                    const double* src = p.Sm + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + a - 1) * 2 * NCELL +
                                         (tx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
                     w[2 * q] = __ldg(src);
                     w[2 * q + 1] = __ldg(src + NCELL);
@@ -599,7 +599,7 @@ __device__ __forceinline__ void walk_classes_fwd_df(const int* __restrict__ list
 // split into (hi, lo) pairs
 template <int Z>
 __device__ __forceinline__ void walk_classes_fwd_df_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
-                                                      const int2* __restrict__ s_nb, const FwdParams& p,
+                                                      const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
                                                       double (&acc)[16], double (&c)[3], double (&t4)[9], DFAcc& f,
                                                       int item) {
     static_assert((Z & 1) == 0, "the x stage needs a > 0");
@@ -618,7 +618,7 @@ __device__ __forceinline__ void walk_classes_fwd_df_x(const int* __restrict__ li
                 const int2 es = s_nb[nb_index(tx, sy, sz)];
                 const int ks = checked_kind(p, es, item);
                 if (ks == K_LEAF) {
-                    const float2* src = p.Smf + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + a - 1) * 2 * NCELL +
+                    const float2* src = p.Smf + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + a - 1) * 2 * NCELL +
                                         (tx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
                     const float2 vp = __ldg(src), vm = __ldg(src + NCELL);
                     wh[2 * q] = vp.x;
@@ -643,7 +643,7 @@ __device__ __forceinline__ void walk_classes_fwd_df_x(const int* __restrict__ li
 template <int Z = 0, class CH>
 __device__ __forceinline__ void walk_classes_fwd_df_all(const int* __restrict__ list, const int* zoff, const int* xc,
                                                         bool xpath, const CH& ch, int tx, int ty, int tz,
-                                                        const int2* __restrict__ s_nb, const FwdParams& p,
+                                                        const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
                                                         double (&acc)[16], double (&c)[3], double (&t4)[9], DFAcc& f,
                                                         int item) {
     const int len = zoff[Z + 1] - zoff[Z];
@@ -651,13 +651,13 @@ __device__ __forceinline__ void walk_classes_fwd_df_all(const int* __restrict__ 
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
             nx = xc[Z];
-            walk_classes_fwd_df_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, p, acc, c, t4, f, item);
+            walk_classes_fwd_df_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, s_sl, p, acc, c, t4, f, item);
         }
     }
     walk_classes_fwd_df<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, c, t4, f,
                            item);
     if constexpr (Z < 6)
-        walk_classes_fwd_df_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, p, acc, c, t4, f, item);
+        walk_classes_fwd_df_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, c, t4, f, item);
 }
 
 // the seven zero patterns of a class list (Z = 7 would be the self pair);
@@ -666,18 +666,18 @@ __device__ __forceinline__ void walk_classes_fwd_df_all(const int* __restrict__ 
 template <int Z = 0, class CH>
 __device__ __forceinline__ void walk_classes_fwd_all(const int* __restrict__ list, const int* zoff, const int* xc,
                                                      bool xpath, const CH& ch, int tx, int ty, int tz,
-                                                     const int2* __restrict__ s_nb, const FwdParams& p,
+                                                     const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
                                                      double (&acc)[16], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
     int nx = 0;
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
             nx = xc[Z];
-            walk_classes_fwd_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, p, acc, item);
+            walk_classes_fwd_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, s_sl, p, acc, item);
         }
     }
     walk_classes_fwd<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, item);
-    if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, p, acc, item);
+    if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, item);
 }
 
 // multipole sources by reflection class (non-leaf targets): the members'
@@ -717,7 +717,7 @@ __device__ __forceinline__ void walk_mclasses_fwd(const int* __restrict__ list, 
 // the prebuilt x butterflies at the positions t + (0, +-b, +-c)
 template <int Z, bool ANG>
 __device__ __forceinline__ void walk_mclasses_fwd_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
-                                                    const int2* __restrict__ s_nb, const FwdParams& p,
+                                                    const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
                                                     double (&acc)[16], double (&c)[3], double (&t4)[9], int item) {
     static_assert((Z & 1) == 0, "the x stage needs a > 0");
     for (int k = 0; k < len; ++k) {
@@ -735,7 +735,7 @@ __device__ __forceinline__ void walk_mclasses_fwd_x(const int* __restrict__ list
                 const int2 es = s_nb[nb_index(tx, sy, sz)];
                 const int ks = checked_kind(p, es, item);
                 if (ks == K_MULTI) {
-                    pos[q] = p.Sx + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + ox - 1) * 32 * NCELL + (tx & 7) +
+                    pos[q] = p.Sx + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + ox - 1) * 32 * NCELL + (tx & 7) +
                              8 * (sy & 7) + 64 * (sz & 7);
                     any = true;
                 } else if (ks != K_NONE) {
@@ -751,20 +751,20 @@ __device__ __forceinline__ void walk_mclasses_fwd_x(const int* __restrict__ list
 template <bool ANG, int Z = 0, class CH>
 __device__ __forceinline__ void walk_mclasses_fwd_all(const int* __restrict__ list, const int (&zoff)[8],
                                                       const int (&xc)[8], bool xpath, const CH& ch, int tx, int ty,
-                                                      int tz, const int2* __restrict__ s_nb, const FwdParams& p,
+                                                      int tz, const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
                                                       double (&acc)[16], double (&c)[3], double (&t4)[9], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
     int nx = 0;
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
             nx = xc[Z];
-            walk_mclasses_fwd_x<Z, ANG>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, p, acc, c, t4, item);
+            walk_mclasses_fwd_x<Z, ANG>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, s_sl, p, acc, c, t4, item);
         }
     }
     walk_mclasses_fwd<Z, ANG>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, c, t4,
                               item);
     if constexpr (Z < 6)
-        walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, p, acc, c, t4, item);
+        walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, c, t4, item);
 }
 
 template <int MODE, bool PAIRED, int EMU, bool NEAR = false, bool PM = true>
@@ -994,6 +994,7 @@ __device__ __forceinline__ bool chunk_combine_fwd(const FwdParams& p, int2 ci, i
 template <int MODE, int EMU>
 __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
+    __shared__ int s_sl[8][27];   // x-table slots of the neighbours (leaf or multipole)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -1018,7 +1019,14 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             if (!persistent) break;
             continue;
         }
-        if (lane < 27) s_nb[warp][lane] = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
+        if (lane < 27) {
+            const int2 e = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
+            s_nb[warp][lane] = e;
+            const int k = e.y & 3;
+            s_sl[warp][lane] = (p.xslot != nullptr && (k == K_LEAF || k == K_MULTI) &&
+                                static_cast<unsigned>(e.x) < static_cast<unsigned>(p.n_nodes))
+                                   ? __ldg(p.xslot + e.x) : -1;
+        }
         __syncwarp();
         const int info = __ldg(p.ninfo + node);
         const int level = info & 0xff;
@@ -1043,9 +1051,9 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             const bool xpath = (EMU & 1) ? p.Smf != nullptr && (info & NI_XMASS) : p.Sm != nullptr && (info & NI_XMASS);
             const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
             if constexpr ((EMU & 1) != 0)
-                walk_classes_fwd_df_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, p, a, c, t4, f, it);
+                walk_classes_fwd_df_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, f, it);
             else
-                walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, p, a, it);
+                walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
             cf += p.L.cf_z[7];
             walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -1054,9 +1062,9 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
                                         c, t4, f, it);
             const int* cn = p.L.lists + p.L.cn_off;
             if constexpr ((EMU & 1) != 0)
-                walk_classes_fwd_df_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, p, a, c, t4, f, it);
+                walk_classes_fwd_df_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, f, it);
             else
-                walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, p, a, it);
+                walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -1088,7 +1096,7 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
                 }
                 const bool xpath = p.Sx != nullptr && (info & NI_XMULTI);
                 const int* ml = p.L.lists + (root ? p.L.mr_off : p.L.mf_off + par * p.L.mf_stride);
-                walk_mclasses_fwd_all<true>(ml, zo, xc, xpath, ch, tx, ty, tz, nb, p, a, c, t4, it);
+                walk_mclasses_fwd_all<true>(ml, zo, xc, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, it);
                 ml += zo[7];
                 const int np = root ? p.L.mr_pairs : p.L.mf_pairs, ns = root ? 0 : p.L.mf_singles;
                 walk_forward<1, true, EMU>(ml + ch.lo(np), ch.n(np), true, tx, ty, tz, nb, p, a, c, t4, f, it);
@@ -1328,7 +1336,7 @@ __device__ __forceinline__ void walk_mclasses_adj(const int* __restrict__ list, 
 // L-bar x butterflies at the positions B + (0, +-b, +-c)
 template <int Z>
 __device__ __forceinline__ void walk_mclasses_adj_x(const int* __restrict__ list, int len, int sx0, int sy0, int sz0,
-                                                    const int2* __restrict__ s_nb, const AdjParams& p,
+                                                    const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const AdjParams& p,
                                                     double (&g)[16], int item) {
     static_assert((Z & 1) == 0, "the x stage needs a > 0");
     for (int k = 0; k < len; ++k) {
@@ -1346,7 +1354,7 @@ __device__ __forceinline__ void walk_mclasses_adj_x(const int* __restrict__ list
                 const int2 et = s_nb[nb_index(sx0, ty, tz)];
                 const int kt = et.y & 3;
                 if ((kt == K_MULTI || kt == K_LEAF) && static_cast<unsigned>(et.x) < static_cast<unsigned>(p.n_nodes)) {
-                    const int slot = __ldg(p.tslot + et.x);
+                    const int slot = s_sl[nb_index(sx0, ty, tz)];
                     if (slot >= 0) {
                         pos[q] = p.Tx + static_cast<size_t>(slot * 7 + ox - 1) * 32 * NCELL + (sx0 & 7) +
                                  8 * (ty & 7) + 64 * (tz & 7);
@@ -1367,18 +1375,18 @@ __device__ __forceinline__ void walk_mclasses_adj_x(const int* __restrict__ list
 template <int Z = 0, class CH>
 __device__ __forceinline__ void walk_mclasses_adj_all(const int* __restrict__ list, const int (&zoff)[8],
                                                       const int (&xc)[8], bool xpath, const CH& ch, int sx0, int sy0,
-                                                      int sz0, const int2* __restrict__ s_nb, const AdjParams& p,
+                                                      int sz0, const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const AdjParams& p,
                                                       double (&g)[16], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
     int nx = 0;
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
             nx = xc[Z];
-            walk_mclasses_adj_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), sx0, sy0, sz0, s_nb, p, g, item);
+            walk_mclasses_adj_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), sx0, sy0, sz0, s_nb, s_sl, p, g, item);
         }
     }
     walk_mclasses_adj<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), sx0, sy0, sz0, s_nb, p, g, item);
-    if constexpr (Z < 6) walk_mclasses_adj_all<Z + 1>(list, zoff, xc, xpath, ch, sx0, sy0, sz0, s_nb, p, g, item);
+    if constexpr (Z < 6) walk_mclasses_adj_all<Z + 1>(list, zoff, xc, xpath, ch, sx0, sy0, sz0, s_nb, s_sl, p, g, item);
 }
 
 // M-bar of one source cell from the gathered g (reduced, h-scaled): expand
@@ -1415,12 +1423,13 @@ __device__ __forceinline__ void store_mbar(double* __restrict__ Mbar, int src, i
 
 template <bool EMU = false, class P>
 __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
-                             int node, int par, int half, int lane, int it);
+                             int* s_sl, int node, int par, int half, int lane, int it);
 
 // EMU: double-float multipole gather and point-mass scatter (MODE 1, 4, 5)
 template <int MODE, bool EMU = false>
 __global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
+    __shared__ int s_sl[8][27];   // x-table slots of the neighbours
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -1435,7 +1444,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int 
         const int item = __ldg(p.items + it);
         if ((MODE & 4) && ((item >> 30) & 1)) {       // point-mass adjoint by target (atomic adds)
             const int tgt = item & 0x3fffffff;
-            scatter_item<EMU>(p, p.nbr, p.ninfo, s_nb[warp], tgt >> 4, (tgt >> 1) & 7, tgt & 1, lane, it);
+            scatter_item<EMU>(p, p.nbr, p.ninfo, s_nb[warp], s_sl[warp], tgt >> 4, (tgt >> 1) & 7, tgt & 1, lane, it);
             __syncwarp();
             if (!persistent) break;
             continue;
@@ -1460,7 +1469,14 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int 
         const bool virt = src >= p.n_nodes;
         const int2* nbt = virt ? p.vnbr + static_cast<size_t>(src - p.n_nodes) * 27
                                : p.nbr + static_cast<size_t>(src) * 27;
-        if (lane < 27) s_nb[warp][lane] = __ldg(nbt + lane);
+        if (lane < 27) {
+            const int2 e = __ldg(nbt + lane);
+            s_nb[warp][lane] = e;
+            const int k = e.y & 3;
+            s_sl[warp][lane] = (p.tslot != nullptr && (k == K_LEAF || k == K_MULTI) &&
+                                static_cast<unsigned>(e.x) < static_cast<unsigned>(p.n_nodes))
+                                   ? __ldg(p.tslot + e.x) : -1;
+        }
         __syncwarp();
         int level, skind;
         if (virt) {
@@ -1501,7 +1517,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int 
                     }
                     const bool xpath = p.Tx != nullptr && (__ldg(p.ninfo + src) & NI_XGATHER);
                     const int* ml = p.L.lists + (root ? p.L.mr_off : p.L.mf_off + par * p.L.mf_stride);
-                    walk_mclasses_adj_all(ml, zo, xc, xpath, ch, sx, sy, sz, s_nb[warp], p, g, it);
+                    walk_mclasses_adj_all(ml, zo, xc, xpath, ch, sx, sy, sz, s_nb[warp], s_sl[warp], p, g, it);
                     ml += zo[7];
                     const int np = root ? p.L.mr_pairs : p.L.mf_pairs, ns = root ? 0 : p.L.mf_singles;
                     walk_adjoint<true, true>(ml + ch.lo(np), ch.n(np), false, false, sx, sy, sz, s_nb[warp], p, g, g4,
@@ -1660,7 +1676,7 @@ __device__ __forceinline__ void walk_classes_scatter(const int* __restrict__ lis
 // difference in xbutterfly_masses_adjoint_kernel)
 template <int Z, bool EMU, class P>
 __device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ list, int len, int tx, int ty, int tz,
-                                                       const int2* __restrict__ s_nb, const P& p,
+                                                       const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const P& p,
                                                        const double (&lb)[16], const float (&lbh)[16],
                                                        const float (&lbl)[16], int item) {
     static_assert((Z & 1) == 0, "the x stage needs a > 0");
@@ -1679,7 +1695,7 @@ __device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ l
                 const int2 es = s_nb[nb_index(tx, sy, sz)];
                 const int ks = es.y & 3;
                 if (ks == K_LEAF && static_cast<unsigned>(es.x) < static_cast<unsigned>(p.n_nodes)) {
-                    dst[q] = p.Sbar + static_cast<size_t>(__ldg(p.xslot + es.x) * 7 + a - 1) * 2 * NCELL + (tx & 7) +
+                    dst[q] = p.Sbar + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + a - 1) * 2 * NCELL + (tx & 7) +
                              8 * (sy & 7) + 64 * (sz & 7);
                     any = true;
                 } else if (ks != K_NONE) {
@@ -1704,7 +1720,7 @@ __device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ l
 template <bool EMU, int Z = 0, class P>
 __device__ __forceinline__ void walk_classes_scatter_all(const int* __restrict__ list, const int* zoff, const int* xc,
                                                          bool xpath, int tx, int ty, int tz,
-                                                         const int2* __restrict__ s_nb, const P& p,
+                                                         const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const P& p,
                                                          const double (&lb)[16], const float (&lbh)[16],
                                                          const float (&lbl)[16], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
@@ -1712,12 +1728,12 @@ __device__ __forceinline__ void walk_classes_scatter_all(const int* __restrict__
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
             nx = xc[Z];
-            walk_classes_scatter_x<Z, EMU>(list + zoff[Z], nx, tx, ty, tz, s_nb, p, lb, lbh, lbl, item);
+            walk_classes_scatter_x<Z, EMU>(list + zoff[Z], nx, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, item);
         }
     }
     walk_classes_scatter<Z, EMU>(list + zoff[Z] + nx, len - nx, tx, ty, tz, s_nb, p, lb, lbh, lbl, item);
     if constexpr (Z < 6)
-        walk_classes_scatter_all<EMU, Z + 1>(list, zoff, xc, xpath, tx, ty, tz, s_nb, p, lb, lbh, lbl, item);
+        walk_classes_scatter_all<EMU, Z + 1>(list, zoff, xc, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, item);
 }
 
 template <bool PAIRED, bool NEAR, bool EMU = false, bool PM = true, class P>
@@ -1786,7 +1802,7 @@ __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int l
 // point-mass adjoint contributions into mbar
 template <bool EMU, class P>
 __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
-                             int node, int par, int half, int lane, int it) {
+                             int* s_sl, int node, int par, int half, int lane, int it) {
     int tx, ty, tz;
     lane_cell(lane, par, half, tx, ty, tz);
     double lb[16];
@@ -1810,7 +1826,13 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
         }
     }
     if (!__any_sync(0xffffffffu, nz)) return;     // targets without an adjoint contribute nothing
-    if (lane < 27) s_nb[lane] = __ldg(nbr + static_cast<size_t>(node) * 27 + lane);
+    if (lane < 27) {
+        const int2 e = __ldg(nbr + static_cast<size_t>(node) * 27 + lane);
+        s_nb[lane] = e;
+        s_sl[lane] = (p.xslot != nullptr && (e.y & 3) == K_LEAF &&
+                      static_cast<unsigned>(e.x) < static_cast<unsigned>(p.n_nodes))
+                         ? __ldg(p.xslot + e.x) : -1;
+    }
     __syncwarp();
     const int info = __ldg(ninfo + node);
     const int level = info & 0xff;
@@ -1819,12 +1841,12 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
         // by reflection class (see the forward); refined near sources over the near list
         const bool xpath = p.Sbar != nullptr && (info & NI_XMASS);
         const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-        walk_classes_scatter_all<EMU>(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        walk_classes_scatter_all<EMU>(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
         cf += p.L.cf_z[7];
         walk_scatter<true, false, EMU>(cf, p.L.cf_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         const int* cn = p.L.lists + p.L.cn_off;
-        walk_classes_scatter_all<EMU>(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        walk_classes_scatter_all<EMU>(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
         walk_scatter<true, false, EMU>(cn + p.L.cn_z[7], p.L.cn_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         if (__any_sync(0xffffffffu, lane < 27 && (s_nb[lane < 27 ? lane : 0].y & 3) == K_MULTI))
             walk_scatter<true, true, EMU, false>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, lbh,
@@ -1845,6 +1867,7 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
 
 __global__ void __launch_bounds__(256) scatter_adjoint_kernel(const ScatParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
+    __shared__ int s_sl[8][27];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -1857,7 +1880,7 @@ __global__ void __launch_bounds__(256) scatter_adjoint_kernel(const ScatParams p
         }
         if (it >= p.n_items) break;
         const int item = __ldg(p.items + it);
-        scatter_item(p, p.nbr, p.ninfo, s_nb[warp], item >> 4, (item >> 1) & 7, item & 1, lane, it);
+        scatter_item(p, p.nbr, p.ninfo, s_nb[warp], s_sl[warp], item >> 4, (item >> 1) & 7, item & 1, lane, it);
         __syncwarp();
         if (!persistent) break;
     }
@@ -2582,7 +2605,7 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
             DFAcc f;
             df_zero(f);
             const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-            walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, false, ch, tx, ty, tz, nb, p, a, it);
+            walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, false, ch, tx, ty, tz, nb, nullptr, p, a, it);
             cf += p.L.cf_z[7];
             walk_forward<2, true, 0>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                      t4, f, it);
@@ -2590,7 +2613,7 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
             walk_forward<2, false, 0>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
                                       c, t4, f, it);
             const int* cn = p.L.lists + p.L.cn_off;
-            walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, false, ch, tx, ty, tz, nb, p, a, it);
+            walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, false, ch, tx, ty, tz, nb, nullptr, p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, 0>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
                                      t4, f, it);
@@ -2763,6 +2786,7 @@ __device__ void scatter_item_com(const AdjParams& p, int2* s_nb, int node, int p
 template <int MODE>
 __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
     __shared__ int2 s_nb[8][27];
+    __shared__ int s_sl[8][27];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     for (;;) {
@@ -2776,7 +2800,7 @@ __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
             const int node = tgt >> 4;
             // a leaf target has a geometric centre: the table path's scatter
             if ((__ldg(p.ninfo + node) >> 8) & 1)
-                scatter_item(p, p.nbr, p.ninfo, s_nb[warp], node, (tgt >> 1) & 7, tgt & 1, lane, it);
+                scatter_item(p, p.nbr, p.ninfo, s_nb[warp], s_sl[warp], node, (tgt >> 1) & 7, tgt & 1, lane, it);
             else
                 scatter_item_com(p, s_nb[warp], node, (tgt >> 1) & 7, tgt & 1, lane, it);
             __syncwarp();
