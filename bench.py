@@ -179,11 +179,11 @@ def fwd_flops(info):
     return info["flops_fwd"]
 
 
-# DRAM bytes (read + written) of one forward_kernel<3> launch on the 64^3
+# DRAM bytes (read + written) of one adjoint_kernel<5> launch on the 64^3
 # polytrope workload with the 8x1 tile, from an ncu capture of that kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 155.31 MB + 44.76 MB).
+# (dram__bytes_read.sum + dram__bytes_write.sum = 115.65 MB + 28.16 MB).
 # Reported only for that workload; None once the kernel changes.
-FORWARD_DRAM_BYTES_POLYTROPE64 = 200_074_240
+ADJOINT_DRAM_BYTES_POLYTROPE64 = 143_807_488
 
 # Nominal FP64 rate of a B300 (1.25 TFLOP/s) at its maximum SM clock (2032 MHz):
 # 1.25e12 / (148 SMs * 2.032e9) = 4.16 FP64 flop per clock per SM.
@@ -393,11 +393,13 @@ def run_ours(args, rank, world):
     ach = fwd_flops(info) / (fwd_ms * 1e-3) / 1e12
     peak_ops = peak / 2                       # FP64 pipe slots: one per FMA
     ach_ops = info["fp64_ops_fwd"] / (fwd_ms * 1e-3) / 1e12
+    adj_ops = info["fp64_ops_adj"] / (adj_ms * 1e-3) / 1e12
     n_m2m = int(len({int(l) for l in tree.level[tree.is_leaf == 0]}))
-    # moments (cube + M2M levels); forward: prescale, the two x-butterfly
-    # tables, the fused launch; adjoint: prescale, the L-bar x butterflies,
-    # the fused launch, the deferred scatter pass; moment adjoint
-    launches_step = (1 + n_m2m) + 4 + 4 + (1 if info["n_virtual"] else 0) + (1 + n_m2m + 1)
+    # moments (cube + M2M levels); forward: prescale, the multipole x table,
+    # the multipole launch, the masses' x and (x, y) tables, the point-mass
+    # launch; adjoint: prescale, the L-bar x butterflies, the fused launch,
+    # the deferred scatter pass; moment adjoint
+    launches_step = (1 + n_m2m) + 6 + 4 + (1 if info["n_virtual"] else 0) + (1 + n_m2m + 1)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -444,23 +446,26 @@ def run_ours(args, rank, world):
                             "frac": info["flops_adj_com"] / (com_adj_ms * 1e-3) / 1e12 / peak},
                 "note": "centre-of-mass expansion centres: the same pairs, derivatives of G evaluated "
                         "per pair at R = C_A - C_B; fractions of the same FP64 peak"},
-        "roofline": {"bound": "alu", "kernel": "forward_kernel<3> (both passes, one launch)",
-                     "achieved": ach_ops, "peak": peak_ops, "unit": "Tinst/s", "frac": ach_ops / peak_ops,
-                     "traffic": (FORWARD_DRAM_BYTES_POLYTROPE64 if args.workload == "polytrope64" else None),
+        "roofline": {"bound": "alu",
+                     "kernel": "adjoint_kernel<5> (multipole gather + point-mass scatter, one launch)",
+                     "achieved": adj_ops, "peak": peak_ops, "unit": "Tinst/s", "frac": adj_ops / peak_ops,
+                     "traffic": (ADJOINT_DRAM_BYTES_POLYTROPE64 if args.workload == "polytrope64" else None),
                      "traffic_unit": "bytes per launch (ncu, 8x1 tile)",
                      "unit_note": ("FP64 pipe thread-instructions per second (an FMA or an add is one pipe slot); "
                                    "achieved: the algorithmic FP64 instructions of the in-domain pairs per "
-                                   "launch (library count) over the launch's CUDA-event time"),
+                                   "launch (library count) over the CUDA-event time of the adjoint call (the "
+                                   "launch and its O(cells) prologue and epilogue kernels)"),
                      "peak_source": (f"nominal B300 FP64 {NOMINAL_FP64_TFLOPS} TFLOP/s = "
                                      f"{NOMINAL_FP64_TFLOPS / 2} T FMA/s at {NOMINAL_SM_MHZ:.0f} MHz, "
                                      f"scaled to the median SM clock sampled in this run ({sm_mhz:.0f} MHz)"),
-                     "flops": {"achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "fp64_pipe_busy": info["ops_adj"] / (adj_ms * 1e-3) / (peak_ops * 1e12),
+                     "forward": {"kernels": "forward_kernel<1> then forward_kernel<2> (the two passes)",
+                                 "achieved": ach_ops, "frac": ach_ops / peak_ops,
+                                 "fp64_pipe_busy": info["ops_fwd"] / (fwd_ms * 1e-3) / (peak_ops * 1e12)},
+                     "flops": {"forward_achieved": ach, "adjoint_achieved": info["flops_adj"] / (adj_ms * 1e-3) / 1e12,
+                               "peak": peak, "unit": "TFLOP/s", "forward_frac": ach / peak,
                                "note": "algorithmic FLOPs of the algorithm run (2 per FMA, 1 per add)"},
-                     "probe_tflops": peak_tflops, "probe": probe_cfg,
-                     "fp64_pipe_busy": info["ops_fwd"] / (fwd_ms * 1e-3) / (peak_ops * 1e12),
-                     "adjoint_achieved": info["fp64_ops_adj"] / (adj_ms * 1e-3) / 1e12,
-                     "adjoint_frac": info["fp64_ops_adj"] / (adj_ms * 1e-3) / 1e12 / peak_ops,
-                     "adjoint_fp64_pipe_busy": info["ops_adj"] / (adj_ms * 1e-3) / (peak_ops * 1e12)},
+                     "probe_tflops": peak_tflops, "probe": probe_cfg},
         "e2e": {"value": world * pairs_step / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(rho_pin.numel() * 8 + Lbar_pin.numel() * 8),
                 "d2h_bytes_per_step": int(L_out.numel() * 8 + rb_out.numel() * 8), "ms": e2e_ms},

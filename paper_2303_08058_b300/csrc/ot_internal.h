@@ -79,6 +79,11 @@ struct Lists {
     // (both or neither x member at every (y, z) sign), which may read their
     // first transform stage from the prebuilt x butterflies
     int cf_x[8], cn_x[8], mf_x[8], mr_x[8];
+    // per point-mass group Z with a, b > 0: the number of xy-complete entries
+    // at the start of the x-complete head (all four or none of the (x, y)
+    // members at every z sign), which may read their first two stages from
+    // the (x, y) table
+    int cf_xy[8], cn_xy[8];
 };
 
 struct FwdParams {
@@ -117,6 +122,8 @@ struct FwdParams {
     const double* Sx;      // [non-leaf slot][7][16][2][512]: Mhat(c + a x) +- Mhat(c - a x), multipole cells
     const double* Sm;      // [leaf slot][7][2][512]: the same for the point masses
     const float2* Smf;     // the masses' table as double-float (hi, lo) pairs (double-float point masses)
+    const double* Sxy;     // [leaf slot][49: (a - 1) 7 + b - 1][4][512]: the masses at c + (+-a, +-b, 0)
+                           // transformed over x and y (null: not built)
     const int* xslot;      // [n]
 };
 
@@ -214,6 +221,8 @@ cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr
                                    double* Tx, cudaStream_t s);
 cudaError_t launch_xbutterfly_masses_adjoint(const int* nodes, int n_list, const int2* nbr, const int* xslot,
                                              const double* Sbar, int n_nodes, double* mbar, cudaStream_t s);
+cudaError_t launch_xybutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
+                                      double* Sxy, cudaStream_t s);
 cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
                                      double* Sm, cudaStream_t s);
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);

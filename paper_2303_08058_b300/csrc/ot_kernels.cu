@@ -660,24 +660,84 @@ __device__ __forceinline__ void walk_classes_fwd_df_all(const int* __restrict__ 
         walk_classes_fwd_df_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, c, t4, f, item);
 }
 
+// xy-complete point-mass classes (a, b > 0) of a leaf target with leaf or
+// empty neighbours: the first two transform stages come from the (x, y)
+// table at the positions t + (0, 0, +-c)
+template <int Z>
+__device__ __forceinline__ void walk_classes_fwd_xy(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                    const int2* __restrict__ s_nb, const int* __restrict__ s_sl,
+                                                    const FwdParams& p, double (&acc)[16], int item) {
+    static_assert((Z & 3) == 0, "the x and y stages need a, b > 0");
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        double w[8];
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[4 * r + q] = 0.0;
+            if ((4 * r) & Z) continue;
+            if ((members >> (4 * r)) & 1u) {
+                const int sz = r ? tz - c : tz + c;
+                const int nbi = nb_index(tx, ty, sz);
+                const int2 es = s_nb[nbi];
+                const int ks = checked_kind(p, es, item);
+                if (ks == K_LEAF) {
+                    const double* src = p.Sxy + static_cast<size_t>(s_sl[nbi] * 49 + (a - 1) * 7 + b - 1) * 4 * NCELL +
+                                        (tx & 7) + 8 * (ty & 7) + 64 * (sz & 7);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w[4 * r + q] = __ldg(src + q * NCELL);
+                    any = true;
+                } else if (ks != K_NONE) {
+                    report(p.status, 7, item);
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(a, b, c));
+        if constexpr (!(Z & 4)) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const double u = w[i], v = w[i | 4];
+                w[i] = u + v;
+                w[i | 4] = u - v;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (!(comp_parity(q) & Z)) acc[q] = fma(w[comp_parity(q)], d[q], acc[q]);
+    }
+}
+
 // the seven zero patterns of a class list (Z = 7 would be the self pair);
 // with xpath, each group's x-complete head (xc[Z] entries, Z without bit 0)
 // takes the prebuilt x butterflies
 template <int Z = 0, class CH>
 __device__ __forceinline__ void walk_classes_fwd_all(const int* __restrict__ list, const int* zoff, const int* xc,
-                                                     bool xpath, const CH& ch, int tx, int ty, int tz,
+                                                     const int* xyc, bool xpath, const CH& ch, int tx, int ty, int tz,
                                                      const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
                                                      double (&acc)[16], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
     int nx = 0;
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
+            int nxy = 0;
+            if constexpr ((Z & 2) == 0) {
+                if (p.Sxy != nullptr) {
+                    nxy = xyc[Z];
+                    walk_classes_fwd_xy<Z>(list + zoff[Z] + ch.lo(nxy), ch.n(nxy), tx, ty, tz, s_nb, s_sl, p, acc, item);
+                }
+            }
             nx = xc[Z];
-            walk_classes_fwd_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, s_sl, p, acc, item);
+            walk_classes_fwd_x<Z>(list + zoff[Z] + nxy + ch.lo(nx - nxy), ch.n(nx - nxy), tx, ty, tz, s_nb, s_sl, p,
+                                  acc, item);
         }
     }
     walk_classes_fwd<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, item);
-    if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, item);
+    if constexpr (Z < 6) walk_classes_fwd_all<Z + 1>(list, zoff, xc, xyc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, item);
 }
 
 // multipole sources by reflection class (non-leaf targets): the members'
@@ -1053,7 +1113,7 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             if constexpr ((EMU & 1) != 0)
                 walk_classes_fwd_df_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, f, it);
             else
-                walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
+                walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, p.L.cf_xy, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
             cf += p.L.cf_z[7];
             walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -1064,7 +1124,7 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             if constexpr ((EMU & 1) != 0)
                 walk_classes_fwd_df_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, f, it);
             else
-                walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
+                walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, p.L.cn_xy, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
@@ -2605,7 +2665,7 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
             DFAcc f;
             df_zero(f);
             const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-            walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, false, ch, tx, ty, tz, nb, nullptr, p, a, it);
+            walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, p.L.cf_xy, false, ch, tx, ty, tz, nb, nullptr, p, a, it);
             cf += p.L.cf_z[7];
             walk_forward<2, true, 0>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                      t4, f, it);
@@ -2613,7 +2673,7 @@ __global__ void __launch_bounds__(256) forward_com_kernel(const FwdParams p) {
             walk_forward<2, false, 0>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
                                       c, t4, f, it);
             const int* cn = p.L.lists + p.L.cn_off;
-            walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, false, ch, tx, ty, tz, nb, nullptr, p, a, it);
+            walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, p.L.cn_xy, false, ch, tx, ty, tz, nb, nullptr, p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, 0>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
                                      t4, f, it);
@@ -3173,6 +3233,42 @@ cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* 
     if (n_list == 0) return cudaSuccess;
     xbutterfly_moments_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Mhat,
                                                                                         n_nodes, Sx);
+    return cudaGetLastError();
+}
+
+// (x, y) butterflies of the masses: for every leaf cell c and a, b = 1..7,
+// the four transforms over x and y of the masses at c + (+-a, +-b, 0),
+// out[pi] = sum_i (-1)^|i & pi| v_i (i, pi: bit 0 x negated / x odd, bit 1 y)
+__global__ void xybutterfly_masses_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
+                                          const double* __restrict__ m, int n_nodes, double* __restrict__ Sxy) {
+    const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (gid >= 49LL * NCELL * n_list) return;
+    const int cell = static_cast<int>(gid % NCELL);
+    const int ab = static_cast<int>((gid / NCELL) % 49);
+    const int slot = static_cast<int>(gid / (49 * NCELL));
+    const int a = ab / 7 + 1, b = ab % 7 + 1;
+    const int node = __ldg(nodes + slot);
+    const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const int2* nb = nbr + static_cast<size_t>(node) * 27;
+    double v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int sx = (i & 1) ? x - a : x + a, sy = (i & 2) ? y - b : y + b;
+        v[i] = mass_at(m, __ldg(nb + nb_index(sx, sy, z)), n_nodes, sx, sy, z);
+    }
+    const double u0 = v[0] + v[1], u1 = v[0] - v[1], u2 = v[2] + v[3], u3 = v[2] - v[3];
+    double* out = Sxy + static_cast<size_t>(slot * 49 + ab) * 4 * NCELL + cell;
+    out[0] = u0 + u2;
+    out[NCELL] = u1 + u3;
+    out[2 * NCELL] = u0 - u2;
+    out[3 * NCELL] = u1 - u3;
+}
+
+cudaError_t launch_xybutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
+                                      double* Sxy, cudaStream_t s) {
+    if (n_list == 0) return cudaSuccess;
+    xybutterfly_masses_kernel<<<blocks_for(49LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, m, n_nodes,
+                                                                                         Sxy);
     return cudaGetLastError();
 }
 

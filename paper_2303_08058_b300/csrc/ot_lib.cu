@@ -125,6 +125,17 @@ inline bool x_complete(int e) {
     return true;
 }
 
+// a class entry whose members come in (x, y) quadruples: at every z sign
+// all four or none of the members with x = +-a, y = +-b
+inline bool xy_complete(int e) {
+    const unsigned m = static_cast<unsigned>(e) >> 24;
+    for (int r = 0; r < 2; ++r) {
+        const unsigned q = (m >> (4 * r)) & 15u;
+        if (q != 0u && q != 15u) return false;
+    }
+    return true;
+}
+
 inline uint64_t node_key(int l, int x, int y, int z) {
     return (static_cast<uint64_t>(l) << 60) | (static_cast<uint64_t>(x) << 40) |
            (static_cast<uint64_t>(y) << 20) | static_cast<uint64_t>(z);
@@ -209,6 +220,8 @@ struct ot_grid {
     int* d_leaf = nullptr;              // leaf nodes in slot order
     double* d_Sx = nullptr;             // [non-leaf slot][7][16][2][512]
     double* d_Sm = nullptr;             // [leaf slot][7][2][512]
+    double* d_Sxy = nullptr;            // [leaf slot][49][4][512]: the masses' (x, y) butterflies
+    bool use_xy = false;                // the (x, y) table fits (its size is capped)
     float2* d_Smf = nullptr;            // the same as double-float pairs
     std::vector<int> tslot, tnodes;     // the gather's L-bar butterflies: slot per node, nodes per slot
     int* d_tslot = nullptr;
@@ -476,8 +489,12 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         // within a group with a > 0, the x-complete classes first (both or
         // neither of the x members at every (y, z) sign): their first
         // transform stage can come from the prebuilt x butterflies
-        for (int z = 0; z < 8; z += 2)
-            std::stable_partition(cls[z].begin(), cls[z].end(), [](int e) { return x_complete(e); });
+        for (int z = 0; z < 8; z += 2) {
+            auto xe = std::stable_partition(cls[z].begin(), cls[z].end(), [](int e) { return x_complete(e); });
+            // and within that head, for a, b > 0, the xy-complete classes
+            // first: their first two stages can come from the (x, y) table
+            if (!(z & 2)) std::stable_partition(cls[z].begin(), xe, [](int e) { return xy_complete(e); });
+        }
     };
     std::vector<int> cfar[8][8], cfar_pair[8], cfar_single[8], cnear[8], cnear_pair, cnear_single;
     for (int p = 0; p < 8; ++p) class_split(far_offs[p], cfar[p], cfar_pair[p], cfar_single[p], false);
@@ -512,7 +529,17 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         while (c < static_cast<int>(v.size()) && x_complete(v[c])) ++c;
         return c;
     };
+    auto xycount = [](const std::vector<int>& v) {
+        int c = 0;
+        while (c < static_cast<int>(v.size()) && xy_complete(v[c])) ++c;
+        return c;
+    };
     for (int z = 0; z < 8; ++z) {
+        Lh.cf_xy[z] = (z & 3) ? 0 : xycount(cfar[0][z]);
+        Lh.cn_xy[z] = (z & 3) ? 0 : xycount(cnear[z]);
+        for (int p = 1; p < 8; ++p)
+            if (!(z & 3) && xycount(cfar[p][z]) != Lh.cf_xy[z])
+                return fail(OT_EINVAL, "internal: parity class stencils differ in shape");
         Lh.cf_x[z] = (z & 1) ? 0 : xcount(cfar[0][z]);
         Lh.cn_x[z] = (z & 1) ? 0 : xcount(cnear[z]);
         Lh.mf_x[z] = (z & 1) ? 0 : xcount(mfar[0][z]);
@@ -668,6 +695,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     g->xslot.assign(n, -1);
     g->n_xnonleaf = g->n_xleaf = 0;
     for (int i = 0; i < n; ++i) g->xslot[i] = g->is_leaf[i] ? g->n_xleaf++ : g->n_xnonleaf++;
+    // the (x, y) table of the masses takes 0.8 MB per leaf sub-grid: built
+    // up to 8 GiB
+    g->use_xy = static_cast<double>(g->n_xleaf) * 49 * 4 * NCELL * sizeof(double) <= 8.0 * (1 << 30);
     for (int i = 0; i < n; ++i) {
         bool same = true;
         for (int j = 0; j < 27 && same; ++j) {
@@ -772,6 +802,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         cmem[cg].resize(cseg_len[cg]);
         const int* zx = cg == 0 ? g->Lh.cf_x : cg == 1 ? g->Lh.cn_x : cg == 2 ? g->Lh.mf_x : g->Lh.mr_x;
         const int* zz = cg == 0 ? g->Lh.cf_z : cg == 1 ? g->Lh.cn_z : cg == 2 ? g->Lh.mf_z : g->Lh.mr_z;
+        static const int none[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int* zxy = cg == 0 ? g->Lh.cf_xy : cg == 1 ? g->Lh.cn_xy : none;
         for (int ph = 0; ph < 16; ++ph) {
             const int par = ph >> 1, half = ph & 1;
             const int off = cg == 0 ? g->Lh.cf_off + par * g->Lh.cf_stride : cg == 1 ? g->Lh.cn_off
@@ -801,13 +833,18 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     } else {
                         cf = cs = class_adds(Z) + class_fmas(Z);
                         fl_f = fl_s = class_adds(Z) + 2 * class_fmas(Z);
-                        // without the x stage: (d - 1) 2^d adds
-                        const int xadds = xe ? class_adds(Z) - (class_adds(Z) / std::max(1, 3 - __builtin_popcount(Z)))
-                                             : class_adds(Z);
+                        // without the x stage: (d - 1) 2^d adds; without the x
+                        // and y stages (xy-complete head, a and b > 0): (d - 2) 2^d
+                        const int d = 3 - __builtin_popcount(Z);
+                        const bool xye = xe && !(Z & 2) && k - zz[Z] < zxy[Z] && g->use_xy;
+                        const int xadds = xye ? class_adds(Z) - 2 * (1 << d) : xe ? class_adds(Z) - (1 << d)
+                                                                                  : class_adds(Z);
                         cfx = xadds + class_fmas(Z);
                         fl_fx = xadds + 2 * class_fmas(Z);
-                        csx = cfx;          // the scatter defers its x stage alike
-                        fl_sx = fl_fx;
+                        // the scatter defers its x stage only
+                        const int sadds = xe ? class_adds(Z) - (1 << d) : class_adds(Z);
+                        csx = sadds + class_fmas(Z);
+                        fl_sx = sadds + 2 * class_fmas(Z);
                     }
                 } else {
                     const int ox = (e & 0xff) - 8, oy = ((e >> 8) & 0xff) - 8, oz = ((e >> 16) & 0xff) - 8;
@@ -1457,6 +1494,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         return st;
     if ((st = g->alloc(&g->d_Sbar, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Smf, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
+    if (g->use_xy &&
+        (st = g->alloc(&g->d_Sxy, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 49 * 4 * NCELL)) != OT_OK)
+        return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
@@ -1513,11 +1553,16 @@ static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, 
 // enqueue one forward pass (mode 1, 2 or 3) on stream s
 static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const double* m, double* L, double* Lc,
                                  int accumulate, cudaStream_t s) {
-    if (mode == 3 && g->precision != 0 && g->schedule == OT_SCHED_PERSISTENT) {
-        // With double-float contractions both passes run as two launches:
-        // fused, the one kernel holds the FP64 or double-float multipole code
-        // and the double-float point-mass code at once, and the mix of the two
-        // item kinds on an SM ran 1.5-1.7x slower than the two launches.
+    if (mode == 3 && (g->precision != 0 || g->use_xy)) {
+        // Both passes as two launches.  With double-float contractions the
+        // one kernel holds the multipole code and the double-float point-mass
+        // code at once, and the mix of the two item kinds on an SM ran
+        // 1.5-1.7x slower than the two launches.  In FP64 with the masses'
+        // (x, y) table the point-mass items stream that table (0.8 MB per
+        // leaf sub-grid) through L2 while the multipole items reread theirs:
+        // fused, the two passes took 8.35 ms against 4.40 + 3.51 ms apart.
+        // The per-sub-grid schedule splits alike, so that both schedules sum
+        // in the same order.
         ot_status st = enqueue_forward(g, 1, M, m, L, Lc, accumulate, s);
         if (st != OT_OK) return st;
         return enqueue_forward(g, 2, M, m, L, nullptr, 1, s);
@@ -1546,6 +1591,10 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         OT_CUDA(launch_xbutterfly_masses(g->d_leaf, g->n_xleaf, g->d_nbr, m, g->n, g->d_Sm, s));
         if (g->precision == 0) {
             p.Sm = g->d_Sm;
+            if (g->use_xy) {
+                OT_CUDA(launch_xybutterfly_masses(g->d_leaf, g->n_xleaf, g->d_nbr, m, g->n, g->d_Sxy, s));
+                p.Sxy = g->d_Sxy;
+            }
         } else {
             // double-float point masses read the table as (hi, lo) pairs
             OT_CUDA(launch_split_masses(g->d_Sm, g->d_Smf, static_cast<size_t>(g->n_xleaf) * 7 * 2 * NCELL, s));
@@ -2119,6 +2168,7 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     // and the x butterflies the warm-up built from the same M and m
     if (g->precision != 2 && g->n_xnonleaf > 0) p.Sx = g->d_Sx;
     if (g->precision == 0 && g->n_xleaf > 0) p.Sm = g->d_Sm;
+    if (g->precision == 0 && g->n_xleaf > 0 && g->use_xy) p.Sxy = g->d_Sxy;
     if (g->precision != 0 && g->n_xleaf > 0) p.Smf = g->d_Smf;
     if (g->n_chunk_ctrs > 0) {
         OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs) * sizeof(int), streams[0]));
