@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-cell interactions/s FP64 (fwd, fwd+adjoint) and % of B300 FP64 roofline"
 UNIT = "interactions/s"
 WORKLOAD = ("uniform level: 512 leaf sub-grids (64^3 cells, h=1) + coarse levels 0-2, n=1 polytrope "
-            "R=28 rho_c=1 floor 1e-10 centred; multipole + monopole passes in one batched launch, then the adjoint")
+            "R=28 rho_c=1 floor 1e-10 centred; multipole and monopole passes as batched launches, then the adjoint")
 
 
 def parse():
@@ -151,7 +151,7 @@ class ClockSampler:
 WORKLOADS = {
     "polytrope64": WORKLOAD,
     "adaptive": ("adaptive octree, levels 3-6 (4,641 sub-grids, 4,061 leaves), n=1 polytrope with seeded centre, "
-                 "refined where rho > 1e-3 rho_c, 2:1 balanced; both passes in one batched launch, then the adjoint"),
+                 "refined where rho > 1e-3 rho_c, 2:1 balanced; both passes as batched launches, then the adjoint"),
     "binary": ("rotating binary star: two n=1 polytropes (q=0.5, R=24 and 19, 60 apart), levels 3-7 "
                "(~9,500 sub-grids, ~8,300 leaves, 4.25M leaf cells), rotated 0.01 rad per step, octree rebuilt "
                "each step; both passes + adjoint per step"),
@@ -425,7 +425,7 @@ def run_ours(args, rank, world):
                          "note": "coarse-fine pairs: point masses that are virtual descendants of a coarser "
                                  "leaf, and coarse leaf targets refined virtually against a refined neighbour's "
                                  "children; both run inside the monopole launch"},
-            "note": "separate launches of one pass each; the fused launch (fwd) runs both"},
+            "note": "one pass per call; fwd runs both passes (two persistent launches)"},
         "adjoint": {"value": pairs_fwd / (adj_ms * 1e-3), "unit": UNIT, "ms": adj_ms},
         "fwd_df64_point_mass": {"value": pairs_fwd / (df_ms * 1e-3), "unit": UNIT, "ms": df_ms,
                                 "note": "point-mass pairs in double-float on the FP32 pipe (within 1e-12 of "
