@@ -177,9 +177,13 @@ ot_status ot_multipole_interactions(ot_grid* grid, const double* M, const double
  * L [n][20][512] is ACCUMULATED into (call after the multipole pass, or zero it). */
 ot_status ot_monopole_interactions(ot_grid* grid, const double* m, double* L, void* stream);
 
-/* Both passes fused in one batched launch (the schedule set by
- * ot_set_schedule; replayed from a CUDA graph when graphs are enabled).
- * L overwritten with the sum of both passes; Lc as above (may be NULL). */
+/* Both passes as batched launches (the schedule set by ot_set_schedule;
+ * replayed from a CUDA graph when graphs are enabled): one launch holding
+ * both passes' work items, or the multipole pass then the monopole pass as
+ * two launches when the point masses read the per-call (x, y) table or the
+ * contractions run in double-float (the same sums either way, up to the
+ * order of the two passes' additions into L).  L overwritten with the sum
+ * of both passes; Lc as above (may be NULL). */
 ot_status ot_interactions(ot_grid* grid, const double* M, const double* m,
                           double* L, double* Lc, void* stream);
 
