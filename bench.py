@@ -2,11 +2,12 @@
 
 One step = the whole path over the uniform 64^3 polytrope workload (512 leaf
 sub-grids plus the coarse levels 0-2: 585 sub-grids, 299,520 cells):
-moments from densities, both interaction passes in one persistent launch
+moments from densities, both interaction passes as persistent launches
 replayed from a CUDA graph (multipole pass at the coarse levels, point-mass
-pass with near field at the leaves), the adjoint of both passes (transposed
-stencil, a gather over sources) for a seeded L-bar, and the adjoint of the
-moments.  Throughput = (forward + adjoint pairs) / step time.
+pass with near field at the leaves), the adjoint of both passes (multipole
+sources gather over the transposed stencil, point masses receive theirs by
+target) for a seeded L-bar, and the adjoint of the moments.  Throughput =
+(forward + adjoint pairs) / step time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -179,11 +180,12 @@ def fwd_flops(info):
     return info["flops_fwd"]
 
 
-# DRAM bytes (read + written) of one adjoint_kernel<5> launch on the 64^3
-# polytrope workload with the 8x1 tile, from an ncu capture of that kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 115.65 MB + 28.16 MB).
-# Reported only for that workload; None once the kernel changes.
-ADJOINT_DRAM_BYTES_POLYTROPE64 = 143_807_488
+# DRAM bytes (read + written) of one forward_kernel<1> launch (the multipole
+# pass) on the 64^3 polytrope workload with the 8x2 tile, from an ncu capture
+# of that kernel (dram__bytes_read.sum + dram__bytes_write.sum).  Reported
+# only for that workload and tile; None once the kernel changes.
+MULTIPOLE_DRAM_BYTES_POLYTROPE64 = 174_318_080     # 140.63 MB read + 33.69 MB written
+MULTIPOLE_DRAM_TILE = (8, 2)
 
 # Nominal FP64 rate of a B300 (1.25 TFLOP/s) at its maximum SM clock (2032 MHz):
 # 1.25e12 / (148 SMs * 2.032e9) = 4.16 FP64 flop per clock per SM.
@@ -281,7 +283,7 @@ def run_ours(args, rank, world):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     g.check()
 
-    # -- dominant kernel: the fused forward launch, timed alone --------------
+    # -- the forward and the adjoint calls, each timed alone ------------------
     fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
     for a, b in fe:
         flush.zero_()
@@ -394,12 +396,17 @@ def run_ours(args, rank, world):
     peak_ops = peak / 2                       # FP64 pipe slots: one per FMA
     ach_ops = info["fp64_ops_fwd"] / (fwd_ms * 1e-3) / 1e12
     adj_ops = info["fp64_ops_adj"] / (adj_ms * 1e-3) / 1e12
+    multi_ms = variant_ms["multipole"]
+    multi_ops = info["fp64_ops_fwd_multi"] / (multi_ms * 1e-3) / 1e12
+    tile = (info["warps_per_block"], info["blocks_per_sm"])
+    traffic = (MULTIPOLE_DRAM_BYTES_POLYTROPE64
+               if args.workload == "polytrope64" and tile == MULTIPOLE_DRAM_TILE else None)
     n_m2m = int(len({int(l) for l in tree.level[tree.is_leaf == 0]}))
     # moments (cube + M2M levels); forward: prescale, the multipole x table,
     # the multipole launch, the masses' x and (x, y) tables, the point-mass
-    # launch; adjoint: prescale, the L-bar x butterflies, the fused launch,
-    # the deferred scatter pass; moment adjoint
-    launches_step = (1 + n_m2m) + 6 + 4 + (1 if info["n_virtual"] else 0) + (1 + n_m2m + 1)
+    # launch; adjoint: prescale, the L-bar x butterflies, the gather launch,
+    # the scatter launch, the deferred scatter pass; moment adjoint
+    launches_step = (1 + n_m2m) + 6 + 5 + (1 if info["n_virtual"] else 0) + (1 + n_m2m + 1)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -447,21 +454,26 @@ def run_ours(args, rank, world):
                 "note": "centre-of-mass expansion centres: the same pairs, derivatives of G evaluated "
                         "per pair at R = C_A - C_B; fractions of the same FP64 peak"},
         "roofline": {"bound": "alu",
-                     "kernel": "adjoint_kernel<5> (multipole gather + point-mass scatter, one launch)",
-                     "achieved": adj_ops, "peak": peak_ops, "unit": "Tinst/s", "frac": adj_ops / peak_ops,
-                     "traffic": (ADJOINT_DRAM_BYTES_POLYTROPE64 if args.workload == "polytrope64" else None),
-                     "traffic_unit": "bytes per launch (ncu, 8x1 tile)",
+                     "kernel": ("forward_kernel<1> (the multipole pass: non-leaf targets, multipole sources "
+                                "with the angular term; one launch, the step's largest)"),
+                     "achieved": multi_ops, "peak": peak_ops, "unit": "Tinst/s", "frac": multi_ops / peak_ops,
+                     "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu, %dx%d tile)" % MULTIPOLE_DRAM_TILE,
                      "unit_note": ("FP64 pipe thread-instructions per second (an FMA or an add is one pipe slot); "
                                    "achieved: the algorithmic FP64 instructions of the in-domain pairs per "
-                                   "launch (library count) over the CUDA-event time of the adjoint call (the "
-                                   "launch and its O(cells) prologue and epilogue kernels)"),
+                                   "launch (library count) over the CUDA-event time of the multipole call (the "
+                                   "launch and its O(cells) prologue kernels)"),
                      "peak_source": (f"nominal B300 FP64 {NOMINAL_FP64_TFLOPS} TFLOP/s = "
                                      f"{NOMINAL_FP64_TFLOPS / 2} T FMA/s at {NOMINAL_SM_MHZ:.0f} MHz, "
                                      f"scaled to the median SM clock sampled in this run ({sm_mhz:.0f} MHz)"),
-                     "fp64_pipe_busy": info["ops_adj"] / (adj_ms * 1e-3) / (peak_ops * 1e12),
+                     "fp64_pipe_busy": info["ops_fwd_multi"] / (multi_ms * 1e-3) / (peak_ops * 1e12),
                      "forward": {"kernels": "forward_kernel<1> then forward_kernel<2> (the two passes)",
                                  "achieved": ach_ops, "frac": ach_ops / peak_ops,
                                  "fp64_pipe_busy": info["ops_fwd"] / (fwd_ms * 1e-3) / (peak_ops * 1e12)},
+                     "adjoint": {"kernels": ("adjoint_kernel<1> (multipole gather) then adjoint_kernel<4> "
+                                             "(point masses by target)"),
+                                 "achieved": adj_ops, "frac": adj_ops / peak_ops,
+                                 "fp64_pipe_busy": info["ops_adj"] / (adj_ms * 1e-3) / (peak_ops * 1e12)},
                      "flops": {"forward_achieved": ach, "adjoint_achieved": info["flops_adj"] / (adj_ms * 1e-3) / 1e12,
                                "peak": peak, "unit": "TFLOP/s", "forward_frac": ach / peak,
                                "note": "algorithmic FLOPs of the algorithm run (2 per FMA, 1 per add)"},

@@ -132,6 +132,9 @@ typedef struct {
                                       forward launch over the in-domain pairs: the FP64 pipe's
                                       work (a class or +-o entry's shared by its members) */
     int64_t fp64_ops_adj;          /* the same for the adjoint in use */
+    int64_t fp64_ops_fwd_multi;    /* the part of fp64_ops_fwd in the multipole pass (the
+                                      launch of ot_multipole_interactions) */
+    int64_t ops_fwd_multi;         /* the part of ops_fwd in the multipole pass */
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the
@@ -195,8 +198,9 @@ ot_status ot_interactions(ot_grid* grid, const double* M, const double* m,
  * by default from the target-ordered walk with atomic adds into mbar (fewer
  * FP64 operations; summation order, hence the last bits, vary from run to
  * run); after ot_set_deterministic(grid, 1) it also comes from the gather
- * (fixed order, bit-reproducible).  Stores nothing from the forward pass.
- * Mbar / mbar may be NULL to skip that half. */
+ * (fixed order, bit-reproducible).  Under the persistent schedule the gather
+ * and the target-ordered walk are two launches.  Stores nothing from the
+ * forward pass.  Mbar / mbar may be NULL to skip that half. */
 ot_status ot_interactions_backward(ot_grid* grid, const double* Lbar, double* Mbar,
                                    double* mbar, void* stream);
 

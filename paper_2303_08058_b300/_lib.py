@@ -52,7 +52,8 @@ class GridInfo(ctypes.Structure):
                 ("flops_fwd_com", ctypes.c_int64), ("flops_adj_com", ctypes.c_int64),
                 ("pairs_refined", ctypes.c_int64), ("pairs_padded_fwd", ctypes.c_int64),
                 ("chunked_subgrids", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("fp64_ops_fwd", ctypes.c_int64), ("fp64_ops_adj", ctypes.c_int64)]
+                ("fp64_ops_fwd", ctypes.c_int64), ("fp64_ops_adj", ctypes.c_int64),
+                ("fp64_ops_fwd_multi", ctypes.c_int64), ("ops_fwd_multi", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -1485,7 +1485,9 @@ template <bool EMU = false, class P>
 __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
                              int* s_sl, int node, int par, int half, int lane, int it);
 
-// EMU: double-float multipole gather and point-mass scatter (MODE 1, 4, 5)
+// MODE 1: multipole gather items; 2, 3: the point masses gathered too (the
+// deterministic adjoint); 4: point-mass items by target (atomic adds).
+// EMU: double-float multipole gather and point-mass scatter (MODE 1, 4)
 template <int MODE, bool EMU = false>
 __global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
@@ -3040,7 +3042,6 @@ cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wp
         switch (mode) {
             case 1: adjoint_kernel<1, true><<<grid, block, 0, s>>>(p, per); break;
             case 4: adjoint_kernel<4, true><<<grid, block, 0, s>>>(p, per); break;
-            case 5: adjoint_kernel<5, true><<<grid, block, 0, s>>>(p, per); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
@@ -3049,7 +3050,6 @@ cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wp
         case 1: adjoint_kernel<1><<<grid, block, 0, s>>>(p, per); break;
         case 2: adjoint_kernel<2><<<grid, block, 0, s>>>(p, per); break;
         case 4: adjoint_kernel<4><<<grid, block, 0, s>>>(p, per); break;
-        case 5: adjoint_kernel<5><<<grid, block, 0, s>>>(p, per); break;
         default: adjoint_kernel<3><<<grid, block, 0, s>>>(p, per); break;
     }
     return cudaGetLastError();
@@ -3082,16 +3082,14 @@ int forward_max_blocks_per_sm(int mode, int wpb) {
     return n;
 }
 
-// mode 1-5 FP64; 9, 12, 13: the double-float variants of modes 1, 4, 5
+// mode 1-4 FP64; 9, 12: the double-float variants of modes 1, 4
 int adjoint_max_blocks_per_sm(int mode, int wpb) {
     int n = 0;
     const void* f = (mode == 1)    ? (const void*)adjoint_kernel<1>
                     : (mode == 2)  ? (const void*)adjoint_kernel<2>
                     : (mode == 4)  ? (const void*)adjoint_kernel<4>
-                    : (mode == 5)  ? (const void*)adjoint_kernel<5>
                     : (mode == 9)  ? (const void*)adjoint_kernel<1, true>
                     : (mode == 12) ? (const void*)adjoint_kernel<4, true>
-                    : (mode == 13) ? (const void*)adjoint_kernel<5, true>
                                    : (const void*)adjoint_kernel<3>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, 32 * wpb, 0);
     return n;

@@ -197,7 +197,7 @@ struct ot_grid {
     float2* d_Mf = nullptr;             // reduced moments as double-float pairs (scratch)
     float2* d_Dt2 = nullptr;            // the derivative table as double-float pairs
     int maxb_emu2[4][9] = {};           // forward with double-float multipole contractions, modes 1 and 3
-    int maxb_adj_emu[14][9] = {};       // double-float adjoint, modes 9, 12, 13 (= 1, 4, 5 + 8)
+    int maxb_adj_emu[13][9] = {};       // double-float adjoint, modes 9, 12 (= 1, 4 + 8)
     int* d_lists = nullptr;
     double* d_hinv = nullptr;
     int* d_items_fwd[4] = {nullptr, nullptr, nullptr, nullptr};     // LPT order, by mode
@@ -249,7 +249,6 @@ struct ot_grid {
     int maxb_fwd[4][9] = {};
     int maxb_adj[4][9] = {};
     int maxb_scat[9] = {};
-    int maxb_fast5[9] = {};
     int maxb_emu[4][9] = {};            // forward with double-float point masses, modes 2 and 3
     int maxb_com_fwd[4][9] = {};        // explicit expansion centres
     int maxb_com_adj[6][9] = {};        // modes 1-3 gather, 4-5 with point-mass items by target
@@ -916,6 +915,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // algorithmic FP64 instructions (one per FMA or add) of the in-domain
     // pairs, shared per entry like the FLOPs: the FP64 pipe's work
     double alg_fwd = 0.0, alg_adj_scat = 0.0, alg_adj_multi = 0.0, alg_adj_det = 0.0;
+    double alg_fwd_multi = 0.0;        // the multipole pass alone (pass 1)
+    long long ops_fwd_multi = 0;
     std::vector<std::pair<long long, int>> fwd[4];
     std::vector<int> node_order_items;
     std::vector<long long> node_cost(n, 0);   // largest item of the node (both passes)
@@ -947,9 +948,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     pairs_ang += cpf + csf;
                     flops_fwd += std::llround(CFL[desc->level[i] == 0 ? 3 : 2][j]);
                     alg_fwd += COP[desc->level[i] == 0 ? 3 : 2][j];
+                    alg_fwd_multi += COP[desc->level[i] == 0 ? 3 : 2][j];
                 } else {
                     flops_fwd += 86 * cpf + 140 * csf;
                     alg_fwd += 51.0 * cpf + 70.0 * csf;
+                    alg_fwd_multi += 51.0 * cpf + 70.0 * csf;
                 }
                 // explicit centres: every multipole pair evaluates its derivatives
                 flops_fwd_com += (cpf + csf) * (leaf ? deriv_flops(19) + 140 : deriv_flops(31) + 200);
@@ -1050,6 +1053,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 ops_adj_scat += 32 * (cost[2] - count_single_mono);
             }
             ops_fwd += 32 * (cost[1] + cost[2]);
+            ops_fwd_multi += 32 * cost[1];
             count_single_mono = 0;
             const int item = (i << 4) | ph;
             node_order_items.push_back(item);
@@ -1370,6 +1374,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     I.chunked_subgrids = g->n_chunk_ctrs / 16;
     I.flops_fwd = flops_fwd;
     I.fp64_ops_fwd = std::llround(alg_fwd);
+    I.fp64_ops_fwd_multi = std::llround(alg_fwd_multi);
+    I.ops_fwd_multi = ops_fwd_multi;
     g->fp64_ops_adj_det = std::llround(alg_adj_det);
     g->fp64_ops_adj_fast = std::llround(alg_adj_multi + alg_adj_scat);
     I.fp64_ops_adj = g->fp64_ops_adj_fast;
@@ -1387,10 +1393,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         g->maxb_emu[3][w] = forward_max_blocks_per_sm(7, w);
         g->maxb_emu2[1][w] = forward_max_blocks_per_sm(5, w);
         g->maxb_emu2[3][w] = forward_max_blocks_per_sm(8, w);
-        for (int m : {9, 12, 13}) g->maxb_adj_emu[m][w] = adjoint_max_blocks_per_sm(m, w);
+        for (int m : {9, 12}) g->maxb_adj_emu[m][w] = adjoint_max_blocks_per_sm(m, w);
         g->maxb_scat[w] = scatter_max_blocks_per_sm(w);
         g->maxb_adj[4 - 4][w] = adjoint_max_blocks_per_sm(4, w);   // slot 0: fused, point masses only
-        g->maxb_fast5[w] = adjoint_max_blocks_per_sm(5, w);
     }
     for (int mode = 1; mode <= 3; ++mode)
         for (int w = 2; w <= 8; w *= 2) {
@@ -1673,27 +1678,33 @@ static ot_status enqueue_scatter(ot_grid* g, double* mbar, cudaStream_t s) {
     return OT_OK;
 }
 
-static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, double* mbar, cudaStream_t s) {
+// lbar_ready: d_Lrbar already holds this call's prescaled L-bar
+static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, double* mbar, cudaStream_t s,
+                                  bool lbar_ready = false) {
     int mode = (Mbar ? 1 : 0) | (mbar ? 2 : 0);
     if (mode == 0) return OT_OK;
     const bool scatter = !g->deterministic && mbar != nullptr;
-    if (mode == 3 && scatter && g->precision == OT_PREC_DF64 && g->schedule == OT_SCHED_PERSISTENT) {
-        // double-float: the gather and the scatter as two launches (one
-        // kernel holding both double-float walks ran 1.35x slower than the
-        // two launches on the 64^3 polytrope)
-        ot_status st = enqueue_backward(g, Lbar, Mbar, nullptr, s);
+    if (mode == 3 && scatter && g->schedule == OT_SCHED_PERSISTENT) {
+        // the multipole gather and the point-mass scatter as two launches:
+        // the gather's kernel holds 254 registers (8 warps per SM), the
+        // scatter's 128 (16 warps per SM); on the 64^3 polytrope the two
+        // launches take 7.19 ms against 7.47 ms for one kernel holding both
+        // walks (double-float: 1.35x)
+        ot_status st = enqueue_backward(g, Lbar, Mbar, nullptr, s, lbar_ready);
         if (st != OT_OK) return st;
-        return enqueue_backward(g, Lbar, nullptr, mbar, s);
+        return enqueue_backward(g, Lbar, nullptr, mbar, s, true);
     }
-    PrepParams pp;
-    std::memset(&pp, 0, sizeof(pp));
-    pp.src = Lbar;
-    pp.dst = g->d_Lrbar;
-    pp.nodes = g->d_all;
-    pp.n_list = g->n;
-    pp.ninfo = g->d_ninfo;
-    for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = g->hinv[l];
-    OT_CUDA(launch_prescale_adjoint(pp, s));
+    if (!lbar_ready) {
+        PrepParams pp;
+        std::memset(&pp, 0, sizeof(pp));
+        pp.src = Lbar;
+        pp.dst = g->d_Lrbar;
+        pp.nodes = g->d_all;
+        pp.n_list = g->n;
+        pp.ninfo = g->d_ninfo;
+        for (int l = 0; l < MAXLEV; ++l) pp.hinv[l] = g->hinv[l];
+        OT_CUDA(launch_prescale_adjoint(pp, s));
+    }
     if (Mbar) OT_CUDA(cudaMemsetAsync(Mbar, 0, static_cast<size_t>(g->n) * NCOMP * NCELL * sizeof(double), s));
     if (mbar) OT_CUDA(cudaMemsetAsync(mbar, 0, static_cast<size_t>(g->n) * NCELL * sizeof(double), s));
     if (scatter && g->schedule == OT_SCHED_PER_SUBGRID) {
@@ -1751,12 +1762,12 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
             OT_CUDA(launch_adjoint(q, mode, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s));
         }
     } else if (scatter) {
-        // one persistent launch: multipole gather items (if Mbar) and
-        // point-mass scatter items, longest first
-        const int k = (mode & 1) ? 1 : 0;
-        p.items = k ? g->d_itemsc_adj_fast1 : g->d_items_adj_fast[0];
-        p.n_items = k ? g->n_itemsc_adj_fast1 : g->n_items_adj_fast[0];
-        int maxb = k ? g->maxb_fast5[g->wpb] : g->maxb_adj[0][g->wpb];
+        // the point-mass adjoint by target as one persistent launch, longest
+        // items first (mode 2 only here: a call that wants M-bar too ran the
+        // gather before it as its own launch)
+        p.items = g->d_items_adj_fast[0];
+        p.n_items = g->n_items_adj_fast[0];
+        int maxb = g->maxb_adj[0][g->wpb];
         if (g->precision == OT_PREC_DF64) {
             // double-float: L-bar split into (hi, lo) pairs in the moments'
             // scratch (calls on one grid are serialized)
@@ -1764,7 +1775,7 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
             p.Lf = g->d_Mf;
             p.Dt2 = g->d_Dt2;
             p.Dt32 = g->d_Dt32;
-            maxb = g->maxb_adj_emu[k ? 13 : 12][g->wpb];
+            maxb = g->maxb_adj_emu[12][g->wpb];
         }
         // FP64 scatter: the x stage of x-complete classes deferred to a pass
         // over the leaf cells
@@ -1775,7 +1786,7 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
             p.xslot = g->d_xslot;
         }
         OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
-        OT_CUDA(launch_adjoint(p, k ? 5 : 4, true, g->wpb, grid_blocks(g, maxb), s));
+        OT_CUDA(launch_adjoint(p, 4, true, g->wpb, grid_blocks(g, maxb), s));
         if (defer)
             OT_CUDA(launch_xbutterfly_masses_adjoint(g->d_leaf, g->n_xleaf, g->d_nbr, g->d_xslot, g->d_Sbar, g->n,
                                                      mbar, s));
@@ -2533,7 +2544,8 @@ ot_status ot_autotune(ot_grid* g, const double* M, const double* m, double* L, d
     } free_mbar{mbar};
     for (int wi = 0; wi < 3; ++wi) {
         const int w = ws[wi];
-        const int maxb = std::max(g->maxb_fwd[3][w], g->maxb_fast5[w]);
+        const int maxb = std::max({g->maxb_fwd[1][w], g->maxb_fwd[2][w], g->maxb_fwd[3][w], g->maxb_adj[0][w],
+                                   g->maxb_adj[1][w]});
         for (int b = 1; b <= std::min(maxb, 16); ++b) {
             g->wpb = w;
             g->bps = b;

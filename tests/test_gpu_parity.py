@@ -229,6 +229,8 @@ def test_schedules_are_bitwise_identical(ot):
         info = g.info()
         assert info["chunked_subgrids"] > 0
         assert 0 < info["fp64_ops_fwd"] < info["ops_fwd"] and 0 < info["fp64_ops_adj"] < info["ops_adj"]
+        assert 0 < info["fp64_ops_fwd_multi"] < info["fp64_ops_fwd"]
+        assert info["fp64_ops_fwd_multi"] < info["ops_fwd_multi"] < info["ops_fwd"]
         g.set_schedule(*sched)
         g.set_deterministic(True)
         M, m = g.moments(dev(rho))
