@@ -14,8 +14,10 @@ fails at least one of them:
 * Newton's third law over closed pair sets; harmonicity of the expansions.
 * Pair coverage: a single point mass through the full multilevel solve must
   give -1/r at every other leaf cell (a missed or doubled pair would not).
-* Full solve against the brute-force pairwise sum and against the closed-form
-  potential of a uniform sphere.
+* Full solve against the brute-force pairwise sum, against the closed-form
+  potentials of a uniform sphere and of an n = 1 polytrope, and against the
+  exact potential of piecewise-constant cells (closed-form cube integrals,
+  themselves checked by cubature and the point-mass limit).
 * The transposed sums against the forward passes (dot-product identity).
 * Virtual descendants of a coarse leaf against explicitly refined leaves.
 """
@@ -437,6 +439,114 @@ def test_uniform_sphere_closed_form_converges(orc):
         core = r < R / 2
         errs.append(np.max(np.abs(phi[core] - exact[core]) / np.abs(exact[core])))
     assert errs[1] < errs[0] and errs[1] < 0.05, errs
+
+
+# ---------------------------------------------------------------------------
+# exact potential of piecewise-constant cells (homogeneous rectangular prisms)
+# ---------------------------------------------------------------------------
+
+def _prism_F(x, y, z):
+    """An antiderivative F of 1/r with d^3 F / dx dy dz = 1/r (the closed form
+    behind the potential of a homogeneous rectangular prism, Nagy 1966 and
+    Waldvogel 1976), for coordinates that are all non-zero."""
+    r = np.sqrt(x * x + y * y + z * z)
+    return (x * y * np.log(z + r) + y * z * np.log(x + r) + z * x * np.log(y + r)
+            - 0.5 * x * x * np.arctan(y * z / (x * r))
+            - 0.5 * y * y * np.arctan(z * x / (y * r))
+            - 0.5 * z * z * np.arctan(x * y / (z * r)))
+
+
+def prism_integral(lo, hi):
+    """The integral of dV / r over the box [lo, hi] (coordinates relative to
+    the field point; [..., 3] arrays): F summed over the 8 corners with the
+    sign of a nested definite integral."""
+    lo = np.asarray(lo, dtype=float)
+    hi = np.asarray(hi, dtype=float)
+    tot = 0.0
+    for i, j, k in itertools.product((0, 1), repeat=3):
+        tot = tot + (-1) ** (3 - i - j - k) * _prism_F((hi if i else lo)[..., 0], (hi if j else lo)[..., 1],
+                                                       (hi if k else lo)[..., 2])
+    return tot
+
+
+def test_prism_integral_closed_form():
+    """The box integral against adaptive cubature (a box off the field point),
+    against the unit cube's integral about its centre reduced to a smooth 2-D
+    integral (int over [0,1]^3 of dV/r = 3/2 int over [0,1]^2 of
+    ds dt / sqrt(1 + s^2 + t^2), by the pyramids where one coordinate is the
+    largest), and far away against the point mass: a cube's first multipole
+    beyond its mass that does not vanish is of order 4, so the difference
+    falls as d^-5."""
+    from scipy import integrate
+    lo, hi = np.array([0.7, -1.3, 2.1]), np.array([1.9, -0.2, 3.0])
+    num = integrate.tplquad(lambda z, y, x: 1.0 / math.sqrt(x * x + y * y + z * z), lo[0], hi[0], lo[1], hi[1],
+                            lo[2], hi[2], epsabs=1e-13, epsrel=1e-12)[0]
+    assert abs(prism_integral(lo, hi) - num) < 1e-11 * num
+    pyr = integrate.dblquad(lambda t, s: 1.0 / math.sqrt(1 + s * s + t * t), 0, 1, 0, 1,
+                            epsabs=1e-14, epsrel=1e-14)[0]
+    # [-1/2, 1/2]^3 = 8 octants, each a quarter of [0, 1]^3 (dV/8, 1/r x 2)
+    assert abs(prism_integral([-0.5] * 3, [0.5] * 3) - 2 * 1.5 * pyr) < 1e-12
+    u = np.array([1.0, 0.37, 0.61])
+    u /= np.linalg.norm(u)
+    c5 = [(prism_integral(d * u - 0.5, d * u + 0.5) - 1.0 / d) * d ** 5 for d in (4.0, 8.0, 16.0)]
+    assert c5[0] > 0 and max(c5) / min(c5) < 1.01, c5
+
+
+def test_full_solve_against_exact_voxel_potential(orc):
+    """Every leaf cell a homogeneous cube: the exact potential at sampled cell
+    centres is the sum of closed-form cube integrals.  The method, by its
+    definition, takes near cells (0 < |o|^2 <= 12) as point masses and omits
+    the cell's own potential; with those terms put back at their exact
+    values, what separates the full solve from the exact potential is the
+    truncation of the multipole expansions and the down-pass alone.  That
+    must stay far below the near-field model error (a dropped or mis-signed
+    coarse-level term would exceed it: a coarse cell's dipole alone is of
+    order 1e-2 of its pair's potential)."""
+    tree = synth.uniform_tree(1, 1.0)          # 16^3 leaf cells, h = 1
+    rng = np.random.default_rng(61)
+    rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
+    L = orc.full_solve(tree, rho)
+    pos, ids = _leaf_cells(tree)
+    dens = rho[ids[:, 0], ids[:, 1]]
+    i_self = prism_integral([-0.5] * 3, [0.5] * 3)
+    trunc, model = [], []
+    for k in rng.choice(len(pos), 64, replace=False):
+        d = pos - pos[k]
+        n2 = np.rint(np.sum(d * d, axis=1)).astype(np.int64)
+        cube = prism_integral(d - 0.5, d + 0.5)
+        exact = -np.sum(dens * cube)                                    # self included
+        near, far = (n2 > 0) & (n2 <= 12), n2 > 12
+        method = -np.sum(dens[far] * cube[far]) - np.sum(dens[near] / np.sqrt(n2[near]))
+        got = L[ids[k, 0], 0, ids[k, 1]]
+        trunc.append(abs(got - method) / abs(exact))
+        model.append(abs(method - (exact + dens[k] * i_self)) / abs(exact))
+    assert max(trunc) < 2e-5, max(trunc)
+    assert max(trunc) < 0.2 * min(model), (max(trunc), min(model))
+    assert max(model) < 5e-4, max(model)
+
+
+@pytest.mark.slow
+def test_polytrope_closed_form_converges(orc):
+    """n = 1 polytrope (G = 1): rho = sin(xi)/xi, xi = pi r / R, whose potential
+    inside is -(4 R^2 / pi)(1 + sin(xi)/xi).  The full solve plus each cell's
+    own potential (closed form) approaches it at second order in h / R, the
+    order of sampling the density at cell centres."""
+    i_self = prism_integral([-0.5] * 3, [0.5] * 3)
+    errs = []
+    for leaf_level, R in ((1, 3.0), (1, 6.0), (2, 12.0)):
+        tree = synth.uniform_tree(leaf_level, 1.0)
+        pos, ids = _leaf_cells(tree)
+        c = np.full(3, 4.0 * 2 ** leaf_level)         # the domain centre, a cell corner
+        r = np.linalg.norm(pos - c, axis=1)
+        xi = np.pi * r / R
+        dens = np.where(r < R, np.sinc(xi / np.pi), 0.0)
+        rho = np.zeros((tree.n, 512))
+        rho[ids[:, 0], ids[:, 1]] = dens
+        L = orc.full_solve(tree, rho)
+        phi = L[ids[:, 0], 0, ids[:, 1]] - dens * i_self
+        exact = np.where(r < R, -(4 * R * R / np.pi) * (1 + np.sinc(xi / np.pi)), -(4 * R ** 3 / np.pi) / r)
+        errs.append(np.max(np.abs(phi - exact) / np.abs(exact)))
+    assert errs[0] / errs[1] > 3 and errs[1] / errs[2] > 3 and errs[2] < 2e-3, errs
 
 
 # ---------------------------------------------------------------------------
