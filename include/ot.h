@@ -65,7 +65,7 @@ typedef enum {
     OT_ECUDA = 3,      /* a CUDA runtime call failed                            */
     OT_ETIMEOUT = 4,   /* a bounded device-side wait ran out                    */
     OT_ESTATE = 5,     /* handle in a bad state (e.g. a latched device fault)   */
-    OT_ENOTSUP = 6,    /* valid request this build does not implement           */
+    OT_ENOTSUP = 6,    /* valid request this library does not implement         */
     OT_EDEVICE = 7     /* a kernel's own bounds check fired                      */
 } ot_status;
 

@@ -25,7 +25,7 @@ __all__ = [
     "Tree", "cell_centres", "single_subgrid", "uniform_tree", "uniform_level",
     "adaptive_tree", "balance_2to1", "polytrope_density", "sample_density",
     "uniform_random_density", "random_moments", "binary_star_field",
-    "choose_probes", "config1", "config2", "config3", "config4_probes",
+    "sparse_lbar", "choose_probes", "config1", "config2", "config3", "config4_probes",
     "config5_step", "STAR_FLOOR",
 ]
 
@@ -214,6 +214,17 @@ def random_moments(tree: Tree, seed: int, positive_mass: bool = True) -> np.ndar
     if positive_mass:
         M[:, 0, :] = rng.uniform(0.5, 1.5, size=(tree.n, NCELL)) * h[:, 0, :] ** 3
     return M
+
+
+def sparse_lbar(tree: Tree, count: int, seed: int):
+    """L-bar [n, 20, 512] that is N(0,1) in all 20 components on ``count``
+    random cells (duplicates merged) and zero elsewhere, and those cells as
+    [k, 2] (node, cell) sorted pairs."""
+    rng = np.random.default_rng(seed)
+    cells = np.unique(np.stack([rng.integers(0, tree.n, count), rng.integers(0, NCELL, count)], 1), axis=0)
+    Lbar = np.zeros((tree.n, 20, NCELL))
+    Lbar[cells[:, 0], :, cells[:, 1]] = rng.standard_normal((len(cells), 20))
+    return Lbar, cells.astype(np.int32)
 
 
 def choose_probes(n_cells: int, count: int, seed: int) -> np.ndarray:

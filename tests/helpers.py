@@ -147,3 +147,42 @@ def spin_torques(M, L):
                         acc = acc + 0.5 * L[:, _k(k, a, b)] * M[:, _k(j, a, b)]
                 tau[:, i] -= eps[i, j, k] * acc
     return tau
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load_golden(name):
+    """Rows of a fixture under tests/golden/ as a float64 array (``#`` lines
+    are the header: workload, recipe, columns)."""
+    return np.loadtxt(os.path.join(GOLDEN, name), comments="#", dtype=np.float64, ndmin=2)
+
+
+def load_golden_constants(name):
+    """``name value`` rows of a fixture as a dict of floats."""
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                key, val = line.split()
+                out[key] = float(val)
+    return out
+
+
+def golden_forward_columns(rows):
+    """(targets [k, 2], L, S [k, 20], Lc, Sc [k, 3]) of forward_small_adaptive.txt."""
+    return (rows[:, :2].astype(np.int32), rows[:, 2:22], rows[:, 22:42], rows[:, 42:45], rows[:, 45:48])
+
+
+def golden_adjoint_columns(rows):
+    """(cells [k, 2], Mbar, SM [k, 20], mbar, Sm [k]) of adjoint_small_adaptive.txt."""
+    return (rows[:, :2].astype(np.int32), rows[:, 2:22], rows[:, 22:42], rows[:, 42], rows[:, 43])
+
+
+def load_golden_script():
+    """tests/golden/make_golden.py as a module (its tree and input recipe)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLDEN, "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
