@@ -141,8 +141,10 @@ typedef struct {
     int max_level;
 } otree;
 
+/* A key that is unique over levels 0..21 for 0 <= x, y, z < 2^l: the level's
+ * own bit 3l above the coordinates' 3l bits. */
 static uint64_t node_key(int l, long x, long y, long z) {
-    return ((uint64_t)l << 60) | ((uint64_t)x << 40) | ((uint64_t)y << 20) | (uint64_t)z;
+    return ((uint64_t)1 << (3 * l)) | ((uint64_t)x << (2 * l)) | ((uint64_t)y << l) | (uint64_t)z;
 }
 
 static otree* key_sort_tree;

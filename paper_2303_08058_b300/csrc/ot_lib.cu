@@ -136,9 +136,12 @@ inline bool xy_complete(int e) {
     return true;
 }
 
+// Locational code of node (l, x, y, z), 0 <= x, y, z < 2^l: a leading 1 at
+// bit 3l marks the level, so the codes of a level lie in [2^3l, 2^(3l+1))
+// and never meet another level's; levels 0..21 fit in 64 bits.
 inline uint64_t node_key(int l, int x, int y, int z) {
-    return (static_cast<uint64_t>(l) << 60) | (static_cast<uint64_t>(x) << 40) |
-           (static_cast<uint64_t>(y) << 20) | static_cast<uint64_t>(z);
+    return (uint64_t{1} << (3 * l)) | (static_cast<uint64_t>(x) << (2 * l)) | (static_cast<uint64_t>(y) << l) |
+           static_cast<uint64_t>(z);
 }
 
 

@@ -22,7 +22,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "Tree", "cell_centres", "single_subgrid", "uniform_tree", "uniform_level",
+    "Tree", "cell_centres", "single_subgrid", "uniform_tree", "uniform_level", "two_level_forest",
     "adaptive_tree", "balance_2to1", "polytrope_density", "sample_density",
     "uniform_random_density", "random_moments", "binary_star_field",
     "sparse_lbar", "choose_probes", "config1", "config2", "config3", "config4_probes",
@@ -116,6 +116,15 @@ def uniform_level(leaf_level: int, h_leaf: float = 1.0) -> Tree:
     s = 2 ** leaf_level
     nodes = {(leaf_level, x, y, z) for z in range(s) for y in range(s) for x in range(s)}
     return _make_tree(nodes, nodes, h_leaf * 2.0 ** leaf_level)
+
+
+def two_level_forest(low: int = 1, high: int = 17, coord=(1, 0, 0)) -> Tree:
+    """Two isolated leaf sub-grids with the same integer coordinates, one on
+    level ``low`` and one on level ``high`` (h = 1 there), and no other node:
+    a tree whose levels differ by 16 puts the two at positions that a level
+    field of 4 bits cannot tell apart."""
+    nodes = {(low, *coord), (high, *coord)}
+    return _make_tree(nodes, nodes, 2.0 ** high)
 
 
 def balance_2to1(nodes: set) -> set:

@@ -875,3 +875,28 @@ def test_angular_term_conserves_angular_momentum(orc, seed):
     t1, _ = torque(True)
     assert t0 > 1e-5 * scale
     assert t1 <= 1e-14 * scale, (t0, t1, scale)
+
+
+@pytest.mark.parametrize("low, high", [(1, 17), (0, 16), (4, 20)])
+def test_levels_sixteen_apart_do_not_alias(orc, low, high):
+    """Node lookups tell levels apart over the whole range 0..20: two leaf
+    sub-grids with the same coordinates on levels 16 apart each see only
+    their own unit mass, as the exact near-field point-mass potential
+    -1 / (|o| h), and nothing from the other."""
+    tree = synth.two_level_forest(low, high, (1, 0, 0) if low > 0 else (0, 0, 0))
+    for k in range(2):
+        c0 = 3 + 8 * 4 + 64 * 2
+        m = np.zeros((tree.n, 512))
+        m[k, c0] = 1.0
+        L = orc.run_pass_grid(tree, "monopole", m=m)["L"]
+        assert np.all(L[1 - k] == 0.0)
+        h = tree.h(tree.level[k])
+        ijk = np.stack(np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij")[::-1], -1).reshape(-1, 3)
+        o = ijk - ijk[c0]
+        r2 = np.sum(o * o, axis=1)
+        seen = L[k, 0] != 0.0
+        near = (r2 > 0) & (r2 <= 12)
+        # near pairs always, far pairs of this level where their parents are
+        # not well separated: each seen cell holds the exact point-mass value
+        assert np.all(seen[near]) and not seen[c0]
+        np.testing.assert_allclose(L[k, 0, seen], -1.0 / (np.sqrt(r2[seen]) * h), rtol=1e-15)
