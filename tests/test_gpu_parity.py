@@ -570,3 +570,36 @@ def test_angular_term_conserves_angular_momentum_gpu(ot, seed):
     T1 = np.linalg.norm(np.sum(np.cross(X, F1) + tau, axis=0))
     assert T0 > 1e-5 * scale
     assert T1 <= 1e-13 * scale, (T0, T1, scale)
+
+
+@pytest.mark.parametrize("cfg", ["config2", "config3", "config5"])
+def test_full_size_random_moment_stress(ot, orc, cfg):
+    """The full-size workloads with stress moments (all 20 components
+    ~ N(0,1) h^(m+3), masses ~ U[0.5, 1.5] h^3) in place of the physical
+    ones: every multipole term and the angular term carry weight at every
+    non-leaf source.  Forward at sampled cells of every level, adjoint
+    for a sparse L-bar against the oracle's transposed sum."""
+    if cfg == "config2":
+        tree = synth.config2()[0]
+    elif cfg == "config3":
+        tree = synth.config3()[0]
+    else:
+        tree = synth.config5_step(0)[0]
+    M = synth.random_moments(tree, seed=91)
+    m = np.ascontiguousarray(M[:, 0, :])
+    g, _, _, L, Lc = gpu_fused(ot, tree, M=M, m=m)
+    levels = np.unique(tree.level)
+    tg = np.concatenate([sample_targets(tree, 24, 92 + int(l), levels=[int(l)]) for l in levels])
+    Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
+    assert np.abs(Lco).max() > 0
+    del L, Lc
+    Lbar, sp = _sparse_lbar(tree, 150, 93)
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    g.check()
+    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=sp)
+    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=sp)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
+    assert_parity(host(mb), mo, Sm, what="mbar")
