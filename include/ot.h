@@ -141,7 +141,10 @@ typedef struct {
  * scratch arena on the current device.  `stream` orders the uploads.
  * Errors: OT_EINVAL (bad description; also a tree that is not 2:1 balanced
  * in the sense the coarse-leaf rule needs: a child of a refined neighbour of
- * a leaf sub-grid that touches the leaf must itself be a leaf), OT_ENOMEM,
+ * a leaf sub-grid that touches the leaf must itself be a leaf; also a
+ * sub-grid whose halo would hold virtual descendants more than 5 levels
+ * below their covering leaf; 2^22 or more sub-grids, or 2^26 or more with
+ * the virtual ones the adjoint adds), OT_ENOMEM,
  * OT_ECUDA, OT_ENOTSUP (stencil_c other than 12, flags other than geometric
  * centres). */
 ot_status ot_grid_create(const ot_grid_desc* desc, void* stream, ot_grid** out);
