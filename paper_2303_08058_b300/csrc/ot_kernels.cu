@@ -1110,20 +1110,33 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             const int2* nb = s_nb[warp];
             const bool xpath = (EMU & 1) ? p.Smf != nullptr && (info & NI_XMASS) : p.Sm != nullptr && (info & NI_XMASS);
             const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-            if constexpr ((EMU & 1) != 0)
-                walk_classes_fwd_df_all(cf, p.L.cf_z, p.L.cf_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, f, it);
-            else
+            const int* cn = p.L.lists + p.L.cn_off;
+            if constexpr ((EMU & 1) != 0) {
+                // one inlined copy of the double-float class walk serves the
+                // far and the near class lists: with a copy for each, the code
+                // of all its paths overflowed the instruction cache on trees
+                // whose leaves take every path
+#pragma unroll 1
+                for (int sgm = 0; sgm < 2; ++sgm) {
+                    int zo[8], xo[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        zo[k] = sgm ? p.L.cn_z[k] : p.L.cf_z[k];
+                        xo[k] = sgm ? p.L.cn_x[k] : p.L.cf_x[k];
+                    }
+                    walk_classes_fwd_df_all(sgm ? cn : cf, zo, xo, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, f,
+                                            it);
+                }
+            } else {
                 walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, p.L.cf_xy, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
+            }
             cf += p.L.cf_z[7];
             walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
                                        t4, f, it);
             cf += p.L.cf_pairs;
             walk_forward<2, false, EMU>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
                                         c, t4, f, it);
-            const int* cn = p.L.lists + p.L.cn_off;
-            if constexpr ((EMU & 1) != 0)
-                walk_classes_fwd_df_all(cn, p.L.cn_z, p.L.cn_x, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, f, it);
-            else
+            if constexpr ((EMU & 1) == 0)
                 walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, p.L.cn_xy, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
             cn += p.L.cn_z[7];
             walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
@@ -1903,12 +1916,28 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
         // by reflection class (see the forward); refined near sources over the near list
         const bool xpath = p.Sbar != nullptr && (info & NI_XMASS);
         const int* cf = p.L.lists + p.L.cf_off + par * p.L.cf_stride;
-        walk_classes_scatter_all<EMU>(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
+        const int* cn = p.L.lists + p.L.cn_off;
+        if constexpr (EMU) {
+            // one inlined copy of the double-float class scatter for the far
+            // and the near class lists (as in the forward)
+#pragma unroll 1
+            for (int sgm = 0; sgm < 2; ++sgm) {
+                int zo[8], xo[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    zo[k] = sgm ? p.L.cn_z[k] : p.L.cf_z[k];
+                    xo[k] = sgm ? p.L.cn_x[k] : p.L.cf_x[k];
+                }
+                walk_classes_scatter_all<EMU>(sgm ? cn : cf, zo, xo, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
+            }
+        } else {
+            walk_classes_scatter_all<EMU>(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
+        }
         cf += p.L.cf_z[7];
         walk_scatter<true, false, EMU>(cf, p.L.cf_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
-        const int* cn = p.L.lists + p.L.cn_off;
-        walk_classes_scatter_all<EMU>(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
+        if constexpr (!EMU)
+            walk_classes_scatter_all<EMU>(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
         walk_scatter<true, false, EMU>(cn + p.L.cn_z[7], p.L.cn_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
         if (__any_sync(0xffffffffu, lane < 27 && (s_nb[lane < 27 ? lane : 0].y & 3) == K_MULTI))
             walk_scatter<true, true, EMU, false>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, lbh,
