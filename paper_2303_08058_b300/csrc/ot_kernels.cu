@@ -1131,16 +1131,29 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
                 walk_classes_fwd_all(cf, p.L.cf_z, p.L.cf_x, p.L.cf_xy, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
             }
             cf += p.L.cf_z[7];
-            walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a, c,
-                                       t4, f, it);
+            cn += p.L.cn_z[7];
+            if constexpr ((EMU & 1) != 0) {
+                // the classes' leftover +-o pairs of both lists through one
+                // inlined copy as well
+#pragma unroll 1
+                for (int sgm = 0; sgm < 2; ++sgm) {
+                    const int np = sgm ? p.L.cn_pairs : p.L.cf_pairs;
+                    walk_forward<2, true, EMU>((sgm ? cn : cf) + ch.lo(np), ch.n(np), false, tx, ty, tz, nb, p, a, c,
+                                               t4, f, it);
+                }
+            } else {
+                walk_forward<2, true, EMU>(cf + ch.lo(p.L.cf_pairs), ch.n(p.L.cf_pairs), false, tx, ty, tz, nb, p, a,
+                                           c, t4, f, it);
+            }
             cf += p.L.cf_pairs;
             walk_forward<2, false, EMU>(cf + ch.lo(p.L.cf_singles), ch.n(p.L.cf_singles), false, tx, ty, tz, nb, p, a,
                                         c, t4, f, it);
-            if constexpr ((EMU & 1) == 0)
-                walk_classes_fwd_all(cn, p.L.cn_z, p.L.cn_x, p.L.cn_xy, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, it);
-            cn += p.L.cn_z[7];
-            walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a, c,
-                                       t4, f, it);
+            if constexpr ((EMU & 1) == 0) {
+                walk_classes_fwd_all(cn - p.L.cn_z[7], p.L.cn_z, p.L.cn_x, p.L.cn_xy, xpath, ch, tx, ty, tz, nb,
+                                     s_sl[warp], p, a, it);
+                walk_forward<2, true, EMU>(cn + ch.lo(p.L.cn_pairs), ch.n(p.L.cn_pairs), false, tx, ty, tz, nb, p, a,
+                                           c, t4, f, it);
+            }
             if (__any_sync(0xffffffffu, lane < 27 && (nb[lane < 27 ? lane : 0].y & 3) == K_MULTI)) {
                 if (MODE & 1) {
                     const int* lf = p.L.lists + par * p.L.far_len;
@@ -1934,11 +1947,18 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
             walk_classes_scatter_all<EMU>(cf, p.L.cf_z, p.L.cf_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
         }
         cf += p.L.cf_z[7];
-        walk_scatter<true, false, EMU>(cf, p.L.cf_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
-        walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
-        if constexpr (!EMU)
+        if constexpr (EMU) {
+#pragma unroll 1
+            for (int sgm = 0; sgm < 2; ++sgm)
+                walk_scatter<true, false, EMU>(sgm ? cn + p.L.cn_z[7] : cf, sgm ? p.L.cn_pairs : p.L.cf_pairs, tx, ty, tz,
+                                               s_nb, p, lb, lbh, lbl, it);
+            walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        } else {
+            walk_scatter<true, false, EMU>(cf, p.L.cf_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+            walk_scatter<false, false, EMU>(cf + p.L.cf_pairs, p.L.cf_singles, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
             walk_classes_scatter_all<EMU>(cn, p.L.cn_z, p.L.cn_x, xpath, tx, ty, tz, s_nb, s_sl, p, lb, lbh, lbl, it);
-        walk_scatter<true, false, EMU>(cn + p.L.cn_z[7], p.L.cn_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+            walk_scatter<true, false, EMU>(cn + p.L.cn_z[7], p.L.cn_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+        }
         if (__any_sync(0xffffffffu, lane < 27 && (s_nb[lane < 27 ? lane : 0].y & 3) == K_MULTI))
             walk_scatter<true, true, EMU, false>(p.L.lists + p.L.near_off, p.L.near_len, tx, ty, tz, s_nb, p, lb, lbh,
                                                  lbl, it);
