@@ -274,9 +274,9 @@ ot_status ot_l2l_com_backward(ot_grid* grid, const double* C, double* Lbar, void
  *   accumulated by two-sums with renormalization -- and the partial sums move
  *   into FP64 accumulators before any of them holds more than 64 products, so
  *   each coefficient stays within ~7e-13 of the sum of |terms| of its FP64
- *   value.  The point-mass classes of leaf targets that read no prebuilt x
- *   table (leaves without x tables, classes on the x = 0 plane) keep the
- *   FP64 class walk, which costs less there.
+ *   value.  Leaf targets without prebuilt x tables (leaves bordering a
+ *   coarser leaf or a refined sub-grid) keep the FP64 class walk for their
+ *   point-mass classes, which costs less there.
  *   Requires point masses m with |m| in [2^-100, 2^100] or m = 0 and
  *   derivative-table values in the same range (true for cell sizes within
  *   2^-10 .. 2^10 of level 0's).

@@ -654,10 +654,14 @@ __device__ __forceinline__ void walk_classes_fwd_df_all(const int* __restrict__ 
             walk_classes_fwd_df_x<Z>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, s_sl, p, acc, c, t4, f, item);
         }
     }
-    // the classes without a prebuilt x stage run the FP64 walk: in
+    // targets without x tables run their classes by the FP64 walk: in
     // double-float their transform and loads cost more issue slots and
     // instruction-cache room than the FP64 pipe time they save
-    walk_classes_fwd<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, item);
+    if (xpath)
+        walk_classes_fwd_df<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, c, t4,
+                               f, item);
+    else
+        walk_classes_fwd<Z>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, item);
     if constexpr (Z < 6)
         walk_classes_fwd_df_all<Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, c, t4, f, item);
 }
