@@ -436,11 +436,12 @@ def run_ours(args, rank, world):
         "adjoint": {"value": pairs_fwd / (adj_ms * 1e-3), "unit": UNIT, "ms": adj_ms},
         "fwd_df64_point_mass": {"value": pairs_fwd / (df_ms * 1e-3), "unit": UNIT, "ms": df_ms,
                                 "note": "point-mass pairs in double-float on the FP32 pipe (within 1e-12 of "
-                                        "the FP64 result); reported beside the FP64 numbers, not as them"},
+                                        "the FP64 result; leaves without x tables keep FP64 point-mass classes); "
+                                        "reported beside the FP64 numbers, not as them"},
         "fwd_df64": {"value": pairs_fwd / (df2_ms * 1e-3), "unit": UNIT, "ms": df2_ms,
                      "note": "point-mass and multipole contractions (with the angular term) in double-float "
-                             "on the FP32 pipe, within 1e-12 of the oracle's sum of |terms|; beside the FP64 "
-                             "numbers, not as them"},
+                             "on the FP32 pipe, within 1e-12 of the oracle's sum of |terms| (leaves without x "
+                             "tables keep FP64 point-mass classes); beside the FP64 numbers, not as them"},
         "adjoint_df64": {"value": pairs_fwd / (dfa_ms * 1e-3), "unit": UNIT, "ms": dfa_ms,
                          "fwd_plus_adjoint": 2 * pairs_fwd / ((df2_ms + dfa_ms) * 1e-3),
                          "note": "the adjoint's multipole gather and point-mass scatter in double-float "
