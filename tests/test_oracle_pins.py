@@ -900,3 +900,18 @@ def test_levels_sixteen_apart_do_not_alias(orc, low, high):
         # not well separated: each seen cell holds the exact point-mass value
         assert np.all(seen[near]) and not seen[c0]
         np.testing.assert_allclose(L[k, 0, seen], -1.0 / (np.sqrt(r2[seen]) * h), rtol=1e-15)
+
+
+def test_massless_targets_have_no_angular_term(orc):
+    """The angular term divides by the target's mass; a target without mass
+    gets exactly zero there (no 0/0) and finite coefficients, while massive
+    targets of the same sub-grid keep a non-zero term."""
+    tree = _single_node_tree()
+    M = synth.random_moments(tree, seed=19)
+    massless = np.zeros(512, dtype=bool)
+    massless[::5] = True
+    M[0, 0, massless] = 0.0
+    r = orc.run_pass_grid(tree, "multipole", M=M)
+    assert np.all(np.isfinite(r["L"])) and np.all(np.isfinite(r["Lc"]))
+    assert np.all(r["Lc"][0][:, massless] == 0.0)
+    assert np.all(np.abs(r["Lc"][0][:, ~massless]).max(axis=0) > 0)
