@@ -69,6 +69,12 @@ def _load():
     lib.oracle_moments_com.restype = I
     lib.oracle_pass_centres.argtypes = [I, P, P, P, ctypes.c_double, P, P, P, I, I, P, P, P, P, P]
     lib.oracle_pass_centres.restype = ctypes.c_longlong
+    lib.oracle_pass_scales.argtypes = [I, P, P, P, ctypes.c_double, P, P, P, I, I, P, P, P, P, P, P, P]
+    lib.oracle_pass_scales.restype = ctypes.c_longlong
+    lib.oracle_pass_adjoint_scales.argtypes = [I, P, P, P, ctypes.c_double, P, I, P, P, P, P, P, I, P]
+    lib.oracle_pass_adjoint_scales.restype = ctypes.c_longlong
+    lib.oracle_D_abs.argtypes = [P, P]
+    lib.oracle_D_abs.restype = None
     lib.oracle_full_solve_com.argtypes = [I, P, P, P, ctypes.c_double, P, I, P, P]
     lib.oracle_full_solve_com.restype = I
     lib.oracle_l2l.argtypes = [P, P, P]
@@ -141,13 +147,15 @@ def moments_com(tree, rho):
     return M, C
 
 
-def run_pass(tree, pass_kind: str, M=None, m=None, targets=None, centres=None):
+def run_pass(tree, pass_kind: str, M=None, m=None, targets=None, centres=None, with_sd: bool = True):
     """Evaluate one pass for the listed targets ([k, 2] node, cell) or all cells.
 
     Returns dict(L=[k,20], S=[k,20], npairs=int) plus Lc, Sc ([k,3]) for the
     multipole pass.  ``pass_kind`` is "multipole" (sources = non-leaf cells,
     uses M) or "monopole" (sources = leaf cells and virtual descendants of
-    coarser leaves, uses m)."""
+    coarser leaves, uses m).  S sums the |terms| of each coefficient; with
+    ``with_sd`` SD (and SDc) sums them with every derivative's own terms
+    expanded (see ``D_abs``)."""
     level, coord, leaf = _tree_args(tree)
     kind = {"multipole": 1, "monopole": 2}[pass_kind]
     if targets is None:
@@ -166,12 +174,18 @@ def run_pass(tree, pass_kind: str, M=None, m=None, targets=None, centres=None):
     S = np.zeros((nt, NCOMP))
     Lc = np.zeros((nt, 3))
     Sc = np.zeros((nt, 3))
+    SD = np.zeros((nt, NCOMP)) if with_sd else None
+    SDc = np.zeros((nt, 3)) if with_sd and kind == 1 else None
     Cv = np.ascontiguousarray(centres, dtype=np.float64) if centres is not None else None
-    npairs = _load().oracle_pass_centres(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Mv), _p(mv), _p(Cv),
-                                         kind, nt, _p(tg), _p(L), _p(Lc), _p(S), _p(Sc))
+    npairs = _load().oracle_pass_scales(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Mv), _p(mv), _p(Cv),
+                                        kind, nt, _p(tg), _p(L), _p(Lc), _p(S), _p(Sc), _p(SD), _p(SDc))
     out = dict(L=L, S=S, npairs=int(npairs))
+    if with_sd:
+        out["SD"] = SD
     if kind == 1:
         out.update(Lc=Lc, Sc=Sc)
+        if with_sd:
+            out["SDc"] = SDc
     return out
 
 
@@ -180,33 +194,49 @@ def run_pass_grid(tree, pass_kind, M=None, m=None, centres=None):
     r = run_pass(tree, pass_kind, M=M, m=m, centres=centres)
     n = tree.n
     out = dict(L=r["L"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(),
-               S=r["S"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(), npairs=r["npairs"])
+               S=r["S"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(),
+               SD=r["SD"].reshape(n, NCELL, NCOMP).transpose(0, 2, 1).copy(), npairs=r["npairs"])
     if "Lc" in r:
         out["Lc"] = r["Lc"].reshape(n, NCELL, 3).transpose(0, 2, 1).copy()
         out["Sc"] = r["Sc"].reshape(n, NCELL, 3).transpose(0, 2, 1).copy()
+        out["SDc"] = r["SDc"].reshape(n, NCELL, 3).transpose(0, 2, 1).copy()
     return out
 
 
-def pass_adjoint(tree, pass_kind: str, Lbar, with_s: bool = False, targets=None, centres=None):
+def pass_adjoint(tree, pass_kind: str, Lbar, with_s: bool = False, targets=None, centres=None,
+                 with_sd: bool = False):
     """Transposed sum of a pass: Mbar [n,20,512] (multipole) or mbar [n,512];
-    with ``with_s`` also the matching sum of |terms|.  ``targets`` ([k, 2]
-    node, cell) restricts the scatter to those target cells; ``centres``
-    ([n, 3, 512]) are expansion centres held fixed (default geometric)."""
+    with ``with_s`` also the matching sum of |terms| S, and with ``with_sd``
+    after it the same sums with every derivative's terms expanded (SD).
+    ``targets`` ([k, 2] node, cell) restricts the scatter to those target
+    cells; ``centres`` ([n, 3, 512]) are expansion centres held fixed
+    (default geometric)."""
     level, coord, leaf = _tree_args(tree)
     kind = {"multipole": 1, "monopole": 2}[pass_kind]
     Lbar = np.ascontiguousarray(Lbar, dtype=np.float64)
     Mbar = np.zeros((tree.n, NCOMP, NCELL))
     mbar = np.zeros((tree.n, NCELL))
     S = np.zeros_like(Mbar if kind == 1 else mbar)
+    SD = np.zeros_like(S) if with_sd else None
     tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int32).reshape(-1, 2)
     Cv = None if centres is None else np.ascontiguousarray(centres, dtype=np.float64)
-    npairs = _load().oracle_pass_adjoint_centres(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Cv), kind,
-                                                 _p(Lbar), _p(Mbar), _p(mbar), _p(S),
-                                                 0 if tg is None else tg.shape[0], _p(tg))
+    npairs = _load().oracle_pass_adjoint_scales(tree.n, _p(level), _p(coord), _p(leaf), tree.h0, _p(Cv), kind,
+                                                _p(Lbar), _p(Mbar), _p(mbar), _p(S), _p(SD),
+                                                0 if tg is None else tg.shape[0], _p(tg))
     out = Mbar if kind == 1 else mbar
     if with_s == "pairs":
         return out, int(npairs)
+    if with_s and with_sd:
+        return out, S, SD
     return (out, S) if with_s else out
+
+
+def D_abs(R) -> np.ndarray:
+    """[35] magnitude sums of the terms of each derivative of G = -1/r at R
+    (the pairing sum of ``D`` with every term in absolute value)."""
+    out = np.zeros(35)
+    _load().oracle_D_abs(_p(np.ascontiguousarray(R, dtype=np.float64)), _p(out))
+    return out
 
 
 def l2l(Lp, d) -> np.ndarray:

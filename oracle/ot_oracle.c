@@ -126,6 +126,24 @@ void oracle_D(const double* R, double* D) {
         D[c] = pairing_sum(comp_idx[c], comp_rank[c], 0, 0u, 0, 1.0, R, g);
 }
 
+/* Magnitudes of every derivative's terms: the same pairing sum with each
+ * term |g_{k - #pairs}| * prod |R| * prod delta taken in absolute value.
+ * The passes' S sums treat each derivative as one exact number; a
+ * derivative is itself a sum of these terms, and any way of evaluating it
+ * rounds by a few units of their magnitude sum, which is the only non-zero
+ * scale where the terms cancel to exactly zero.  The passes accumulate
+ * SD = sum over the contraction's terms of |coefficient * moment| * Dabs. */
+void oracle_D_abs(const double* R, double* Dabs) {
+    build_tables();
+    double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    double r = sqrt(r2);
+    double g[5], Ra[3] = {fabs(R[0]), fabs(R[1]), fabs(R[2])};
+    g[0] = 1.0 / r;
+    for (int k = 1; k <= 4; k++) g[k] = (2.0 * k - 1.0) * g[k - 1] / r2;
+    for (int c = 0; c < NCOMP4; c++)
+        Dabs[c] = pairing_sum(comp_idx[c], comp_rank[c], 0, 0u, 0, 1.0, Ra, g);
+}
+
 /* ------------------------------------------------------------------------ */
 /* tree lookup                                                               */
 /* ------------------------------------------------------------------------ */
@@ -433,9 +451,12 @@ static void refined_pairs(const otree* t, int l, const long* g, const long* q, i
 }
 
 /* One target cell of one pass.  pass 1: multipole sources (M), pass 2: point
- * masses (m).  Writes L[20] (+ Lc[3] for pass 1), S = sum of |terms|. */
+ * masses (m).  Writes L[20] (+ Lc[3] for pass 1), S = sum of |terms|, and,
+ * where SD (SDc) is not NULL, the same sums with each derivative's terms
+ * expanded (oracle_D_abs). */
 static long long target_pass(const otree* t, int pass, const double* M, const double* m, const double* C,
-                             int T, int a, double* L, double* Lc, double* S, double* Sc) {
+                             int T, int a, double* L, double* Lc, double* S, double* Sc, double* SD,
+                             double* SDc) {
     int l = t->level[T];
     double h = t->h0 / pow(2.0, l);
     long g[3] = {8L * t->coord[3 * T] + (a & 7), 8L * t->coord[3 * T + 1] + ((a >> 3) & 7),
@@ -443,6 +464,9 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
     int leafT = t->is_leaf[T];
     for (int c = 0; c < NCOMP; c++) { L[c] = 0.0; S[c] = 0.0; }
     for (int i = 0; i < 3; i++) { Lc[i] = 0.0; Sc[i] = 0.0; }
+    if (SD) for (int c = 0; c < NCOMP; c++) SD[c] = 0.0;
+    if (SDc) for (int i = 0; i < 3; i++) SDc[i] = 0.0;
+    double Da[NCOMP4];
     double mA = 0.0;
     if (pass == 1) mA = M[((size_t)T * NCOMP + 0) * NCELL + a];
     long long npairs = 0;
@@ -471,10 +495,12 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                         for (int cv = 0; cv < 8; cv++) {
                             double D[NCOMP4];
                             oracle_D(Rc[cs][cv], D);
+                            if (SD) oracle_D_abs(Rc[cs][cv], Da);
                             for (int J = 0; J < NCOMP; J++) {
                                 double term = 0.125 * ms * D[J];
                                 L[J] += term;
                                 S[J] += fabs(term);
+                                if (SD) SD[J] += fabs(0.125 * ms) * Da[J];
                             }
                         }
                     }
@@ -488,6 +514,7 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                 }
                 double D[NCOMP4];
                 oracle_D(R, D);
+                if (SD || SDc) oracle_D_abs(R, Da);
                 npairs++;
                 if (pass == 2) {
                     double mass = m[(size_t)B * NCELL + cb] * scale;
@@ -495,6 +522,7 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                         double term = mass * D[J];
                         L[J] += term;
                         S[J] += fabs(term);
+                        if (SD) SD[J] += fabs(mass) * Da[J];
                     }
                     continue;
                 }
@@ -511,9 +539,11 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                             for (int s = 0; s < mm; s++) { it[s] = v % 3; v /= 3; }
                             for (int s = 0; s < nJ; s++) full[s] = comp_idx[J][s];
                             for (int s = 0; s < mm; s++) full[nJ + s] = it[s];
-                            double term = cm * MB[(size_t)comp_of(it, mm) * NCELL] * D[comp_of(full, nJ + mm)];
+                            double cmM = cm * MB[(size_t)comp_of(it, mm) * NCELL];
+                            double term = cmM * D[comp_of(full, nJ + mm)];
                             L[J] += term;
                             S[J] += fabs(term);
+                            if (SD) SD[J] += fabs(cmM) * Da[comp_of(full, nJ + mm)];
                         }
                     }
                 }
@@ -533,6 +563,9 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
                              * the target octupole: count both in the magnitude sum */
                             Sc[i] += fabs((1.0 / 6.0) * MB[(size_t)c3 * NCELL] * d4) +
                                      fabs((1.0 / 6.0) * (mB / mA) * M3A * d4);
+                            if (SDc)
+                                SDc[i] += (fabs((1.0 / 6.0) * MB[(size_t)c3 * NCELL]) +
+                                           fabs((1.0 / 6.0) * (mB / mA) * M3A)) * Da[comp_of(full, 4)];
                         }
                     }
                 }
@@ -542,14 +575,16 @@ static long long target_pass(const otree* t, int pass, const double* M, const do
 
 /* targets: [nt][2] (node, cell) or NULL for every cell of every node in order.
  * L, S: [nt][20]; Lc, Sc: [nt][3] (pass 1 only; may be NULL). */
-long long oracle_pass_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
-                              const double* M, const double* m, const double* C, int pass, int nt,
-                              const int* targets, double* L, double* Lc, double* S, double* Sc);
+long long oracle_pass_scales(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
+                             const double* M, const double* m, const double* C, int pass, int nt,
+                             const int* targets, double* L, double* Lc, double* S, double* Sc, double* SD,
+                             double* SDc);
 
 long long oracle_pass(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
                       const double* M, const double* m, int pass, int nt, const int* targets,
                       double* L, double* Lc, double* S, double* Sc) {
-    return oracle_pass_centres(n, level, coord, is_leaf, h0, M, m, NULL, pass, nt, targets, L, Lc, S, Sc);
+    return oracle_pass_scales(n, level, coord, is_leaf, h0, M, m, NULL, pass, nt, targets, L, Lc, S, Sc, NULL,
+                              NULL);
 }
 
 /* The same with expansion centres C [n][3][512] (NULL: geometric): the pair
@@ -557,6 +592,15 @@ long long oracle_pass(int n, const int* level, const int* coord, const uint8_t* 
 long long oracle_pass_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
                               const double* M, const double* m, const double* C, int pass, int nt,
                               const int* targets, double* L, double* Lc, double* S, double* Sc) {
+    return oracle_pass_scales(n, level, coord, is_leaf, h0, M, m, C, pass, nt, targets, L, Lc, S, Sc, NULL, NULL);
+}
+
+/* The same, with the expanded-derivative magnitude sums SD [nt][20] and SDc
+ * [nt][3] too (either may be NULL). */
+long long oracle_pass_scales(int n, const int* level, const int* coord, const uint8_t* is_leaf, double h0,
+                             const double* M, const double* m, const double* C, int pass, int nt,
+                             const int* targets, double* L, double* Lc, double* S, double* Sc, double* SD,
+                             double* SDc) {
     otree t;
     tree_init(&t, n, level, coord, is_leaf, h0);
     if (!targets) nt = n * NCELL;
@@ -565,10 +609,12 @@ long long oracle_pass_centres(int n, const int* level, const int* coord, const u
     for (int k = 0; k < nt; k++) {
         int T = targets ? targets[2 * k] : k / NCELL;
         int a = targets ? targets[2 * k + 1] : k % NCELL;
-        double lc[3], sc[3];
-        total += target_pass(&t, pass, M, m, C, T, a, L + (size_t)k * NCOMP, lc, S + (size_t)k * NCOMP, sc);
+        double lc[3], sc[3], sdc[3];
+        total += target_pass(&t, pass, M, m, C, T, a, L + (size_t)k * NCOMP, lc, S + (size_t)k * NCOMP, sc,
+                             SD ? SD + (size_t)k * NCOMP : NULL, SDc ? sdc : NULL);
         if (Lc) for (int i = 0; i < 3; i++) Lc[(size_t)k * 3 + i] = lc[i];
         if (Sc) for (int i = 0; i < 3; i++) Sc[(size_t)k * 3 + i] = sc[i];
+        if (SDc) for (int i = 0; i < 3; i++) SDc[(size_t)k * 3 + i] = sdc[i];
     }
     tree_free(&t);
     return total;
@@ -592,6 +638,9 @@ int oracle_pass_adjoint(int n, const int* level, const int* coord, const uint8_t
 long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf,
                                       double h0, const double* C, int pass, const double* Lbar, double* Mbar,
                                       double* mbar, double* Sbar, int nt, const int* targets);
+long long oracle_pass_adjoint_scales(int n, const int* level, const int* coord, const uint8_t* is_leaf,
+                                     double h0, const double* C, int pass, const double* Lbar, double* Mbar,
+                                     double* mbar, double* Sbar, double* SDbar, int nt, const int* targets);
 
 /* Same, scattering only from the listed target cells ([nt][2] node, cell);
  * returns the number of pairs walked. */
@@ -607,6 +656,15 @@ long long oracle_pass_adjoint_targets(int n, const int* level, const int* coord,
 long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord, const uint8_t* is_leaf,
                                       double h0, const double* C, int pass, const double* Lbar, double* Mbar,
                                       double* mbar, double* Sbar, int nt, const int* targets) {
+    return oracle_pass_adjoint_scales(n, level, coord, is_leaf, h0, C, pass, Lbar, Mbar, mbar, Sbar, NULL, nt,
+                                      targets);
+}
+
+/* The same, with SDbar (the shape of Sbar, may be NULL): the magnitude sums
+ * with each derivative's terms expanded (oracle_D_abs). */
+long long oracle_pass_adjoint_scales(int n, const int* level, const int* coord, const uint8_t* is_leaf,
+                                     double h0, const double* C, int pass, const double* Lbar, double* Mbar,
+                                     double* mbar, double* Sbar, double* SDbar, int nt, const int* targets) {
     otree t;
     long long npairs = 0;
     tree_init(&t, n, level, coord, is_leaf, h0);
@@ -614,6 +672,8 @@ long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord,
     if (pass == 1) memset(Mbar, 0, sizeof(double) * nout);
     else memset(mbar, 0, sizeof(double) * nout);
     if (Sbar) memset(Sbar, 0, sizeof(double) * nout);
+    if (SDbar) memset(SDbar, 0, sizeof(double) * nout);
+    double Da[NCOMP4];
     long total = targets ? nt : (long)n * NCELL;
     for (long k = 0; k < total; k++) {
         int T = targets ? targets[2 * k] : (int)(k / NCELL);
@@ -644,17 +704,20 @@ long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord,
                             refined_pairs(&t, l, g, q, cs_, Rc);
                             npairs += 1;   /* one stencil pair */
                             for (int cs = 0; cs < 8; cs++) {
-                                double acc = 0.0, sacc = 0.0;
+                                double acc = 0.0, sacc = 0.0, sdacc = 0.0;
                                 for (int cv = 0; cv < 8; cv++) {
                                     double D[NCOMP4];
                                     oracle_D(Rc[cs][cv], D);
+                                    if (SDbar) oracle_D_abs(Rc[cs][cv], Da);
                                     for (int J = 0; J < NCOMP; J++) {
                                         acc += 0.125 * LA[(size_t)J * NCELL] * D[J];
                                         sacc += fabs(0.125 * LA[(size_t)J * NCELL] * D[J]);
+                                        if (SDbar) sdacc += fabs(0.125 * LA[(size_t)J * NCELL]) * Da[J];
                                     }
                                 }
                                 mbar[(size_t)cs_[cs][0] * NCELL + cs_[cs][1]] += acc;
                                 if (Sbar) Sbar[(size_t)cs_[cs][0] * NCELL + cs_[cs][1]] += sacc;
+                                if (SDbar) SDbar[(size_t)cs_[cs][0] * NCELL + cs_[cs][1]] += sdacc;
                             }
                             continue;
                         }
@@ -667,14 +730,17 @@ long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord,
                         }
                         double D[NCOMP4];
                         oracle_D(R, D);
+                        if (SDbar) oracle_D_abs(R, Da);
                         if (pass == 2) {
-                            double acc = 0.0, sacc = 0.0;
+                            double acc = 0.0, sacc = 0.0, sdacc = 0.0;
                             for (int J = 0; J < NCOMP; J++) {
                                 acc += LA[(size_t)J * NCELL] * D[J];
                                 sacc += fabs(LA[(size_t)J * NCELL] * D[J]);
+                                if (SDbar) sdacc += fabs(LA[(size_t)J * NCELL]) * Da[J];
                             }
                             mbar[(size_t)B * NCELL + cb] += scale * acc;
                             if (Sbar) Sbar[(size_t)B * NCELL + cb] += scale * sacc;
+                            if (SDbar) SDbar[(size_t)B * NCELL + cb] += scale * sdacc;
                             continue;
                         }
                         double* MB = Mbar + (size_t)B * NCOMP * NCELL + cb;
@@ -693,7 +759,9 @@ long long oracle_pass_adjoint_centres(int n, const int* level, const int* coord,
                                     for (int s = 0; s < mm; s++) full[nJ + s] = it[s];
                                     double term = cm * lbar * D[comp_of(full, nJ + mm)];
                                     MB[(size_t)comp_of(it, mm) * NCELL] += term;
-                                    if (Sbar) Sbar[(size_t)B * NCOMP * NCELL + (size_t)comp_of(it, mm) * NCELL + cb] += fabs(term);
+                                    const size_t si = (size_t)B * NCOMP * NCELL + (size_t)comp_of(it, mm) * NCELL + cb;
+                                    if (Sbar) Sbar[si] += fabs(term);
+                                    if (SDbar) SDbar[si] += fabs(cm * lbar) * Da[comp_of(full, nJ + mm)];
                                 }
                             }
                         }

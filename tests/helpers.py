@@ -5,32 +5,79 @@ import numpy as np
 
 TOL = 1e-12   # per-coefficient bound: |gpu - oracle| <= TOL * sum_pairs |term|
 
+# The oracle's S treats every derivative value as one exact number, but a
+# derivative is itself a sum of terms (a pairing sum of g_k(r) times
+# coordinates), and any evaluation of it -- the oracle's pairing sum, the
+# library's table -- rounds by a few units of those terms' magnitude sum.
+# Where the terms cancel exactly (d^xyy G at (-6,-3,0), d^yyz G at (0,2,4))
+# that rounding is all that is left, and S of a coefficient fed by such
+# pairs alone is zero or rounding noise.  The oracle's SD counts each
+# contraction term with its derivative's terms expanded; the bar allows
+# DERIV_TOL (45 units of roundoff) of SD on top of TOL of S.
+DERIV_TOL = 1e-14
 
-RANK_BLOCKS = [slice(0, 1), slice(1, 4), slice(4, 10), slice(10, 20)]
+
+def eff(S, SD):
+    """The magnitude sum the bar divides by, in units of TOL: S + SD *
+    DERIV_TOL / TOL."""
+    return np.asarray(S, dtype=np.float64) + (DERIV_TOL / TOL) * np.asarray(SD, dtype=np.float64)
 
 
-def rank_block_sums(S, axis=1):
-    """S summed over the components of the same order (0 | 1-3 | 4-9 | 10-19;
-    a 3-component axis is one block).  The kernels derive the z-z trace
-    components of each order from the others (the derivative tensors are
-    harmonic), so the rounding error of a coefficient is bounded by the
-    magnitude sums of its order block, not of its own terms alone."""
+def fwd_scale(r, lc=False):
+    """eff() of a forward pass result of the oracle (its L, or with ``lc`` its Lc)."""
+    return eff(r["Sc"], r["SDc"]) if lc else eff(r["S"], r["SD"])
+
+
+def adjoint_with_scale(orc, *args, **kw):
+    """The oracle's transposed sum and the eff() of its magnitude sums."""
+    out, S, SD = orc.pass_adjoint(*args, with_s=True, with_sd=True, **kw)
+    return out, eff(S, SD)
+
+
+# The kernels accumulate 16 of the 20 coefficients of an expansion and derive
+# the other four from them, because every derivative tensor of G = -1/r is
+# harmonic (a zero trace over any index pair).  A derived coefficient is a
+# different formula, not a different summation order, so its rounding is
+# bounded by the magnitude sums of the coefficients it is computed from, not
+# by its own.  For each derived component (storage index): the (source index,
+# weight) pairs of its formula.
+#   Taylor coefficients L:      zz = -(xx + yy), xzz = -(xxx + xyy),
+#                               yzz = -(xxy + yyy), zzz = -(xxz + yyz)
+#   moment adjoints Mbar (the gradient with respect to the raw moments, whose
+#   unique components carry multiplicities 1, 3, 3, 6):
+#                               zz = -(xx + yy), xzz = -(3 xxx + xyy),
+#                               yzz = -(xxy + 3 yyy), zzz = -(xxz + yyz) / 3
+DERIVED = {
+    "L": {9: ((4, 1.0), (7, 1.0)), 15: ((10, 1.0), (13, 1.0)),
+          18: ((11, 1.0), (16, 1.0)), 19: ((12, 1.0), (17, 1.0))},
+    "Mbar": {9: ((4, 1.0), (7, 1.0)), 15: ((10, 3.0), (13, 1.0)),
+             18: ((11, 1.0), (16, 3.0)), 19: ((12, 1.0 / 3.0), (17, 1.0 / 3.0))},
+}
+
+
+def coefficient_scale(S, kind=None, axis=1):
+    """The per-coefficient denominator of the parity bar: the oracle's own sum
+    of |terms| S for every accumulated coefficient; for a derived one (kind
+    "L" or "Mbar", 20 components along ``axis``) the weighted S of the
+    coefficients its formula reads.  kind None (Lc, mbar, masses): S itself."""
     S = np.asarray(S, dtype=np.float64)
-    blocks = RANK_BLOCKS if S.shape[axis] == 20 else [slice(0, S.shape[axis])]
-    out = np.empty_like(S)
-    for sl in blocks:
-        idx = [slice(None)] * S.ndim
-        idx[axis] = sl
-        out[tuple(idx)] = S[tuple(idx)].sum(axis=axis, keepdims=True)
+    if kind is None:
+        return S
+    assert S.shape[axis] == 20, (kind, S.shape)
+    out = S.copy()
+    Sm = np.moveaxis(S, axis, 0)
+    om = np.moveaxis(out, axis, 0)
+    for q, srcs in DERIVED[kind].items():
+        om[q] = sum(w * Sm[k] for k, w in srcs)
     return out
 
 
-def parity_ratio(got, ref, S, block_axis=None):
-    """max over entries of |got - ref| / S (entries with S == 0 must match
-    exactly); with ``block_axis`` S is summed over each order block first."""
-    got, ref, S = (np.asarray(a, dtype=np.float64) for a in (got, ref, S))
-    if block_axis is not None:
-        S = rank_block_sums(S, block_axis)
+def parity_ratio(got, ref, S, kind=None, axis=1):
+    """max over entries of |got - ref| / scale, scale the per-coefficient
+    denominator of ``coefficient_scale`` (entries with scale 0 must match
+    exactly)."""
+    got, ref = (np.asarray(a, dtype=np.float64) for a in (got, ref))
+    S = coefficient_scale(S, kind, axis)
     err = np.abs(got - ref)
     zero = S == 0
     if np.any(err[zero] != 0):
@@ -40,8 +87,14 @@ def parity_ratio(got, ref, S, block_axis=None):
     return float(np.max(r)) if r.size else 0.0
 
 
-def assert_parity(got, ref, S, tol=TOL, what="", block_axis=None):
-    r = parity_ratio(got, ref, S, block_axis)
+def own_s_ratio(got, ref, S):
+    """The same ratio with every coefficient's own S (derived ones included),
+    reported beside the bar, not asserted."""
+    return parity_ratio(got, ref, S, None)
+
+
+def assert_parity(got, ref, S, tol=TOL, what="", kind=None, axis=1):
+    r = parity_ratio(got, ref, S, kind, axis)
     assert r <= tol, f"{what}: max |gpu - oracle| / S = {r:.3e} > {tol:.0e}"
     return r
 
@@ -61,11 +114,14 @@ def sample_targets(tree, count, seed, levels=None):
     return np.stack([pick, cells], axis=1).astype(np.int32)
 
 
-def oracle_full_solve_at(orc, tree, M, m, cells):
+def oracle_full_solve_at(orc, tree, M, m, cells, kind="L"):
     """The oracle's full multilevel solve at the given leaf cells only: each
     cell's own passes plus its ancestors' passes, shifted down level by level
     (the local-expansion shift between geometric cell centres); S follows the
-    same chain with |d|.  Returns (L, S) [k, 20]."""
+    same chain with |d|, starting from each pass's per-coefficient scale
+    (``coefficient_scale`` of kind "L": the passes derive four coefficients,
+    the shift then moves all 20; kind None chains the oracle's own S).
+    Returns (L, S) [k, 20]; compare with kind None."""
     idx = tree.index()
     chains, need = [], {}
     for node, cell in cells:
@@ -83,7 +139,8 @@ def oracle_full_solve_at(orc, tree, M, m, cells):
     r1 = orc.run_pass(tree, "multipole", M=M, targets=tg)
     r2 = orc.run_pass(tree, "monopole", m=m, targets=tg)
     Lp = {k: r1["L"][i] + r2["L"][i] for i, k in enumerate(need)}
-    Sp = {k: r1["S"][i] + r2["S"][i] for i, k in enumerate(need)}
+    S12 = fwd_scale(r1) + fwd_scale(r2) if kind is not None else r1["S"] + r2["S"]
+    Sp = {k: coefficient_scale(S12[i], kind, axis=0) for i, k in enumerate(need)}
     L, S = [], []
     for chain in chains:
         nd, cc, gl, l = chain[0]
@@ -96,6 +153,37 @@ def oracle_full_solve_at(orc, tree, M, m, cells):
         L.append(acc)
         S.append(sacc)
     return np.array(L), np.array(S)
+
+
+def full_solve_scale(orc, tree, M, m, centres=None, kind="L"):
+    """[n, 20, 512] per-coefficient scale of the full multilevel solve at
+    every cell: each cell's pass scale (the oracle's S of both passes through
+    ``coefficient_scale`` of kind "L") plus its parent cell's full scale
+    shifted down by |d|, d the offset between the two expansion centres
+    (geometric, or ``centres`` [n, 3, 512]); kind None chains the oracle's
+    own S.  Compare with kind None."""
+    r1 = orc.run_pass_grid(tree, "multipole", M=M, centres=centres)
+    r2 = orc.run_pass_grid(tree, "monopole", m=m, centres=centres)
+    S = coefficient_scale(fwd_scale(r1) + fwd_scale(r2) if kind is not None else r1["S"] + r2["S"], kind, axis=1)
+    idx = tree.index()
+    cell = np.arange(512)
+    local = np.stack([cell % 8, (cell // 8) % 8, cell // 64], 1)
+    for node in np.argsort(tree.level, kind="stable"):
+        lv = int(tree.level[node])
+        if lv == 0:
+            continue
+        g = 8 * tree.coord[node] + local
+        gp = g >> 1
+        parent = idx[(lv - 1, *(tree.coord[node] // 2))]
+        pcell = (gp % 8) @ np.array([1, 8, 64])
+        if centres is None:
+            h = tree.h0 / 2 ** lv
+            d = (g + 0.5) * h - (gp + 0.5) * (2 * h)
+        else:
+            d = centres[node].T - centres[parent][:, pcell].T
+        for c in range(512):
+            S[node, :, c] += orc.l2l(S[parent, :, pcell[c]], np.abs(d[c]))
+    return S
 
 
 # stored components: 0; x y z; xx xy xz yy yz zz; xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz

@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import synth
-from helpers import assert_parity, oracle_threads, sample_targets
+from helpers import adjoint_with_scale, assert_parity, full_solve_scale, fwd_scale, oracle_threads, sample_targets
 
 pytestmark = pytest.mark.gpu
 
@@ -69,7 +69,7 @@ def oracle_com_inputs(orc, tree, rho):
 def oracle_com_passes(orc, tree, M, m, C, tg):
     r1 = orc.run_pass(tree, "multipole", M=M, targets=tg, centres=C)
     r2 = orc.run_pass(tree, "monopole", m=m, targets=tg, centres=C)
-    return r1["L"] + r2["L"], r1["S"] + r2["S"], r1["Lc"], r1["Sc"]
+    return r1["L"] + r2["L"], fwd_scale(r1) + fwd_scale(r2), r1["Lc"], fwd_scale(r1, lc=True)
 
 
 def geometric_centres(tree):
@@ -121,8 +121,8 @@ def test_com_passes_all_cells(ot, orc, which):
     g.check()
     tg = all_targets(tree)
     Lo, S, Lco, Sc = oracle_com_passes(orc, tree, M, m, C, tg)
-    assert_parity(at_targets(host(L), tg), Lo, S, what="L", block_axis=1)
-    assert_parity(at_targets(host(Lc), tg), Lco, Sc, what="Lc", block_axis=1)
+    assert_parity(at_targets(host(L), tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(host(Lc), tg), Lco, Sc, what="Lc")
 
 
 @pytest.mark.parametrize("seed", [93, 94])
@@ -140,8 +140,8 @@ def test_com_random_moments_random_centres(ot, orc, seed):
     L2, Lc2 = g.multipole(dev(M), centres=dev(C))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "multipole", M=M, centres=C)
-    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
-    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
+    assert_parity(host(L), r["L"], fwd_scale(r), what="L", kind="L")
+    assert_parity(host(Lc), r["Lc"], fwd_scale(r, lc=True), what="Lc")
     assert np.max(np.abs(r["Lc"])) > 0
     assert torch.equal(L, L2) and torch.equal(Lc, Lc2)
 
@@ -158,10 +158,10 @@ def test_com_monopole_only_and_split_passes(ot, orc):
     L, Lc = g.interactions_com(dev(M), dev(m), dev(C))
     torch.cuda.synchronize()
     r2 = orc.run_pass_grid(tree, "monopole", m=m, centres=C)
-    assert_parity(host(L2), r2["L"], r2["S"], what="L (point masses)", block_axis=1)
+    assert_parity(host(L2), r2["L"], fwd_scale(r2), what="L (point masses)", kind="L")
     r1 = orc.run_pass_grid(tree, "multipole", M=M, centres=C)
-    S = r1["S"] + r2["S"]
-    assert_parity(host(L1) + host(L2), host(L), S, what="split vs fused", block_axis=1)
+    S = fwd_scale(r1) + fwd_scale(r2)
+    assert_parity(host(L1) + host(L2), host(L), S, what="split vs fused", kind="L")
     assert torch.equal(Lc, Lc1)
 
 
@@ -181,8 +181,8 @@ def test_com_path_with_geometric_centres_matches_table_path(ot, orc):
     r1 = orc.run_pass(tree, "multipole", M=M, targets=tg)
     r2 = orc.run_pass(tree, "monopole", m=m, targets=tg)
     for L, Lc in ((Lcom, Lccom), (Ltab, Lctab)):
-        assert_parity(at_targets(host(L), tg), r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
-        assert_parity(at_targets(host(Lc), tg), r1["Lc"], r1["Sc"], what="Lc", block_axis=1)
+        assert_parity(at_targets(host(L), tg), r1["L"] + r2["L"], fwd_scale(r1) + fwd_scale(r2), what="L", kind="L")
+        assert_parity(at_targets(host(Lc), tg), r1["Lc"], fwd_scale(r1, lc=True), what="Lc")
 
 
 # ---------------------------------------------------------------------------
@@ -211,9 +211,9 @@ def test_com_adjoint_matches_oracle(ot, orc, which, deterministic):
     Mb, mb = g.backward_com(dev(Lbar), dev(Cg))
     torch.cuda.synchronize()
     g.check()
-    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg, centres=C)
-    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg, centres=C)
-    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=tg, centres=C)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg, centres=C)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
     assert_parity(host(mb), mo, Sm, what="mbar")
     assert np.max(np.abs(mo)) > 0
 
@@ -279,8 +279,10 @@ def test_com_full_solve_matches_oracle(ot, orc, which):
     g = ot.OTGrid.from_tree(tree)
     L, _, _ = g.solve_com(dev(rho))
     torch.cuda.synchronize()
-    Lo, So = orc.full_solve(tree, rho, with_s=True, com=True)
-    assert_parity(host(L), Lo, So, what="L", block_axis=1)
+    Lo = orc.full_solve(tree, rho, com=True)
+    Mo, Co = orc.moments_com(tree, rho)
+    So = full_solve_scale(orc, tree, Mo, np.ascontiguousarray(Mo[:, 0, :]), centres=Co)
+    assert_parity(host(L), Lo, So, what="L")
 
 
 # ---------------------------------------------------------------------------
@@ -297,8 +299,8 @@ def test_com_full_size_sampled(ot, orc, cfg):
     g.check()
     tg = np.concatenate([sample_targets(tree, 100, 104), sample_targets(tree, 40, 105, levels=[0, 1, 2])])
     Lo, S, Lco, Sc = oracle_com_passes(orc, tree, M, m, C, tg)
-    assert_parity(at_targets(host(L), tg), Lo, S, what="L", block_axis=1)
-    assert_parity(at_targets(host(Lc), tg), Lco, Sc, what="Lc", block_axis=1)
+    assert_parity(at_targets(host(L), tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(host(Lc), tg), Lco, Sc, what="Lc")
     # the GPU's own moments and centres on the same tree
     Mg, _, Cg = g.moments_com(dev(rho))
     torch.cuda.synchronize()

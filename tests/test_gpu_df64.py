@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import synth
-from helpers import assert_parity, oracle_threads, sample_targets
+from helpers import adjoint_with_scale, assert_parity, fwd_scale, oracle_threads, sample_targets
 
 pytestmark = pytest.mark.gpu
 
@@ -69,8 +69,8 @@ def test_df64_all_cells(ot, orc, which, prec):
     r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
     r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
     got = host(L)[tg[:, 0], :, tg[:, 1]]
-    assert_parity(got, r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
-    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], r1["Sc"], what="Lc", block_axis=1)
+    assert_parity(got, r1["L"] + r2["L"], fwd_scale(r1) + fwd_scale(r2), what="L", kind="L")
+    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], fwd_scale(r1, lc=True), what="Lc")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -90,7 +90,7 @@ def test_df64_full_size_sampled(ot, orc, cfg, prec):
     tg = sample_targets(tree, 200, 82)
     r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
     r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
-    assert_parity(Ldf[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
+    assert_parity(Ldf[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], fwd_scale(r1) + fwd_scale(r2), what="L", kind="L")
     # every cell: double-float within 1e-12 of the FP64 path relative to the
     # coefficient-order block magnitude of the FP64 result
     scale = np.max(np.abs(L64), axis=(0, 2), keepdims=True)
@@ -110,8 +110,8 @@ def test_df64_random_moments_every_term(ot, orc, seed):
     torch.cuda.synchronize()
     g.check()
     r = orc.run_pass_grid(tree, "multipole", M=M)
-    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
-    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
+    assert_parity(host(L), r["L"], fwd_scale(r), what="L", kind="L")
+    assert_parity(host(Lc), r["Lc"], fwd_scale(r, lc=True), what="Lc")
 
 
 def test_df64_multipole_pass_differs_from_fp64_by_rounding_only(ot):
@@ -155,10 +155,10 @@ def test_df64_adjoint_matches_oracle(ot, orc, which):
     Mb1, _ = g.backward(dev(Lbar), want=(True, False))      # the multipole half alone
     torch.cuda.synchronize()
     g.check()
-    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg)
-    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
-    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
-    assert_parity(host(Mb1), Mo, SM, what="Mbar (alone)", block_axis=1)
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=tg)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
+    assert_parity(host(Mb1), Mo, SM, what="Mbar (alone)", kind="Mbar")
     assert_parity(host(mb), mo, Sm, what="mbar")
 
 

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import synth
-from helpers import assert_parity, oracle_threads
+from helpers import assert_parity, full_solve_scale, oracle_threads
 
 pytestmark = pytest.mark.gpu
 
@@ -48,8 +48,10 @@ def test_full_solve_matches_oracle(ot, orc, which):
     g = ot.OTGrid.from_tree(tree)
     L, _ = g.solve(dev(rho))
     torch.cuda.synchronize()
-    Lo, So = orc.full_solve(tree, rho, with_s=True)
-    assert_parity(host(L), Lo, So, what="L", block_axis=1)
+    Lo = orc.full_solve(tree, rho)
+    Mo = orc.moments(tree, rho)
+    So = full_solve_scale(orc, tree, Mo, np.ascontiguousarray(Mo[:, 0, :]))
+    assert_parity(host(L), Lo, So, what="L")
 
 
 def test_l2l_adjoint_dot_product(ot):

@@ -40,8 +40,8 @@ def test_gpu_forward_matches_golden(case):
     torch.cuda.synchronize()
     g.check()
     Lg, Lcg = Lg.cpu().numpy(), Lcg.cpu().numpy()
-    assert_parity(Lg[tg[:, 0], :, tg[:, 1]], L, S, what="L", block_axis=1)
-    assert_parity(Lcg[tg[:, 0], :, tg[:, 1]], Lc, Sc, what="Lc", block_axis=1)
+    assert_parity(Lg[tg[:, 0], :, tg[:, 1]], L, S, what="L", kind="L")
+    assert_parity(Lcg[tg[:, 0], :, tg[:, 1]], Lc, Sc, what="Lc")
 
 
 @pytest.mark.parametrize("deterministic", [False, True])
@@ -54,5 +54,5 @@ def test_gpu_adjoint_matches_golden(case, deterministic):
     torch.cuda.synchronize()
     g.check()
     Mbg, mbg = Mbg.cpu().numpy(), mbg.cpu().numpy()
-    assert_parity(Mbg[cells[:, 0], :, cells[:, 1]], Mb, SM, what="Mbar", block_axis=1)
+    assert_parity(Mbg[cells[:, 0], :, cells[:, 1]], Mb, SM, what="Mbar", kind="Mbar")
     assert_parity(mbg[cells[:, 0], cells[:, 1]], mb, Sm, what="mbar")

@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import synth
-from helpers import assert_parity, oracle_threads, sample_targets
+from helpers import adjoint_with_scale, assert_parity, fwd_scale, oracle_threads, sample_targets
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +65,7 @@ def gpu_fused(ot, tree, rho=None, M=None, m=None, schedule=None, orc=None):
 def oracle_both(orc, tree, M, m, targets=None):
     r1 = orc.run_pass(tree, "multipole", M=M, targets=targets)
     r2 = orc.run_pass(tree, "monopole", m=m, targets=targets)
-    return r1["L"] + r2["L"], r1["S"] + r2["S"], r1["Lc"], r1["Sc"], r1["npairs"], r2["npairs"]
+    return r1["L"] + r2["L"], fwd_scale(r1) + fwd_scale(r2), r1["Lc"], fwd_scale(r1, lc=True), r1["npairs"], r2["npairs"]
 
 
 def at_targets(L, targets):
@@ -124,8 +124,8 @@ def test_config1_multipole_all_cells(ot, orc):
     L, Lc = g.multipole(dev(M))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "multipole", M=M)
-    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
-    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
+    assert_parity(host(L), r["L"], fwd_scale(r), what="L", kind="L")
+    assert_parity(host(Lc), r["Lc"], fwd_scale(r, lc=True), what="Lc")
     assert g.info()["pairs_multipole"] == r["npairs"]
 
 
@@ -139,8 +139,8 @@ def test_single_subgrid_random_moments_all_terms(ot, orc, seed):
     L, Lc = g.multipole(dev(M))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "multipole", M=M)
-    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
-    assert_parity(host(Lc), r["Lc"], r["Sc"], what="Lc", block_axis=1)
+    assert_parity(host(L), r["L"], fwd_scale(r), what="L", kind="L")
+    assert_parity(host(Lc), r["Lc"], fwd_scale(r, lc=True), what="Lc")
     assert np.max(np.abs(r["Lc"])) > 0
 
 
@@ -153,7 +153,7 @@ def test_root_leaf_subgrid_root_and_near_stencils(ot, orc):
     L = g.monopole(dev(m))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "monopole", m=m)
-    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
+    assert_parity(host(L), r["L"], fwd_scale(r), what="L", kind="L")
     assert g.info()["pairs_monopole"] == r["npairs"] == 512 * 511
 
 
@@ -165,7 +165,7 @@ def test_monopole_uniform_level(ot, orc):
     L = g.monopole(dev(m))
     torch.cuda.synchronize()
     r = orc.run_pass_grid(tree, "monopole", m=m)
-    assert_parity(host(L), r["L"], r["S"], what="L", block_axis=1)
+    assert_parity(host(L), r["L"], fwd_scale(r), what="L", kind="L")
     assert g.info()["pairs_monopole"] == r["npairs"]
 
 
@@ -175,8 +175,8 @@ def test_fused_uniform_tree_with_coarse_levels(ot, orc):
     g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
     tg = all_targets(tree)
     Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
     info = g.info()
     assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
 
@@ -198,8 +198,8 @@ def test_fused_adaptive_virtual_descendants(ot, orc):
     assert info["pairs_virtual"] > 0 and info["n_virtual"] > 0
     tg = all_targets(tree)
     Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
     assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
 
 
@@ -265,8 +265,8 @@ def test_adjoint_dense_single_subgrid(ot, orc):
     g = ot.OTGrid.from_tree(tree)
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
-    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True)
-    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
     assert np.all(host(mb) == 0)
 
 
@@ -281,9 +281,9 @@ def test_adjoint_matches_oracle_transposed_sum(ot, orc, which, deterministic):
     g.set_deterministic(deterministic)
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
-    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=tg)
-    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
-    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=tg)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
     assert_parity(host(mb), mo, Sm, what="mbar")
     assert np.max(np.abs(mo)) > 0
 
@@ -365,11 +365,40 @@ def test_config2_full_size_sampled(ot, orc):
     g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
     tg = np.concatenate([sample_targets(tree, 96, 61, levels=[3]), sample_targets(tree, 48, 62, levels=[0, 1, 2])])
     Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
     # every leaf cell: potential negative, the field points inward (towards the star centre)
     leaf = tree.level == 3
     assert np.all(L[leaf, 0, :] < 0)
+
+
+def test_config2_every_coarse_cell(ot, orc):
+    """Every cell of levels 0-2 of the 64^3 workload (73 sub-grids, 37,376
+    cells: the root's walk, every chunked item, every angular-term lane)
+    against the oracle, forward; and the multipole adjoint at every one of
+    those cells for an L-bar dense on levels 0-1 and on 512 sampled level-2
+    cells (a coarse source is seen by targets of its own level only, so its
+    M-bar is the complete transposed sum of that L-bar; the oracle's scatter
+    is serial, hence the sample)."""
+    tree, rho = synth.config2()
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
+    coarse = np.nonzero(tree.level <= 2)[0]
+    assert len(coarse) == 73
+    tg = np.stack(np.meshgrid(coarse, np.arange(512), indexing="ij"), -1).reshape(-1, 2).astype(np.int32)
+    Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    del L, Lc
+    Lbar = np.zeros((tree.n, 20, 512))
+    rng = np.random.default_rng(66)
+    lvl2 = tg[tree.level[tg[:, 0]] == 2]
+    sp = np.concatenate([tg[tree.level[tg[:, 0]] <= 1], lvl2[rng.choice(len(lvl2), 512, replace=False)]])
+    Lbar[sp[:, 0], :, sp[:, 1]] = rng.standard_normal((len(sp), 20))
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=sp)
+    assert_parity(host(Mb)[coarse], Mo[coarse], SM[coarse], what="Mbar", kind="Mbar")
+    assert np.all(host(mb) == 0)
 
 
 def test_config2_adjoint_full_size_dot_product(ot):
@@ -398,7 +427,7 @@ def test_config2_adjoint_sampled_against_oracle(ot, orc):
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
     tg = np.stack([leaf_nodes[probes // 512], probes % 512], 1).astype(np.int32)
-    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg)
     assert_parity(host(mb), mo, Sm, what="mbar")
     assert np.all(host(Mb) == 0)    # L-bar only on leaf cells: no multipole source sees it
 
@@ -414,8 +443,8 @@ def test_adaptive_workloads_sampled(ot, orc, cfg):
     assert info["pairs_virtual"] > 0
     tg = sample_targets(tree, 160, 65)
     Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
 
 
 # ---------------------------------------------------------------------------
@@ -591,15 +620,15 @@ def test_full_size_random_moment_stress(ot, orc, cfg):
     levels = np.unique(tree.level)
     tg = np.concatenate([sample_targets(tree, 24, 92 + int(l), levels=[int(l)]) for l in levels])
     Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
-    assert_parity(at_targets(L, tg), Lo, S, what="L", block_axis=1)
-    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc", block_axis=1)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
     assert np.abs(Lco).max() > 0
     del L, Lc
     Lbar, sp = _sparse_lbar(tree, 150, 93)
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
     g.check()
-    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=sp)
-    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=sp)
-    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=sp)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=sp)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
     assert_parity(host(mb), mo, Sm, what="mbar")

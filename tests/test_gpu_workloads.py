@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import synth
-from helpers import assert_parity, oracle_full_solve_at, oracle_threads, sample_targets
+from helpers import adjoint_with_scale, assert_parity, fwd_scale, oracle_full_solve_at, oracle_threads, sample_targets
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +58,7 @@ def test_config4_probe_loss_gradient(ot, orc):
     Lbar = np.zeros((tree.n, 20, 512))
     Lbar[pn, 0, pc] = 2.0 * host(L)[pn, 0, pc]
     tg = np.stack([pn, pc], 1).astype(np.int32)
-    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=tg)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg)
     assert_parity(grad[leaf_nodes], mo[leaf_nodes], Sm[leaf_nodes], what="d loss / d rho")
     assert np.all(grad[tree.level < 3] == 0)
 
@@ -103,8 +103,8 @@ def test_config5_binary_star_steps(ot, orc, step):
     tg = sample_targets(tree, 120, 100 + step)
     r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
     r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
-    assert_parity(host(L)[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], r1["S"] + r2["S"], what="L", block_axis=1)
-    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], r1["Sc"], what="Lc", block_axis=1)
+    assert_parity(host(L)[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], fwd_scale(r1) + fwd_scale(r2), what="L", kind="L")
+    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], fwd_scale(r1, lc=True), what="Lc")
 
     rng = np.random.default_rng(200 + step)
     sp = np.unique(sample_targets(tree, 200, 300 + step), axis=0)
@@ -112,9 +112,9 @@ def test_config5_binary_star_steps(ot, orc, step):
     Lbar[sp[:, 0], :, sp[:, 1]] = rng.standard_normal((len(sp), 20))
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
-    Mo, SM = orc.pass_adjoint(tree, "multipole", Lbar, with_s=True, targets=sp)
-    mo, Sm = orc.pass_adjoint(tree, "monopole", Lbar, with_s=True, targets=sp)
-    assert_parity(host(Mb), Mo, SM, what="Mbar", block_axis=1)
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=sp)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=sp)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
     assert_parity(host(mb), mo, Sm, what="mbar")
 
     Lbar_d = dev(rng.standard_normal((tree.n, 20, 512)))
@@ -187,7 +187,7 @@ def test_config4_full_solve_probe_loss_gradient(ot, orc):
 
     Mo = orc.moments(tree, rho_h)
     Lo, So = oracle_full_solve_at(orc, tree, Mo, np.ascontiguousarray(Mo[:, 0, :]), list(zip(pn, pc)))
-    assert_parity(host(L)[pn, :, pc], Lo, So, what="full-solve L at the probes", block_axis=1)
+    assert_parity(host(L)[pn, :, pc], Lo, So, what="full-solve L at the probes")
 
     rng = np.random.default_rng(6)
     inside = np.argwhere(rho_h[leaf_nodes] > 1e-3)

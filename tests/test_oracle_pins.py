@@ -81,6 +81,42 @@ def test_D_matches_sympy(orc, R):
         assert abs(got[c] - exact) <= 1e-14 * max(abs(exact), scale), (R, e, got[c], exact)
 
 
+@pytest.mark.parametrize("R", [(0, 2, 4), (-6, -3, 0), (3, -1, 2), (0.7, -2.5, 1.3)])
+def test_D_abs_matches_sympy_term_magnitudes(orc, R):
+    """The magnitude sums of the derivatives' terms (the scale SD of the
+    parity bar): write G = f(u), u = x^2 + y^2 + z^2; sympy expands d^K f(u)
+    into sum_j f^(j)(u) Q_j(x, y, z), whose terms for one j share a sign, so
+    the magnitude sum is sum_j |f^(j)(u)| Q_j(|x|, |y|, |z|) (Q_j has
+    non-negative coefficients).  Where the derivative cancels exactly, the
+    magnitude sum stays of the derivative's order of size."""
+    x, y, z, u = sympy.symbols("x y z u", real=True)
+    f = sympy.Function("f")
+    F = -u ** sympy.Rational(-1, 2)
+    expr0 = f(x ** 2 + y ** 2 + z ** 2)
+    Ra = [abs(sympy.nsimplify(v)) for v in R]
+    u0 = sum(sympy.nsimplify(v) ** 2 for v in R)
+    got = orc.D_abs(np.array(R, dtype=float))
+    for c, e in enumerate(EXPS):
+        d = sympy.expand(sympy.diff(expr0, x, e[0], y, e[1], z, e[2]))
+        total = sympy.Integer(0)
+        for j in range(RANK[c] + 1):
+            fj = f(x ** 2 + y ** 2 + z ** 2) if j == 0 else sympy.Subs(sympy.Derivative(f(u), (u, j)), u,
+                                                                       x ** 2 + y ** 2 + z ** 2)
+            Q = sympy.expand(d.coeff(fj))
+            poly = sympy.Poly(Q, x, y, z) if Q != 0 else None
+            if poly is None:
+                continue
+            assert all(co >= 0 for co in poly.coeffs()), (e, j, Q)
+            fval = sympy.diff(F, u, j).subs(u, u0)
+            total += abs(fval) * poly.as_expr().subs({x: Ra[0], y: Ra[1], z: Ra[2]})
+        exact = float(sympy.N(total, 40))
+        assert abs(got[c] - exact) <= 1e-14 * exact, (R, e, got[c], exact)
+        assert got[c] >= abs(orc.D(np.array(R, dtype=float))[c]) * (1 - 1e-15)
+    if tuple(R) == (0, 2, 4):
+        c = EXPS.index((0, 2, 1))
+        assert orc.D(np.array(R, dtype=float))[c] == 0.0 and got[c] > 0.1 / 20 ** 2
+
+
 # ---------------------------------------------------------------------------
 # moments
 # ---------------------------------------------------------------------------
@@ -808,17 +844,31 @@ def test_mirror_symmetry(orc):
 def test_sampled_full_solve_helper_matches_whole_grid(orc):
     """The tests' per-cell full solve (own passes plus the ancestors' passes
     shifted down) reproduces the oracle's whole-grid full solve."""
-    from helpers import oracle_full_solve_at
+    from helpers import full_solve_scale, oracle_full_solve_at
     tree = synth.uniform_tree(1, 1.0)
     rng = np.random.default_rng(28)
     rho = rng.uniform(0.5, 1.5, size=(tree.n, 512))
     L, S = orc.full_solve(tree, rho, with_s=True)
     M = orc.moments(tree, rho)
     cells = [(int(i), int(c)) for i in np.nonzero(tree.is_leaf)[0][:3] for c in (0, 77, 511)]
-    Lc, Sc = oracle_full_solve_at(orc, tree, M, np.ascontiguousarray(M[:, 0, :]), cells)
+    Lc, Sc = oracle_full_solve_at(orc, tree, M, np.ascontiguousarray(M[:, 0, :]), cells, kind=None)
     for k, (i, c) in enumerate(cells):
         np.testing.assert_allclose(Lc[k], L[i, :, c], rtol=0, atol=1e-13 * np.max(S[i, :, c]))
         np.testing.assert_allclose(Sc[k], S[i, :, c], rtol=1e-12)
+    # the whole-grid chain of the same scale
+    Sg = full_solve_scale(orc, tree, M, np.ascontiguousarray(M[:, 0, :]), kind=None)
+    np.testing.assert_allclose(Sg, S, rtol=1e-12)
+    # the bar's scale: at the root level, the accumulated coefficients'
+    # S + 1e-2 SD of both passes, the derived ones the sums they are formed from
+    Sd = full_solve_scale(orc, tree, M, np.ascontiguousarray(M[:, 0, :]))
+    r1 = orc.run_pass_grid(tree, "multipole", M=M)
+    r2 = orc.run_pass_grid(tree, "monopole", m=np.ascontiguousarray(M[:, 0, :]))
+    Se = r1["S"] + r2["S"] + 1e-2 * (r1["SD"] + r2["SD"])
+    root = np.nonzero(tree.level == 0)[0]
+    acc = [q for q in range(20) if q not in (9, 15, 18, 19)]
+    np.testing.assert_allclose(Sd[root][:, acc], Se[root][:, acc], rtol=1e-12)
+    np.testing.assert_allclose(Sd[root][:, 9], Se[root][:, 4] + Se[root][:, 7], rtol=1e-12)
+    assert np.all(Sd[:, acc] >= S[:, acc] * (1 - 1e-12))
 
 
 _EPS = np.zeros((3, 3, 3))
