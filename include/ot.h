@@ -320,19 +320,25 @@ ot_status ot_autotune(ot_grid* grid, const double* M, const double* m, double* L
  * call the kernels -- code recording a CUDA graph by stream capture (an
  * allocation is not a stream operation and breaks the capture), real-time
  * loops that forbid allocator calls after set-up, hosts whose device memory
- * is owned by another allocator.  It computes exactly what
- * ot_multipole_interactions computes (same kernels, same summation order;
- * M, L, Lc as there, centres implied NULL), but keeps its scratch (the
- * pre-scaled, reduced source moments, 64 KiB per sub-grid) in one static
- * device array of OT_NOALLOC_SCRATCH_BYTES instead of the grid's arena, and
- * calls no cudaMalloc, cudaFree or allocating library routine.
+ * is owned by another allocator.  It computes the multipole pass of
+ * ot_multipole_interactions (M, L, Lc as there, centres implied NULL) with
+ * the same pair set, derivative table and contractions, but not the same
+ * instruction path: it runs in FP64 whatever ot_set_precision chose, on the
+ * persistent schedule, without the prebuilt x-butterfly tables and without
+ * splitting long work items into chunks, so its result equals
+ * ot_multipole_interactions' within the parity bar (1e-12 of each
+ * coefficient's sum of |terms|), not bit for bit.  Its scratch (the
+ * pre-scaled, reduced source moments, 64 KiB per sub-grid) lives in one
+ * static device array of OT_NOALLOC_SCRATCH_BYTES instead of the grid's
+ * arena, and it calls no cudaMalloc, cudaFree or allocating library routine.
  *   - Limit: the non-leaf sub-grids' node indices must span at most
  *     OT_NOALLOC_SCRATCH_BYTES / 64 KiB = 256 consecutive indices; larger
  *     grids are rejected with OT_EINVAL and a message.
- *   - The array is set up on the first call on each device (one
- *     cudaGetSymbolAddress with that device current); make that first call
- *     before any stream capture.  Every device that loads the library holds
- *     the array until the process exits.
+ *   - The array's device address is looked up (cudaGetSymbolAddress, with
+ *     the device current) on the first call on each device, and again only
+ *     if that device's context was replaced; make that first call before any
+ *     stream capture.  Every device that loads the library holds the array
+ *     until the process exits.
  *   - All calls share the one array, which keeps the last call's contents;
  *     each call writes every scratch entry it reads before reading it, so
  *     nothing needs clearing.  Calls whose GPU work overlaps (other streams,
