@@ -135,6 +135,9 @@ typedef struct {
     int64_t fp64_ops_fwd_multi;    /* the part of fp64_ops_fwd in the multipole pass (the
                                       launch of ot_multipole_interactions) */
     int64_t ops_fwd_multi;         /* the part of ops_fwd in the multipole pass */
+    int64_t fp64_ops_adj_multi;    /* the part of fp64_ops_adj in the multipole gather (the
+                                      adjoint's first launch; the rest is the point masses) */
+    int64_t ops_adj_multi;         /* the part of ops_adj in the multipole gather */
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the
@@ -358,7 +361,10 @@ ot_status ot_multipole_interactions_noalloc(ot_grid* grid, const double* M, doub
  *   1: a cudaLaunchHostFunc callback (the host-task analogue),
  *   2: an event polled by the launching thread between submissions and
  *      afterwards (the event-polling analogue),
- *   3: one batched persistent launch over all sub-grids, one event.
+ *   3: one batched persistent launch over all sub-grids, one event,
+ *   4: an event per launch, polled with cudaEventQuery by a pool of 4 host
+ *      threads draining a shared queue while the launching thread keeps
+ *      submitting (event polling by the scheduler's worker threads).
  * L, Lc are overwritten with the forward result.  Outputs: wall time from
  * the first submission to the last completion, mean and max latency from a
  * sub-grid's submission to its completion being seen on the host.  Host
@@ -377,12 +383,21 @@ ot_status ot_completion_study(ot_grid* grid, const double* M, const double* m, d
  * OT_EDEVICE with the failing work item in ot_last_error(). */
 ot_status ot_grid_check(ot_grid* grid, void* stream);
 
-/* FP64 FMA throughput probe: `blocks` x 256 threads each run `iters` rounds of
- * 16 independent FMAs -- variant 0: chains a = a*b + c; variant 1: 16
- * accumulators a_j += s * x_j (the contraction's operand pattern).
- * out [blocks*256] receives the results (keeps them live).  Time it with
- * events; 2 * blocks * 256 * iters * 16 flops per launch. */
+/* FP64 FMA throughput probe: `blocks` x 256 threads each run `iters` rounds
+ * of independent FMAs -- variant 0: 16 chains a = a*b + c; variant 1: 16
+ * accumulators a_j += s * x_j; variant 2: the point-mass contraction's
+ * pattern, 64 rows of 16 values staged in shared memory, each row times one
+ * of 4 per-thread values accumulated into 16 sums (1024 FMAs per round; the
+ * only variant whose operands arrive from shared memory, as the
+ * interaction kernels' do).  FMAs per round: 16, 16, 1024.  out
+ * [blocks*256] receives the results (keeps them live).  Time it with events. */
 ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, int32_t variant, void* stream);
+
+/* Kernels this library has launched in this process so far, across all
+ * grids and threads: each kernel launched directly counts once, each kernel
+ * inside a replayed CUDA graph once per replay (recording a graph counts
+ * nothing).  Reads a counter, no device work.  OT_EINVAL if out is NULL. */
+ot_status ot_launch_count(int64_t* out);
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* ot_last_error(void);

@@ -6,7 +6,8 @@ binding: ``OTGrid`` (grid handle and every ABI call) and ``FMMInteractions``
 """
 from ._lib import (EXPORTS, OT_PREC_DF64, OT_PREC_DF64_POINT_MASS, OT_PREC_FP64,  # noqa: F401
                    OT_SCHED_PER_SUBGRID, OT_SCHED_PERSISTENT, OTError, load)
-from .fmm import FMMInteractions, OTGrid, fp64_fma_probe, potential_and_gradient  # noqa: F401
+from .fmm import (FP64_PROBE_FMA_PER_ROUND, FMMInteractions, OTGrid, fp64_fma_probe, launch_count,  # noqa: F401
+                  potential_and_gradient)
 
-__all__ = ["OTGrid", "FMMInteractions", "potential_and_gradient", "fp64_fma_probe", "OTError", "load",
+__all__ = ["OTGrid", "FMMInteractions", "potential_and_gradient", "fp64_fma_probe", "FP64_PROBE_FMA_PER_ROUND", "launch_count", "OTError", "load",
            "OT_SCHED_PERSISTENT", "OT_SCHED_PER_SUBGRID", "OT_PREC_FP64", "OT_PREC_DF64_POINT_MASS", "OT_PREC_DF64", "EXPORTS"]

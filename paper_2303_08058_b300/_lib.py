@@ -24,7 +24,7 @@ EXPORTS = ["ot_grid_create", "ot_grid_destroy", "ot_grid_info", "ot_moments", "o
            "ot_fp64_fma_probe", "ot_multipole_interactions_noalloc", "ot_l2l", "ot_l2l_backward",
            "ot_set_deterministic", "ot_set_precision", "ot_completion_study",
            "ot_moments_com", "ot_interactions_com", "ot_interactions_backward_com", "ot_l2l_com",
-           "ot_l2l_com_backward", "ot_last_error"]
+           "ot_l2l_com_backward", "ot_launch_count", "ot_last_error"]
 
 
 class OTError(RuntimeError):
@@ -53,7 +53,8 @@ class GridInfo(ctypes.Structure):
                 ("pairs_refined", ctypes.c_int64), ("pairs_padded_fwd", ctypes.c_int64),
                 ("chunked_subgrids", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("fp64_ops_fwd", ctypes.c_int64), ("fp64_ops_adj", ctypes.c_int64),
-                ("fp64_ops_fwd_multi", ctypes.c_int64), ("ops_fwd_multi", ctypes.c_int64)]
+                ("fp64_ops_fwd_multi", ctypes.c_int64), ("ops_fwd_multi", ctypes.c_int64),
+                ("fp64_ops_adj_multi", ctypes.c_int64), ("ops_adj_multi", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -101,6 +102,7 @@ def load():
         "ot_interactions_backward_com": [P, P, P, P, P, P],
         "ot_l2l_com": [P, P, P, P],
         "ot_l2l_com_backward": [P, P, P, P],
+        "ot_launch_count": [ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -264,4 +264,13 @@ cudaError_t launch_split_moments(const double* Mhat, float2* Mf, const int* node
 cudaError_t launch_split_masses(const double* m, float2* mf, size_t n, cudaStream_t s);
 int adjoint_max_blocks_per_sm(int mode, int wpb);
 
+// Kernel launches issued by the launchers above: a process-wide total and
+// the calling thread's own count.  A launcher counts its kernel when the
+// launch succeeds; a graph capture takes its kernels back out
+// (launch_count_adjust with minus the thread's count over the capture) and
+// every replay of the graph adds them again.
+long long launch_count_total();
+long long launch_count_thread();
+void launch_count_adjust(long long delta);
+
 }  // namespace otk

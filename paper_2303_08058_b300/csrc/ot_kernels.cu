@@ -18,6 +18,8 @@
 // A warp owns 32 target cells of one parity class of one sub-grid, so the
 // stencil offset, its table row and the neighbour lookup are warp-uniform;
 // integer address arithmetic runs on the integer pipes.
+#include <atomic>
+
 #include "ot_internal.h"
 
 namespace otk {
@@ -3012,7 +3014,8 @@ __global__ void __launch_bounds__(256) adjoint_com_kernel(const AdjParams p) {
 // ---------------------------------------------------------------------------
 
 // variant 0: 16 chains a = a * b + c; variant 1: 16 accumulators a += s * x[j]
-// (the contraction's pattern: shared scalar, distinct multiplier per chain)
+// (shared scalar, distinct multiplier per chain).  Streams of FP64 operations
+// on register operands alone keep the FP64 pipe about 84 % busy.
 template <int VARIANT>
 __global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, int iters) {
     constexpr int K = 16;
@@ -3033,9 +3036,71 @@ __global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, int iters)
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// variant 2, the point-mass contraction's pattern: 64 rows of 16 derivative
+// values staged in shared memory (128-bit loads), each row's 16 values times
+// one of 4 per-thread source values accumulated into 16 sums -- 1024 DFMAs
+// per iteration with operands arriving from shared memory, which keeps the
+// FP64 pipe busy at its full issue rate.
+__global__ void __launch_bounds__(256) fp64_probe_contraction_kernel(double* out, int iters) {
+    __shared__ double2 rows[64][8];
+    for (int t = threadIdx.x; t < 64 * 8; t += blockDim.x) {
+        const int r = t >> 3, c = t & 7;
+        const double v = 1e-3 * (1.0 + 0.01 * r + 0.001 * c);
+        rows[r][c] = make_double2(v, 0.5 * v);
+    }
+    __syncthreads();
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    double src[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double lo = 1.0 + 1e-3 * (threadIdx.x + q), hi = 1.0 + 1e-3 * (threadIdx.x + q + 4);
+        src[q] = (q & 1) ? hi - lo : lo + hi;
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll 1
+        for (int o = 0; o < 64; o += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const double2 d = rows[o + q][c];
+                    acc[2 * c] = fma(src[q], d.x, acc[2 * c]);
+                    acc[2 * c + 1] = fma(src[q], d.y, acc[2 * c + 1]);
+                }
+            }
+        }
+    }
+    double z = 0.0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) z += acc[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = z;
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+
+namespace {
+std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;
+
+inline cudaError_t counted(cudaError_t e) {
+    if (e == cudaSuccess) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        ++t_launches;
+    }
+    return e;
+}
+}  // namespace
+
+long long launch_count_total() { return g_launches.load(std::memory_order_relaxed); }
+long long launch_count_thread() { return t_launches; }
+void launch_count_adjust(long long delta) {
+    g_launches.fetch_add(delta, std::memory_order_relaxed);
+    t_launches += delta;
+}
 
 cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
@@ -3054,7 +3119,7 @@ cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wp
         case 15: forward_kernel<3, 3><<<grid, block, 0, s>>>(p, per); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 // reduced moments of the listed nodes as double-float pairs (hi, lo)
@@ -3072,7 +3137,7 @@ cudaError_t launch_split_moments(const double* Mhat, float2* Mf, const int* node
     if (n_list == 0) return cudaSuccess;
     const long long n = 1LL * n_list * NRED * NCELL;
     split_moments_kernel<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(Mhat, Mf, nodes, n_list);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 __global__ void split_masses_kernel(const double* __restrict__ m, float2* __restrict__ mf, size_t n) {
@@ -3086,7 +3151,7 @@ __global__ void split_masses_kernel(const double* __restrict__ m, float2* __rest
 cudaError_t launch_split_masses(const double* m, float2* mf, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     split_masses_kernel<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(m, mf, n);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wpb, int grid, cudaStream_t s) {
@@ -3099,7 +3164,7 @@ cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wp
             case 4: adjoint_kernel<4, true><<<grid, block, 0, s>>>(p, per); break;
             default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
+        return counted(cudaGetLastError());
     }
     switch (mode) {
         case 1: adjoint_kernel<1><<<grid, block, 0, s>>>(p, per); break;
@@ -3107,13 +3172,13 @@ cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wp
         case 4: adjoint_kernel<4><<<grid, block, 0, s>>>(p, per); break;
         default: adjoint_kernel<3><<<grid, block, 0, s>>>(p, per); break;
     }
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_scatter_adjoint(const ScatParams& p, bool persistent, int wpb, int grid, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
     scatter_adjoint_kernel<<<grid, 32 * wpb, 0, s>>>(p, persistent ? 1 : 0);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 int scatter_max_blocks_per_sm(int wpb) {
@@ -3278,7 +3343,7 @@ __global__ void xbutterfly_masses_kernel(const int* __restrict__ nodes, int n_li
 cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s) {
     if (p.n_list == 0) return cudaSuccess;
     prescale_moments_kernel<<<blocks_for(1LL * p.n_list * NCELL, 256), 256, 0, s>>>(p);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* nbr, const double* Mhat, int n_nodes,
@@ -3286,7 +3351,7 @@ cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* 
     if (n_list == 0) return cudaSuccess;
     xbutterfly_moments_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Mhat,
                                                                                         n_nodes, Sx);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 // (x, y) butterflies of the masses: for every leaf cell c and a, b = 1..7,
@@ -3322,7 +3387,7 @@ cudaError_t launch_xybutterfly_masses(const int* nodes, int n_list, const int2* 
     if (n_list == 0) return cudaSuccess;
     xybutterfly_masses_kernel<<<blocks_for(49LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, m, n_nodes,
                                                                                          Sxy);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_xbutterfly_masses_adjoint(const int* nodes, int n_list, const int2* nbr, const int* xslot,
@@ -3330,7 +3395,7 @@ cudaError_t launch_xbutterfly_masses_adjoint(const int* nodes, int n_list, const
     if (n_list == 0) return cudaSuccess;
     xbutterfly_masses_adjoint_kernel<<<blocks_for(1LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, xslot,
                                                                                              Sbar, n_nodes, mbar);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr, const double* Lrbar, int n_nodes,
@@ -3338,7 +3403,7 @@ cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr
     if (n_list == 0) return cudaSuccess;
     xbutterfly_lbar_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Lrbar, n_nodes,
                                                                                      Tx);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
@@ -3346,39 +3411,39 @@ cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* n
     if (n_list == 0) return cudaSuccess;
     xbutterfly_masses_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, m, n_nodes,
                                                                                        Sm);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s) {
     if (p.n_list == 0) return cudaSuccess;
     prescale_adjoint_kernel<<<blocks_for(1LL * p.n_list * NCELL, 256), 256, 0, s>>>(p);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_restrict_virtual(const double* vbar, const int* vmap, int n_rows, double* mbar, cudaStream_t s) {
     if (n_rows == 0) return cudaSuccess;
     restrict_virtual_kernel<<<blocks_for(n_rows, 256), 256, 0, s>>>(vbar, vmap, n_rows, mbar);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_cube_moments(const double* rho, double* M, double* m, const int* nodes, int n_list,
                                 const int* ninfo, const double* hinv, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
     cube_moments_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(rho, M, m, nodes, n_list, ninfo, hinv);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_m2m(double* M, double* m, const int* parents, int n_list, const int* children,
                        const int* ninfo, const double* hinv, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
     m2m_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(M, m, parents, n_list, children, ninfo, hinv);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_moments_adjoint_init(const double* Mbar, const double* mbar, double* Mb, int n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     moments_adjoint_init_kernel<<<blocks_for(1LL * n * NCOMP * NCELL, 256), 256, 0, s>>>(Mbar, mbar, Mb, n);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_m2m_adjoint(double* Mb, const int* parents, int n_list, const int* children, const int* ninfo,
@@ -3386,14 +3451,14 @@ cudaError_t launch_m2m_adjoint(double* Mb, const int* parents, int n_list, const
     if (n_list == 0) return cudaSuccess;
     m2m_adjoint_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(Mb, parents, n_list, children,
                                                                                   ninfo, hinv);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_cube_adjoint(const double* Mb, double* rhobar, const int* nodes, int n_list, const int* ninfo,
                                 const double* hinv, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
     cube_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(Mb, rhobar, nodes, n_list, ninfo, hinv);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_geometric_centres(double* C, const int* nodes, int n_list, const int* ninfo, const int* ncoord,
@@ -3401,7 +3466,7 @@ cudaError_t launch_geometric_centres(double* C, const int* nodes, int n_list, co
     if (n_list == 0) return cudaSuccess;
     geometric_centres_kernel<<<blocks_for(1LL * n_list * NCELL, 256), 256, 0, s>>>(C, nodes, n_list, ninfo, ncoord,
                                                                                     h0);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_m2m_com(double* M, double* m, double* C, const int* parents, int n_list, const int* children,
@@ -3409,7 +3474,7 @@ cudaError_t launch_m2m_com(double* M, double* m, double* C, const int* parents, 
     if (n_list == 0) return cudaSuccess;
     m2m_com_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(M, m, C, parents, n_list, children, ninfo,
                                                                           ncoord, h0);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_l2l_com(double* L, const double* C, const int* parents, int n_list, const int* children,
@@ -3417,7 +3482,7 @@ cudaError_t launch_l2l_com(double* L, const double* C, const int* parents, int n
     if (n_list == 0) return cudaSuccess;
     l2l_com_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(L, C, parents, n_list, children, ninfo,
                                                                               ncoord, h0);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_l2l_com_adjoint(double* Lb, const double* C, const int* parents, int n_list, const int* children,
@@ -3425,7 +3490,7 @@ cudaError_t launch_l2l_com_adjoint(double* Lb, const double* C, const int* paren
     if (n_list == 0) return cudaSuccess;
     l2l_com_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(Lb, C, parents, n_list, children,
                                                                                   ninfo, ncoord, h0);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_forward_com(const FwdParams& p, int mode, int wpb, int grid, cudaStream_t s) {
@@ -3435,7 +3500,7 @@ cudaError_t launch_forward_com(const FwdParams& p, int mode, int wpb, int grid, 
         case 2: forward_com_kernel<2><<<grid, 32 * wpb, 0, s>>>(p); break;
         default: forward_com_kernel<3><<<grid, 32 * wpb, 0, s>>>(p); break;
     }
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_adjoint_com(const AdjParams& p, int mode, int wpb, int grid, cudaStream_t s) {
@@ -3447,7 +3512,7 @@ cudaError_t launch_adjoint_com(const AdjParams& p, int mode, int wpb, int grid, 
         case 4: adjoint_com_kernel<4><<<grid, 32 * wpb, 0, s>>>(p); break;
         default: adjoint_com_kernel<5><<<grid, 32 * wpb, 0, s>>>(p); break;
     }
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 int deriv_flops(int ncomp) {
@@ -3477,7 +3542,7 @@ cudaError_t launch_l2l(double* L, const int* parents, int n_list, const int* chi
                        const double* hinv, cudaStream_t s) {
     if (n_list == 0) return cudaSuccess;
     l2l_kernel<<<blocks_for(1LL * n_list * 8 * NCELL, 128), 128, 0, s>>>(L, parents, n_list, children, ninfo, hinv);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_l2l_adjoint(double* Lb, const int* parents, int n_list, const int* children, const int* ninfo,
@@ -3485,13 +3550,14 @@ cudaError_t launch_l2l_adjoint(double* Lb, const int* parents, int n_list, const
     if (n_list == 0) return cudaSuccess;
     l2l_adjoint_kernel<<<blocks_for(1LL * n_list * NCELL, 128), 128, 0, s>>>(Lb, parents, n_list, children, ninfo,
                                                                              hinv);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, int variant, cudaStream_t s) {
     if (variant == 0) fp64_probe_kernel<0><<<blocks, 256, 0, s>>>(out, iters);
-    else fp64_probe_kernel<1><<<blocks, 256, 0, s>>>(out, iters);
-    return cudaGetLastError();
+    else if (variant == 1) fp64_probe_kernel<1><<<blocks, 256, 0, s>>>(out, iters);
+    else fp64_probe_contraction_kernel<<<blocks, 256, 0, s>>>(out, iters);
+    return counted(cudaGetLastError());
 }
 
 }  // namespace otk

@@ -9,11 +9,13 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <set>
 #include <new>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
@@ -277,6 +279,7 @@ struct ot_grid {
     int schedule = OT_SCHED_PERSISTENT;
     int wpb = 4, bps = 0, use_graph = 1;
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, long long> graph_kernels;   // kernels recorded in each graph
 
     ot_grid_info_t info{};
 
@@ -1382,6 +1385,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     g->fp64_ops_adj_det = std::llround(alg_adj_det);
     g->fp64_ops_adj_fast = std::llround(alg_adj_multi + alg_adj_scat);
     I.fp64_ops_adj = g->fp64_ops_adj_fast;
+    I.fp64_ops_adj_multi = std::llround(alg_adj_multi);
+    I.ops_adj_multi = ops_adj_multi;
     g->flops_adj_det = flops_adj;
     g->ops_adj_det = ops_adj;
     g->flops_adj_fast = flops_adj_multi + flops_adj_scat;
@@ -1983,10 +1988,15 @@ static ot_status run_graphed(ot_grid* g, const GraphKey& key, cudaStream_t s, F 
     if (it == g->graphs.end()) {
         if (g->graphs.size() >= 16) {
             cudaGraphExecDestroy(g->graphs.begin()->second);
+            g->graph_kernels.erase(g->graphs.begin()->first);
             g->graphs.erase(g->graphs.begin());
         }
         OT_CUDA(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const long long before = launch_count_thread();
         ot_status st = body(g->cap_stream);
+        // the captured kernels are not launches yet: each replay counts them
+        const long long recorded = launch_count_thread() - before;
+        launch_count_adjust(-recorded);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
         if (st != OT_OK) {
@@ -1999,8 +2009,10 @@ static ot_status run_graphed(ot_grid* g, const GraphKey& key, cudaStream_t s, F 
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail(OT_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
         it = g->graphs.emplace(key, exec).first;
+        g->graph_kernels[key] = recorded;
     }
     OT_CUDA(cudaGraphLaunch(it->second, s));
+    launch_count_adjust(g->graph_kernels[key]);
     return OT_OK;
 }
 
@@ -2104,6 +2116,7 @@ ot_status ot_set_schedule(ot_grid* g, int32_t schedule, int32_t warps_per_block,
     if (g->wpb != warps_per_block || g->bps != blocks_per_sm || g->schedule != schedule) {
         for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
         g->graphs.clear();
+        g->graph_kernels.clear();
     }
     g->schedule = schedule;
     g->wpb = warps_per_block;
@@ -2149,7 +2162,7 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     CHECK_PTR(M, "M");
     CHECK_PTR(m, "m");
     CHECK_PTR(L, "L");
-    if (mechanism < 0 || mechanism > 3) return fail(OT_EINVAL, "mechanism must be 0..3");
+    if (mechanism < 0 || mechanism > 4) return fail(OT_EINVAL, "mechanism must be 0..4");
     if (n_streams < 1 || n_streams > 128) return fail(OT_EINVAL, "n_streams must be in [1, 128]");
     if (!(timeout_s > 0.0)) return fail(OT_EINVAL, "timeout_s must be positive");
     std::memset(out, 0, sizeof(*out));
@@ -2192,7 +2205,7 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     std::vector<CompletionSlot> slots(n);
     std::atomic<int> done_count{0};
     std::vector<cudaEvent_t> events;
-    if (mechanism == 2) {
+    if (mechanism == 2 || mechanism == 4) {
         events.resize(n, nullptr);
         for (auto& e : events) OT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
@@ -2207,7 +2220,97 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     const auto deadline = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
     bool timed_out = false;
     long long launches = 0;
-    if (mechanism == 3) {
+    if (mechanism == 4) {
+        // a pool of host threads drains a shared queue of pending events with
+        // cudaEventQuery while the launching thread keeps submitting: the
+        // analogue of event polling by the task scheduler's worker threads
+        const int n_workers = 4;
+        std::mutex qm;
+        std::deque<int> queue;
+        std::atomic<bool> stop{false};
+        std::atomic<int> first_error{0};
+        const int dev = g->device;
+        auto worker = [&]() {
+            cudaSetDevice(dev);
+            std::vector<int> mine, again;
+            while (!stop.load(std::memory_order_acquire)) {
+                {
+                    std::lock_guard<std::mutex> lock(qm);
+                    while (!queue.empty() && mine.size() < 64) {
+                        mine.push_back(queue.front());
+                        queue.pop_front();
+                    }
+                }
+                if (mine.empty()) {
+                    std::this_thread::yield();
+                    continue;
+                }
+                for (int i : mine) {
+                    const cudaError_t q = cudaEventQuery(events[i]);
+                    if (q == cudaSuccess) {
+                        slots[i].done = Clock::now();
+                        done_count.fetch_add(1, std::memory_order_acq_rel);
+                    } else if (q == cudaErrorNotReady) {
+                        again.push_back(i);
+                    } else {
+                        int zero = 0;
+                        first_error.compare_exchange_strong(zero, static_cast<int>(q));
+                        slots[i].done = Clock::now();
+                        done_count.fetch_add(1, std::memory_order_acq_rel);
+                    }
+                }
+                mine.clear();
+                if (!again.empty()) {
+                    std::lock_guard<std::mutex> lock(qm);
+                    for (int i : again) queue.push_back(i);
+                    again.clear();
+                }
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int w = 0; w < n_workers; ++w) pool.emplace_back(worker);
+        struct PoolGuard {
+            std::vector<std::thread>& pool;
+            std::atomic<bool>& stop;
+            ~PoolGuard() {
+                stop.store(true, std::memory_order_release);
+                for (auto& t : pool)
+                    if (t.joinable()) t.join();
+            }
+        } pguard{pool, stop};
+        ot_status submit = OT_OK;
+        for (int i = 0; i < n && submit == OT_OK; ++i) {
+            cudaStream_t s = streams[i % n_streams];
+            FwdParams q = p;
+            q.items = g->d_itemsc_node + g->itemc_node_start[i];
+            q.n_items = g->itemc_node_start[i + 1] - g->itemc_node_start[i];
+            slots[i].submitted = Clock::now();
+            cudaError_t e = launch_forward(q, 3, false, g->wpb, (q.n_items + g->wpb - 1) / g->wpb, s);
+            if (e == cudaSuccess) e = cudaEventRecord(events[i], s);
+            if (e != cudaSuccess) {
+                submit = fail(OT_ECUDA, "%s", cudaGetErrorString(e));
+                break;
+            }
+            ++launches;
+            std::lock_guard<std::mutex> lock(qm);
+            queue.push_back(i);
+        }
+        while (submit == OT_OK && done_count.load(std::memory_order_acquire) < n) {
+            if (Clock::now() > deadline) {
+                timed_out = true;
+                break;
+            }
+            std::this_thread::yield();
+        }
+        stop.store(true, std::memory_order_release);
+        for (auto& t : pool) t.join();
+        if (submit != OT_OK) {
+            cudaDeviceSynchronize();
+            return submit;
+        }
+        if (first_error.load() != 0)
+            return fail(OT_ECUDA, "event query: %s", cudaGetErrorString(static_cast<cudaError_t>(first_error.load())));
+    } else if (mechanism == 3) {
         // one batched persistent launch over every sub-grid, one completion
         g->schedule = OT_SCHED_PERSISTENT;
         for (auto& sl : slots) sl.submitted = Clock::now();
@@ -2613,10 +2716,16 @@ ot_status ot_fp64_fma_probe(double* out, int32_t blocks, int32_t iters, int32_t 
     GUARD_BEGIN
     CHECK_PTR(out, "out");
     if (blocks <= 0 || iters <= 0) return fail(OT_EINVAL, "blocks and iters must be positive");
-    if (variant != 0 && variant != 1) return fail(OT_EINVAL, "variant must be 0 or 1");
+    if (variant < 0 || variant > 2) return fail(OT_EINVAL, "variant must be 0, 1 or 2");
     OT_CUDA(launch_fp64_probe(out, blocks, iters, variant, static_cast<cudaStream_t>(stream)));
     return OT_OK;
     GUARD_END
+}
+
+ot_status ot_launch_count(int64_t* out) {
+    if (!out) return fail(OT_EINVAL, "out is NULL");
+    *out = launch_count_total();
+    return OT_OK;
 }
 
 }  // extern "C"

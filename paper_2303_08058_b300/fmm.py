@@ -143,7 +143,8 @@ class OTGrid:
 
     def completion_study(self, M, m, mechanism, n_streams=1, timeout_s=60.0, L=None, Lc=None):
         """Per-sub-grid launches with completion signalled by mechanism 0 (stream
-        sync), 1 (host callback), 2 (event polling) or 3 (one batched launch)."""
+        sync), 1 (host callback), 2 (event polling by the launching thread),
+        4 (event polling by a pool of host threads) or 3 (one batched launch)."""
         L = L if L is not None else self.zeros(self.n, NCOMP, NCELL)
         Lc = Lc if Lc is not None else self.zeros(self.n, 3, NCELL)
         out = _lib.CompletionStats()
@@ -246,6 +247,18 @@ class OTGrid:
         self.l2l(L, stream=stream)
         return L, Lc
 
+    def step_buffers(self) -> dict:
+        """The device buffers (and the side stream) ``step_host`` works in:
+        rho, Lbar, M, m, L, Lc, Mb, mb, rb, allocated once.  Calls that run on
+        them directly (moments, interactions, backward, moments_backward)
+        replay the same graphs as step_host."""
+        return {"copy": torch.cuda.Stream(device=self.device),
+                "rho": self.zeros(self.n, NCELL), "Lbar": self.zeros(self.n, NCOMP, NCELL),
+                "M": self.zeros(self.n, NCOMP, NCELL), "m": self.zeros(self.n, NCELL),
+                "L": self.zeros(self.n, NCOMP, NCELL), "Lc": self.zeros(self.n, 3, NCELL),
+                "Mb": self.zeros(self.n, NCOMP, NCELL), "mb": self.zeros(self.n, NCELL),
+                "rb": self.zeros(self.n, NCELL)}
+
     def step_host(self, rho_h, Lbar_h, L_h, rhobar_h, work=None, stream=None):
         """One forward + adjoint step between pinned host buffers: rho_h [n, 512]
         and Lbar_h [n, 20, 512] in; L_h [n, 20, 512] (both passes) and rhobar_h
@@ -260,16 +273,7 @@ class OTGrid:
         if work is None:
             work = {}
         if not work:
-            work["copy"] = torch.cuda.Stream(device=self.device)
-            work["rho"] = self.zeros(self.n, NCELL)
-            work["Lbar"] = self.zeros(self.n, NCOMP, NCELL)
-            work["M"] = self.zeros(self.n, NCOMP, NCELL)
-            work["m"] = self.zeros(self.n, NCELL)
-            work["L"] = self.zeros(self.n, NCOMP, NCELL)
-            work["Lc"] = self.zeros(self.n, 3, NCELL)
-            work["Mb"] = self.zeros(self.n, NCOMP, NCELL)
-            work["mb"] = self.zeros(self.n, NCELL)
-            work["rb"] = self.zeros(self.n, NCELL)
+            work.update(self.step_buffers())
         cp = work["copy"]
         start, lbar_in, fwd_done = (torch.cuda.Event() for _ in range(3))
         start.record(main)
@@ -313,12 +317,26 @@ def _l2l_backward(grid, Lbar, stream=None):
     return Lbar
 
 
+# FMAs one thread runs per round of each probe variant
+FP64_PROBE_FMA_PER_ROUND = {0: 16, 1: 16, 2: 1024}
+
+
 def fp64_fma_probe(out, blocks, iters, variant=0, stream=None):
-    """FP64 FMA probe: writes blocks x 256 doubles into ``out``."""
+    """FP64 FMA probe: writes blocks x 256 doubles into ``out``; a thread runs
+    FP64_PROBE_FMA_PER_ROUND[variant] FMAs per round."""
     lib = _lib.load()
     if out.numel() < int(blocks) * 256:
         raise ValueError(f"out holds {out.numel()} doubles, the probe writes {int(blocks) * 256}")
     _lib.check(lib.ot_fp64_fma_probe(_ptr(out), int(blocks), int(iters), int(variant), _stream(stream)))
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process (graph replays count
+    every kernel they hold; recording a graph counts none)."""
+    lib = _lib.load()
+    n = ctypes.c_int64(0)
+    _lib.check(lib.ot_launch_count(ctypes.byref(n)))
+    return int(n.value)
 
 
 class FMMInteractions(torch.autograd.Function):

@@ -68,6 +68,12 @@ def test_host_argument_checks_without_device(lib):
     assert lib.ot_set_schedule(None, 0, 4, 0, 1) == _lib.OT_EINVAL
     assert lib.ot_interactions(None, None, None, None, None, None) == _lib.OT_EINVAL
     assert lib.ot_fp64_fma_probe(None, 1, 1, 0, None) == _lib.OT_EINVAL
+    assert lib.ot_fp64_fma_probe(ctypes.c_void_p(0x1000), 1, 1, 3, None) == _lib.OT_EINVAL
+    assert b"variant" in lib.ot_last_error()
+    # the launch counter reads a host counter: no device needed
+    assert lib.ot_launch_count(None) == _lib.OT_EINVAL
+    cnt = ctypes.c_int64(-1)
+    assert lib.ot_launch_count(ctypes.byref(cnt)) == _lib.OT_OK and cnt.value >= 0
     # a pointer that is not a live grid handle is refused before any use
     fake = ctypes.c_void_p(0x1000)
     assert lib.ot_grid_destroy(fake) == _lib.OT_EINVAL

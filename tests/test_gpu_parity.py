@@ -500,23 +500,30 @@ def test_abi_rejects_bad_input(ot):
 
 def test_fp64_probe_runs(ot):
     out = torch.zeros(148 * 256, dtype=torch.float64, device="cuda")
-    for variant in (0, 1):
-        ot.fp64_fma_probe(out, 148, 100, variant)
+    for variant in (0, 1, 2):
+        ot.fp64_fma_probe(out, 148, 10, variant)
         torch.cuda.synchronize()
         assert np.all(np.isfinite(host(out))) and np.all(host(out) > 0)
 
 
-@pytest.mark.parametrize("mechanism", [0, 1, 2, 3])
-def test_completion_study_results_and_stats(ot, mechanism):
+@pytest.mark.parametrize("mechanism", [0, 1, 2, 3, 4])
+def test_completion_study_results_and_stats(ot, orc, mechanism):
     """Per-sub-grid launches over 4 streams, whatever signals their
-    completion, give the batched launch's result; the stats are sane."""
+    completion (stream sync, host callback, event polling by the launching
+    thread or by a host thread pool, one batched launch), give the oracle's
+    result at every cell of the small adaptive tree, and the batched
+    launch's bits; the stats are sane."""
     tree = _small_adaptive()
     rho = synth.uniform_random_density(tree, seed=90)
+    M, m = oracle_moments(orc, tree, rho)
     g = ot.OTGrid.from_tree(tree)
-    M, m = g.moments(dev(rho))
-    L_ref, Lc_ref = g.interactions(M, m)
-    stats, L, Lc = g.completion_study(M, m, mechanism, n_streams=4)
+    L_ref, Lc_ref = g.interactions(dev(M), dev(m))
+    stats, L, Lc = g.completion_study(dev(M), dev(m), mechanism, n_streams=4)
     torch.cuda.synchronize()
+    tg = all_targets(tree)
+    Lo, S, Lco, Sc, _, _ = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(host(L), tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(host(Lc), tg), Lco, Sc, what="Lc")
     np.testing.assert_array_equal(host(Lc), host(Lc_ref))
     scale = np.max(np.abs(host(L_ref)))
     assert np.max(np.abs(host(L) - host(L_ref))) <= 1e-13 * scale

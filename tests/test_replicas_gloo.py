@@ -27,7 +27,8 @@ def _worker(rank, world, port, q):
     import torch.distributed as dist
     r, w = bench.dist_init(None)
     bench.barrier(w)
-    value, ms = bench.aggregate(w, steps=10, pairs_step=1000, local_seconds=1.0 + r)   # rank 1 is slower
+    # each rank ran 10 steps of 1000 pairs; rank 1 is slower
+    value, ms = bench.aggregate(w, pairs_local=10 * 1000, local_seconds=1.0 + r, steps=10)
     q.put((r, w, value, ms))
     dist.destroy_process_group()
 
