@@ -117,14 +117,16 @@ struct FwdParams {
     const int2* cinfo;     // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
     double* part;          // [slots][PART_VALS][32] chunk accumulators
     int* chunk_ctr;        // [counters] chunks finished per (node, parity, half), zeroed per launch
-    // prebuilt x butterflies (null: not built for this launch); a node's slot
-    // in its kind's table is xslot[node]
-    const double* Sx;      // [non-leaf slot][7][16][2][512]: Mhat(c + a x) +- Mhat(c - a x), multipole cells
-    const double* Sm;      // [leaf slot][7][2][512]: the same for the point masses
+    // prebuilt x butterflies (null: not built for this launch), per slot of a
+    // space of regions (nodes and virtual blocks): X around non-leaf nodes, M
+    // around leaf nodes; nslot[node][j] is the slot of the node's neighbour
+    // region j in its own kind's space (-1: outside the domain)
+    const double* Sx;      // [X slot][7][16][2][512]: Mhat(c + a x) +- Mhat(c - a x), multipole cells
+    const double* Sm;      // [M slot][7][2][512]: the same for the point masses
     const float2* Smf;     // the masses' table as double-float (hi, lo) pairs (double-float point masses)
-    const double* Sxy;     // [leaf slot][49: (a - 1) 7 + b - 1][4][512]: the masses at c + (+-a, +-b, 0)
+    const double* Sxy;     // [M slot][49: (a - 1) 7 + b - 1][4][512]: the masses at c + (+-a, +-b, 0)
                            // transformed over x and y (null: not built)
-    const int* xslot;      // [n]
+    const int* nslot;      // [n][27]
 };
 
 struct AdjParams {
@@ -155,14 +157,13 @@ struct AdjParams {
     const float2* Dt2;     // [NOFF][DROW] the derivative table as (hi, lo) pairs
     const float* Dt32;     // [NOFF][32] hi then lo parts of the 16 point-mass derivatives
     // prebuilt x butterflies of the targets' reduced L-bar (null: not built)
-    const double* Tx;      // [tslot][7][16][2][512]: Lrbar(c + a x) +- Lrbar(c - a x) over real cells
-    const int* tslot;      // [n]: slot of a node at a level with non-leaf nodes, else -1
+    const double* Tx;      // [X slot][7][16][2][512]: Lrbar(c + a x) +- Lrbar(c - a x) over real cells
     // the point-mass scatter's x stage deferred (null: scatter to mbar directly):
     // a leaf target with leaf or empty neighbours adds its x-complete classes'
     // two x channels at the positions t + (0, +-b, +-c), and a later pass
     // (xbutterfly_masses_adjoint) forms the members' sums and differences
-    double* Sbar;          // [leaf slot][7][2][512], zeroed before the launch
-    const int* xslot;      // [n]: leaf slot
+    double* Sbar;          // [M slot][7][2][512], zeroed before the launch
+    const int* nslot;      // [n][27]: neighbour regions' slots (M for leaf nodes, X for non-leaf)
     // chunked multipole gather items (bit 31 set: source in bits 4-25, chunk
     // index in bits 26-29); null: every item is whole
     const int2* cinfo;     // [n]: partial slot base, counter base << 4 | (chunks - 1); x < 0: whole
@@ -187,7 +188,7 @@ struct ScatParams {
     const int* child_of;   // as in FwdParams
     const double* Dv;
     double* Sbar;          // as in AdjParams (null here: the plain schedule scatters directly)
-    const int* xslot;
+    const int* nslot;
 };
 
 struct PrepParams {
@@ -215,16 +216,20 @@ cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wp
 cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wpb, int grid,
                            cudaStream_t s);
 cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s);
-cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* nbr, const double* Mhat, int n_nodes,
-                                      double* Sx, cudaStream_t s);
-cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr, const double* Lrbar, int n_nodes,
-                                   double* Tx, cudaStream_t s);
-cudaError_t launch_xbutterfly_masses_adjoint(const int* nodes, int n_list, const int2* nbr, const int* xslot,
-                                             const double* Sbar, int n_nodes, double* mbar, cudaStream_t s);
-cudaError_t launch_xybutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
-                                      double* Sxy, cudaStream_t s);
-cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
-                                     double* Sm, cudaStream_t s);
+// x-butterfly builders over the slots of a region space: snb [slots][27]
+// holds each slot's region's neighbour entries
+cudaError_t launch_xbutterfly_moments(const int2* snb, int n_slots, const double* Mhat, int n_nodes, double* Sx,
+                                      cudaStream_t s);
+cudaError_t launch_xbutterfly_lbar(const int2* snb, int n_slots, const double* Lrbar, int n_nodes, double* Tx,
+                                   cudaStream_t s);
+// the scatter's deferred x stage: per point-mass region of space M (own
+// entry ent, M slots of its regions at x-1, x, x+1 in xs)
+cudaError_t launch_xbutterfly_masses_adjoint(const int2* ent, const int* xs, int n_members, const double* Sbar,
+                                             int n_nodes, double* mbar, cudaStream_t s);
+cudaError_t launch_xybutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sxy,
+                                      cudaStream_t s);
+cudaError_t launch_xbutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sm,
+                                     cudaStream_t s);
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);
 cudaError_t launch_restrict_virtual(const double* vbar, const int* vmap, int n_pairs_map,
                                     double* mbar, cudaStream_t s);

@@ -506,16 +506,17 @@ __device__ __forceinline__ void walk_classes_fwd_x(const int* __restrict__ list,
             if ((2 * q) & Z) continue;
             if ((members >> (2 * q)) & 1u) {
                 const int sy = (q & 1) ? ty - b : ty + b, sz = (q & 2) ? tz - c : tz + c;
-                const int2 es = s_nb[nb_index(tx, sy, sz)];
-                const int ks = checked_kind(p, es, item);
-                if (ks == K_LEAF) {
-                    const double* src = p.Sm + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + a - 1) * 2 * NCELL +
+                const int nbi = nb_index(tx, sy, sz);
+                const int ks = checked_kind(p, s_nb[nbi], item);
+                const int slot = s_sl[nbi];
+                if (slot >= 0) {
+                    const double* src = p.Sm + static_cast<size_t>(slot * 7 + a - 1) * 2 * NCELL +
                                         (tx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
                     w[2 * q] = __ldg(src);
                     w[2 * q + 1] = __ldg(src + NCELL);
                     any = true;
                 } else if (ks != K_NONE) {
-                    report(p.status, 7, item);    // the node's flag promised leaf or empty neighbours
+                    report(p.status, 7, item);    // the node's flag promised a table slot for every region
                 }
             }
         }
@@ -617,10 +618,11 @@ __device__ __forceinline__ void walk_classes_fwd_df_x(const int* __restrict__ li
             if ((2 * q) & Z) continue;
             if ((members >> (2 * q)) & 1u) {
                 const int sy = (q & 1) ? ty - b : ty + b, sz = (q & 2) ? tz - cc : tz + cc;
-                const int2 es = s_nb[nb_index(tx, sy, sz)];
-                const int ks = checked_kind(p, es, item);
-                if (ks == K_LEAF) {
-                    const float2* src = p.Smf + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + a - 1) * 2 * NCELL +
+                const int nbi = nb_index(tx, sy, sz);
+                const int ks = checked_kind(p, s_nb[nbi], item);
+                const int slot = s_sl[nbi];
+                if (slot >= 0) {
+                    const float2* src = p.Smf + static_cast<size_t>(slot * 7 + a - 1) * 2 * NCELL +
                                         (tx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
                     const float2 vp = __ldg(src), vm = __ldg(src + NCELL);
                     wh[2 * q] = vp.x;
@@ -690,10 +692,10 @@ __device__ __forceinline__ void walk_classes_fwd_xy(const int* __restrict__ list
             if ((members >> (4 * r)) & 1u) {
                 const int sz = r ? tz - c : tz + c;
                 const int nbi = nb_index(tx, ty, sz);
-                const int2 es = s_nb[nbi];
-                const int ks = checked_kind(p, es, item);
-                if (ks == K_LEAF) {
-                    const double* src = p.Sxy + static_cast<size_t>(s_sl[nbi] * 49 + (a - 1) * 7 + b - 1) * 4 * NCELL +
+                const int ks = checked_kind(p, s_nb[nbi], item);
+                const int slot = s_sl[nbi];
+                if (slot >= 0) {
+                    const double* src = p.Sxy + static_cast<size_t>(slot * 49 + (a - 1) * 7 + b - 1) * 4 * NCELL +
                                         (tx & 7) + 8 * (ty & 7) + 64 * (sz & 7);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) w[4 * r + q] = __ldg(src + q * NCELL);
@@ -800,14 +802,15 @@ __device__ __forceinline__ void walk_mclasses_fwd_x(const int* __restrict__ list
             if ((2 * q) & Z) continue;
             if ((members >> (2 * q)) & 1u) {
                 const int sy = (q & 1) ? ty - oy : ty + oy, sz = (q & 2) ? tz - oz : tz + oz;
-                const int2 es = s_nb[nb_index(tx, sy, sz)];
-                const int ks = checked_kind(p, es, item);
-                if (ks == K_MULTI) {
-                    pos[q] = p.Sx + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + ox - 1) * 32 * NCELL + (tx & 7) +
+                const int nbi = nb_index(tx, sy, sz);
+                const int ks = checked_kind(p, s_nb[nbi], item);
+                const int slot = s_sl[nbi];
+                if (slot >= 0) {
+                    pos[q] = p.Sx + static_cast<size_t>(slot * 7 + ox - 1) * 32 * NCELL + (tx & 7) +
                              8 * (sy & 7) + 64 * (sz & 7);
                     any = true;
                 } else if (ks != K_NONE) {
-                    report(p.status, 7, item);    // the node's flag promised multipole or empty neighbours
+                    report(p.status, 7, item);    // the node's flag promised a table slot for every region
                 }
             }
         }
@@ -1091,9 +1094,8 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             const int2 e = __ldg(p.nbr + static_cast<size_t>(node) * 27 + lane);
             s_nb[warp][lane] = e;
             const int k = e.y & 3;
-            s_sl[warp][lane] = (p.xslot != nullptr && (k == K_LEAF || k == K_MULTI) &&
-                                static_cast<unsigned>(e.x) < static_cast<unsigned>(p.n_nodes))
-                                   ? __ldg(p.xslot + e.x) : -1;
+            s_sl[warp][lane] = (p.nslot != nullptr && k != K_NONE) ? __ldg(p.nslot + static_cast<size_t>(node) * 27 + lane)
+                                                                    : -1;
         }
         __syncwarp();
         const int info = __ldg(p.ninfo + node);
@@ -1445,19 +1447,15 @@ __device__ __forceinline__ void walk_mclasses_adj_x(const int* __restrict__ list
             if ((2 * q) & Z) continue;
             if ((members >> (2 * q)) & 1u) {
                 const int ty = (q & 1) ? sy0 - oy : sy0 + oy, tz = (q & 2) ? sz0 - oz : sz0 + oz;
-                const int2 et = s_nb[nb_index(sx0, ty, tz)];
-                const int kt = et.y & 3;
-                if ((kt == K_MULTI || kt == K_LEAF) && static_cast<unsigned>(et.x) < static_cast<unsigned>(p.n_nodes)) {
-                    const int slot = s_sl[nb_index(sx0, ty, tz)];
-                    if (slot >= 0) {
-                        pos[q] = p.Tx + static_cast<size_t>(slot * 7 + ox - 1) * 32 * NCELL + (sx0 & 7) +
-                                 8 * (ty & 7) + 64 * (tz & 7);
-                        any = true;
-                    } else {
-                        report(p.status, 7, item);
-                    }
+                const int nbi = nb_index(sx0, ty, tz);
+                const int kt = s_nb[nbi].y & 3;
+                const int slot = s_sl[nbi];
+                if (slot >= 0) {
+                    pos[q] = p.Tx + static_cast<size_t>(slot * 7 + ox - 1) * 32 * NCELL + (sx0 & 7) +
+                             8 * (ty & 7) + 64 * (tz & 7);
+                    any = true;
                 } else if (kt != K_NONE) {
-                    report(p.status, 7, item);    // the source's flag promised real or empty neighbours
+                    report(p.status, 7, item);    // the source's flag promised a table slot for every region
                 }
             }
         }
@@ -1569,9 +1567,8 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const AdjParams p, int 
             const int2 e = __ldg(nbt + lane);
             s_nb[warp][lane] = e;
             const int k = e.y & 3;
-            s_sl[warp][lane] = (p.tslot != nullptr && (k == K_LEAF || k == K_MULTI) &&
-                                static_cast<unsigned>(e.x) < static_cast<unsigned>(p.n_nodes))
-                                   ? __ldg(p.tslot + e.x) : -1;
+            s_sl[warp][lane] = (p.nslot != nullptr && !virt && k != K_NONE)
+                                   ? __ldg(p.nslot + static_cast<size_t>(src) * 27 + lane) : -1;
         }
         __syncwarp();
         int level, skind;
@@ -1788,14 +1785,15 @@ __device__ __forceinline__ void walk_classes_scatter_x(const int* __restrict__ l
             if ((2 * q) & Z) continue;
             if ((members >> (2 * q)) & 1u) {
                 const int sy = (q & 1) ? ty - b : ty + b, sz = (q & 2) ? tz - c : tz + c;
-                const int2 es = s_nb[nb_index(tx, sy, sz)];
-                const int ks = es.y & 3;
-                if (ks == K_LEAF && static_cast<unsigned>(es.x) < static_cast<unsigned>(p.n_nodes)) {
-                    dst[q] = p.Sbar + static_cast<size_t>(s_sl[nb_index(tx, sy, sz)] * 7 + a - 1) * 2 * NCELL + (tx & 7) +
+                const int nbi = nb_index(tx, sy, sz);
+                const int ks = s_nb[nbi].y & 3;
+                const int slot = s_sl[nbi];
+                if (slot >= 0) {
+                    dst[q] = p.Sbar + static_cast<size_t>(slot * 7 + a - 1) * 2 * NCELL + (tx & 7) +
                              8 * (sy & 7) + 64 * (sz & 7);
                     any = true;
                 } else if (ks != K_NONE) {
-                    report(p.status, 7, item);    // the target's flag promised leaf or empty neighbours
+                    report(p.status, 7, item);    // the target's flag promised a table slot for every region
                 }
             }
         }
@@ -1925,9 +1923,8 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
     if (lane < 27) {
         const int2 e = __ldg(nbr + static_cast<size_t>(node) * 27 + lane);
         s_nb[lane] = e;
-        s_sl[lane] = (p.xslot != nullptr && (e.y & 3) == K_LEAF &&
-                      static_cast<unsigned>(e.x) < static_cast<unsigned>(p.n_nodes))
-                         ? __ldg(p.xslot + e.x) : -1;
+        s_sl[lane] = (p.nslot != nullptr && (e.y & 3) != K_NONE) ? __ldg(p.nslot + static_cast<size_t>(node) * 27 + lane)
+                                                                 : -1;
     }
     __syncwarp();
     const int info = __ldg(ninfo + node);
@@ -3222,20 +3219,20 @@ static inline int blocks_for(long long n, int per) { return static_cast<int>((n 
 // v(c + a x) + v(c - a x) and v(c + a x) - v(c - a x), v the value the pass
 // reads at that position (reduced moments of multipole cells; point masses
 // of leaf and virtual cells), 0 elsewhere
-__global__ void xbutterfly_moments_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
-                                          const double* __restrict__ Mhat, int n_nodes, double* __restrict__ Sx) {
+__global__ void xbutterfly_moments_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ Mhat,
+                                          int n_nodes, double* __restrict__ Sx) {
     const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (gid >= 7LL * NCELL * n_list) return;
+    if (gid >= 7LL * NCELL * n_slots) return;
     const int cell = static_cast<int>(gid % NCELL);
     const int a = static_cast<int>((gid / NCELL) % 7) + 1;
     const int slot = static_cast<int>(gid / (7 * NCELL));
-    const int node = __ldg(nodes + slot);
     const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const int2* nb = snb + static_cast<size_t>(slot) * 27;
     const double* src[2] = {nullptr, nullptr};
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
         const int sx = sd ? x - a : x + a;
-        const int2 e = __ldg(nbr + static_cast<size_t>(node) * 27 + nb_index(sx, y, z));
+        const int2 e = __ldg(nb + nb_index(sx, y, z));
         if ((e.y & 3) == K_MULTI && static_cast<unsigned>(e.x) < static_cast<unsigned>(n_nodes))
             src[sd] = Mhat + static_cast<size_t>(e.x) * NRED * NCELL + (sx & 7) + 8 * y + 64 * z;
     }
@@ -3251,20 +3248,20 @@ __global__ void xbutterfly_moments_kernel(const int* __restrict__ nodes, int n_l
 
 // the same over the targets' reduced L-bar: multipole and leaf cells of the
 // node's level (the multipole gather's targets)
-__global__ void xbutterfly_lbar_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
-                                       const double* __restrict__ Lrbar, int n_nodes, double* __restrict__ Tx) {
+__global__ void xbutterfly_lbar_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ Lrbar,
+                                       int n_nodes, double* __restrict__ Tx) {
     const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (gid >= 7LL * NCELL * n_list) return;
+    if (gid >= 7LL * NCELL * n_slots) return;
     const int cell = static_cast<int>(gid % NCELL);
     const int a = static_cast<int>((gid / NCELL) % 7) + 1;
     const int slot = static_cast<int>(gid / (7 * NCELL));
-    const int node = __ldg(nodes + slot);
     const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const int2* nb = snb + static_cast<size_t>(slot) * 27;
     const double* src[2] = {nullptr, nullptr};
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
         const int sx = sd ? x - a : x + a;
-        const int2 e = __ldg(nbr + static_cast<size_t>(node) * 27 + nb_index(sx, y, z));
+        const int2 e = __ldg(nb + nb_index(sx, y, z));
         const int k = e.y & 3;
         if ((k == K_MULTI || k == K_LEAF) && static_cast<unsigned>(e.x) < static_cast<unsigned>(n_nodes))
             src[sd] = Lrbar + static_cast<size_t>(e.x) * NRED * NCELL + (sx & 7) + 8 * y + 64 * z;
@@ -3294,45 +3291,58 @@ __device__ __forceinline__ double mass_at(const double* __restrict__ m, int2 e, 
     return 0.0;
 }
 
-// the transpose of xbutterfly_masses_kernel: each leaf cell c collects, for
-// a = 1..7, the deferred x channels (A, B) of the positions c - a x (c is
-// their +a member: A + B) and c + a x (their -a member: A - B)
-__global__ void xbutterfly_masses_adjoint_kernel(const int* __restrict__ nodes, int n_list,
-                                                 const int2* __restrict__ nbr, const int* __restrict__ xslot,
-                                                 const double* __restrict__ Sbar, int n_nodes,
+// the transpose of xbutterfly_masses_kernel: each cell c of a point-mass
+// region (a leaf node or a virtual block) collects, for a = 1..7, the
+// deferred x channels (A, B) of the positions c - a x (c is their +a member:
+// A + B) and c + a x (their -a member: A - B), and adds the sum to its mass
+// adjoint (a virtual cell's, times 8^-d, to the cell of its coarse leaf)
+__global__ void xbutterfly_masses_adjoint_kernel(const int2* __restrict__ ent, const int* __restrict__ xs,
+                                                 int n_members, const double* __restrict__ Sbar, int n_nodes,
                                                  double* __restrict__ mbar) {
     const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (gid >= 1LL * NCELL * n_list) return;
+    if (gid >= 1LL * NCELL * n_members) return;
     const int cell = static_cast<int>(gid % NCELL);
-    const int node = __ldg(nodes + static_cast<int>(gid / NCELL));
+    const int k = static_cast<int>(gid / NCELL);
     const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
-    const int2* nb = nbr + static_cast<size_t>(node) * 27;
+    int cs[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) cs[r] = __ldg(xs + 3 * k + r);
     double acc = 0.0;
     for (int a = 1; a <= 7; ++a) {
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
             const int qx = sd ? x + a : x - a;         // the position whose member c is
-            const int2 e = __ldg(nb + nb_index(qx, y, z));
-            if ((e.y & 3) != K_LEAF || static_cast<unsigned>(e.x) >= static_cast<unsigned>(n_nodes)) continue;
-            const double* src = Sbar + static_cast<size_t>(__ldg(xslot + e.x) * 7 + a - 1) * 2 * NCELL + (qx & 7) +
-                                8 * y + 64 * z;
+            const int slot = cs[(qx >> 3) + 1];
+            if (slot < 0) continue;
+            const double* src = Sbar + static_cast<size_t>(slot * 7 + a - 1) * 2 * NCELL + (qx & 7) + 8 * y + 64 * z;
             const double A = __ldg(src), B = __ldg(src + NCELL);
             acc += sd ? A - B : A + B;
         }
     }
-    mbar[static_cast<size_t>(node) * NCELL + cell] += acc;
+    if (acc == 0.0) return;
+    const int2 e = __ldg(ent + k);
+    if (static_cast<unsigned>(e.x) >= static_cast<unsigned>(n_nodes)) return;
+    if ((e.y & 3) == K_LEAF) {
+        atomicAdd(mbar + static_cast<size_t>(e.x) * NCELL + cell, acc);
+    } else if ((e.y & 3) == K_VIRT) {
+        const unsigned meta = static_cast<unsigned>(e.y);
+        const int d = (meta >> 2) & 7;
+        const int vx = static_cast<int>(((meta >> 8) & 0xffu) + x) >> d;
+        const int vy = static_cast<int>(((meta >> 16) & 0xffu) + y) >> d;
+        const int vz = static_cast<int>((meta >> 24) + z) >> d;
+        atomicAdd(mbar + static_cast<size_t>(e.x) * NCELL + vx + 8 * vy + 64 * vz, acc * pow2i(-3 * d));
+    }
 }
 
-__global__ void xbutterfly_masses_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
-                                         const double* __restrict__ m, int n_nodes, double* __restrict__ Sm) {
+__global__ void xbutterfly_masses_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ m,
+                                         int n_nodes, double* __restrict__ Sm) {
     const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (gid >= 7LL * NCELL * n_list) return;
+    if (gid >= 7LL * NCELL * n_slots) return;
     const int cell = static_cast<int>(gid % NCELL);
     const int a = static_cast<int>((gid / NCELL) % 7) + 1;
     const int slot = static_cast<int>(gid / (7 * NCELL));
-    const int node = __ldg(nodes + slot);
     const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
-    const int2* nb = nbr + static_cast<size_t>(node) * 27;
+    const int2* nb = snb + static_cast<size_t>(slot) * 27;
     const double vp = mass_at(m, __ldg(nb + nb_index(x + a, y, z)), n_nodes, x + a, y, z);
     const double vm = mass_at(m, __ldg(nb + nb_index(x - a, y, z)), n_nodes, x - a, y, z);
     double* out = Sm + static_cast<size_t>(slot * 7 + a - 1) * 2 * NCELL + cell;
@@ -3346,28 +3356,26 @@ cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s) {
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_xbutterfly_moments(const int* nodes, int n_list, const int2* nbr, const double* Mhat, int n_nodes,
-                                      double* Sx, cudaStream_t s) {
-    if (n_list == 0) return cudaSuccess;
-    xbutterfly_moments_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Mhat,
-                                                                                        n_nodes, Sx);
+cudaError_t launch_xbutterfly_moments(const int2* snb, int n_slots, const double* Mhat, int n_nodes, double* Sx,
+                                      cudaStream_t s) {
+    if (n_slots == 0) return cudaSuccess;
+    xbutterfly_moments_kernel<<<blocks_for(7LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, Mhat, n_nodes, Sx);
     return counted(cudaGetLastError());
 }
 
 // (x, y) butterflies of the masses: for every leaf cell c and a, b = 1..7,
 // the four transforms over x and y of the masses at c + (+-a, +-b, 0),
 // out[pi] = sum_i (-1)^|i & pi| v_i (i, pi: bit 0 x negated / x odd, bit 1 y)
-__global__ void xybutterfly_masses_kernel(const int* __restrict__ nodes, int n_list, const int2* __restrict__ nbr,
-                                          const double* __restrict__ m, int n_nodes, double* __restrict__ Sxy) {
+__global__ void xybutterfly_masses_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ m,
+                                          int n_nodes, double* __restrict__ Sxy) {
     const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (gid >= 49LL * NCELL * n_list) return;
+    if (gid >= 49LL * NCELL * n_slots) return;
     const int cell = static_cast<int>(gid % NCELL);
     const int ab = static_cast<int>((gid / NCELL) % 49);
     const int slot = static_cast<int>(gid / (49 * NCELL));
     const int a = ab / 7 + 1, b = ab % 7 + 1;
-    const int node = __ldg(nodes + slot);
     const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
-    const int2* nb = nbr + static_cast<size_t>(node) * 27;
+    const int2* nb = snb + static_cast<size_t>(slot) * 27;
     double v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -3382,35 +3390,32 @@ __global__ void xybutterfly_masses_kernel(const int* __restrict__ nodes, int n_l
     out[3 * NCELL] = u1 - u3;
 }
 
-cudaError_t launch_xybutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
-                                      double* Sxy, cudaStream_t s) {
-    if (n_list == 0) return cudaSuccess;
-    xybutterfly_masses_kernel<<<blocks_for(49LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, m, n_nodes,
-                                                                                         Sxy);
+cudaError_t launch_xybutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sxy,
+                                      cudaStream_t s) {
+    if (n_slots == 0) return cudaSuccess;
+    xybutterfly_masses_kernel<<<blocks_for(49LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, m, n_nodes, Sxy);
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_xbutterfly_masses_adjoint(const int* nodes, int n_list, const int2* nbr, const int* xslot,
-                                             const double* Sbar, int n_nodes, double* mbar, cudaStream_t s) {
-    if (n_list == 0) return cudaSuccess;
-    xbutterfly_masses_adjoint_kernel<<<blocks_for(1LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, xslot,
-                                                                                             Sbar, n_nodes, mbar);
+cudaError_t launch_xbutterfly_masses_adjoint(const int2* ent, const int* xs, int n_members, const double* Sbar,
+                                             int n_nodes, double* mbar, cudaStream_t s) {
+    if (n_members == 0) return cudaSuccess;
+    xbutterfly_masses_adjoint_kernel<<<blocks_for(1LL * NCELL * n_members, 256), 256, 0, s>>>(ent, xs, n_members, Sbar,
+                                                                                                n_nodes, mbar);
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_xbutterfly_lbar(const int* nodes, int n_list, const int2* nbr, const double* Lrbar, int n_nodes,
-                                   double* Tx, cudaStream_t s) {
-    if (n_list == 0) return cudaSuccess;
-    xbutterfly_lbar_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, Lrbar, n_nodes,
-                                                                                     Tx);
+cudaError_t launch_xbutterfly_lbar(const int2* snb, int n_slots, const double* Lrbar, int n_nodes, double* Tx,
+                                   cudaStream_t s) {
+    if (n_slots == 0) return cudaSuccess;
+    xbutterfly_lbar_kernel<<<blocks_for(7LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, Lrbar, n_nodes, Tx);
     return counted(cudaGetLastError());
 }
 
-cudaError_t launch_xbutterfly_masses(const int* nodes, int n_list, const int2* nbr, const double* m, int n_nodes,
-                                     double* Sm, cudaStream_t s) {
-    if (n_list == 0) return cudaSuccess;
-    xbutterfly_masses_kernel<<<blocks_for(7LL * NCELL * n_list, 256), 256, 0, s>>>(nodes, n_list, nbr, m, n_nodes,
-                                                                                       Sm);
+cudaError_t launch_xbutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sm,
+                                     cudaStream_t s) {
+    if (n_slots == 0) return cudaSuccess;
+    xbutterfly_masses_kernel<<<blocks_for(7LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, m, n_nodes, Sm);
     return counted(cudaGetLastError());
 }
 

@@ -218,21 +218,27 @@ struct ot_grid {
     int2* d_cinfo = nullptr;
     double* d_part = nullptr;           // [slots][28][32] chunk accumulators
     int* d_chunk_ctr = nullptr;         // [counters] chunks finished per (node, parity, half)
-    // prebuilt x butterflies of the classes' first transform stage
-    std::vector<int> xslot;             // [n]: slot among the non-leaf (leaf) nodes
-    int n_xnonleaf = 0, n_xleaf = 0;
-    int* d_xslot = nullptr;
-    int* d_leaf = nullptr;              // leaf nodes in slot order
-    double* d_Sx = nullptr;             // [non-leaf slot][7][16][2][512]
-    double* d_Sm = nullptr;             // [leaf slot][7][2][512]
-    double* d_Sxy = nullptr;            // [leaf slot][49][4][512]: the masses' (x, y) butterflies
+    // prebuilt x butterflies of the classes' first transform stage, per slot
+    // of two spaces of regions (nodes and virtual blocks): M around leaf
+    // nodes, X around non-leaf nodes
+    std::vector<int> nslot;             // [n][27]: slot of each neighbour region in the node's space, -1: none
+    std::vector<int2> snbM, snbX;       // [slot][27]: each slot's region's neighbour entries
+    int n_slotM = 0, n_slotX = 0;
+    int* d_nslot = nullptr;
+    int2* d_snbM = nullptr;
+    int2* d_snbX = nullptr;
+    std::vector<int2> mem_ent;          // point-mass regions of M: own entry (leaf node or virtual block)
+    std::vector<int> mem_xs;            // [member][3]: M slots of the regions at x-1, x, x+1 (-1: none)
+    int2* d_mem_ent = nullptr;
+    int* d_mem_xs = nullptr;
+    int* d_leaf = nullptr;              // childless nodes (cube moments)
+    double* d_Sx = nullptr;             // [X slot][7][16][2][512]: reduced moments
+    double* d_Sm = nullptr;             // [M slot][7][2][512]: masses
+    double* d_Sxy = nullptr;            // [M slot][49][4][512]: the masses' (x, y) butterflies
     bool use_xy = false;                // the (x, y) table fits (its size is capped)
-    float2* d_Smf = nullptr;            // the same as double-float pairs
-    std::vector<int> tslot, tnodes;     // the gather's L-bar butterflies: slot per node, nodes per slot
-    int* d_tslot = nullptr;
-    int* d_tnodes = nullptr;
-    double* d_Tx = nullptr;             // [tslot][7][16][2][512]
-    double* d_Sbar = nullptr;           // [leaf slot][7][2][512]: the point-mass scatter's deferred x stage
+    float2* d_Smf = nullptr;            // the masses' table as double-float pairs
+    double* d_Tx = nullptr;             // [X slot][7][16][2][512]: reduced L-bar of real cells
+    double* d_Sbar = nullptr;           // [M slot][7][2][512]: the point-mass scatter's deferred x stage
     // chunked multipole gather items of the adjoint (modes 1 and 3, and the
     // default adjoint's merged list); they share d_part and d_chunk_ctr
     std::vector<int> itemsc_adj[4], itemsc_adj_node[4], itemc_adj_start[4], itemsc_adj_fast1;
@@ -613,8 +619,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     g->nbr.assign(static_cast<size_t>(n) * 27, int2{-1, K_NONE});
     g->ninfo.resize(n);
     std::map<std::tuple<int, long, long, long>, int> vindex;   // (level, q) -> virtual id
-    struct VNode { int level; long q[3]; int leaf; int d; };
+    struct VNode { int level; long q[3]; int leaf; int d; int2 e; };
     std::vector<VNode> vnodes;
+    // region of each neighbour position: a node (its index) or a virtual
+    // block (n + its virtual id); -1 outside the domain / without data
+    std::vector<int> nreg(static_cast<size_t>(n) * 27, -1);
     for (int i = 0; i < n; ++i) {
         const int l = desc->level[i];
         g->ninfo[i] = l | (g->is_leaf[i] << 8);
@@ -628,13 +637,17 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     long vq[3];
                     ot_status st = B.entry(l, q, false, &e, &vd, vq);
                     if (st != OT_OK) return st;
-                    g->nbr[static_cast<size_t>(i) * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = e;
+                    const size_t jj = static_cast<size_t>(i) * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                    g->nbr[jj] = e;
                     if ((e.y & 3) == K_VIRT) {
                         auto key = std::make_tuple(l, q[0], q[1], q[2]);
                         if (!vindex.count(key)) {
                             vindex[key] = static_cast<int>(vnodes.size());
-                            vnodes.push_back(VNode{l, {q[0], q[1], q[2]}, e.x, vd});
+                            vnodes.push_back(VNode{l, {q[0], q[1], q[2]}, e.x, vd, e});
                         }
+                        nreg[jj] = n + vindex[key];
+                    } else if ((e.y & 3) != K_NONE) {
+                        nreg[jj] = e.x;
                     }
                 }
     }
@@ -692,46 +705,117 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     }
 
     // --- prebuilt x butterflies ----------------------------------------------
-    // A node's classes may read their first transform stage from per-cell x
-    // butterflies when every position of its 27-neighbourhood lies in a node
-    // whose butterflies are built (multipole sources: non-leaf nodes; point
-    // masses: leaf nodes) or outside the domain.  Slots: index among the
-    // non-leaf, resp. leaf, nodes.
-    g->xslot.assign(n, -1);
-    g->n_xnonleaf = g->n_xleaf = 0;
-    for (int i = 0; i < n; ++i) g->xslot[i] = g->is_leaf[i] ? g->n_xleaf++ : g->n_xnonleaf++;
-    // the (x, y) table of the masses takes 0.8 MB per leaf sub-grid: built
-    // up to 8 GiB
-    g->use_xy = static_cast<double>(g->n_xleaf) * 49 * 4 * NCELL * sizeof(double) <= 8.0 * (1 << 30);
-    for (int i = 0; i < n; ++i) {
-        bool same = true;
-        for (int j = 0; j < 27 && same; ++j) {
-            const int k = g->nbr[static_cast<size_t>(i) * 27 + j].y & 3;
-            same = k == K_NONE || k == (g->is_leaf[i] ? K_LEAF : K_MULTI);
-        }
-        if (same) g->ninfo[i] |= g->is_leaf[i] ? NI_XMASS : NI_XMULTI;
-    }
-    // the adjoint's gather: butterflies of the targets' L-bar for every node
-    // of a level that has non-leaf nodes; a non-leaf source without virtual
-    // neighbours reads them
+    // A class's first transform stage along x at a position q -- the sum and
+    // the difference of the values a cells to either side, a = 1..7 -- is
+    // built per call for every cell of every region that can hold such a q:
+    // the same-level blocks of the 27-neighbourhoods of the nodes that read
+    // it.  A region is a node or a virtual block (a same-level block covered
+    // by a coarser leaf).  Two slot spaces:
+    //   M: the regions around leaf nodes -- the point masses of the leaf
+    //      targets' classes (leaf cells and virtual descendants; 0 in
+    //      refined blocks) and the point-mass scatter's deferred x stage;
+    //   X: the regions around non-leaf nodes -- the reduced moments of
+    //      non-leaf cells (0 elsewhere) for the non-leaf targets' classes,
+    //      and the reduced L-bar of real cells for the multipole gather.
+    // nslot[i][j] is the slot of node i's neighbour region j in the space of
+    // node i's kind (M for a leaf, X otherwise); every slot carries its
+    // region's 27 neighbour entries (snb) for the builder kernels.
     {
-        std::vector<char> lvl_nonleaf(MAXLEV, 0);
-        for (int i = 0; i < n; ++i)
-            if (!g->is_leaf[i]) lvl_nonleaf[desc->level[i]] = 1;
-        g->tslot.assign(n, -1);
-        g->tnodes.clear();
-        for (int i = 0; i < n; ++i)
-            if (lvl_nonleaf[desc->level[i]]) {
-                g->tslot[i] = static_cast<int>(g->tnodes.size());
-                g->tnodes.push_back(i);
-            }
+        const int nregions = n + g->nvirt;
+        std::vector<int> slotM(nregions, -1), slotX(nregions, -1), regM, regX;
         for (int i = 0; i < n; ++i) {
-            if (g->is_leaf[i]) continue;
-            bool real = true;
-            for (int j = 0; j < 27 && real; ++j) real = (g->nbr[static_cast<size_t>(i) * 27 + j].y & 3) != K_VIRT;
-            if (real) g->ninfo[i] |= NI_XGATHER;
+            std::vector<int>& slot = g->is_leaf[i] ? slotM : slotX;
+            std::vector<int>& reg = g->is_leaf[i] ? regM : regX;
+            for (int j = 0; j < 27; ++j) {
+                const int r = nreg[static_cast<size_t>(i) * 27 + j];
+                if (r >= 0 && slot[r] < 0) {
+                    slot[r] = static_cast<int>(reg.size());
+                    reg.push_back(r);
+                }
+            }
+        }
+        // the 27 neighbour entries of a region (a node's own; a virtual
+        // block's as the forward sees them); false if a position needs a
+        // virtual descendant deeper than the limit
+        auto region_row = [&](int r, int2* row) -> bool {
+            if (r < n) {
+                std::memcpy(row, &g->nbr[static_cast<size_t>(r) * 27], 27 * sizeof(int2));
+                return true;
+            }
+            const VNode& V = vnodes[r - n];
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const long q[3] = {V.q[0] + dx, V.q[1] + dy, V.q[2] + dz};
+                        int vd;
+                        long vq[3];
+                        int2 e;
+                        if (B.entry(V.level, q, false, &e, &vd, vq) != OT_OK) {
+                            g_last_error.clear();
+                            return false;
+                        }
+                        row[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = e;
+                    }
+            return true;
+        };
+        std::vector<char> okM(regM.size(), 1), okX(regX.size(), 1);
+        g->snbM.assign(regM.size() * 27, int2{-1, K_NONE});
+        g->snbX.assign(regX.size() * 27, int2{-1, K_NONE});
+        for (size_t k = 0; k < regM.size(); ++k) okM[k] = region_row(regM[k], &g->snbM[k * 27]);
+        for (size_t k = 0; k < regX.size(); ++k) okX[k] = region_row(regX[k], &g->snbX[k * 27]);
+        g->n_slotM = static_cast<int>(regM.size());
+        g->n_slotX = static_cast<int>(regX.size());
+        g->nslot.assign(static_cast<size_t>(n) * 27, -1);
+        for (int i = 0; i < n; ++i) {
+            const bool leaf = g->is_leaf[i];
+            bool ok = true;
+            for (int j = 0; j < 27; ++j) {
+                const int r = nreg[static_cast<size_t>(i) * 27 + j];
+                if (r < 0) continue;
+                const int sl = leaf ? slotM[r] : slotX[r];
+                g->nslot[static_cast<size_t>(i) * 27 + j] = sl;
+                ok = ok && (leaf ? okM[sl] : okX[sl]);
+            }
+            // every class of the node may read its first stage from the
+            // tables (multipole gather included for non-leaf sources)
+            if (ok) g->ninfo[i] |= leaf ? NI_XMASS : (NI_XMULTI | NI_XGATHER);
+        }
+        // the scatter's deferred x stage: each point-mass region of space M
+        // (leaf node or virtual block) collects, per cell, from the centres
+        // a cells to either side in x -- in the regions at x-1, x, x+1
+        g->mem_ent.clear();
+        g->mem_xs.clear();
+        for (size_t k = 0; k < regM.size(); ++k) {
+            const int r = regM[k];
+            int2 self;
+            long q[3];
+            int lvl;
+            if (r < n) {
+                if (!g->is_leaf[r]) continue;
+                self = int2{r, K_LEAF};
+                lvl = desc->level[r];
+                for (int a = 0; a < 3; ++a) q[a] = desc->coord[3 * r + a];
+            } else {
+                self = vnodes[r - n].e;
+                lvl = vnodes[r - n].level;
+                for (int a = 0; a < 3; ++a) q[a] = vnodes[r - n].q[a];
+            }
+            int xs[3] = {-1, -1, -1};
+            for (int dx = -1; dx <= 1; ++dx) {
+                const long qq[3] = {q[0] + dx, q[1], q[2]};
+                int rr = B.find(lvl, qq[0], qq[1], qq[2]);
+                if (rr < 0) {
+                    auto it = vindex.find(std::make_tuple(lvl, qq[0], qq[1], qq[2]));
+                    if (it != vindex.end()) rr = n + it->second;
+                }
+                if (rr >= 0 && slotM[rr] >= 0 && okM[slotM[rr]]) xs[dx + 1] = slotM[rr];
+            }
+            g->mem_ent.push_back(self);
+            g->mem_xs.insert(g->mem_xs.end(), xs, xs + 3);
         }
     }
+    // the (x, y) table of the masses takes 0.8 MB per slot: built up to 16 GiB
+    g->use_xy = static_cast<double>(g->n_slotM) * 49 * 4 * NCELL * sizeof(double) <= 16.0 * (1u << 30);
 
     // --- exact pair counts, FLOPs and per-item costs ------------------------
     // For each (parity, half) warp pattern and list entry: which of the 27
@@ -1489,9 +1573,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     g->n_cube = static_cast<int>(cube.size());
     UP(g->d_cube, cube);
     UP(g->d_leaf, cube);
-    UP(g->d_xslot, g->xslot);
-    UP(g->d_tslot, g->tslot);
-    UP(g->d_tnodes, g->tnodes);
+    UP(g->d_nslot, g->nslot);
+    UP(g->d_snbM, g->snbM);
+    UP(g->d_snbX, g->snbX);
+    UP(g->d_mem_ent, g->mem_ent);
+    UP(g->d_mem_xs, g->mem_xs);
     for (auto& L : g->m2m) {
         UP(L.d_parents, L.parents);
         UP(L.d_children, L.children);
@@ -1499,16 +1585,15 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_vmap, vmap);
 #undef UP
     if ((st = g->alloc(&g->d_Mhat, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
-    if ((st = g->alloc(&g->d_Sx, static_cast<size_t>(std::max(g->n_xnonleaf, 1)) * 7 * 32 * NCELL)) != OT_OK)
+    if ((st = g->alloc(&g->d_Sx, static_cast<size_t>(std::max(g->n_slotX, 1)) * 7 * 32 * NCELL)) != OT_OK)
         return st;
-    if ((st = g->alloc(&g->d_Sm, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
-    if ((st = g->alloc(&g->d_Tx, static_cast<size_t>(std::max<size_t>(g->tnodes.size(), 1)) * 7 * 32 * NCELL)) !=
-        OT_OK)
+    if ((st = g->alloc(&g->d_Sm, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Tx, static_cast<size_t>(std::max(g->n_slotX, 1)) * 7 * 32 * NCELL)) != OT_OK)
         return st;
-    if ((st = g->alloc(&g->d_Sbar, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
-    if ((st = g->alloc(&g->d_Smf, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Sbar, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
+    if ((st = g->alloc(&g->d_Smf, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if (g->use_xy &&
-        (st = g->alloc(&g->d_Sxy, static_cast<size_t>(std::max(g->n_xleaf, 1)) * 49 * 4 * NCELL)) != OT_OK)
+        (st = g->alloc(&g->d_Sxy, static_cast<size_t>(std::max(g->n_slotM, 1)) * 49 * 4 * NCELL)) != OT_OK)
         return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
@@ -1558,7 +1643,7 @@ static FwdParams fwd_params(ot_grid* g, const double* m, double* L, double* Lc, 
     p.status = g->d_status;
     p.child_of = g->d_child_of;
     p.Dv = g->d_Dv;
-    p.xslot = g->d_xslot;
+    p.nslot = g->d_nslot;
     for (int l = 0; l < MAXLEV; ++l) p.hinv[l] = g->hinv[l];
     return p;
 }
@@ -1596,21 +1681,21 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
     if ((mode & 1) && Lc) OT_CUDA(cudaMemsetAsync(Lc, 0, static_cast<size_t>(g->n) * 3 * NCELL * sizeof(double), s));
     FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
     // prebuilt x butterflies of the class transforms (FP64 contractions only)
-    if ((mode & 1) && g->precision != 2 && g->n_xnonleaf > 0) {
-        OT_CUDA(launch_xbutterfly_moments(g->d_nonleaf, g->n_nonleaf, g->d_nbr, g->d_Mhat, g->n, g->d_Sx, s));
+    if ((mode & 1) && g->precision != 2 && g->n_slotX > 0) {
+        OT_CUDA(launch_xbutterfly_moments(g->d_snbX, g->n_slotX, g->d_Mhat, g->n, g->d_Sx, s));
         p.Sx = g->d_Sx;
     }
-    if ((mode & 2) && g->n_xleaf > 0) {
-        OT_CUDA(launch_xbutterfly_masses(g->d_leaf, g->n_xleaf, g->d_nbr, m, g->n, g->d_Sm, s));
+    if ((mode & 2) && g->n_slotM > 0) {
+        OT_CUDA(launch_xbutterfly_masses(g->d_snbM, g->n_slotM, m, g->n, g->d_Sm, s));
         if (g->precision == 0) {
             p.Sm = g->d_Sm;
             if (g->use_xy) {
-                OT_CUDA(launch_xybutterfly_masses(g->d_leaf, g->n_xleaf, g->d_nbr, m, g->n, g->d_Sxy, s));
+                OT_CUDA(launch_xybutterfly_masses(g->d_snbM, g->n_slotM, m, g->n, g->d_Sxy, s));
                 p.Sxy = g->d_Sxy;
             }
         } else {
             // double-float point masses read the table as (hi, lo) pairs
-            OT_CUDA(launch_split_masses(g->d_Sm, g->d_Smf, static_cast<size_t>(g->n_xleaf) * 7 * 2 * NCELL, s));
+            OT_CUDA(launch_split_masses(g->d_Sm, g->d_Smf, static_cast<size_t>(g->n_slotM) * 7 * 2 * NCELL, s));
             p.Smf = g->d_Smf;
         }
     }
@@ -1735,13 +1820,12 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
         if (g->n_chunk_ctrs_adj > 0)
             OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs_adj) * sizeof(int), s));
         // the targets' L-bar x butterflies for the FP64 multipole gather
-        if (g->precision != 2 && !g->tnodes.empty()) {
-            OT_CUDA(launch_xbutterfly_lbar(g->d_tnodes, static_cast<int>(g->tnodes.size()), g->d_nbr, g->d_Lrbar, g->n,
-                                           g->d_Tx, s));
+        if (g->precision != 2 && g->n_slotX > 0) {
+            OT_CUDA(launch_xbutterfly_lbar(g->d_snbX, g->n_slotX, g->d_Lrbar, g->n, g->d_Tx, s));
             p.Tx = g->d_Tx;
         }
     }
-    p.tslot = g->d_tslot;
+    p.nslot = g->d_nslot;
     p.counter = g->d_counters + 1;
     p.nbr = g->d_nbr;
     p.vnbr = g->d_vnbr;
@@ -1787,17 +1871,16 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
         }
         // FP64 scatter: the x stage of x-complete classes deferred to a pass
         // over the leaf cells
-        const bool defer = g->n_xleaf > 0;
+        const bool defer = !g->mem_ent.empty();
         if (defer) {
-            OT_CUDA(cudaMemsetAsync(g->d_Sbar, 0, static_cast<size_t>(g->n_xleaf) * 7 * 2 * NCELL * sizeof(double), s));
+            OT_CUDA(cudaMemsetAsync(g->d_Sbar, 0, static_cast<size_t>(g->n_slotM) * 7 * 2 * NCELL * sizeof(double), s));
             p.Sbar = g->d_Sbar;
-            p.xslot = g->d_xslot;
         }
         OT_CUDA(cudaMemsetAsync(g->d_counters + 1, 0, sizeof(int), s));
         OT_CUDA(launch_adjoint(p, 4, true, g->wpb, grid_blocks(g, maxb), s));
         if (defer)
-            OT_CUDA(launch_xbutterfly_masses_adjoint(g->d_leaf, g->n_xleaf, g->d_nbr, g->d_xslot, g->d_Sbar, g->n,
-                                                     mbar, s));
+            OT_CUDA(launch_xbutterfly_masses_adjoint(g->d_mem_ent, g->d_mem_xs, static_cast<int>(g->mem_ent.size()),
+                                                     g->d_Sbar, g->n, mbar, s));
     } else {
         int maxb = g->maxb_adj[mode][g->wpb];
         if (g->precision == OT_PREC_DF64 && mode == 1) {
@@ -2193,10 +2276,10 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     p.part = g->d_part;
     p.chunk_ctr = g->d_chunk_ctr;
     // and the x butterflies the warm-up built from the same M and m
-    if (g->precision != 2 && g->n_xnonleaf > 0) p.Sx = g->d_Sx;
-    if (g->precision == 0 && g->n_xleaf > 0) p.Sm = g->d_Sm;
-    if (g->precision == 0 && g->n_xleaf > 0 && g->use_xy) p.Sxy = g->d_Sxy;
-    if (g->precision != 0 && g->n_xleaf > 0) p.Smf = g->d_Smf;
+    if (g->precision != 2 && g->n_slotX > 0) p.Sx = g->d_Sx;
+    if (g->precision == 0 && g->n_slotM > 0) p.Sm = g->d_Sm;
+    if (g->precision == 0 && g->n_slotM > 0 && g->use_xy) p.Sxy = g->d_Sxy;
+    if (g->precision != 0 && g->n_slotM > 0) p.Smf = g->d_Smf;
     if (g->n_chunk_ctrs > 0) {
         OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs) * sizeof(int), streams[0]));
         OT_CUDA(cudaStreamSynchronize(streams[0]));
