@@ -51,6 +51,9 @@ WORKLOADS = {
                     "then the adjoint"),
     "adaptive": ("adaptive octree, levels 3-6 (4,641 sub-grids, 4,061 leaves), n=1 polytrope with seeded centre, "
                  "refined where rho > 1e-3 rho_c, 2:1 balanced; both passes as batched launches, then the adjoint"),
+    "adaptive_small": ("adaptive octree, levels 3-6, the same recipe with a smaller star (R = 3 level-3 cells, 1,385 "
+                       "sub-grids), "
+                       "for profiler captures that must stay within a few GB; both passes, then the adjoint"),
 }
 
 
@@ -69,7 +72,8 @@ def parse():
                     help="skip the measurements beside the headline (per-launch roofline, per-sub-grid "
                          "launches, the 64^3 workload, double-float and centre-of-mass variants)")
     ap.add_argument("--tile", default=None, help="WxB: warps per block x blocks per SM (skips the autotuner)")
-    ap.add_argument("--workload", choices=["binary", "polytrope64", "adaptive", "integration"], default="binary")
+    ap.add_argument("--workload", choices=["binary", "polytrope64", "adaptive", "adaptive_small", "integration"],
+                    default="binary")
     return ap.parse_args()
 
 
@@ -192,6 +196,8 @@ def make_workload(name):
     import synth
     if name == "adaptive":
         tree, rho, _ = synth.config3()
+    elif name == "adaptive_small":
+        tree, rho, _ = synth.config3(radius_l3_cells=3.0)
     elif name == "binary":
         tree, rho = synth.config5_step(0)
     else:
