@@ -838,14 +838,17 @@ __device__ __forceinline__ void walk_mclasses_fwd_all(const int* __restrict__ li
         walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, c, t4, item);
 }
 
-template <int MODE, bool PAIRED, int EMU, bool NEAR = false, bool PM = true>
+template <int MODE, bool PAIRED, int EMU, bool NEAR = false, bool PM = true, bool NEG = false>
 __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int len, bool angular,
                                              int tx, int ty, int tz, const int2* __restrict__ s_nb,
                                              const FwdParams& p, double (&a)[16], double (&c)[3],
                                              double (&t4)[9], DFAcc& f, int item) {
     for (int k = 0; k < len; ++k) {
         const int po = __ldg(list + k);
-        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        // NEG (single walks only): the list's offsets negated, the other
+        // members of its +-o pairs
+        const int sg = NEG ? -1 : 1;
+        const int ox = sg * ((po & 0xff) - 8), oy = sg * (((po >> 8) & 0xff) - 8), oz = sg * (((po >> 16) & 0xff) - 8);
         const int px = tx + ox, py = ty + oy, pz = tz + oz;   // in [-7, 14]
         const int mx = tx - ox, my = ty - oy, mz = tz - oz;
         const int2 ep = s_nb[nb_index(px, py, pz)];
@@ -1211,6 +1214,18 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             if (level == 0) {
                 walk_forward<MODE, true, EMU>(p.L.lists + p.L.root_off + ch.lo(p.L.root_len), ch.n(p.L.root_len),
                                               !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
+            } else if (MODE == 1 && leafT && !(EMU & 2)) {
+                // a leaf target's multipole sources lie in refined neighbours,
+                // mostly on one side: the two members of a +-o pair run as
+                // single entries, each only where some lane has a source
+                const int* lf = p.L.lists + par * p.L.far_len;
+                const int ns = p.L.far_len - p.L.far_pairs;
+                walk_forward<MODE, false, EMU>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), false, tx, ty, tz,
+                                               s_nb[warp], p, a, c, t4, f, it);
+                walk_forward<MODE, false, EMU, false, true, true>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs),
+                                                                  false, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
+                walk_forward<MODE, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), false, tx, ty, tz,
+                                               s_nb[warp], p, a, c, t4, f, it);
             } else {
                 const int* lf = p.L.lists + par * p.L.far_len;
                 const int ns = p.L.far_len - p.L.far_pairs;
@@ -1219,7 +1234,7 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
                 walk_forward<MODE, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), !leafT, tx, ty, tz,
                                                s_nb[warp], p, a, c, t4, f, it);
             }
-            if (leafT)
+            if (leafT && (MODE & 2))
                 walk_forward<MODE, true, EMU, true>(p.L.lists + p.L.near_off + ch.lo(p.L.near_len), ch.n(p.L.near_len),
                                                     false, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
         }
@@ -3363,37 +3378,56 @@ cudaError_t launch_xbutterfly_moments(const int2* snb, int n_slots, const double
     return counted(cudaGetLastError());
 }
 
-// (x, y) butterflies of the masses: for every leaf cell c and a, b = 1..7,
-// the four transforms over x and y of the masses at c + (+-a, +-b, 0),
-// out[pi] = sum_i (-1)^|i & pi| v_i (i, pi: bit 0 x negated / x odd, bit 1 y)
+// (x, y) butterflies of the masses: for every cell c of a slot's region and
+// a, b = 1..7, the four transforms over x and y of the masses at
+// c + (+-a, +-b, 0), out[pi] = sum_i (-1)^|i & pi| v_i (i, pi: bit 0 x
+// negated / x odd, bit 1 y).  A block of 256 threads covers four z layers
+// of one slot's region: it stages the masses of those layers in the 3 x 3
+// regions around it in shared memory once, then each thread runs all 49
+// (a, b) of its cell, every store of a warp covering 32 consecutive cells.
 __global__ void xybutterfly_masses_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ m,
                                           int n_nodes, double* __restrict__ Sxy) {
-    const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (gid >= 49LL * NCELL * n_slots) return;
-    const int cell = static_cast<int>(gid % NCELL);
-    const int ab = static_cast<int>((gid / NCELL) % 49);
-    const int slot = static_cast<int>(gid / (49 * NCELL));
-    const int a = ab / 7 + 1, b = ab % 7 + 1;
-    const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
-    const int2* nb = snb + static_cast<size_t>(slot) * 27;
-    double v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int sx = (i & 1) ? x - a : x + a, sy = (i & 2) ? y - b : y + b;
-        v[i] = mass_at(m, __ldg(nb + nb_index(sx, sy, z)), n_nodes, sx, sy, z);
+    __shared__ double sm[9][256];
+    const long long first = static_cast<long long>(blockIdx.x) * blockDim.x;
+    const int slot = static_cast<int>(first / NCELL);
+    const int z0 = static_cast<int>(first % NCELL) >> 6;          // 0 or 4
+    if (slot < n_slots) {
+        const int2* nb = snb + static_cast<size_t>(slot) * 27 + 9;    // the z = 0 layer of the regions
+        for (int t = threadIdx.x; t < 9 * 256; t += blockDim.x) {
+            const int r = t >> 8, c = t & 255;
+            sm[r][c] = mass_at(m, __ldg(nb + r), n_nodes, c & 7, (c >> 3) & 7, z0 + (c >> 6));
+        }
     }
-    const double u0 = v[0] + v[1], u1 = v[0] - v[1], u2 = v[2] + v[3], u3 = v[2] - v[3];
-    double* out = Sxy + static_cast<size_t>(slot * 49 + ab) * 4 * NCELL + cell;
-    out[0] = u0 + u2;
-    out[NCELL] = u1 + u3;
-    out[2 * NCELL] = u0 - u2;
-    out[3 * NCELL] = u1 - u3;
+    __syncthreads();
+    const long long gid = first + threadIdx.x;
+    if (gid >= 1LL * NCELL * n_slots) return;
+    const int cell = static_cast<int>(gid % NCELL);
+    const int x = cell & 7, y = (cell >> 3) & 7, zl = (cell >> 6) - z0;
+    double* out = Sxy + static_cast<size_t>(slot) * 49 * 4 * NCELL + cell;
+#pragma unroll 1
+    for (int a = 1; a <= 7; ++a) {
+#pragma unroll
+        for (int b = 1; b <= 7; ++b) {
+            double v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int sx = (i & 1) ? x - a : x + a, sy = (i & 2) ? y - b : y + b;
+                v[i] = sm[((sx + 8) >> 3) + 3 * ((sy + 8) >> 3)][(sx & 7) + 8 * (sy & 7) + 64 * zl];
+            }
+            const double u0 = v[0] + v[1], u1 = v[0] - v[1], u2 = v[2] + v[3], u3 = v[2] - v[3];
+            double* o = out + static_cast<size_t>((a - 1) * 7 + b - 1) * 4 * NCELL;
+            o[0] = u0 + u2;
+            o[NCELL] = u1 + u3;
+            o[2 * NCELL] = u0 - u2;
+            o[3 * NCELL] = u1 - u3;
+        }
+    }
 }
 
 cudaError_t launch_xybutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sxy,
                                       cudaStream_t s) {
     if (n_slots == 0) return cudaSuccess;
-    xybutterfly_masses_kernel<<<blocks_for(49LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, m, n_nodes, Sxy);
+    xybutterfly_masses_kernel<<<blocks_for(1LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, m, n_nodes, Sxy);
     return counted(cudaGetLastError());
 }
 

@@ -824,6 +824,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // paired / single entries.  Segments: 0 far, 1 near, 2 root.
     const int seg_len[3] = {g->far_len, g->near_len, g->root_len};
     std::vector<uint32_t> mask[16][3];
+    std::vector<uint32_t> maskside[16][3][2];   // the neighbours each member of an entry reaches
     std::vector<uint8_t> pflag[16][3];
     long long cnt[3][2][27];   // [segment][paired][neighbour]: pairs over all 512 cells
     std::memset(cnt, 0, sizeof(cnt));
@@ -833,12 +834,14 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             const int* lst = (sg == 0) ? &g->lists[par * g->far_len]
                            : (sg == 1) ? &g->lists[8 * g->far_len] : &g->lists[8 * g->far_len + g->near_len];
             mask[ph][sg].resize(seg_len[sg]);
+            maskside[ph][sg][0].resize(seg_len[sg]);
+            maskside[ph][sg][1].resize(seg_len[sg]);
             pflag[ph][sg].resize(seg_len[sg]);
             for (int k = 0; k < seg_len[sg]; ++k) {
                 const int po = lst[k];
                 const int paired = (po >> 24) & 1;
                 const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
-                uint32_t m = 0;
+                uint32_t m = 0, ms[2] = {0, 0};
                 for (int lane = 0; lane < 32; ++lane) {
                     const int tx = (par & 1) + 2 * (lane & 3), ty = ((par >> 1) & 1) + 2 * ((lane >> 2) & 3),
                               tz = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
@@ -847,10 +850,13 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         const int nb = ((tx + sgn * ox + 8) >> 3) + 3 * ((ty + sgn * oy + 8) >> 3) +
                                        9 * ((tz + sgn * oz + 8) >> 3);
                         m |= 1u << nb;
+                        ms[side] |= 1u << nb;
                         cnt[sg][paired][nb]++;
                     }
                 }
                 mask[ph][sg][k] = m;
+                maskside[ph][sg][0][k] = ms[0];
+                maskside[ph][sg][1][k] = ms[1];
                 pflag[ph][sg][k] = static_cast<uint8_t>(paired);
             }
         }
@@ -1039,6 +1045,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     flops_fwd += std::llround(CFL[desc->level[i] == 0 ? 3 : 2][j]);
                     alg_fwd += COP[desc->level[i] == 0 ? 3 : 2][j];
                     alg_fwd_multi += COP[desc->level[i] == 0 ? 3 : 2][j];
+                } else if (desc->level[i] > 0) {
+                    // a leaf target's multipole sources, every pair a single entry
+                    flops_fwd += 140 * (cpf + csf);
+                    alg_fwd += 70.0 * (cpf + csf);
+                    alg_fwd_multi += 70.0 * (cpf + csf);
                 } else {
                     flops_fwd += 86 * cpf + 140 * csf;
                     alg_fwd += 51.0 * cpf + 70.0 * csf;
@@ -1089,8 +1100,16 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 const std::vector<uint8_t>& pf = pflag[ph][sg];
                 for (size_t k = 0; k < mk.size(); ++k) {
                     if (mk[k] & mm) {
-                        if (sg == 1) cost[2] += 8 * 18;     // refined near source: 8 paired contractions
-                        else cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
+                        if (sg == 1) {
+                            cost[2] += 8 * 18;     // refined near source: 8 paired contractions
+                        } else if (leaf && desc->level[i] > 0) {
+                            // a leaf target's multipole sources: the members of a
+                            // pair run as single entries, each where it reaches one
+                            cost[1] += ((maskside[ph][sg][0][k] & mm) ? 70 : 0) +
+                                       ((pf[k] && (maskside[ph][sg][1][k] & mm)) ? 70 : 0);
+                        } else {
+                            cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
+                        }
                     }
                     if (mk[k] & mo) {
                         cost[2] += pf[k] ? 18 : 16;
