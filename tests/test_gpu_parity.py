@@ -532,6 +532,31 @@ def test_completion_study_results_and_stats(ot, orc, mechanism):
     assert stats["wall_ms"] > 0
 
 
+def test_launch_count_direct_and_graphed(ot):
+    """ot_launch_count: the forward and the adjoint count the same kernels
+    whether their calls launch them directly or replay them from CUDA graphs
+    (recording a graph counts none)."""
+    tree = _small_adaptive()
+    rho = dev(synth.uniform_random_density(tree, seed=140))
+    Lbar = dev(np.random.default_rng(141).standard_normal((tree.n, 20, 512)))
+    counts = []
+    for graph in (False, True):
+        g = ot.OTGrid.from_tree(tree)
+        g.set_schedule(ot.OT_SCHED_PERSISTENT, 4, 0, graph)
+        M, m = g.moments(rho)
+        L, Lc = g.interactions(M, m)           # records the graphs when enabled
+        Mb, mb = g.backward(Lbar)
+        torch.cuda.synchronize()
+        c0 = ot.launch_count()
+        for _ in range(3):
+            g.interactions(M, m, L, Lc)
+            g.backward(Lbar, Mb, mb)
+        torch.cuda.synchronize()
+        counts.append(ot.launch_count() - c0)
+        g.close()
+    assert counts[0] == counts[1] > 0 and counts[0] % 3 == 0, counts
+
+
 def test_autotune_cache(ot, tmp_path):
     """A tuned tile shape is stored under the tree's and device's key and
     applied without timing by the next grid on the same tree."""
