@@ -209,6 +209,10 @@ constexpr int NI_XMASS = 1 << 10;
 // bit 11: a non-leaf source whose multipole gather may read the targets'
 // prebuilt L-bar x butterflies (no virtual neighbour)
 constexpr int NI_XGATHER = 1 << 11;
+// bits 13-14: the axis along which a node's target items split their two
+// halves (0 z, 1 x, 2 y): the axis of the node's faces whose neighbours hold
+// no source of its passes, so that a warp's lanes reach such a face together
+constexpr int NI_SLAB_SHIFT = 13;
 
 // launchers (ot_kernels.cu)
 cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid,

@@ -117,6 +117,17 @@ __device__ __forceinline__ void lane_cell(int lane, int par, int half, int& x, i
     z = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
 }
 
+// the same with the item's two halves split along axis `slab` (0 z, 1 x,
+// 2 y): the warp's 32 cells are 2 layers of that axis times 4 x 4 of the
+// others, all of one parity
+__device__ __forceinline__ void lane_cell_slab(int lane, int par, int half, int slab, int& x, int& y, int& z) {
+    const int u = lane & 3, v = (lane >> 2) & 3, w = 2 * half + (lane >> 4);
+    const int cx = slab == 1 ? w : u, cy = slab == 2 ? w : (slab == 1 ? u : v), cz = slab == 0 ? w : v;
+    x = (par & 1) + 2 * cx;
+    y = ((par >> 1) & 1) + 2 * cy;
+    z = ((par >> 2) & 1) + 2 * cz;
+}
+
 // ---------------------------------------------------------------------------
 // forward stencil walk
 // ---------------------------------------------------------------------------
@@ -1105,7 +1116,7 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
         const int level = info & 0xff;
         const bool leafT = (info >> 8) & 1;
         int tx, ty, tz;
-        lane_cell(lane, par, half, tx, ty, tz);
+        lane_cell_slab(lane, par, half, (info >> NI_SLAB_SHIFT) & 3, tx, ty, tz);
         double a[16], c[3], t4[9];
         DFAcc f;
         df_zero(f);
@@ -1913,7 +1924,7 @@ template <bool EMU, class P>
 __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict__ nbr, const int* __restrict__ ninfo, int2* s_nb,
                              int* s_sl, int node, int par, int half, int lane, int it) {
     int tx, ty, tz;
-    lane_cell(lane, par, half, tx, ty, tz);
+    lane_cell_slab(lane, par, half, (__ldg(ninfo + node) >> NI_SLAB_SHIFT) & 3, tx, ty, tz);
     double lb[16];
     float lbh[16], lbl[16];
     bool nz = false;

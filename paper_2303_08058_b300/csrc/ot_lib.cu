@@ -146,6 +146,33 @@ inline uint64_t node_key(int l, int x, int y, int z) {
            static_cast<uint64_t>(z);
 }
 
+// the cell a lane of a target item holds (the kernels' lane_cell_slab)
+inline void lane_cell_host(int lane, int par, int half, int slab, int& x, int& y, int& z) {
+    const int u = lane & 3, v = (lane >> 2) & 3, w = 2 * half + (lane >> 4);
+    const int cx = slab == 1 ? w : u, cy = slab == 2 ? w : (slab == 1 ? u : v), cz = slab == 0 ? w : v;
+    x = (par & 1) + 2 * cx;
+    y = ((par >> 1) & 1) + 2 * cy;
+    z = ((par >> 2) & 1) + 2 * cz;
+}
+
+// The axis along which a node's target items split their halves (0 z, 1 x,
+// 2 y): the one with the most faces whose neighbour holds no source of the
+// node's main pass (refined or outside the domain for a leaf; leaf, virtual
+// or outside for a non-leaf node), z on ties.  Lanes then reach such a face
+// together, and entries that only reach it are skipped by whole warps.
+inline int slab_axis(const int2* nb27, bool leaf) {
+    static const int face[6] = {12, 14, 10, 16, 4, 22};   // -x +x -y +y -z +z
+    int bad[3] = {0, 0, 0};                               // x, y, z
+    for (int f = 0; f < 6; ++f) {
+        const int k = nb27[face[f]].y & 3;
+        const bool none = leaf ? (k == K_MULTI || k == K_NONE) : (k != K_MULTI);
+        if (none) bad[f / 2]++;
+    }
+    if (bad[0] > bad[2] && bad[0] >= bad[1]) return 1;
+    if (bad[1] > bad[2] && bad[1] > bad[0]) return 2;
+    return 0;
+}
+
 
 }  // namespace
 
@@ -814,6 +841,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             g->mem_xs.insert(g->mem_xs.end(), xs, xs + 3);
         }
     }
+    for (int i = 0; i < n; ++i)
+        g->ninfo[i] |= slab_axis(&g->nbr[static_cast<size_t>(i) * 27], g->is_leaf[i]) << NI_SLAB_SHIFT;
     // the (x, y) table of the masses takes 0.8 MB per slot: built up to 16 GiB
     g->use_xy = static_cast<double>(g->n_slotM) * 49 * 4 * NCELL * sizeof(double) <= 16.0 * (1u << 30);
 
@@ -823,8 +852,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // per neighbour how many (cell, source) pairs land there, split by
     // paired / single entries.  Segments: 0 far, 1 near, 2 root.
     const int seg_len[3] = {g->far_len, g->near_len, g->root_len};
-    std::vector<uint32_t> mask[16][3];
-    std::vector<uint32_t> maskside[16][3][2];   // the neighbours each member of an entry reaches
+    // [slab][pattern][segment]: the masks for each of the three lane layouts
+    std::vector<uint32_t> mask[3][16][3];
+    std::vector<uint32_t> maskside[3][16][3][2];   // the neighbours each member of an entry reaches
     std::vector<uint8_t> pflag[16][3];
     long long cnt[3][2][27];   // [segment][paired][neighbour]: pairs over all 512 cells
     std::memset(cnt, 0, sizeof(cnt));
@@ -833,30 +863,34 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         for (int sg = 0; sg < 3; ++sg) {
             const int* lst = (sg == 0) ? &g->lists[par * g->far_len]
                            : (sg == 1) ? &g->lists[8 * g->far_len] : &g->lists[8 * g->far_len + g->near_len];
-            mask[ph][sg].resize(seg_len[sg]);
-            maskside[ph][sg][0].resize(seg_len[sg]);
-            maskside[ph][sg][1].resize(seg_len[sg]);
+            for (int sl = 0; sl < 3; ++sl) {
+                mask[sl][ph][sg].resize(seg_len[sg]);
+                maskside[sl][ph][sg][0].resize(seg_len[sg]);
+                maskside[sl][ph][sg][1].resize(seg_len[sg]);
+            }
             pflag[ph][sg].resize(seg_len[sg]);
             for (int k = 0; k < seg_len[sg]; ++k) {
                 const int po = lst[k];
                 const int paired = (po >> 24) & 1;
                 const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
-                uint32_t m = 0, ms[2] = {0, 0};
-                for (int lane = 0; lane < 32; ++lane) {
-                    const int tx = (par & 1) + 2 * (lane & 3), ty = ((par >> 1) & 1) + 2 * ((lane >> 2) & 3),
-                              tz = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
-                    for (int side = 0; side <= paired; ++side) {
-                        const int sgn = side ? -1 : 1;
-                        const int nb = ((tx + sgn * ox + 8) >> 3) + 3 * ((ty + sgn * oy + 8) >> 3) +
-                                       9 * ((tz + sgn * oz + 8) >> 3);
-                        m |= 1u << nb;
-                        ms[side] |= 1u << nb;
-                        cnt[sg][paired][nb]++;
+                for (int sl = 0; sl < 3; ++sl) {
+                    uint32_t m = 0, ms[2] = {0, 0};
+                    for (int lane = 0; lane < 32; ++lane) {
+                        int tx, ty, tz;
+                        lane_cell_host(lane, par, half, sl, tx, ty, tz);
+                        for (int side = 0; side <= paired; ++side) {
+                            const int sgn = side ? -1 : 1;
+                            const int nb = ((tx + sgn * ox + 8) >> 3) + 3 * ((ty + sgn * oy + 8) >> 3) +
+                                           9 * ((tz + sgn * oz + 8) >> 3);
+                            m |= 1u << nb;
+                            ms[side] |= 1u << nb;
+                            if (sl == 0) cnt[sg][paired][nb]++;
+                        }
                     }
+                    mask[sl][ph][sg][k] = m;
+                    maskside[sl][ph][sg][0][k] = ms[0];
+                    maskside[sl][ph][sg][1][k] = ms[1];
                 }
-                mask[ph][sg][k] = m;
-                maskside[ph][sg][0][k] = ms[0];
-                maskside[ph][sg][1][k] = ms[1];
                 pflag[ph][sg][k] = static_cast<uint8_t>(paired);
             }
         }
@@ -871,7 +905,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     // 3 the same, root.
     const int cseg_len[4] = {g->Lh.cf_stride, g->Lh.cn_z[7] + g->Lh.cn_pairs, g->Lh.mf_stride,
                              g->Lh.mr_z[7] + g->Lh.mr_pairs};
-    std::vector<uint32_t> cmask[16][4];
+    std::vector<uint32_t> cmask[3][16][4];
     std::vector<int> ccost_f[4], ccost_s[4], cmem[4];
     double cfl_f[4][27], cfl_s[4][27], cop_f[4][27], cop_s[4][27];   // FLOPs; FP64 instructions
     // the forward's figures for a node whose x-complete classes read the
@@ -904,7 +938,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             const int off = cg == 0 ? g->Lh.cf_off + par * g->Lh.cf_stride : cg == 1 ? g->Lh.cn_off
                           : cg == 2 ? g->Lh.mf_off + par * g->Lh.mf_stride : g->Lh.mr_off;
             const int* lst = &g->lists[off];
-            cmask[ph][cg].resize(cseg_len[cg]);
+            for (int sl = 0; sl < 3; ++sl) cmask[sl][ph][cg].resize(cseg_len[cg]);
             for (int k = 0; k < cseg_len[cg]; ++k) {
                 const int e = lst[k];
                 std::vector<std::array<int, 3>> mem;
@@ -966,10 +1000,20 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 ccost_sx[cg][k] = csx;
                 ccost_s[cg][k] = cs;
                 cmem[cg][k] = static_cast<int>(mem.size());
+                for (int sl = 1; sl < 3; ++sl) {
+                    uint32_t ml = 0;
+                    for (int lane = 0; lane < 32; ++lane) {
+                        int tx, ty, tz;
+                        lane_cell_host(lane, par, half, sl, tx, ty, tz);
+                        for (auto& o : mem)
+                            ml |= 1u << (((tx + o[0] + 8) >> 3) + 3 * ((ty + o[1] + 8) >> 3) + 9 * ((tz + o[2] + 8) >> 3));
+                    }
+                    cmask[sl][ph][cg][k] = ml;
+                }
                 uint32_t m = 0;
                 for (int lane = 0; lane < 32; ++lane) {
-                    const int tx = (par & 1) + 2 * (lane & 3), ty = ((par >> 1) & 1) + 2 * ((lane >> 2) & 3),
-                              tz = ((par >> 2) & 1) + 2 * (2 * half + (lane >> 4));
+                    int tx, ty, tz;
+                    lane_cell_host(lane, par, half, 0, tx, ty, tz);
                     for (auto& o : mem) {
                         const int nb = ((tx + o[0] + 8) >> 3) + 3 * ((ty + o[1] + 8) >> 3) + 9 * ((tz + o[2] + 8) >> 3);
                         m |= 1u << nb;
@@ -983,7 +1027,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         cop_sx[cg][nb] += static_cast<double>(csx) / mem.size();
                     }
                 }
-                cmask[ph][cg][k] = m;
+                cmask[0][ph][cg][k] = m;
             }
         }
     }
@@ -1093,10 +1137,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             if (mv >> j & 1u) pairs_virt += cp + cs;
         }
         g->node_item_start[i] = static_cast<int>(node_order_items.size());
+        const int sl = (g->ninfo[i] >> NI_SLAB_SHIFT) & 3;   // the node's item lane layout
         for (int ph = 0; ph < 16; ++ph) {
             long long cost[3] = {0, 0, 0};   // [1] multipole class, [2] point-mass class
             auto scan = [&](int sg) {
-                const std::vector<uint32_t>& mk = mask[ph][sg];
+                const std::vector<uint32_t>& mk = mask[sl][ph][sg];
                 const std::vector<uint8_t>& pf = pflag[ph][sg];
                 for (size_t k = 0; k < mk.size(); ++k) {
                     if (mk[k] & mm) {
@@ -1105,8 +1150,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         } else if (leaf && desc->level[i] > 0) {
                             // a leaf target's multipole sources: the members of a
                             // pair run as single entries, each where it reaches one
-                            cost[1] += ((maskside[ph][sg][0][k] & mm) ? 70 : 0) +
-                                       ((pf[k] && (maskside[ph][sg][1][k] & mm)) ? 70 : 0);
+                            cost[1] += ((maskside[sl][ph][sg][0][k] & mm) ? 70 : 0) +
+                                       ((pf[k] && (maskside[sl][ph][sg][1][k] & mm)) ? 70 : 0);
                         } else {
                             cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
                         }
@@ -1131,8 +1176,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 mo = mo_keep;
                 long long cost_s = cost[2];    // refined near sources
                 for (int cg = 0; cg < 2; ++cg)
-                    for (size_t k = 0; k < cmask[ph][cg].size(); ++k)
-                        if (cmask[ph][cg][k] & mo) {
+                    for (size_t k = 0; k < cmask[sl][ph][cg].size(); ++k)
+                        if (cmask[sl][ph][cg][k] & mo) {
                             cost[2] += CCF[cg][k];
                             cost_s += xnode ? ccost_sx[cg][k] : ccost_s[cg][k];
                             lanes += 32;
@@ -1143,8 +1188,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 // multipole sources by class, point masses (leaf neighbours)
                 // over the far list
                 const int cgm = desc->level[i] == 0 ? 3 : 2;
-                for (size_t k = 0; k < cmask[ph][cgm].size(); ++k)
-                    if (cmask[ph][cgm][k] & mm) {
+                for (size_t k = 0; k < cmask[sl][ph][cgm].size(); ++k)
+                    if (cmask[sl][ph][cgm][k] & mm) {
                         cost[1] += CCF[cgm][k];
                         lanes += 32;
                         padded += 32 * cmem[cgm][k];
@@ -1275,17 +1320,17 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         for (int ph = 0; ph < 16; ++ph) {
             long long cst = 0;
             if (leaf) {
-                for (size_t k = 0; k < mask[ph][s1].size(); ++k)
-                    if (mask[ph][s1][k] & (tv | tw)) cst += pflag[ph][s1][k] ? 32 : 16;
+                for (size_t k = 0; k < mask[0][ph][s1].size(); ++k)
+                    if (mask[0][ph][s1][k] & (tv | tw)) cst += pflag[ph][s1][k] ? 32 : 16;
             } else {
                 const int cgm = lvl == 0 ? 3 : 2;
                 const bool xs = !virt && (g->ninfo[i] & NI_XGATHER);
-                for (size_t k = 0; k < cmask[ph][cgm].size(); ++k)
-                    if (cmask[ph][cgm][k] & tv) cst += xs ? ccost_sx[cgm][k] : ccost_s[cgm][k];
+                for (size_t k = 0; k < cmask[0][ph][cgm].size(); ++k)
+                    if (cmask[0][ph][cgm][k] & tv) cst += xs ? ccost_sx[cgm][k] : ccost_s[cgm][k];
             }
             if (leaf)
-                for (size_t k = 0; k < mask[ph][1].size(); ++k)
-                    if (mask[ph][1][k] & (tl | tw)) cst += 32;
+                for (size_t k = 0; k < mask[0][ph][1].size(); ++k)
+                    if (mask[0][ph][1][k] & (tl | tw)) cst += 32;
             if (cst == 0) continue;
             ops_adj += 32 * cst;
             if (!leaf) {
