@@ -265,10 +265,15 @@ def launch_breakdown(g, work, stream, flush=None):
 NOMINAL_FP64_TFLOPS = 1.25
 NOMINAL_SM_MHZ = 2032.0
 
-# DRAM bytes (read + written) per launch of the dominant kernel, from an ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of that kernel on the
-# named workload; None until captured for the kernel as it is now.
-DRAM_BYTES = {}
+# DRAM bytes (read + written) per launch of a launch's kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of that
+# kernel as it is now, keyed by (workload, launch, tile); a key not here
+# reports null.
+DRAM_BYTES = {
+    ("binary", "multipole", (8, 1)): 35_819_085_056 + 567_903_232,
+    ("polytrope64", "multipole", (8, 1)): 126_960_128 + 34_222_080,
+    ("polytrope64", "multipole", (8, 2)): 219_168_768 + 40_501_248,
+}
 
 
 def fp64_peak(ot, dev, stream):
@@ -297,6 +302,7 @@ def roofline_block(launches, peak_inst, probe_cfg, sm_mhz, workload, info, pairs
     """The dominant launch's roofline in FP64 pipe thread-instructions per
     second against the probe's measured rate, with the nominal and the
     survey's per-pair FLOP counts beside it."""
+    tile = (info["warps_per_block"], info["blocks_per_sm"])
     dom = max(launches, key=lambda k: launches[k]["ms"])
     L = launches[dom]
     peak = peak_inst / 1e12
@@ -305,11 +311,12 @@ def roofline_block(launches, peak_inst, probe_cfg, sm_mhz, workload, info, pairs
     # the angular term at non-leaf targets), a point-mass pair 20 FMAs; the
     # adjoint the same; 2 flops per FMA
     sec8d_fwd = 2 * (84 * info["pairs_multipole"] + 40 * info["pairs_angular"] + 20 * info["pairs_monopole"])
-    traffic = DRAM_BYTES.get((workload, dom))
+    traffic = DRAM_BYTES.get((workload, dom, tile))
     return {
         "bound": "alu", "kernel": L["kernel"], "launch": dom,
         "achieved": L["achieved"], "peak": peak, "unit": "Tinst/s", "frac": L["achieved"] / peak,
-        "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+        "traffic": traffic,
+        "traffic_unit": ("bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, tile %dx%d)" % tile),
         "unit_note": ("FP64 pipe thread-instructions per second (one per FMA, add or multiply); achieved: the "
                       "algorithmic FP64 instructions of the launch's in-domain pairs (library count) over the "
                       "CUDA-event time of its ABI call (the launch and its O(cells) prologue kernels)"),

@@ -3394,44 +3394,52 @@ cudaError_t launch_xbutterfly_moments(const int2* snb, int n_slots, const double
 // c + (+-a, +-b, 0), out[pi] = sum_i (-1)^|i & pi| v_i (i, pi: bit 0 x
 // negated / x odd, bit 1 y).  A block of 256 threads covers four z layers
 // of one slot's region: it stages the masses of those layers in the 3 x 3
-// regions around it in shared memory once, then each thread runs all 49
-// (a, b) of its cell, every store of a warp covering 32 consecutive cells.
+// regions around it in shared memory once; per a it then forms the x stage
+// (the sum and the difference of the masses a cells to either side in x)
+// at the rows y - 7 .. y + 14 once, shared by the seven b of every cell, and
+// each thread runs the y stage of its cell, every store of a warp covering
+// 32 consecutive cells.  The operations per output are those of the
+// transform written out, so the table is the same to the bit.
 __global__ void xybutterfly_masses_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ m,
                                           int n_nodes, double* __restrict__ Sxy) {
+    constexpr int ROWS = 22;                  // y' = -7 .. 14
     __shared__ double sm[9][256];
+    __shared__ double sx[2][4][ROWS][8];      // [sum, difference][z layer][y' + 7][x]
     const long long first = static_cast<long long>(blockIdx.x) * blockDim.x;
     const int slot = static_cast<int>(first / NCELL);
+    if (slot >= n_slots) return;              // whole blocks: a slot is two blocks of 256 cells
     const int z0 = static_cast<int>(first % NCELL) >> 6;          // 0 or 4
-    if (slot < n_slots) {
-        const int2* nb = snb + static_cast<size_t>(slot) * 27 + 9;    // the z = 0 layer of the regions
-        for (int t = threadIdx.x; t < 9 * 256; t += blockDim.x) {
-            const int r = t >> 8, c = t & 255;
-            sm[r][c] = mass_at(m, __ldg(nb + r), n_nodes, c & 7, (c >> 3) & 7, z0 + (c >> 6));
-        }
+    const int2* nb = snb + static_cast<size_t>(slot) * 27 + 9;    // the z = 0 layer of the regions
+    for (int t = threadIdx.x; t < 9 * 256; t += blockDim.x) {
+        const int r = t >> 8, c = t & 255;
+        sm[r][c] = mass_at(m, __ldg(nb + r), n_nodes, c & 7, (c >> 3) & 7, z0 + (c >> 6));
     }
     __syncthreads();
-    const long long gid = first + threadIdx.x;
-    if (gid >= 1LL * NCELL * n_slots) return;
-    const int cell = static_cast<int>(gid % NCELL);
+    const int cell = static_cast<int>((first + threadIdx.x) % NCELL);
     const int x = cell & 7, y = (cell >> 3) & 7, zl = (cell >> 6) - z0;
     double* out = Sxy + static_cast<size_t>(slot) * 49 * 4 * NCELL + cell;
 #pragma unroll 1
     for (int a = 1; a <= 7; ++a) {
+        for (int t = threadIdx.x; t < 4 * ROWS * 8; t += blockDim.x) {
+            const int px = t & 7, row = (t >> 3) % ROWS, pz = t / (ROWS * 8);
+            const int py = row - 7, xp = px + a, xm = px - a;
+            const double vp = sm[((xp + 8) >> 3) + 3 * ((py + 8) >> 3)][(xp & 7) + 8 * (py & 7) + 64 * pz];
+            const double vm = sm[((xm + 8) >> 3) + 3 * ((py + 8) >> 3)][(xm & 7) + 8 * (py & 7) + 64 * pz];
+            sx[0][pz][row][px] = vp + vm;
+            sx[1][pz][row][px] = vp - vm;
+        }
+        __syncthreads();
 #pragma unroll
         for (int b = 1; b <= 7; ++b) {
-            double v[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int sx = (i & 1) ? x - a : x + a, sy = (i & 2) ? y - b : y + b;
-                v[i] = sm[((sx + 8) >> 3) + 3 * ((sy + 8) >> 3)][(sx & 7) + 8 * (sy & 7) + 64 * zl];
-            }
-            const double u0 = v[0] + v[1], u1 = v[0] - v[1], u2 = v[2] + v[3], u3 = v[2] - v[3];
+            const double u0 = sx[0][zl][y + b + 7][x], u1 = sx[1][zl][y + b + 7][x];
+            const double u2 = sx[0][zl][y - b + 7][x], u3 = sx[1][zl][y - b + 7][x];
             double* o = out + static_cast<size_t>((a - 1) * 7 + b - 1) * 4 * NCELL;
             o[0] = u0 + u2;
             o[NCELL] = u1 + u3;
             o[2 * NCELL] = u0 - u2;
             o[3 * NCELL] = u1 - u3;
         }
+        __syncthreads();
     }
 }
 

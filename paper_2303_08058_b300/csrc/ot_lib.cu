@@ -251,6 +251,7 @@ struct ot_grid {
     std::vector<int> nslot;             // [n][27]: slot of each neighbour region in the node's space, -1: none
     std::vector<int2> snbM, snbX;       // [slot][27]: each slot's region's neighbour entries
     int n_slotM = 0, n_slotX = 0;
+    int n_slotXY = 0;                   // M slots [0, n_slotXY): the leaves' z columns, the (x, y) table's
     int* d_nslot = nullptr;
     int2* d_snbM = nullptr;
     int2* d_snbX = nullptr;
@@ -750,6 +751,20 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     {
         const int nregions = n + g->nvirt;
         std::vector<int> slotM(nregions, -1), slotX(nregions, -1), regM, regX;
+        // space M numbers first the regions in the z columns of the leaves
+        // (neighbours j = 4, 13, 22: dx = dy = 0): the (x, y) table is read
+        // only at centres t + (0, 0, +-c), so it covers slots [0, n_slotXY)
+        for (int i = 0; i < n; ++i) {
+            if (!g->is_leaf[i]) continue;
+            for (int j = 4; j < 27; j += 9) {
+                const int r = nreg[static_cast<size_t>(i) * 27 + j];
+                if (r >= 0 && slotM[r] < 0) {
+                    slotM[r] = static_cast<int>(regM.size());
+                    regM.push_back(r);
+                }
+            }
+        }
+        g->n_slotXY = static_cast<int>(regM.size());
         for (int i = 0; i < n; ++i) {
             std::vector<int>& slot = g->is_leaf[i] ? slotM : slotX;
             std::vector<int>& reg = g->is_leaf[i] ? regM : regX;
@@ -844,7 +859,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     for (int i = 0; i < n; ++i)
         g->ninfo[i] |= slab_axis(&g->nbr[static_cast<size_t>(i) * 27], g->is_leaf[i]) << NI_SLAB_SHIFT;
     // the (x, y) table of the masses takes 0.8 MB per slot: built up to 16 GiB
-    g->use_xy = static_cast<double>(g->n_slotM) * 49 * 4 * NCELL * sizeof(double) <= 16.0 * (1u << 30);
+    g->use_xy = static_cast<double>(g->n_slotXY) * 49 * 4 * NCELL * sizeof(double) <= 16.0 * (1u << 30);
 
     // --- exact pair counts, FLOPs and per-item costs ------------------------
     // For each (parity, half) warp pattern and list entry: which of the 27
@@ -1657,7 +1672,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if ((st = g->alloc(&g->d_Sbar, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Smf, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if (g->use_xy &&
-        (st = g->alloc(&g->d_Sxy, static_cast<size_t>(std::max(g->n_slotM, 1)) * 49 * 4 * NCELL)) != OT_OK)
+        (st = g->alloc(&g->d_Sxy, static_cast<size_t>(std::max(g->n_slotXY, 1)) * 49 * 4 * NCELL)) != OT_OK)
         return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
@@ -1754,7 +1769,7 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         if (g->precision == 0) {
             p.Sm = g->d_Sm;
             if (g->use_xy) {
-                OT_CUDA(launch_xybutterfly_masses(g->d_snbM, g->n_slotM, m, g->n, g->d_Sxy, s));
+                OT_CUDA(launch_xybutterfly_masses(g->d_snbM, g->n_slotXY, m, g->n, g->d_Sxy, s));
                 p.Sxy = g->d_Sxy;
             }
         } else {
