@@ -269,11 +269,7 @@ NOMINAL_SM_MHZ = 2032.0
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of that
 # kernel as it is now, keyed by (workload, launch, tile); a key not here
 # reports null.
-DRAM_BYTES = {
-    ("binary", "multipole", (8, 1)): 35_819_085_056 + 567_903_232,
-    ("polytrope64", "multipole", (8, 1)): 126_960_128 + 34_222_080,
-    ("polytrope64", "multipole", (8, 2)): 219_168_768 + 40_501_248,
-}
+DRAM_BYTES = {}
 
 
 def fp64_peak(ot, dev, stream):

@@ -480,6 +480,22 @@ def emit():
                 w(f"  a[{j}] = fma({src}[{k}], d[{di}], a[{j}]);\n")
     w("}\n\n")
 
+    # multipole sources paired by a reflection along one axis A: the member
+    # at o' (o with its A component negated) sees d^K G(o') = (-1)^{K_A}
+    # d^K G(o), so a[J] += (K_A of J+K even ? rs[K] : rd[K]) * d[J+K] with
+    # the row of o
+    for A, name in enumerate("xyz"):
+        w(f"// paired along {name}: 70 FMAs for two multipole pairs at o and o reflected along {name}\n"
+          f"// (rs = r(o) + r(o'), rd = r(o) - r(o'), d the row of o)\n")
+        w(f"__device__ __forceinline__ void ot_multi_fwd_{name}pair(double (&a)[16], const double (&rs)[16],\n"
+          f"                                                   const double (&rd)[16], const double (&d)[36]) {{\n")
+        for k in range(16):
+            for (j, kk, di) in terms:
+                if kk == k:
+                    src = "rs" if ROW[di][A] % 2 == 0 else "rd"
+                    w(f"  a[{j}] = fma({src}[{k}], d[{di}], a[{j}]);\n")
+        w("}\n\n")
+
     # paired multipole adjoint: g[K] += sum_J (even order of J+K ? ls[J] : ld[J]) * d[J+K]
     w("// paired: 70 FMAs for two targets (ls = lb+ + lb-, ld = lb+ - lb-)\n")
     w("__device__ __forceinline__ void ot_multi_adj_pair(double (&g)[16], const double (&ls)[16], const double (&ld)[16],\n"

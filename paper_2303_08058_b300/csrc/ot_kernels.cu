@@ -961,6 +961,70 @@ __device__ __forceinline__ void walk_forward(const int* __restrict__ list, int l
     }
 }
 
+// a leaf target's multipole sources (cells of refined neighbours) by its
+// axis-pair list: an entry o pairs with o reflected along axis A.  Where
+// some lane has a multipole source at both members the two share the row of
+// o through the sum and the difference of their moments (d^K G at the
+// reflection is (-1)^{K_A} d^K G(o)); where only one member has one in some
+// lane it runs alone with its own row; otherwise the entry is skipped
+template <int A>
+__device__ __forceinline__ void walk_multi_apairs(const int* __restrict__ list, int len, bool paired, int tx,
+                                                  int ty, int tz, const int2* __restrict__ s_nb,
+                                                  const FwdParams& p, double (&a)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        const int rx = A == 0 ? -ox : ox, ry = A == 1 ? -oy : oy, rz = A == 2 ? -oz : oz;
+        const int px = tx + ox, py = ty + oy, pz = tz + oz;
+        const int qx = tx + rx, qy = ty + ry, qz = tz + rz;
+        const int2 e1 = s_nb[nb_index(px, py, pz)];
+        const bool v1 = checked_kind(p, e1, item) == K_MULTI;
+        int2 e2 = make_int2(-1, 0);
+        bool v2 = false;
+        if (paired) {
+            e2 = s_nb[nb_index(qx, qy, qz)];
+            v2 = checked_kind(p, e2, item) == K_MULTI;
+        }
+        const bool a1 = __any_sync(0xffffffffu, v1), a2 = __any_sync(0xffffffffu, v2);
+        if (!a1 && !a2) continue;
+        double r[16];
+        double d[36];
+        if (a1 && a2) {
+            double rm[16];
+            source_moments(p, e1, v1, px, py, pz, r);
+            source_moments(p, e2, v2, qx, qy, qz, rm);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const double t = r[q];
+                r[q] = t + rm[q];     // sum
+                rm[q] = t - rm[q];    // difference
+            }
+            load_row(d, p.Dt, offset_row(ox, oy, oz));
+            if constexpr (A == 0) ot_multi_fwd_xpair(a, r, rm, d);
+            else if constexpr (A == 1) ot_multi_fwd_ypair(a, r, rm, d);
+            else ot_multi_fwd_zpair(a, r, rm, d);
+        } else if (a1) {
+            source_moments(p, e1, v1, px, py, pz, r);
+            load_row(d, p.Dt, offset_row(ox, oy, oz));
+            ot_multi_fwd(a, r, d);
+        } else {
+            source_moments(p, e2, v2, qx, qy, qz, r);
+            load_row(d, p.Dt, offset_row(rx, ry, rz));
+            ot_multi_fwd(a, r, d);
+        }
+    }
+}
+
+template <int A, class CH>
+__device__ __forceinline__ void walk_multi_apair_list(const CH& ch, int par, int tx, int ty, int tz,
+                                                      const int2* __restrict__ s_nb, const FwdParams& p,
+                                                      double (&a)[16], int item) {
+    const int* al = p.L.lists + p.L.ap_off[A] + par * p.L.ap_len[A];
+    const int np = p.L.ap_pairs[A], ns = p.L.ap_len[A] - np;
+    walk_multi_apairs<A>(al + ch.lo(np), ch.n(np), true, tx, ty, tz, s_nb, p, a, item);
+    walk_multi_apairs<A>(al + np + ch.lo(ns), ch.n(ns), false, tx, ty, tz, s_nb, p, a, item);
+}
+
 template <int MODE>
 __device__ __forceinline__ void store_forward(const FwdParams& p, int node, int level, bool leafT, int tcell,
                                               const double (&a)[16], const double (&c)[3],
@@ -1227,16 +1291,16 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
                                               !leafT, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
             } else if (MODE == 1 && leafT && !(EMU & 2)) {
                 // a leaf target's multipole sources lie in refined neighbours,
-                // mostly on one side: the two members of a +-o pair run as
-                // single entries, each only where some lane has a source
-                const int* lf = p.L.lists + par * p.L.far_len;
-                const int ns = p.L.far_len - p.L.far_pairs;
-                walk_forward<MODE, false, EMU>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), false, tx, ty, tz,
-                                               s_nb[warp], p, a, c, t4, f, it);
-                walk_forward<MODE, false, EMU, false, true, true>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs),
-                                                                  false, tx, ty, tz, s_nb[warp], p, a, c, t4, f, it);
-                walk_forward<MODE, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), false, tx, ty, tz,
-                                               s_nb[warp], p, a, c, t4, f, it);
+                // mostly on one side: paired with their reflections along the
+                // node's axis, each pair or member only where some lane has a
+                // source
+                const int A = (info >> NI_APAIR_SHIFT) & 3;
+                if (A == 0)
+                    walk_multi_apair_list<0>(ch, par, tx, ty, tz, s_nb[warp], p, a, it);
+                else if (A == 1)
+                    walk_multi_apair_list<1>(ch, par, tx, ty, tz, s_nb[warp], p, a, it);
+                else
+                    walk_multi_apair_list<2>(ch, par, tx, ty, tz, s_nb[warp], p, a, it);
             } else {
                 const int* lf = p.L.lists + par * p.L.far_len;
                 const int ns = p.L.far_len - p.L.far_pairs;

@@ -173,6 +173,23 @@ inline int slab_axis(const int2* nb27, bool leaf) {
     return 0;
 }
 
+// the axis (0 x, 1 y, 2 z) along which a leaf node's multipole sources pair
+// with their reflections: the one with the fewest faces on refined
+// neighbours; ties go to the axis its items split their halves along (slab
+// 0 z, 1 x, 2 y), then to the lower axis
+inline int pair_axis(const int2* nb27, int slab) {
+    static const int face[6] = {12, 14, 10, 16, 4, 22};   // -x +x -y +y -z +z
+    int refined[3] = {0, 0, 0};
+    for (int f = 0; f < 6; ++f)
+        if ((nb27[face[f]].y & 3) == K_MULTI) refined[f / 2]++;
+    const int split = slab == 0 ? 2 : slab == 1 ? 0 : 1;
+    int best = split;
+    for (int a = 0; a < 3; ++a)
+        if (refined[a] < refined[best] || (refined[a] == refined[best] && a != split && best != split && a < best))
+            best = a;
+    return best;
+}
+
 
 }  // namespace
 
@@ -621,6 +638,37 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     Lh.mr_off = static_cast<int>(g->lists.size());
     for (int z = 0; z < 7; ++z) g->lists.insert(g->lists.end(), mroot[z].begin(), mroot[z].end());
     g->lists.insert(g->lists.end(), mroot_pair.begin(), mroot_pair.end());
+    // a leaf target's multipole sources paired along one axis A: per A and
+    // parity, the offsets o with o_A > 0 whose reflection along A is in the
+    // same far list, then every other offset as a single
+    for (int A = 0; A < 3; ++A) {
+        Lh.ap_off[A] = static_cast<int>(g->lists.size());
+        for (int p = 0; p < 8; ++p) {
+            std::set<int> in;
+            for (auto& o : far_offs[p]) in.insert(key(o[0], o[1], o[2]));
+            std::vector<int> pp, ss;
+            for (auto& o : far_offs[p]) {
+                std::array<int, 3> r = o;
+                r[A] = -r[A];
+                if (o[A] != 0 && in.count(key(r[0], r[1], r[2]))) {
+                    if (o[A] > 0) pp.push_back(pack_offset(o[0], o[1], o[2]));
+                } else {
+                    ss.push_back(pack_offset(o[0], o[1], o[2]));
+                }
+            }
+            if (2 * pp.size() + ss.size() != far_offs[p].size())
+                return fail(OT_EINVAL, "internal: axis-pair stencils do not cover the offsets");
+            if (p == 0) {
+                Lh.ap_pairs[A] = static_cast<int>(pp.size());
+                Lh.ap_len[A] = static_cast<int>(pp.size() + ss.size());
+            } else if (Lh.ap_pairs[A] != static_cast<int>(pp.size()) ||
+                       Lh.ap_len[A] != static_cast<int>(pp.size() + ss.size())) {
+                return fail(OT_EINVAL, "internal: parity axis-pair stencils differ in shape");
+            }
+            g->lists.insert(g->lists.end(), pp.begin(), pp.end());
+            g->lists.insert(g->lists.end(), ss.begin(), ss.end());
+        }
+    }
     {
         // every far and near offset exactly once
         long long nf = 2LL * Lh.cf_pairs + Lh.cf_singles, nn = 2LL * Lh.cn_pairs;
@@ -856,8 +904,12 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             g->mem_xs.insert(g->mem_xs.end(), xs, xs + 3);
         }
     }
-    for (int i = 0; i < n; ++i)
-        g->ninfo[i] |= slab_axis(&g->nbr[static_cast<size_t>(i) * 27], g->is_leaf[i]) << NI_SLAB_SHIFT;
+    for (int i = 0; i < n; ++i) {
+        const int2* nb27 = &g->nbr[static_cast<size_t>(i) * 27];
+        const int sl = slab_axis(nb27, g->is_leaf[i]);
+        g->ninfo[i] |= sl << NI_SLAB_SHIFT;
+        if (g->is_leaf[i]) g->ninfo[i] |= pair_axis(nb27, sl) << NI_APAIR_SHIFT;
+    }
     // the (x, y) table of the masses takes 0.8 MB per slot: built up to 16 GiB
     g->use_xy = static_cast<double>(g->n_slotXY) * 49 * 4 * NCELL * sizeof(double) <= 16.0 * (1u << 30);
 
@@ -910,6 +962,37 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             }
         }
     }
+    // The axis-pair lists of a leaf target's multipole sources: per axis A,
+    // lane layout and warp pattern, the neighbours each member of an entry
+    // reaches; per A the pairs landing in each neighbour over all 512 cells,
+    // by paired / single entries.
+    std::vector<uint32_t> amask[3][3][16][2];   // [A][slab][pattern][member]
+    long long acnt[3][2][27];                   // [A][paired][neighbour]
+    std::memset(acnt, 0, sizeof(acnt));
+    for (int A = 0; A < 3; ++A)
+        for (int ph = 0; ph < 16; ++ph) {
+            const int par = ph >> 1, half = ph & 1;
+            const int* lst = &g->lists[g->Lh.ap_off[A] + par * g->Lh.ap_len[A]];
+            for (int sl = 0; sl < 3; ++sl)
+                for (int side = 0; side < 2; ++side) amask[A][sl][ph][side].assign(g->Lh.ap_len[A], 0u);
+            for (int k = 0; k < g->Lh.ap_len[A]; ++k) {
+                const int po = lst[k];
+                const int paired = k < g->Lh.ap_pairs[A] ? 1 : 0;
+                int o[3] = {(po & 0xff) - 8, ((po >> 8) & 0xff) - 8, ((po >> 16) & 0xff) - 8};
+                for (int sl = 0; sl < 3; ++sl)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        int t[3];
+                        lane_cell_host(lane, par, half, sl, t[0], t[1], t[2]);
+                        for (int side = 0; side <= paired; ++side) {
+                            int q[3] = {t[0] + o[0], t[1] + o[1], t[2] + o[2]};
+                            if (side) q[A] = t[A] - o[A];
+                            const int nb = ((q[0] + 8) >> 3) + 3 * ((q[1] + 8) >> 3) + 9 * ((q[2] + 8) >> 3);
+                            amask[A][sl][ph][side][k] |= 1u << nb;
+                            if (sl == 0) acnt[A][paired][nb]++;
+                        }
+                    }
+            }
+        }
     // The class lists of leaf targets (point masses): per warp pattern and
     // entry the neighbours its members reach; per entry its FP64 instructions
     // per lane (forward, scatter adjoint), members and FLOPs; per neighbour
@@ -1105,10 +1188,14 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                     alg_fwd += COP[desc->level[i] == 0 ? 3 : 2][j];
                     alg_fwd_multi += COP[desc->level[i] == 0 ? 3 : 2][j];
                 } else if (desc->level[i] > 0) {
-                    // a leaf target's multipole sources, every pair a single entry
-                    flops_fwd += 140 * (cpf + csf);
-                    alg_fwd += 70.0 * (cpf + csf);
-                    alg_fwd_multi += 70.0 * (cpf + csf);
+                    // a leaf target's multipole sources by the node's axis-pair
+                    // list: 70 FMAs + 32 adds per two pairs, 70 FMAs single
+                    const int A = (g->ninfo[i] >> NI_APAIR_SHIFT) & 3;
+                    const long long ap = acnt[A][1][j], as = acnt[A][0][j];
+                    if (ap + as != cpf + csf) return fail(OT_EINVAL, "internal: axis-pair counts differ");
+                    flops_fwd += 86 * ap + 140 * as;
+                    alg_fwd += 51.0 * ap + 70.0 * as;
+                    alg_fwd_multi += 51.0 * ap + 70.0 * as;
                 } else {
                     flops_fwd += 86 * cpf + 140 * csf;
                     alg_fwd += 51.0 * cpf + 70.0 * csf;
@@ -1163,10 +1250,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         if (sg == 1) {
                             cost[2] += 8 * 18;     // refined near source: 8 paired contractions
                         } else if (leaf && desc->level[i] > 0) {
-                            // a leaf target's multipole sources: the members of a
-                            // pair run as single entries, each where it reaches one
-                            cost[1] += ((maskside[sl][ph][sg][0][k] & mm) ? 70 : 0) +
-                                       ((pf[k] && (maskside[sl][ph][sg][1][k] & mm)) ? 70 : 0);
+                            // not reached: a leaf target's multipole sources run
+                            // by the axis-pair lists (below)
                         } else {
                             cost[1] += (pf[k] ? 102 : 70) + (leaf ? 0 : 30);
                         }
@@ -1182,11 +1267,29 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                 }
             };
             if (by_class) {
-                // multipole sources (refined neighbours) by the full lists, point
-                // masses by class
+                // multipole sources (refined neighbours) by the node's axis-pair
+                // list: an entry runs as a pair where both members reach a
+                // refined neighbour in some lane, as a single where one does;
+                // refined near sources by the near list; point masses by class
+                if (mm != 0) {
+                    const int A = (g->ninfo[i] >> NI_APAIR_SHIFT) & 3;
+                    const std::vector<uint32_t>& m0 = amask[A][sl][ph][0];
+                    const std::vector<uint32_t>& m1 = amask[A][sl][ph][1];
+                    for (size_t k = 0; k < m0.size(); ++k) {
+                        const bool a0 = (m0[k] & mm) != 0, a1 = (m1[k] & mm) != 0;
+                        if (a0 && a1) {
+                            cost[1] += 102;
+                            lanes += 32;
+                            padded += 64;
+                        } else if (a0 || a1) {
+                            cost[1] += 70;
+                            lanes += 32;
+                            padded += 32;
+                        }
+                    }
+                }
                 const uint32_t mo_keep = mo;
                 mo = 0;
-                scan(s1);
                 scan(1);
                 mo = mo_keep;
                 long long cost_s = cost[2];    // refined near sources
