@@ -269,7 +269,10 @@ NOMINAL_SM_MHZ = 2032.0
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of that
 # kernel as it is now, keyed by (workload, launch, tile); a key not here
 # reports null.
-DRAM_BYTES = {}
+DRAM_BYTES = {
+    ("binary", "multipole", (8, 1)): 35_080_582_656 + 534_574_592,
+    ("polytrope64", "multipole", (8, 2)): 197_047_808 + 33_955_584,
+}
 
 
 def fp64_peak(ot, dev, stream):
