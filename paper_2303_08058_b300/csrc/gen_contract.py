@@ -469,6 +469,17 @@ def emit():
         w(f"  a[{j}] = fma({'s' if rank(IND16[j]) % 2 == 0 else 'dm'}, d[{j}], a[{j}]);\n")
     w("}\n\n")
 
+    # point masses paired by a reflection along one axis A (the member at o'
+    # is o with its A component negated): a[J] += (J_A even ? s : dm) * d[J]
+    for A, name in enumerate("xyz"):
+        w(f"// paired along {name}: 16 FMAs for two point-mass pairs at o and o reflected along {name}\n"
+          f"// (s = m(o) + m(o'), dm = m(o) - m(o'), d the row of o)\n")
+        w(f"__device__ __forceinline__ void ot_mono_fwd_{name}pair(double (&a)[16], double s, double dm,\n"
+          f"                                                  const double (&d)[36]) {{\n")
+        for j in range(16):
+            w(f"  a[{j}] = fma({'s' if IND16[j][A] % 2 == 0 else 'dm'}, d[{j}], a[{j}]);\n")
+        w("}\n\n")
+
     # paired multipole sources: a[J] += (even order of J+K ? rs[K] : rd[K]) * d[J+K]
     w("// paired: 70 FMAs for two multipole pairs (rs = r+ + r-, rd = r+ - r-)\n")
     w("__device__ __forceinline__ void ot_multi_fwd_pair(double (&a)[16], const double (&rs)[16], const double (&rd)[16],\n"
@@ -528,6 +539,23 @@ def emit():
         else:
             w(f"  {v} = fma(lb[{j}], d[{j}], {v});\n")
     w("}\n\n")
+
+    # the same split by the parity of J_A: the source at t+o receives e + q,
+    # the one at o reflected along A receives e - q
+    for A, name in enumerate("xyz"):
+        w(f"// 16 FP64 ops: e = the part of <lb, d> with an even {name} order, q = the odd part\n")
+        w(f"__device__ __forceinline__ void ot_mono_adj_split_{name}(double& e, double& q, const double (&lb)[16],\n"
+          f"                                                    const double (&d)[36]) {{\n")
+        first = {0: True, 1: True}
+        for j in range(16):
+            par = IND16[j][A] % 2
+            v = "e" if par == 0 else "q"
+            if first[par]:
+                w(f"  {v} = lb[{j}] * d[{j}];\n")
+                first[par] = False
+            else:
+                w(f"  {v} = fma(lb[{j}], d[{j}], {v});\n")
+        w("}\n\n")
 
     # double-float (FP32 hi + lo) point-mass contraction, paired form:
     # a[J] += x * D[J] with x = s (even order) or dm (odd order); the row

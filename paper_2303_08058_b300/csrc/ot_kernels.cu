@@ -683,40 +683,62 @@ __device__ __forceinline__ void walk_classes_fwd_df_all(const int* __restrict__ 
 
 // xy-complete point-mass classes (a, b > 0) of a leaf target with leaf or
 // empty neighbours: the first two transform stages come from the (x, y)
-// table at the positions t + (0, 0, +-c)
+// table at the positions t + (0, 0, +-c).  The walk is software-pipelined:
+// the next entry's table values are requested before this entry's
+// transform and FMAs, so their latency (the table streams from DRAM)
+// overlaps the FP64 work.
+template <int Z>
+__device__ __forceinline__ bool xy_fetch(int e, int tx, int ty, int tz, const int2* __restrict__ s_nb,
+                                         const int* __restrict__ s_sl, const FwdParams& p, double (&w)[8],
+                                         int item) {
+    const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
+    const unsigned members = static_cast<unsigned>(e) >> 24;
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[4 * r + q] = 0.0;
+        if ((4 * r) & Z) continue;
+        if ((members >> (4 * r)) & 1u) {
+            const int sz = r ? tz - c : tz + c;
+            const int nbi = nb_index(tx, ty, sz);
+            const int ks = checked_kind(p, s_nb[nbi], item);
+            const int slot = s_sl[nbi];
+            if (slot >= 0) {
+                const double* src = p.Sxy + static_cast<size_t>(slot * 49 + (a - 1) * 7 + b - 1) * 4 * NCELL +
+                                    (tx & 7) + 8 * (ty & 7) + 64 * (sz & 7);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[4 * r + q] = __ldg(src + q * NCELL);
+                any = true;
+            } else if (ks != K_NONE) {
+                report(p.status, 7, item);
+            }
+        }
+    }
+    return any;
+}
+
 template <int Z>
 __device__ __forceinline__ void walk_classes_fwd_xy(const int* __restrict__ list, int len, int tx, int ty, int tz,
                                                     const int2* __restrict__ s_nb, const int* __restrict__ s_sl,
                                                     const FwdParams& p, double (&acc)[16], int item) {
     static_assert((Z & 3) == 0, "the x and y stages need a, b > 0");
+    if (len <= 0) return;
+    int en = __ldg(list);
+    double wn[8];
+    bool anyn = xy_fetch<Z>(en, tx, ty, tz, s_nb, s_sl, p, wn, item);
     for (int k = 0; k < len; ++k) {
-        const int e = __ldg(list + k);
-        const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
-        const unsigned members = static_cast<unsigned>(e) >> 24;
+        const int e = en;
         double w[8];
-        bool any = false;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) w[4 * r + q] = 0.0;
-            if ((4 * r) & Z) continue;
-            if ((members >> (4 * r)) & 1u) {
-                const int sz = r ? tz - c : tz + c;
-                const int nbi = nb_index(tx, ty, sz);
-                const int ks = checked_kind(p, s_nb[nbi], item);
-                const int slot = s_sl[nbi];
-                if (slot >= 0) {
-                    const double* src = p.Sxy + static_cast<size_t>(slot * 49 + (a - 1) * 7 + b - 1) * 4 * NCELL +
-                                        (tx & 7) + 8 * (ty & 7) + 64 * (sz & 7);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) w[4 * r + q] = __ldg(src + q * NCELL);
-                    any = true;
-                } else if (ks != K_NONE) {
-                    report(p.status, 7, item);
-                }
-            }
+        for (int q = 0; q < 8; ++q) w[q] = wn[q];
+        const bool any = anyn;
+        if (k + 1 < len) {
+            en = __ldg(list + k + 1);
+            anyn = xy_fetch<Z>(en, tx, ty, tz, s_nb, s_sl, p, wn, item);
         }
         if (!__any_sync(0xffffffffu, any)) continue;
+        const int a = e & 0xff, b = (e >> 8) & 0xff, c = (e >> 16) & 0xff;
         double d[36];
         load_row16(d, p.Dt, offset_row(a, b, c));
         if constexpr (!(Z & 4)) {
@@ -1025,6 +1047,50 @@ __device__ __forceinline__ void walk_multi_apair_list(const CH& ch, int par, int
     walk_multi_apairs<A>(al + np + ch.lo(ns), ch.n(ns), false, tx, ty, tz, s_nb, p, a, item);
 }
 
+// a non-leaf target's point-mass sources (leaf cells and virtual
+// descendants in its neighbours) by its axis-pair list: an entry o and its
+// reflection along axis A share the row of o through the sum and the
+// difference of their masses (a member without a point mass counts 0, and
+// a lone member's sum and difference are its mass, exactly); the entry is
+// skipped where no lane has a point mass at either member
+template <int A>
+__device__ __forceinline__ void walk_mono_apairs(const int* __restrict__ list, int len, bool paired, int tx,
+                                                 int ty, int tz, const int2* __restrict__ s_nb,
+                                                 const FwdParams& p, double (&a)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        const int px = tx + ox, py = ty + oy, pz = tz + oz;
+        const int qx = A == 0 ? tx - ox : px, qy = A == 1 ? ty - oy : py, qz = A == 2 ? tz - oz : pz;
+        const int2 e1 = s_nb[nb_index(px, py, pz)];
+        const int k1 = checked_kind(p, e1, item);
+        int2 e2 = make_int2(-1, 0);
+        int k2 = K_NONE;
+        if (paired) {
+            e2 = s_nb[nb_index(qx, qy, qz)];
+            k2 = checked_kind(p, e2, item);
+        }
+        if (!__any_sync(0xffffffffu, k1 >= K_LEAF || k2 >= K_LEAF)) continue;
+        const double m1 = source_mass(p, e1, k1, px, py, pz);
+        const double m2 = paired ? source_mass(p, e2, k2, qx, qy, qz) : 0.0;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(ox, oy, oz));
+        if constexpr (A == 0) ot_mono_fwd_xpair(a, m1 + m2, m1 - m2, d);
+        else if constexpr (A == 1) ot_mono_fwd_ypair(a, m1 + m2, m1 - m2, d);
+        else ot_mono_fwd_zpair(a, m1 + m2, m1 - m2, d);
+    }
+}
+
+template <int A, class CH>
+__device__ __forceinline__ void walk_mono_apair_list(const CH& ch, int par, int tx, int ty, int tz,
+                                                     const int2* __restrict__ s_nb, const FwdParams& p,
+                                                     double (&a)[16], int item) {
+    const int* al = p.L.lists + p.L.ap_off[A] + par * p.L.ap_len[A];
+    const int np = p.L.ap_pairs[A], ns = p.L.ap_len[A] - np;
+    walk_mono_apairs<A>(al + ch.lo(np), ch.n(np), true, tx, ty, tz, s_nb, p, a, item);
+    walk_mono_apairs<A>(al + np + ch.lo(ns), ch.n(ns), false, tx, ty, tz, s_nb, p, a, item);
+}
+
 template <int MODE>
 __device__ __forceinline__ void store_forward(const FwdParams& p, int node, int level, bool leafT, int tcell,
                                               const double (&a)[16], const double (&c)[3],
@@ -1278,12 +1344,23 @@ __global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdPara
             }
             if ((MODE & 2) && level > 0 &&
                 __any_sync(0xffffffffu, lane < 27 && (nb[lane < 27 ? lane : 0].y & 3) >= K_LEAF)) {
-                const int* lf = p.L.lists + par * p.L.far_len;
-                const int ns = p.L.far_len - p.L.far_pairs;
-                walk_forward<2, true, EMU>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), true, tx, ty, tz, nb, p,
-                                           a, c, t4, f, it);
-                walk_forward<2, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), true, tx, ty, tz, nb, p, a, c,
-                                            t4, f, it);
+                if constexpr ((EMU & 1) == 0) {
+                    // point masses (leaf neighbours) paired along the node's axis
+                    const int A = (info >> NI_APAIR_SHIFT) & 3;
+                    if (A == 0)
+                        walk_mono_apair_list<0>(ch, par, tx, ty, tz, nb, p, a, it);
+                    else if (A == 1)
+                        walk_mono_apair_list<1>(ch, par, tx, ty, tz, nb, p, a, it);
+                    else
+                        walk_mono_apair_list<2>(ch, par, tx, ty, tz, nb, p, a, it);
+                } else {
+                    const int* lf = p.L.lists + par * p.L.far_len;
+                    const int ns = p.L.far_len - p.L.far_pairs;
+                    walk_forward<2, true, EMU>(lf + ch.lo(p.L.far_pairs), ch.n(p.L.far_pairs), true, tx, ty, tz, nb,
+                                               p, a, c, t4, f, it);
+                    walk_forward<2, false, EMU>(lf + p.L.far_pairs + ch.lo(ns), ch.n(ns), true, tx, ty, tz, nb, p, a,
+                                                c, t4, f, it);
+                }
             }
         } else {
             if (level == 0) {
@@ -1982,6 +2059,56 @@ __device__ __forceinline__ void walk_scatter(const int* __restrict__ list, int l
     }
 }
 
+// the point-mass adjoint of a non-leaf target by its axis-pair list: with
+// e, q the parts of <lb, row(o)> with an even and an odd A order, the source
+// at t+o receives e + q and the one at o reflected along A receives e - q
+template <int A, class P>
+__device__ __forceinline__ void walk_scatter_apairs(const int* __restrict__ list, int len, bool paired, int tx,
+                                                    int ty, int tz, const int2* __restrict__ s_nb, const P& p,
+                                                    const double (&lb)[16], int item) {
+    for (int k = 0; k < len; ++k) {
+        const int po = __ldg(list + k);
+        const int ox = (po & 0xff) - 8, oy = ((po >> 8) & 0xff) - 8, oz = ((po >> 16) & 0xff) - 8;
+        const int px = tx + ox, py = ty + oy, pz = tz + oz;
+        const int qx = A == 0 ? tx - ox : px, qy = A == 1 ? ty - oy : py, qz = A == 2 ? tz - oz : pz;
+        const int2 e1 = s_nb[nb_index(px, py, pz)];
+        int k1 = e1.y & 3;
+        if (k1 != K_NONE && static_cast<unsigned>(e1.x) >= static_cast<unsigned>(p.n_nodes)) {
+            report(p.status, 3, item);
+            k1 = K_NONE;
+        }
+        int2 e2 = make_int2(-1, 0);
+        int k2 = K_NONE;
+        if (paired) {
+            e2 = s_nb[nb_index(qx, qy, qz)];
+            k2 = e2.y & 3;
+            if (k2 != K_NONE && static_cast<unsigned>(e2.x) >= static_cast<unsigned>(p.n_nodes)) {
+                report(p.status, 3, item);
+                k2 = K_NONE;
+            }
+        }
+        if (!__any_sync(0xffffffffu, k1 >= K_LEAF || k2 >= K_LEAF)) continue;
+        double d[36];
+        load_row16(d, p.Dt, offset_row(ox, oy, oz));
+        double e, q;
+        if constexpr (A == 0) ot_mono_adj_split_x(e, q, lb, d);
+        else if constexpr (A == 1) ot_mono_adj_split_y(e, q, lb, d);
+        else ot_mono_adj_split_z(e, q, lb, d);
+        scatter_mass(p, e1, k1, px, py, pz, e + q);
+        if (paired) scatter_mass(p, e2, k2, qx, qy, qz, e - q);
+    }
+}
+
+template <int A, class P>
+__device__ __forceinline__ void walk_scatter_apair_list(int par, int tx, int ty, int tz,
+                                                        const int2* __restrict__ s_nb, const P& p,
+                                                        const double (&lb)[16], int item) {
+    const int* al = p.L.lists + p.L.ap_off[A] + par * p.L.ap_len[A];
+    const int np = p.L.ap_pairs[A];
+    walk_scatter_apairs<A>(al, np, true, tx, ty, tz, s_nb, p, lb, item);
+    walk_scatter_apairs<A>(al + np, p.L.ap_len[A] - np, false, tx, ty, tz, s_nb, p, lb, item);
+}
+
 // one scatter work item: the warp's 32 target cells of `node` push their
 // point-mass adjoint contributions into mbar
 template <bool EMU, class P>
@@ -2061,6 +2188,15 @@ __device__ __forceinline__ void scatter_item(const P& p, const int2* __restrict_
     }
     if (level == 0) {
         walk_scatter<true, false, EMU>(p.L.lists + p.L.root_off, p.L.root_len, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);
+    } else if (!EMU && !leafT) {
+        // a non-leaf target: its point-mass sources paired along its axis
+        const int A = (info >> NI_APAIR_SHIFT) & 3;
+        if (A == 0)
+            walk_scatter_apair_list<0>(par, tx, ty, tz, s_nb, p, lb, it);
+        else if (A == 1)
+            walk_scatter_apair_list<1>(par, tx, ty, tz, s_nb, p, lb, it);
+        else
+            walk_scatter_apair_list<2>(par, tx, ty, tz, s_nb, p, lb, it);
     } else {
         const int* lf = p.L.lists + par * p.L.far_len;
         walk_scatter<true, false, EMU>(lf, p.L.far_pairs, tx, ty, tz, s_nb, p, lb, lbh, lbl, it);

@@ -173,15 +173,18 @@ inline int slab_axis(const int2* nb27, bool leaf) {
     return 0;
 }
 
-// the axis (0 x, 1 y, 2 z) along which a leaf node's multipole sources pair
-// with their reflections: the one with the fewest faces on refined
-// neighbours; ties go to the axis its items split their halves along (slab
-// 0 z, 1 x, 2 y), then to the lower axis
-inline int pair_axis(const int2* nb27, int slab) {
+// the axis (0 x, 1 y, 2 z) along which a node's sources of the other kind
+// pair with their reflections (a leaf node's multipole sources, a non-leaf
+// node's point masses): the one with the fewest faces on neighbours holding
+// such sources; ties go to the axis its items split their halves along
+// (slab 0 z, 1 x, 2 y), then to the lower axis
+inline int pair_axis(const int2* nb27, int slab, bool leaf) {
     static const int face[6] = {12, 14, 10, 16, 4, 22};   // -x +x -y +y -z +z
     int refined[3] = {0, 0, 0};
-    for (int f = 0; f < 6; ++f)
-        if ((nb27[face[f]].y & 3) == K_MULTI) refined[f / 2]++;
+    for (int f = 0; f < 6; ++f) {
+        const int k = nb27[face[f]].y & 3;
+        if (leaf ? k == K_MULTI : (k == K_LEAF || k == K_VIRT)) refined[f / 2]++;
+    }
     const int split = slab == 0 ? 2 : slab == 1 ? 0 : 1;
     int best = split;
     for (int a = 0; a < 3; ++a)
@@ -908,7 +911,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         const int2* nb27 = &g->nbr[static_cast<size_t>(i) * 27];
         const int sl = slab_axis(nb27, g->is_leaf[i]);
         g->ninfo[i] |= sl << NI_SLAB_SHIFT;
-        if (g->is_leaf[i]) g->ninfo[i] |= pair_axis(nb27, sl) << NI_APAIR_SHIFT;
+        g->ninfo[i] |= pair_axis(nb27, sl, g->is_leaf[i]) << NI_APAIR_SHIFT;
     }
     // the (x, y) table of the masses takes 0.8 MB per slot: built up to 16 GiB
     g->use_xy = static_cast<double>(g->n_slotXY) * 49 * 4 * NCELL * sizeof(double) <= 16.0 * (1u << 30);
@@ -1226,6 +1229,15 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         flops_adj_scat += std::llround(cfl_s[0][j] + cfl_s[1][j]);
                         alg_adj_scat += cop_s[0][j] + cop_s[1][j];
                     }
+                } else if (!leaf && desc->level[i] > 0) {
+                    // a non-leaf target's point masses by its axis-pair list
+                    const int A = (g->ninfo[i] >> NI_APAIR_SHIFT) & 3;
+                    const long long ap = acnt[A][1][j], as = acnt[A][0][j];
+                    if (ap + as != cp + cs) return fail(OT_EINVAL, "internal: axis-pair counts differ");
+                    flops_fwd += 17 * ap + 32 * as;
+                    flops_adj_scat += 16 * ap + 32 * as;
+                    alg_fwd += 9.0 * ap + 16.0 * as;
+                    alg_adj_scat += 9.0 * ap + 17.0 * as;
                 } else {
                     flops_fwd += 17 * cp + 32 * cs;
                     flops_adj_scat += 16 * cp + 32 * cs;
@@ -1312,11 +1324,31 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         lanes += 32;
                         padded += 32 * cmem[cgm][k];
                     }
-                const uint32_t mm_keep = mm;
-                mm = 0;
-                scan(s1);
-                mm = mm_keep;
-                ops_adj_scat += 32 * (cost[2] - count_single_mono);
+                if (desc->level[i] > 0) {
+                    // point masses (leaf neighbours) by the node's axis-pair
+                    // list: an entry runs where some lane has a point mass at
+                    // either member, 16 FMAs + 2 adds forward and adjoint
+                    if (mo != 0) {
+                        const int A = (g->ninfo[i] >> NI_APAIR_SHIFT) & 3;
+                        const std::vector<uint32_t>& m0 = amask[A][sl][ph][0];
+                        const std::vector<uint32_t>& m1 = amask[A][sl][ph][1];
+                        for (size_t k = 0; k < m0.size(); ++k) {
+                            const bool a0 = (m0[k] & mo) != 0, a1 = (m1[k] & mo) != 0;
+                            if (a0 || a1) {
+                                cost[2] += 18;
+                                lanes += 32;
+                                padded += (a0 && a1) ? 64 : 32;
+                            }
+                        }
+                    }
+                    ops_adj_scat += 32 * cost[2];
+                } else {
+                    const uint32_t mm_keep = mm;
+                    mm = 0;
+                    scan(s1);
+                    mm = mm_keep;
+                    ops_adj_scat += 32 * (cost[2] - count_single_mono);
+                }
             } else {
                 scan(s1);
                 scan(1);

@@ -203,6 +203,30 @@ def test_fused_adaptive_virtual_descendants(ot, orc):
     assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
 
 
+def test_leaf_targets_next_to_refined_faces_every_cell(ot, orc):
+    """Leaf targets whose multipole sources sit in refined face neighbours on
+    each of the three axes: the level-2 leaves around two refined level-2
+    nodes walk those sources paired with their reflections along an axis
+    parallel to the refined face (or alone); every cell of the tree against
+    the oracle, both passes."""
+    def refine(l, c, h0):
+        return l == 2 and tuple(c) in {(1, 2, 1), (2, 1, 2)}
+    tree = synth.adaptive_tree(refine, 2, 3, 8.0)
+    assert tree.n == 1 + 8 + 64 + 16
+    rho = synth.uniform_random_density(tree, seed=47)
+    g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
+    tg = all_targets(tree)
+    Lo, S, Lco, Sc, n1, n2 = oracle_both(orc, tree, M, m, tg)
+    assert_parity(at_targets(L, tg), Lo, S, what="L", kind="L")
+    assert_parity(at_targets(Lc, tg), Lco, Sc, what="Lc")
+    info = g.info()
+    assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
+    # the multipole pass alone (the launch with the axis-pair walk)
+    L1, _ = g.multipole(dev(M))
+    r1 = orc.run_pass(tree, "multipole", M=M, targets=tg)
+    assert_parity(at_targets(host(L1), tg), r1["L"], fwd_scale(r1), what="L multipole pass", kind="L")
+
+
 def test_separate_passes_equal_fused(ot):
     tree = _small_adaptive()
     rho = synth.uniform_random_density(tree, seed=47)
