@@ -265,8 +265,8 @@ class OTGrid:
         [n, 512] (the density adjoint of Lbar through both passes and the
         moments) out; the angular term is computed (work["Lc"]) but stays on
         the device.  The large copies run on a side stream, overlapped with
-        the kernels: Lbar uploads during the moments and the forward, L
-        downloads during the adjoint.  ``work`` (a dict this method fills on
+        the kernels: Lbar uploads (after rho) during the moments and the
+        forward, L downloads during the adjoint.  ``work`` (a dict this method fills on
         first use) keeps the device buffers between calls.  Asynchronous on
         ``stream``; the outputs are ready when it completes."""
         main = stream if stream is not None else torch.cuda.current_stream()
@@ -275,14 +275,18 @@ class OTGrid:
         if not work:
             work.update(self.step_buffers())
         cp = work["copy"]
-        start, lbar_in, fwd_done = (torch.cuda.Event() for _ in range(3))
-        start.record(main)
-        cp.wait_event(start)                      # the previous step has released the buffers
+        rho_in, lbar_in, fwd_done = (torch.cuda.Event() for _ in range(3))
+        with torch.cuda.stream(main):
+            work["rho"].copy_(rho_h, non_blocking=True)
+        rho_in.record(main)
+        # the L-bar upload after the densities' (host-to-device copies from two
+        # streams can queue on one copy engine, and the moments need rho
+        # first); waiting on main also means the previous step released the
+        # buffers
+        cp.wait_event(rho_in)
         with torch.cuda.stream(cp):
             work["Lbar"].copy_(Lbar_h, non_blocking=True)
             lbar_in.record(cp)
-        with torch.cuda.stream(main):
-            work["rho"].copy_(rho_h, non_blocking=True)
         self.moments(work["rho"], work["M"], work["m"], stream=main)
         self.interactions(work["M"], work["m"], work["L"], work["Lc"], stream=main)
         fwd_done.record(main)
