@@ -272,6 +272,8 @@ struct ot_grid {
     std::vector<int2> snbM, snbX;       // [slot][27]: each slot's region's neighbour entries
     int n_slotM = 0, n_slotX = 0;
     int n_slotXY = 0;                   // M slots [0, n_slotXY): the leaves' z columns, the (x, y) table's
+    int n_slotXyz = 0;                  // X slots [0, n_slotXyz): the yz planes of the non-leaf nodes, the
+                                        // x tables' (read only at t + (0, +-b, +-c))
     int* d_nslot = nullptr;
     int2* d_snbM = nullptr;
     int2* d_snbX = nullptr;
@@ -816,6 +818,20 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             }
         }
         g->n_slotXY = static_cast<int>(regM.size());
+        // space X likewise numbers first the regions in the yz planes of the
+        // non-leaf nodes (neighbours with dx = 0): the x tables of reduced
+        // moments and L-bar are read only at t + (0, +-b, +-c)
+        for (int i = 0; i < n; ++i) {
+            if (g->is_leaf[i]) continue;
+            for (int j = 1; j < 27; j += 3) {
+                const int r = nreg[static_cast<size_t>(i) * 27 + j];
+                if (r >= 0 && slotX[r] < 0) {
+                    slotX[r] = static_cast<int>(regX.size());
+                    regX.push_back(r);
+                }
+            }
+        }
+        g->n_slotXyz = static_cast<int>(regX.size());
         for (int i = 0; i < n; ++i) {
             std::vector<int>& slot = g->is_leaf[i] ? slotM : slotX;
             std::vector<int>& reg = g->is_leaf[i] ? regM : regX;
@@ -1799,10 +1815,10 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_vmap, vmap);
 #undef UP
     if ((st = g->alloc(&g->d_Mhat, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
-    if ((st = g->alloc(&g->d_Sx, static_cast<size_t>(std::max(g->n_slotX, 1)) * 7 * 32 * NCELL)) != OT_OK)
+    if ((st = g->alloc(&g->d_Sx, static_cast<size_t>(std::max(g->n_slotXyz, 1)) * 7 * 32 * NCELL)) != OT_OK)
         return st;
     if ((st = g->alloc(&g->d_Sm, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
-    if ((st = g->alloc(&g->d_Tx, static_cast<size_t>(std::max(g->n_slotX, 1)) * 7 * 32 * NCELL)) != OT_OK)
+    if ((st = g->alloc(&g->d_Tx, static_cast<size_t>(std::max(g->n_slotXyz, 1)) * 7 * 32 * NCELL)) != OT_OK)
         return st;
     if ((st = g->alloc(&g->d_Sbar, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Smf, static_cast<size_t>(std::max(g->n_slotM, 1)) * 7 * 2 * NCELL)) != OT_OK) return st;
@@ -1896,7 +1912,7 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
     FwdParams p = fwd_params(g, m, L, (mode & 1) ? Lc : nullptr, 1);
     // prebuilt x butterflies of the class transforms (FP64 contractions only)
     if ((mode & 1) && g->precision != 2 && g->n_slotX > 0) {
-        OT_CUDA(launch_xbutterfly_moments(g->d_snbX, g->n_slotX, g->d_Mhat, g->n, g->d_Sx, s));
+        OT_CUDA(launch_xbutterfly_moments(g->d_snbX, g->n_slotXyz, g->d_Mhat, g->n, g->d_Sx, s));
         p.Sx = g->d_Sx;
     }
     if ((mode & 2) && g->n_slotM > 0) {
@@ -2035,7 +2051,7 @@ static ot_status enqueue_backward(ot_grid* g, const double* Lbar, double* Mbar, 
             OT_CUDA(cudaMemsetAsync(g->d_chunk_ctr, 0, static_cast<size_t>(g->n_chunk_ctrs_adj) * sizeof(int), s));
         // the targets' L-bar x butterflies for the FP64 multipole gather
         if (g->precision != 2 && g->n_slotX > 0) {
-            OT_CUDA(launch_xbutterfly_lbar(g->d_snbX, g->n_slotX, g->d_Lrbar, g->n, g->d_Tx, s));
+            OT_CUDA(launch_xbutterfly_lbar(g->d_snbX, g->n_slotXyz, g->d_Lrbar, g->n, g->d_Tx, s));
             p.Tx = g->d_Tx;
         }
     }
