@@ -225,8 +225,10 @@ constexpr int NI_SLAB_SHIFT = 13;
 constexpr int NI_APAIR_SHIFT = 15;
 
 // launchers (ot_kernels.cu)
+// one_block_per_sm: the grid holds one block per SM, so the FP64 multipole
+// pass may take the register budget of a single resident block
 cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid,
-                           cudaStream_t s);
+                           cudaStream_t s, bool one_block_per_sm = false);
 cudaError_t launch_adjoint(const AdjParams& p, int mode, bool persistent, int wpb, int grid,
                            cudaStream_t s);
 cudaError_t launch_prescale_moments(const PrepParams& p, cudaStream_t s);

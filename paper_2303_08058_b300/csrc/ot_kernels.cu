@@ -1206,8 +1206,10 @@ __device__ __forceinline__ bool chunk_combine_fwd(const FwdParams& p, int2 ci, i
     return true;
 }
 
-template <int MODE, int EMU>
-__global__ void __launch_bounds__(256, EMU ? 1 : 2) forward_kernel(const FwdParams p, int persistent) {
+// MINB: resident blocks of 256 threads per SM the register allocation must
+// allow (2 caps a thread at 128 registers, 1 at 255)
+template <int MODE, int EMU, int MINB = (EMU ? 1 : 2)>
+__global__ void __launch_bounds__(256, MINB) forward_kernel(const FwdParams p, int persistent) {
     __shared__ int2 s_nb[8][27];
     __shared__ int s_sl[8][27];   // x-table slots of the neighbours (leaf or multipole)
     const int lane = threadIdx.x & 31;
@@ -3325,7 +3327,8 @@ void launch_count_adjust(long long delta) {
     t_launches += delta;
 }
 
-cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid, cudaStream_t s) {
+cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wpb, int grid, cudaStream_t s,
+                           bool one_block_per_sm) {
     if (p.n_items == 0) return cudaSuccess;
     const dim3 block(32 * wpb);
     const int per = persistent ? 1 : 0;
@@ -3333,7 +3336,14 @@ cudaError_t launch_forward(const FwdParams& p, int mode, bool persistent, int wp
     // contractions too when split moments are given
     const int emu = (p.mf != nullptr && (mode & 2) ? 1 : 0) | (p.Mf != nullptr && (mode & 1) ? 2 : 0);
     switch (mode * 4 + emu) {
-        case 4: forward_kernel<1, 0><<<grid, block, 0, s>>>(p, per); break;
+        case 4:
+            // at 128 registers the multipole pass spills; with one block per
+            // SM it keeps its working set in registers
+            if (one_block_per_sm)
+                forward_kernel<1, 0, 1><<<grid, block, 0, s>>>(p, per);
+            else
+                forward_kernel<1, 0><<<grid, block, 0, s>>>(p, per);
+            break;
         case 6: forward_kernel<1, 2><<<grid, block, 0, s>>>(p, per); break;
         case 8: forward_kernel<2, 0><<<grid, block, 0, s>>>(p, per); break;
         case 9: forward_kernel<2, 1><<<grid, block, 0, s>>>(p, per); break;

@@ -1966,7 +1966,8 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         OT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int), s));
         const int maxb = emu2 ? g->maxb_emu2[mode][g->wpb]
                          : emu ? g->maxb_emu[mode][g->wpb] : g->maxb_fwd[mode][g->wpb];
-        OT_CUDA(launch_forward(p, mode, true, g->wpb, grid_blocks(g, maxb), s));
+        const int blocks = grid_blocks(g, maxb);
+        OT_CUDA(launch_forward(p, mode, true, g->wpb, blocks, s, blocks == g->num_sms));
     }
     return OT_OK;
 }
