@@ -203,16 +203,24 @@ def test_fused_adaptive_virtual_descendants(ot, orc):
     assert (info["pairs_multipole"], info["pairs_monopole"]) == (n1, n2)
 
 
-def test_leaf_targets_next_to_refined_faces_every_cell(ot, orc):
-    """Leaf targets whose multipole sources sit in refined face neighbours on
-    each of the three axes: the level-2 leaves around two refined level-2
-    nodes walk those sources paired with their reflections along an axis
-    parallel to the refined face (or alone); every cell of the tree against
-    the oracle, both passes."""
+def _refined_faces_tree():
+    """89 sub-grids: levels 0-2 full, two level-2 nodes refined, so that level-2
+    leaves have refined face neighbours on each of the three axes and the
+    refined nodes (and their parents) have leaf neighbours."""
     def refine(l, c, h0):
         return l == 2 and tuple(c) in {(1, 2, 1), (2, 1, 2)}
     tree = synth.adaptive_tree(refine, 2, 3, 8.0)
     assert tree.n == 1 + 8 + 64 + 16
+    return tree
+
+
+def test_leaf_targets_next_to_refined_faces_every_cell(ot, orc):
+    """Leaf targets whose multipole sources sit in refined face neighbours on
+    each of the three axes walk those sources paired with their reflections
+    along an axis parallel to the refined face (or alone), and non-leaf
+    targets their point masses likewise; every cell of the tree against the
+    oracle, both passes."""
+    tree = _refined_faces_tree()
     rho = synth.uniform_random_density(tree, seed=47)
     g, M, m, L, Lc = gpu_fused(ot, tree, rho, orc=orc)
     tg = all_targets(tree)
@@ -305,6 +313,23 @@ def test_adjoint_matches_oracle_transposed_sum(ot, orc, which, deterministic):
     g.set_deterministic(deterministic)
     Mb, mb = g.backward(dev(Lbar))
     torch.cuda.synchronize()
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=tg)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
+    assert_parity(host(mb), mo, Sm, what="mbar")
+    assert np.max(np.abs(mo)) > 0
+
+
+def test_refined_faces_adjoint_against_oracle(ot, orc):
+    """The point-mass adjoint by target (non-leaf targets' point masses in
+    axis pairs, atomic adds) and the multipole gather on the tree with
+    refined faces on all three axes, against the oracle's transposed sums."""
+    tree = _refined_faces_tree()
+    Lbar, tg = _sparse_lbar(tree, 600, 52)
+    g = ot.OTGrid.from_tree(tree)
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    g.check()
     Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=tg)
     mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg)
     assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
