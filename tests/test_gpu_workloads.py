@@ -207,3 +207,70 @@ def test_config4_full_solve_probe_loss_gradient(ot, orc):
         fd = (f(rp) - f(rm)) / (2 * step)
         noise = np.finfo(np.float64).eps * abs(loss0) / step
         assert abs(grad[n, c] - fd) <= 1e-4 * abs(fd) + noise, (n, c, grad[n, c], fd, noise)
+
+
+def _boundary_nodes(tree):
+    """Leaf nodes with a refined (non-leaf) neighbour of their level, and
+    non-leaf nodes with a leaf neighbour of their level or a coarser leaf
+    covering a neighbour position (a virtual source)."""
+    idx = tree.index()
+
+    def kind(l, q):
+        if any(v < 0 or v >= (1 << l) for v in q):
+            return None
+        j = idx.get((l, *q))
+        if j is not None:
+            return "leaf" if tree.is_leaf[j] else "multi"
+        for d in range(1, l + 1):
+            j = idx.get((l - d, *(v >> d for v in q)))
+            if j is not None:
+                return "leaf" if tree.is_leaf[j] else None
+        return None
+
+    leaf_next_multi, multi_next_leaf = [], []
+    for i in range(tree.n):
+        l, c = int(tree.level[i]), [int(v) for v in tree.coord[i]]
+        if l == 0:
+            continue
+        kinds = {kind(l, (c[0] + dx, c[1] + dy, c[2] + dz))
+                 for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1) if (dx, dy, dz) != (0, 0, 0)}
+        if tree.is_leaf[i] and "multi" in kinds:
+            leaf_next_multi.append(i)
+        if not tree.is_leaf[i] and "leaf" in kinds:
+            multi_next_leaf.append(i)
+    return np.array(leaf_next_multi), np.array(multi_next_leaf)
+
+
+def test_config5_coarse_fine_targets_sampled(ot, orc):
+    """The binary star's first tree at full size, sampled where the walks
+    that pair sources with their reflections along one axis run: cells of
+    leaf targets next to refined sub-grids (their multipole sources) and of
+    non-leaf targets next to leaves (their point masses), forward of both
+    passes and the adjoint of a sparse L-bar on those cells."""
+    tree, rho = synth.config5_step(0)
+    leaves, nonleaves = _boundary_nodes(tree)
+    assert len(leaves) > 1000 and len(nonleaves) > 500
+    rng = np.random.default_rng(400)
+    tg = np.concatenate([
+        np.stack([rng.choice(leaves, 96), rng.integers(0, 512, 96)], 1),
+        np.stack([rng.choice(nonleaves, 96), rng.integers(0, 512, 96)], 1)]).astype(np.int32)
+    tg = np.unique(tg, axis=0)
+    g = ot.OTGrid.from_tree(tree)
+    Mh = orc.moments(tree, rho)
+    mh = np.ascontiguousarray(Mh[:, 0, :])
+    L, Lc = g.interactions(dev(Mh), dev(mh))
+    torch.cuda.synchronize()
+    r1 = orc.run_pass(tree, "multipole", M=Mh, targets=tg)
+    r2 = orc.run_pass(tree, "monopole", m=mh, targets=tg)
+    assert_parity(host(L)[tg[:, 0], :, tg[:, 1]], r1["L"] + r2["L"], fwd_scale(r1) + fwd_scale(r2), what="L", kind="L")
+    assert_parity(host(Lc)[tg[:, 0], :, tg[:, 1]], r1["Lc"], fwd_scale(r1, lc=True), what="Lc")
+    Lbar = np.zeros((tree.n, 20, 512))
+    Lbar[tg[:, 0], :, tg[:, 1]] = rng.standard_normal((len(tg), 20))
+    Mb, mb = g.backward(dev(Lbar))
+    torch.cuda.synchronize()
+    Mo, SM = adjoint_with_scale(orc, tree, "multipole", Lbar, targets=tg)
+    mo, Sm = adjoint_with_scale(orc, tree, "monopole", Lbar, targets=tg)
+    assert_parity(host(Mb), Mo, SM, what="Mbar", kind="Mbar")
+    assert_parity(host(mb), mo, Sm, what="mbar")
+    g.check()
+    g.close()
