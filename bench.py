@@ -270,8 +270,7 @@ NOMINAL_SM_MHZ = 2032.0
 # kernel as it is now, keyed by (workload, launch, tile); a key not here
 # reports null.
 DRAM_BYTES = {
-    ("binary", "multipole", (8, 1)): 34_601_091_072 + 242_455_296,
-    ("polytrope64", "multipole", (8, 2)): 178_241_024 + 32_380_416,
+    ("binary", "multipole", (8, 1)): 62_876_049_664 + 257_986_048,
 }
 
 

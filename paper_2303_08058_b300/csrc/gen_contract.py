@@ -333,6 +333,66 @@ def mclass_fwd_x_code(Z, ang):
     return name, "".join(lines), n_add, n_fma
 
 
+def xy_plan(Z, need):
+    """the transform with the x and y stages prebuilt (order x, y, then z):
+    the stage-2 values to load and the z stage's butterflies"""
+    order = [0, 1] + ([2] if not (Z >> 2) & 1 else [])
+    needed = [None] * (len(order) + 1)
+    needed[len(order)] = set(need)
+    for t in range(len(order), 0, -1):
+        b = 1 << order[t - 1]
+        prev = set()
+        for x in needed[t]:
+            prev |= {x & ~b, x | b}
+        needed[t - 1] = prev
+    ops = []
+    for t in range(3, len(order) + 1):
+        b = 1 << order[t - 1]
+        for x in sorted(needed[t]):
+            lo, hi = x & ~b, x | b
+            ops.append((t, x, "+" if x == lo else "-", lo, hi))
+    return sorted(needed[2]), ops, len(order)
+
+
+def mclass_fwd_xy_code(Z, ang):
+    """ot_mclass_fwd_code with the x and y stages prebuilt: for a class with
+    a, b > 0 (Z without bits 0, 1) whose (x, y) members are all present or all
+    absent at each z sign, the transforms over x and y of the members' reduced
+    moments at the positions q = t + (0, 0, +-c) are read from a table built
+    once per call (pos[r] points at component 0's channel 0 at the z member r,
+    0 for +c and 1 for -c; channel ch = x parity + 2 y parity of component k
+    at pos[r] + 4 k NCELL + ch: a cell's four channels are adjacent and read
+    as two 16-byte pairs)"""
+    assert not (Z & 3)
+    name = f"ot_mclass_fwd_xy_z{Z}" + ("_ang" if ang else "")
+    lines = [f"__device__ __forceinline__ void {name}(double (&a)[16], double (&c)[3], double (&t4)[9],\n"
+             f"    const double* const (&pos)[2], const double* __restrict__ row) {{\n"]
+    terms = mclass_terms(Z, ang)
+    n_add = n_fma = 0
+    for k in range(16):
+        if not terms[k]:
+            continue
+        lines.append("  {\n")
+        need = sorted({pi for (pi, _, _, _) in terms[k]})
+        loads, ops, nst = xy_plan(Z, need)
+        pairs = sorted({((x >> 2) & 1, (x >> 1) & 1) for x in loads})
+        for (r, h) in pairs:
+            lines.append(f"    const double2 p{r}{h} = pos[{r}] ? __ldg(reinterpret_cast<const double2*>(pos[{r}] + "
+                         f"{4 * k} * NCELL + {2 * h})) : make_double2(0.0, 0.0);\n")
+        for x in loads:
+            r, h = (x >> 2) & 1, (x >> 1) & 1
+            lines.append(f"    const double v2_{x} = p{r}{h}.{'y' if x & 1 else 'x'};\n")
+        for (t, x, op, lo, hi) in ops:
+            lines.append(f"    const double v{t}_{x} = v{t - 1}_{lo} {op} v{t - 1}_{hi};\n")
+            n_add += 1
+        for (pi, kind, idx, di) in terms[k]:
+            lines.append(f"    {kind}[{idx}] = fma(v{nst}_{pi}, __ldg(row + {di}), {kind}[{idx}]);\n")
+            n_fma += 1
+        lines.append("  }\n")
+    lines.append("}\n\n")
+    return name, "".join(lines), n_add, n_fma
+
+
 def mclass_adj_code(Z):
     """the transpose (multipole gather by source): the members are targets,
     per target component j the transform of their reduced L-bar feeds
@@ -678,6 +738,19 @@ def emit():
           f"    if constexpr (ANG) ot_mclass_fwd_x_z{Z}_ang(a, c, t4, pos, row);\n"
           f"    else ot_mclass_fwd_x_z{Z}(a, c, t4, pos, row);\n  }}\n")
     w("}\n\n")
+    for Z in (0, 4):
+        for ang in (False, True):
+            name, code, n_add, n_fma = mclass_fwd_xy_code(Z, ang)
+            w(f"// x and y stages prebuilt: {n_add} adds + {n_fma} FMAs\n")
+            w(code)
+    w("template <int Z, bool ANG>\n"
+      "__device__ __forceinline__ void ot_mclass_fwd_xy(double (&a)[16], double (&c)[3], double (&t4)[9],\n"
+      "                                                 const double* const (&pos)[2], const double* __restrict__ row) {\n")
+    for i, Z in enumerate((0, 4)):
+        w(f"  {'if' if i == 0 else 'else if'} constexpr (Z == {Z}) {{\n"
+          f"    if constexpr (ANG) ot_mclass_fwd_xy_z{Z}_ang(a, c, t4, pos, row);\n"
+          f"    else ot_mclass_fwd_xy_z{Z}(a, c, t4, pos, row);\n  }}\n")
+    w("}\n\n")
     for Z in range(7):
         name, code, n_add, n_fma = mclass_adj_code(Z)
         w(f"// adjoint: {n_add} adds + {n_fma} FMAs\n")
@@ -747,6 +820,10 @@ def emit_counts():
     xa = {(ang, Z): (mclass_fwd_x_code(Z, ang)[2] if not (Z & 1) else 0) for ang in (False, True) for Z in range(7)}
     out.append("constexpr int OT_MCLASS_X_ADDS[2][7] = {" + ", ".join(
         "{" + ", ".join(str(xa[ang, Z]) for Z in range(7)) + "}" for ang in (False, True)) + "};\n")
+    out.append("// FP64 adds of ot_mclass_fwd_xy_z<Z>[_ang] (x and y stages prebuilt; 0 for Z with bit 0 or 1), [ang][Z]\n")
+    xya = {(ang, Z): (mclass_fwd_xy_code(Z, ang)[2] if not (Z & 3) else 0) for ang in (False, True) for Z in range(7)}
+    out.append("constexpr int OT_MCLASS_XY_ADDS[2][7] = {" + ", ".join(
+        "{" + ", ".join(str(xya[ang, Z]) for Z in range(7)) + "}" for ang in (False, True)) + "};\n")
     ax = [mclass_adj_x_code(Z)[2] if not (Z & 1) else 0 for Z in range(7)]
     out.append("// FP64 adds of ot_mclass_adj_x_z<Z> (x stage prebuilt; 0 for Z with bit 0)\n")
     out.append("constexpr int OT_MCLASS_ADJ_X_ADDS[7] = {" + ", ".join(str(a) for a in ax) + "};\n")

@@ -84,6 +84,10 @@ struct Lists {
     // members at every z sign), which may read their first two stages from
     // the (x, y) table
     int cf_xy[8], cn_xy[8];
+    // the same for the multipole lists (far per parity, root): xy-complete
+    // entries at the start of the x-complete head, which may read their first
+    // two stages from the reduced moments' (x, y) table
+    int mf_xy[8], mr_xy[8];
     // a leaf target's multipole sources (refined neighbours) paired along
     // one axis A: per A, the far list of each parity (stride ap_len[A]) as
     // ap_pairs[A] entries o with o_A > 0 whose reflection along A is also in
@@ -131,6 +135,8 @@ struct FwdParams {
     const float2* Smf;     // the masses' table as double-float (hi, lo) pairs (double-float point masses)
     const double* Sxy;     // [M slot][49: (a - 1) 7 + b - 1][4][512]: the masses at c + (+-a, +-b, 0)
                            // transformed over x and y (null: not built)
+    const double* Sxym;    // [X slot][49][16][512][4]: the same for the reduced moments, component by
+                           // component, a cell's four channels adjacent (null: not built)
     const int* nslot;      // [n][27]
 };
 
@@ -244,6 +250,8 @@ cudaError_t launch_xbutterfly_masses_adjoint(const int2* ent, const int* xs, int
                                              int n_nodes, double* mbar, cudaStream_t s);
 cudaError_t launch_xybutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sxy,
                                       cudaStream_t s);
+cudaError_t launch_xybutterfly_moments(const int2* snb, int n_slots, const double* Mhat, int n_nodes, double* Sxym,
+                                       cudaStream_t s);
 cudaError_t launch_xbutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sm,
                                      cudaStream_t s);
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);

@@ -852,23 +852,74 @@ __device__ __forceinline__ void walk_mclasses_fwd_x(const int* __restrict__ list
     }
 }
 
+// xy-complete multipole classes (a, b > 0) of a node whose neighbours are
+// all multipole or empty: the first two transform stages of every source
+// component come from the moments' (x, y) table at the positions
+// t + (0, 0, +-c)
+template <int Z, bool ANG>
+__device__ __forceinline__ void walk_mclasses_fwd_xy(const int* __restrict__ list, int len, int tx, int ty, int tz,
+                                                     const int2* __restrict__ s_nb, const int* __restrict__ s_sl,
+                                                     const FwdParams& p, double (&acc)[16], double (&c)[3],
+                                                     double (&t4)[9], int item) {
+    static_assert((Z & 3) == 0, "the x and y stages need a, b > 0");
+    for (int k = 0; k < len; ++k) {
+        const int e = __ldg(list + k);
+        const int ox = e & 0xff, oy = (e >> 8) & 0xff, oz = (e >> 16) & 0xff;
+        const unsigned members = static_cast<unsigned>(e) >> 24;
+        const double* pos[2];
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            pos[r] = nullptr;
+            if ((4 * r) & Z) continue;
+            if ((members >> (4 * r)) & 1u) {
+                const int sz = r ? tz - oz : tz + oz;
+                const int nbi = nb_index(tx, ty, sz);
+                const int ks = checked_kind(p, s_nb[nbi], item);
+                const int slot = s_sl[nbi];
+                if (slot >= 0) {
+                    pos[r] = p.Sxym + (static_cast<size_t>((slot * 49 + (ox - 1) * 7 + oy - 1) * 16) * NCELL +
+                                       (tx & 7) + 8 * (ty & 7) + 64 * (sz & 7)) * 4;
+                    any = true;
+                } else if (ks != K_NONE) {
+                    report(p.status, 7, item);    // the node's flag promised a table slot for every region
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        ot_mclass_fwd_xy<Z, ANG>(acc, c, t4, pos, p.Dt + static_cast<size_t>(offset_row(ox, oy, oz)) * DROW);
+    }
+}
+
 template <bool ANG, int Z = 0, class CH>
 __device__ __forceinline__ void walk_mclasses_fwd_all(const int* __restrict__ list, const int (&zoff)[8],
-                                                      const int (&xc)[8], bool xpath, const CH& ch, int tx, int ty,
-                                                      int tz, const int2* __restrict__ s_nb, const int* __restrict__ s_sl, const FwdParams& p,
-                                                      double (&acc)[16], double (&c)[3], double (&t4)[9], int item) {
+                                                      const int (&xc)[8], const int (&xyc)[8], bool xpath,
+                                                      const CH& ch, int tx, int ty, int tz,
+                                                      const int2* __restrict__ s_nb, const int* __restrict__ s_sl,
+                                                      const FwdParams& p, double (&acc)[16], double (&c)[3],
+                                                      double (&t4)[9], int item) {
     const int len = zoff[Z + 1] - zoff[Z];
     int nx = 0;
     if constexpr ((Z & 1) == 0) {
         if (xpath) {
+            int nxy = 0;
+            if constexpr ((Z & 2) == 0) {
+                if (p.Sxym != nullptr) {
+                    nxy = xyc[Z];
+                    walk_mclasses_fwd_xy<Z, ANG>(list + zoff[Z] + ch.lo(nxy), ch.n(nxy), tx, ty, tz, s_nb, s_sl, p,
+                                                 acc, c, t4, item);
+                }
+            }
             nx = xc[Z];
-            walk_mclasses_fwd_x<Z, ANG>(list + zoff[Z] + ch.lo(nx), ch.n(nx), tx, ty, tz, s_nb, s_sl, p, acc, c, t4, item);
+            walk_mclasses_fwd_x<Z, ANG>(list + zoff[Z] + nxy + ch.lo(nx - nxy), ch.n(nx - nxy), tx, ty, tz, s_nb,
+                                        s_sl, p, acc, c, t4, item);
         }
     }
     walk_mclasses_fwd<Z, ANG>(list + zoff[Z] + nx + ch.lo(len - nx), ch.n(len - nx), tx, ty, tz, s_nb, p, acc, c, t4,
                               item);
     if constexpr (Z < 6)
-        walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, xc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, c, t4, item);
+        walk_mclasses_fwd_all<ANG, Z + 1>(list, zoff, xc, xyc, xpath, ch, tx, ty, tz, s_nb, s_sl, p, acc, c, t4,
+                                          item);
 }
 
 template <int MODE, bool PAIRED, int EMU, bool NEAR = false, bool PM = true, bool NEG = false>
@@ -1330,15 +1381,16 @@ __global__ void __launch_bounds__(256, MINB) forward_kernel(const FwdParams p, i
             const int2* nb = s_nb[warp];
             if (MODE & 1) {
                 const bool root = level == 0;
-                int zo[8], xc[8];
+                int zo[8], xc[8], xyc[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     zo[q] = root ? p.L.mr_z[q] : p.L.mf_z[q];
                     xc[q] = root ? p.L.mr_x[q] : p.L.mf_x[q];
+                    xyc[q] = root ? p.L.mr_xy[q] : p.L.mf_xy[q];
                 }
                 const bool xpath = p.Sx != nullptr && (info & NI_XMULTI);
                 const int* ml = p.L.lists + (root ? p.L.mr_off : p.L.mf_off + par * p.L.mf_stride);
-                walk_mclasses_fwd_all<true>(ml, zo, xc, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, it);
+                walk_mclasses_fwd_all<true>(ml, zo, xc, xyc, xpath, ch, tx, ty, tz, nb, s_sl[warp], p, a, c, t4, it);
                 ml += zo[7];
                 const int np = root ? p.L.mr_pairs : p.L.mf_pairs, ns = root ? 0 : p.L.mf_singles;
                 walk_forward<1, true, EMU>(ml + ch.lo(np), ch.n(np), true, tx, ty, tz, nb, p, a, c, t4, f, it);
@@ -3657,6 +3709,74 @@ cudaError_t launch_xybutterfly_masses(const int2* snb, int n_slots, const double
                                       cudaStream_t s) {
     if (n_slots == 0) return cudaSuccess;
     xybutterfly_masses_kernel<<<blocks_for(1LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, m, n_nodes, Sxy);
+    return counted(cudaGetLastError());
+}
+
+// (x, y) butterflies of the reduced moments, component by component: for
+// every cell c of a slot's region, a, b = 1..7 and component k, the four
+// transforms over x and y of Mhat_k at c + (+-a, +-b, 0) (multipole cells;
+// 0 elsewhere), in the masses' table's channel order, a cell's four channels
+// adjacent.  A block of 256
+// threads covers four z layers of one slot's region; per component it stages
+// the 3 x 3 regions' values in shared memory, per a it forms the x stage (as
+// the x table does, the same bits) at the rows y - 7 .. y + 14, and each
+// thread runs the y stage of its cell.
+__global__ void xybutterfly_moments_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ Mhat,
+                                           int n_nodes, double* __restrict__ Sxym) {
+    constexpr int ROWS = 22;                  // y' = -7 .. 14
+    __shared__ double sm[9][256];
+    __shared__ double sx[2][4][ROWS][8];      // [sum, difference][z layer][y' + 7][x]
+    const long long first = static_cast<long long>(blockIdx.x) * blockDim.x;
+    const int slot = static_cast<int>(first / NCELL);
+    if (slot >= n_slots) return;              // whole blocks: a slot is two blocks of 256 cells
+    const int z0 = static_cast<int>(first % NCELL) >> 6;          // 0 or 4
+    const int2* nb = snb + static_cast<size_t>(slot) * 27 + 9;    // the z = 0 layer of the regions
+    const int cell = static_cast<int>((first + threadIdx.x) % NCELL);
+    const int x = cell & 7, y = (cell >> 3) & 7, zl = (cell >> 6) - z0;
+    // layout [slot][(a - 1) 7 + b - 1][k][cell][channel]: a cell's four
+    // channels adjacent (one 32-byte sector)
+    double* out = Sxym + (static_cast<size_t>(slot) * 49 * 16 * NCELL + cell) * 4;
+#pragma unroll 1
+    for (int k = 0; k < 16; ++k) {
+        __syncthreads();                      // the previous component's reads of sm are done
+        for (int t = threadIdx.x; t < 9 * 256; t += blockDim.x) {
+            const int r = t >> 8, c = t & 255;
+            const int2 e = __ldg(nb + r);
+            sm[r][c] = ((e.y & 3) == K_MULTI && static_cast<unsigned>(e.x) < static_cast<unsigned>(n_nodes))
+                           ? __ldg(Mhat + (static_cast<size_t>(e.x) * NRED + k) * NCELL + c + 64 * z0)
+                           : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int a = 1; a <= 7; ++a) {
+            for (int t = threadIdx.x; t < 4 * ROWS * 8; t += blockDim.x) {
+                const int px = t & 7, row = (t >> 3) % ROWS, pz = t / (ROWS * 8);
+                const int py = row - 7, xp = px + a, xm = px - a;
+                const double vp = sm[((xp + 8) >> 3) + 3 * ((py + 8) >> 3)][(xp & 7) + 8 * (py & 7) + 64 * pz];
+                const double vm = sm[((xm + 8) >> 3) + 3 * ((py + 8) >> 3)][(xm & 7) + 8 * (py & 7) + 64 * pz];
+                sx[0][pz][row][px] = vp + vm;
+                sx[1][pz][row][px] = vp - vm;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 1; b <= 7; ++b) {
+                const double u0 = sx[0][zl][y + b + 7][x], u1 = sx[1][zl][y + b + 7][x];
+                const double u2 = sx[0][zl][y - b + 7][x], u3 = sx[1][zl][y - b + 7][x];
+                double2* o = reinterpret_cast<double2*>(
+                    out + (static_cast<size_t>((a - 1) * 7 + b - 1) * 16 + k) * NCELL * 4);
+                o[0] = make_double2(u0 + u2, u1 + u3);
+                o[1] = make_double2(u0 - u2, u1 - u3);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_xybutterfly_moments(const int2* snb, int n_slots, const double* Mhat, int n_nodes, double* Sxym,
+                                       cudaStream_t s) {
+    if (n_slots == 0) return cudaSuccess;
+    xybutterfly_moments_kernel<<<blocks_for(1LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, Mhat, n_nodes,
+                                                                                       Sxym);
     return counted(cudaGetLastError());
 }
 

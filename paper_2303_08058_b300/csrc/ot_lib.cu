@@ -274,6 +274,7 @@ struct ot_grid {
     int n_slotXY = 0;                   // M slots [0, n_slotXY): the leaves' z columns, the (x, y) table's
     int n_slotXyz = 0;                  // X slots [0, n_slotXyz): the yz planes of the non-leaf nodes, the
                                         // x tables' (read only at t + (0, +-b, +-c))
+    int n_slotXz = 0;                   // X slots [0, n_slotXz): their z columns, the moments' (x, y) table's
     int* d_nslot = nullptr;
     int2* d_snbM = nullptr;
     int2* d_snbX = nullptr;
@@ -285,6 +286,8 @@ struct ot_grid {
     double* d_Sx = nullptr;             // [X slot][7][16][2][512]: reduced moments
     double* d_Sm = nullptr;             // [M slot][7][2][512]: masses
     double* d_Sxy = nullptr;            // [M slot][49][4][512]: the masses' (x, y) butterflies
+    double* d_Sxym = nullptr;           // [X slot][49][16][512][4]: the reduced moments' (x, y) butterflies
+    bool use_xym = false;               // the moments' (x, y) table fits (its size is capped)
     bool use_xy = false;                // the (x, y) table fits (its size is capped)
     float2* d_Smf = nullptr;            // the masses' table as double-float pairs
     double* d_Tx = nullptr;             // [X slot][7][16][2][512]: reduced L-bar of real cells
@@ -604,6 +607,11 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         Lh.cf_x[z] = (z & 1) ? 0 : xcount(cfar[0][z]);
         Lh.cn_x[z] = (z & 1) ? 0 : xcount(cnear[z]);
         Lh.mf_x[z] = (z & 1) ? 0 : xcount(mfar[0][z]);
+        Lh.mf_xy[z] = (z & 3) ? 0 : xycount(mfar[0][z]);
+        Lh.mr_xy[z] = (z & 3) ? 0 : xycount(mroot[z]);
+        for (int p = 1; p < 8; ++p)
+            if (!(z & 3) && xycount(mfar[p][z]) != Lh.mf_xy[z])
+                return fail(OT_EINVAL, "internal: parity class stencils differ in shape");
         Lh.mr_x[z] = (z & 1) ? 0 : xcount(mroot[z]);
         for (int p = 1; p < 8; ++p)
             if (((z & 1) == 0) && (xcount(cfar[p][z]) != Lh.cf_x[z] || xcount(mfar[p][z]) != Lh.mf_x[z]))
@@ -818,9 +826,21 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             }
         }
         g->n_slotXY = static_cast<int>(regM.size());
-        // space X likewise numbers first the regions in the yz planes of the
-        // non-leaf nodes (neighbours with dx = 0): the x tables of reduced
-        // moments and L-bar are read only at t + (0, +-b, +-c)
+        // space X likewise numbers first the regions in the z columns of the
+        // non-leaf nodes (the moments' (x, y) table, read at t + (0, 0, +-c)),
+        // then the rest of their yz planes (neighbours with dx = 0): the x
+        // tables of reduced moments and L-bar are read only at t + (0, +-b, +-c)
+        for (int i = 0; i < n; ++i) {
+            if (g->is_leaf[i]) continue;
+            for (int j = 4; j < 27; j += 9) {
+                const int r = nreg[static_cast<size_t>(i) * 27 + j];
+                if (r >= 0 && slotX[r] < 0) {
+                    slotX[r] = static_cast<int>(regX.size());
+                    regX.push_back(r);
+                }
+            }
+        }
+        g->n_slotXz = static_cast<int>(regX.size());
         for (int i = 0; i < n; ++i) {
             if (g->is_leaf[i]) continue;
             for (int j = 1; j < 27; j += 3) {
@@ -931,6 +951,8 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     }
     // the (x, y) table of the masses takes 0.8 MB per slot: built up to 16 GiB
     g->use_xy = static_cast<double>(g->n_slotXY) * 49 * 4 * NCELL * sizeof(double) <= 16.0 * (1u << 30);
+    // the moments' (x, y) table takes 12.8 MB per slot: built up to 48 GiB
+    g->use_xym = static_cast<double>(g->n_slotXz) * 49 * 64 * NCELL * sizeof(double) <= 48.0 * (1u << 30);
 
     // --- exact pair counts, FLOPs and per-item costs ------------------------
     // For each (parity, half) warp pattern and list entry: which of the 27
@@ -1048,8 +1070,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
         cmem[cg].resize(cseg_len[cg]);
         const int* zx = cg == 0 ? g->Lh.cf_x : cg == 1 ? g->Lh.cn_x : cg == 2 ? g->Lh.mf_x : g->Lh.mr_x;
         const int* zz = cg == 0 ? g->Lh.cf_z : cg == 1 ? g->Lh.cn_z : cg == 2 ? g->Lh.mf_z : g->Lh.mr_z;
-        static const int none[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        const int* zxy = cg == 0 ? g->Lh.cf_xy : cg == 1 ? g->Lh.cn_xy : none;
+        const int* zxy = cg == 0 ? g->Lh.cf_xy : cg == 1 ? g->Lh.cn_xy : cg == 2 ? g->Lh.mf_xy : g->Lh.mr_xy;
         for (int ph = 0; ph < 16; ++ph) {
             const int par = ph >> 1, half = ph & 1;
             const int off = cg == 0 ? g->Lh.cf_off + par * g->Lh.cf_stride : cg == 1 ? g->Lh.cn_off
@@ -1072,8 +1093,13 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
                         cs = OT_MCLASS_ADJ_ADDS[Z] + OT_MCLASS_ADJ_FMAS[Z];
                         fl_f = OT_MCLASS_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z];
                         fl_s = OT_MCLASS_ADJ_ADDS[Z] + 2 * OT_MCLASS_ADJ_FMAS[Z];
-                        cfx = xe ? OT_MCLASS_X_ADDS[1][Z] + OT_MCLASS_FMAS[1][Z] : cf;
-                        fl_fx = xe ? OT_MCLASS_X_ADDS[1][Z] + 2 * OT_MCLASS_FMAS[1][Z] : fl_f;
+                        // the x stage prebuilt (x-complete head); the x and y
+                        // stages (its xy-complete head, a and b > 0)
+                        const bool xye = xe && !(Z & 2) && k - zz[Z] < zxy[Z] && g->use_xym;
+                        const int madds = xye ? OT_MCLASS_XY_ADDS[1][Z] : xe ? OT_MCLASS_X_ADDS[1][Z]
+                                                                              : OT_MCLASS_ADDS[1][Z];
+                        cfx = madds + OT_MCLASS_FMAS[1][Z];
+                        fl_fx = madds + 2 * OT_MCLASS_FMAS[1][Z];
                         csx = xe ? OT_MCLASS_ADJ_X_ADDS[Z] + OT_MCLASS_ADJ_FMAS[Z] : cs;
                         fl_sx = xe ? OT_MCLASS_ADJ_X_ADDS[Z] + 2 * OT_MCLASS_ADJ_FMAS[Z] : fl_s;
                     } else {
@@ -1825,6 +1851,9 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     if (g->use_xy &&
         (st = g->alloc(&g->d_Sxy, static_cast<size_t>(std::max(g->n_slotXY, 1)) * 49 * 4 * NCELL)) != OT_OK)
         return st;
+    if (g->use_xym &&
+        (st = g->alloc(&g->d_Sxym, static_cast<size_t>(std::max(g->n_slotXz, 1)) * 49 * 64 * NCELL)) != OT_OK)
+        return st;
     if ((st = g->alloc(&g->d_Lrbar, static_cast<size_t>(n) * NRED * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_vbar, static_cast<size_t>(std::max(g->nvirt, 1)) * NCELL)) != OT_OK) return st;
     if ((st = g->alloc(&g->d_Mb, static_cast<size_t>(n) * NCOMP * NCELL)) != OT_OK) return st;
@@ -1914,6 +1943,10 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
     if ((mode & 1) && g->precision != 2 && g->n_slotX > 0) {
         OT_CUDA(launch_xbutterfly_moments(g->d_snbX, g->n_slotXyz, g->d_Mhat, g->n, g->d_Sx, s));
         p.Sx = g->d_Sx;
+        if (g->use_xym) {
+            OT_CUDA(launch_xybutterfly_moments(g->d_snbX, g->n_slotXz, g->d_Mhat, g->n, g->d_Sxym, s));
+            p.Sxym = g->d_Sxym;
+        }
     }
     if ((mode & 2) && g->n_slotM > 0) {
         OT_CUDA(launch_xbutterfly_masses(g->d_snbM, g->n_slotM, m, g->n, g->d_Sm, s));
@@ -2508,6 +2541,7 @@ ot_status ot_completion_study(ot_grid* g, const double* M, const double* m, doub
     p.chunk_ctr = g->d_chunk_ctr;
     // and the x butterflies the warm-up built from the same M and m
     if (g->precision != 2 && g->n_slotX > 0) p.Sx = g->d_Sx;
+    if (g->precision != 2 && g->use_xym && g->n_slotXz > 0) p.Sxym = g->d_Sxym;
     if (g->precision == 0 && g->n_slotM > 0) p.Sm = g->d_Sm;
     if (g->precision == 0 && g->n_slotM > 0 && g->use_xy) p.Sxy = g->d_Sxy;
     if (g->precision != 0 && g->n_slotM > 0) p.Smf = g->d_Smf;
