@@ -270,7 +270,8 @@ NOMINAL_SM_MHZ = 2032.0
 # kernel as it is now, keyed by (workload, launch, tile); a key not here
 # reports null.
 DRAM_BYTES = {
-    ("binary", "multipole", (8, 1)): 62_876_049_664 + 257_986_048,
+    ("binary", "multipole", (8, 1)): 61_975_926_528 + 255_350_272,
+    ("polytrope64", "multipole", (8, 2)): 3_285_455_616 + 154_134_272,
 }
 
 
