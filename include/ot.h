@@ -141,7 +141,15 @@ typedef struct {
 } ot_grid_info_t;
 
 /* Builds neighbour tables, stencils, the derivative table, work lists and the
- * scratch arena on the current device.  `stream` orders the uploads.
+ * scratch arena on the current device.  `stream` orders the uploads.  The
+ * arena holds, besides per-sub-grid scratch, the tables the passes rebuild
+ * each call: x butterflies of the reduced moments, L-bar and the masses
+ * (0.9 MB, 0.9 MB and 57 KB per region slot), the masses' (x, y) table
+ * (0.8 MB per slot in the leaves' z columns, used up to 16 GiB) and the
+ * reduced moments' (x, y) table (12.8 MB per slot in the non-leaf nodes' z
+ * columns, used up to 48 GiB; about 21 GB on a 9,500-sub-grid octree);
+ * a table over its cap is not allocated and its classes take the
+ * x-butterfly walk instead.
  * Errors: OT_EINVAL (bad description; also a tree that is not 2:1 balanced
  * in the sense the coarse-leaf rule needs: a child of a refined neighbour of
  * a leaf sub-grid that touches the leaf must itself be a leaf; also a
