@@ -299,17 +299,18 @@ def fp64_peak(ot, dev, stream):
 
 def roofline_block(launches, peak_inst, probe_cfg, sm_mhz, workload, info, pairs_fwd, fwd_ms, adj_ms):
     """The dominant launch's roofline in FP64 pipe thread-instructions per
-    second against the probe's measured rate, with the nominal and the
-    survey's per-pair FLOP counts beside it."""
+    second against the probe's measured rate, with the nominal peak and the
+    naive contraction's per-pair FLOP counts beside it."""
     tile = (info["warps_per_block"], info["blocks_per_sm"])
     dom = max(launches, key=lambda k: launches[k]["ms"])
     L = launches[dom]
     peak = peak_inst / 1e12
     nominal = NOMINAL_FP64_TFLOPS / 2 * (sm_mhz or NOMINAL_SM_MHZ) / NOMINAL_SM_MHZ
-    # the survey's per-pair FLOP counts: a multipole pair 84 FMAs (+40 for
-    # the angular term at non-leaf targets), a point-mass pair 20 FMAs; the
-    # adjoint the same; 2 flops per FMA
-    sec8d_fwd = 2 * (84 * info["pairs_multipole"] + 40 * info["pairs_angular"] + 20 * info["pairs_monopole"])
+    # the naive contraction's per-pair FLOP counts (all 20 components, no
+    # pairing, no classes): a multipole pair 84 FMAs (+40 for the angular
+    # term at non-leaf targets), a point-mass pair 20 FMAs; the adjoint the
+    # same; 2 flops per FMA
+    naive_fwd = 2 * (84 * info["pairs_multipole"] + 40 * info["pairs_angular"] + 20 * info["pairs_monopole"])
     traffic = DRAM_BYTES.get((workload, dom, tile))
     return {
         "bound": "alu", "kernel": L["kernel"], "launch": dom,
@@ -327,12 +328,12 @@ def roofline_block(launches, peak_inst, probe_cfg, sm_mhz, workload, info, pairs
                              f"at {NOMINAL_SM_MHZ:.0f} MHz, scaled to the median SM clock of the timed region")},
         "launches": {k: {"ms": v["ms"], "achieved": v["achieved"], "frac": v["achieved"] / peak,
                          "executed_frac": v["executed"] / peak} for k, v in launches.items()},
-        "sec8d": {"fwd_flop": sec8d_fwd, "forward_tflops": sec8d_fwd / (fwd_ms * 1e-3) / 1e12,
-                  "adjoint_tflops": sec8d_fwd / (adj_ms * 1e-3) / 1e12,
-                  "note": ("effective rate: the survey's per-pair counts (multipole 168 flop + 80 for the angular "
-                           "term, point mass 40 flop) over the forward / adjoint time; above the FP64 peak because "
-                           "the kernels share one derivative row among up to 8 reflected sources (reflection "
-                           "classes), the traceless reduction and the +-o pairing")},
+        "naive_flops": {"fwd_flop": naive_fwd, "forward_tflops": naive_fwd / (fwd_ms * 1e-3) / 1e12,
+                        "adjoint_tflops": naive_fwd / (adj_ms * 1e-3) / 1e12,
+                        "note": ("effective rate: the naive per-pair counts (multipole 168 flop + 80 for the angular "
+                                 "term, point mass 40 flop) over the forward / adjoint time; above the FP64 peak "
+                                 "because the kernels share one derivative row among up to 8 reflected sources "
+                                 "(reflection classes), the traceless reduction and the pairings")},
     }
 
 
