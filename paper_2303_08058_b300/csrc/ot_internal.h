@@ -250,8 +250,7 @@ cudaError_t launch_xbutterfly_masses_adjoint(const int2* ent, const int* xs, int
                                              int n_nodes, double* mbar, cudaStream_t s);
 cudaError_t launch_xybutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sxy,
                                       cudaStream_t s);
-cudaError_t launch_xybutterfly_moments(const int2* snb, int n_slots, const double* Mhat, int n_nodes, double* Sxym,
-                                       cudaStream_t s);
+cudaError_t launch_xybutterfly_moments(const int* ys, int n_slots, const double* Sx, double* Sxym, cudaStream_t s);
 cudaError_t launch_xbutterfly_masses(const int2* snb, int n_slots, const double* m, int n_nodes, double* Sm,
                                      cudaStream_t s);
 cudaError_t launch_prescale_adjoint(const PrepParams& p, cudaStream_t s);

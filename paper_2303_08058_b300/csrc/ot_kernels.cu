@@ -3716,67 +3716,53 @@ cudaError_t launch_xybutterfly_masses(const int2* snb, int n_slots, const double
 // every cell c of a slot's region, a, b = 1..7 and component k, the four
 // transforms over x and y of Mhat_k at c + (+-a, +-b, 0) (multipole cells;
 // 0 elsewhere), in the masses' table's channel order, a cell's four channels
-// adjacent.  A block of 256
-// threads covers four z layers of one slot's region; per component it stages
-// the 3 x 3 regions' values in shared memory, per a it forms the x stage (as
-// the x table does, the same bits) at the rows y - 7 .. y + 14, and each
-// thread runs the y stage of its cell.
-__global__ void xybutterfly_moments_kernel(const int2* __restrict__ snb, int n_slots, const double* __restrict__ Mhat,
-                                           int n_nodes, double* __restrict__ Sxym) {
-    constexpr int ROWS = 22;                  // y' = -7 .. 14
-    __shared__ double sm[9][256];
-    __shared__ double sx[2][4][ROWS][8];      // [sum, difference][z layer][y' + 7][x]
-    const long long first = static_cast<long long>(blockIdx.x) * blockDim.x;
-    const int slot = static_cast<int>(first / NCELL);
-    if (slot >= n_slots) return;              // whole blocks: a slot is two blocks of 256 cells
-    const int z0 = static_cast<int>(first % NCELL) >> 6;          // 0 or 4
-    const int2* nb = snb + static_cast<size_t>(slot) * 27 + 9;    // the z = 0 layer of the regions
-    const int cell = static_cast<int>((first + threadIdx.x) % NCELL);
-    const int x = cell & 7, y = (cell >> 3) & 7, zl = (cell >> 6) - z0;
-    // layout [slot][(a - 1) 7 + b - 1][k][cell][channel]: a cell's four
-    // channels adjacent (one 32-byte sector)
+// adjacent.  Built from the x table (the y stage only: its sums and
+// differences at c + (0, +-b, 0) read from the slots of the regions at y-1,
+// y, y+1, so the same bits as a transform from the moments); a thread owns
+// one cell, and a block's cells share the x-table rows they read through L1.
+__global__ void xybutterfly_moments_kernel(const int* __restrict__ ys, int n_slots, const double* __restrict__ Sx,
+                                           double* __restrict__ Sxym) {
+    const long long gid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (gid >= 1LL * NCELL * n_slots) return;
+    const int slot = static_cast<int>(gid / NCELL);
+    const int cell = static_cast<int>(gid % NCELL);
+    const int x = cell & 7, y = (cell >> 3) & 7, z = cell >> 6;
+    const int s_lo = __ldg(ys + 3 * slot), s_mid = __ldg(ys + 3 * slot + 1), s_hi = __ldg(ys + 3 * slot + 2);
+    // layout [slot][(a - 1) 7 + b - 1][k][cell][channel]
     double* out = Sxym + (static_cast<size_t>(slot) * 49 * 16 * NCELL + cell) * 4;
 #pragma unroll 1
-    for (int k = 0; k < 16; ++k) {
-        __syncthreads();                      // the previous component's reads of sm are done
-        for (int t = threadIdx.x; t < 9 * 256; t += blockDim.x) {
-            const int r = t >> 8, c = t & 255;
-            const int2 e = __ldg(nb + r);
-            sm[r][c] = ((e.y & 3) == K_MULTI && static_cast<unsigned>(e.x) < static_cast<unsigned>(n_nodes))
-                           ? __ldg(Mhat + (static_cast<size_t>(e.x) * NRED + k) * NCELL + c + 64 * z0)
-                           : 0.0;
-        }
-        __syncthreads();
+    for (int a = 1; a <= 7; ++a) {
 #pragma unroll 1
-        for (int a = 1; a <= 7; ++a) {
-            for (int t = threadIdx.x; t < 4 * ROWS * 8; t += blockDim.x) {
-                const int px = t & 7, row = (t >> 3) % ROWS, pz = t / (ROWS * 8);
-                const int py = row - 7, xp = px + a, xm = px - a;
-                const double vp = sm[((xp + 8) >> 3) + 3 * ((py + 8) >> 3)][(xp & 7) + 8 * (py & 7) + 64 * pz];
-                const double vm = sm[((xm + 8) >> 3) + 3 * ((py + 8) >> 3)][(xm & 7) + 8 * (py & 7) + 64 * pz];
-                sx[0][pz][row][px] = vp + vm;
-                sx[1][pz][row][px] = vp - vm;
-            }
-            __syncthreads();
+        for (int k = 0; k < 16; ++k) {
 #pragma unroll
             for (int b = 1; b <= 7; ++b) {
-                const double u0 = sx[0][zl][y + b + 7][x], u1 = sx[1][zl][y + b + 7][x];
-                const double u2 = sx[0][zl][y - b + 7][x], u3 = sx[1][zl][y - b + 7][x];
+                const int yp = y + b, ym = y - b;
+                const int sp = yp >= 8 ? s_hi : s_mid, sm = ym < 0 ? s_lo : s_mid;
+                double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+                if (sp >= 0) {
+                    const double* q = Sx + (static_cast<size_t>(sp * 7 + a - 1) * 32 + 2 * k) * NCELL + x +
+                                      8 * (yp & 7) + 64 * z;
+                    u0 = __ldg(q);
+                    u1 = __ldg(q + NCELL);
+                }
+                if (sm >= 0) {
+                    const double* q = Sx + (static_cast<size_t>(sm * 7 + a - 1) * 32 + 2 * k) * NCELL + x +
+                                      8 * (ym & 7) + 64 * z;
+                    u2 = __ldg(q);
+                    u3 = __ldg(q + NCELL);
+                }
                 double2* o = reinterpret_cast<double2*>(
                     out + (static_cast<size_t>((a - 1) * 7 + b - 1) * 16 + k) * NCELL * 4);
                 o[0] = make_double2(u0 + u2, u1 + u3);
                 o[1] = make_double2(u0 - u2, u1 - u3);
             }
-            __syncthreads();
         }
     }
 }
 
-cudaError_t launch_xybutterfly_moments(const int2* snb, int n_slots, const double* Mhat, int n_nodes, double* Sxym,
-                                       cudaStream_t s) {
+cudaError_t launch_xybutterfly_moments(const int* ys, int n_slots, const double* Sx, double* Sxym, cudaStream_t s) {
     if (n_slots == 0) return cudaSuccess;
-    xybutterfly_moments_kernel<<<blocks_for(1LL * NCELL * n_slots, 256), 256, 0, s>>>(snb, n_slots, Mhat, n_nodes,
-                                                                                       Sxym);
+    xybutterfly_moments_kernel<<<blocks_for(1LL * NCELL * n_slots, 256), 256, 0, s>>>(ys, n_slots, Sx, Sxym);
     return counted(cudaGetLastError());
 }
 

@@ -280,6 +280,8 @@ struct ot_grid {
     int2* d_snbX = nullptr;
     std::vector<int2> mem_ent;          // point-mass regions of M: own entry (leaf node or virtual block)
     std::vector<int> mem_xs;            // [member][3]: M slots of the regions at x-1, x, x+1 (-1: none)
+    std::vector<int> xym_ys;            // [X slot < n_slotXz][3]: X slots of the regions at y-1, y, y+1
+    int* d_xym_ys = nullptr;
     int2* d_mem_ent = nullptr;
     int* d_mem_xs = nullptr;
     int* d_leaf = nullptr;              // childless nodes (cube moments)
@@ -941,6 +943,33 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
             }
             g->mem_ent.push_back(self);
             g->mem_xs.insert(g->mem_xs.end(), xs, xs + 3);
+        }
+        // the moments' (x, y) table is built from the x table: for each of
+        // its slots (the z columns of the non-leaf nodes) the X slots of the
+        // regions at y-1, y, y+1, all in the yz planes the x table covers
+        g->xym_ys.assign(static_cast<size_t>(std::max(g->n_slotXz, 1)) * 3, -1);
+        for (int k = 0; k < g->n_slotXz; ++k) {
+            const int r = regX[k];
+            long q[3];
+            int lvl;
+            if (r < n) {
+                lvl = desc->level[r];
+                for (int a = 0; a < 3; ++a) q[a] = desc->coord[3 * r + a];
+            } else {
+                lvl = vnodes[r - n].level;
+                for (int a = 0; a < 3; ++a) q[a] = vnodes[r - n].q[a];
+            }
+            for (int dy = -1; dy <= 1; ++dy) {
+                int rr = B.find(lvl, q[0], q[1] + dy, q[2]);
+                if (rr < 0) {
+                    auto it = vindex.find(std::make_tuple(lvl, q[0], q[1] + dy, q[2]));
+                    if (it != vindex.end()) rr = n + it->second;
+                }
+                if (rr >= 0 && slotX[rr] >= 0 && slotX[rr] < g->n_slotXyz)
+                    g->xym_ys[static_cast<size_t>(k) * 3 + dy + 1] = slotX[rr];
+            }
+            if (g->xym_ys[static_cast<size_t>(k) * 3 + 1] != k)
+                return fail(OT_EINVAL, "internal: a z-column slot is not its own y neighbour");
         }
     }
     for (int i = 0; i < n; ++i) {
@@ -1834,6 +1863,7 @@ static ot_status build_grid(ot_grid* g, const ot_grid_desc* desc, cudaStream_t s
     UP(g->d_snbX, g->snbX);
     UP(g->d_mem_ent, g->mem_ent);
     UP(g->d_mem_xs, g->mem_xs);
+    UP(g->d_xym_ys, g->xym_ys);
     for (auto& L : g->m2m) {
         UP(L.d_parents, L.parents);
         UP(L.d_children, L.children);
@@ -1944,7 +1974,7 @@ static ot_status enqueue_forward(ot_grid* g, int mode, const double* M, const do
         OT_CUDA(launch_xbutterfly_moments(g->d_snbX, g->n_slotXyz, g->d_Mhat, g->n, g->d_Sx, s));
         p.Sx = g->d_Sx;
         if (g->use_xym) {
-            OT_CUDA(launch_xybutterfly_moments(g->d_snbX, g->n_slotXz, g->d_Mhat, g->n, g->d_Sxym, s));
+            OT_CUDA(launch_xybutterfly_moments(g->d_xym_ys, g->n_slotXz, g->d_Sx, g->d_Sxym, s));
             p.Sxym = g->d_Sxym;
         }
     }
