@@ -88,8 +88,9 @@ struct Lists {
     // entries at the start of the x-complete head, which may read their first
     // two stages from the reduced moments' (x, y) table
     int mf_xy[8], mr_xy[8];
-    // a leaf target's multipole sources (refined neighbours) paired along
-    // one axis A: per A, the far list of each parity (stride ap_len[A]) as
+    // a leaf target's multipole sources (refined neighbours) and a non-leaf
+    // target's point masses (leaf neighbours) paired along one axis A: per
+    // A, the far list of each parity (stride ap_len[A]) as
     // ap_pairs[A] entries o with o_A > 0 whose reflection along A is also in
     // the list, then the remaining offsets as singles
     int ap_off[3], ap_len[3], ap_pairs[3];
@@ -224,10 +225,11 @@ constexpr int NI_XGATHER = 1 << 11;
 // halves (0 z, 1 x, 2 y): the axis of the node's faces whose neighbours hold
 // no source of its passes, so that a warp's lanes reach such a face together
 constexpr int NI_SLAB_SHIFT = 13;
-// bits 15-16: for a leaf node, the axis (0 x, 1 y, 2 z) along which its
-// multipole sources pair with their reflections: the axis with the fewest
-// faces on refined neighbours, so that both members of a pair tend to lie
-// in the same refined neighbour
+// bits 15-16: the axis (0 x, 1 y, 2 z) along which a node's sources of the
+// other kind pair with their reflections (a leaf node's multipole sources, a
+// non-leaf node's point masses): the axis with the fewest faces on
+// neighbours holding such sources, so that both members of a pair tend to
+// lie in the same neighbour
 constexpr int NI_APAIR_SHIFT = 15;
 
 // launchers (ot_kernels.cu)
